@@ -1,0 +1,34 @@
+"""FP64 CPU oracle for the pressure-correction Poisson solve on the Jacobi-transformed shell.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It shares
+no code with the CUDA library (``paper_2305_17875_gb300``) and imports nothing
+from it.
+
+Every function is plain numpy / scipy in float64 and follows the paper:
+
+* ``grid``      - mapping (Section 2), radial clustering (Eq. stretching) and the
+                  five-step face metric (Section 3.2, Eqs. jacobi/skewness).
+* ``operator``  - the conservative discretisation of d_p(G_pq d_q phi)
+                  (Section 3.3, Eqs. PC_8, PC_term1-3), assembled as a sparse matrix.
+* ``mg``        - geometric multigrid on that operator (the paper's own solver is
+                  HYPRE SMG, Section 3.6; the cycle here is this library's design,
+                  restated plainly so every GPU step has a CPU twin).
+* ``direct``    - bordered sparse direct solve of the same system (tiny grids).
+* ``mms``       - manufactured solutions with closed-form Laplacians (pins only).
+
+Parity status: every function is pinned by a ``-m "not gpu"`` test except the
+multigrid convergence factor, which the paper does not give
+(parity unpinned: convergence factor only; the converged answer is pinned by
+the direct solve).
+"""
+
+from .grid import Shell, shell, face_metrics, cell_volume, vertex, analytic_face_metrics
+from .operator import assemble, apply_rows
+from . import mg, direct
+
+__all__ = [
+    "Shell", "shell", "face_metrics", "cell_volume", "vertex", "analytic_face_metrics",
+    "assemble", "apply_rows", "mg", "direct",
+]
