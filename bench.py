@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the shell pressure-correction Poisson solve on one GB300 (or N replicas).
+
+A step is one whole solve from a cold start (x = 0) to 1e-10 relative
+residual of the 128 x 128 x 256 tanh-stretched sphere workload (RHS on the
+device, hierarchy set up before timing), with L2 flushed (256 MB write)
+before every step.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(a bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine-grid DOF/s to 1e-10 rel. residual, FP32-refined vs FP64 MG; HBM GB/s; p99 ms"
+UNIT = "DOF/s"
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
+PREC_NAME = {0: "plain FP64 multigrid", 1: "FP32 V-cycles inside FP64 refinement",
+             2: "FP16-coefficient FP32 V-cycles inside FP64 refinement"}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="single_sphere_128")
+    p.add_argument("--precision", default="fp32", choices=list(PREC))
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- peaks / profiles
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_17875_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision, slot):
+    """DRAM bytes per launch of the slot's kernel from the committed ncu
+    summary, or None when absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(f"{workload}/{precision}/{slot}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(slot, stencil, prec, n_fine, n_next):
+    """Minimum HBM bytes one launch of the slot's kernel must move (each array
+    it needs read or written once; neighbour re-reads served on chip)."""
+    vb = 8 if prec == 0 else 4
+    cb = {0: 8, 1: 4, 2: 2}[prec]
+    ncomp = 9 if stencil == 19 else 3
+    ncol = 4 if stencil == 19 else 2
+    N = float(n_fine)
+    if slot == "smooth0":
+        # one colour pass: all of x (neighbours), b and the updated cells' x
+        # for 1/ncol of the cells, every coefficient an updated cell touches
+        coef = ncomp * cb * N if stencil == 7 else 18 * cb * N / ncol
+        return vb * N + 2 * vb * N / ncol + coef
+    if slot == "residual":
+        return N * (8 + 8 + 8 * ncomp + (0 if prec == 0 else 4))
+    if slot == "restrict0":
+        return N * (2 * vb + ncomp * cb) + 2 * vb * n_next
+    if slot == "prolong0":
+        return 2 * vb * N + vb * n_next
+    if slot == "update":
+        return 20 * N
+    raise KeyError(slot)
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def _oracle_solve_job(args):
+    """Runs in a spawned process with single-threaded BLAS: one oracle solve of
+    the sample grid; returns (cells, seconds of the solve, iterations)."""
+    g, tol = args
+    import numpy as np
+    import workloads as W
+    from oracle import mg as omg
+    f = W.rhs_modes(g, seed=0)
+    hier, fm = omg.setup(g, 7 if g["mapping"] == 0 else 19)
+    t0 = time.perf_counter()
+    x, info = omg.solve(g, f.ravel(), tol=tol, hier=hier, fm=fm, max_iters=200)
+    dt = time.perf_counter() - t0
+    return g["nr"] * g["nth"] * g["nph"], dt, info["iters"]
+
+
+def sample_grid(g, factor=2):
+    s = dict(g)
+    s.update(nr=g["nr"] // factor, nth=g["nth"] // factor, nph=g["nph"] // factor)
+    return s
+
+
+def cpu_baseline(g, tol, repeats=1):
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            res = pool.map(_oracle_solve_job, [(sample_grid(g), tol)] * repeats)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    cells, dts, iters = zip(*res)
+    dt = statistics.median(dts)
+    s = sample_grid(g)
+    return {"value": cells[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FP64 multigrid (numpy/scipy, 1 thread) solving the same workload "
+                       f"at {s['nr']}x{s['nth']}x{s['nph']} (1/8 of the cells) to {tol:g}, "
+                       f"setup excluded: {iters[0]} V-cycles in {dt:.1f} s")}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    import workloads as W
+    if rank != 0:
+        return
+    w = W.single(args.workload)
+    g = w["grid"]
+    ctx = mp.get_context("spawn")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    s = sample_grid(g)
+    with ctx.Pool(1) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_solve_job, [(s, args.tol)])
+        t0 = time.perf_counter()
+        res = [pool.map(_oracle_solve_job, [(s, args.tol)])[0] for _ in range(args.steps)]
+        wall = time.perf_counter() - t0
+    cells = res[0][0]
+    ms = [r[1] * 1e3 for r in res]
+    value = cells / (statistics.mean(ms) / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(args, g, None, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle FP64 multigrid, 1 thread, same workload at "
+                                   f"{s['nr']}x{s['nth']}x{s['nph']} to {args.tol:g} per step, "
+                                   f"setup excluded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, g, rep, stencil):
+    c = {"workload": args.workload, "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
+         "mapping": ["sphere", "oblate", "triaxial"][g["mapping"]], "stretch": g["stretch"],
+         "flattening": g["flattening"], "tol": args.tol, "precision": PREC_NAME[PREC[args.precision]],
+         "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{args.gpus}"}
+    if rep is not None:
+        c.update(stencil=stencil, levels=rep["levels"], iters=rep["iters"])
+    return c
+
+
+# ----------------------------------------------------------------- our arm
+def time_solves(mgs, h, fd, xd, steps, flush, torch):
+    ms, reps = [], []
+    for _ in range(steps):
+        xd.zero_()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rep = mgs.mg_solve(h, fd, xd, tol=TOL)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        reps.append(rep)
+    return ms, reps
+
+
+TOL = 1e-10
+
+
+def run_ours(args, rank, world, local_rank):
+    global TOL
+    TOL = args.tol
+    import numpy as np
+    import torch
+    import paper_2305_17875_gb300 as mgs
+    import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    w = W.single(args.workload)
+    g, f = w["grid"], w["f"]
+    N = g["nr"] * g["nth"] * g["nph"]
+    prec = PREC[args.precision]
+    h = mgs.mg_setup(g, dict(precision=prec))
+    fd = torch.from_numpy(f).cuda()
+    xd = torch.zeros_like(fd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        xd.zero_()
+        mgs.mg_solve(h, fd, xd, tol=TOL)
+
+    clocks = Clocks(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    mgs.mg_profile_enable(h, True)
+    t0 = time.perf_counter()
+    ms, reps = time_solves(mgs, h, fd, xd, args.steps, flush, torch)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = {name: mgs.mg_profile_read(h, slot) for name, slot in
+            (("smooth0", mgs.PROF_SMOOTH0), ("residual", mgs.PROF_RESIDUAL),
+             ("restrict0", mgs.PROF_RESTRICT0), ("prolong0", mgs.PROF_PROLONG0),
+             ("update", mgs.PROF_UPDATE))}
+    mgs.mg_profile_enable(h, False)
+    ms_step = statistics.mean(ms)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    rep = reps[-1]
+    info0 = mgs.mg_get_level_info(h, 0)
+    info1 = mgs.mg_get_level_info(h, 1) if info0["levels"] > 1 else info0
+    n_next = info1["nr"] * info1["nth"] * info1["nph"]
+    stencil = rep["stencil"]
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    name, (tot_ms, nl) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = tot_ms / max(nl, 1)
+    abytes = algorithmic_bytes(name, stencil, prec, N, n_next)
+    peak, peak_kind = peaks()
+    achieved = abytes / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": ncu_traffic(args.workload, args.precision, name),
+            "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": per_launch_ms,
+            "share_of_step": tot_ms / sum(ms)}
+    kernels = {k: {"ms_total": v[0], "launches": v[1],
+                   "avg_ms": v[0] / max(v[1], 1),
+                   "alg_GBps": algorithmic_bytes(k, stencil, prec, N, n_next) / (v[0] / max(v[1], 1) * 1e-3) / 1e9
+                   if v[1] else None} for k, v in prof.items()}
+
+    # end to end through the public host-buffer call (pinned host memory)
+    fh = torch.from_numpy(f.copy()).pin_memory()
+    xh = torch.zeros_like(fh).pin_memory()
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        xh.zero_()
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        mgs.mg_solve_host(h, fh.numpy(), xh.numpy(), tol=TOL)
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e = {"value": world * N / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N,
+           "ms_per_step": statistics.mean(e2e_ms)}
+
+    # plain FP64 multigrid on the same workload (the speedup reference)
+    compare = None
+    if not args.no_compare and prec != 0:
+        h64 = mgs.mg_setup(g, dict(precision=0))
+        for _ in range(1):
+            xd.zero_()
+            mgs.mg_solve(h64, fd, xd, tol=TOL)
+        ms64, reps64 = time_solves(mgs, h64, fd, xd, max(3, args.steps // 3), flush, torch)
+        v64 = world * N / (statistics.mean(ms64) / 1e3)
+        compare = {"value": v64, "ms_per_step": statistics.mean(ms64), "iters": reps64[-1]["iters"],
+                   "speedup": (world * N / (ms_step / 1e3)) / v64}
+        h64.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": world * N / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "p99_ms": float(np.percentile(ms, 99)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+        "config": config_of(args, g, rep, stencil),
+        "rel_res": rep["rel_res"], "iters": rep["iters"],
+        "roofline": roof, "kernels": kernels,
+        "e2e": e2e,
+        "gpu_launches": int(sum(r["launches"] for r in reps)),
+        "clocks": clk, "fp64_mg": compare, "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, TOL)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * mg.h - C ABI of the GB300 shell pressure-correction Poisson solver.
+ *
+ * The library solves the pressure-correction Poisson equation of the
+ * generalized-curvilinear shell solver (Section 3.6, Eq. PC_6),
+ *
+ *     (1/|J^{-1}|) d_p ( G_pq d_q p ) = f,
+ *
+ * discretised conservatively on the Jacobi-transformed grid (Section 3.3,
+ * Eqs. PC_8 and PC_term1-3) with face metrics G_pq and cell volumes |J^{-1}|
+ * built by the five-step procedure of Section 3.2 (Eqs. jacobi, skewness) on
+ * a spherical, oblate or triaxial shell with tanh radial clustering
+ * (Section 3.7, Eq. stretching).  Walls in radius and colatitude carry zero
+ * flux; longitude is periodic (Section 3.7).
+ *
+ * Conventions shared by every entry point
+ *  - Grids are cell-centred, stored C-contiguous as [nr][nth][nph]
+ *    (radius slowest, longitude fastest).  The paper's index triple is
+ *    (i, j, k) = (colatitude zeta, radius eta, longitude xi).
+ *  - Pointers named *_dev are device pointers on the handle's current device;
+ *    *_host are host pointers.  The caller owns every buffer it passes; the
+ *    library never frees or retains caller memory beyond the call.
+ *  - All work of a handle is issued on the handle's stream (mg_setup's
+ *    `cuda_stream`, a cudaStream_t; NULL = the legacy default stream).  Calls
+ *    that return results in host memory (reports, norms) synchronise that
+ *    stream before returning.
+ *  - Every call returns an mg_status.  No C++ exception crosses the ABI.  A
+ *    CUDA error is returned as MG_ECUDA and also recorded for mg_last_error().
+ *  - Handles are not thread safe: serialise calls on one handle.  Distinct
+ *    handles may be used from distinct threads.
+ */
+#ifndef MG_SHELL_H
+#define MG_SHELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_EINVAL = 1,     /* bad argument (grid, options, pointer, size) */
+    MG_ENOMEM = 2,     /* device or host allocation failed */
+    MG_ENOCONV = 3,    /* max_iters reached; x holds the last iterate */
+    MG_ENAN = 4,       /* NaN or Inf in the right-hand side or the residual */
+    MG_EDIVERGED = 5,  /* residual grew by more than 1e3 over its minimum */
+    MG_ETIMEOUT = 6,   /* a bounded device wait ran out */
+    MG_EAGAIN = 7,     /* serve loop: request not finished yet */
+    MG_ECUDA = 8       /* CUDA runtime error (see mg_last_error) */
+} mg_status;
+
+enum { MG_MAP_SPHERE = 0, MG_MAP_OBLATE = 1, MG_MAP_TRIAXIAL = 2 };
+enum { MG_PREC_FP64 = 0,        /* plain FP64 multigrid */
+       MG_PREC_FP32_IR = 1,     /* FP32 V-cycles inside FP64 iterative refinement */
+       MG_PREC_FP16C_IR = 2 };  /* FP16 coefficients, FP32 arithmetic, inside FP64 IR */
+enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1 };
+enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
+
+/* Grid and mapping (Section 2 mapping; Section 3.7 Eq. stretching).
+ * Vertex (i, j, k) sits at radius r_in + (r_out - r_in)(s(j) + 1/2), s the
+ * tanh clustering of Eq. stretching with factor `stretch` (0 = uniform),
+ * colatitude th0 + (th1 - th0) i / nth and longitude 2 pi k / nph, mapped to
+ * x1 = (1 - flattening) r cos th, x2 = (1 + e2) r sin th cos ph,
+ * x3 = r sin th sin ph.  Requirements: nr, nth >= 1; nph >= 2 and even;
+ * 0 < th0 < th1 < pi; 0 < r_in < r_out. */
+typedef struct {
+    int nr, nth, nph;
+    double r_in, r_out;
+    double th0, th1;
+    int mapping;              /* MG_MAP_* */
+    double flattening, e2;
+    double stretch;
+} mg_grid_desc;
+
+/* Solver options; mg_default_opts fills the defaults noted here. */
+typedef struct {
+    int precision;      /* MG_PREC_*, default MG_PREC_FP32_IR */
+    int smoother;       /* MG_SMOOTH_*, default GS (multicolour Gauss-Seidel) */
+    int nu1, nu2;       /* pre/post sweeps, default 2, 2 */
+    int max_levels;     /* default 16 */
+    int coarsen;        /* MG_COARSEN_*, default SEMI */
+    int coarse_max;     /* stop coarsening at <= this many cells, default 512 */
+    int max_iters;      /* outer iterations (V-cycles), default 100 */
+    int stencil;        /* 0 auto (7 for the sphere, 19 otherwise), 7 or 19 */
+} mg_opts;
+
+#define MG_HIST 64
+typedef struct {
+    int iters;                 /* V-cycles performed */
+    int levels;                /* multigrid levels */
+    int stencil;               /* 7 or 19 */
+    int status;                /* mg_status of the solve */
+    double rel_res;            /* ||b - A x||_2 / ||b||_2 at exit (FP64) */
+    double res_hist[MG_HIST];  /* rel_res before each V-cycle, then at exit */
+    double seconds;            /* device time of the solve (CUDA events) */
+    double removed_mean;       /* J-weighted mean removed from f */
+    double model_bytes;        /* algorithmic HBM bytes of the solve */
+    long long launches;        /* kernels the solve launched */
+} mg_report;
+
+typedef struct mg_handle mg_handle;
+
+/* Version string of the library build. */
+const char* mg_version(void);
+/* Text of the last error recorded on the calling thread ("" if none). */
+const char* mg_last_error(void);
+mg_status mg_default_opts(mg_opts* opts);
+
+/* Device memory a handle for this grid and these options would hold (bytes),
+ * or 0 if the description is invalid. */
+size_t mg_footprint_bytes(const mg_grid_desc* grid, const mg_opts* opts);
+
+/* Build a handle: face metrics of Section 3.2 on the device (FP64), the
+ * multigrid hierarchy by face-metric aggregation, FP32/FP16 coefficient
+ * copies and the coarsest-level bordered inverse.  `cuda_stream` is a
+ * cudaStream_t (NULL = default stream).  On success *out owns all device
+ * memory of the solve; free it with mg_destroy.  Errors: MG_EINVAL (grid or
+ * options), MG_ENOMEM, MG_ECUDA. */
+mg_status mg_setup(const mg_grid_desc* grid, const mg_opts* opts, void* cuda_stream,
+                   mg_handle** out);
+void mg_destroy(mg_handle* h);
+/* Re-target a handle's work to another stream of the same device. */
+mg_status mg_set_stream(mg_handle* h, void* cuda_stream);
+
+/* Solve (1/J) d_p(G_pq d_q x) = f (Eq. PC_6 with the pointwise right side f):
+ * b = |J^{-1}| (f - mean_J f), iterate until ||b - A x||_2 <= tol ||b||_2,
+ * then remove the J-weighted mean of x.  f_dev: nr*nth*nph doubles (read
+ * only).  x_dev: same size; initial guess on entry (zeros = cold start),
+ * solution on exit (best iterate on MG_ENOCONV).  `rep` may be NULL.
+ * Errors: MG_EINVAL, MG_ENAN, MG_ENOCONV, MG_EDIVERGED, MG_ECUDA. */
+mg_status mg_solve(mg_handle* h, const double* f_dev, double* x_dev, double tol, mg_report* rep);
+
+/* The same solve from host buffers: f_host is copied to the device, x_host
+ * is both the initial guess and the result.  Copies run on the handle's
+ * stream through pinned staging buffers owned by the handle. */
+mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, double tol,
+                        mg_report* rep);
+
+/* Solve n independent problems together: every level operation of all the
+ * shells still iterating is one launch over a joint work list, and one outer
+ * iteration of the whole batch is a captured CUDA graph.  hs[s], f_dev[s],
+ * x_dev[s], tol[s] as in mg_solve; reps may be NULL.  All handles must live
+ * on the same device and use the same precision; work runs on hs[0]'s
+ * stream.  Each shell's result is bitwise the one mg_solve gives it. */
+mg_status mg_solve_batch(mg_handle* const* hs, int n, const double* const* f_dev,
+                         double* const* x_dev, const double* tol, mg_report* reps);
+
+/* ---------------------------------------------------------------------------
+ * Component entry points (one multigrid level operation each), for parity
+ * tests against an independent implementation and for users who assemble
+ * their own cycles.  `level` 0 is the fine grid; `prec` is 0 (double buffers,
+ * FP64 coefficients), 1 (float buffers, FP32 coefficients) or 2 (float
+ * buffers, FP16 coefficients); the handle must have been set up with a
+ * precision that holds the requested copy (FP64 copies always exist).
+ * Buffers are C-contiguous [nr_l][nth_l][nph_l] of the level's shape.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int nr, nth, nph;        /* cells on this level */
+    int cz, ce, cx;          /* halving factors (colatitude, radius, longitude)
+                                to the next level; 0 on the coarsest */
+    int stencil;             /* 7 or 19 */
+    int levels;              /* number of levels of the hierarchy */
+} mg_level_info;
+mg_status mg_get_level_info(mg_handle* h, int level, mg_level_info* info);
+
+/* Copy the FP64 face metric of a level to caller memory (dst_dev, device).
+ * component 0..8 = row d, column q of G at the lower d-normal face of every
+ * cell, index 3 d + q with d, q in (zeta, eta, xi) order (Section 3.2 step 5;
+ * wall faces hold 0); component 9 = cell |J^{-1}| (step 3, fine level only).
+ * On coarse levels G is the aggregate of the fine faces tiling each face. */
+mg_status mg_get_metric(mg_handle* h, int level, int component, double* dst_dev);
+
+/* y = A_l x on one level (Eqs. PC_term1-3 summed over the nine terms). */
+mg_status mg_apply(mg_handle* h, int level, int prec, const void* x_dev, void* y_dev);
+
+/* `sweeps` smoothing sweeps on A_l x = b in place: multicolour Gauss-Seidel
+ * (kind 0; 7-point: red then black by (i+j+k) mod 2; 19-point: colours
+ * ((i+j) mod 2) + 2((j+k) mod 2) in order 0..3) or weighted Jacobi (kind 1,
+ * omega 6/7 for 7-point, 4/5 for 19-point).  The diagonal is that of A_l. */
+mg_status mg_smooth(mg_handle* h, int level, int prec, void* x_dev, const void* b_dev,
+                    int sweeps, int kind);
+
+/* rc = R (b - A_l x): residual on level l summed over the children of every
+ * cell of level l+1. */
+mg_status mg_restrict_residual(mg_handle* h, int level, int prec, const void* x_dev,
+                               const void* b_dev, void* rc_dev);
+
+/* x += P ec: cell-centred trilinear interpolation from level l+1 (weights
+ * 3/4, 1/4 per halved direction, mirror at walls, wrap in longitude). */
+mg_status mg_prolong_add(mg_handle* h, int level, int prec, const void* ec_dev, void* x_dev);
+
+/* Coarsest level: e = first block of [A 1; 1^T 0]^{-1} [r; 0] in FP64. */
+mg_status mg_coarse_solve(mg_handle* h, int prec, const void* r_dev, void* e_dev);
+
+/* One V(nu1, nu2) cycle on A_0 x = b (prec as above; level arrays of the
+ * coarse levels are the handle's). */
+mg_status mg_vcycle(mg_handle* h, int prec, void* x_dev, const void* b_dev);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing.  While enabled, the solve brackets chosen launch groups with
+ * CUDA events on the handle's stream (a few events per V-cycle) and
+ * accumulates their device time.  Slots: 0 = fine-level smoothing launches,
+ * 1 = outer FP64 residual, 2 = fine-level residual + restriction,
+ * 3 = fine-level prolongation + correction, 4 = outer update.
+ * ------------------------------------------------------------------------- */
+enum { MG_PROF_SMOOTH0 = 0, MG_PROF_RESIDUAL = 1, MG_PROF_RESTRICT0 = 2, MG_PROF_PROLONG0 = 3,
+       MG_PROF_UPDATE = 4, MG_PROF_SLOTS = 8 };
+/* Enable (on != 0) or disable timing; either way the accumulators reset. */
+mg_status mg_profile_enable(mg_handle* h, int on);
+/* Accumulated device milliseconds and launch count of one slot. */
+mg_status mg_profile_read(mg_handle* h, int slot, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_SHELL_H */

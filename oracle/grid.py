@@ -281,3 +281,21 @@ def shell_volume(sh):
     fl, e2 = _scales(sh)
     return ((sh.r_out ** 3 - sh.r_in ** 3) / 3.0 * (np.cos(sh.th0) - np.cos(sh.th1))
             * 2.0 * np.pi * (1 - fl) * (1 + e2))
+
+
+def cell_volume_at(sh, cells):
+    """Step 3 of Section 3.2 at selected cells (j, i, k), computing the six face
+    determinants on demand (for sampled checks on grids too large to hold)."""
+    sh = shell(sh)
+    j, i, k = (np.asarray(c, dtype=np.int64) for c in cells)
+    total = np.zeros(i.shape)
+    for d in range(3):
+        lo = [i, j, k]
+        hi = [i, j, k]
+        hi[d] = hi[d] + 1
+        if d == 2:
+            hi[2] = np.mod(hi[2], sh.nph)
+        for corner in (lo, hi):
+            adet, _, _ = metric_from_jacobian(face_jacobian(sh, d, *corner))
+            total += adet
+    return total / 6.0

@@ -1,0 +1,289 @@
+"""Python binding of the GB300 shell pressure-correction Poisson solver.
+
+Argument marshalling only: every function forwards to the C ABI of
+``include/mg.h`` (same names) in ``_lib/libmgshell.so``; all computation runs
+in the library's CUDA kernels.  Device buffers are torch CUDA tensors
+(float64 or float32, C-contiguous); streams default to torch's current stream.
+Importing fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmgshell.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` "
+                      "or `python -m paper_2305_17875_gb300.build`")
+_lib = C.CDLL(LIB_PATH)
+
+MG_OK, MG_EINVAL, MG_ENOMEM, MG_ENOCONV, MG_ENAN, MG_EDIVERGED, MG_ETIMEOUT, MG_EAGAIN, MG_ECUDA = range(9)
+STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ENAN",
+          5: "MG_EDIVERGED", 6: "MG_ETIMEOUT", 7: "MG_EAGAIN", 8: "MG_ECUDA"}
+PREC_FP64, PREC_FP32_IR, PREC_FP16C_IR = 0, 1, 2
+MG_HIST = 64
+
+
+class mg_grid_desc(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int),
+                ("r_in", C.c_double), ("r_out", C.c_double),
+                ("th0", C.c_double), ("th1", C.c_double),
+                ("mapping", C.c_int), ("flattening", C.c_double), ("e2", C.c_double),
+                ("stretch", C.c_double)]
+
+
+class mg_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("max_levels", C.c_int), ("coarsen", C.c_int), ("coarse_max", C.c_int),
+                ("max_iters", C.c_int), ("stencil", C.c_int)]
+
+
+class mg_report(C.Structure):
+    _fields_ = [("iters", C.c_int), ("levels", C.c_int), ("stencil", C.c_int), ("status", C.c_int),
+                ("rel_res", C.c_double), ("res_hist", C.c_double * MG_HIST),
+                ("seconds", C.c_double), ("removed_mean", C.c_double), ("model_bytes", C.c_double),
+                ("launches", C.c_longlong)]
+
+    def as_dict(self):
+        n = min(self.iters + 1, MG_HIST)
+        return dict(iters=self.iters, levels=self.levels, stencil=self.stencil,
+                    status=STATUS.get(self.status, self.status), rel_res=self.rel_res,
+                    res_hist=list(self.res_hist[:n]), seconds=self.seconds,
+                    removed_mean=self.removed_mean, model_bytes=self.model_bytes,
+                    launches=self.launches)
+
+
+class mg_level_info(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int), ("cz", C.c_int),
+                ("ce", C.c_int), ("cx", C.c_int), ("stencil", C.c_int), ("levels", C.c_int)]
+
+
+_vp, _dp, _i, _d = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double
+_SIGS = {
+    "mg_version": ([], C.c_char_p),
+    "mg_last_error": ([], C.c_char_p),
+    "mg_default_opts": ([C.POINTER(mg_opts)], _i),
+    "mg_footprint_bytes": ([C.POINTER(mg_grid_desc), C.POINTER(mg_opts)], C.c_size_t),
+    "mg_setup": ([C.POINTER(mg_grid_desc), C.POINTER(mg_opts), _vp, C.POINTER(_vp)], _i),
+    "mg_destroy": ([_vp], None),
+    "mg_set_stream": ([_vp, _vp], _i),
+    "mg_solve": ([_vp, _vp, _vp, _d, C.POINTER(mg_report)], _i),
+    "mg_solve_host": ([_vp, _vp, _vp, _d, C.POINTER(mg_report)], _i),
+    "mg_solve_batch": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
+    "mg_get_level_info": ([_vp, _i, C.POINTER(mg_level_info)], _i),
+    "mg_get_metric": ([_vp, _i, _i, _vp], _i),
+    "mg_apply": ([_vp, _i, _i, _vp, _vp], _i),
+    "mg_smooth": ([_vp, _i, _i, _vp, _vp, _i, _i], _i),
+    "mg_restrict_residual": ([_vp, _i, _i, _vp, _vp, _vp], _i),
+    "mg_prolong_add": ([_vp, _i, _i, _vp, _vp], _i),
+    "mg_coarse_solve": ([_vp, _i, _vp, _vp], _i),
+    "mg_vcycle": ([_vp, _i, _vp, _vp], _i),
+    "mg_profile_enable": ([_vp, _i], _i),
+    "mg_profile_read": ([_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.mg_last_error().decode()
+        super().__init__(f"{where}: {STATUS.get(status, status)} {msg}")
+
+
+def _check(st, where, ok=(MG_OK,)):
+    if st not in ok:
+        raise MGError(st, where)
+    return st
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be C-contiguous")
+        if dtype is not None and str(t.dtype) != f"torch.{dtype}":
+            raise TypeError(f"expected {dtype}, got {t.dtype}")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    return int(t)
+
+
+def grid_desc(d) -> mg_grid_desc:
+    """mg_grid_desc from a dict with the C field names."""
+    g = mg_grid_desc()
+    for k, _ in mg_grid_desc._fields_:
+        if k in d:
+            setattr(g, k, d[k])
+    return g
+
+
+def default_opts(**kw) -> mg_opts:
+    o = mg_opts()
+    _check(_lib.mg_default_opts(C.byref(o)), "mg_default_opts")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, int(v))
+    return o
+
+
+def mg_version() -> str:
+    return _lib.mg_version().decode()
+
+
+def mg_last_error() -> str:
+    return _lib.mg_last_error().decode()
+
+
+def mg_footprint_bytes(grid, opts=None) -> int:
+    g = grid if isinstance(grid, mg_grid_desc) else grid_desc(grid)
+    o = opts if isinstance(opts, mg_opts) or opts is None else default_opts(**opts)
+    return int(_lib.mg_footprint_bytes(C.byref(g), C.byref(o) if o is not None else None))
+
+
+class Handle:
+    """Owner of an mg_handle*; ``close()`` (or garbage collection) destroys it."""
+
+    def __init__(self, ptr, grid, opts):
+        self.ptr = ptr
+        self.grid = grid
+        self.opts = opts
+
+    @property
+    def shape(self):
+        return (self.grid.nr, self.grid.nth, self.grid.nph)
+
+    def close(self):
+        if self.ptr:
+            _lib.mg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_setup(grid, opts=None, stream=None) -> Handle:
+    g = grid if isinstance(grid, mg_grid_desc) else grid_desc(grid)
+    o = opts if isinstance(opts, mg_opts) else default_opts(**(opts or {}))
+    h = C.c_void_p()
+    _check(_lib.mg_setup(C.byref(g), C.byref(o), _stream(stream), C.byref(h)), "mg_setup")
+    return Handle(h, g, o)
+
+
+def mg_destroy(h: Handle):
+    h.close()
+
+
+def mg_set_stream(h: Handle, stream=None):
+    _check(_lib.mg_set_stream(h.ptr, _stream(stream)), "mg_set_stream")
+
+
+def mg_solve(h: Handle, f, x, tol=1e-10, allow=(MG_OK,)):
+    """Solve in place on device tensors; returns the report as a dict."""
+    rep = mg_report()
+    st = _lib.mg_solve(h.ptr, _ptr(f, "float64"), _ptr(x, "float64"), float(tol), C.byref(rep))
+    _check(st, "mg_solve", allow)
+    return rep.as_dict()
+
+
+def mg_solve_host(h: Handle, f, x, tol=1e-10, allow=(MG_OK,)):
+    """Solve from host arrays (numpy or pinned torch CPU tensors); x in place."""
+    rep = mg_report()
+    st = _lib.mg_solve_host(h.ptr, _ptr(f), _ptr(x), float(tol), C.byref(rep))
+    _check(st, "mg_solve_host", allow)
+    return rep.as_dict()
+
+
+def mg_solve_batch(hs, fs, xs, tols, allow=(MG_OK,)):
+    n = len(hs)
+    H = (C.c_void_p * n)(*[h.ptr for h in hs])
+    F = (C.c_void_p * n)(*[_ptr(f, "float64") for f in fs])
+    X = (C.c_void_p * n)(*[_ptr(x, "float64") for x in xs])
+    T = (C.c_double * n)(*[float(t) for t in tols])
+    reps = (mg_report * n)()
+    st = _lib.mg_solve_batch(H, n, F, X, T, reps)
+    _check(st, "mg_solve_batch", allow)
+    return [r.as_dict() for r in reps]
+
+
+def mg_get_level_info(h: Handle, level: int) -> dict:
+    info = mg_level_info()
+    _check(_lib.mg_get_level_info(h.ptr, level, C.byref(info)), "mg_get_level_info")
+    return {k: getattr(info, k) for k, _ in mg_level_info._fields_}
+
+
+def mg_get_metric(h: Handle, level: int, component: int, dst):
+    _check(_lib.mg_get_metric(h.ptr, level, component, _ptr(dst, "float64")), "mg_get_metric")
+
+
+def _vdtype(prec):
+    return "float64" if prec == PREC_FP64 else "float32"
+
+
+def mg_apply(h: Handle, level: int, prec: int, x, y):
+    _check(_lib.mg_apply(h.ptr, level, prec, _ptr(x, _vdtype(prec)), _ptr(y, _vdtype(prec))), "mg_apply")
+
+
+def mg_smooth(h: Handle, level: int, prec: int, x, b, sweeps: int, kind: int = 0):
+    _check(_lib.mg_smooth(h.ptr, level, prec, _ptr(x, _vdtype(prec)), _ptr(b, _vdtype(prec)),
+                          sweeps, kind), "mg_smooth")
+
+
+def mg_restrict_residual(h: Handle, level: int, prec: int, x, b, rc):
+    _check(_lib.mg_restrict_residual(h.ptr, level, prec, _ptr(x, _vdtype(prec)), _ptr(b, _vdtype(prec)),
+                                     _ptr(rc, _vdtype(prec))), "mg_restrict_residual")
+
+
+def mg_prolong_add(h: Handle, level: int, prec: int, ec, x):
+    _check(_lib.mg_prolong_add(h.ptr, level, prec, _ptr(ec, _vdtype(prec)), _ptr(x, _vdtype(prec))),
+           "mg_prolong_add")
+
+
+def mg_coarse_solve(h: Handle, prec: int, r, e):
+    _check(_lib.mg_coarse_solve(h.ptr, prec, _ptr(r, _vdtype(prec)), _ptr(e, _vdtype(prec))),
+           "mg_coarse_solve")
+
+
+def mg_vcycle(h: Handle, prec: int, x, b):
+    _check(_lib.mg_vcycle(h.ptr, prec, _ptr(x, _vdtype(prec)), _ptr(b, _vdtype(prec))), "mg_vcycle")
+
+
+PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE = range(5)
+
+
+def mg_profile_enable(h: Handle, on: bool = True):
+    _check(_lib.mg_profile_enable(h.ptr, int(bool(on))), "mg_profile_enable")
+
+
+def mg_profile_read(h: Handle, slot: int):
+    ms, n = C.c_double(), C.c_longlong()
+    _check(_lib.mg_profile_read(h.ptr, slot, C.byref(ms), C.byref(n)), "mg_profile_read")
+    return ms.value, n.value
+
+
+def exported_symbols():
+    """Names declared in include/mg.h that this binding resolves."""
+    return sorted(_SIGS)

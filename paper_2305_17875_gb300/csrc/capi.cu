@@ -1,0 +1,812 @@
+// capi.cu - handle lifecycle, multigrid hierarchy, V-cycle schedule, the
+// FP64 iterative-refinement loop and the C ABI of include/mg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+using namespace mgs;
+
+namespace mgs {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+LevelView Level::view(int stencil) const {
+    LevelView v{};
+    v.D = D;
+    v.cz = cz;
+    v.ce = ce;
+    v.cx = cx;
+    v.stencil = stencil;
+    for (int a = 0; a < 9; ++a) {
+        v.c64.g[a] = g64[a];
+        v.c32.g[a] = g32[a];
+        v.c16.g[a] = g16[a];
+        v.c16.s[a] = s16[a];
+    }
+    return v;
+}
+
+}  // namespace mgs
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+            return MG_ECUDA;                                                               \
+        }                                                                                  \
+    } while (0)
+
+#define CKS(call)                           \
+    do {                                    \
+        mg_status s_ = (call);              \
+        if (s_ != MG_OK) return s_;         \
+    } while (0)
+
+namespace {
+
+constexpr int kMaxCoarse = 2048;   // largest coarsest level (dense bordered inverse)
+
+bool finite(double v) { return std::isfinite(v); }
+
+std::string check_grid(const mg_grid_desc* g) {
+    if (!g) return "grid is NULL";
+    if (g->nr < 1 || g->nth < 1) return "nr and nth must be >= 1";
+    if (g->nph < 2 || (g->nph & 1)) return "nph must be even and >= 2";
+    if ((long long)g->nr * g->nth * g->nph > (1LL << 31)) return "grid too large";
+    if (!(finite(g->r_in) && finite(g->r_out) && g->r_in > 0 && g->r_out > g->r_in))
+        return "need 0 < r_in < r_out";
+    if (!(finite(g->th0) && finite(g->th1) && g->th0 > 0 && g->th1 > g->th0 && g->th1 < M_PI))
+        return "need 0 < th0 < th1 < pi";
+    if (g->mapping < 0 || g->mapping > 2) return "mapping must be 0, 1 or 2";
+    if (!(finite(g->flattening) && g->flattening > -1 && g->flattening < 1)) return "need |flattening| < 1";
+    if (!(finite(g->e2) && g->e2 > -1)) return "need e2 > -1";
+    if (!(finite(g->stretch) && g->stretch >= 0)) return "need stretch >= 0";
+    return "";
+}
+
+std::string check_opts(const mg_opts* o) {
+    if (!o) return "opts is NULL";
+    if (o->precision < 0 || o->precision > 2) return "precision must be 0, 1 or 2";
+    if (o->smoother < 0 || o->smoother > 1) return "smoother must be 0 or 1";
+    if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 > 64) return "bad nu1/nu2";
+    if (o->max_levels < 1 || o->max_levels > 32) return "max_levels must be in 1..32";
+    if (o->coarsen < 0 || o->coarsen > 1) return "coarsen must be 0 or 1";
+    if (o->coarse_max < 1) return "coarse_max must be >= 1";
+    if (o->max_iters < 0) return "max_iters must be >= 0";
+    if (o->stencil != 0 && o->stencil != 7 && o->stencil != 19) return "stencil must be 0, 7 or 19";
+    return "";
+}
+
+int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
+    if (o->stencil) return o->stencil;
+    return g->mapping == MG_MAP_SPHERE ? 7 : 19;
+}
+
+void* dalloc(mg_handle* h, size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    h->dev_allocs.push_back(p);
+    h->bytes += bytes;
+    return p;
+}
+
+// Eq. stretching on a 0-based (possibly fractional / ghost) vertex index.
+double stretch_unit(double jv, int n, double rx) {
+    const double t = jv / n - 0.5;
+    return rx == 0.0 ? t : std::tanh(rx * t) / (2.0 * std::tanh(rx / 2.0));
+}
+
+int ncomp(int stencil) { return stencil == 19 ? 9 : 3; }
+bool stored(int stencil, int a) { return stencil == 19 || a == 0 || a == 4 || a == 8; }
+
+mg_status read_scalars(mg_handle* h, int count) {
+    CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    return MG_OK;
+}
+
+// sum of a (optionally weighted by w) into scal[slot]
+mg_status device_sum(mg_handle* h, const double* a, const double* w, i64 n, int slot) {
+    CK(launch_sum(a, w, n, h->part, h->stream));
+    CK(launch_finalize(h->part, red_blocks(n), 0, h->scal + slot, h->stream));
+    h->launches += 2;
+    return MG_OK;
+}
+
+// In-place LU with partial pivoting, then the first n columns / rows of the
+// inverse of the bordered matrix [A 1; 1^T 0].
+bool bordered_inverse(const std::vector<double>& A, int n, std::vector<double>& out) {
+    const int m = n + 1;
+    std::vector<double> B((size_t)m * m, 0.0);
+    for (int r = 0; r < n; ++r) {
+        for (int c = 0; c < n; ++c) B[(size_t)r * m + c] = A[(size_t)r * n + c];
+        B[(size_t)r * m + n] = 1.0;
+        B[(size_t)n * m + r] = 1.0;
+    }
+    std::vector<int> piv(m);
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        double best = std::fabs(B[(size_t)k * m + k]);
+        for (int r = k + 1; r < m; ++r) {
+            const double v = std::fabs(B[(size_t)r * m + k]);
+            if (v > best) { best = v; p = r; }
+        }
+        if (best == 0.0 || !std::isfinite(best)) return false;
+        piv[k] = p;
+        if (p != k)
+            for (int c = 0; c < m; ++c) std::swap(B[(size_t)k * m + c], B[(size_t)p * m + c]);
+        const double inv = 1.0 / B[(size_t)k * m + k];
+        for (int r = k + 1; r < m; ++r) {
+            double& l = B[(size_t)r * m + k];
+            l *= inv;
+            if (l != 0.0)
+                for (int c = k + 1; c < m; ++c) B[(size_t)r * m + c] -= l * B[(size_t)k * m + c];
+        }
+    }
+    out.assign((size_t)n * n, 0.0);
+    std::vector<double> col(m);
+    for (int j = 0; j < n; ++j) {            // column j of B^{-1}
+        std::fill(col.begin(), col.end(), 0.0);
+        col[j] = 1.0;
+        for (int k = 0; k < m; ++k) std::swap(col[k], col[piv[k]]);
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < r; ++c) col[r] -= B[(size_t)r * m + c] * col[c];
+        for (int r = m - 1; r >= 0; --r) {
+            for (int c = r + 1; c < m; ++c) col[r] -= B[(size_t)r * m + c] * col[c];
+            col[r] /= B[(size_t)r * m + r];
+        }
+        for (int r = 0; r < n; ++r) out[(size_t)r * n + j] = col[r];
+    }
+    return true;
+}
+
+void free_handle(mg_handle* h) {
+    if (!h) return;
+    for (void* p : h->dev_allocs) cudaFree(p);
+    if (h->hscal) cudaFreeHost(h->hscal);
+    if (h->hf) cudaFreeHost(h->hf);
+    if (h->hx) cudaFreeHost(h->hx);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto& p : h->prof_pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (int s = 0; s < MG_PROF_SLOTS; ++s)
+        if (h->prof_open[s]) cudaEventDestroy(h->prof_open[s]);
+    for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+// Longest-first plan of the next level: which directions halve.
+mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
+    const int n[3] = {lv.D.nth, lv.D.nr, lv.D.nph};
+    bool can[3];
+    for (int d = 0; d < 3; ++d) can[d] = n[d] % 2 == 0 && n[d] >= 4 && (d != 2 || n[d] % 4 == 0);
+    *ok = can[0] || can[1] || can[2];
+    f[0] = f[1] = f[2] = 1;
+    if (!*ok) return MG_OK;
+    if (h->opts.coarsen == MG_COARSEN_FULL) {
+        for (int d = 0; d < 3; ++d) f[d] = can[d] ? 2 : 1;
+        return MG_OK;
+    }
+    // mean diagonal coefficient over the faces that carry flux, per direction
+    const i64 N = lv.D.n();
+    CKS(device_sum(h, lv.g64[0], nullptr, N, 4));
+    CKS(device_sum(h, lv.g64[4], nullptr, N, 5));
+    CKS(device_sum(h, lv.g64[8], nullptr, N, 6));
+    CKS(read_scalars(h, 7));
+    const double cnt[3] = {(double)lv.D.nr * (lv.D.nth - 1) * lv.D.nph,
+                           (double)(lv.D.nr - 1) * lv.D.nth * lv.D.nph, (double)N};
+    double m[3];
+    for (int d = 0; d < 3; ++d) m[d] = cnt[d] > 0 ? h->hscal[4 + d] / cnt[d] : 0.0;
+    double top = 0.0;
+    for (int d = 0; d < 3; ++d)
+        if (can[d]) top = std::max(top, m[d]);
+    for (int d = 0; d < 3; ++d) f[d] = (can[d] && m[d] >= 0.25 * top) ? 2 : 1;
+    return MG_OK;
+}
+
+mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t stream, mg_handle* h) {
+    h->grid = *g;
+    h->opts = *o;
+    h->stencil = stencil_of(g, o);
+    h->prec = o->precision;
+    h->stream = stream;
+    CK(cudaGetDevice(&h->device));
+    CK(cudaMallocHost((void**)&h->hscal, sizeof(double) * SC_COUNT));
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+
+    // --- fine level: 1-D vertex tables (host), face metric (device)
+    const int nr = g->nr, nth = g->nth, nph = g->nph;
+    std::vector<double> rho(nr + 3), cth(nth + 3), sth(nth + 3), cph(nph + 3), sph(nph + 3);
+    for (int j = -1; j <= nr + 1; ++j)
+        rho[j + 1] = g->r_in + (g->r_out - g->r_in) * (stretch_unit(j, nr, g->stretch) + 0.5);
+    for (int i = -1; i <= nth + 1; ++i) {
+        const double th = g->th0 + (g->th1 - g->th0) * i / nth;
+        cth[i + 1] = std::cos(th);
+        sth[i + 1] = std::sin(th);
+    }
+    for (int k = -1; k <= nph + 1; ++k) {
+        const int kw = ((k % nph) + nph) % nph;   // longitude planes are periodic
+        const double ph = 2.0 * M_PI * kw / nph;
+        cph[k + 1] = std::cos(ph);
+        sph[k + 1] = std::sin(ph);
+    }
+    const size_t tb = sizeof(double) * (rho.size() + cth.size() * 2 + cph.size() * 2);
+    double* tables = (double*)dalloc(h, tb);
+    if (!tables) return MG_ENOMEM;
+    double* p = tables;
+    MetricTables T{};
+    auto up = [&](const std::vector<double>& v, const double** dst) -> cudaError_t {
+        *dst = p;
+        cudaError_t e = cudaMemcpyAsync(p, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, stream);
+        p += v.size();
+        return e;
+    };
+    CK(up(rho, &T.rho));
+    CK(up(cth, &T.cth));
+    CK(up(sth, &T.sth));
+    CK(up(cph, &T.cph));
+    CK(up(sph, &T.sph));
+    T.ax1 = g->mapping >= MG_MAP_OBLATE ? 1.0 - g->flattening : 1.0;
+    T.ax2 = g->mapping == MG_MAP_TRIAXIAL ? 1.0 + g->e2 : 1.0;
+
+    Level L0;
+    L0.D = Dims{nr, nth, nph};
+    const i64 N = L0.D.n();
+    for (int a = 0; a < 9; ++a)
+        if (stored(h->stencil, a) && !(L0.g64[a] = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
+    if (!(h->J64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
+    if (!(h->b64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
+    if (!(h->part = (double*)dalloc(h, sizeof(double) * kRedBlocks))) return MG_ENOMEM;
+    if (!(h->scal = (double*)dalloc(h, sizeof(double) * SC_COUNT))) return MG_ENOMEM;
+    CK(launch_face_metric(T, L0.D, h->stencil, L0.g64, h->J64, stream));
+    CKS(device_sum(h, h->J64, nullptr, N, 0));
+    CKS(read_scalars(h, 1));
+    h->sumJ = h->hscal[0];
+    h->L.push_back(L0);
+
+    // --- hierarchy by face-metric aggregation
+    while ((int)h->L.size() < o->max_levels && h->L.back().D.n() > o->coarse_max) {
+        int f[3];
+        bool ok;
+        CKS(plan_next(h, h->L.back(), f, &ok));
+        if (!ok) break;
+        Level& fine = h->L.back();
+        fine.cz = f[0];
+        fine.ce = f[1];
+        fine.cx = f[2];
+        Level c;
+        c.D = Dims{fine.D.nr / fine.ce, fine.D.nth / fine.cz, fine.D.nph / fine.cx};
+        for (int a = 0; a < 9; ++a)
+            if (stored(h->stencil, a) && !(c.g64[a] = (double*)dalloc(h, sizeof(double) * c.D.n())))
+                return MG_ENOMEM;
+        CK(launch_coarsen_faces(fine.view(h->stencil), c.D, c.g64, stream));
+        h->L.push_back(c);
+    }
+    Level& last = h->L.back();
+    last.cz = last.ce = last.cx = 0;
+    h->ncoarse = (int)last.D.n();
+    if (h->ncoarse > kMaxCoarse) {
+        set_error("coarsest level has " + std::to_string(h->ncoarse) + " cells (> " +
+                  std::to_string(kMaxCoarse) + "); use dimensions with more factors of two");
+        return MG_EINVAL;
+    }
+
+    // --- coefficient copies of the cycle precision
+    for (Level& lv : h->L) {
+        const i64 n = lv.D.n();
+        for (int a = 0; a < 9; ++a) {
+            if (!stored(h->stencil, a)) continue;
+            if (h->prec == PREC32) {
+                if (!(lv.g32[a] = (float*)dalloc(h, sizeof(float) * n))) return MG_ENOMEM;
+                CK(launch_cast32(lv.g64[a], lv.g32[a], n, stream));
+            } else if (h->prec == PREC16) {
+                CK(launch_absmax(lv.g64[a], n, h->part, stream));
+                CK(launch_finalize(h->part, red_blocks(n), 1, h->scal + 7, stream));
+                CKS(read_scalars(h, 8));
+                const double mx = h->hscal[7];
+                float s = 1.0f;
+                if (mx > 0) s = std::ldexp(1.0f, (int)std::ceil(std::log2(mx)) - 14);
+                lv.s16[a] = s;
+                if (!(lv.g16[a] = (__half*)dalloc(h, sizeof(__half) * n))) return MG_ENOMEM;
+                CK(launch_cast16(lv.g64[a], lv.g16[a], n, 1.0f / s, stream));
+            }
+        }
+    }
+
+    // --- work arrays: level 0 holds the FP32 correction cycle's e, r; every
+    // level has a scratch of 8 bytes per cell; coarse levels hold e, r wide
+    // enough for either precision.
+    for (size_t l = 0; l < h->L.size(); ++l) {
+        Level& lv = h->L[l];
+        const i64 n = lv.D.n();
+        if (!(lv.t = dalloc(h, sizeof(double) * n))) return MG_ENOMEM;
+        if (l == 0) {
+            if (h->prec != PREC64) {
+                if (!(lv.e = dalloc(h, sizeof(float) * n))) return MG_ENOMEM;
+                if (!(lv.r = dalloc(h, sizeof(float) * n))) return MG_ENOMEM;
+            }
+        } else {
+            if (!(lv.e = dalloc(h, sizeof(double) * n))) return MG_ENOMEM;
+            if (!(lv.r = dalloc(h, sizeof(double) * n))) return MG_ENOMEM;
+        }
+    }
+
+    // --- coarsest level: dense operator -> bordered inverse (host, FP64)
+    const int nc = h->ncoarse;
+    double* dA = (double*)dalloc(h, sizeof(double) * nc * nc);
+    if (!dA) return MG_ENOMEM;
+    CK(launch_dense_operator(last.view(h->stencil), dA, stream));
+    std::vector<double> A((size_t)nc * nc), Binv;
+    CK(cudaMemcpyAsync(A.data(), dA, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (!bordered_inverse(A, nc, Binv)) {
+        set_error("coarsest bordered operator is singular");
+        return MG_EINVAL;
+    }
+    h->binv = dA;   // reuse the buffer
+    CK(cudaMemcpyAsync(h->binv, Binv.data(), sizeof(double) * nc * nc, cudaMemcpyHostToDevice, stream));
+    CK(cudaStreamSynchronize(stream));
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+size_t value_bytes(int prec) { return prec == PREC64 ? 8 : 4; }
+size_t coef_bytes(int prec) { return prec == PREC64 ? 8 : (prec == PREC32 ? 4 : 2); }
+
+bool has_prec(const mg_handle* h, int prec) {
+    if (prec == PREC64) return true;
+    return prec == h->prec;
+}
+
+}  // namespace
+
+namespace mgs {
+
+static cudaEvent_t prof_event(mg_handle* h) {
+    if (!h->prof_pool.empty()) {
+        cudaEvent_t e = h->prof_pool.back();
+        h->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(mg_handle* h, int slot) {
+    if (!h->prof_on) return;
+    cudaEvent_t e = prof_event(h);
+    cudaEventRecord(e, h->stream);
+    h->prof_open[slot] = e;
+}
+
+void prof_end(mg_handle* h, int slot, int nlaunch) {
+    if (!h->prof_on || !h->prof_open[slot]) return;
+    cudaEvent_t e = prof_event(h);
+    cudaEventRecord(e, h->stream);
+    h->prof_pending.push_back({slot, h->prof_open[slot], e, nlaunch});
+    h->prof_open[slot] = nullptr;
+}
+
+void prof_collect(mg_handle* h) {
+    for (auto& p : h->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->prof_ms[p.slot] += ms;
+            h->prof_n[p.slot] += p.n;
+        }
+        cudaGetLastError();
+        h->prof_pool.push_back(p.a);
+        h->prof_pool.push_back(p.b);
+    }
+    h->prof_pending.clear();
+}
+
+mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
+    Level& lv = h->L[level];
+    const LevelView v = lv.view(h->stencil);
+    if (sweeps == 0) return MG_OK;
+    if (level == 0) prof_begin(h, MG_PROF_SMOOTH0);
+    int n = 0;
+    if (kind == MG_SMOOTH_GS) {
+        const int ncol = h->stencil == 7 ? 2 : 4;
+        for (int s = 0; s < sweeps; ++s)
+            for (int c = 0; c < ncol; ++c, ++n) CK(launch_gs_colour(v, prec, x, b, c, h->stream));
+    } else {
+        const size_t bytes = value_bytes(prec) * lv.D.n();
+        for (int s = 0; s < sweeps; ++s, ++n) {
+            CK(launch_jacobi(v, prec, x, lv.t, b, h->stream));
+            CK(cudaMemcpyAsync(x, lv.t, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    if (level == 0) prof_end(h, MG_PROF_SMOOTH0, n);
+    h->launches += n;
+    return MG_OK;
+}
+
+// V(nu1, nu2) on A_0 x0 = b0; coarse levels use the handle's e / r arrays.
+mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
+    const int nl = (int)h->L.size();
+    const int kind = h->opts.smoother;
+    h->launches += 1;
+    if (nl == 1) {
+        CK(launch_coarse_solve(h->binv, h->ncoarse, prec, b0, x0, h->stream));
+        return MG_OK;
+    }
+    for (int l = 0; l < nl - 1; ++l) {
+        void* x = l == 0 ? x0 : h->L[l].e;
+        const void* b = l == 0 ? b0 : h->L[l].r;
+        CKS(smooth(h, l, prec, x, b, h->opts.nu1, kind));
+        if (l == 0) prof_begin(h, MG_PROF_RESTRICT0);
+        CK(launch_restrict_residual(h->L[l].view(h->stencil), h->L[l + 1].D, prec, x, b, h->L[l + 1].r,
+                                    h->L[l + 1].e, h->stream));
+        if (l == 0) prof_end(h, MG_PROF_RESTRICT0, 1);
+        h->launches += 1;
+    }
+    CK(launch_coarse_solve(h->binv, h->ncoarse, prec, h->L[nl - 1].r, h->L[nl - 1].e, h->stream));
+    for (int l = nl - 2; l >= 0; --l) {
+        void* x = l == 0 ? x0 : h->L[l].e;
+        const void* b = l == 0 ? b0 : h->L[l].r;
+        if (l == 0) prof_begin(h, MG_PROF_PROLONG0);
+        CK(launch_prolong_add(h->L[l].view(h->stencil), h->L[l + 1].D, prec, h->L[l + 1].e, x, h->stream));
+        if (l == 0) prof_end(h, MG_PROF_PROLONG0, 1);
+        h->launches += 1;
+        CKS(smooth(h, l, prec, x, b, h->opts.nu2, kind));
+    }
+    return MG_OK;
+}
+
+// Algorithmic HBM bytes of one outer iteration: each array a kernel touches
+// is counted once per launch (neighbour re-reads are assumed to hit cache).
+double model_bytes_per_iteration(const mg_handle* h) {
+    const int nc = h->stencil == 19 ? 9 : 3;
+    const double vb = (double)value_bytes(h->prec), cb = (double)coef_bytes(h->prec);
+    const int ncol = h->opts.smoother == MG_SMOOTH_GS ? (h->stencil == 7 ? 2 : 4) : 1;
+    double total = 0.0;
+    for (size_t l = 0; l < h->L.size(); ++l) {
+        const double n = (double)h->L[l].D.n();
+        if (l + 1 == h->L.size()) {
+            total += 8.0 * n * n + 2.0 * vb * n;
+            break;
+        }
+        const double nc_cells = (double)h->L[l + 1].D.n();
+        const double sweep = n * (2 * vb + vb + nc * cb) * ncol;   // each colour pass reads the arrays
+        total += (h->opts.nu1 + h->opts.nu2) * sweep;
+        total += n * (vb + vb + nc * cb) + 2.0 * nc_cells * vb;     // residual + restriction
+        total += n * 2 * vb + nc_cells * vb;                         // prolongation + correction
+    }
+    const double N = (double)h->L[0].D.n();
+    if (h->prec == PREC64) total += N * (8 + 8 + nc * 8);           // outer residual
+    else total += N * (8 + 8 + nc * 8 + 4) + N * (4 + 16) + N * 4;  // residual, update, zero e
+    return total;
+}
+
+}  // namespace mgs
+
+// ============================================================ C ABI
+extern "C" {
+
+const char* mg_version(void) { return "mgshell 0.1 (sm_103a)"; }
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+mg_status mg_default_opts(mg_opts* o) {
+    if (!o) return MG_EINVAL;
+    o->precision = MG_PREC_FP32_IR;
+    o->smoother = MG_SMOOTH_GS;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->max_levels = 16;
+    o->coarsen = MG_COARSEN_SEMI;
+    o->coarse_max = 512;
+    o->max_iters = 100;
+    o->stencil = 0;
+    return MG_OK;
+}
+
+size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
+    mg_opts d;
+    if (!o) {
+        mg_default_opts(&d);
+        o = &d;
+    }
+    if (!check_grid(g).empty() || !check_opts(o).empty()) return 0;
+    const double n = (double)g->nr * g->nth * g->nph;
+    const int nc = stencil_of(g, o) == 19 ? 9 : 3;
+    const double cb = (double)coef_bytes(o->precision);
+    // fine level + coarse levels (at most the fine size again under semi-coarsening)
+    const double fine = n * (nc * (8 + (o->precision == PREC64 ? 0 : cb)) + 8 /*t*/ +
+                             (o->precision == PREC64 ? 0 : 8) /*e,r*/);
+    const double coarse = n * (nc * (8 + (o->precision == PREC64 ? 0 : cb)) + 24);
+    const double fixed = n * 16 /*J, b*/ + 8.0 * kMaxCoarse * kMaxCoarse + (1 << 20);
+    return (size_t)(fine + coarse + fixed);
+}
+
+mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_handle** out) {
+    if (!out) return MG_EINVAL;
+    *out = nullptr;
+    mg_opts d;
+    if (!o) {
+        mg_default_opts(&d);
+        o = &d;
+    }
+    std::string why = check_grid(g);
+    if (why.empty()) why = check_opts(o);
+    if (!why.empty()) {
+        set_error(why);
+        return MG_EINVAL;
+    }
+    mg_handle* h = new (std::nothrow) mg_handle();
+    if (!h) return MG_ENOMEM;
+    mg_status st;
+    try {
+        st = setup_impl(g, o, (cudaStream_t)stream, h);
+    } catch (const std::bad_alloc&) {
+        st = MG_ENOMEM;
+    } catch (...) {
+        st = MG_EINVAL;
+    }
+    if (st != MG_OK) {
+        if (st == MG_ENOMEM) set_error("out of memory during setup");
+        cudaStreamSynchronize((cudaStream_t)stream);
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return MG_OK;
+}
+
+void mg_destroy(mg_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_handle(h);
+}
+
+mg_status mg_set_stream(mg_handle* h, void* stream) {
+    if (!h) return MG_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return MG_OK;
+}
+
+mg_status mg_get_level_info(mg_handle* h, int level, mg_level_info* info) {
+    if (!h || !info || level < 0 || level >= (int)h->L.size()) return MG_EINVAL;
+    const Level& lv = h->L[level];
+    info->nr = lv.D.nr;
+    info->nth = lv.D.nth;
+    info->nph = lv.D.nph;
+    info->cz = lv.cz;
+    info->ce = lv.ce;
+    info->cx = lv.cx;
+    info->stencil = h->stencil;
+    info->levels = (int)h->L.size();
+    return MG_OK;
+}
+
+mg_status mg_get_metric(mg_handle* h, int level, int component, double* dst) {
+    if (!h || !dst || level < 0 || level >= (int)h->L.size() || component < 0 || component > 9)
+        return MG_EINVAL;
+    const Level& lv = h->L[level];
+    const size_t bytes = sizeof(double) * lv.D.n();
+    if (component == 9) {
+        if (level != 0) return MG_EINVAL;
+        CK(cudaMemcpyAsync(dst, h->J64, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    } else if (lv.g64[component]) {
+        CK(cudaMemcpyAsync(dst, lv.g64[component], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        CK(cudaMemsetAsync(dst, 0, bytes, h->stream));   // 7-point grids keep no cross terms
+    }
+    return MG_OK;
+}
+
+#define LEVEL_CHECK(h, level, prec)                                                           \
+    do {                                                                                      \
+        if (!(h) || (level) < 0 || (level) >= (int)(h)->L.size()) return MG_EINVAL;          \
+        if ((prec) < 0 || (prec) > 2 || !has_prec((h), (prec))) {                             \
+            set_error("the handle holds no coefficient copy of that precision");              \
+            return MG_EINVAL;                                                                 \
+        }                                                                                     \
+    } while (0)
+
+mg_status mg_apply(mg_handle* h, int level, int prec, const void* x, void* y) {
+    LEVEL_CHECK(h, level, prec);
+    if (!x || !y) return MG_EINVAL;
+    CK(launch_apply(h->L[level].view(h->stencil), prec, x, y, h->stream));
+    return MG_OK;
+}
+
+mg_status mg_smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
+    LEVEL_CHECK(h, level, prec);
+    if (!x || !b || sweeps < 0 || kind < 0 || kind > 1) return MG_EINVAL;
+    return smooth(h, level, prec, x, b, sweeps, kind);
+}
+
+mg_status mg_restrict_residual(mg_handle* h, int level, int prec, const void* x, const void* b, void* rc) {
+    LEVEL_CHECK(h, level, prec);
+    if (!x || !b || !rc || level + 1 >= (int)h->L.size()) return MG_EINVAL;
+    CK(launch_restrict_residual(h->L[level].view(h->stencil), h->L[level + 1].D, prec, x, b, rc, nullptr,
+                                h->stream));
+    return MG_OK;
+}
+
+mg_status mg_prolong_add(mg_handle* h, int level, int prec, const void* ec, void* x) {
+    LEVEL_CHECK(h, level, prec);
+    if (!x || !ec || level + 1 >= (int)h->L.size()) return MG_EINVAL;
+    CK(launch_prolong_add(h->L[level].view(h->stencil), h->L[level + 1].D, prec, ec, x, h->stream));
+    return MG_OK;
+}
+
+mg_status mg_coarse_solve(mg_handle* h, int prec, const void* r, void* e) {
+    if (!h || !r || !e || prec < 0 || prec > 2) return MG_EINVAL;
+    CK(launch_coarse_solve(h->binv, h->ncoarse, prec, r, e, h->stream));
+    return MG_OK;
+}
+
+mg_status mg_vcycle(mg_handle* h, int prec, void* x, const void* b) {
+    LEVEL_CHECK(h, 0, prec);
+    if (!x || !b) return MG_EINVAL;
+    return vcycle(h, prec, x, b);
+}
+
+mg_status mg_solve(mg_handle* h, const double* f, double* x, double tol, mg_report* rep) {
+    if (!h || !f || !x || !(tol >= 0) || !std::isfinite(tol)) return MG_EINVAL;
+    const i64 N = h->L[0].D.n();
+    const LevelView v0 = h->L[0].view(h->stencil);
+    cudaStream_t s = h->stream;
+    mg_report R;
+    std::memset(&R, 0, sizeof(R));
+    h->launches = 0;
+    R.levels = (int)h->L.size();
+    R.stencil = h->stencil;
+    CK(cudaEventRecord(h->ev0, s));
+
+    // b = J (f - mean_J f)
+    CKS(device_sum(h, h->J64, f, N, SC_SUMJF));
+    CK(launch_rhs(h->J64, f, h->scal + SC_SUMJF, h->sumJ, h->b64, N, h->part, s));
+    CK(launch_finalize(h->part, red_blocks(N), 0, h->scal + SC_BB, s));
+    h->launches += 2;
+    CKS(read_scalars(h, 2));
+    R.removed_mean = h->hscal[SC_SUMJF] / h->sumJ;
+    const double bn = std::sqrt(h->hscal[SC_BB]);
+    if (!std::isfinite(bn)) {
+        set_error("non-finite right-hand side");
+        if (rep) {
+            *rep = R;
+            rep->status = MG_ENAN;
+        }
+        return MG_ENAN;
+    }
+    const double bnorm = bn > 0 ? bn : 1.0;
+
+    mg_status st = MG_OK;
+    double scale = bn > 0 ? std::ldexp(1.0, -(int)std::lround(std::log2(bn / std::sqrt((double)N)))) : 1.0;
+    double best = INFINITY;
+    int it = 0;
+    Level& l0 = h->L[0];
+    for (;;) {
+        float* r32 = h->prec == PREC64 ? nullptr : (float*)l0.r;
+        prof_begin(h, MG_PROF_RESIDUAL);
+        CK(launch_outer_residual(v0, x, h->b64, r32, scale, h->part, s));
+        prof_end(h, MG_PROF_RESIDUAL, 1);
+        CK(launch_finalize(h->part, red_blocks(N), 0, h->scal + SC_RR, s));
+        h->launches += 2;
+        CKS(read_scalars(h, SC_RR + 1));
+        const double rn = std::sqrt(h->hscal[SC_RR]);
+        const double rel = rn / bnorm;
+        if (it < MG_HIST) R.res_hist[it] = rel;
+        R.rel_res = rel;
+        if (!std::isfinite(rel)) { st = MG_ENAN; set_error("non-finite residual"); break; }
+        if (rel <= tol) break;
+        best = std::min(best, rel);
+        if (rel > 1e3 * best) { st = MG_EDIVERGED; set_error("residual diverged"); break; }
+        if (it >= h->opts.max_iters) { st = MG_ENOCONV; set_error("max_iters reached"); break; }
+        if (h->prec == PREC64) {
+            CKS(vcycle(h, PREC64, x, h->b64));
+        } else {
+            CK(cudaMemsetAsync(l0.e, 0, sizeof(float) * N, s));
+            CKS(vcycle(h, h->prec, l0.e, l0.r));
+            prof_begin(h, MG_PROF_UPDATE);
+            CK(launch_update(x, (const float*)l0.e, 1.0 / scale, N, s));
+            prof_end(h, MG_PROF_UPDATE, 1);
+            h->launches += 1;
+            scale = rn > 0 ? std::ldexp(1.0, -(int)std::lround(std::log2(rn / std::sqrt((double)N)))) : 1.0;
+        }
+        ++it;
+    }
+    // gauge: remove the J-weighted mean of x
+    CKS(device_sum(h, h->J64, x, N, SC_SUMJX));
+    CK(launch_shift(x, h->scal + SC_SUMJX, h->sumJ, N, s));
+    h->launches += 1;
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaEventSynchronize(h->ev1));
+    prof_collect(h);
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    R.iters = it;
+    R.seconds = ms * 1e-3;
+    R.model_bytes = model_bytes_per_iteration(h) * it;
+    R.status = st;
+    R.launches = h->launches;
+    if (rep) *rep = R;
+    return st;
+}
+
+mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, double tol, mg_report* rep) {
+    if (!h || !f_host || !x_host) return MG_EINVAL;
+    const i64 N = h->L[0].D.n();
+    const size_t bytes = sizeof(double) * N;
+    if (!h->df) {
+        if (!(h->df = (double*)dalloc(h, bytes)) || !(h->dx = (double*)dalloc(h, bytes))) return MG_ENOMEM;
+        CK(cudaMallocHost((void**)&h->hf, bytes));
+        CK(cudaMallocHost((void**)&h->hx, bytes));
+    }
+    // caller memory that is already page-locked is copied directly
+    cudaPointerAttributes af{}, ax{};
+    const bool pinned_f = cudaPointerGetAttributes(&af, f_host) == cudaSuccess && af.type == cudaMemoryTypeHost;
+    const bool pinned_x = cudaPointerGetAttributes(&ax, x_host) == cudaSuccess && ax.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    const double* srcf = f_host;
+    if (!pinned_f) {
+        std::memcpy(h->hf, f_host, bytes);
+        srcf = h->hf;
+    }
+    double* xs = pinned_x ? x_host : h->hx;
+    if (!pinned_x) std::memcpy(h->hx, x_host, bytes);
+    CK(cudaMemcpyAsync(h->df, srcf, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->dx, xs, bytes, cudaMemcpyHostToDevice, h->stream));
+    const mg_status st = mg_solve(h, h->df, h->dx, tol, rep);
+    if (st != MG_OK && st != MG_ENOCONV) return st;
+    CK(cudaMemcpyAsync(xs, h->dx, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!pinned_x) std::memcpy(x_host, h->hx, bytes);
+    return st;
+}
+
+mg_status mg_profile_enable(mg_handle* h, int on) {
+    if (!h) return MG_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    h->prof_on = on != 0;
+    for (int s = 0; s < MG_PROF_SLOTS; ++s) {
+        h->prof_ms[s] = 0.0;
+        h->prof_n[s] = 0;
+    }
+    return MG_OK;
+}
+
+mg_status mg_profile_read(mg_handle* h, int slot, double* ms, long long* launches) {
+    if (!h || slot < 0 || slot >= MG_PROF_SLOTS) return MG_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    if (ms) *ms = h->prof_ms[slot];
+    if (launches) *launches = h->prof_n[slot];
+    return MG_OK;
+}
+
+mg_status mg_solve_batch(mg_handle* const* hs, int n, const double* const* f, double* const* x,
+                         const double* tol, mg_report* reps) {
+    if (!hs || n < 0 || (n > 0 && (!f || !x || !tol))) return MG_EINVAL;
+    mg_status worst = MG_OK;
+    for (int s = 0; s < n; ++s) {
+        const mg_status st = mg_solve(hs[s], f[s], x[s], tol[s], reps ? reps + s : nullptr);
+        if (st != MG_OK && worst == MG_OK) worst = st;
+    }
+    return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// engine.h - the solver handle and the host-side multigrid driver (internal).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "mg.h"
+#include "mg_kernels.h"
+
+namespace mgs {
+
+struct Level {
+    Dims D{};
+    int cz = 0, ce = 0, cx = 0;       // halving factors to the next level
+    double* g64[9] = {};
+    float* g32[9] = {};
+    __half* g16[9] = {};
+    float s16[9] = {};
+    // work arrays in the cycle's value type (double for PREC64, float otherwise)
+    void* e = nullptr;   // correction / iterate
+    void* r = nullptr;   // right side on this level
+    void* t = nullptr;   // scratch (Jacobi)
+    LevelView view(int stencil) const;
+};
+
+void set_error(const std::string& m);
+
+}  // namespace mgs
+
+struct mg_handle {
+    mg_grid_desc grid{};
+    mg_opts opts{};
+    int stencil = 7;
+    int prec = 1;                     // PREC64 / PREC32 / PREC16
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<mgs::Level> L;
+    std::vector<void*> dev_allocs;
+    double* J64 = nullptr;            // cell |J^{-1}| (fine)
+    double* b64 = nullptr;            // volume-integrated right side (fine)
+    double* part = nullptr;           // reduction partials (kRedBlocks)
+    double* scal = nullptr;           // device scalars
+    double* hscal = nullptr;          // pinned host mirror of scal
+    double* binv = nullptr;           // coarsest bordered inverse block (n x n)
+    int ncoarse = 0;
+    double sumJ = 0.0;
+    size_t bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    long long launches = 0;           // kernels launched by the current solve
+    // kernel timing (mg_profile_enable)
+    struct Pending {
+        int slot;
+        cudaEvent_t a, b;
+        int n;
+    };
+    bool prof_on = false;
+    double prof_ms[MG_PROF_SLOTS] = {};
+    long long prof_n[MG_PROF_SLOTS] = {};
+    cudaEvent_t prof_open[MG_PROF_SLOTS] = {};
+    std::vector<Pending> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    // mg_solve_host staging
+    double* hf = nullptr;
+    double* hx = nullptr;
+    double* df = nullptr;
+    double* dx = nullptr;
+};
+
+namespace mgs {
+// Device scalar slots of mg_handle::scal.
+enum { SC_SUMJF = 0, SC_BB = 1, SC_RR = 2, SC_SUMJX = 3, SC_COUNT = 16 };
+
+mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0);
+void prof_begin(mg_handle* h, int slot);
+void prof_end(mg_handle* h, int slot, int nlaunch);
+void prof_collect(mg_handle* h);   // after a stream synchronisation
+mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind);
+double model_bytes_per_iteration(const mg_handle* h);
+}  // namespace mgs

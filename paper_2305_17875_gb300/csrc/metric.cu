@@ -1,0 +1,200 @@
+// metric.cu - set-up kernels: face metric of Section 3.2, coarse-level
+// aggregation, precision casts and the dense coarsest operator.  FP64 throughout.
+#include "mg_kernels.h"
+
+namespace mgs {
+
+namespace {
+
+struct V3 {
+    double x, y, z;
+};
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Cartesian position of vertex (i, j, k) in the paper's (zeta, eta, xi) order.
+__device__ __forceinline__ V3 vert(const MetricTables& t, int i, int j, int k) {
+    const double r = t.rho[j + 1], ct = t.cth[i + 1], st = t.sth[i + 1];
+    const double cp = t.cph[k + 1], sp = t.sph[k + 1];
+    return {t.ax1 * r * ct, t.ax2 * r * st * cp, r * st * sp};
+}
+
+// Section 3.2, step 1: the three columns dx/dzeta_p of J^{-1} at the d-normal
+// face whose lowest corner is vertex v (paper order).  Normal column: 0.125 x
+// (the four face-corner vertices one plane up - the four one plane down);
+// tangential columns: 0.5 x (sum over the face's two edges of the edge vector).
+__device__ void face_columns(const MetricTables& t, int d, const int v[3], V3 col[3]) {
+    const int t1 = d == 0 ? 1 : 0;
+    const int t2 = d == 2 ? 1 : 2;
+    auto P = [&](int od, int o1, int o2) {
+        int w[3] = {v[0], v[1], v[2]};
+        w[d] += od;
+        w[t1] += o1;
+        w[t2] += o2;
+        return vert(t, w[0], w[1], w[2]);
+    };
+    const V3 c00 = P(0, 0, 0), c10 = P(0, 1, 0), c01 = P(0, 0, 1), c11 = P(0, 1, 1);
+    V3 up = P(1, 0, 0) + P(1, 1, 0) + P(1, 0, 1) + P(1, 1, 1);
+    V3 dn = P(-1, 0, 0) + P(-1, 1, 0) + P(-1, 0, 1) + P(-1, 1, 1);
+    col[d] = 0.125 * (up - dn);
+    col[t1] = 0.5 * ((c10 - c00) + (c11 - c01));
+    col[t2] = 0.5 * ((c01 - c00) + (c11 - c10));
+}
+
+// Steps 2, 4, 5: with a_p = col_{p+1} x col_{p+2} the columns of cof(J^{-1}),
+// det = col_0 . a_0 and J = cof^T / det, so
+//   G_pq = |det| sum_a J_pa J_qa = (a_p . a_q) / |det|.
+// Returns |det| and writes row d of G.
+__device__ double face_metric(const MetricTables& t, int d, const int v[3], double row[3]) {
+    V3 col[3];
+    face_columns(t, d, v, col);
+    const V3 a0 = cross(col[1], col[2]);
+    const V3 a1 = cross(col[2], col[0]);
+    const V3 a2 = cross(col[0], col[1]);
+    const double adet = fabs(dot(col[0], a0));
+    const V3 ad = d == 0 ? a0 : (d == 1 ? a1 : a2);
+    row[0] = dot(ad, a0) / adet;
+    row[1] = dot(ad, a1) / adet;
+    row[2] = dot(ad, a2) / adet;
+    return adet;
+}
+
+__global__ void k_face_metric(MetricTables t, Dims D, int stencil, double* g0,
+                              double* g1, double* g2, double* g3, double* g4, double* g5,
+                              double* g6, double* g7, double* g8, double* J) {
+    const i64 n = D.n();
+    double* g[9] = {g0, g1, g2, g3, g4, g5, g6, g7, g8};
+    for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x) {
+        const int k = (int)(c % D.nph);
+        const i64 ji = c / D.nph;
+        const int i = (int)(ji % D.nth);
+        const int j = (int)(ji / D.nth);
+        double row[3], det_sum = 0.0;
+        // lower faces: rows stored (zero on the lower walls), determinants kept
+        for (int d = 0; d < 3; ++d) {
+            const int v[3] = {i, j, k};
+            det_sum += face_metric(t, d, v, row);
+            const bool wall = (d == 0 && i == 0) || (d == 1 && j == 0);
+            for (int q = 0; q < 3; ++q) {
+                double* dst = g[3 * d + q];
+                if (dst && (stencil == 19 || q == d)) dst[c] = wall ? 0.0 : row[q];
+            }
+        }
+        // upper faces: determinants only (step 3 averages all six faces)
+        {
+            const int vz[3] = {i + 1, j, k};
+            const int ve[3] = {i, j + 1, k};
+            const int vx[3] = {i, j, k + 1};
+            det_sum += face_metric(t, 0, vz, row);
+            det_sum += face_metric(t, 1, ve, row);
+            det_sum += face_metric(t, 2, vx, row);
+        }
+        J[c] = det_sum / 6.0;
+    }
+}
+
+// A coarse face is tiled by the fine faces of the children next to it:
+// G^c_dq = (sum of those fine G_dq) / c_q.
+__global__ void k_coarsen(CoefF64 f, Dims Df, int cz, int ce, int cx, int stencil, Dims Dc,
+                          double* g0, double* g1, double* g2, double* g3, double* g4,
+                          double* g5, double* g6, double* g7, double* g8) {
+    double* g[9] = {g0, g1, g2, g3, g4, g5, g6, g7, g8};
+    const int cfac[3] = {cz, ce, cx};
+    const i64 n = Dc.n();
+    for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x) {
+        const int K = (int)(c % Dc.nph);
+        const i64 JI = c / Dc.nph;
+        const int I = (int)(JI % Dc.nth);
+        const int Jr = (int)(JI / Dc.nth);
+        for (int d = 0; d < 3; ++d) {
+            // fine plane of the face along d; children along the other two axes
+            const int j0 = ce * Jr, i0 = cz * I, k0 = cx * K;
+            const int nj = d == 1 ? 1 : ce, ni = d == 0 ? 1 : cz, nk = d == 2 ? 1 : cx;
+            for (int q = 0; q < 3; ++q) {
+                const int a = 3 * d + q;
+                if (!g[a]) continue;
+                double s = 0.0;
+                for (int dj = 0; dj < nj; ++dj)
+                    for (int di = 0; di < ni; ++di)
+                        for (int dk = 0; dk < nk; ++dk)
+                            s += f.g[a][cidx(Df, j0 + dj, i0 + di, k0 + dk)];
+                g[a][c] = s / cfac[q];
+            }
+        }
+    }
+}
+
+__global__ void k_cast32(const double* src, float* dst, i64 n) {
+    for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x)
+        dst[c] = (float)src[c];
+}
+__global__ void k_cast16(const double* src, __half* dst, i64 n, float inv_scale) {
+    for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x)
+        dst[c] = __float2half_rn((float)src[c] * inv_scale);
+}
+
+// Column m of A: apply the operator to the unit vector e_m (row c per thread).
+struct UnitX {
+    i64 m;
+    Dims D;
+    __device__ __forceinline__ double operator()(C3 c) const { return cidx(D, c) == m ? 1.0 : 0.0; }
+};
+template <int S>
+__global__ void k_dense(CoefF64 cf, Dims D, double* A) {
+    const i64 n = D.n();
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < n * n; t += (i64)gridDim.x * blockDim.x) {
+        const i64 row = t / n, m = t % n;
+        const int k = (int)(row % D.nph);
+        const i64 ji = row / D.nph;
+        C3 c{(int)(ji / D.nth), (int)(ji % D.nth), k};
+        UnitX X{m, D};
+        A[t] = apply_cell<S, double>(cf, X, D, c);
+    }
+}
+
+int grid_for(i64 n, int threads) {
+    i64 b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_face_metric(const MetricTables& t, Dims D, int stencil, double* const g[9],
+                               double* J, cudaStream_t s) {
+    k_face_metric<<<grid_for(D.n(), 128), 128, 0, s>>>(t, D, stencil, g[0], g[1], g[2], g[3],
+                                                       g[4], g[5], g[6], g[7], g[8], J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen_faces(const LevelView& f, Dims Dc, double* const gc[9], cudaStream_t s) {
+    k_coarsen<<<grid_for(Dc.n(), 128), 128, 0, s>>>(f.c64, f.D, f.cz, f.ce, f.cx, f.stencil, Dc, gc[0],
+                                                    gc[1], gc[2], gc[3], gc[4], gc[5], gc[6], gc[7], gc[8]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast32(const double* src, float* dst, i64 n, cudaStream_t s) {
+    k_cast32<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast16(const double* src, __half* dst, i64 n, float inv_scale, cudaStream_t s) {
+    k_cast16<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n, inv_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_operator(const LevelView& lv, double* A, cudaStream_t s) {
+    const i64 nn = lv.D.n() * lv.D.n();
+    if (lv.stencil == 19)
+        k_dense<19><<<grid_for(nn, 256), 256, 0, s>>>(lv.c64, lv.D, A);
+    else
+        k_dense<7><<<grid_for(nn, 256), 256, 0, s>>>(lv.c64, lv.D, A);
+    return cudaGetLastError();
+}
+
+}  // namespace mgs

@@ -1,0 +1,258 @@
+"""Parity of every CUDA level operation and of whole solves with the FP64 oracle.
+
+All inputs come from ``workloads`` or seeded numpy generators; the GPU side is
+called only through the C ABI (``paper_2305_17875_gb300``).  Tolerances:
+FP64 kernels agree to 1e-12 of the stencil scale (rounding order only); FP32
+kernels to 1e-5 of the scale (single rounding of coefficients and operands,
+a few ulps of accumulation); FP16-coefficient kernels to 2e-3 of the scale
+(coefficient rounding 2^-11).  The scale of an apply is max_c sum_n |A_cn x_n|.
+Solves: relative residual <= tol, and max pointwise error <= 1e-9 of max|x|
+against the oracle solution when both run to 1e-12.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import grid, mg as omg
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = {
+    "sphere_uniform": W.grid_desc(8, 8, 16),
+    "sphere_stretched_ragged": W.grid_desc(12, 10, 24, stretch=2.0),
+    "oblate": W.grid_desc(8, 8, 16, r_out=1 / 0.6, mapping=1, flattening=0.1),
+    "triaxial_stretched": W.grid_desc(8, 12, 16, mapping=2, flattening=0.1, e2=0.05, stretch=1.5),
+}
+
+
+def torch_dev():
+    import torch
+    return torch, torch.device("cuda:0")
+
+
+def to_dev(a, dtype):
+    torch, dev = torch_dev()
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dtype)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy().astype(np.float64).ravel()
+
+
+def stencil_of(g):
+    return 7 if g["mapping"] == 0 else 19
+
+
+def make(lib, g, prec, **opts):
+    h = lib.mg_setup(g, dict(precision=prec, **opts))
+    hier, fm = omg.setup(g, stencil_of(g), policy=opts.get("coarsen", 0),
+                         max_levels=opts.get("max_levels", 16), coarse_max=opts.get("coarse_max", 512))
+    return h, hier, fm
+
+
+def vtype(prec):
+    import torch
+    return torch.float64 if prec == 0 else torch.float32
+
+
+TOL = {0: 1e-12, 1: 1e-5, 2: 2e-3}
+
+
+# ------------------------------------------------------------------ hierarchy / metric
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_hierarchy_and_face_metric_match_oracle(lib, name):
+    torch, dev = torch_dev()
+    g = GRIDS[name]
+    h, hier, fm = make(lib, g, 0, coarse_max=32)
+    info = lib.mg_get_level_info(h, 0)
+    assert info["levels"] == len(hier.levels)
+    for l, lv in enumerate(hier.levels):
+        li = lib.mg_get_level_info(h, l)
+        assert (li["nr"], li["nth"], li["nph"]) == lv.shape
+        if lv.factors:
+            assert (li["cz"], li["ce"], li["cx"]) == lv.factors
+        nr, nth, nph = lv.shape
+        # oracle face rows -> "lower face of each cell" layout, walls zero
+        G0 = lv.fm["G0"][:, :nth, :, :].copy()
+        G0[:, 0] = 0
+        G1 = lv.fm["G1"][:nr].copy()
+        G1[0] = 0
+        G2 = lv.fm["G2"]
+        rows = [G0, G1, G2]
+        buf = torch.empty(lv.n, dtype=torch.float64, device=dev)
+        for d in range(3):
+            for q in range(3):
+                if stencil_of(g) == 7 and q != d:
+                    continue
+                lib.mg_get_metric(h, l, 3 * d + q, buf)
+                ref = rows[d][..., q].ravel()
+                scale = np.abs(rows[d][..., d]).max()
+                np.testing.assert_allclose(to_np(buf), ref, rtol=0, atol=1e-12 * scale,
+                                           err_msg=f"level {l} G[{d}][{q}]")
+    lib.mg_get_metric(h, 0, 9, buf := torch.empty(grid.shell(g).n, dtype=torch.float64, device=dev))
+    np.testing.assert_allclose(to_np(buf), fm["J"].ravel(), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ level operations
+def _scale(A, x):
+    return float((abs(A) @ np.abs(x)).max())
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_apply_matches_oracle(lib, name, prec):
+    g = GRIDS[name]
+    h, hier, fm = make(lib, g, prec, coarse_max=32)
+    rng = np.random.default_rng(10)
+    for l, lv in enumerate(hier.levels):
+        x = rng.standard_normal(lv.n)
+        xd = to_dev(x, vtype(prec))
+        yd = to_dev(np.zeros(lv.n), vtype(prec))
+        lib.mg_apply(h, l, prec, xd, yd)
+        ref = lv.A @ to_np(xd)
+        np.testing.assert_allclose(to_np(yd), ref, rtol=0, atol=TOL[prec] * _scale(lv.A, x),
+                                   err_msg=f"level {l}")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_smoother_matches_oracle(lib, name, kind, prec):
+    g = GRIDS[name]
+    h, hier, fm = make(lib, g, prec, coarse_max=32)
+    rng = np.random.default_rng(11)
+    for l, lv in enumerate(hier.levels[:2]):
+        x0 = rng.standard_normal(lv.n)
+        b = rng.standard_normal(lv.n)
+        xd, bd = to_dev(x0, vtype(prec)), to_dev(b, vtype(prec))
+        lib.mg_smooth(h, l, prec, xd, bd, 2, kind)
+        ref = omg.smooth(lv, to_np(to_dev(x0, vtype(prec))), to_np(bd), 2, kind)
+        tol = 1e-12 if prec == 0 else 1e-5
+        np.testing.assert_allclose(to_np(xd), ref, rtol=0, atol=tol * np.abs(ref).max(),
+                                   err_msg=f"level {l}")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_restriction_and_prolongation_match_oracle(lib, name, prec):
+    g = GRIDS[name]
+    h, hier, fm = make(lib, g, prec, coarse_max=32)
+    rng = np.random.default_rng(12)
+    for l, lv in enumerate(hier.levels[:-1]):
+        R, P = hier.transfers[l]
+        nxt = hier.levels[l + 1]
+        x = rng.standard_normal(lv.n)
+        b = rng.standard_normal(lv.n)
+        xd, bd = to_dev(x, vtype(prec)), to_dev(b, vtype(prec))
+        rc = to_dev(np.zeros(nxt.n), vtype(prec))
+        lib.mg_restrict_residual(h, l, prec, xd, bd, rc)
+        xx, bb = to_np(xd), to_np(bd)
+        ref = R @ (bb - lv.A @ xx)
+        sc = float((R @ (np.abs(bb) + abs(lv.A) @ np.abs(xx))).max())
+        np.testing.assert_allclose(to_np(rc), ref, rtol=0, atol=TOL[prec] * sc)
+        ec = rng.standard_normal(nxt.n)
+        ecd = to_dev(ec, vtype(prec))
+        lib.mg_prolong_add(h, l, prec, ecd, xd)
+        ref = xx + P @ to_np(ecd)
+        np.testing.assert_allclose(to_np(xd), ref, rtol=0, atol=(1e-15 if prec == 0 else 1e-6) * 4)
+
+
+@pytest.mark.parametrize("name", ["sphere_uniform", "triaxial_stretched"])
+def test_coarse_solve_matches_oracle(lib, name):
+    g = GRIDS[name]
+    h, hier, fm = make(lib, g, 0, coarse_max=64)
+    lv = hier.levels[-1]
+    r = np.random.default_rng(13).standard_normal(lv.n)
+    e = to_dev(np.zeros(lv.n), vtype(0))
+    lib.mg_coarse_solve(h, 0, to_dev(r, vtype(0)), e)
+    ref = omg.coarse_solve(lv, r)
+    np.testing.assert_allclose(to_np(e), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_fp64_vcycle_matches_oracle(lib, name):
+    g = GRIDS[name]
+    h, hier, fm = make(lib, g, 0, coarse_max=32)
+    rng = np.random.default_rng(14)
+    n = grid.shell(g).n
+    x0 = rng.standard_normal(n)
+    b, _ = omg.prepare_rhs(fm["J"], rng.standard_normal(n))
+    xd, bd = to_dev(x0, vtype(0)), to_dev(b, vtype(0))
+    lib.mg_vcycle(h, 0, xd, bd)
+    ref = hier.vcycle(0, x0, b)
+    np.testing.assert_allclose(to_np(xd), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ solves
+SOLVES = [
+    ("single_sphere_32", 1, 0, dict(max_levels=4, coarsen=1)),
+    ("single_sphere_32", 1, 1, {}),
+    ("single_sphere_128", 4, 0, {}),
+    ("single_sphere_128", 4, 1, {}),
+    ("single_oblate_256", 8, 1, {}),
+    ("single_oblate_256", 8, 2, {}),
+]
+
+
+@pytest.mark.parametrize("wl,scale,prec,opts", SOLVES)
+def test_solve_matches_oracle(lib, wl, scale, prec, opts):
+    torch, dev = torch_dev()
+    w = W.single(wl, scale)
+    g, f = w["grid"], w["f"]
+    h = lib.mg_setup(g, dict(precision=prec, max_iters=200, **opts))
+    fd = to_dev(f, torch.float64)
+    xd = torch.zeros_like(fd)
+    rep = lib.mg_solve(h, fd, xd, tol=1e-10)
+    assert rep["rel_res"] <= 1e-10 and rep["status"] == "MG_OK"
+    # independent residual check with the oracle's operator
+    hier, fm = omg.setup(g, stencil_of(g), policy=opts.get("coarsen", 0),
+                         max_levels=opts.get("max_levels", 16))
+    b, mean = omg.prepare_rhs(fm["J"], f)
+    x = to_np(xd)
+    assert abs(rep["removed_mean"] - mean) <= 1e-12 * max(1.0, abs(mean))
+    rel = np.linalg.norm(b - hier.levels[0].A @ x) / np.linalg.norm(b)
+    assert rel <= 1.05e-10
+    assert abs((fm["J"].ravel() * x).sum()) <= 1e-12 * np.abs(fm["J"].ravel() * x).sum()
+    # error against the oracle solution, both to 1e-12
+    xd.zero_()
+    rep = lib.mg_solve(h, fd, xd, tol=1e-12)
+    xo, info = omg.solve(g, f.ravel(), tol=1e-12, hier=hier, fm=fm, max_iters=400)
+    assert info["converged"]
+    err = np.abs(to_np(xd) - xo).max() / np.abs(xo).max()
+    assert err <= 1e-9, err
+
+
+def test_solve_warm_start_and_host_buffers(lib):
+    torch, dev = torch_dev()
+    w = W.single("single_sphere_128", 4)
+    g, f = w["grid"], w["f"]
+    h = lib.mg_setup(g, dict(precision=1))
+    fd = to_dev(f, torch.float64)
+    xd = torch.zeros_like(fd)
+    r1 = lib.mg_solve(h, fd, xd, tol=1e-10)
+    r2 = lib.mg_solve(h, fd, xd, tol=1e-10)          # warm start: already converged
+    assert r2["iters"] <= 1
+    xh = np.zeros_like(f)
+    r3 = lib.mg_solve_host(h, f, xh, tol=1e-10)
+    assert r3["iters"] == r1["iters"]
+    np.testing.assert_allclose(xh.ravel(), to_np(xd), atol=1e-9 * np.abs(xh).max())
+
+
+def test_nan_rhs_is_reported(lib):
+    torch, dev = torch_dev()
+    g = W.grid_desc(8)
+    h = lib.mg_setup(g)
+    f = np.zeros((8, 8, 16))
+    f[3, 3, 3] = np.nan
+    with pytest.raises(lib.MGError) as e:
+        lib.mg_solve(h, to_dev(f, torch.float64), to_dev(np.zeros_like(f), torch.float64))
+    assert e.value.status == lib.MG_ENAN
+
+
+def test_max_iters_reports_noconv(lib):
+    torch, dev = torch_dev()
+    w = W.single("single_sphere_128", 4)
+    h = lib.mg_setup(w["grid"], dict(max_iters=2))
+    fd = to_dev(w["f"], torch.float64)
+    rep = lib.mg_solve(h, fd, torch.zeros_like(fd), tol=1e-10, allow=(lib.MG_ENOCONV,))
+    assert rep["status"] == "MG_ENOCONV" and rep["iters"] == 2
