@@ -203,10 +203,11 @@ mg_status mg_vcycle(mg_handle* h, int prec, void* x_dev, const void* b_dev);
  * CUDA events on the handle's stream (a few events per V-cycle) and
  * accumulates their device time.  Slots: 0 = fine-level smoothing launches,
  * 1 = outer FP64 residual, 2 = fine-level residual + restriction,
- * 3 = fine-level prolongation + correction, 4 = outer update.
+ * 3 = fine-level prolongation + correction, 4 = outer update, 5 = the
+ * single-launch coarse tail of the V-cycle.
  * ------------------------------------------------------------------------- */
 enum { MG_PROF_SMOOTH0 = 0, MG_PROF_RESIDUAL = 1, MG_PROF_RESTRICT0 = 2, MG_PROF_PROLONG0 = 3,
-       MG_PROF_UPDATE = 4, MG_PROF_SLOTS = 8 };
+       MG_PROF_UPDATE = 4, MG_PROF_TAIL = 5, MG_PROF_SLOTS = 8 };
 /* Enable (on != 0) or disable timing; either way the accumulators reset. */
 mg_status mg_profile_enable(mg_handle* h, int on);
 /* Accumulated device milliseconds and launch count of one slot. */

@@ -9,8 +9,8 @@ own cell-centred design, written out plainly so every GPU step has a CPU twin:
   coarsening factor along q (keeps the stencil pattern, A 1 = 0 and 1^T A = 0);
 * coarsening policy: a direction may halve while its cell count is even and
   >= 4 (longitude additionally stays even); with the ``semi`` policy only the
-  directions whose mean diagonal coefficient is >= 1/4 of the strongest are
-  halved (semi-coarsening toward isotropy, the idea behind SMG);
+  directions whose mean diagonal coefficient is >= SEMI_RATIO = 0.7 of the
+  strongest are halved (semi-coarsening toward isotropy, the idea behind SMG);
 * restriction: sum over children (b is volume integrated);
 * prolongation: cell-centred trilinear (3/4, 1/4 per halved direction),
   mirror at walls, wrap in longitude;
@@ -33,6 +33,7 @@ from .operator import assemble
 
 SEMI, FULL = 0, 1
 GS, JACOBI = 0, 1
+SEMI_RATIO = 0.7
 
 
 @dataclass
@@ -44,6 +45,7 @@ class Level:
     D: np.ndarray = None
     factors: tuple = None  # (c_zeta, c_eta, c_xi) to the next level, or None
     colours: list = field(default_factory=list)
+    colour_rows: list = field(default_factory=list)   # A restricted to each colour's rows
 
     @property
     def n(self):
@@ -66,6 +68,7 @@ def make_level(shape, fm, stencil):
     col = colour_of(lv.shape, stencil)
     ncol = 2 if stencil == 7 else 4
     lv.colours = [np.nonzero(col == c)[0] for c in range(ncol)]
+    lv.colour_rows = [lv.A[idx] for idx in lv.colours]
     return lv
 
 
@@ -91,7 +94,7 @@ def plan_factors(shape, fm, policy):
     else:
         m = mean_diagonal_coefficients(shape, fm)
         top = max(m[d] for d in can)
-        chosen = [d for d in can if m[d] >= 0.25 * top]
+        chosen = [d for d in can if m[d] >= SEMI_RATIO * top]
     return tuple(2 if d in chosen else 1 for d in range(3))
 
 
@@ -170,8 +173,8 @@ def smooth(lv, x, b, sweeps, kind=GS):
     x = np.array(x, dtype=np.float64, copy=True)
     if kind == GS:
         for _ in range(sweeps):
-            for idx in lv.colours:
-                x[idx] += (b[idx] - lv.A[idx] @ x) / lv.D[idx]
+            for idx, rows in zip(lv.colours, lv.colour_rows):
+                x[idx] += (b[idx] - rows @ x) / lv.D[idx]
     else:
         w = 6.0 / 7.0 if lv.stencil == 7 else 4.0 / 5.0
         for _ in range(sweeps):

@@ -271,7 +271,7 @@ def mg_vcycle(h: Handle, prec: int, x, b):
     _check(_lib.mg_vcycle(h.ptr, prec, _ptr(x, _vdtype(prec)), _ptr(b, _vdtype(prec))), "mg_vcycle")
 
 
-PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE = range(5)
+PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL = range(6)
 
 
 def mg_profile_enable(h: Handle, on: bool = True):

@@ -1,8 +1,10 @@
 // capi.cu - handle lifecycle, multigrid hierarchy, V-cycle schedule, the
 // FP64 iterative-refinement loop and the C ABI of include/mg.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -53,6 +55,14 @@ LevelView Level::view(int stencil) const {
 namespace {
 
 constexpr int kMaxCoarse = 2048;   // largest coarsest level (dense bordered inverse)
+// Semi-coarsening: a direction halves only if its mean diagonal coefficient is
+// at least this fraction of the strongest coarsenable direction's.
+constexpr double kSemiRatio = 0.7;
+// Levels at or below this many cells (never the fine level) can run as one
+// launch: the coarse tail, one cluster of 8 CTAs x 512 threads (opt-in with
+// MG_TAIL=1: on the 128 x 128 x 256 sphere it measured slower than graph-
+// launched per-level kernels, 11.1 vs 9.7 ms per solve).
+constexpr i64 kTailCells = 65536;
 
 bool finite(double v) { return std::isfinite(v); }
 
@@ -187,7 +197,36 @@ void free_handle(mg_handle* h) {
     for (int s = 0; s < MG_PROF_SLOTS; ++s)
         if (h->prof_open[s]) cudaEventDestroy(h->prof_open[s]);
     for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+    for (auto& p : h->graph_events) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    plan_destroy(h->solo);
+    plan_destroy(h->batch);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+// The index decoders divide by magic numbers; check them against true
+// division on boundary and sampled dividends up to the level's cell count.
+bool fastdiv_ok(const Dims& D) {
+    const FastDiv* fd[3] = {&D.dph, &D.dth, &D.dhk};
+    const unsigned long long top = (unsigned long long)D.n() + 2;
+    for (const FastDiv* f : fd) {
+        unsigned long long n = 0;
+        for (int it = 0; it < 4096 && n < top; ++it) {
+            const unsigned v = (unsigned)n;
+            if (f->div(v) != v / f->d) return false;
+            n = n < 64 ? n + 1 : n + n / 7 + 1;
+        }
+        for (unsigned long long v : {(unsigned long long)f->d - 1, (unsigned long long)f->d,
+                                     (unsigned long long)f->d + 1, top - 1, 0x7fffffffull}) {
+            if (f->div((unsigned)v) != (unsigned)v / f->d) return false;
+        }
+    }
+    return true;
 }
 
 // Longest-first plan of the next level: which directions halve.
@@ -215,7 +254,7 @@ mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
     double top = 0.0;
     for (int d = 0; d < 3; ++d)
         if (can[d]) top = std::max(top, m[d]);
-    for (int d = 0; d < 3; ++d) f[d] = (can[d] && m[d] >= 0.25 * top) ? 2 : 1;
+    for (int d = 0; d < 3; ++d) f[d] = (can[d] && m[d] >= kSemiRatio * top) ? 2 : 1;
     return MG_OK;
 }
 
@@ -224,8 +263,16 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     h->opts = *o;
     h->stencil = stencil_of(g, o);
     h->prec = o->precision;
-    h->stream = stream;
+    h->user_stream = stream;
+    h->use_graph = std::getenv("MG_NO_GRAPH") == nullptr;
+    h->fused_rb = std::getenv("MG_FUSED_RB") != nullptr;   // one-pass tile sweeps: opt-in
     CK(cudaGetDevice(&h->device));
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->ev_in, h->user_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+    stream = h->stream;
     CK(cudaMallocHost((void**)&h->hscal, sizeof(double) * SC_COUNT));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
@@ -272,8 +319,10 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         if (stored(h->stencil, a) && !(L0.g64[a] = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
     if (!(h->J64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
     if (!(h->b64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
+    if (!(h->x64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
     if (!(h->part = (double*)dalloc(h, sizeof(double) * kRedBlocks))) return MG_ENOMEM;
     if (!(h->scal = (double*)dalloc(h, sizeof(double) * SC_COUNT))) return MG_ENOMEM;
+    if (!(h->one_task = (BTask*)dalloc(h, sizeof(BTask)))) return MG_ENOMEM;
     CK(launch_face_metric(T, L0.D, h->stencil, L0.g64, h->J64, stream));
     CKS(device_sum(h, h->J64, nullptr, N, 0));
     CKS(read_scalars(h, 1));
@@ -298,6 +347,11 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         CK(launch_coarsen_faces(fine.view(h->stencil), c.D, c.g64, stream));
         h->L.push_back(c);
     }
+    for (const Level& lv : h->L)
+        if (!fastdiv_ok(lv.D)) {
+            set_error("index divisor self-check failed");
+            return MG_EINVAL;
+        }
     Level& last = h->L.back();
     last.cz = last.ce = last.cx = 0;
     h->ncoarse = (int)last.D.n();
@@ -361,6 +415,27 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     }
     h->binv = dA;   // reuse the buffer
     CK(cudaMemcpyAsync(h->binv, Binv.data(), sizeof(double) * nc * nc, cudaMemcpyHostToDevice, stream));
+
+    // --- coarse tail: the deepest run of levels small enough for one cluster
+    const int nl = (int)h->L.size();
+    int t = nl;
+    while (t - 1 >= 1 && h->L[t - 1].D.n() <= kTailCells) --t;
+    const bool want_tail = std::getenv("MG_TAIL") != nullptr && o->smoother == MG_SMOOTH_GS &&
+                           nl - t >= 2 && nl - t <= kMaxTail &&
+                           tail_max_clusters(h->tail_cluster, h->stencil, h->prec) > 0;
+    if (want_tail) {
+        TailTask task{};
+        task.nlev = nl - t;
+        task.nu1 = o->nu1;
+        task.nu2 = o->nu2;
+        task.binv = h->binv;
+        task.ncoarse = nc;
+        for (int l = t; l < nl; ++l) task.lev[l - t] = TailLevel{h->L[l].view(h->stencil), h->L[l].e, h->L[l].r};
+        if (!(h->tail_dev = (TailTask*)dalloc(h, sizeof(TailTask)))) return MG_ENOMEM;
+        CK(cudaMemcpyAsync(h->tail_dev, &task, sizeof(TailTask), cudaMemcpyHostToDevice, stream));
+        h->tail_host = task;
+        h->tail_level = t;
+    }
     CK(cudaStreamSynchronize(stream));
     CK(cudaGetLastError());
     return MG_OK;
@@ -389,19 +464,38 @@ static cudaEvent_t prof_event(mg_handle* h) {
     return e;
 }
 
+// Inside a stream capture the events become event-record nodes of the graph
+// (re-recorded at every replay and read after each one).
+static void prof_record(mg_handle* h, cudaEvent_t e) {
+    if (h->capturing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, h->stream);
+}
+
 void prof_begin(mg_handle* h, int slot) {
     if (!h->prof_on) return;
     cudaEvent_t e = prof_event(h);
-    cudaEventRecord(e, h->stream);
+    prof_record(h, e);
     h->prof_open[slot] = e;
 }
 
 void prof_end(mg_handle* h, int slot, int nlaunch) {
     if (!h->prof_on || !h->prof_open[slot]) return;
     cudaEvent_t e = prof_event(h);
-    cudaEventRecord(e, h->stream);
-    h->prof_pending.push_back({slot, h->prof_open[slot], e, nlaunch});
+    prof_record(h, e);
+    if (h->capturing) h->graph_events.push_back({slot, h->prof_open[slot], e, nlaunch});
+    else h->prof_pending.push_back({slot, h->prof_open[slot], e, nlaunch});
     h->prof_open[slot] = nullptr;
+}
+
+static void graph_prof_collect(mg_handle* h) {
+    for (auto& p : h->graph_events) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->prof_ms[p.slot] += ms;
+            h->prof_n[p.slot] += p.n;
+        }
+        cudaGetLastError();
+    }
 }
 
 void prof_collect(mg_handle* h) {
@@ -424,7 +518,24 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
     if (sweeps == 0) return MG_OK;
     if (level == 0) prof_begin(h, MG_PROF_SMOOTH0);
     int n = 0;
-    if (kind == MG_SMOOTH_GS) {
+    if (kind == MG_SMOOTH_GS && h->fused_rb && h->stencil == 7 && rb7_fits(lv.D)) {
+        // one-pass red-black sweeps ping-pong between x and the level's scratch
+        void* bufs[2] = {x, lv.t};
+        for (int s = 0; s < sweeps; ++s, ++n) {
+            BTask t{};
+            t.v = v;
+            t.x = bufs[s & 1];
+            t.y = bufs[(s + 1) & 1];
+            t.b = b;
+            t.block0 = 0;
+            t.nblocks = rb7_tiles(lv.D);
+            CK(cudaMemcpyAsync(h->one_task, &t, sizeof(BTask), cudaMemcpyHostToDevice, h->stream));
+            CK(launch_batch(h->one_task, 1, t.nblocks, nullptr, BOP_RB7, 0, 7, prec, h->stream));
+        }
+        if (sweeps & 1) {
+            CK(cudaMemcpyAsync(x, lv.t, value_bytes(prec) * lv.D.n(), cudaMemcpyDeviceToDevice, h->stream));
+        }
+    } else if (kind == MG_SMOOTH_GS) {
         const int ncol = h->stencil == 7 ? 2 : 4;
         for (int s = 0; s < sweeps; ++s)
             for (int c = 0; c < ncol; ++c, ++n) CK(launch_gs_colour(v, prec, x, b, c, h->stream));
@@ -449,7 +560,9 @@ mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
         CK(launch_coarse_solve(h->binv, h->ncoarse, prec, b0, x0, h->stream));
         return MG_OK;
     }
-    for (int l = 0; l < nl - 1; ++l) {
+    // levels [0, top) run launch by launch; level top starts the tail, or is the coarsest
+    const int top = h->tail_level > 0 ? h->tail_level : nl - 1;
+    for (int l = 0; l < top; ++l) {
         void* x = l == 0 ? x0 : h->L[l].e;
         const void* b = l == 0 ? b0 : h->L[l].r;
         CKS(smooth(h, l, prec, x, b, h->opts.nu1, kind));
@@ -459,8 +572,14 @@ mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
         if (l == 0) prof_end(h, MG_PROF_RESTRICT0, 1);
         h->launches += 1;
     }
-    CK(launch_coarse_solve(h->binv, h->ncoarse, prec, h->L[nl - 1].r, h->L[nl - 1].e, h->stream));
-    for (int l = nl - 2; l >= 0; --l) {
+    if (h->tail_level > 0) {
+        prof_begin(h, MG_PROF_TAIL);
+        CK(launch_tail(h->tail_dev, 1, h->tail_cluster, h->stencil, prec, h->stream));
+        prof_end(h, MG_PROF_TAIL, 1);
+    } else {
+        CK(launch_coarse_solve(h->binv, h->ncoarse, prec, h->L[nl - 1].r, h->L[nl - 1].e, h->stream));
+    }
+    for (int l = top - 1; l >= 0; --l) {
         void* x = l == 0 ? x0 : h->L[l].e;
         const void* b = l == 0 ? b0 : h->L[l].r;
         if (l == 0) prof_begin(h, MG_PROF_PROLONG0);
@@ -496,6 +615,20 @@ double model_bytes_per_iteration(const mg_handle* h) {
     else total += N * (8 + 8 + nc * 8 + 4) + N * (4 + 16) + N * 4;  // residual, update, zero e
     return total;
 }
+
+// Orders a call's work after the caller's stream and the caller's stream
+// after the call's work (the handle computes on a private stream).
+struct StreamJoin {
+    mg_handle* h;
+    explicit StreamJoin(mg_handle* hh) : h(hh) {
+        cudaEventRecord(h->ev_in, h->user_stream);
+        cudaStreamWaitEvent(h->stream, h->ev_in, 0);
+    }
+    ~StreamJoin() {
+        cudaEventRecord(h->ev_out, h->stream);
+        cudaStreamWaitEvent(h->user_stream, h->ev_out, 0);
+    }
+};
 
 }  // namespace mgs
 
@@ -554,6 +687,8 @@ mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_han
     }
     mg_handle* h = new (std::nothrow) mg_handle();
     if (!h) return MG_ENOMEM;
+    static std::atomic<unsigned long long> next_serial{1};
+    h->serial = next_serial++;
     mg_status st;
     try {
         st = setup_impl(g, o, (cudaStream_t)stream, h);
@@ -580,7 +715,7 @@ void mg_destroy(mg_handle* h) {
 
 mg_status mg_set_stream(mg_handle* h, void* stream) {
     if (!h) return MG_EINVAL;
-    h->stream = (cudaStream_t)stream;
+    h->user_stream = (cudaStream_t)stream;
     return MG_OK;
 }
 
@@ -603,6 +738,7 @@ mg_status mg_get_metric(mg_handle* h, int level, int component, double* dst) {
         return MG_EINVAL;
     const Level& lv = h->L[level];
     const size_t bytes = sizeof(double) * lv.D.n();
+    StreamJoin join(h);
     if (component == 9) {
         if (level != 0) return MG_EINVAL;
         CK(cudaMemcpyAsync(dst, h->J64, bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -626,6 +762,7 @@ mg_status mg_get_metric(mg_handle* h, int level, int component, double* dst) {
 mg_status mg_apply(mg_handle* h, int level, int prec, const void* x, void* y) {
     LEVEL_CHECK(h, level, prec);
     if (!x || !y) return MG_EINVAL;
+    StreamJoin join(h);
     CK(launch_apply(h->L[level].view(h->stencil), prec, x, y, h->stream));
     return MG_OK;
 }
@@ -633,12 +770,14 @@ mg_status mg_apply(mg_handle* h, int level, int prec, const void* x, void* y) {
 mg_status mg_smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
     LEVEL_CHECK(h, level, prec);
     if (!x || !b || sweeps < 0 || kind < 0 || kind > 1) return MG_EINVAL;
+    StreamJoin join(h);
     return smooth(h, level, prec, x, b, sweeps, kind);
 }
 
 mg_status mg_restrict_residual(mg_handle* h, int level, int prec, const void* x, const void* b, void* rc) {
     LEVEL_CHECK(h, level, prec);
     if (!x || !b || !rc || level + 1 >= (int)h->L.size()) return MG_EINVAL;
+    StreamJoin join(h);
     CK(launch_restrict_residual(h->L[level].view(h->stencil), h->L[level + 1].D, prec, x, b, rc, nullptr,
                                 h->stream));
     return MG_OK;
@@ -647,12 +786,14 @@ mg_status mg_restrict_residual(mg_handle* h, int level, int prec, const void* x,
 mg_status mg_prolong_add(mg_handle* h, int level, int prec, const void* ec, void* x) {
     LEVEL_CHECK(h, level, prec);
     if (!x || !ec || level + 1 >= (int)h->L.size()) return MG_EINVAL;
+    StreamJoin join(h);
     CK(launch_prolong_add(h->L[level].view(h->stencil), h->L[level + 1].D, prec, ec, x, h->stream));
     return MG_OK;
 }
 
 mg_status mg_coarse_solve(mg_handle* h, int prec, const void* r, void* e) {
     if (!h || !r || !e || prec < 0 || prec > 2) return MG_EINVAL;
+    StreamJoin join(h);
     CK(launch_coarse_solve(h->binv, h->ncoarse, prec, r, e, h->stream));
     return MG_OK;
 }
@@ -660,90 +801,15 @@ mg_status mg_coarse_solve(mg_handle* h, int prec, const void* r, void* e) {
 mg_status mg_vcycle(mg_handle* h, int prec, void* x, const void* b) {
     LEVEL_CHECK(h, 0, prec);
     if (!x || !b) return MG_EINVAL;
+    StreamJoin join(h);
     return vcycle(h, prec, x, b);
 }
 
 mg_status mg_solve(mg_handle* h, const double* f, double* x, double tol, mg_report* rep) {
     if (!h || !f || !x || !(tol >= 0) || !std::isfinite(tol)) return MG_EINVAL;
-    const i64 N = h->L[0].D.n();
-    const LevelView v0 = h->L[0].view(h->stencil);
-    cudaStream_t s = h->stream;
-    mg_report R;
-    std::memset(&R, 0, sizeof(R));
-    h->launches = 0;
-    R.levels = (int)h->L.size();
-    R.stencil = h->stencil;
-    CK(cudaEventRecord(h->ev0, s));
-
-    // b = J (f - mean_J f)
-    CKS(device_sum(h, h->J64, f, N, SC_SUMJF));
-    CK(launch_rhs(h->J64, f, h->scal + SC_SUMJF, h->sumJ, h->b64, N, h->part, s));
-    CK(launch_finalize(h->part, red_blocks(N), 0, h->scal + SC_BB, s));
-    h->launches += 2;
-    CKS(read_scalars(h, 2));
-    R.removed_mean = h->hscal[SC_SUMJF] / h->sumJ;
-    const double bn = std::sqrt(h->hscal[SC_BB]);
-    if (!std::isfinite(bn)) {
-        set_error("non-finite right-hand side");
-        if (rep) {
-            *rep = R;
-            rep->status = MG_ENAN;
-        }
-        return MG_ENAN;
-    }
-    const double bnorm = bn > 0 ? bn : 1.0;
-
-    mg_status st = MG_OK;
-    double scale = bn > 0 ? std::ldexp(1.0, -(int)std::lround(std::log2(bn / std::sqrt((double)N)))) : 1.0;
-    double best = INFINITY;
-    int it = 0;
-    Level& l0 = h->L[0];
-    for (;;) {
-        float* r32 = h->prec == PREC64 ? nullptr : (float*)l0.r;
-        prof_begin(h, MG_PROF_RESIDUAL);
-        CK(launch_outer_residual(v0, x, h->b64, r32, scale, h->part, s));
-        prof_end(h, MG_PROF_RESIDUAL, 1);
-        CK(launch_finalize(h->part, red_blocks(N), 0, h->scal + SC_RR, s));
-        h->launches += 2;
-        CKS(read_scalars(h, SC_RR + 1));
-        const double rn = std::sqrt(h->hscal[SC_RR]);
-        const double rel = rn / bnorm;
-        if (it < MG_HIST) R.res_hist[it] = rel;
-        R.rel_res = rel;
-        if (!std::isfinite(rel)) { st = MG_ENAN; set_error("non-finite residual"); break; }
-        if (rel <= tol) break;
-        best = std::min(best, rel);
-        if (rel > 1e3 * best) { st = MG_EDIVERGED; set_error("residual diverged"); break; }
-        if (it >= h->opts.max_iters) { st = MG_ENOCONV; set_error("max_iters reached"); break; }
-        if (h->prec == PREC64) {
-            CKS(vcycle(h, PREC64, x, h->b64));
-        } else {
-            CK(cudaMemsetAsync(l0.e, 0, sizeof(float) * N, s));
-            CKS(vcycle(h, h->prec, l0.e, l0.r));
-            prof_begin(h, MG_PROF_UPDATE);
-            CK(launch_update(x, (const float*)l0.e, 1.0 / scale, N, s));
-            prof_end(h, MG_PROF_UPDATE, 1);
-            h->launches += 1;
-            scale = rn > 0 ? std::ldexp(1.0, -(int)std::lround(std::log2(rn / std::sqrt((double)N)))) : 1.0;
-        }
-        ++it;
-    }
-    // gauge: remove the J-weighted mean of x
-    CKS(device_sum(h, h->J64, x, N, SC_SUMJX));
-    CK(launch_shift(x, h->scal + SC_SUMJX, h->sumJ, N, s));
-    h->launches += 1;
-    CK(cudaEventRecord(h->ev1, s));
-    CK(cudaEventSynchronize(h->ev1));
-    prof_collect(h);
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    R.iters = it;
-    R.seconds = ms * 1e-3;
-    R.model_bytes = model_bytes_per_iteration(h) * it;
-    R.status = st;
-    R.launches = h->launches;
-    if (rep) *rep = R;
-    return st;
+    StreamJoin join(h);
+    if (!h->solo) CKS(plan_create(&h, 1, &h->solo));
+    return plan_solve(h->solo, &f, &x, &tol, rep);
 }
 
 mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, double tol, mg_report* rep) {
@@ -801,12 +867,37 @@ mg_status mg_profile_read(mg_handle* h, int slot, double* ms, long long* launche
 mg_status mg_solve_batch(mg_handle* const* hs, int n, const double* const* f, double* const* x,
                          const double* tol, mg_report* reps) {
     if (!hs || n < 0 || (n > 0 && (!f || !x || !tol))) return MG_EINVAL;
-    mg_status worst = MG_OK;
+    if (n == 0) return MG_OK;
     for (int s = 0; s < n; ++s) {
-        const mg_status st = mg_solve(hs[s], f[s], x[s], tol[s], reps ? reps + s : nullptr);
-        if (st != MG_OK && worst == MG_OK) worst = st;
+        if (!hs[s] || !f[s] || !x[s] || !(tol[s] >= 0) || !std::isfinite(tol[s])) return MG_EINVAL;
+        for (int q = 0; q < s; ++q)
+            if (hs[q] == hs[s]) {
+                set_error("a handle appears twice in the batch");
+                return MG_EINVAL;
+            }
     }
-    return worst;
+    mg_handle* h0 = hs[0];
+    StreamJoin join(h0);
+    std::vector<unsigned long long> key;
+    for (int s = 0; s < n; ++s) key.push_back(hs[s]->serial);
+    if (!h0->batch || h0->batch_key != key) {
+        plan_destroy(h0->batch);
+        h0->batch = nullptr;
+        h0->batch_key.clear();
+        CKS(plan_create(hs, n, &h0->batch));
+        h0->batch_key = key;
+    }
+    // the other handles' caller streams are ordered before the batch as well
+    for (int s = 1; s < n; ++s) {
+        CK(cudaEventRecord(hs[s]->ev_in, hs[s]->user_stream));
+        CK(cudaStreamWaitEvent(h0->stream, hs[s]->ev_in, 0));
+    }
+    const mg_status st = plan_solve(h0->batch, f, x, tol, reps);
+    for (int s = 1; s < n; ++s) {
+        CK(cudaEventRecord(hs[s]->ev_out, h0->stream));
+        CK(cudaStreamWaitEvent(hs[s]->user_stream, hs[s]->ev_out, 0));
+    }
+    return st;
 }
 
 }  // extern "C"

@@ -9,6 +9,8 @@
 
 namespace mgs {
 
+struct Plan;
+
 struct Level {
     Dims D{};
     int cz = 0, ce = 0, cx = 0;       // halving factors to the next level
@@ -32,11 +34,14 @@ struct mg_handle {
     mg_opts opts{};
     int stencil = 7;
     int prec = 1;                     // PREC64 / PREC32 / PREC16
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;        // private work stream of the handle
+    cudaStream_t user_stream = nullptr;   // caller's stream; joined by events
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int device = 0;
     std::vector<mgs::Level> L;
     std::vector<void*> dev_allocs;
     double* J64 = nullptr;            // cell |J^{-1}| (fine)
+    double* x64 = nullptr;            // the iterate (fine); copied from / to the caller's x
     double* b64 = nullptr;            // volume-integrated right side (fine)
     double* part = nullptr;           // reduction partials (kRedBlocks)
     double* scal = nullptr;           // device scalars
@@ -59,6 +64,20 @@ struct mg_handle {
     cudaEvent_t prof_open[MG_PROF_SLOTS] = {};
     std::vector<Pending> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
+    // outer iterations run as captured graphs (solver.cu)
+    bool use_graph = true;
+    bool fused_rb = false;            // one-pass red-black tile sweeps (opt-in, MG_FUSED_RB=1)
+    mgs::BTask* one_task = nullptr;   // task table of stand-alone one-pass sweeps
+    int tail_level = 0;               // first level of the single-launch coarse tail (0: none)
+    int tail_cluster = 8;             // CTAs per tail cluster
+    mgs::TailTask* tail_dev = nullptr;
+    mgs::TailTask tail_host{};
+    bool capturing = false;
+    std::vector<Pending> graph_events;     // event nodes inside the current graph
+    mgs::Plan* solo = nullptr;             // the batch-of-one plan of mg_solve
+    mgs::Plan* batch = nullptr;            // last mg_solve_batch plan led by this handle
+    std::vector<unsigned long long> batch_key;   // serials of the batch plan's handles
+    unsigned long long serial = 0;                // unique per handle in the process
     // mg_solve_host staging
     double* hf = nullptr;
     double* hx = nullptr;
@@ -67,13 +86,15 @@ struct mg_handle {
 };
 
 namespace mgs {
-// Device scalar slots of mg_handle::scal.
-enum { SC_SUMJF = 0, SC_BB = 1, SC_RR = 2, SC_SUMJX = 3, SC_COUNT = 16 };
 
 mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0);
 void prof_begin(mg_handle* h, int slot);
 void prof_end(mg_handle* h, int slot, int nlaunch);
 void prof_collect(mg_handle* h);   // after a stream synchronisation
+// batch plans (solver.cu)
+mg_status plan_create(mg_handle* const* hs, int n, Plan** out);
+void plan_destroy(Plan* pl);
+mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps);
 mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind);
 double model_bytes_per_iteration(const mg_handle* h);
 }  // namespace mgs

@@ -70,10 +70,8 @@ __global__ void k_face_metric(MetricTables t, Dims D, int stencil, double* g0,
     const i64 n = D.n();
     double* g[9] = {g0, g1, g2, g3, g4, g5, g6, g7, g8};
     for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x) {
-        const int k = (int)(c % D.nph);
-        const i64 ji = c / D.nph;
-        const int i = (int)(ji % D.nth);
-        const int j = (int)(ji / D.nth);
+        const C3 cc = decode(D, c);
+        const int k = cc.k, i = cc.i, j = cc.j;
         double row[3], det_sum = 0.0;
         // lower faces: rows stored (zero on the lower walls), determinants kept
         for (int d = 0; d < 3; ++d) {
@@ -107,10 +105,8 @@ __global__ void k_coarsen(CoefF64 f, Dims Df, int cz, int ce, int cx, int stenci
     const int cfac[3] = {cz, ce, cx};
     const i64 n = Dc.n();
     for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x) {
-        const int K = (int)(c % Dc.nph);
-        const i64 JI = c / Dc.nph;
-        const int I = (int)(JI % Dc.nth);
-        const int Jr = (int)(JI / Dc.nth);
+        const C3 cc = decode(Dc, c);
+        const int K = cc.k, I = cc.i, Jr = cc.j;
         for (int d = 0; d < 3; ++d) {
             // fine plane of the face along d; children along the other two axes
             const int j0 = ce * Jr, i0 = cz * I, k0 = cx * K;

@@ -17,8 +17,35 @@ namespace mgs {
 
 typedef long long i64;
 
+// Division of 32-bit unsigned n by a fixed d with one high multiply:
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, n / d = (hi32(n m) + n) >> s
+// (the round-up method of Granlund and Montgomery, exact for all n < 2^32).
+struct FastDiv {
+    unsigned d = 1, m = 1, s = 0;
+    __host__ __device__ FastDiv() {}
+    __host__ __device__ explicit FastDiv(unsigned dd) : d(dd ? dd : 1) {
+        s = 0;
+        while ((1ull << s) < d) ++s;
+        m = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+    }
+    __host__ __device__ __forceinline__ unsigned div(unsigned n) const {
+#ifdef __CUDA_ARCH__
+        const unsigned t = __umulhi(n, m);
+#else
+        const unsigned t = (unsigned)(((unsigned long long)n * m) >> 32);
+#endif
+        return (unsigned)(((unsigned long long)t + n) >> s);
+    }
+};
+
+// Cells per direction, with the divisors the kernels decode indices by.
+// Grids hold fewer than 2^31 cells, so linear indices are 32-bit.
 struct Dims {
-    int nr, nth, nph;
+    int nr = 0, nth = 0, nph = 0;
+    FastDiv dph, dth, dhk;   // by nph, by nth, by nph / 2
+    __host__ __device__ Dims() {}
+    __host__ __device__ Dims(int r, int t, int p)
+        : nr(r), nth(t), nph(p), dph((unsigned)p), dth((unsigned)t), dhk((unsigned)(p >= 2 ? p / 2 : 1)) {}
     __host__ __device__ i64 n() const { return (i64)nr * nth * nph; }
 };
 
@@ -26,10 +53,32 @@ struct C3 {
     int j, i, k;
 };
 
-__host__ __device__ __forceinline__ i64 cidx(const Dims& D, int j, int i, int k) {
-    return ((i64)j * D.nth + i) * D.nph + k;
+__host__ __device__ __forceinline__ int cidx(const Dims& D, int j, int i, int k) {
+    return (j * D.nth + i) * D.nph + k;
 }
-__host__ __device__ __forceinline__ i64 cidx(const Dims& D, C3 c) { return cidx(D, c.j, c.i, c.k); }
+__host__ __device__ __forceinline__ int cidx(const Dims& D, C3 c) { return cidx(D, c.j, c.i, c.k); }
+
+// linear cell index -> (j, i, k)
+__host__ __device__ __forceinline__ C3 decode(const Dims& D, i64 cl) {
+    const unsigned c = (unsigned)cl;
+    const unsigned q = D.dph.div(c);
+    const unsigned j = D.dth.div(q);
+    C3 r;
+    r.k = (int)(c - q * (unsigned)D.nph);
+    r.i = (int)(q - j * (unsigned)D.nth);
+    r.j = (int)j;
+    return r;
+}
+
+// work item t of a colour pass (rows of nph / 2 items) -> (kk, i, j)
+__host__ __device__ __forceinline__ void decode_half(const Dims& D, i64 tl, int& kk, int& i, int& j) {
+    const unsigned t = (unsigned)tl;
+    const unsigned row = D.dhk.div(t);
+    const unsigned jj = D.dth.div(row);
+    kk = (int)(t - row * (unsigned)(D.nph >> 1));
+    i = (int)(row - jj * (unsigned)D.nth);
+    j = (int)jj;
+}
 
 // Neighbour along paper direction q (0 zeta -> i, 1 eta -> j, 2 xi -> k):
 // mirror-clamp at the colatitude and radial walls, wrap in longitude.
@@ -111,6 +160,44 @@ __device__ __forceinline__ T apply_cell(const CF& cf, const XA& X, const Dims& D
     return acc;
 }
 
+// r_c = b_c - (A x)_c with every face term fused into one multiply-add on r:
+// r = b - sum_d [F_d(upper) - F_d(lower)], each F expanded term by term.
+// Same operator as apply_cell; fewer FP64 instructions (FP64 issues at about
+// 1/64 of the FP32 rate on GB300, so the outer residual is instruction bound).
+template <int S, int d, typename XA>
+__device__ __forceinline__ double face_into(double r, double sgn, const CoefF64& cf, const XA& X, const Dims& D,
+                                            C3 L, C3 U) {
+    const i64 u = cidx(D, U);
+    r = fma(sgn * cf(4 * d, u), X(U) - X(L), r);
+    if (S == 19) {
+        if (d != 0) {
+            const double w = sgn * 0.25 * cf(3 * d + 0, u);
+            r = fma(w, (X(shift<0>(L, +1, D)) + X(shift<0>(U, +1, D))) - (X(shift<0>(L, -1, D)) + X(shift<0>(U, -1, D))), r);
+        }
+        if (d != 1) {
+            const double w = sgn * 0.25 * cf(3 * d + 1, u);
+            r = fma(w, (X(shift<1>(L, +1, D)) + X(shift<1>(U, +1, D))) - (X(shift<1>(L, -1, D)) + X(shift<1>(U, -1, D))), r);
+        }
+        if (d != 2) {
+            const double w = sgn * 0.25 * cf(3 * d + 2, u);
+            r = fma(w, (X(shift<2>(L, +1, D)) + X(shift<2>(U, +1, D))) - (X(shift<2>(L, -1, D)) + X(shift<2>(U, -1, D))), r);
+        }
+    }
+    return r;
+}
+
+template <int S, typename XA>
+__device__ __forceinline__ double residual_cell(const CoefF64& cf, const XA& X, const Dims& D, C3 c, double b) {
+    double r = b;
+    if (c.j > 0) r = face_into<S, 1>(r, +1.0, cf, X, D, shift<1>(c, -1, D), c);
+    if (c.j < D.nr - 1) r = face_into<S, 1>(r, -1.0, cf, X, D, c, shift<1>(c, +1, D));
+    if (c.i > 0) r = face_into<S, 0>(r, +1.0, cf, X, D, shift<0>(c, -1, D), c);
+    if (c.i < D.nth - 1) r = face_into<S, 0>(r, -1.0, cf, X, D, c, shift<0>(c, +1, D));
+    r = face_into<S, 2>(r, +1.0, cf, X, D, shift<2>(c, -1, D), c);
+    r = face_into<S, 2>(r, -1.0, cf, X, D, c, shift<2>(c, +1, D));
+    return r;
+}
+
 // Exact diagonal A_cc of the operator above.  Besides -sum of the six G_dd, a
 // cross term reaches x_c itself when a tangential neighbour is mirrored onto c
 // at a wall: +G_dq/4 at an upper face and -G_dq/4 at a lower face when c is
@@ -154,6 +241,65 @@ __device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
     }
     return dg;
 }
+
+// ---------------------------------------------------------------- 7-point fast path
+// The 7-point operator at cell c = (j, i, k) from one base index: neighbours
+// at c -/+ 1 (longitude, wrapped), c -/+ nph (colatitude), c -/+ nth*nph
+// (radius).  Lower wall faces store G = 0 and upper wall faces are not read;
+// a neighbour across a wall is replaced by x_c, which meets a zero
+// coefficient.  Same operator as apply_cell with S = 7 (Eq. PC_term1 in each
+// direction); each coefficient is loaded once for A x and the diagonal.
+template <typename T>
+struct Cell7 {
+    int c;
+    T xc, xjm, xjp, xim, xip, xkm, xkp;   // x at c and its six neighbours
+    T el, eu, zl, zu, xl, xu;            // G of the six faces
+    template <typename CF, typename XL>
+    __device__ __forceinline__ void load(const CF& cf, const Dims& D, int j, int i, int k, const XL& X) {
+        const int plane = D.nth * D.nph;
+        c = (j * D.nth + i) * D.nph + k;
+        const int km = k == 0 ? c + D.nph - 1 : c - 1;
+        const int kp = k == D.nph - 1 ? c - D.nph + 1 : c + 1;
+        const bool jl = j > 0, ju = j + 1 < D.nr, il = i > 0, iu = i + 1 < D.nth;
+        xc = X(c);
+        el = (T)cf(4, c);
+        eu = ju ? (T)cf(4, c + plane) : (T)0;
+        zl = (T)cf(0, c);
+        zu = iu ? (T)cf(0, c + D.nph) : (T)0;
+        xl = (T)cf(8, c);
+        xu = (T)cf(8, kp);
+        xjm = jl ? X(c - plane) : xc;
+        xjp = ju ? X(c + plane) : xc;
+        xim = il ? X(c - D.nph) : xc;
+        xip = iu ? X(c + D.nph) : xc;
+        xkm = X(km);
+        xkp = X(kp);
+    }
+    __device__ __forceinline__ T ax() const {
+        return eu * (xjp - xc) - el * (xc - xjm) + zu * (xip - xc) - zl * (xc - xim) + xu * (xkp - xc) -
+               xl * (xc - xkm);
+    }
+    __device__ __forceinline__ T diag() const { return -(el + eu + zl + zu + xl + xu); }
+    // Gauss-Seidel / Jacobi step x_c + (b - A x)_c / A_cc
+    __device__ __forceinline__ T gs(T b) const { return xc + (b - ax()) / diag(); }
+    // b - A x with every face term fused into one multiply-add
+    __device__ __forceinline__ T resid(T b) const {
+        T r = b;
+        r = fma(el, xc - xjm, r);
+        r = fma(eu, xc - xjp, r);
+        r = fma(zl, xc - xim, r);
+        r = fma(zu, xc - xip, r);
+        r = fma(xl, xc - xkm, r);
+        r = fma(xu, xc - xkp, r);
+        return r;
+    }
+};
+
+template <typename T>
+struct XLin {   // x by linear index
+    const T* x;
+    __device__ __forceinline__ T operator()(int c) const { return x[c]; }
+};
 
 // ---------------------------------------------------------------- reductions
 // Fixed-shape block sum (blockDim.x = 256); deterministic for a given launch.

@@ -35,12 +35,28 @@ cudaError_t launch_cast32(const double* src, float* dst, i64 n, cudaStream_t s);
 cudaError_t launch_cast16(const double* src, __half* dst, i64 n, float inv_scale, cudaStream_t s);
 cudaError_t launch_dense_operator(const LevelView& lv, double* A, cudaStream_t s);
 
-// ---- reductions (solve.cu); partials has room for kRedBlocks doubles
+// Device scalar slots of a solve (mg_handle::scal).
+enum {
+    SC_SUMJF = 0,   // sum J f
+    SC_BB = 1,      // ||b||^2
+    SC_RR = 2,      // ||r||^2 of the latest outer residual
+    SC_SUMJX = 3,   // sum J x (gauge)
+    SC_SCUR = 8,    // power-of-two scale for the next FP32 residual
+    SC_SUSED = 9,   // scale the latest FP32 residual was written with
+    SC_COUNT = 16
+};
+enum { FIN_SUM = 0, FIN_MAX = 1, FIN_SCALE = 2 };
+
+// ---- reductions (outer.cu); partials has room for kRedBlocks doubles
 constexpr int kRedBlocks = 1216;   // 8 x 152 SMs; fixed so results are reproducible
 int red_blocks(i64 n);
 cudaError_t launch_sum(const double* a, const double* w, i64 n, double* partials, cudaStream_t s);
 cudaError_t launch_absmax(const double* a, i64 n, double* partials, cudaStream_t s);
-cudaError_t launch_finalize(const double* partials, int nparts, int op, double* out, cudaStream_t s);
+// op FIN_SUM / FIN_MAX: out[0] = sum / max of the partials.  FIN_SCALE: out[0]
+// = sum, and scal[SC_SCUR] = 2^-round(log2(sqrt(sum / n))) (the scale that
+// brings the next FP32 residual to unit RMS).
+cudaError_t launch_finalize(const double* partials, int nparts, int op, double* out, cudaStream_t s,
+                            double* scal = nullptr, i64 n = 1);
 
 // ---- level operations (stencil.cu); x/b/y are double* for PREC64, float* otherwise
 cudaError_t launch_apply(const LevelView& lv, int prec, const void* x, void* y, cudaStream_t s);
@@ -55,13 +71,82 @@ cudaError_t launch_prolong_add(const LevelView& lv, Dims Dc, int prec, const voi
 cudaError_t launch_coarse_solve(const double* binv, int n, int prec, const void* r, void* e,
                                 cudaStream_t s);
 
-// ---- outer FP64 pieces (solve.cu)
-// r = b - A64 x; writes r32 = float(r * scale) when r32 != nullptr and
-// partials of ||r||^2 (red_blocks(n) doubles).
+// ---- coarse tail (stencil.cu): the V-cycle from a level down to the coarsest
+// and back in one launch; one thread-block cluster of csize CTAs per task.
+constexpr int kMaxTail = 16;
+constexpr int kTailThreads = 512;
+struct TailLevel {
+    LevelView v;       // dims, factors to the next level, coefficients
+    void* e;           // iterate / correction of the level
+    void* r;           // right side of the level
+};
+struct TailTask {
+    TailLevel lev[kMaxTail];
+    int nlev;          // levels in the tail (the last one is the coarsest)
+    int nu1, nu2;
+    const double* binv;
+    int ncoarse;
+    const int* active; // per-shell flags of a batch (null: always run)
+    int shell;
+};
+cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s);
+// Clusters of csize tail CTAs that can be co-resident (0: cluster launch unavailable).
+int tail_max_clusters(int csize, int stencil, int prec);
+
+// ---- batched level operations (batch.cu)
+enum {
+    BOP_GS = 0,       // colour pass: x, b
+    BOP_JACOBI,       // x -> y with b
+    BOP_RESTRICT,     // x, b -> y = rc, z = ec zeroed
+    BOP_PROLONG,      // x += P b   (b = coarse e)
+    BOP_RESID,        // FP64: x, b -> y = r32 (or null), z = partials, scal
+    BOP_UPDATE,       // x (double) += b (float) / scal[SC_SUSED]; n cells
+    BOP_ZERO,         // n 32-bit words of x
+    BOP_COPY,         // n 32-bit words b -> x
+    BOP_SUM,          // partials z of sum b * y (y may be null); n cells
+    BOP_RHS,          // x = y (J) * (b (f) - scal[SC_SUMJF] / aux), partials z of ||x||^2
+    BOP_SHIFT,        // x -= scal[SC_SUMJX] / aux
+    BOP_FINALIZE,     // scal[slot] = sum of n partials z; y (if set) gets a copy
+    BOP_COARSE,       // x = binv b, n rows
+    BOP_RB7           // one red-black sweep of the 7-point operator, x -> y (tiles)
+};
+// Tiles of the one-pass red-black sweep (colatitude x radius x longitude).
+constexpr int kRbJ = 8, kRbI = 8, kRbK = 64;
+inline int rb7_tiles(const Dims& D) {
+    return ((D.nr + kRbJ - 1) / kRbJ) * ((D.nth + kRbI - 1) / kRbI) * ((D.nph + kRbK - 1) / kRbK);
+}
+inline bool rb7_fits(const Dims& D) { return D.nph >= kRbK; }
+struct BTask {
+    LevelView v;       // level of the task (dims, factors, coefficients, stencil)
+    Dims Dc;           // next-coarser level (restriction / prolongation)
+    void* x;
+    const void* b;
+    void* y;
+    void* z;
+    double* scal;      // the shell's device scalars
+    const double* binv;
+    i64 n;             // element / row / partial count of vector operations
+    i64 ncells;        // fine cells (scale of the next FP32 residual)
+    double aux;        // sum J
+    int slot;          // FINALIZE destination
+    int fin_scale;     // FINALIZE also sets scal[SC_SCUR]
+    int block0;        // first virtual block of the task in its launch
+    int nblocks;       // virtual blocks (work mapping of a stand-alone launch)
+    int shell;         // index of the active flag
+};
+static_assert(sizeof(BTask) % 4 == 0, "BTask is staged in shared memory word by word");
+// All tasks of one launch share `stencil` (7 or 19) for the stencil ops.
+cudaError_t launch_batch(const BTask* tasks, int ntasks, int total_blocks, const int* active, int op, int colour,
+                         int stencil, int prec, cudaStream_t s);
+
+// ---- outer FP64 pieces (outer.cu)
+// r = b - A64 x; partials of ||r||^2 (red_blocks(n) doubles).  When r32 is
+// given, writes r32 = float(r * scal[SC_SCUR]) and records the scale used in
+// scal[SC_SUSED].
 cudaError_t launch_outer_residual(const LevelView& lv, const double* x, const double* b, float* r32,
-                                  double scale, double* partials, cudaStream_t s);
-// x += e * inv_scale
-cudaError_t launch_update(double* x, const float* e, double inv_scale, i64 n, cudaStream_t s);
+                                  double* scal, double* partials, cudaStream_t s);
+// x += e / scal[SC_SUSED]
+cudaError_t launch_update(double* x, const float* e, const double* scal, i64 n, cudaStream_t s);
 // b = J (f - num[0] / den), partials of ||b||^2
 cudaError_t launch_rhs(const double* J, const double* f, const double* num, double den, double* b,
                        i64 n, double* partials, cudaStream_t s);

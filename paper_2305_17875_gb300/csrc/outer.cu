@@ -13,21 +13,14 @@ constexpr int kT = 256;
 #define GRID_STRIDE(var, n) \
     for (i64 var = blockIdx.x * (i64)blockDim.x + threadIdx.x; var < (n); var += (i64)gridDim.x * blockDim.x)
 
-__device__ __forceinline__ C3 decode(const Dims& D, i64 c) {
-    C3 r;
-    r.k = (int)(c % D.nph);
-    const i64 ji = c / D.nph;
-    r.i = (int)(ji % D.nth);
-    r.j = (int)(ji / D.nth);
-    return r;
-}
-
 template <int S>
 __global__ void __launch_bounds__(kT) k_outer_residual(CoefF64 cf, Dims D, const double* __restrict__ x,
                                                         const double* __restrict__ b, float* __restrict__ r32,
-                                                        double scale, double* __restrict__ partials) {
+                                                        double* scal, double* __restrict__ partials) {
     __shared__ double sh[8];
     XRead<double> X{x, D};
+    const double scale = r32 ? scal[SC_SCUR] : 1.0;
+    if (r32 && blockIdx.x == 0 && threadIdx.x == 0) scal[SC_SUSED] = scale;
     double acc = 0.0;
     GRID_STRIDE(c, D.n()) {
         const double r = b[c] - apply_cell<S, double>(cf, X, D, decode(D, c));
@@ -61,12 +54,21 @@ __global__ void __launch_bounds__(kT) k_absmax(const double* __restrict__ a, i64
     }
 }
 
-// op 0: sum, op 1: max.  One block; fixed order.
-__global__ void k_finalize(const double* __restrict__ partials, int np, int op, double* __restrict__ out) {
+// 2^-round(log2(rms)) for rms = sqrt(sum / n): exact power of two.
+__device__ double unit_scale(double sum, i64 n) {
+    const double rms = sqrt(sum / (double)n);
+    if (!(rms > 0.0) || !isfinite(rms)) return 1.0;
+    return ldexp(1.0, -(int)lround(log2(rms)));
+}
+
+// FIN_SUM / FIN_SCALE: sum, FIN_MAX: max.  One block; fixed order.
+__global__ void k_finalize(const double* __restrict__ partials, int np, int op, double* __restrict__ out,
+                           double* __restrict__ scal, i64 n) {
     __shared__ double sh[8];
     double v = 0.0;
-    for (int p = threadIdx.x; p < np; p += blockDim.x) v = op ? fmax(v, partials[p]) : v + partials[p];
-    if (op) {
+    const bool mx = op == FIN_MAX;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) v = mx ? fmax(v, partials[p]) : v + partials[p];
+    if (mx) {
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
         if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
         __syncthreads();
@@ -77,12 +79,17 @@ __global__ void k_finalize(const double* __restrict__ partials, int np, int op, 
         }
     } else {
         const double s = block_sum_256(v, sh);
-        if (threadIdx.x == 0) out[0] = s;
+        if (threadIdx.x == 0) {
+            out[0] = s;
+            if (op == FIN_SCALE) scal[SC_SCUR] = unit_scale(s, n);
+        }
     }
 }
 
-__global__ void __launch_bounds__(kT) k_update(double* __restrict__ x, const float* __restrict__ e, double inv_scale, i64 n) {
-    GRID_STRIDE(c, n) x[c] = fma((double)e[c], inv_scale, x[c]);
+__global__ void __launch_bounds__(kT) k_update(double* __restrict__ x, const float* __restrict__ e,
+                                                const double* __restrict__ scal, i64 n) {
+    const double inv = 1.0 / scal[SC_SUSED];   // exact: a power of two
+    GRID_STRIDE(c, n) x[c] = fma((double)e[c], inv, x[c]);
 }
 
 __global__ void __launch_bounds__(kT) k_rhs(const double* __restrict__ J, const double* __restrict__ f,
@@ -114,12 +121,12 @@ int red_blocks(i64 n) {
 }
 
 cudaError_t launch_outer_residual(const LevelView& lv, const double* x, const double* b, float* r32,
-                                  double scale, double* partials, cudaStream_t s) {
+                                  double* scal, double* partials, cudaStream_t s) {
     const int nb = red_blocks(lv.D.n());
     if (lv.stencil == 19)
-        k_outer_residual<19><<<nb, kT, 0, s>>>(lv.c64, lv.D, x, b, r32, scale, partials);
+        k_outer_residual<19><<<nb, kT, 0, s>>>(lv.c64, lv.D, x, b, r32, scal, partials);
     else
-        k_outer_residual<7><<<nb, kT, 0, s>>>(lv.c64, lv.D, x, b, r32, scale, partials);
+        k_outer_residual<7><<<nb, kT, 0, s>>>(lv.c64, lv.D, x, b, r32, scal, partials);
     return cudaGetLastError();
 }
 
@@ -133,15 +140,16 @@ cudaError_t launch_absmax(const double* a, i64 n, double* partials, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double* partials, int nparts, int op, double* out, cudaStream_t s) {
-    k_finalize<<<1, kT, 0, s>>>(partials, nparts, op, out);
+cudaError_t launch_finalize(const double* partials, int nparts, int op, double* out, cudaStream_t s,
+                            double* scal, i64 n) {
+    k_finalize<<<1, kT, 0, s>>>(partials, nparts, op, out, scal, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(double* x, const float* e, double inv_scale, i64 n, cudaStream_t s) {
+cudaError_t launch_update(double* x, const float* e, const double* scal, i64 n, cudaStream_t s) {
     i64 nb = (n + kT - 1) / kT;
     if (nb > 152 * 16) nb = 152 * 16;
-    k_update<<<(int)nb, kT, 0, s>>>(x, e, inv_scale, n);
+    k_update<<<(int)nb, kT, 0, s>>>(x, e, scal, n);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,732 @@
+// solver.cu - the solve driver: FP64 iterative refinement (or plain FP64
+// multigrid) over a batch of shells, one launch per level operation for all
+// shells, the outer iteration captured as one CUDA graph.  A single solve is
+// the batch of one.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace mgs {
+
+namespace {
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+            return MG_ECUDA;                                                               \
+        }                                                                                  \
+    } while (0)
+#define CKS(call)                   \
+    do {                            \
+        mg_status s_ = (call);      \
+        if (s_ != MG_OK) return s_; \
+    } while (0)
+
+// Virtual grid of a task: one thread per work item up to 16 blocks per SM,
+// grid-stride beyond.
+int vblocks(i64 work) {
+    i64 b = (work + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// one launch of a level operation over some tasks
+struct Launch {
+    int op = 0, colour = 0;
+    int stencil = 0;               // stencil shared by the tasks of stencil operations
+    int t0 = 0, nt = 0, total = 0;
+    int prof = -1, prof_n = 0;     // profiling slot around this launch
+    int tail_stencil = 0;          // >0: a coarse-tail launch of this stencil
+};
+
+struct Program {
+    std::vector<BTask> tasks;
+    std::vector<Launch> launches;
+    std::vector<TailTask> tails;   // tail tasks (7-point first, then 19-point)
+
+    Launch& begin(int op, int colour = 0, int stencil = 0) {
+        Launch L;
+        L.op = op;
+        L.colour = colour;
+        L.stencil = stencil;
+        L.t0 = (int)tasks.size();
+        launches.push_back(L);
+        return launches.back();
+    }
+    void add(BTask t, int nblocks) {
+        Launch& L = launches.back();
+        t.block0 = L.total;
+        t.nblocks = nblocks;
+        L.total += nblocks;
+        L.nt += 1;
+        tasks.push_back(t);
+    }
+    void drop_empty() {
+        launches.erase(std::remove_if(launches.begin(), launches.end(),
+                                      [](const Launch& L) { return L.nt == 0 && L.tail_stencil == 0; }),
+                       launches.end());
+    }
+};
+
+size_t vbytes(int prec) { return prec == PREC64 ? 8 : 4; }
+
+}  // namespace
+
+struct Plan {
+    std::vector<mg_handle*> hs;
+    int prec = 1;
+    cudaStream_t stream = nullptr;
+    Program iter;                 // one outer iteration (graph)
+    BTask* d_iter = nullptr;
+    TailTask* d_tails = nullptr;
+    int* d_active = nullptr;      // per-shell flags
+    int* h_active = nullptr;      // pinned
+    double* d_fin = nullptr;      // per shell: [sum J f, ||b||^2, ||r||^2, sum J x]
+    double* h_fin = nullptr;      // pinned
+    BTask* d_call = nullptr;      // prologue / epilogue tasks of the current call
+    size_t call_cap = 0;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_prof = false;
+    long long graph_launches = 0;
+};
+
+namespace {
+
+mg_handle* lead(Plan* p) { return p->hs[0]; }
+
+BTask task_of(const mg_handle* h, int level) {
+    BTask t{};
+    t.v = h->L[level].view(h->stencil);
+    if (level + 1 < (int)h->L.size()) t.Dc = h->L[level + 1].D;
+    t.scal = h->scal;
+    return t;
+}
+
+// Level-ell iterate / right side of shell s inside the cycle.
+void level_bufs(const mg_handle* h, int prec, int level, void** x, const void** b) {
+    if (level == 0) {
+        *x = prec == PREC64 ? (void*)h->x64 : h->L[0].e;
+        *b = prec == PREC64 ? (const void*)h->b64 : (const void*)h->L[0].r;
+    } else {
+        *x = h->L[level].e;
+        *b = h->L[level].r;
+    }
+}
+
+int top_of(const mg_handle* h) { return h->tail_level > 0 ? h->tail_level : (int)h->L.size() - 1; }
+
+// One-pass red-black sweeps apply to 7-point Gauss-Seidel levels wide enough
+// for the longitude tiles.
+bool fused_level(const mg_handle* h, int level) {
+    return h->fused_rb && h->stencil == 7 && h->opts.smoother == MG_SMOOTH_GS && rb7_fits(h->L[level].D);
+}
+
+void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
+    const int prec = pl->prec;
+    int maxc = 0;
+    bool any_jacobi = false, any_fused = false;
+    for (mg_handle* h : pl->hs) {
+        if (level >= top_of(h)) continue;
+        if (h->opts.smoother == MG_SMOOTH_JACOBI) any_jacobi = true;
+        else if (fused_level(h, level)) any_fused = true;
+        else maxc = std::max(maxc, h->stencil == 7 ? 2 : 4);
+    }
+    for (int sw = 0; sw < sweeps; ++sw) {
+        if (any_fused) {   // ping-pong between the level iterate and its scratch
+            Launch& L = P.begin(BOP_RB7, 0, 7);
+            if (level == 0) {
+                L.prof = MG_PROF_SMOOTH0;
+                L.prof_n = 1;
+            }
+            for (size_t s = 0; s < pl->hs.size(); ++s) {
+                mg_handle* h = pl->hs[s];
+                if (level >= top_of(h) || !fused_level(h, level)) continue;
+                BTask t = task_of(h, level);
+                void* xb;
+                const void* bb;
+                level_bufs(h, prec, level, &xb, &bb);
+                t.x = (sw & 1) ? h->L[level].t : xb;
+                t.y = (sw & 1) ? xb : h->L[level].t;
+                t.b = bb;
+                t.shell = (int)s;
+                P.add(t, rb7_tiles(h->L[level].D));
+            }
+        }
+        for (int c = 0; c < maxc; ++c)
+            for (int st : {7, 19}) {
+            Launch& L = P.begin(BOP_GS, c, st);
+            if (level == 0) {
+                L.prof = MG_PROF_SMOOTH0;
+                L.prof_n = 1;
+            }
+            for (size_t s = 0; s < pl->hs.size(); ++s) {
+                mg_handle* h = pl->hs[s];
+                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_GS || h->stencil != st) continue;
+                if (fused_level(h, level) || c >= (h->stencil == 7 ? 2 : 4)) continue;
+                BTask t = task_of(h, level);
+                level_bufs(h, prec, level, &t.x, &t.b);
+                t.shell = (int)s;
+                const Dims& D = h->L[level].D;
+                P.add(t, vblocks((i64)D.nr * D.nth * (D.nph / 2)));
+            }
+        }
+        if (any_jacobi) {
+            for (int st : {7, 19}) {
+            Launch& L = P.begin(BOP_JACOBI, 0, st);
+            if (level == 0) {
+                L.prof = MG_PROF_SMOOTH0;
+                L.prof_n = 1;
+            }
+            for (size_t s = 0; s < pl->hs.size(); ++s) {
+                mg_handle* h = pl->hs[s];
+                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_JACOBI || h->stencil != st) continue;
+                BTask t = task_of(h, level);
+                level_bufs(h, prec, level, &t.x, &t.b);
+                t.y = h->L[level].t;
+                t.shell = (int)s;
+                P.add(t, vblocks(h->L[level].D.n()));
+            }
+            }
+            P.begin(BOP_COPY);
+            for (size_t s = 0; s < pl->hs.size(); ++s) {
+                mg_handle* h = pl->hs[s];
+                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_JACOBI) continue;
+                BTask t{};
+                void* x;
+                const void* b;
+                level_bufs(h, prec, level, &x, &b);
+                t.x = x;
+                t.b = h->L[level].t;
+                t.n = h->L[level].D.n() * (i64)(vbytes(prec) / 4);
+                t.shell = (int)s;
+                P.add(t, vblocks(t.n));
+            }
+        }
+    }
+    if (any_fused && (sweeps & 1)) {   // an odd count ends in the scratch: copy back
+        P.begin(BOP_COPY);
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            if (level >= top_of(h) || !fused_level(h, level)) continue;
+            BTask t{};
+            void* xb;
+            const void* bb;
+            level_bufs(h, prec, level, &xb, &bb);
+            t.x = xb;
+            t.b = h->L[level].t;
+            t.n = h->L[level].D.n() * (i64)(vbytes(prec) / 4);
+            t.shell = (int)s;
+            P.add(t, vblocks(t.n));
+        }
+    }
+}
+
+// Outer FP64 residual and its norm for every shell.
+void add_residual(Program& P, Plan* pl) {
+    for (int st : {7, 19}) {
+    Launch& L = P.begin(BOP_RESID, 0, st);
+    L.prof = MG_PROF_RESIDUAL;
+    L.prof_n = 1;
+    for (size_t s = 0; s < pl->hs.size(); ++s) {
+        mg_handle* h = pl->hs[s];
+        if (h->stencil != st) continue;
+        BTask t = task_of(h, 0);
+        t.x = h->x64;
+        t.b = h->b64;
+        t.y = pl->prec == PREC64 ? nullptr : h->L[0].r;
+        t.z = h->part;
+        t.shell = (int)s;
+        P.add(t, red_blocks(h->L[0].D.n()));
+    }
+    }
+    P.begin(BOP_FINALIZE);
+    for (size_t s = 0; s < pl->hs.size(); ++s) {
+        mg_handle* h = pl->hs[s];
+        BTask t{};
+        t.scal = h->scal;
+        t.z = h->part;
+        t.n = red_blocks(h->L[0].D.n());
+        t.slot = SC_RR;
+        t.fin_scale = 1;
+        t.ncells = h->L[0].D.n();
+        t.y = pl->d_fin + 4 * s + 2;
+        t.shell = (int)s;
+        P.add(t, 1);
+    }
+}
+
+void build_iteration(Plan* pl) {
+    Program& P = pl->iter;
+    const int prec = pl->prec;
+    int depth = 0;
+    for (mg_handle* h : pl->hs) depth = std::max(depth, top_of(h));
+    if (prec != PREC64) {
+        P.begin(BOP_ZERO);
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            BTask t{};
+            t.x = h->L[0].e;
+            t.n = h->L[0].D.n();
+            t.shell = (int)s;
+            P.add(t, vblocks(t.n));
+        }
+    }
+    // down leg
+    for (int l = 0; l < depth; ++l) {
+        add_smooth(P, pl, l, pl->hs[0]->opts.nu1);
+        for (int st : {7, 19}) {
+        Launch& L = P.begin(BOP_RESTRICT, 0, st);
+        if (l == 0) {
+            L.prof = MG_PROF_RESTRICT0;
+            L.prof_n = 1;
+        }
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            if (l >= top_of(h) || h->stencil != st) continue;
+            BTask t = task_of(h, l);
+            level_bufs(h, prec, l, &t.x, &t.b);
+            t.y = h->L[l + 1].r;
+            t.z = h->L[l + 1].e;
+            t.shell = (int)s;
+            P.add(t, vblocks(h->L[l + 1].D.n()));
+        }
+        }
+    }
+    // bottom: coarse tails (one launch per stencil) and dense coarse solves
+    for (int st : {7, 19}) {
+        bool any = false;
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            if (h->tail_level <= 0 || h->stencil != st) continue;
+            TailTask tt = h->tail_host;
+            tt.active = pl->d_active;
+            tt.shell = (int)s;
+            P.tails.push_back(tt);
+            any = true;
+        }
+        if (any) {
+            Launch& L = P.begin(-1);
+            L.tail_stencil = st;
+            L.prof = MG_PROF_TAIL;
+            L.prof_n = 1;
+        }
+    }
+    P.begin(BOP_COARSE);
+    for (size_t s = 0; s < pl->hs.size(); ++s) {
+        mg_handle* h = pl->hs[s];
+        if (h->tail_level > 0) continue;
+        BTask t{};
+        const int nl = (int)h->L.size();
+        t.binv = h->binv;
+        t.n = h->ncoarse;
+        void* x;
+        const void* b;
+        level_bufs(h, prec, nl - 1, &x, &b);
+        t.x = x;
+        t.b = b;
+        t.shell = (int)s;
+        P.add(t, std::min((h->ncoarse + 7) / 8, 152 * 4));
+    }
+    // up leg
+    for (int l = depth - 1; l >= 0; --l) {
+        Launch& L = P.begin(BOP_PROLONG);
+        if (l == 0) {
+            L.prof = MG_PROF_PROLONG0;
+            L.prof_n = 1;
+        }
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            if (l >= top_of(h)) continue;
+            BTask t = task_of(h, l);
+            level_bufs(h, prec, l, &t.x, &t.b);
+            t.b = h->L[l + 1].e;
+            t.shell = (int)s;
+            P.add(t, vblocks(h->L[l].D.n()));
+        }
+        add_smooth(P, pl, l, pl->hs[0]->opts.nu2);
+    }
+    if (prec != PREC64) {
+        Launch& L = P.begin(BOP_UPDATE);
+        L.prof = MG_PROF_UPDATE;
+        L.prof_n = 1;
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            BTask t{};
+            t.x = h->x64;
+            t.b = h->L[0].e;
+            t.scal = h->scal;
+            t.n = h->L[0].D.n();
+            t.shell = (int)s;
+            P.add(t, vblocks(t.n));
+        }
+    }
+    add_residual(P, pl);
+    P.drop_empty();
+}
+
+mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const int* active) {
+    mg_handle* h0 = lead(pl);
+    for (const Launch& L : P.launches) {
+        if (L.prof >= 0) prof_begin(h0, L.prof);
+        if (L.tail_stencil) {
+            int first = 0, n = 0;
+            for (size_t i = 0; i < P.tails.size(); ++i) {
+                const int st = P.tails[i].lev[0].v.stencil;
+                if (st != L.tail_stencil) continue;
+                if (n == 0) first = (int)i;
+                ++n;
+            }
+            CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream));
+        } else {
+            CK(launch_batch(d_tasks + L.t0, L.nt, L.total, active, L.op, L.colour, L.stencil, pl->prec,
+                            pl->stream));
+        }
+        if (L.prof >= 0) prof_end(h0, L.prof, L.prof_n);
+        h0->launches += 1;
+    }
+    return MG_OK;
+}
+
+mg_status upload_call(Plan* pl, const Program& P) {
+    const size_t need = P.tasks.size() * sizeof(BTask);
+    if (need > pl->call_cap) {
+        if (pl->d_call) cudaFree(pl->d_call);
+        pl->d_call = nullptr;
+        const size_t cap = std::max(need, (size_t)64 * sizeof(BTask));
+        CK(cudaMalloc(&pl->d_call, cap));
+        pl->call_cap = cap;
+    }
+    if (need) CK(cudaMemcpyAsync(pl->d_call, P.tasks.data(), need, cudaMemcpyHostToDevice, pl->stream));
+    return MG_OK;
+}
+
+mg_status build_graph(Plan* pl) {
+    mg_handle* h0 = lead(pl);
+    if (pl->gexec) {
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
+    }
+    for (auto& p : h0->graph_events) {
+        h0->prof_pool.push_back(p.a);
+        h0->prof_pool.push_back(p.b);
+    }
+    h0->graph_events.clear();
+    const long long before = h0->launches;
+    CK(cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal));
+    h0->capturing = true;
+    const mg_status st = run_program(pl, pl->iter, pl->d_iter, pl->d_active);
+    h0->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(pl->stream, &g);
+    if (st != MG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    CK(e);
+    pl->graph_launches = h0->launches - before;
+    h0->launches = before;
+    const cudaError_t ei = cudaGraphInstantiate(&pl->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    pl->graph_prof = h0->prof_on;
+    return MG_OK;
+}
+
+mg_status read_fin(Plan* pl) {
+    CK(cudaMemcpyAsync(pl->h_fin, pl->d_fin, sizeof(double) * 4 * pl->hs.size(), cudaMemcpyDeviceToHost,
+                       pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    prof_collect(lead(pl));
+    return MG_OK;
+}
+
+}  // namespace
+
+void plan_destroy(Plan* pl) {
+    if (!pl) return;
+    if (pl->stream) cudaStreamSynchronize(pl->stream);
+    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+    if (pl->d_iter) cudaFree(pl->d_iter);
+    if (pl->d_tails) cudaFree(pl->d_tails);
+    if (pl->d_active) cudaFree(pl->d_active);
+    if (pl->d_fin) cudaFree(pl->d_fin);
+    if (pl->d_call) cudaFree(pl->d_call);
+    if (pl->h_active) cudaFreeHost(pl->h_active);
+    if (pl->h_fin) cudaFreeHost(pl->h_fin);
+    delete pl;
+}
+
+mg_status plan_create(mg_handle* const* hs, int n, Plan** out) {
+    *out = nullptr;
+    if (n <= 0) return MG_EINVAL;
+    Plan* pl = new Plan();
+    pl->hs.assign(hs, hs + n);
+    pl->prec = hs[0]->prec;
+    pl->stream = hs[0]->stream;
+    for (int s = 0; s < n; ++s)
+        if (!hs[s] || hs[s]->prec != pl->prec || hs[s]->device != hs[0]->device) {
+            plan_destroy(pl);
+            set_error("batch handles must share device and precision");
+            return MG_EINVAL;
+        }
+    auto fail = [&](cudaError_t e) {
+        set_error(std::string("batch plan: ") + cudaGetErrorString(e));
+        plan_destroy(pl);
+        return MG_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&pl->d_active, sizeof(int) * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&pl->d_fin, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&pl->h_active, sizeof(int) * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&pl->h_fin, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
+    build_iteration(pl);
+    const size_t tb = pl->iter.tasks.size() * sizeof(BTask);
+    if ((e = cudaMalloc(&pl->d_iter, tb ? tb : 16)) != cudaSuccess) return fail(e);
+    if (tb && (e = cudaMemcpyAsync(pl->d_iter, pl->iter.tasks.data(), tb, cudaMemcpyHostToDevice, pl->stream)) !=
+                  cudaSuccess)
+        return fail(e);
+    // tail tasks grouped by stencil in launch order
+    std::stable_sort(pl->iter.tails.begin(), pl->iter.tails.end(),
+                     [](const TailTask& a, const TailTask& b) { return a.lev[0].v.stencil < b.lev[0].v.stencil; });
+    const size_t ttb = pl->iter.tails.size() * sizeof(TailTask);
+    if (ttb) {
+        if ((e = cudaMalloc(&pl->d_tails, ttb)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(pl->d_tails, pl->iter.tails.data(), ttb, cudaMemcpyHostToDevice, pl->stream)) !=
+            cudaSuccess)
+            return fail(e);
+    }
+    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return fail(e);
+    *out = pl;
+    return MG_OK;
+}
+
+// Solve every shell of the plan; the stop logic per shell is the one of a
+// lone solve, so a shell's iterates do not depend on its batch companions.
+mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps) {
+    const int n = (int)pl->hs.size();
+    mg_handle* h0 = lead(pl);
+    cudaStream_t s = pl->stream;
+    h0->launches = 0;
+    CK(cudaEventRecord(h0->ev0, s));
+    for (int i = 0; i < n; ++i) pl->h_active[i] = 1;
+    CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+
+    // prologue: x in, b = J (f - mean_J f), first residual
+    Program pro;
+    pro.begin(BOP_COPY);
+    for (int i = 0; i < n; ++i) {
+        BTask t{};
+        t.x = pl->hs[i]->x64;
+        t.b = x[i];
+        t.n = 2 * pl->hs[i]->L[0].D.n();
+        t.shell = i;
+        pro.add(t, vblocks(t.n));
+    }
+    pro.begin(BOP_SUM);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.b = h->J64;
+        t.y = (void*)f[i];
+        t.z = h->part;
+        t.n = h->L[0].D.n();
+        t.shell = i;
+        pro.add(t, red_blocks(t.n));
+    }
+    pro.begin(BOP_FINALIZE);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.scal = h->scal;
+        t.z = h->part;
+        t.n = red_blocks(h->L[0].D.n());
+        t.slot = SC_SUMJF;
+        t.y = pl->d_fin + 4 * i + 0;
+        t.shell = i;
+        pro.add(t, 1);
+    }
+    pro.begin(BOP_RHS);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.x = h->b64;
+        t.b = f[i];
+        t.y = h->J64;
+        t.z = h->part;
+        t.scal = h->scal;
+        t.aux = h->sumJ;
+        t.n = h->L[0].D.n();
+        t.shell = i;
+        pro.add(t, red_blocks(t.n));
+    }
+    pro.begin(BOP_FINALIZE);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.scal = h->scal;
+        t.z = h->part;
+        t.n = red_blocks(h->L[0].D.n());
+        t.slot = SC_BB;
+        t.fin_scale = 1;
+        t.ncells = h->L[0].D.n();
+        t.y = pl->d_fin + 4 * i + 1;
+        t.shell = i;
+        pro.add(t, 1);
+    }
+    add_residual(pro, pl);
+    CKS(upload_call(pl, pro));
+    CKS(run_program(pl, pro, pl->d_call, nullptr));
+    CKS(read_fin(pl));
+
+    struct State {
+        double bnorm = 1.0, best = INFINITY;
+        int it = 0;
+        mg_status st = MG_OK;
+        bool done = false;
+        mg_report R;
+    };
+    std::vector<State> S(n);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        std::memset(&S[i].R, 0, sizeof(mg_report));
+        S[i].R.levels = (int)h->L.size();
+        S[i].R.stencil = h->stencil;
+        S[i].R.removed_mean = pl->h_fin[4 * i] / h->sumJ;
+        const double bn = std::sqrt(pl->h_fin[4 * i + 1]);
+        if (!std::isfinite(bn)) {
+            S[i].st = MG_ENAN;
+            S[i].done = true;
+            set_error("non-finite right-hand side");
+        }
+        S[i].bnorm = bn > 0 ? bn : 1.0;
+    }
+    const bool use_graph = h0->use_graph;
+    for (;;) {
+        int nactive = 0;
+        for (int i = 0; i < n; ++i) {
+            State& q = S[i];
+            if (q.done) {
+                pl->h_active[i] = 0;
+                continue;
+            }
+            const double rel = std::sqrt(pl->h_fin[4 * i + 2]) / q.bnorm;
+            if (q.it < MG_HIST) q.R.res_hist[q.it] = rel;
+            q.R.rel_res = rel;
+            if (!std::isfinite(rel)) {
+                q.st = MG_ENAN;
+                set_error("non-finite residual");
+                q.done = true;
+            } else if (rel <= tol[i]) {
+                q.done = true;
+            } else {
+                q.best = std::min(q.best, rel);
+                if (rel > 1e3 * q.best) {
+                    q.st = MG_EDIVERGED;
+                    set_error("residual diverged");
+                    q.done = true;
+                } else if (q.it >= pl->hs[i]->opts.max_iters) {
+                    q.st = MG_ENOCONV;
+                    set_error("max_iters reached");
+                    q.done = true;
+                }
+            }
+            pl->h_active[i] = q.done ? 0 : 1;
+            nactive += q.done ? 0 : 1;
+        }
+        if (!nactive) break;
+        CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        if (use_graph) {
+            if (!pl->gexec || pl->graph_prof != h0->prof_on) CKS(build_graph(pl));
+            CK(cudaGraphLaunch(pl->gexec, s));
+            h0->launches += pl->graph_launches;
+        } else {
+            CKS(run_program(pl, pl->iter, pl->d_iter, pl->d_active));
+        }
+        CKS(read_fin(pl));
+        if (use_graph && h0->prof_on) {
+            for (auto& p : h0->graph_events) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                    h0->prof_ms[p.slot] += ms;
+                    h0->prof_n[p.slot] += p.n;
+                }
+                cudaGetLastError();
+            }
+        }
+        for (int i = 0; i < n; ++i)
+            if (pl->h_active[i]) S[i].it += 1;
+    }
+
+    // epilogue: gauge (J-weighted mean of x removed), x out
+    Program epi;
+    epi.begin(BOP_SUM);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.b = h->J64;
+        t.y = h->x64;
+        t.z = h->part;
+        t.n = h->L[0].D.n();
+        t.shell = i;
+        epi.add(t, red_blocks(t.n));
+    }
+    epi.begin(BOP_FINALIZE);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.scal = h->scal;
+        t.z = h->part;
+        t.n = red_blocks(h->L[0].D.n());
+        t.slot = SC_SUMJX;
+        t.y = pl->d_fin + 4 * i + 3;
+        t.shell = i;
+        epi.add(t, 1);
+    }
+    epi.begin(BOP_SHIFT);
+    for (int i = 0; i < n; ++i) {
+        mg_handle* h = pl->hs[i];
+        BTask t{};
+        t.x = h->x64;
+        t.scal = h->scal;
+        t.aux = h->sumJ;
+        t.n = h->L[0].D.n();
+        t.shell = i;
+        epi.add(t, vblocks(t.n));
+    }
+    epi.begin(BOP_COPY);
+    for (int i = 0; i < n; ++i) {
+        BTask t{};
+        t.x = x[i];
+        t.b = pl->hs[i]->x64;
+        t.n = 2 * pl->hs[i]->L[0].D.n();
+        t.shell = i;
+        epi.add(t, vblocks(t.n));
+    }
+    CKS(upload_call(pl, epi));
+    CKS(run_program(pl, epi, pl->d_call, nullptr));
+    CK(cudaEventRecord(h0->ev1, s));
+    CK(cudaEventSynchronize(h0->ev1));
+    prof_collect(h0);
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h0->ev0, h0->ev1));
+    mg_status worst = MG_OK;
+    for (int i = 0; i < n; ++i) {
+        State& q = S[i];
+        q.R.iters = q.it;
+        q.R.seconds = ms * 1e-3;
+        q.R.model_bytes = model_bytes_per_iteration(pl->hs[i]) * q.it;
+        q.R.status = q.st;
+        q.R.launches = h0->launches;
+        if (reps) reps[i] = q.R;
+        if (q.st != MG_OK && worst == MG_OK) worst = q.st;
+    }
+    return worst;
+}
+
+}  // namespace mgs

@@ -2,6 +2,8 @@
 // (Section 3.3, Eqs. PC_term1-3): apply, multicolour Gauss-Seidel, weighted
 // Jacobi, fused residual + restriction, trilinear prolongation + correction,
 // and the coarsest-level dense solve.
+#include <cooperative_groups.h>
+
 #include "mg_kernels.h"
 
 namespace mgs {
@@ -17,38 +19,38 @@ int blocks_for(i64 work) {
     return (int)(b < 1 ? 1 : b);
 }
 
-__device__ __forceinline__ C3 decode(const Dims& D, i64 c) {
-    C3 r;
-    r.k = (int)(c % D.nph);
-    const i64 ji = c / D.nph;
-    r.i = (int)(ji % D.nth);
-    r.j = (int)(ji / D.nth);
-    return r;
-}
-
 #define GRID_STRIDE(var, n) \
     for (i64 var = blockIdx.x * (i64)blockDim.x + threadIdx.x; var < (n); var += (i64)gridDim.x * blockDim.x)
 
-template <int S, typename T, typename CF>
-__global__ void __launch_bounds__(kThreads) k_apply(CF cf, Dims D, const T* __restrict__ x, T* __restrict__ y) {
-    XRead<T> X{x, D};
-    GRID_STRIDE(c, D.n()) { y[c] = apply_cell<S, T>(cf, X, D, decode(D, c)); }
+// Loads of values that other CTAs of a cluster may have written earlier in the
+// same launch go through L2 (CG = true); otherwise plain loads.
+template <typename T, bool CG>
+__device__ __forceinline__ T ldv(const T* p) {
+    if (CG) return __ldcg(p);
+    return *p;
 }
+template <typename T, bool CG>
+struct XAcc {
+    const T* x;
+    Dims D;
+    __device__ __forceinline__ T operator()(C3 c) const { return ldv<T, CG>(x + cidx(D, c)); }
+};
+
+// ---- range forms: work items first, first + stride, ... (one launch or one cluster)
 
 // One colour of multicolour Gauss-Seidel, in place: x_c += (b_c - (A x)_c) / A_cc
 // for every cell of the colour.  Cells of one colour share no stencil entry, so
 // the pass equals the sequential sweep over that colour.
 // 7-point: colour (i + j + k) mod 2.  19-point: ((i + j) mod 2) + 2 ((j + k) mod 2).
-template <int S, typename T, typename CF>
-__global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* __restrict__ b, int colour) {
-    XRead<T> X{x, D};
+template <int S, typename T, typename CF, bool CG>
+__device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* x, const T* b, int colour,
+                                                i64 first, i64 stride) {
+    XAcc<T, CG> X{x, D};
     const int hk = D.nph >> 1;
     const i64 work = (i64)D.nr * D.nth * hk;
-    GRID_STRIDE(t, work) {
-        const int kk = (int)(t % hk);
-        const i64 row = t / hk;
-        const int i = (int)(row % D.nth);
-        const int j = (int)(row / D.nth);
+    for (i64 t = first; t < work; t += stride) {
+        int kk, i, j;
+        decode_half(D, t, kk, i, j);
         int k;
         if (S == 7) {
             k = 2 * kk + ((colour + i + j) & 1);
@@ -58,37 +60,24 @@ __global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* _
         }
         const C3 c{j, i, k};
         const i64 id = cidx(D, c);
-        const T r = b[id] - apply_cell<S, T>(cf, X, D, c);
-        x[id] += r / diag_cell<S, T>(cf, D, c);
-    }
-}
-
-// Weighted Jacobi, out of place: xo = x + omega (b - A x) / diag(A).
-template <int S, typename T, typename CF>
-__global__ void __launch_bounds__(kThreads) k_jacobi(CF cf, Dims D, const T* __restrict__ x, T* __restrict__ xo,
-                                                      const T* __restrict__ b, T omega) {
-    XRead<T> X{x, D};
-    GRID_STRIDE(c, D.n()) {
-        const C3 cc = decode(D, c);
-        const T r = b[c] - apply_cell<S, T>(cf, X, D, cc);
-        xo[c] = x[c] + omega * r / diag_cell<S, T>(cf, D, cc);
+        const T r = ldv<T, CG>(b + id) - apply_cell<S, T>(cf, X, D, c);
+        x[id] = ldv<T, CG>(x + id) + r / diag_cell<S, T>(cf, D, c);
     }
 }
 
 // rc(C) = sum over the children c of C of (b - A x)_c; optionally zero ec.
-template <int S, typename T, typename CF>
-__global__ void __launch_bounds__(kThreads) k_restrict(CF cf, Dims D, const T* __restrict__ x, const T* __restrict__ b,
-                                                        Dims Dc, int cz, int ce, int cx, T* __restrict__ rc,
-                                                        T* __restrict__ ec_zero) {
-    XRead<T> X{x, D};
-    GRID_STRIDE(t, Dc.n()) {
+template <int S, typename T, typename CF, bool CG>
+__device__ __forceinline__ void restrict_range(const CF& cf, const Dims& D, const T* x, const T* b, const Dims& Dc,
+                                               int cz, int ce, int cx, T* rc, T* ec_zero, i64 first, i64 stride) {
+    XAcc<T, CG> X{x, D};
+    for (i64 t = first; t < Dc.n(); t += stride) {
         const C3 C = decode(Dc, t);
         T s = 0;
         for (int dj = 0; dj < ce; ++dj)
             for (int di = 0; di < cz; ++di)
                 for (int dk = 0; dk < cx; ++dk) {
                     const C3 c{ce * C.j + dj, cz * C.i + di, cx * C.k + dk};
-                    s += b[cidx(D, c)] - apply_cell<S, T>(cf, X, D, c);
+                    s += ldv<T, CG>(b + cidx(D, c)) - apply_cell<S, T>(cf, X, D, c);
                 }
         rc[t] = s;
         if (ec_zero) ec_zero[t] = 0;
@@ -115,10 +104,11 @@ __device__ __forceinline__ void lin1d(int f, int c, int nc, bool periodic, int i
     w[1] = 0.25f;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prolong(Dims D, Dims Dc, int cz, int ce, int cx, const T* __restrict__ ec,
-                                                       T* __restrict__ x) {
-    GRID_STRIDE(c, D.n()) {
+// x += P ec (cell-centred trilinear).
+template <typename T, bool CG>
+__device__ __forceinline__ void prolong_range(const Dims& D, const Dims& Dc, int cz, int ce, int cx, const T* ec,
+                                              T* x, i64 first, i64 stride) {
+    for (i64 c = first; c < D.n(); c += stride) {
         const C3 f = decode(D, c);
         int ij[2], ii[2], ik[2];
         float wj[2], wi[2], wk[2];
@@ -130,22 +120,131 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Dims D, Dims Dc, int cz, i
             for (int bb = 0; bb < 2; ++bb)
                 for (int e = 0; e < 2; ++e) {
                     const T w = (T)wj[a] * (T)wi[bb] * (T)wk[e];
-                    if (w != (T)0) s += w * ec[cidx(Dc, ij[a], ii[bb], ik[e])];
+                    if (w != (T)0) s += w * ldv<T, CG>(ec + cidx(Dc, ij[a], ii[bb], ik[e]));
                 }
-        x[c] += s;
+        x[c] = ldv<T, CG>(x + c) + s;
     }
 }
 
 // e = Binv r (FP64 accumulate), one warp per row.
-template <typename T>
-__global__ void k_coarse(const double* __restrict__ binv, int n, const T* __restrict__ r, T* __restrict__ e) {
-    const int warps = (gridDim.x * blockDim.x) >> 5;
+template <typename T, bool CG>
+__device__ __forceinline__ void coarse_range(const double* binv, int n, const T* r, T* e, int warp_first,
+                                             int warp_stride) {
     const int lane = threadIdx.x & 31;
-    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
+    for (int row = warp_first; row < n; row += warp_stride) {
         double s = 0.0;
-        for (int m = lane; m < n; m += 32) s += binv[(i64)row * n + m] * (double)r[m];
+        for (int m = lane; m < n; m += 32) s += __ldg(binv + (i64)row * n + m) * (double)ldv<T, CG>(r + m);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) e[row] = (T)s;
+    }
+}
+
+// ---- one-launch kernels
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_apply(CF cf, Dims D, const T* __restrict__ x, T* __restrict__ y) {
+    XRead<T> X{x, D};
+    GRID_STRIDE(c, D.n()) { y[c] = apply_cell<S, T>(cf, X, D, decode(D, c)); }
+}
+
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* __restrict__ b, int colour) {
+    gs_colour_range<S, T, CF, false>(cf, D, x, b, colour, blockIdx.x * (i64)blockDim.x + threadIdx.x,
+                                     (i64)gridDim.x * blockDim.x);
+}
+
+// Weighted Jacobi, out of place: xo = x + omega (b - A x) / diag(A).
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_jacobi(CF cf, Dims D, const T* __restrict__ x, T* __restrict__ xo,
+                                                      const T* __restrict__ b, T omega) {
+    XRead<T> X{x, D};
+    GRID_STRIDE(c, D.n()) {
+        const C3 cc = decode(D, c);
+        const T r = b[c] - apply_cell<S, T>(cf, X, D, cc);
+        xo[c] = x[c] + omega * r / diag_cell<S, T>(cf, D, cc);
+    }
+}
+
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_restrict(CF cf, Dims D, const T* __restrict__ x, const T* __restrict__ b,
+                                                        Dims Dc, int cz, int ce, int cx, T* __restrict__ rc,
+                                                        T* __restrict__ ec_zero) {
+    restrict_range<S, T, CF, false>(cf, D, x, b, Dc, cz, ce, cx, rc, ec_zero,
+                                    blockIdx.x * (i64)blockDim.x + threadIdx.x, (i64)gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong(Dims D, Dims Dc, int cz, int ce, int cx, const T* __restrict__ ec,
+                                                       T* __restrict__ x) {
+    prolong_range<T, false>(D, Dc, cz, ce, cx, ec, x, blockIdx.x * (i64)blockDim.x + threadIdx.x,
+                            (i64)gridDim.x * blockDim.x);
+}
+
+template <typename T>
+__global__ void k_coarse(const double* __restrict__ binv, int n, const T* __restrict__ r, T* __restrict__ e) {
+    coarse_range<T, false>(binv, n, r, e, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                           (gridDim.x * blockDim.x) >> 5);
+}
+
+// ---- the coarse tail: every level from the tail's top to the coarsest in one
+// launch, one thread-block cluster per task, a cluster barrier between phases.
+template <int P>
+struct CoefOf;
+template <>
+struct CoefOf<PREC64> {
+    typedef CoefF64 type;
+    __device__ static const CoefF64& get(const LevelView& v) { return v.c64; }
+};
+template <>
+struct CoefOf<PREC32> {
+    typedef CoefF32 type;
+    __device__ static const CoefF32& get(const LevelView& v) { return v.c32; }
+};
+template <>
+struct CoefOf<PREC16> {
+    typedef CoefF16 type;
+    __device__ static const CoefF16& get(const LevelView& v) { return v.c16; }
+};
+
+template <int S, typename T, int P>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __restrict__ tasks, int csize) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const TailTask& tk = tasks[blockIdx.x / csize];
+    if (tk.active && !tk.active[tk.shell]) return;     // uniform over the cluster
+    const i64 first = (i64)cl.block_rank() * blockDim.x + threadIdx.x;
+    const i64 stride = (i64)csize * blockDim.x;
+    const int ncol = S == 7 ? 2 : 4;
+    const int nl = tk.nlev;
+    for (int l = 0; l < nl - 1; ++l) {
+        const TailLevel& L = tk.lev[l];
+        const TailLevel& C = tk.lev[l + 1];
+        const auto& cf = CoefOf<P>::get(L.v);
+        for (int sw = 0; sw < tk.nu1; ++sw)
+            for (int c = 0; c < ncol; ++c) {
+                gs_colour_range<S, T, typename CoefOf<P>::type, true>(cf, L.v.D, (T*)L.e, (const T*)L.r, c, first,
+                                                                      stride);
+                cl.sync();
+            }
+        restrict_range<S, T, typename CoefOf<P>::type, true>(cf, L.v.D, (const T*)L.e, (const T*)L.r, C.v.D,
+                                                             L.v.cz, L.v.ce, L.v.cx, (T*)C.r, (T*)C.e, first,
+                                                             stride);
+        cl.sync();
+    }
+    coarse_range<T, true>(tk.binv, tk.ncoarse, (const T*)tk.lev[nl - 1].r, (T*)tk.lev[nl - 1].e, (int)(first >> 5),
+                          (int)(stride >> 5));
+    cl.sync();
+    for (int l = nl - 2; l >= 0; --l) {
+        const TailLevel& L = tk.lev[l];
+        const TailLevel& C = tk.lev[l + 1];
+        const auto& cf = CoefOf<P>::get(L.v);
+        prolong_range<T, true>(L.v.D, C.v.D, L.v.cz, L.v.ce, L.v.cx, (const T*)C.e, (T*)L.e, first, stride);
+        cl.sync();
+        for (int sw = 0; sw < tk.nu2; ++sw)
+            for (int c = 0; c < ncol; ++c) {
+                gs_colour_range<S, T, typename CoefOf<P>::type, true>(cf, L.v.D, (T*)L.e, (const T*)L.r, c, first,
+                                                                      stride);
+                cl.sync();
+            }
     }
 }
 
@@ -221,6 +320,66 @@ cudaError_t launch_coarse_solve(const double* binv, int n, int prec, const void*
         k_coarse<double><<<nb, kThreads, 0, s>>>(binv, n, (const double*)r, (double*)e);
     else
         k_coarse<float><<<nb, kThreads, 0, s>>>(binv, n, (const float*)r, (float*)e);
+    return cudaGetLastError();
+}
+
+template <int S, typename T, int P>
+static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntasks * csize, 1, 1);
+    cfg.blockDim = dim3(kTailThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tail<S, T, P>, tasks, csize);
+}
+
+template <int S, typename T, int P>
+static int tail_clusters(int csize) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize, 1, 1);
+    cfg.blockDim = dim3(kTailThreads, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tail<S, T, P>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int tail_max_clusters(int csize, int stencil, int prec) {
+    if (prec == PREC64)
+        return stencil == 19 ? tail_clusters<19, double, PREC64>(csize) : tail_clusters<7, double, PREC64>(csize);
+    if (prec == PREC32)
+        return stencil == 19 ? tail_clusters<19, float, PREC32>(csize) : tail_clusters<7, float, PREC32>(csize);
+    return stencil == 19 ? tail_clusters<19, float, PREC16>(csize) : tail_clusters<7, float, PREC16>(csize);
+}
+
+cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s) {
+    cudaError_t e;
+    if (prec == PREC64)
+        e = stencil == 19 ? tail_launch<19, double, PREC64>(tasks, ntasks, csize, s)
+                          : tail_launch<7, double, PREC64>(tasks, ntasks, csize, s);
+    else if (prec == PREC32)
+        e = stencil == 19 ? tail_launch<19, float, PREC32>(tasks, ntasks, csize, s)
+                          : tail_launch<7, float, PREC32>(tasks, ntasks, csize, s);
+    else
+        e = stencil == 19 ? tail_launch<19, float, PREC16>(tasks, ntasks, csize, s)
+                          : tail_launch<7, float, PREC16>(tasks, ntasks, csize, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -169,8 +169,11 @@ def test_coarse_solve_matches_oracle(lib, name):
     np.testing.assert_allclose(to_np(e), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("tail", [False, True])
 @pytest.mark.parametrize("name", list(GRIDS))
-def test_fp64_vcycle_matches_oracle(lib, name):
+def test_fp64_vcycle_matches_oracle(lib, name, tail, monkeypatch):
+    if tail:
+        monkeypatch.setenv("MG_TAIL", "1")
     g = GRIDS[name]
     h, hier, fm = make(lib, g, 0, coarse_max=32)
     rng = np.random.default_rng(14)
@@ -194,8 +197,13 @@ SOLVES = [
 ]
 
 
+@pytest.mark.parametrize("path", ["default", "tail", "no_graph"])
 @pytest.mark.parametrize("wl,scale,prec,opts", SOLVES)
-def test_solve_matches_oracle(lib, wl, scale, prec, opts):
+def test_solve_matches_oracle(lib, wl, scale, prec, opts, path, monkeypatch):
+    if path == "tail":
+        monkeypatch.setenv("MG_TAIL", "1")
+    elif path == "no_graph":
+        monkeypatch.setenv("MG_NO_GRAPH", "1")
     torch, dev = torch_dev()
     w = W.single(wl, scale)
     g, f = w["grid"], w["f"]
@@ -256,3 +264,34 @@ def test_max_iters_reports_noconv(lib):
     fd = to_dev(w["f"], torch.float64)
     rep = lib.mg_solve(h, fd, torch.zeros_like(fd), tol=1e-10, allow=(lib.MG_ENOCONV,))
     assert rep["status"] == "MG_ENOCONV" and rep["iters"] == 2
+
+
+FUSED_GRIDS = {
+    # nph >= 64 takes the one-pass red-black kernel (8 x 8 x 64 tiles); partial
+    # tiles in every direction, and a grid whose longitude ring wraps onto itself
+    "fused_ragged": W.grid_desc(6, 20, 96),
+    "fused_stretched": W.grid_desc(12, 20, 72, stretch=2.0),
+    "fused_exact_tiles": W.grid_desc(8, 16, 64),
+    "fused_many_tiles": W.grid_desc(16, 24, 192, stretch=1.0),
+}
+
+
+@pytest.mark.parametrize("path", ["one_pass", "colour_passes"])
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("name", list(FUSED_GRIDS))
+def test_fused_red_black_sweep_matches_oracle(lib, name, prec, sweeps, path, monkeypatch):
+    if path == "one_pass":
+        monkeypatch.setenv("MG_FUSED_RB", "1")
+    g = FUSED_GRIDS[name]
+    h = lib.mg_setup(g, dict(precision=prec))
+    fm = grid.face_metrics(grid.shell(g))
+    lv = omg.make_level(grid.shell(g).shape, fm, 7)
+    rng = np.random.default_rng(15)
+    x0 = rng.standard_normal(lv.n)
+    b = rng.standard_normal(lv.n) * np.abs(lv.D)
+    xd, bd = to_dev(x0, vtype(prec)), to_dev(b, vtype(prec))
+    lib.mg_smooth(h, 0, prec, xd, bd, sweeps, 0)
+    ref = omg.smooth(lv, to_np(to_dev(x0, vtype(prec))), to_np(bd), sweeps, omg.GS)
+    tol = {0: 1e-12, 1: 1e-5, 2: 3e-3}[prec]
+    np.testing.assert_allclose(to_np(xd), ref, rtol=0, atol=tol * np.abs(ref).max())
