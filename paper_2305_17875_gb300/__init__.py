@@ -85,6 +85,7 @@ _SIGS = {
     "mg_vcycle": ([_vp, _i, _vp, _vp], _i),
     "mg_profile_enable": ([_vp, _i], _i),
     "mg_profile_read": ([_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], _i),
+    "mg_project_rhs_noalloc": ([_vp, _vp, _vp, C.c_longlong, _vp, _vp], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -282,6 +283,18 @@ def mg_profile_read(h: Handle, slot: int):
     ms, n = C.c_double(), C.c_longlong()
     _check(_lib.mg_profile_read(h.ptr, slot, C.byref(ms), C.byref(n)), "mg_profile_read")
     return ms.value, n.value
+
+
+def mg_project_rhs_noalloc(J, f, b, mean=None, stream=None):
+    """b = J (f - mean_J f) with no device allocation (the library's static
+    scratch holds the partial sums); for callers that cannot allocate, e.g.
+    inside a stream capture.  J, f, b: float64 device tensors of one size;
+    mean: optional float64 device tensor of one element."""
+    n = J.numel()
+    if f.numel() != n or b.numel() != n:
+        raise ValueError("J, f and b must have the same size")
+    _check(_lib.mg_project_rhs_noalloc(_ptr(J, "float64"), _ptr(f, "float64"), _ptr(b, "float64"), n,
+                                       _stream(stream), _ptr(mean, "float64")), "mg_project_rhs_noalloc")
 
 
 def exported_symbols():
