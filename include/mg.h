@@ -199,6 +199,54 @@ mg_status mg_coarse_solve(mg_handle* h, int prec, const void* r_dev, void* e_dev
 mg_status mg_vcycle(mg_handle* h, int prec, void* x_dev, const void* b_dev);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of independent solve requests (a library
+ * pattern; the paper, which solves one pressure correction per time
+ * substep, has no counterpart).  Requests are admitted while the device
+ * memory reserved for admitted requests (mg_footprint_bytes + their f and x)
+ * stays within max_bytes and fewer than max_slots iterate; worker threads
+ * build each request's hierarchy (or reuse an idle one of the same grid and
+ * options, kept up to cache_bytes) and upload its right side; every step of
+ * the server is one outer iteration of all admitted requests as one batch.
+ * Requests that become ready join at the next step and converged ones retire
+ * at once, so their work overlaps on the device.  Each result is bitwise the
+ * one mg_solve gives for the same grid, options, f and a zero initial guess.
+ * ------------------------------------------------------------------------- */
+typedef struct mg_server mg_server;
+typedef struct {
+    size_t max_bytes;     /* device bytes for admitted requests; 0 = 80% of free memory */
+    int max_slots;        /* requests iterating at once (default 64) */
+    int setup_threads;    /* host threads building hierarchies (default 4) */
+    size_t cache_bytes;   /* idle hierarchies kept for reuse; 0 = max_bytes / 4 */
+    int device;           /* CUDA device; -1 = the calling thread's current device */
+} mg_serve_opts;
+typedef struct {
+    long long queued;               /* submitted, not yet admitted */
+    long long active;               /* admitted, not yet retired */
+    long long steps;                /* batched outer iterations run */
+    long long retired;              /* requests finished */
+    long long cache_hits;           /* hierarchies reused */
+    long long cached_hierarchies;   /* idle hierarchies held */
+    size_t bytes_reserved;          /* device bytes reserved for admitted requests */
+} mg_serve_stats_t;
+mg_status mg_serve_default_opts(mg_serve_opts* opts);
+/* Start a server (threads and a stream on `device`).  Free with mg_serve_destroy. */
+mg_status mg_serve_create(const mg_serve_opts* opts, mg_server** out);
+/* Queue one solve: grid and options as in mg_setup (opts may be NULL), f_host
+ * the pointwise right side (nr*nth*nph doubles, copied before the call
+ * returns), tolerance as in mg_solve.  *ticket identifies the request. */
+mg_status mg_serve_submit(mg_server* sv, const mg_grid_desc* grid, const mg_opts* opts, const double* f_host,
+                          double tol, uint64_t* ticket);
+/* MG_EAGAIN while the request is queued or iterating; otherwise its final
+ * status, with the solution copied to x_host (nr*nth*nph doubles, may be
+ * NULL) and the report (seconds = latency from submit to result) to rep.
+ * A finished ticket is released by the poll that returns it. */
+mg_status mg_serve_poll(mg_server* sv, uint64_t ticket, double* x_host, mg_report* rep);
+mg_status mg_serve_stats(mg_server* sv, mg_serve_stats_t* out);
+/* Stop the threads, wait for the device, free everything; unfinished
+ * requests are dropped. */
+void mg_serve_destroy(mg_server* sv);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with
  * CUDA events on the handle's stream (a few events per V-cycle) and
  * accumulates their device time.  Slots: 0 = fine-level smoothing launches,

@@ -58,6 +58,17 @@ class mg_report(C.Structure):
                     launches=self.launches)
 
 
+class mg_serve_opts(C.Structure):
+    _fields_ = [("max_bytes", C.c_size_t), ("max_slots", C.c_int), ("setup_threads", C.c_int),
+                ("cache_bytes", C.c_size_t), ("device", C.c_int)]
+
+
+class mg_serve_stats_t(C.Structure):
+    _fields_ = [("queued", C.c_longlong), ("active", C.c_longlong), ("steps", C.c_longlong),
+                ("retired", C.c_longlong), ("cache_hits", C.c_longlong),
+                ("cached_hierarchies", C.c_longlong), ("bytes_reserved", C.c_size_t)]
+
+
 class mg_level_info(C.Structure):
     _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int), ("cz", C.c_int),
                 ("ce", C.c_int), ("cx", C.c_int), ("stencil", C.c_int), ("levels", C.c_int)]
@@ -86,6 +97,13 @@ _SIGS = {
     "mg_profile_enable": ([_vp, _i], _i),
     "mg_profile_read": ([_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], _i),
     "mg_project_rhs_noalloc": ([_vp, _vp, _vp, C.c_longlong, _vp, _vp], _i),
+    "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
+    "mg_serve_create": ([C.POINTER(mg_serve_opts), C.POINTER(_vp)], _i),
+    "mg_serve_submit": ([_vp, C.POINTER(mg_grid_desc), C.POINTER(mg_opts), _vp, _d,
+                         C.POINTER(C.c_uint64)], _i),
+    "mg_serve_poll": ([_vp, C.c_uint64, _vp, C.POINTER(mg_report)], _i),
+    "mg_serve_stats": ([_vp, C.POINTER(mg_serve_stats_t)], _i),
+    "mg_serve_destroy": ([_vp], None),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -283,6 +301,69 @@ def mg_profile_read(h: Handle, slot: int):
     ms, n = C.c_double(), C.c_longlong()
     _check(_lib.mg_profile_read(h.ptr, slot, C.byref(ms), C.byref(n)), "mg_profile_read")
     return ms.value, n.value
+
+
+class Server:
+    """Owner of an mg_server*."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            _lib.mg_serve_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_serve_create(**kw) -> Server:
+    o = mg_serve_opts()
+    _check(_lib.mg_serve_default_opts(C.byref(o)), "mg_serve_default_opts")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, int(v))
+    p = C.c_void_p()
+    _check(_lib.mg_serve_create(C.byref(o), C.byref(p)), "mg_serve_create")
+    return Server(p)
+
+
+def mg_serve_submit(sv: Server, grid, f, tol=1e-10, opts=None) -> int:
+    g = grid if isinstance(grid, mg_grid_desc) else grid_desc(grid)
+    o = opts if isinstance(opts, mg_opts) else default_opts(**(opts or {}))
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    if f.size != g.nr * g.nth * g.nph:
+        raise ValueError("f has the wrong size")
+    t = C.c_uint64()
+    _check(_lib.mg_serve_submit(sv.ptr, C.byref(g), C.byref(o), f.ctypes.data, float(tol), C.byref(t)),
+           "mg_serve_submit")
+    return t.value
+
+
+def mg_serve_poll(sv: Server, ticket: int, x=None):
+    """None while the request runs; else (status name, report dict)."""
+    rep = mg_report()
+    st = _lib.mg_serve_poll(sv.ptr, C.c_uint64(ticket), _ptr(x), C.byref(rep))
+    if st == MG_EAGAIN:
+        return None
+    if st not in (MG_OK, MG_ENOCONV):
+        raise MGError(st, "mg_serve_poll")
+    return STATUS[st], rep.as_dict()
+
+
+def mg_serve_stats(sv: Server) -> dict:
+    s = mg_serve_stats_t()
+    _check(_lib.mg_serve_stats(sv.ptr, C.byref(s)), "mg_serve_stats")
+    return {k: getattr(s, k) for k, _ in mg_serve_stats_t._fields_}
+
+
+def mg_serve_destroy(sv: Server):
+    sv.close()
 
 
 def mg_project_rhs_noalloc(J, f, b, mean=None, stream=None):

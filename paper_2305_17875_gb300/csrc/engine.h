@@ -1,6 +1,7 @@
 // engine.h - the solver handle and the host-side multigrid driver (internal).
 #pragma once
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -92,9 +93,23 @@ void prof_begin(mg_handle* h, int slot);
 void prof_end(mg_handle* h, int slot, int nlaunch);
 void prof_collect(mg_handle* h);   // after a stream synchronisation
 // batch plans (solver.cu)
-mg_status plan_create(mg_handle* const* hs, int n, Plan** out);
+struct SolveState {             // one shell's outer-iteration bookkeeping
+    double bnorm = 1.0, best = INFINITY, tol = 0.0, rr = 0.0;
+    int it = 0;
+    mg_status st = MG_OK;
+    bool done = false;
+    mg_report R{};
+};
+// A plan launches on its lead handle's private stream, or on ``stream`` for
+// its whole life when one is given (callers whose handles come and go).
+mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stream = nullptr);
+mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n);
 void plan_destroy(Plan* pl);
 mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps);
+mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const double* tol, SolveState* S);
+int plan_check(Plan* pl, SolveState* S);
+mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph);
+mg_status plan_finish(Plan* pl, double* const* x);
 mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind);
 double model_bytes_per_iteration(const mg_handle* h);
 }  // namespace mgs

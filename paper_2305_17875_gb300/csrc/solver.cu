@@ -82,13 +82,18 @@ struct Plan {
     std::vector<mg_handle*> hs;
     int prec = 1;
     cudaStream_t stream = nullptr;
+    cudaStream_t fixed = nullptr; // when set, the plan launches here instead of on its lead handle's stream
     Program iter;                 // one outer iteration (graph)
+    // device buffers, grown on demand and reused when the plan is re-targeted
     BTask* d_iter = nullptr;
+    size_t iter_cap = 0;
     TailTask* d_tails = nullptr;
+    size_t tails_cap = 0;
     int* d_active = nullptr;      // per-shell flags
     int* h_active = nullptr;      // pinned
     double* d_fin = nullptr;      // per shell: [sum J f, ||b||^2, ||r||^2, sum J x]
     double* h_fin = nullptr;      // pinned
+    size_t dact_cap = 0, hact_cap = 0, dfin_cap = 0, hfin_cap = 0;
     BTask* d_call = nullptr;      // prologue / epilogue tasks of the current call
     size_t call_cap = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -462,62 +467,80 @@ void plan_destroy(Plan* pl) {
     delete pl;
 }
 
-mg_status plan_create(mg_handle* const* hs, int n, Plan** out) {
-    *out = nullptr;
+namespace {
+
+template <typename P>
+cudaError_t grow(P** ptr, size_t* cap, size_t need, bool pinned) {
+    if (need <= *cap && *ptr) return cudaSuccess;
+    const size_t c = std::max(need, *cap * 2 + 1);
+    if (*ptr) {
+        if (pinned) cudaFreeHost(*ptr);
+        else cudaFree(*ptr);
+        *ptr = nullptr;
+    }
+    cudaError_t e = pinned ? cudaMallocHost((void**)ptr, sizeof(P) * c) : cudaMalloc((void**)ptr, sizeof(P) * c);
+    if (e == cudaSuccess) *cap = c;
+    return e;
+}
+
+}  // namespace
+
+// Point a plan at a (new) set of handles: rebuild the iteration tables and
+// upload them into the plan's buffers (grown only when too small).
+mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n) {
     if (n <= 0) return MG_EINVAL;
-    Plan* pl = new Plan();
-    pl->hs.assign(hs, hs + n);
-    pl->prec = hs[0]->prec;
-    pl->stream = hs[0]->stream;
     for (int s = 0; s < n; ++s)
-        if (!hs[s] || hs[s]->prec != pl->prec || hs[s]->device != hs[0]->device) {
-            plan_destroy(pl);
+        if (!hs[s] || hs[s]->prec != hs[0]->prec || hs[s]->device != hs[0]->device) {
             set_error("batch handles must share device and precision");
             return MG_EINVAL;
         }
-    auto fail = [&](cudaError_t e) {
-        set_error(std::string("batch plan: ") + cudaGetErrorString(e));
-        plan_destroy(pl);
-        return MG_ECUDA;
-    };
-    cudaError_t e;
-    if ((e = cudaMalloc(&pl->d_active, sizeof(int) * n)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&pl->d_fin, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
-    if ((e = cudaMallocHost(&pl->h_active, sizeof(int) * n)) != cudaSuccess) return fail(e);
-    if ((e = cudaMallocHost(&pl->h_fin, sizeof(double) * 4 * n)) != cudaSuccess) return fail(e);
+    if (pl->stream) CK(cudaStreamSynchronize(pl->stream));
+    pl->hs.assign(hs, hs + n);
+    pl->prec = hs[0]->prec;
+    pl->stream = pl->fixed ? pl->fixed : hs[0]->stream;
+    if (pl->gexec) {
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
+    }
+    CK(grow(&pl->d_active, &pl->dact_cap, (size_t)n, false));
+    CK(grow(&pl->h_active, &pl->hact_cap, (size_t)n, true));
+    CK(grow(&pl->d_fin, &pl->dfin_cap, (size_t)4 * n, false));
+    CK(grow(&pl->h_fin, &pl->hfin_cap, (size_t)4 * n, true));
+    pl->iter = Program();
     build_iteration(pl);
-    const size_t tb = pl->iter.tasks.size() * sizeof(BTask);
-    if ((e = cudaMalloc(&pl->d_iter, tb ? tb : 16)) != cudaSuccess) return fail(e);
-    if (tb && (e = cudaMemcpyAsync(pl->d_iter, pl->iter.tasks.data(), tb, cudaMemcpyHostToDevice, pl->stream)) !=
-                  cudaSuccess)
-        return fail(e);
-    // tail tasks grouped by stencil in launch order
     std::stable_sort(pl->iter.tails.begin(), pl->iter.tails.end(),
                      [](const TailTask& a, const TailTask& b) { return a.lev[0].v.stencil < b.lev[0].v.stencil; });
-    const size_t ttb = pl->iter.tails.size() * sizeof(TailTask);
-    if (ttb) {
-        if ((e = cudaMalloc(&pl->d_tails, ttb)) != cudaSuccess) return fail(e);
-        if ((e = cudaMemcpyAsync(pl->d_tails, pl->iter.tails.data(), ttb, cudaMemcpyHostToDevice, pl->stream)) !=
-            cudaSuccess)
-            return fail(e);
+    CK(grow(&pl->d_iter, &pl->iter_cap, pl->iter.tasks.size() + 1, false));
+    if (!pl->iter.tasks.empty())
+        CK(cudaMemcpyAsync(pl->d_iter, pl->iter.tasks.data(), sizeof(BTask) * pl->iter.tasks.size(),
+                           cudaMemcpyHostToDevice, pl->stream));
+    if (!pl->iter.tails.empty()) {
+        CK(grow(&pl->d_tails, &pl->tails_cap, pl->iter.tails.size(), false));
+        CK(cudaMemcpyAsync(pl->d_tails, pl->iter.tails.data(), sizeof(TailTask) * pl->iter.tails.size(),
+                           cudaMemcpyHostToDevice, pl->stream));
     }
-    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return fail(e);
+    CK(cudaStreamSynchronize(pl->stream));
+    return MG_OK;
+}
+
+mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stream) {
+    *out = nullptr;
+    if (n <= 0) return MG_EINVAL;
+    Plan* pl = new Plan();
+    pl->fixed = stream;
+    const mg_status st = plan_reset(pl, hs, n);
+    if (st != MG_OK) {
+        plan_destroy(pl);
+        return st;
+    }
     *out = pl;
     return MG_OK;
 }
 
-// Solve every shell of the plan; the stop logic per shell is the one of a
-// lone solve, so a shell's iterates do not depend on its batch companions.
-mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps) {
+// Prologue for every shell of the plan: x in, b = J (f - mean_J f), first
+// residual and its norm; initialises the per-shell states.
+mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const double* tol, SolveState* S) {
     const int n = (int)pl->hs.size();
-    mg_handle* h0 = lead(pl);
-    cudaStream_t s = pl->stream;
-    h0->launches = 0;
-    CK(cudaEventRecord(h0->ev0, s));
-    for (int i = 0; i < n; ++i) pl->h_active[i] = 1;
-    CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
-
-    // prologue: x in, b = J (f - mean_J f), first residual
     Program pro;
     pro.begin(BOP_COPY);
     for (int i = 0; i < n; ++i) {
@@ -583,46 +606,43 @@ mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const d
     CKS(upload_call(pl, pro));
     CKS(run_program(pl, pro, pl->d_call, nullptr));
     CKS(read_fin(pl));
-
-    struct State {
-        double bnorm = 1.0, best = INFINITY;
-        int it = 0;
-        mg_status st = MG_OK;
-        bool done = false;
-        mg_report R;
-    };
-    std::vector<State> S(n);
     for (int i = 0; i < n; ++i) {
         mg_handle* h = pl->hs[i];
-        std::memset(&S[i].R, 0, sizeof(mg_report));
-        S[i].R.levels = (int)h->L.size();
-        S[i].R.stencil = h->stencil;
-        S[i].R.removed_mean = pl->h_fin[4 * i] / h->sumJ;
+        SolveState& q = S[i];
+        q = SolveState();
+        q.tol = tol[i];
+        std::memset(&q.R, 0, sizeof(mg_report));
+        q.R.levels = (int)h->L.size();
+        q.R.stencil = h->stencil;
+        q.R.removed_mean = pl->h_fin[4 * i] / h->sumJ;
         const double bn = std::sqrt(pl->h_fin[4 * i + 1]);
         if (!std::isfinite(bn)) {
-            S[i].st = MG_ENAN;
-            S[i].done = true;
+            q.st = MG_ENAN;
+            q.done = true;
             set_error("non-finite right-hand side");
         }
-        S[i].bnorm = bn > 0 ? bn : 1.0;
+        q.bnorm = bn > 0 ? bn : 1.0;
+        q.rr = pl->h_fin[4 * i + 2];
     }
-    const bool use_graph = h0->use_graph;
-    for (;;) {
-        int nactive = 0;
-        for (int i = 0; i < n; ++i) {
-            State& q = S[i];
-            if (q.done) {
-                pl->h_active[i] = 0;
-                continue;
-            }
-            const double rel = std::sqrt(pl->h_fin[4 * i + 2]) / q.bnorm;
+    return MG_OK;
+}
+
+// The stop test of every shell (the same rule as a lone solve); returns the
+// number still iterating and sets the active flags (host side).
+int plan_check(Plan* pl, SolveState* S) {
+    const int n = (int)pl->hs.size();
+    int nactive = 0;
+    for (int i = 0; i < n; ++i) {
+        SolveState& q = S[i];
+        if (!q.done) {
+            const double rel = std::sqrt(q.rr) / q.bnorm;
             if (q.it < MG_HIST) q.R.res_hist[q.it] = rel;
             q.R.rel_res = rel;
             if (!std::isfinite(rel)) {
                 q.st = MG_ENAN;
                 set_error("non-finite residual");
                 q.done = true;
-            } else if (rel <= tol[i]) {
+            } else if (rel <= q.tol) {
                 q.done = true;
             } else {
                 q.best = std::min(q.best, rel);
@@ -636,34 +656,48 @@ mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const d
                     q.done = true;
                 }
             }
-            pl->h_active[i] = q.done ? 0 : 1;
-            nactive += q.done ? 0 : 1;
         }
-        if (!nactive) break;
-        CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
-        if (use_graph) {
-            if (!pl->gexec || pl->graph_prof != h0->prof_on) CKS(build_graph(pl));
-            CK(cudaGraphLaunch(pl->gexec, s));
-            h0->launches += pl->graph_launches;
-        } else {
-            CKS(run_program(pl, pl->iter, pl->d_iter, pl->d_active));
-        }
-        CKS(read_fin(pl));
-        if (use_graph && h0->prof_on) {
-            for (auto& p : h0->graph_events) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                    h0->prof_ms[p.slot] += ms;
-                    h0->prof_n[p.slot] += p.n;
-                }
-                cudaGetLastError();
-            }
-        }
-        for (int i = 0; i < n; ++i)
-            if (pl->h_active[i]) S[i].it += 1;
+        pl->h_active[i] = q.done ? 0 : 1;
+        nactive += q.done ? 0 : 1;
     }
+    return nactive;
+}
 
-    // epilogue: gauge (J-weighted mean of x removed), x out
+// One outer iteration for the shells whose flag plan_check set, then the new
+// residual norms into the states.
+mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph) {
+    const int n = (int)pl->hs.size();
+    mg_handle* h0 = lead(pl);
+    CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, pl->stream));
+    if (use_graph) {
+        if (!pl->gexec || pl->graph_prof != h0->prof_on) CKS(build_graph(pl));
+        CK(cudaGraphLaunch(pl->gexec, pl->stream));
+        h0->launches += pl->graph_launches;
+    } else {
+        CKS(run_program(pl, pl->iter, pl->d_iter, pl->d_active));
+    }
+    CKS(read_fin(pl));
+    if (use_graph && h0->prof_on) {
+        for (auto& p : h0->graph_events) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                h0->prof_ms[p.slot] += ms;
+                h0->prof_n[p.slot] += p.n;
+            }
+            cudaGetLastError();
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (pl->h_active[i]) {
+            S[i].it += 1;
+            S[i].rr = pl->h_fin[4 * i + 2];
+        }
+    return MG_OK;
+}
+
+// Epilogue for every shell of the plan: remove the J-weighted mean, x out.
+mg_status plan_finish(Plan* pl, double* const* x) {
+    const int n = (int)pl->hs.size();
     Program epi;
     epi.begin(BOP_SUM);
     for (int i = 0; i < n; ++i) {
@@ -710,6 +744,21 @@ mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const d
     }
     CKS(upload_call(pl, epi));
     CKS(run_program(pl, epi, pl->d_call, nullptr));
+    return MG_OK;
+}
+
+// Solve every shell of the plan; the stop logic per shell is the one of a
+// lone solve, so a shell's iterates do not depend on its batch companions.
+mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps) {
+    const int n = (int)pl->hs.size();
+    mg_handle* h0 = lead(pl);
+    cudaStream_t s = pl->stream;
+    h0->launches = 0;
+    CK(cudaEventRecord(h0->ev0, s));
+    std::vector<SolveState> S(n);
+    CKS(plan_start(pl, f, x, tol, S.data()));
+    while (plan_check(pl, S.data()) > 0) CKS(plan_iterate(pl, S.data(), h0->use_graph));
+    CKS(plan_finish(pl, x));
     CK(cudaEventRecord(h0->ev1, s));
     CK(cudaEventSynchronize(h0->ev1));
     prof_collect(h0);
@@ -717,7 +766,7 @@ mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const d
     CK(cudaEventElapsedTime(&ms, h0->ev0, h0->ev1));
     mg_status worst = MG_OK;
     for (int i = 0; i < n; ++i) {
-        State& q = S[i];
+        SolveState& q = S[i];
         q.R.iters = q.it;
         q.R.seconds = ms * 1e-3;
         q.R.model_bytes = model_bytes_per_iteration(pl->hs[i]) * q.it;
