@@ -38,6 +38,13 @@ class Shell:
     e2: float = 0.0            # x2 scaled by (1 + e2)
     stretch: float = 0.0       # rx_2 of Eq. stretching; 0 = uniform
 
+    def __post_init__(self):
+        # Section 3.2's normal derivative at a longitude face differences the
+        # vertex planes one cell to either side; with two cells around the
+        # circle both are the same plane and the face determinant is zero.
+        if self.nph < 4 or self.nph % 2:
+            raise ValueError("nph must be even and >= 4")
+
     @property
     def shape(self):
         return (self.nr, self.nth, self.nph)

@@ -69,6 +69,159 @@ __device__ __forceinline__ void gs_pass(const CF& cf, const Dims& D, T* x, const
     }
 }
 
+// ---- four-cell groups (vec4 levels): the same per-cell arithmetic as the
+// scalar forms, with the longitude rows moved as 16-byte vectors.
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+}
+__device__ __forceinline__ void ldg4(const float* p, float v[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void ldg4(const double* p, double v[4]) {
+    const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *(reinterpret_cast<double2*>(p) + 1) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// x, b and the six face coefficients of the four cells (j, i, k0 .. k0 + 3)
+// of a 7-point level; cell(m) gives the Cell7 of cell k0 + m.
+template <typename T>
+struct Group7 {
+    int c0;
+    T X0[4], Jm[4], Jp[4], Im[4], Ip[4], EL[4], EU[4], ZL[4], ZU[4], XL[4];
+    T xkm, xkp, xu3;
+    template <typename CF>
+    __device__ __forceinline__ void load(const CF& cf, const Dims& D, const T* x, int j, int i, int k0) {
+        const int plane = D.nth * D.nph;
+        c0 = (j * D.nth + i) * D.nph + k0;
+        const int rb = c0 - k0;
+        const bool jl = j > 0, ju = j + 1 < D.nr, il = i > 0, iu = i + 1 < D.nth;
+        ld4(x + c0, X0);
+        if (jl) ld4(x + c0 - plane, Jm);
+        else for (int m = 0; m < 4; ++m) Jm[m] = X0[m];
+        if (ju) ld4(x + c0 + plane, Jp);
+        else for (int m = 0; m < 4; ++m) Jp[m] = X0[m];
+        if (il) ld4(x + c0 - D.nph, Im);
+        else for (int m = 0; m < 4; ++m) Im[m] = X0[m];
+        if (iu) ld4(x + c0 + D.nph, Ip);
+        else for (int m = 0; m < 4; ++m) Ip[m] = X0[m];
+        const int kw = k0 + 4 == D.nph ? rb : c0 + 4;
+        xkm = x[k0 == 0 ? rb + D.nph - 1 : c0 - 1];
+        xkp = x[kw];
+        cf.load4(4, c0, EL);
+        if (ju) cf.load4(4, c0 + plane, EU);
+        else for (int m = 0; m < 4; ++m) EU[m] = (T)0;
+        cf.load4(0, c0, ZL);
+        if (iu) cf.load4(0, c0 + D.nph, ZU);
+        else for (int m = 0; m < 4; ++m) ZU[m] = (T)0;
+        cf.load4(8, c0, XL);
+        xu3 = (T)cf(8, kw);
+    }
+    __device__ __forceinline__ Cell7<T> cell(int m) const {   // m a compile-time constant after unrolling
+        Cell7<T> q;
+        q.c = c0 + m;
+        q.xc = X0[m], q.xjm = Jm[m], q.xjp = Jp[m], q.xim = Im[m], q.xip = Ip[m];
+        q.xkm = m == 0 ? xkm : X0[m == 0 ? 0 : m - 1];
+        q.xkp = m == 3 ? xkp : X0[m == 3 ? 3 : m + 1];
+        q.el = EL[m], q.eu = EU[m], q.zl = ZL[m], q.zu = ZU[m], q.xl = XL[m];
+        q.xu = m == 3 ? xu3 : XL[m == 3 ? 3 : m + 1];
+        return q;
+    }
+};
+
+// One colour of the 7-point red-black pass over groups: in a group the cells
+// of the colour are k0 + p and k0 + p + 2, p = (colour + i + j) & 1.
+template <typename T, typename CF>
+__device__ __forceinline__ void gs_pass7v(const CF& cf, const Dims& D, T* x, const T* b, int colour, i64 first,
+                                          i64 stride) {
+    const int nq = D.nph >> 2;
+    const i64 work = (i64)D.nr * D.nth * nq;
+    for (i64 t = first; t < work; t += stride) {
+        const unsigned row = D.dq.div((unsigned)t);
+        const unsigned jj = D.dth.div(row);
+        const int k0 = 4 * (int)((unsigned)t - row * (unsigned)nq);
+        const int i = (int)(row - jj * (unsigned)D.nth), j = (int)jj;
+        Group7<T> g;
+        g.load(cf, D, x, j, i, k0);
+        T B[4];
+        ldg4(b + g.c0, B);
+        // the group is written back whole (16-byte store, full sectors); the two
+        // cells of the other colour keep the values every reader sees this pass
+        T out[4] = {g.X0[0], g.X0[1], g.X0[2], g.X0[3]};
+        if (((colour + i + j) & 1) == 0) {
+            out[0] = g.cell(0).gs(B[0]);
+            out[2] = g.cell(2).gs(B[2]);
+        } else {
+            out[1] = g.cell(1).gs(B[1]);
+            out[3] = g.cell(3).gs(B[3]);
+        }
+        st4(x + g.c0, out);
+    }
+}
+
+// 7-point residual + children-sum restriction over groups of four fine
+// longitude cells in every child row: four coarse cells when longitude is
+// not halved, two when it is.  Sums in the order of the scalar form.
+template <typename T, typename CF>
+__device__ __forceinline__ void restrict_pass7v(const CF& cf, const Dims& D, const T* x, const T* b, const Dims& Dc,
+                                                int cz, int ce, int cx, T* rc, T* ec_zero, i64 first, i64 stride) {
+    const int nq = D.nph >> 2;
+    const i64 work = (i64)Dc.nr * Dc.nth * nq;
+    for (i64 t = first; t < work; t += stride) {
+        const unsigned row = D.dq.div((unsigned)t);
+        const unsigned J = Dc.dth.div(row);
+        const int q = (int)((unsigned)t - row * (unsigned)nq);
+        const int I = (int)(row - J * (unsigned)Dc.nth);
+        T s[4] = {(T)0, (T)0, (T)0, (T)0};
+        for (int dj = 0; dj < ce; ++dj)
+            for (int di = 0; di < cz; ++di) {
+                Group7<T> g;
+                g.load(cf, D, x, ce * (int)J + dj, cz * I + di, 4 * q);
+                T B[4];
+                ldg4(b + g.c0, B);
+                const T r0 = g.cell(0).resid(B[0]), r1 = g.cell(1).resid(B[1]);
+                const T r2 = g.cell(2).resid(B[2]), r3 = g.cell(3).resid(B[3]);
+                if (cx == 1) {
+                    s[0] += r0, s[1] += r1, s[2] += r2, s[3] += r3;
+                } else {
+                    s[0] += r0;
+                    s[0] += r1;
+                    s[1] += r2;
+                    s[1] += r3;
+                }
+            }
+        const int cb = ((int)J * Dc.nth + I) * Dc.nph;
+        if (cx == 1) {
+            st4(rc + cb + 4 * q, s);
+            if (ec_zero) {
+                const T z[4] = {(T)0, (T)0, (T)0, (T)0};
+                st4(ec_zero + cb + 4 * q, z);
+            }
+        } else {
+            st2(rc + cb + 2 * q, s[0], s[1]);
+            if (ec_zero) st2(ec_zero + cb + 2 * q, (T)0, (T)0);
+        }
+    }
+}
+
 template <int S, typename T, typename CF>
 __device__ __forceinline__ void jacobi_pass(const CF& cf, const Dims& D, const T* x, T* xo, const T* b, i64 first,
                                             i64 stride) {
@@ -133,13 +286,67 @@ __device__ __forceinline__ void prolong_pass(const Dims& D, const Dims& Dc, int 
         lin1d(f.i, cz, Dc.nth, false, ii, wi);
         lin1d(f.k, cx, Dc.nph, true, ik, wk);
         T s = 0;
-        for (int a = 0; a < 2; ++a)
-            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a >= ce) break;   // only the entries with nonzero weight
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb) {
+                if (bb >= cz) break;
+#pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const T w = (T)wj[a] * (T)wi[bb] * (T)wk[e];
-                    if (w != (T)0) s += w * ec[cidx(Dc, ij[a], ii[bb], ik[e])];
+                    if (e >= cx) break;
+                    s = fma((T)wj[a] * (T)wi[bb] * (T)wk[e], ec[cidx(Dc, ij[a], ii[bb], ik[e])], s);
                 }
+            }
+        }
         x[c] = x[c] + s;
+    }
+}
+
+// Prolongation over groups of four fine longitude cells: the coarse rows and
+// weights along radius and colatitude are shared by the group.  Same weights
+// and summation order as prolong_pass.
+template <typename T>
+__device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, int cz, int ce, int cx, const T* ec,
+                                               T* x, i64 first, i64 stride) {
+    const int nq = D.nph >> 2;
+    const i64 work = (i64)D.nr * D.nth * nq;
+    for (i64 t = first; t < work; t += stride) {
+        const unsigned row = D.dq.div((unsigned)t);
+        const unsigned jj = D.dth.div(row);
+        const int k0 = 4 * (int)((unsigned)t - row * (unsigned)nq);
+        const int i = (int)(row - jj * (unsigned)D.nth), j = (int)jj;
+        int ij[2], ii[2];
+        float wj[2], wi[2];
+        lin1d(j, ce, Dc.nr, false, ij, wj);
+        lin1d(i, cz, Dc.nth, false, ii, wi);
+        const int c0 = (j * D.nth + i) * D.nph + k0;
+        T X[4];
+        ld4(x + c0, X);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            int ik[2];
+            float wk[2];
+            lin1d(k0 + m, cx, Dc.nph, true, ik, wk);
+            T s = 0;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (a >= ce) break;   // only the entries with nonzero weight
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb) {
+                    if (bb >= cz) break;
+                    const int rowc = (ij[a] * Dc.nth + ii[bb]) * Dc.nph;
+                    const T wab = (T)wj[a] * (T)wi[bb];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (e >= cx) break;
+                        s = fma(wab * (T)wk[e], ec[rowc + ik[e]], s);
+                    }
+                }
+            }
+            X[m] = X[m] + s;
+        }
+        st4(x + c0, X);
     }
 }
 
@@ -155,33 +362,42 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
     typedef typename Prec<P>::T T;
     const auto& cf = Prec<P>::cf(tk.v);
     if constexpr (OP == BOP_GS) {
-        gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
+        if (S == 7 && vec4(tk.v.D)) gs_pass7v<T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
+        else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
     } else if constexpr (OP == BOP_JACOBI) {
         jacobi_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (T*)tk.y, (const T*)tk.b, first, stride);
     } else if constexpr (OP == BOP_RESTRICT) {
-        restrict_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
-                            (T*)tk.y, (T*)tk.z, first, stride);
+        if (S == 7 && vec4(tk.v.D))
+            restrict_pass7v<T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
+                               (T*)tk.y, (T*)tk.z, first, stride);
+        else
+            restrict_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
+                                (T*)tk.y, (T*)tk.z, first, stride);
     } else if constexpr (OP == BOP_PROLONG) {
-        prolong_pass<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
+        if (vec4(tk.v.D))
+            prolong_pass_v<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
+        else
+            prolong_pass<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
     } else if constexpr (OP == BOP_RESID) {   // FP64 outer residual on the fine level (+ FP32 cast)
-        XRead<double> X{(const double*)tk.x, tk.v.D};
         const double* b = (const double*)tk.b;
         float* r32 = (float*)tk.y;
         double* scal = tk.scal;
         const double scale = r32 ? scal[SC_SCUR] : 1.0;
         if (r32 && lb == 0 && threadIdx.x == 0) scal[SC_SUSED] = scale;
         double acc = 0.0;
-        for (i64 c = first; c < tk.v.D.n(); c += stride) {
+        const float scale32 = (float)scale;   // a power of two: exact in FP32
+        const i64 N = tk.v.D.n();
+        for (i64 c = first; c < N; c += stride) {
+            const C3 cc = decode(tk.v.D, c);
             double r;
             if constexpr (S == 7) {
-                const C3 cc = decode(tk.v.D, c);
                 Cell7<double> q;
                 q.load(tk.v.c64, tk.v.D, cc.j, cc.i, cc.k, XLin<double>{(const double*)tk.x});
-                r = q.resid(b[c]);
+                r = q.resid_rows(__ldcs(b + c), __ldcs(tk.a64 + c));
             } else {
-                r = residual_cell<S>(tk.v.c64, X, tk.v.D, decode(tk.v.D, c), b[c]);
+                r = resid_rows19(tk.a64, N, (const double*)tk.x, tk.v.D, (int)c, cc, __ldcs(b + c));
             }
-            if (r32) r32[c] = (float)(r * scale);
+            if (r32) r32[c] = narrow_rn(r) * scale32;
             acc = fma(r, r, acc);
         }
         const double s = block_sum_256(acc, sh);
@@ -189,8 +405,15 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
     }
 }
 
+// Stencil passes are latency bound: cap their registers for four resident
+// CTAs per SM.
+template <int P, int OP>
+constexpr int min_ctas() {
+    return P != PREC64 && OP == BOP_GS ? 4 : (P != PREC64 && OP == BOP_RESTRICT ? 3 : 1);
+}
+
 template <int P, int OP, int S>
-__global__ void __launch_bounds__(kBT) k_batch(const BTask* __restrict__ tasks, int ntasks, int total,
+__global__ void __launch_bounds__(kBT, min_ctas<P, OP>()) k_batch(const BTask* __restrict__ tasks, int ntasks, int total,
                                                 const int* __restrict__ active, int colour, int early_trigger) {
     __shared__ double sh[8];
     __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];
@@ -223,18 +446,33 @@ __global__ void __launch_bounds__(kBT) k_batch(const BTask* __restrict__ tasks, 
         const int lb = vb - tk.block0;
         const i64 first = (i64)lb * kBT + threadIdx.x;
         const i64 stride = (i64)tk.nblocks * kBT;
+        // vector operations: groups of four elements (16-byte aligned arrays),
+        // then the remainder
+        const bool al = ((reinterpret_cast<uintptr_t>(tk.x) | reinterpret_cast<uintptr_t>(tk.b)) & 15) == 0;
+        const i64 n4 = al ? tk.n >> 2 : 0;
         if constexpr (OP == BOP_UPDATE) {
             double* x = (double*)tk.x;
             const float* e = (const float*)tk.b;
-            const double inv = 1.0 / tk.scal[SC_SUSED];
-            for (i64 c = first; c < tk.n; c += stride) x[c] = fma((double)e[c], inv, x[c]);
+            const int k = -pow2_exponent(tk.scal[SC_SUSED]);   // e / s = e * 2^k exactly
+            for (i64 g = first; g < n4; g += stride) {
+                float E[4];
+                double X[4];
+                ldg4(e + 4 * g, E);
+                ld4(x + 4 * g, X);
+                for (int m = 0; m < 4; ++m) X[m] += scaled_widen(E[m], k);
+                st4(x + 4 * g, X);
+            }
+            for (i64 c = 4 * n4 + first; c < tk.n; c += stride) x[c] += scaled_widen(e[c], k);
         } else if constexpr (OP == BOP_ZERO) {
             unsigned* x = (unsigned*)tk.x;
-            for (i64 c = first; c < tk.n; c += stride) x[c] = 0u;
+            for (i64 g = first; g < n4; g += stride) reinterpret_cast<uint4*>(x)[g] = make_uint4(0u, 0u, 0u, 0u);
+            for (i64 c = 4 * n4 + first; c < tk.n; c += stride) x[c] = 0u;
         } else if constexpr (OP == BOP_COPY) {
             unsigned* x = (unsigned*)tk.x;
             const unsigned* b = (const unsigned*)tk.b;
-            for (i64 c = first; c < tk.n; c += stride) x[c] = b[c];
+            for (i64 g = first; g < n4; g += stride)
+                reinterpret_cast<uint4*>(x)[g] = __ldg(reinterpret_cast<const uint4*>(b) + g);
+            for (i64 c = 4 * n4 + first; c < tk.n; c += stride) x[c] = b[c];
         } else if constexpr (OP == BOP_SUM) {
             const double* a = (const double*)tk.b;
             const double* w = (const double*)tk.y;
@@ -319,8 +557,7 @@ struct Faces7b {
     }
     // x_c + (b - A x)_c / A_cc from the six neighbour values
     __device__ __forceinline__ T update(T b, T xc, T xel, T xeu, T xzl, T xzu, T xxl, T xxu) const {
-        const T ax = eu * (xeu - xc) - el * (xc - xel) + zu * (xzu - xc) - zl * (xc - xzl) +
-                     xu * (xxu - xc) - xl * (xc - xxl);
+        const T ax = ax7(xc, xel, xeu, xzl, xzu, xxl, xxu, el, eu, zl, zu, xl, xu);
         const T dg = -(el + eu + zl + zu + xl + xu);
         return xc + (b - ax) / dg;
     }
@@ -439,6 +676,42 @@ __global__ void __launch_bounds__(kRB7) k_rb7(const BTask* __restrict__ tasks, i
     if (!early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// Self-check of narrow_rn and scaled_widen against the hardware conversions on
+// a million bit patterns: splitmix64 draws with exponents around the FP32
+// range (normal, subnormal and overflowing results), rounding ties of both
+// parities, zeros, infinities and NaNs.  Counts mismatches into *bad.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_convert_check(int n, unsigned* bad) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const unsigned long long h = splitmix64((unsigned long long)t);
+        // FP64 -> FP32
+        unsigned long long e = 1023 - 160 + (h >> 40) % 321;          // 2^-160 .. 2^160
+        unsigned long long m = splitmix64(h) & 0xfffffffffffffull;
+        if ((t & 7) == 1) m = (m & ~0x1fffffffull) | 0x10000000ull;     // exact tie
+        if ((t & 7) == 2) m = (m & ~0x1fffffffull) | 0x0fffffffull;     // just below a tie
+        if (t == 3) e = 0, m = 0;                                       // zero
+        if (t == 4) e = 0x7ff, m = 0;                                   // infinity
+        if (t == 5) e = 0x7ff, m = 1;                                   // NaN
+        if (t == 6) e = 1023 + 127, m = 0xfffffffffffffull;             // rounds to infinity
+        const double d = __longlong_as_double((long long)(((h & 1) << 63) | (e << 52) | m));
+        const float a = narrow_rn(d), b = __double2float_rn(d);
+        const bool same = (__float_as_uint(a) == __float_as_uint(b)) || (a != a && b != b);
+        // FP32 -> FP64 times 2^k
+        const unsigned fb = (unsigned)(splitmix64(h + 1) >> 32);
+        const float f = __uint_as_float((t & 15) == 9 ? (fb & 0x807fffffu) : fb);   // some subnormals
+        const int k = (int)((h >> 8) % 241) - 120;
+        const double w = scaled_widen(f, k), v = ldexp((double)f, k);
+        const bool same_w = (__double_as_longlong(w) == __double_as_longlong(v)) || (w != w && v != v);
+        if (!same || !same_w) atomicAdd(bad, 1u);
+    }
+}
+
 bool use_pdl() {
     static const bool on = std::getenv("MG_NO_PDL") == nullptr;
     return on;
@@ -515,6 +788,11 @@ static cudaError_t rb7_launch(const BTask* tasks, int ntasks, int total, const i
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_rb7<P>, tasks, ntasks, total, active, early);
+}
+
+cudaError_t launch_convert_check(unsigned* bad, cudaStream_t s) {
+    k_convert_check<<<512, 256, 0, s>>>(1 << 20, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BTask* tasks, int ntasks, int total_blocks, const int* active, int op, int colour,

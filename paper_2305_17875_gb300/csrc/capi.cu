@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -69,7 +70,7 @@ bool finite(double v) { return std::isfinite(v); }
 std::string check_grid(const mg_grid_desc* g) {
     if (!g) return "grid is NULL";
     if (g->nr < 1 || g->nth < 1) return "nr and nth must be >= 1";
-    if (g->nph < 2 || (g->nph & 1)) return "nph must be even and >= 2";
+    if (g->nph < 4 || (g->nph & 1)) return "nph must be even and >= 4";   // two cells degenerate the face metric
     if ((long long)g->nr * g->nth * g->nph > (1LL << 31)) return "grid too large";
     if (!(finite(g->r_in) && finite(g->r_out) && g->r_in > 0 && g->r_out > g->r_in))
         return "need 0 < r_in < r_out";
@@ -212,7 +213,7 @@ void free_handle(mg_handle* h) {
 // The index decoders divide by magic numbers; check them against true
 // division on boundary and sampled dividends up to the level's cell count.
 bool fastdiv_ok(const Dims& D) {
-    const FastDiv* fd[3] = {&D.dph, &D.dth, &D.dhk};
+    const FastDiv* fd[4] = {&D.dph, &D.dth, &D.dhk, &D.dq};
     const unsigned long long top = (unsigned long long)D.n() + 2;
     for (const FastDiv* f : fd) {
         unsigned long long n = 0;
@@ -227,6 +228,27 @@ bool fastdiv_ok(const Dims& D) {
         }
     }
     return true;
+}
+
+// The outer loop converts between FP64 and FP32 on the integer pipes; check
+// those conversions against the hardware ones once per device and process.
+mg_status conversion_check(mg_handle* h) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (h->device >= 0 && h->device < 64 && done[h->device]) return MG_OK;
+    unsigned* bad = (unsigned*)h->part;
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), h->stream));
+    CK(launch_convert_check(bad, h->stream));
+    unsigned hb = 0;
+    CK(cudaMemcpyAsync(&hb, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hb != 0) {
+        set_error("FP64/FP32 conversion self-check failed on " + std::to_string(hb) + " values");
+        return MG_EINVAL;
+    }
+    if (h->device >= 0 && h->device < 64) done[h->device] = true;
+    return MG_OK;
 }
 
 // Longest-first plan of the next level: which directions halve.
@@ -324,6 +346,11 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     if (!(h->scal = (double*)dalloc(h, sizeof(double) * SC_COUNT))) return MG_ENOMEM;
     if (!(h->one_task = (BTask*)dalloc(h, sizeof(BTask)))) return MG_ENOMEM;
     CK(launch_face_metric(T, L0.D, h->stencil, L0.g64, h->J64, stream));
+    {
+        const i64 rows = h->stencil == 19 ? 19 : 1;
+        if (!(L0.a64 = (double*)dalloc(h, sizeof(double) * rows * N))) return MG_ENOMEM;
+        CK(launch_assemble_rows(L0.view(h->stencil), L0.a64, stream));
+    }
     CKS(device_sum(h, h->J64, nullptr, N, 0));
     CKS(read_scalars(h, 1));
     h->sumJ = h->hscal[0];
@@ -352,6 +379,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
             set_error("index divisor self-check failed");
             return MG_EINVAL;
         }
+    CKS(conversion_check(h));
     Level& last = h->L.back();
     last.cz = last.ce = last.cx = 0;
     h->ncoarse = (int)last.D.n();
@@ -419,7 +447,10 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     // --- coarse tail: the deepest run of levels small enough for one cluster
     const int nl = (int)h->L.size();
     int t = nl;
-    while (t - 1 >= 1 && h->L[t - 1].D.n() <= kTailCells) --t;
+    i64 tail_cells = kTailCells;
+    if (const char* v = std::getenv("MG_TAIL_CELLS")) tail_cells = std::atoll(v);
+    if (const char* v = std::getenv("MG_TAIL_CLUSTER")) h->tail_cluster = std::max(1, std::min(8, std::atoi(v)));
+    while (t - 1 >= 1 && h->L[t - 1].D.n() <= tail_cells) --t;
     const bool want_tail = std::getenv("MG_TAIL") != nullptr && o->smoother == MG_SMOOTH_GS &&
                            nl - t >= 2 && nl - t <= kMaxTail &&
                            tail_max_clusters(h->tail_cluster, h->stencil, h->prec) > 0;
@@ -667,7 +698,8 @@ size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
     const double fine = n * (nc * (8 + (o->precision == PREC64 ? 0 : cb)) + 8 /*t*/ +
                              (o->precision == PREC64 ? 0 : 8) /*e,r*/);
     const double coarse = n * (nc * (8 + (o->precision == PREC64 ? 0 : cb)) + 24);
-    const double fixed = n * 16 /*J, b*/ + 8.0 * kMaxCoarse * kMaxCoarse + (1 << 20);
+    const double rows = n * 8 * (nc == 9 ? 19 : 1);   // assembled fine rows
+    const double fixed = n * 16 /*J, b*/ + rows + 8.0 * kMaxCoarse * kMaxCoarse + (1 << 20);
     return (size_t)(fine + coarse + fixed);
 }
 

@@ -19,6 +19,7 @@ struct Level {
     float* g32[9] = {};
     __half* g16[9] = {};
     float s16[9] = {};
+    double* a64 = nullptr;            // assembled FP64 rows (fine level only; outer residual)
     // work arrays in the cycle's value type (double for PREC64, float otherwise)
     void* e = nullptr;   // correction / iterate
     void* r = nullptr;   // right side on this level

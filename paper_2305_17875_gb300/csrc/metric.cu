@@ -153,6 +153,32 @@ __global__ void k_dense(CoefF64 cf, Dims D, double* A) {
     }
 }
 
+// Assembled operator rows of a level (row_off order): coefficient n of cell c is
+// the operator applied to the unit vector of neighbour n, evaluated at c.  A
+// neighbour that coincides with an earlier one (a longitude ring of two cells)
+// keeps its coefficient on the earlier entry and stores 0.
+template <int S>
+__global__ void k_assemble(CoefF64 cf, Dims D, double* a) {
+    const i64 N = D.n();
+    for (i64 cl = blockIdx.x * (i64)blockDim.x + threadIdx.x; cl < N; cl += (i64)gridDim.x * blockDim.x) {
+        const C3 p = decode(D, cl);
+        if (S == 7) {
+            a[cl] = diag_cell<7, double>(cf, D, p);
+            continue;
+        }
+        i64 t[19];
+        for (int n = 0; n < 19; ++n) {
+            const int j = p.j + row_off(n, 0), i = p.i + row_off(n, 1);
+            int k = p.k + row_off(n, 2);
+            k = k < 0 ? k + D.nph : (k >= D.nph ? k - D.nph : k);
+            t[n] = (j < 0 || j >= D.nr || i < 0 || i >= D.nth) ? -1 : (i64)cidx(D, j, i, k);
+            bool dup = false;
+            for (int m = 0; m < n; ++m) dup = dup || (t[n] >= 0 && t[m] == t[n]);
+            a[n * N + cl] = (t[n] < 0 || dup) ? 0.0 : apply_cell<19, double>(cf, UnitX{t[n], D}, D, p);
+        }
+    }
+}
+
 int grid_for(i64 n, int threads) {
     i64 b = (n + threads - 1) / threads;
     if (b > 152 * 32) b = 152 * 32;
@@ -165,6 +191,12 @@ cudaError_t launch_face_metric(const MetricTables& t, Dims D, int stencil, doubl
                                double* J, cudaStream_t s) {
     k_face_metric<<<grid_for(D.n(), 128), 128, 0, s>>>(t, D, stencil, g[0], g[1], g[2], g[3],
                                                        g[4], g[5], g[6], g[7], g[8], J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s) {
+    if (lv.stencil == 19) k_assemble<19><<<grid_for(lv.D.n(), 128), 128, 0, s>>>(lv.c64, lv.D, a);
+    else k_assemble<7><<<grid_for(lv.D.n(), 256), 256, 0, s>>>(lv.c64, lv.D, a);
     return cudaGetLastError();
 }
 

@@ -42,12 +42,18 @@ struct FastDiv {
 // Grids hold fewer than 2^31 cells, so linear indices are 32-bit.
 struct Dims {
     int nr = 0, nth = 0, nph = 0;
-    FastDiv dph, dth, dhk;   // by nph, by nth, by nph / 2
+    FastDiv dph, dth, dhk, dq;   // by nph, by nth, by nph / 2, by nph / 4
     __host__ __device__ Dims() {}
     __host__ __device__ Dims(int r, int t, int p)
-        : nr(r), nth(t), nph(p), dph((unsigned)p), dth((unsigned)t), dhk((unsigned)(p >= 2 ? p / 2 : 1)) {}
+        : nr(r), nth(t), nph(p), dph((unsigned)p), dth((unsigned)t), dhk((unsigned)(p >= 2 ? p / 2 : 1)),
+          dq((unsigned)(p >= 4 ? p / 4 : 1)) {}
     __host__ __device__ i64 n() const { return (i64)nr * nth * nph; }
 };
+
+// Rows of a level split into groups of four longitude cells (aligned 16-byte
+// vectors of FP32) when nph is a multiple of 4; the batched level operations
+// then work on whole groups.
+__host__ __device__ __forceinline__ bool vec4(const Dims& D) { return (D.nph & 3) == 0; }
 
 struct C3 {
     int j, i, k;
@@ -101,10 +107,20 @@ __device__ __forceinline__ C3 shift(C3 c, int s, const Dims& D) {
 struct CoefF64 {
     const double* g[9];
     __device__ __forceinline__ double operator()(int a, i64 idx) const { return __ldg(g[a] + idx); }
+    // four consecutive cells from idx (a multiple of 4)
+    __device__ __forceinline__ void load4(int a, int idx, double v[4]) const {
+        const double2 p = __ldg(reinterpret_cast<const double2*>(g[a] + idx));
+        const double2 q = __ldg(reinterpret_cast<const double2*>(g[a] + idx) + 1);
+        v[0] = p.x, v[1] = p.y, v[2] = q.x, v[3] = q.y;
+    }
 };
 struct CoefF32 {
     const float* g[9];
     __device__ __forceinline__ float operator()(int a, i64 idx) const { return __ldg(g[a] + idx); }
+    __device__ __forceinline__ void load4(int a, int idx, float v[4]) const {
+        const float4 p = __ldg(reinterpret_cast<const float4*>(g[a] + idx));
+        v[0] = p.x, v[1] = p.y, v[2] = p.z, v[3] = p.w;
+    }
 };
 // FP16 storage, FP32 arithmetic: value = half * s[a] (s a power of two per level
 // and component, chosen so the largest magnitude lands in [2^13, 2^14)).
@@ -113,6 +129,12 @@ struct CoefF16 {
     float s[9];
     __device__ __forceinline__ float operator()(int a, i64 idx) const {
         return __half2float(__ldg(g[a] + idx)) * s[a];
+    }
+    __device__ __forceinline__ void load4(int a, int idx, float v[4]) const {
+        const uint2 p = __ldg(reinterpret_cast<const uint2*>(g[a] + idx));
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
+        v[0] = lo.x * s[a], v[1] = lo.y * s[a], v[2] = hi.x * s[a], v[3] = hi.y * s[a];
     }
 };
 
@@ -127,75 +149,40 @@ struct XRead {
 // Flux through the face between L and U = L + e_d, with the metric row of U's
 // lower d-face:  F = G_dd (x_U - x_L)
 //                  + sum_{q != d} G_dq / 4 [ (x_{L+q} + x_{U+q}) - (x_{L-q} + x_{U-q}) ].
-template <int S, int d, int q, typename T, typename CF, typename XA>
-__device__ __forceinline__ T cross_term(const CF& cf, const XA& X, const Dims& D, C3 L, C3 U, i64 u) {
-    T w = (T)0.25 * (T)cf(3 * d + q, u);
-    T plus = X(shift<q>(L, +1, D)) + X(shift<q>(U, +1, D));
-    T minus = X(shift<q>(L, -1, D)) + X(shift<q>(U, -1, D));
-    return w * (plus - minus);
+// The per-cell arithmetic is written as explicit multiply-add chains, so every
+// kernel that evaluates a cell (whatever the compiler would contract) rounds
+// identically and all schedules of a solve give the same bits.
+template <int d, int q, typename T, typename XA>
+__device__ __forceinline__ T cross_diff(const XA& X, const Dims& D, C3 L, C3 U) {
+    const T plus = X(shift<q>(L, +1, D)) + X(shift<q>(U, +1, D));
+    const T minus = X(shift<q>(L, -1, D)) + X(shift<q>(U, -1, D));
+    return plus - minus;
 }
 
+// acc + sgn F for the face (L, U)
 template <int S, int d, typename T, typename CF, typename XA>
-__device__ __forceinline__ T face_flux(const CF& cf, const XA& X, const Dims& D, C3 L, C3 U) {
+__device__ __forceinline__ T add_flux(T acc, T sgn, const CF& cf, const XA& X, const Dims& D, C3 L, C3 U) {
     const i64 u = cidx(D, U);
-    T F = (T)cf(4 * d, u) * (X(U) - X(L));           // 4 d = 3 d + d
+    acc = fma(sgn * (T)cf(4 * d, u), X(U) - X(L), acc);   // 4 d = 3 d + d
     if (S == 19) {
-        if (d != 0) F += cross_term<S, d, 0, T>(cf, X, D, L, U, u);
-        if (d != 1) F += cross_term<S, d, 1, T>(cf, X, D, L, U, u);
-        if (d != 2) F += cross_term<S, d, 2, T>(cf, X, D, L, U, u);
+        if (d != 0) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 0, u), cross_diff<d, 0, T>(X, D, L, U), acc);
+        if (d != 1) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 1, u), cross_diff<d, 1, T>(X, D, L, U), acc);
+        if (d != 2) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 2, u), cross_diff<d, 2, T>(X, D, L, U), acc);
     }
-    return F;
+    return acc;
 }
 
 // (A x)_c = sum_d F_d(c + 1/2 e_d) - F_d(c - 1/2 e_d); wall faces carry no flux.
 template <int S, typename T, typename CF, typename XA>
 __device__ __forceinline__ T apply_cell(const CF& cf, const XA& X, const Dims& D, C3 c) {
     T acc = 0;
-    if (c.j > 0) acc -= face_flux<S, 1, T>(cf, X, D, shift<1>(c, -1, D), c);
-    if (c.j < D.nr - 1) acc += face_flux<S, 1, T>(cf, X, D, c, shift<1>(c, +1, D));
-    if (c.i > 0) acc -= face_flux<S, 0, T>(cf, X, D, shift<0>(c, -1, D), c);
-    if (c.i < D.nth - 1) acc += face_flux<S, 0, T>(cf, X, D, c, shift<0>(c, +1, D));
-    acc -= face_flux<S, 2, T>(cf, X, D, shift<2>(c, -1, D), c);
-    acc += face_flux<S, 2, T>(cf, X, D, c, shift<2>(c, +1, D));
+    if (c.j > 0) acc = add_flux<S, 1>(acc, (T)-1, cf, X, D, shift<1>(c, -1, D), c);
+    if (c.j < D.nr - 1) acc = add_flux<S, 1>(acc, (T)1, cf, X, D, c, shift<1>(c, +1, D));
+    if (c.i > 0) acc = add_flux<S, 0>(acc, (T)-1, cf, X, D, shift<0>(c, -1, D), c);
+    if (c.i < D.nth - 1) acc = add_flux<S, 0>(acc, (T)1, cf, X, D, c, shift<0>(c, +1, D));
+    acc = add_flux<S, 2>(acc, (T)-1, cf, X, D, shift<2>(c, -1, D), c);
+    acc = add_flux<S, 2>(acc, (T)1, cf, X, D, c, shift<2>(c, +1, D));
     return acc;
-}
-
-// r_c = b_c - (A x)_c with every face term fused into one multiply-add on r:
-// r = b - sum_d [F_d(upper) - F_d(lower)], each F expanded term by term.
-// Same operator as apply_cell; fewer FP64 instructions (FP64 issues at about
-// 1/64 of the FP32 rate on GB300, so the outer residual is instruction bound).
-template <int S, int d, typename XA>
-__device__ __forceinline__ double face_into(double r, double sgn, const CoefF64& cf, const XA& X, const Dims& D,
-                                            C3 L, C3 U) {
-    const i64 u = cidx(D, U);
-    r = fma(sgn * cf(4 * d, u), X(U) - X(L), r);
-    if (S == 19) {
-        if (d != 0) {
-            const double w = sgn * 0.25 * cf(3 * d + 0, u);
-            r = fma(w, (X(shift<0>(L, +1, D)) + X(shift<0>(U, +1, D))) - (X(shift<0>(L, -1, D)) + X(shift<0>(U, -1, D))), r);
-        }
-        if (d != 1) {
-            const double w = sgn * 0.25 * cf(3 * d + 1, u);
-            r = fma(w, (X(shift<1>(L, +1, D)) + X(shift<1>(U, +1, D))) - (X(shift<1>(L, -1, D)) + X(shift<1>(U, -1, D))), r);
-        }
-        if (d != 2) {
-            const double w = sgn * 0.25 * cf(3 * d + 2, u);
-            r = fma(w, (X(shift<2>(L, +1, D)) + X(shift<2>(U, +1, D))) - (X(shift<2>(L, -1, D)) + X(shift<2>(U, -1, D))), r);
-        }
-    }
-    return r;
-}
-
-template <int S, typename XA>
-__device__ __forceinline__ double residual_cell(const CoefF64& cf, const XA& X, const Dims& D, C3 c, double b) {
-    double r = b;
-    if (c.j > 0) r = face_into<S, 1>(r, +1.0, cf, X, D, shift<1>(c, -1, D), c);
-    if (c.j < D.nr - 1) r = face_into<S, 1>(r, -1.0, cf, X, D, c, shift<1>(c, +1, D));
-    if (c.i > 0) r = face_into<S, 0>(r, +1.0, cf, X, D, shift<0>(c, -1, D), c);
-    if (c.i < D.nth - 1) r = face_into<S, 0>(r, -1.0, cf, X, D, c, shift<0>(c, +1, D));
-    r = face_into<S, 2>(r, +1.0, cf, X, D, shift<2>(c, -1, D), c);
-    r = face_into<S, 2>(r, -1.0, cf, X, D, c, shift<2>(c, +1, D));
-    return r;
 }
 
 // Exact diagonal A_cc of the operator above.  Besides -sum of the six G_dd, a
@@ -228,7 +215,7 @@ __device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
             if (hasEl) w -= (T)cf(3, self);
             w += (T)cf(6, xu);                 // xi faces, column zeta
             w -= (T)cf(6, self);
-            dg += (T)0.25 * sz * w;
+            dg = fma((T)0.25 * sz, w, dg);
         }
         if (se != (T)0) {
             T w = 0;
@@ -236,7 +223,7 @@ __device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
             if (hasZl) w -= (T)cf(1, self);
             w += (T)cf(7, xu);                 // xi faces, column eta
             w -= (T)cf(7, self);
-            dg += (T)0.25 * se * w;
+            dg = fma((T)0.25 * se, w, dg);
         }
     }
     return dg;
@@ -249,6 +236,20 @@ __device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
 // a neighbour across a wall is replaced by x_c, which meets a zero
 // coefficient.  Same operator as apply_cell with S = 7 (Eq. PC_term1 in each
 // direction); each coefficient is loaded once for A x and the diagonal.
+// (A x)_c of the 7-point operator from the six neighbour values and face
+// coefficients, as one explicit multiply-add chain (see apply_cell).
+template <typename T>
+__device__ __forceinline__ T ax7(T xc, T xjm, T xjp, T xim, T xip, T xkm, T xkp, T el, T eu, T zl, T zu, T xl,
+                                 T xu) {
+    T a = eu * (xjp - xc);
+    a = fma(-el, xc - xjm, a);
+    a = fma(zu, xip - xc, a);
+    a = fma(-zl, xc - xim, a);
+    a = fma(xu, xkp - xc, a);
+    a = fma(-xl, xc - xkm, a);
+    return a;
+}
+
 template <typename T>
 struct Cell7 {
     int c;
@@ -276,12 +277,22 @@ struct Cell7 {
         xkp = X(kp);
     }
     __device__ __forceinline__ T ax() const {
-        return eu * (xjp - xc) - el * (xc - xjm) + zu * (xip - xc) - zl * (xc - xim) + xu * (xkp - xc) -
-               xl * (xc - xkm);
+        return ax7(xc, xjm, xjp, xim, xip, xkm, xkp, el, eu, zl, zu, xl, xu);
     }
     __device__ __forceinline__ T diag() const { return -(el + eu + zl + zu + xl + xu); }
     // Gauss-Seidel / Jacobi step x_c + (b - A x)_c / A_cc
     __device__ __forceinline__ T gs(T b) const { return xc + (b - ax()) / diag(); }
+    // b - A x with the centre coefficient a0 = A_cc stored: seven multiply-adds
+    __device__ __forceinline__ T resid_rows(T b, T a0) const {
+        T r = fma(-a0, xc, b);
+        r = fma(-el, xjm, r);
+        r = fma(-eu, xjp, r);
+        r = fma(-zl, xim, r);
+        r = fma(-zu, xip, r);
+        r = fma(-xl, xkm, r);
+        r = fma(-xu, xkp, r);
+        return r;
+    }
     // b - A x with every face term fused into one multiply-add
     __device__ __forceinline__ T resid(T b) const {
         T r = b;
@@ -294,6 +305,84 @@ struct Cell7 {
         return r;
     }
 };
+
+// ---------------------------------------------------------------- assembled rows
+// The operator row of a cell as explicit coefficients on its neighbour cells,
+// for the FP64 outer residual, which is FP64-issue bound: 19 multiply-adds per
+// cell instead of about 80 FP64 instructions of the face form.  Order of the
+// 19 neighbours (dj, di, dk): centre, -/+ radius, -/+ colatitude, -/+
+// longitude, then the radius-colatitude, radius-longitude and
+// colatitude-longitude edges, each as (-,-), (-,+), (+,-), (+,+).  A neighbour
+// beyond a wall has coefficient 0 (its mirrored contributions sit on the cell
+// it is mirrored onto).  The 7-point row stores only the centre; its six face
+// coefficients are the G arrays themselves.
+__host__ __device__ constexpr int row_off(int n, int axis) {   // axis 0 radius, 1 colatitude, 2 longitude
+    if (n == 0) return 0;
+    if (n <= 6) return (n - 1) / 2 == axis ? (((n - 1) & 1) ? 1 : -1) : 0;
+    const int g = (n - 7) / 4, m = (n - 7) & 3;
+    const int a0 = g == 2 ? 1 : 0, a1 = g == 0 ? 1 : 2;
+    if (axis == a0) return (m >> 1) ? 1 : -1;
+    if (axis == a1) return (m & 1) ? 1 : -1;
+    return 0;
+}
+
+// b_c - (A x)_c from the 19 assembled coefficients a[n * N + c] (row_off order).
+__device__ __forceinline__ double resid_rows19(const double* __restrict__ a, i64 N, const double* __restrict__ x,
+                                               const Dims& D, int c, C3 p, double b) {
+    const int plane = D.nth * D.nph;
+    const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
+    const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
+    const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
+    double r = b;
+#pragma unroll
+    for (int n = 0; n < 19; ++n) {
+        const int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
+        r = fma(-__ldcs(a + n * N + c), __ldg(x + c + o), r);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- IEEE-754 conversions
+// Conversions by exponent arithmetic.  FP64 instructions issue at a small
+// fraction of the FP32 rate on this GPU, so the FP64 <-> FP32
+// conversions of the outer loop are done on the integer pipes: exact
+// re-biasing of the exponent, and round-to-nearest-even of the 29 dropped
+// mantissa bits.  Zero, subnormal, infinite and NaN inputs, and results
+// outside the normal range, take the hardware conversion.
+
+// k with s = 2^k, for s a normal power of two (the residual scales).
+__device__ __forceinline__ int pow2_exponent(double s) {
+    return (int)((__double_as_longlong(s) >> 52) & 0x7ff) - 1023;
+}
+
+// The rare cases, kept out of line so the common path is not predicated
+// through them.
+static __device__ __noinline__ double widen_slow(float f, int k) { return ldexp((double)f, k); }
+static __device__ __noinline__ float narrow_slow(double d) { return __double2float_rn(d); }
+
+// (double)f * 2^k, exact.
+__device__ __forceinline__ double scaled_widen(float f, int k) {
+    const unsigned u = __float_as_uint(f);
+    const int ef = (int)((u >> 23) & 0xff);
+    const int ed = ef + (1023 - 127) + k;
+    if (ef == 0 || ef == 0xff || ed <= 0 || ed >= 0x7ff) return widen_slow(f, k);
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)ed << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// (float)d, round to nearest even.
+__device__ __forceinline__ float narrow_rn(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((u >> 52) & 0x7ff);
+    const int ef = e - (1023 - 127);
+    if (ef <= 0 || ef >= 0xff) return narrow_slow(d);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    const unsigned rest = (unsigned)(m & 0x1fffffffu);   // the 29 dropped bits
+    unsigned bits = ((unsigned)(u >> 63) << 31) | ((unsigned)ef << 23) | (unsigned)(m >> 29);
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) ? 1u : 0u;   // carries into the exponent
+    return __uint_as_float(bits);
+}
 
 template <typename T>
 struct XLin {   // x by linear index

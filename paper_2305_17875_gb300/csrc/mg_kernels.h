@@ -31,6 +31,9 @@ struct MetricTables {
 cudaError_t launch_face_metric(const MetricTables& t, Dims D, int stencil, double* const g[9],
                                double* J, cudaStream_t s);
 cudaError_t launch_coarsen_faces(const LevelView& fine, Dims Dc, double* const gc[9], cudaStream_t s);
+// Assembled FP64 rows of a level (row_off order): 19 x n doubles for the
+// 19-point operator, n (the centre coefficient) for the 7-point one.
+cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s);
 cudaError_t launch_cast32(const double* src, float* dst, i64 n, cudaStream_t s);
 cudaError_t launch_cast16(const double* src, __half* dst, i64 n, float inv_scale, cudaStream_t s);
 cudaError_t launch_dense_operator(const LevelView& lv, double* A, cudaStream_t s);
@@ -125,6 +128,7 @@ struct BTask {
     void* z;
     double* scal;      // the shell's device scalars
     const double* binv;
+    const double* a64; // assembled FP64 rows of the level (outer residual)
     i64 n;             // element / row / partial count of vector operations
     i64 ncells;        // fine cells (scale of the next FP32 residual)
     double aux;        // sum J
@@ -135,22 +139,11 @@ struct BTask {
     int shell;         // index of the active flag
 };
 static_assert(sizeof(BTask) % 4 == 0, "BTask is staged in shared memory word by word");
+// Checks the integer-pipe FP64 <-> FP32 conversions (narrow_rn, scaled_widen)
+// against the hardware ones; *bad (zeroed by the caller) counts mismatches.
+cudaError_t launch_convert_check(unsigned* bad, cudaStream_t s);
 // All tasks of one launch share `stencil` (7 or 19) for the stencil ops.
 cudaError_t launch_batch(const BTask* tasks, int ntasks, int total_blocks, const int* active, int op, int colour,
                          int stencil, int prec, cudaStream_t s);
-
-// ---- outer FP64 pieces (outer.cu)
-// r = b - A64 x; partials of ||r||^2 (red_blocks(n) doubles).  When r32 is
-// given, writes r32 = float(r * scal[SC_SCUR]) and records the scale used in
-// scal[SC_SUSED].
-cudaError_t launch_outer_residual(const LevelView& lv, const double* x, const double* b, float* r32,
-                                  double* scal, double* partials, cudaStream_t s);
-// x += e / scal[SC_SUSED]
-cudaError_t launch_update(double* x, const float* e, const double* scal, i64 n, cudaStream_t s);
-// b = J (f - num[0] / den), partials of ||b||^2
-cudaError_t launch_rhs(const double* J, const double* f, const double* num, double den, double* b,
-                       i64 n, double* partials, cudaStream_t s);
-// x -= num[0] / den
-cudaError_t launch_shift(double* x, const double* num, double den, i64 n, cudaStream_t s);
 
 }  // namespace mgs

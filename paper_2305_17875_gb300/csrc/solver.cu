@@ -36,6 +36,18 @@ int vblocks(i64 work) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// Work items (threads) of the batched level operations; 7-point colour passes
+// and restrictions and every prolongation work on groups of four longitude
+// cells when nph is a multiple of 4, vector operations on groups of four.
+i64 gs_items(const Dims& D, int stencil) {
+    return (i64)D.nr * D.nth * (stencil == 7 && vec4(D) ? D.nph / 4 : D.nph / 2);
+}
+i64 restrict_items(const Dims& D, const Dims& Dc, int stencil) {
+    return stencil == 7 && vec4(D) ? (i64)Dc.nr * Dc.nth * (D.nph / 4) : Dc.n();
+}
+i64 prolong_items(const Dims& D) { return vec4(D) ? D.n() / 4 : D.n(); }
+i64 vector_items(i64 n) { return (n + 3) / 4; }
+
 // one launch of a level operation over some tasks
 struct Launch {
     int op = 0, colour = 0;
@@ -177,8 +189,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
                 t.shell = (int)s;
-                const Dims& D = h->L[level].D;
-                P.add(t, vblocks((i64)D.nr * D.nth * (D.nph / 2)));
+                P.add(t, vblocks(gs_items(h->L[level].D, h->stencil)));
             }
         }
         if (any_jacobi) {
@@ -210,7 +221,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 t.b = h->L[level].t;
                 t.n = h->L[level].D.n() * (i64)(vbytes(prec) / 4);
                 t.shell = (int)s;
-                P.add(t, vblocks(t.n));
+                P.add(t, vblocks(vector_items(t.n)));
             }
         }
     }
@@ -227,7 +238,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
             t.b = h->L[level].t;
             t.n = h->L[level].D.n() * (i64)(vbytes(prec) / 4);
             t.shell = (int)s;
-            P.add(t, vblocks(t.n));
+            P.add(t, vblocks(vector_items(t.n)));
         }
     }
 }
@@ -244,6 +255,7 @@ void add_residual(Program& P, Plan* pl) {
         BTask t = task_of(h, 0);
         t.x = h->x64;
         t.b = h->b64;
+        t.a64 = h->L[0].a64;
         t.y = pl->prec == PREC64 ? nullptr : h->L[0].r;
         t.z = h->part;
         t.shell = (int)s;
@@ -279,7 +291,7 @@ void build_iteration(Plan* pl) {
             t.x = h->L[0].e;
             t.n = h->L[0].D.n();
             t.shell = (int)s;
-            P.add(t, vblocks(t.n));
+            P.add(t, vblocks(vector_items(t.n)));
         }
     }
     // down leg
@@ -299,7 +311,7 @@ void build_iteration(Plan* pl) {
             t.y = h->L[l + 1].r;
             t.z = h->L[l + 1].e;
             t.shell = (int)s;
-            P.add(t, vblocks(h->L[l + 1].D.n()));
+            P.add(t, vblocks(restrict_items(h->L[l].D, h->L[l + 1].D, h->stencil)));
         }
         }
     }
@@ -352,7 +364,7 @@ void build_iteration(Plan* pl) {
             level_bufs(h, prec, l, &t.x, &t.b);
             t.b = h->L[l + 1].e;
             t.shell = (int)s;
-            P.add(t, vblocks(h->L[l].D.n()));
+            P.add(t, vblocks(prolong_items(h->L[l].D)));
         }
         add_smooth(P, pl, l, pl->hs[0]->opts.nu2);
     }
@@ -368,7 +380,7 @@ void build_iteration(Plan* pl) {
             t.scal = h->scal;
             t.n = h->L[0].D.n();
             t.shell = (int)s;
-            P.add(t, vblocks(t.n));
+            P.add(t, vblocks(vector_items(t.n)));
         }
     }
     add_residual(P, pl);
@@ -549,7 +561,7 @@ mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const d
         t.b = x[i];
         t.n = 2 * pl->hs[i]->L[0].D.n();
         t.shell = i;
-        pro.add(t, vblocks(t.n));
+        pro.add(t, vblocks(vector_items(t.n)));
     }
     pro.begin(BOP_SUM);
     for (int i = 0; i < n; ++i) {
@@ -740,7 +752,7 @@ mg_status plan_finish(Plan* pl, double* const* x) {
         t.b = pl->hs[i]->x64;
         t.n = 2 * pl->hs[i]->L[0].D.n();
         t.shell = i;
-        epi.add(t, vblocks(t.n));
+        epi.add(t, vblocks(vector_items(t.n)));
     }
     CKS(upload_call(pl, epi));
     CKS(run_program(pl, epi, pl->d_call, nullptr));

@@ -35,6 +35,11 @@ struct XAcc {
     Dims D;
     __device__ __forceinline__ T operator()(C3 c) const { return ldv<T, CG>(x + cidx(D, c)); }
 };
+template <typename T, bool CG>
+struct XLinAcc {   // by linear index (Cell7)
+    const T* x;
+    __device__ __forceinline__ T operator()(int c) const { return ldv<T, CG>(x + c); }
+};
 
 // ---- range forms: work items first, first + stride, ... (one launch or one cluster)
 
@@ -58,10 +63,16 @@ __device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* 
             if (((i + j) & 1) != (colour & 1)) continue;
             k = 2 * kk + (((colour >> 1) + j) & 1);
         }
-        const C3 c{j, i, k};
-        const i64 id = cidx(D, c);
-        const T r = ldv<T, CG>(b + id) - apply_cell<S, T>(cf, X, D, c);
-        x[id] = ldv<T, CG>(x + id) + r / diag_cell<S, T>(cf, D, c);
+        if constexpr (S == 7) {   // the 7-point fast form (same arithmetic as the batched passes)
+            Cell7<T> q;
+            q.load(cf, D, j, i, k, XLinAcc<T, CG>{x});
+            x[q.c] = q.gs(ldv<T, CG>(b + q.c));
+        } else {
+            const C3 c{j, i, k};
+            const i64 id = cidx(D, c);
+            const T r = ldv<T, CG>(b + id) - apply_cell<S, T>(cf, X, D, c);
+            x[id] = ldv<T, CG>(x + id) + r / diag_cell<S, T>(cf, D, c);
+        }
     }
 }
 
@@ -77,7 +88,13 @@ __device__ __forceinline__ void restrict_range(const CF& cf, const Dims& D, cons
             for (int di = 0; di < cz; ++di)
                 for (int dk = 0; dk < cx; ++dk) {
                     const C3 c{ce * C.j + dj, cz * C.i + di, cx * C.k + dk};
-                    s += ldv<T, CG>(b + cidx(D, c)) - apply_cell<S, T>(cf, X, D, c);
+                    if constexpr (S == 7) {
+                        Cell7<T> q;
+                        q.load(cf, D, c.j, c.i, c.k, XLinAcc<T, CG>{x});
+                        s += q.resid(ldv<T, CG>(b + q.c));
+                    } else {
+                        s += ldv<T, CG>(b + cidx(D, c)) - apply_cell<S, T>(cf, X, D, c);
+                    }
                 }
         rc[t] = s;
         if (ec_zero) ec_zero[t] = 0;
@@ -116,12 +133,19 @@ __device__ __forceinline__ void prolong_range(const Dims& D, const Dims& Dc, int
         lin1d(f.i, cz, Dc.nth, false, ii, wi);
         lin1d(f.k, cx, Dc.nph, true, ik, wk);
         T s = 0;
-        for (int a = 0; a < 2; ++a)
-            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a >= ce) break;   // only the entries with nonzero weight
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb) {
+                if (bb >= cz) break;
+#pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const T w = (T)wj[a] * (T)wi[bb] * (T)wk[e];
-                    if (w != (T)0) s += w * ldv<T, CG>(ec + cidx(Dc, ij[a], ii[bb], ik[e]));
+                    if (e >= cx) break;
+                    s = fma((T)wj[a] * (T)wi[bb] * (T)wk[e], ldv<T, CG>(ec + cidx(Dc, ij[a], ii[bb], ik[e])), s);
                 }
+            }
+        }
         x[c] = ldv<T, CG>(x + c) + s;
     }
 }

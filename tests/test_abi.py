@@ -50,6 +50,7 @@ def test_host_side_validation_without_gpu(so):
     g = dict(nr=8, nth=8, nph=16, r_in=1.0, r_out=2.0, th0=0.5, th1=2.6)
     assert mgs.mg_footprint_bytes(g) > 8 * 8 * 8 * 16
     assert mgs.mg_footprint_bytes(dict(g, nph=15)) == 0           # odd longitude count
+    assert mgs.mg_footprint_bytes(dict(g, nph=2)) == 0            # degenerate longitude faces
     assert mgs.mg_footprint_bytes(dict(g, r_out=0.5)) == 0        # r_out < r_in
     assert mgs.mg_footprint_bytes(dict(g, th1=3.5)) == 0          # beyond the pole
     with pytest.raises(mgs.MGError) as e:

@@ -186,6 +186,39 @@ def test_fp64_vcycle_matches_oracle(lib, name, tail, monkeypatch):
     np.testing.assert_allclose(to_np(xd), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
 
 
+# ------------------------------------------------------------------ batched iterates
+ITER_GRIDS = {
+    # nph % 4 == 0: four-cell groups on every level down to nph = 4
+    "sphere_groups": W.grid_desc(8, 8, 16),
+    # nph % 4 == 2: scalar forms
+    "sphere_stretched_nph18": W.grid_desc(6, 10, 18, stretch=2.0),
+    "triaxial_stretched": GRIDS["triaxial_stretched"],
+    # the smallest longitude ring (nph = 4; the coarse levels reach nph = 2)
+    "sphere_nph4": W.grid_desc(6, 4, 4),
+    "triaxial_nph4": W.grid_desc(4, 4, 4, mapping=2, flattening=0.1, e2=0.05),
+}
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+@pytest.mark.parametrize("name", list(ITER_GRIDS))
+def test_fp64_batched_iterates_match_oracle(lib, name, iters):
+    """Plain FP64 multigrid through the batched engine: the iterate after k
+    V-cycles and the residual history (assembled FP64 rows) against the
+    oracle's V-cycles on the same right side."""
+    torch, dev = torch_dev()
+    g = ITER_GRIDS[name]
+    n = grid.shell(g).n
+    f = np.random.default_rng(21).standard_normal(n)
+    h, hier, fm = make(lib, g, 0, coarse_max=16, max_iters=iters)
+    fd = to_dev(f, torch.float64)
+    xd = torch.zeros_like(fd)
+    rep = lib.mg_solve(h, fd, xd, tol=1e-300, allow=(lib.MG_ENOCONV,))
+    xo, info = omg.solve(g, f, tol=1e-300, hier=hier, fm=fm, max_iters=iters)
+    assert rep["iters"] == info["iters"] == iters
+    np.testing.assert_allclose(to_np(xd), xo, rtol=0, atol=1e-11 * np.abs(xo).max())
+    np.testing.assert_allclose(rep["res_hist"], info["hist"], rtol=1e-9, atol=0)
+
+
 # ------------------------------------------------------------------ solves
 SOLVES = [
     ("single_sphere_32", 1, 0, dict(max_levels=4, coarsen=1)),
@@ -228,6 +261,32 @@ def test_solve_matches_oracle(lib, wl, scale, prec, opts, path, monkeypatch):
     assert info["converged"]
     err = np.abs(to_np(xd) - xo).max() / np.abs(xo).max()
     assert err <= 1e-9, err
+
+
+@pytest.mark.parametrize("wl,scale,prec", [("single_sphere_128", 4, 1), ("single_sphere_128", 4, 0),
+                                             ("single_oblate_256", 8, 1), ("single_sphere_32", 1, 2)])
+def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypatch):
+    """The coarse tail, the one-pass red-black tiles and the per-level launches
+    share the per-cell arithmetic, so every schedule gives the same bits."""
+    torch, dev = torch_dev()
+    w = W.single(wl, scale)
+    fd = to_dev(w["f"], torch.float64)
+    out = {}
+    for name, env in [("default", {}), ("tail", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192"}),
+                      ("tail_big", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4"}),
+                      ("fused", {"MG_FUSED_RB": "1"}), ("no_graph", {"MG_NO_GRAPH": "1"})]:
+        for k in ("MG_TAIL", "MG_TAIL_CELLS", "MG_TAIL_CLUSTER", "MG_FUSED_RB", "MG_NO_GRAPH"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        h = lib.mg_setup(w["grid"], dict(precision=prec))
+        xd = torch.zeros_like(fd)
+        rep = lib.mg_solve(h, fd, xd, tol=1e-10)
+        out[name] = (to_np(xd), rep["iters"])
+        h.close()
+    for name, (x, it) in out.items():
+        assert it == out["default"][1], name
+        assert np.array_equal(x, out["default"][0]), name
 
 
 def test_solve_warm_start_and_host_buffers(lib):

@@ -361,3 +361,14 @@ def test_planted_operator_mistakes_are_caught(monkeypatch):
         monkeypatch.setattr(operator, "_face_terms", bad)
         assert _interior_truncation(sh, "bump", 19) > 4 * good
         monkeypatch.setattr(operator, "_face_terms", orig)
+
+
+def test_two_cell_longitude_ring_is_rejected():
+    """With nph = 2 the longitude-face normal derivative of Section 3.2
+    differences one vertex plane against itself: the determinant is exactly
+    zero, so such grids are refused rather than given an infinite metric."""
+    with pytest.raises(ValueError):
+        grid.Shell(8, 8, 2)
+    with pytest.raises(ValueError):
+        grid.Shell(8, 8, 6 + 1)
+    assert grid.Shell(8, 8, 4).n == 256
