@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--requests", type=int, default=600, help="serve_stream: requests to submit")
+    p.add_argument("--rate", type=float, default=200.0, help="serve_stream: Poisson arrival rate (1/s)")
     return p.parse_args()
 
 
@@ -213,6 +215,10 @@ def cpu_baseline(g, tol, repeats=1):
 def run_reference(args, rank, world):
     import workloads as W
     if rank != 0:
+        return
+    if args.workload not in W.SINGLE:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times single solves only; "
+                                                              f"{args.workload} is not one"}), flush=True)
         return
     w = W.single(args.workload)
     g = w["grid"]
@@ -390,6 +396,170 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- batch of uneven shells
+def run_batch(args, rank, world, local_rank):
+    """64 shells of uneven size solved together (one launch per level
+    operation over all shells, captured outer iterations); value = fine cells
+    of all shells / batch solve time.  Also times the same shells solved one
+    after another and the plain FP64 multigrid batch."""
+    import torch
+    import paper_2305_17875_gb300 as mgs
+    import workloads as W
+    torch.cuda.set_device(local_rank)
+    items = W.batch_shells(64)
+    prec = PREC[args.precision]
+    hs, fds, xds, cells = [], [], [], 0
+    for it in items:
+        g = it["grid"]
+        hs.append(mgs.mg_setup(g, dict(precision=prec)))
+        fds.append(torch.from_numpy(W.batch_rhs(it)).cuda())
+        xds.append(torch.zeros_like(fds[-1]))
+        cells += g["nr"] * g["nth"] * g["nph"]
+    tols = [args.tol] * len(hs)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def batch_once(handles):
+        for x in xds:
+            x.zero_()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = mgs.mg_solve_batch(handles, fds, xds, tols)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), reps
+
+    for _ in range(args.warmup):
+        batch_once(hs)
+    clocks = Clocks(local_rank)
+    torch.cuda.synchronize()
+    clocks.start()
+    mgs.mg_profile_enable(hs[0], True)
+    runs = [batch_once(hs) for _ in range(args.steps)]
+    mgs.mg_profile_enable(hs[0], False)
+    clk = clocks.stop()
+    ms = [r[0] for r in runs]
+    reps = runs[-1][1]
+    ms_step = statistics.mean(ms)
+    # the same shells one after another
+    seq = 0.0
+    for h, f, x in zip(hs, fds, xds):
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mgs.mg_solve(h, f, x, tol=args.tol)
+        e1.record()
+        e1.synchronize()
+        seq += e0.elapsed_time(e1)
+    compare = None
+    if not args.no_compare and prec != 0:
+        h64 = [mgs.mg_setup(it["grid"], dict(precision=0)) for it in items]
+        batch_once(h64)
+        ms64 = [batch_once(h64)[0] for _ in range(max(1, args.steps // 3))]
+        compare = {"value": world * cells / (statistics.mean(ms64) / 1e3), "ms_per_step": statistics.mean(ms64),
+                   "speedup": statistics.mean(ms64) / ms_step}
+        for h in h64:
+            h.close()
+    if rank != 0:
+        return
+    iters = [r["iters"] for r in reps]
+    line = {
+        "metric": METRIC, "value": world * cells / (ms_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "p99_ms": float(__import__("numpy").percentile(ms, 99)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+        "config": {"workload": "batch_64", "shells": len(hs), "cells": cells, "tol": args.tol,
+                   "precision": PREC_NAME[prec], "l2": "flushed (256 MB write) before every step",
+                   "parallelism": f"replicas x{world}"},
+        "iters": {"min": min(iters), "max": max(iters)}, "max_rel_res": max(r["rel_res"] for r in reps),
+        "sequential_ms": seq, "batching_speedup": seq / ms_step,
+        "gpu_launches": int(reps[0]["launches"]) * args.steps, "clocks": clk, "fp64_mg": compare,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- serve stream
+def run_serve(args, rank, world, local_rank):
+    """Requests of the serve stream submitted at their Poisson arrival times
+    into the continuous-batching serve loop; latency = submit to result
+    (report.seconds), value = fine cells served / wall time.  Compared with
+    plain FP64 solves of the same requests one at a time (set-up included in
+    both, each request being a new grid)."""
+    import numpy as np
+    import torch
+    import paper_2305_17875_gb300 as mgs
+    import workloads as W
+    torch.cuda.set_device(local_rank)
+    reqs = W.serve_stream(n=args.requests, rate=args.rate)
+    pool = {}   # two right sides per size (the sizes are a small discrete set)
+    for q, r in enumerate(reqs):
+        key = r["grid"]["nr"]
+        if key not in pool:
+            pool[key] = [W.rhs_modes(r["grid"], seed=2000 + key), W.rhs_modes(r["grid"], seed=3000 + key)]
+        r["f"] = pool[key][q & 1]
+    prec = PREC[args.precision]
+    sv = mgs.mg_serve_create(max_slots=64, setup_threads=8)
+    # warm-up: one small request through the loop
+    g0 = W.grid_desc(32, r_out=2.0, mapping=1, flattening=0.05)
+    t = mgs.mg_serve_submit(sv, g0, W.rhs_modes(g0), 1e-8, dict(precision=prec))
+    while mgs.mg_serve_poll(sv, t, None) is None:
+        time.sleep(0.001)
+    tickets, out = [], {}
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(out) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt]["t_arrive"] <= now:
+            r = reqs[nxt]
+            tickets.append(mgs.mg_serve_submit(sv, r["grid"], r["f"], r["tol"], dict(precision=prec)))
+            nxt += 1
+        for q, tk in enumerate(tickets):
+            if q in out:
+                continue
+            res = mgs.mg_serve_poll(sv, tk, None)
+            if res is not None:
+                out[q] = res[1]
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    stats = mgs.mg_serve_stats(sv)
+    sv.close()
+    lat = np.array([out[q]["seconds"] * 1e3 for q in range(len(reqs))])
+    cells = sum(r["grid"]["nr"] * r["grid"]["nth"] * r["grid"]["nph"] for r in reqs)
+    # sequential plain FP64 (set-up + solve per request) on a prefix of the stream
+    nseq = min(len(reqs), 40)
+    x = None
+    t1 = time.perf_counter()
+    seq_cells = 0
+    for r in reqs[:nseq]:
+        h = mgs.mg_setup(r["grid"], dict(precision=0))
+        fd = torch.from_numpy(r["f"]).cuda()
+        x = torch.zeros_like(fd)
+        mgs.mg_solve(h, fd, x, tol=r["tol"])
+        torch.cuda.synchronize()
+        h.close()
+        seq_cells += r["grid"]["nr"] * r["grid"]["nth"] * r["grid"]["nph"]
+    seq_wall = time.perf_counter() - t1
+    if rank != 0:
+        return
+    value = world * cells / wall
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(reqs), "warmup": 1,
+        "ms_per_step": wall * 1e3 / len(reqs), "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)), "req_per_s": len(reqs) / wall,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+        "config": {"workload": "serve_stream", "requests": len(reqs), "rate_per_s": args.rate,
+                   "precision": PREC_NAME[prec], "sizes": sorted(pool), "parallelism": f"replicas x{world}"},
+        "serve_stats": stats,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(8 * cells / len(reqs)),
+                "d2h_bytes_per_step": int(8 * cells / len(reqs))},
+        "sequential_fp64": {"requests": nseq, "req_per_s": nseq / seq_wall, "value": seq_cells / seq_wall,
+                            "includes": "set-up and solve per request"},
+        "throughput_vs_sequential_fp64": (len(reqs) / wall) / (nseq / seq_wall),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -402,6 +572,10 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch_64":
+        run_batch(args, rank, world, local_rank)
+    elif args.workload == "serve_stream":
+        run_serve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

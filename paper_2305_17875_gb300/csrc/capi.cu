@@ -112,6 +112,24 @@ void* dalloc(mg_handle* h, size_t bytes) {
     return p;
 }
 
+// Set-up scratch on the handle's stream, freed (stream-ordered) when the
+// guard leaves scope.
+struct TmpDev {
+    void* p = nullptr;
+    cudaStream_t s;
+    TmpDev(size_t bytes, cudaStream_t st) : s(st) {
+        if (cudaMallocAsync(&p, bytes ? bytes : 16, s) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    ~TmpDev() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    TmpDev(const TmpDev&) = delete;
+    TmpDev& operator=(const TmpDev&) = delete;
+};
+
 // Eq. stretching on a 0-based (possibly fractional / ghost) vertex index.
 double stretch_unit(double jv, int n, double rx) {
     const double t = jv / n - 0.5;
@@ -138,51 +156,6 @@ mg_status device_sum(mg_handle* h, const double* a, const double* w, i64 n, int 
 
 // In-place LU with partial pivoting, then the first n columns / rows of the
 // inverse of the bordered matrix [A 1; 1^T 0].
-bool bordered_inverse(const std::vector<double>& A, int n, std::vector<double>& out) {
-    const int m = n + 1;
-    std::vector<double> B((size_t)m * m, 0.0);
-    for (int r = 0; r < n; ++r) {
-        for (int c = 0; c < n; ++c) B[(size_t)r * m + c] = A[(size_t)r * n + c];
-        B[(size_t)r * m + n] = 1.0;
-        B[(size_t)n * m + r] = 1.0;
-    }
-    std::vector<int> piv(m);
-    for (int k = 0; k < m; ++k) {
-        int p = k;
-        double best = std::fabs(B[(size_t)k * m + k]);
-        for (int r = k + 1; r < m; ++r) {
-            const double v = std::fabs(B[(size_t)r * m + k]);
-            if (v > best) { best = v; p = r; }
-        }
-        if (best == 0.0 || !std::isfinite(best)) return false;
-        piv[k] = p;
-        if (p != k)
-            for (int c = 0; c < m; ++c) std::swap(B[(size_t)k * m + c], B[(size_t)p * m + c]);
-        const double inv = 1.0 / B[(size_t)k * m + k];
-        for (int r = k + 1; r < m; ++r) {
-            double& l = B[(size_t)r * m + k];
-            l *= inv;
-            if (l != 0.0)
-                for (int c = k + 1; c < m; ++c) B[(size_t)r * m + c] -= l * B[(size_t)k * m + c];
-        }
-    }
-    out.assign((size_t)n * n, 0.0);
-    std::vector<double> col(m);
-    for (int j = 0; j < n; ++j) {            // column j of B^{-1}
-        std::fill(col.begin(), col.end(), 0.0);
-        col[j] = 1.0;
-        for (int k = 0; k < m; ++k) std::swap(col[k], col[piv[k]]);
-        for (int r = 0; r < m; ++r)
-            for (int c = 0; c < r; ++c) col[r] -= B[(size_t)r * m + c] * col[c];
-        for (int r = m - 1; r >= 0; --r) {
-            for (int c = r + 1; c < m; ++c) col[r] -= B[(size_t)r * m + c] * col[c];
-            col[r] /= B[(size_t)r * m + r];
-        }
-        for (int r = 0; r < n; ++r) out[(size_t)r * n + j] = col[r];
-    }
-    return true;
-}
-
 void free_handle(mg_handle* h) {
     if (!h) return;
     for (void* p : h->dev_allocs) cudaFree(p);
@@ -429,20 +402,31 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         }
     }
 
-    // --- coarsest level: dense operator -> bordered inverse (host, FP64)
+    // --- coarsest level: dense operator -> bordered inverse (device, FP64)
     const int nc = h->ncoarse;
-    double* dA = (double*)dalloc(h, sizeof(double) * nc * nc);
-    if (!dA) return MG_ENOMEM;
-    CK(launch_dense_operator(last.view(h->stencil), dA, stream));
-    std::vector<double> A((size_t)nc * nc), Binv;
-    CK(cudaMemcpyAsync(A.data(), dA, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
-    if (!bordered_inverse(A, nc, Binv)) {
-        set_error("coarsest bordered operator is singular");
-        return MG_EINVAL;
+    if (!(h->binv = (double*)dalloc(h, sizeof(double) * nc * nc))) return MG_ENOMEM;
+    {
+        const size_t m = (size_t)nc + 1;
+        TmpDev tA(sizeof(double) * nc * nc, stream);
+        TmpDev tw(sizeof(double) * (m * m + m) + sizeof(int) * (2 * m + 1), stream);
+        if (!tA.p || !tw.p) return MG_ENOMEM;
+        double* dA = (double*)tA.p;
+        double* work = (double*)tw.p;
+        double* col = work + m * m;
+        int* piv = (int*)(col + m);
+        int* perm = piv + m;
+        int* bad = perm + m;
+        CK(cudaMemsetAsync(bad, 0, sizeof(int), stream));
+        CK(launch_dense_operator(last.view(h->stencil), dA, stream));
+        CK(launch_bordered_inverse(dA, nc, work, col, piv, perm, bad, h->binv, stream));
+        int hbad = 0;
+        CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        if (hbad) {
+            set_error("coarsest bordered operator is singular");
+            return MG_EINVAL;
+        }
     }
-    h->binv = dA;   // reuse the buffer
-    CK(cudaMemcpyAsync(h->binv, Binv.data(), sizeof(double) * nc * nc, cudaMemcpyHostToDevice, stream));
 
     // --- coarse tail: the deepest run of levels small enough for one cluster
     const int nl = (int)h->L.size();

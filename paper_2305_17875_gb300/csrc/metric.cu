@@ -179,6 +179,94 @@ __global__ void k_assemble(CoefF64 cf, Dims D, double* a) {
     }
 }
 
+// ---- in-place Gauss-Jordan inversion with partial pivoting (FP64), for the
+// bordered coarsest matrix [A 1; 1^T 0] of order m.  Step k: the pivot row
+// (largest |M[r][k]|, r >= k) is swapped into row k, row k is scaled, and
+// every other row eliminated; the row swaps are undone on the columns at the
+// end.  A zero pivot (singular matrix) sets *bad.
+__global__ void k_bordered(const double* __restrict__ A, int n, double* __restrict__ M) {
+    const int m = n + 1;
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < (i64)m * m; t += (i64)gridDim.x * blockDim.x) {
+        const int r = (int)(t / m), c = (int)(t % m);
+        M[t] = r < n && c < n ? A[(i64)r * n + c] : (r == n && c == n ? 0.0 : 1.0);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_gj_pivot(double* M, int m, int k, double* col, int* piv, int* bad) {
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    __shared__ int p_sh;
+    double best = -1.0;
+    int arg = k;
+    for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
+        const double v = fabs(M[(i64)r * m + k]);
+        if (v > best) best = v, arg = r;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, arg, o);
+        if (ov > best || (ov == best && oi < arg)) best = ov, arg = oi;
+    }
+    if ((threadIdx.x & 31) == 0) bv[threadIdx.x >> 5] = best, bi[threadIdx.x >> 5] = arg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = -1.0;
+        int a = k;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            if (bv[w] > b || (bv[w] == b && bi[w] < a)) b = bv[w], a = bi[w];
+        if (!(b > 0.0)) *bad = 1;
+        p_sh = a;
+        piv[k] = a;
+    }
+    __syncthreads();
+    const int p = p_sh;
+    if (p != k)
+        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+            const double a = M[(i64)k * m + c];
+            M[(i64)k * m + c] = M[(i64)p * m + c];
+            M[(i64)p * m + c] = a;
+        }
+    __syncthreads();
+    const double d = M[(i64)k * m + k];
+    const double inv = d != 0.0 ? 1.0 / d : 0.0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) col[r] = r == k ? 0.0 : M[(i64)r * m + k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += blockDim.x)
+        M[(i64)k * m + c] = c == k ? inv : M[(i64)k * m + c] * inv;
+}
+
+__global__ void k_gj_elim(double* __restrict__ M, int m, int k, const double* __restrict__ col) {
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < (i64)m * m; t += (i64)gridDim.x * blockDim.x) {
+        const int r = (int)(t / m), c = (int)(t % m);
+        if (r == k) continue;
+        const double f = col[r];
+        const double v = c == k ? 0.0 : M[t];
+        M[t] = fma(-f, M[(i64)k * m + c], v);
+    }
+}
+
+// Undo the row swaps on the columns, last swap first: perm[c] = the column of
+// M that ends at position c.  One thread (O(m)).
+__global__ void k_gj_perm(const int* __restrict__ piv, int m, int* __restrict__ perm) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int c = 0; c < m; ++c) perm[c] = c;
+    for (int k = m - 1; k >= 0; --k) {
+        const int a = perm[k];
+        perm[k] = perm[piv[k]];
+        perm[piv[k]] = a;
+    }
+}
+
+// binv = leading n x n block of the unscrambled inverse.
+__global__ void k_gj_finish(const double* __restrict__ M, int m, const int* __restrict__ perm,
+                            double* __restrict__ binv) {
+    const int n = m - 1;
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < (i64)n * n; t += (i64)gridDim.x * blockDim.x) {
+        const int r = (int)(t / n), c = (int)(t % n);
+        binv[t] = M[(i64)r * m + perm[c]];
+    }
+}
+
 int grid_for(i64 n, int threads) {
     i64 b = (n + threads - 1) / threads;
     if (b > 152 * 32) b = 152 * 32;
@@ -191,6 +279,20 @@ cudaError_t launch_face_metric(const MetricTables& t, Dims D, int stencil, doubl
                                double* J, cudaStream_t s) {
     k_face_metric<<<grid_for(D.n(), 128), 128, 0, s>>>(t, D, stencil, g[0], g[1], g[2], g[3],
                                                        g[4], g[5], g[6], g[7], g[8], J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double* col, int* piv, int* perm,
+                                   int* bad, double* binv, cudaStream_t s) {
+    const int m = n + 1;
+    const i64 mm = (i64)m * m;
+    k_bordered<<<grid_for(mm, 256), 256, 0, s>>>(A, n, work);
+    for (int k = 0; k < m; ++k) {
+        k_gj_pivot<<<1, 1024, 0, s>>>(work, m, k, col, piv, bad);
+        k_gj_elim<<<grid_for(mm, 256), 256, 0, s>>>(work, m, k, col);
+    }
+    k_gj_perm<<<1, 1, 0, s>>>(piv, m, perm);
+    k_gj_finish<<<grid_for((i64)n * n, 256), 256, 0, s>>>(work, m, perm, binv);
     return cudaGetLastError();
 }
 

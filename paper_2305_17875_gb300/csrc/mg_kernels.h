@@ -37,6 +37,11 @@ cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s)
 cudaError_t launch_cast32(const double* src, float* dst, i64 n, cudaStream_t s);
 cudaError_t launch_cast16(const double* src, __half* dst, i64 n, float inv_scale, cudaStream_t s);
 cudaError_t launch_dense_operator(const LevelView& lv, double* A, cudaStream_t s);
+// Leading n x n block of [A 1; 1^T 0]^{-1} (A: n x n row-major) by Gauss-Jordan
+// elimination on the device.  work: (n+1)^2 doubles, col: n+1 doubles, piv and
+// perm: n+1 ints each, *bad (zeroed by the caller) set on a zero pivot.
+cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double* col, int* piv, int* perm,
+                                   int* bad, double* binv, cudaStream_t s);
 
 // Device scalar slots of a solve (mg_handle::scal).
 enum {
