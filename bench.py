@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="single_sphere_128")
+    p.add_argument("--scale", type=int, default=1, help="single workloads: shrink every dimension by this factor "
+                                                         "(small cases for profiling; not a bench line)")
     p.add_argument("--precision", default="fp32", choices=list(PREC))
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
@@ -63,9 +65,11 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources of the batched level kernels (the ones the roofline
+    reports on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_17875_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in ("batch.cu", "mg_internal.cuh", "mg_kernels.h"):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
@@ -100,7 +104,10 @@ def algorithmic_bytes(slot, stencil, prec, n_fine, n_next):
         coef = ncomp * cb * N if stencil == 7 else 18 * cb * N / ncol
         return vb * N + 2 * vb * N / ncol + coef
     if slot == "residual":
-        return N * (8 + 8 + 8 * ncomp + (0 if prec == 0 else 4))
+        # x, b, the FP64 operator rows (7-point: the three face arrays and the
+        # stored centre; 19-point: the 19 assembled coefficients), FP32 r out
+        rows = 8 * (ncomp + 1) if stencil == 7 else 8 * 19
+        return N * (8 + 8 + rows + (0 if prec == 0 else 4))
     if slot == "restrict0":
         return N * (2 * vb + ncomp * cb) + 2 * vb * n_next
     if slot == "prolong0":
@@ -251,7 +258,8 @@ def run_reference(args, rank, world):
 
 
 def config_of(args, g, rep, stencil):
-    c = {"workload": args.workload, "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
+    name = args.workload if getattr(args, "scale", 1) == 1 else f"{args.workload}/{args.scale}"
+    c = {"workload": name, "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
          "mapping": ["sphere", "oblate", "triaxial"][g["mapping"]], "stretch": g["stretch"],
          "flattening": g["flattening"], "tol": args.tol, "precision": PREC_NAME[PREC[args.precision]],
          "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{args.gpus}"}
@@ -292,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    w = W.single(args.workload)
+    w = W.single(args.workload, args.scale)
     g, f = w["grid"], w["f"]
     N = g["nr"] * g["nth"] * g["nph"]
     prec = PREC[args.precision]
