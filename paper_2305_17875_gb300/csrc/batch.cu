@@ -39,32 +39,36 @@ struct Prec<PREC16> {
     __device__ static const CF& cf(const LevelView& v) { return v.c16; }
 };
 
-// multicolour Gauss-Seidel colour pass (same cell mapping as stencil.cu)
+// multicolour Gauss-Seidel colour pass (same cells and arithmetic as stencil.cu)
 template <int S, typename T, typename CF>
 __device__ __forceinline__ void gs_pass(const CF& cf, const Dims& D, T* x, const T* b, int colour, i64 first,
                                         i64 stride) {
-    XRead<T> X{x, D};
     const int hk = D.nph >> 1;
-    const i64 work = (i64)D.nr * D.nth * hk;
-    for (i64 t = first; t < work; t += stride) {
-        int kk, i, j;
-        decode_half(D, t, kk, i, j);
-        int k;
-        if (S == 7) {
-            k = 2 * kk + ((colour + i + j) & 1);
-        } else {
-            if (((i + j) & 1) != (colour & 1)) continue;
-            k = 2 * kk + (((colour >> 1) + j) & 1);
-        }
-        if constexpr (S == 7) {
+    if constexpr (S == 7) {
+        const i64 work = (i64)D.nr * D.nth * hk;
+        for (i64 t = first; t < work; t += stride) {
+            int kk, i, j;
+            decode_half(D, t, kk, i, j);
             Cell7<T> q;
-            q.load(cf, D, j, i, k, XLin<T>{x});
+            q.load(cf, D, j, i, 2 * kk + ((colour + i + j) & 1), XLin<T>{x});
             x[q.c] = q.gs(b[q.c]);
-        } else {
-            const C3 c{j, i, k};
-            const i64 id = cidx(D, c);
-            const T r = b[id] - apply_cell<S, T>(cf, X, D, c);
-            x[id] = x[id] + r / diag_cell<S, T>(cf, D, c);
+        }
+    } else {
+        // 19 points: only rows with (i + j) = colour mod 2 hold cells of the colour
+        const int nth2 = (D.nth + 1) >> 1;
+        const i64 work = (i64)D.nr * nth2 * hk;
+        for (i64 t = first; t < work; t += stride) {
+            const unsigned row = D.dhk.div((unsigned)t);
+            const unsigned jj = D.dth2.div(row);
+            const int kk = (int)((unsigned)t - row * (unsigned)hk);
+            const int j = (int)jj, i = 2 * (int)(row - jj * (unsigned)nth2) + ((colour ^ j) & 1);
+            if (i >= D.nth) continue;
+            const C3 p{j, i, 2 * kk + (((colour >> 1) + j) & 1)};
+            const int c = cidx(D, p);
+            Nbr19<T> X;
+            X.load(XLin<T>{x}, D, c, p);
+            const T r = b[c] - apply19<T>(cf, X, D, c, p);
+            x[c] = X.v[0] + r / diag_cell<S, T>(cf, D, p);
         }
     }
 }
@@ -222,6 +226,166 @@ __device__ __forceinline__ void restrict_pass7v(const CF& cf, const Dims& D, con
     }
 }
 
+// ---- 19-point four-cell groups (residual + restriction).  x on the nine (j, i) rows around the group
+// (radius and colatitude clamped at the walls: mirror ghosts) as 16-byte
+// vectors, with the longitude halo of the five rows the stencil reaches
+// along k; coefficients streamed face by face as vectors.  Each cell's
+// arithmetic is apply19's chain (same bits).
+template <typename T>
+struct Group19 {
+    int c0, rb, kw;      // first cell, its row start, the longitude index after the group (wrapped)
+    T R[9][4];           // row (dj, di) at (dj + 1) * 3 + (di + 1)
+    T lo[9], hi[9];      // longitude k0 - 1 and k0 + 4 of the rows with dj == 0 or di == 0
+    bool ju, iu;
+    int plane;
+    __device__ __forceinline__ void load(const T* x, const Dims& D, int j, int i, int k0) {
+        plane = D.nth * D.nph;
+        c0 = (j * D.nth + i) * D.nph + k0;
+        rb = c0 - k0;
+        kw = k0 + 4 == D.nph ? 0 : k0 + 4;
+        ju = j + 1 < D.nr;
+        iu = i + 1 < D.nth;
+        const int oj[3] = {j > 0 ? -plane : 0, 0, ju ? plane : 0};
+        const int oi[3] = {i > 0 ? -D.nph : 0, 0, iu ? D.nph : 0};
+        const int km = k0 == 0 ? D.nph - 1 : k0 - 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int r = a * 3 + b, o = oj[a] + oi[b];
+                ld4(x + c0 + o, R[r]);
+                if (a == 1 || b == 1) {
+                    lo[r] = x[rb + o + km];
+                    hi[r] = x[rb + o + kw];
+                }
+            }
+    }
+    // x at offset (dj, di, dk) from cell m of the group
+    template <int m, int dj, int di, int dk>
+    __device__ __forceinline__ T at() const {
+        constexpr int r = (dj + 1) * 3 + (di + 1), pos = m + dk;
+        return pos < 0 ? lo[r] : (pos > 3 ? hi[r] : R[r][pos < 0 ? 0 : (pos > 3 ? 3 : pos)]);
+    }
+    // x at offset a along paper direction da and b along db (0 zeta -> i, 1 eta -> j, 2 xi -> k)
+    template <int m, int da, int a, int db, int b>
+    __device__ __forceinline__ T atd() const {
+        return at<m, (da == 1 ? a : 0) + (db == 1 ? b : 0), (da == 0 ? a : 0) + (db == 0 ? b : 0),
+                  (da == 2 ? a : 0) + (db == 2 ? b : 0)>();
+    }
+};
+
+// acc + sgn F for the d-face of cell m of the group; G[q][m] is component
+// 3d + q of the face's metric row.
+template <int d, int side, int m, typename T>
+__device__ __forceinline__ T face19g(T acc, const Group19<T>& g, const T G[3][4]) {
+    constexpr int sL = side < 0 ? -1 : 0, sU = side < 0 ? 0 : 1;
+    const T sgn = (T)side;
+    acc = fma(sgn * G[d][m], g.template atd<m, d, sU, d, 0>() - g.template atd<m, d, sL, d, 0>(), acc);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (q == d) continue;
+        T plus, minus;
+        if (q == 0) {
+            plus = g.template atd<m, d, sL, 0, 1>() + g.template atd<m, d, sU, 0, 1>();
+            minus = g.template atd<m, d, sL, 0, -1>() + g.template atd<m, d, sU, 0, -1>();
+        } else if (q == 1) {
+            plus = g.template atd<m, d, sL, 1, 1>() + g.template atd<m, d, sU, 1, 1>();
+            minus = g.template atd<m, d, sL, 1, -1>() + g.template atd<m, d, sU, 1, -1>();
+        } else {
+            plus = g.template atd<m, d, sL, 2, 1>() + g.template atd<m, d, sU, 2, 1>();
+            minus = g.template atd<m, d, sL, 2, -1>() + g.template atd<m, d, sU, 2, -1>();
+        }
+        acc = fma(sgn * (T)0.25 * G[q][m], plus - minus, acc);
+    }
+    return acc;
+}
+
+template <int d, int side, int MASK, typename T>
+__device__ __forceinline__ void face19g_all(T acc[4], const Group19<T>& g, const T G[3][4]) {
+    if (MASK & 1) acc[0] = face19g<d, side, 0>(acc[0], g, G);
+    if (MASK & 2) acc[1] = face19g<d, side, 1>(acc[1], g, G);
+    if (MASK & 4) acc[2] = face19g<d, side, 2>(acc[2], g, G);
+    if (MASK & 8) acc[3] = face19g<d, side, 3>(acc[3], g, G);
+}
+
+// (A x) of the group's cells in MASK (bit m), in apply19's face order.  Lower
+// faces read the cells' own metric rows, upper faces those of the next cell
+// along the direction; wall faces carry no flux and are skipped.
+template <int MASK, typename T, typename CF>
+__device__ __forceinline__ void apply19_group(const CF& cf, const Dims& D, const Group19<T>& g, int j, int i,
+                                              T acc[4]) {
+    T G[3][4];
+    for (int m = 0; m < 4; ++m) acc[m] = (T)0;
+    if (j > 0) {
+        for (int q = 0; q < 3; ++q) cf.load4(3 + q, g.c0, G[q]);
+        face19g_all<1, -1, MASK>(acc, g, G);
+    }
+    if (g.ju) {
+        for (int q = 0; q < 3; ++q) cf.load4(3 + q, g.c0 + g.plane, G[q]);
+        face19g_all<1, 1, MASK>(acc, g, G);
+    }
+    if (i > 0) {
+        for (int q = 0; q < 3; ++q) cf.load4(q, g.c0, G[q]);
+        face19g_all<0, -1, MASK>(acc, g, G);
+    }
+    if (g.iu) {
+        for (int q = 0; q < 3; ++q) cf.load4(q, g.c0 + D.nph, G[q]);
+        face19g_all<0, 1, MASK>(acc, g, G);
+    }
+    for (int q = 0; q < 3; ++q) cf.load4(6 + q, g.c0, G[q]);
+    face19g_all<2, -1, MASK>(acc, g, G);
+    // upper longitude faces: the next cell's lower face
+    for (int q = 0; q < 3; ++q) {
+        const T nxt = (T)cf(6 + q, g.rb + g.kw);
+        G[q][0] = G[q][1], G[q][1] = G[q][2], G[q][2] = G[q][3], G[q][3] = nxt;
+    }
+    face19g_all<2, 1, MASK>(acc, g, G);
+}
+
+// 19-point residual + children-sum restriction over groups (as restrict_pass7v).
+template <typename T, typename CF>
+__device__ __forceinline__ void restrict_pass19v(const CF& cf, const Dims& D, const T* x, const T* b, const Dims& Dc,
+                                                 int cz, int ce, int cx, T* rc, T* ec_zero, i64 first, i64 stride) {
+    const int nq = D.nph >> 2;
+    const i64 work = (i64)Dc.nr * Dc.nth * nq;
+    for (i64 t = first; t < work; t += stride) {
+        const unsigned row = D.dq.div((unsigned)t);
+        const unsigned J = Dc.dth.div(row);
+        const int q = (int)((unsigned)t - row * (unsigned)nq);
+        const int I = (int)(row - J * (unsigned)Dc.nth);
+        T s[4] = {(T)0, (T)0, (T)0, (T)0};
+        for (int dj = 0; dj < ce; ++dj)
+            for (int di = 0; di < cz; ++di) {
+                const int j = ce * (int)J + dj, i = cz * I + di;
+                Group19<T> g;
+                g.load(x, D, j, i, 4 * q);
+                T B[4], ax[4];
+                ldg4(b + g.c0, B);
+                apply19_group<15>(cf, D, g, j, i, ax);
+                const T r0 = B[0] - ax[0], r1 = B[1] - ax[1], r2 = B[2] - ax[2], r3 = B[3] - ax[3];
+                if (cx == 1) {
+                    s[0] += r0, s[1] += r1, s[2] += r2, s[3] += r3;
+                } else {
+                    s[0] += r0;
+                    s[0] += r1;
+                    s[1] += r2;
+                    s[1] += r3;
+                }
+            }
+        const int cb = ((int)J * Dc.nth + I) * Dc.nph;
+        if (cx == 1) {
+            st4(rc + cb + 4 * q, s);
+            if (ec_zero) {
+                const T z[4] = {(T)0, (T)0, (T)0, (T)0};
+                st4(ec_zero + cb + 4 * q, z);
+            }
+        } else {
+            st2(rc + cb + 2 * q, s[0], s[1]);
+            if (ec_zero) st2(ec_zero + cb + 2 * q, (T)0, (T)0);
+        }
+    }
+}
+
 template <int S, typename T, typename CF>
 __device__ __forceinline__ void jacobi_pass(const CF& cf, const Dims& D, const T* x, T* xo, const T* b, i64 first,
                                             i64 stride) {
@@ -237,7 +401,6 @@ __device__ __forceinline__ void jacobi_pass(const CF& cf, const Dims& D, const T
 template <int S, typename T, typename CF>
 __device__ __forceinline__ void restrict_pass(const CF& cf, const Dims& D, const T* x, const T* b, const Dims& Dc,
                                               int cz, int ce, int cx, T* rc, T* ec_zero, i64 first, i64 stride) {
-    XRead<T> X{x, D};
     for (i64 t = first; t < Dc.n(); t += stride) {
         const C3 C = decode(Dc, t);
         T s = 0;
@@ -250,7 +413,10 @@ __device__ __forceinline__ void restrict_pass(const CF& cf, const Dims& D, const
                         q.load(cf, D, c.j, c.i, c.k, XLin<T>{x});
                         s += q.resid(b[q.c]);
                     } else {
-                        s += b[cidx(D, c)] - apply_cell<S, T>(cf, X, D, c);
+                        const int id = cidx(D, c);
+                        Nbr19<T> X;
+                        X.load(XLin<T>{x}, D, id, c);
+                        s += b[id] - apply19<T>(cf, X, D, id, c);
                     }
                 }
         rc[t] = s;
@@ -323,6 +489,52 @@ __device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, in
         const int c0 = (j * D.nth + i) * D.nph + k0;
         T X[4];
         ld4(x + c0, X);
+        if (cx == 1) {   // longitude not halved: coarse groups of four, weight 1 along k
+            T s[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (a >= ce) break;
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb) {
+                    if (bb >= cz) break;
+                    const T wab = (T)wj[a] * (T)wi[bb];
+                    T E[4];
+                    ldg4(ec + (ij[a] * Dc.nth + ii[bb]) * Dc.nph + k0, E);
+                    for (int m = 0; m < 4; ++m) s[m] = fma(wab * (T)1.0f, E[m], s[m]);
+                }
+            }
+            for (int m = 0; m < 4; ++m) X[m] = X[m] + s[m];
+            st4(x + c0, X);
+            continue;
+        }
+        if (cx == 2) {   // halved: fine k0..k0+3 from coarse K0-1 .. K0+2, K0 = k0 / 2
+            const int K0 = k0 >> 1;
+            const int Km = K0 == 0 ? Dc.nph - 1 : K0 - 1, Kp = K0 + 2 == Dc.nph ? 0 : K0 + 2;
+            T s[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (a >= ce) break;
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb) {
+                    if (bb >= cz) break;
+                    const T wab = (T)wj[a] * (T)wi[bb];
+                    const T* er = ec + (ij[a] * Dc.nth + ii[bb]) * Dc.nph;
+                    const T e0 = er[K0], e1 = er[K0 + 1], em = er[Km], ep = er[Kp];
+                    // weights 3/4 on the coarse cell, 1/4 on its neighbour (e = 0, 1)
+                    s[0] = fma(wab * (T)0.75f, e0, s[0]);
+                    s[0] = fma(wab * (T)0.25f, em, s[0]);
+                    s[1] = fma(wab * (T)0.75f, e0, s[1]);
+                    s[1] = fma(wab * (T)0.25f, e1, s[1]);
+                    s[2] = fma(wab * (T)0.75f, e1, s[2]);
+                    s[2] = fma(wab * (T)0.25f, e0, s[2]);
+                    s[3] = fma(wab * (T)0.75f, e1, s[3]);
+                    s[3] = fma(wab * (T)0.25f, ep, s[3]);
+                }
+            }
+            for (int m = 0; m < 4; ++m) X[m] = X[m] + s[m];
+            st4(x + c0, X);
+            continue;
+        }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             int ik[2];
@@ -362,6 +574,8 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
     typedef typename Prec<P>::T T;
     const auto& cf = Prec<P>::cf(tk.v);
     if constexpr (OP == BOP_GS) {
+        // 19 points: the scalar form (a group would load four cells to update two
+        // with twice the registers); 7 points: groups when nph is a multiple of 4
         if (S == 7 && vec4(tk.v.D)) gs_pass7v<T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
         else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
     } else if constexpr (OP == BOP_JACOBI) {
@@ -370,6 +584,9 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         if (S == 7 && vec4(tk.v.D))
             restrict_pass7v<T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
                                (T*)tk.y, (T*)tk.z, first, stride);
+        else if (S == 19 && vec4(tk.v.D))
+            restrict_pass19v<T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
+                                (T*)tk.y, (T*)tk.z, first, stride);
         else
             restrict_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
                                 (T*)tk.y, (T*)tk.z, first, stride);
@@ -407,13 +624,16 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
 
 // Stencil passes are latency bound: cap their registers for four resident
 // CTAs per SM.
-template <int P, int OP>
+template <int P, int OP, int S>
 constexpr int min_ctas() {
-    return P != PREC64 && OP == BOP_GS ? 4 : (P != PREC64 && OP == BOP_RESTRICT ? 3 : 1);
+    if (P == PREC64 || (OP != BOP_GS && OP != BOP_RESTRICT)) return 1;
+    if (OP == BOP_GS) return 4;
+    if (S == 19) return 2;                 // the 19-point restriction groups hold ~100 values per thread
+    return P == PREC32 ? 3 : 1;
 }
 
 template <int P, int OP, int S>
-__global__ void __launch_bounds__(kBT, min_ctas<P, OP>()) k_batch(const BTask* __restrict__ tasks, int ntasks, int total,
+__global__ void __launch_bounds__(kBT, min_ctas<P, OP, S>()) k_batch(const BTask* __restrict__ tasks, int ntasks, int total,
                                                 const int* __restrict__ active, int colour, int early_trigger) {
     __shared__ double sh[8];
     __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];

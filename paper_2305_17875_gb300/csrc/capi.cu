@@ -186,7 +186,7 @@ void free_handle(mg_handle* h) {
 // The index decoders divide by magic numbers; check them against true
 // division on boundary and sampled dividends up to the level's cell count.
 bool fastdiv_ok(const Dims& D) {
-    const FastDiv* fd[4] = {&D.dph, &D.dth, &D.dhk, &D.dq};
+    const FastDiv* fd[5] = {&D.dph, &D.dth, &D.dhk, &D.dq, &D.dth2};
     const unsigned long long top = (unsigned long long)D.n() + 2;
     for (const FastDiv* f : fd) {
         unsigned long long n = 0;

@@ -42,11 +42,11 @@ struct FastDiv {
 // Grids hold fewer than 2^31 cells, so linear indices are 32-bit.
 struct Dims {
     int nr = 0, nth = 0, nph = 0;
-    FastDiv dph, dth, dhk, dq;   // by nph, by nth, by nph / 2, by nph / 4
+    FastDiv dph, dth, dhk, dq, dth2;   // by nph, nth, nph / 2, nph / 4, (nth + 1) / 2
     __host__ __device__ Dims() {}
     __host__ __device__ Dims(int r, int t, int p)
         : nr(r), nth(t), nph(p), dph((unsigned)p), dth((unsigned)t), dhk((unsigned)(p >= 2 ? p / 2 : 1)),
-          dq((unsigned)(p >= 4 ? p / 4 : 1)) {}
+          dq((unsigned)(p >= 4 ? p / 4 : 1)), dth2((unsigned)((t + 1) / 2)) {}
     __host__ __device__ i64 n() const { return (i64)nr * nth * nph; }
 };
 
@@ -324,6 +324,83 @@ __host__ __device__ constexpr int row_off(int n, int axis) {   // axis 0 radius,
     if (axis == a0) return (m >> 1) ? 1 : -1;
     if (axis == a1) return (m & 1) ? 1 : -1;
     return 0;
+}
+
+// Entry of the 19-point neighbourhood at offset (dj, di, dk), in row_off order.
+__host__ __device__ constexpr int row_index(int dj, int di, int dk) {
+    return (dj == 0 && di == 0 && dk == 0) ? 0
+           : (di == 0 && dk == 0)          ? (dj < 0 ? 1 : 2)
+           : (dj == 0 && dk == 0)          ? (di < 0 ? 3 : 4)
+           : (dj == 0 && di == 0)          ? (dk < 0 ? 5 : 6)
+           : dk == 0                        ? 7 + 2 * (dj > 0) + (di > 0)
+           : di == 0                        ? 11 + 2 * (dj > 0) + (dk > 0)
+                                            : 15 + 2 * (di > 0) + (dk > 0);
+}
+
+// x on the 19-point neighbourhood of cell c, with the operator's neighbour
+// rules: mirror (clamp) at the radial and colatitude walls, wrap in longitude.
+template <typename T>
+struct Nbr19 {
+    T v[19];
+    template <typename XL>
+    __device__ __forceinline__ void load(const XL& X, const Dims& D, int c, C3 p) {
+        const int plane = D.nth * D.nph;
+        const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
+        const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
+        const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
+#pragma unroll
+        for (int n = 0; n < 19; ++n) v[n] = X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
+    }
+    // value at offset a along paper direction da and b along direction db
+    // (directions 0 zeta -> i, 1 eta -> j, 2 xi -> k)
+    template <int da, int a, int db, int b>
+    __device__ __forceinline__ T at() const {
+        constexpr int dj = (da == 1 ? a : 0) + (db == 1 ? b : 0);
+        constexpr int di = (da == 0 ? a : 0) + (db == 0 ? b : 0);
+        constexpr int dk = (da == 2 ? a : 0) + (db == 2 ? b : 0);
+        return v[row_index(dj, di, dk)];
+    }
+};
+
+// acc + sgn F for the lower (side -1) or upper (side +1) d-face of the cell,
+// from registers: the arithmetic of add_flux step by step (same bits).
+template <int d, int side, typename T, typename CF>
+__device__ __forceinline__ T add_flux19(T acc, const CF& cf, const Nbr19<T>& X, int u) {
+    constexpr int sL = side < 0 ? -1 : 0, sU = side < 0 ? 0 : 1;
+    const T sgn = (T)side;
+    acc = fma(sgn * (T)cf(4 * d, u), X.template at<d, sU, d, 0>() - X.template at<d, sL, d, 0>(), acc);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (q == d) continue;
+        T plus, minus;
+        if (q == 0) {
+            plus = X.template at<d, sL, 0, 1>() + X.template at<d, sU, 0, 1>();
+            minus = X.template at<d, sL, 0, -1>() + X.template at<d, sU, 0, -1>();
+        } else if (q == 1) {
+            plus = X.template at<d, sL, 1, 1>() + X.template at<d, sU, 1, 1>();
+            minus = X.template at<d, sL, 1, -1>() + X.template at<d, sU, 1, -1>();
+        } else {
+            plus = X.template at<d, sL, 2, 1>() + X.template at<d, sU, 2, 1>();
+            minus = X.template at<d, sL, 2, -1>() + X.template at<d, sU, 2, -1>();
+        }
+        acc = fma(sgn * (T)0.25 * (T)cf(3 * d + q, u), plus - minus, acc);
+    }
+    return acc;
+}
+
+// (A x)_c of the 19-point operator from the loaded neighbourhood; equal bit
+// for bit to apply_cell<19>.
+template <typename T, typename CF>
+__device__ __forceinline__ T apply19(const CF& cf, const Nbr19<T>& X, const Dims& D, int c, C3 p) {
+    const int plane = D.nth * D.nph;
+    T acc = 0;
+    if (p.j > 0) acc = add_flux19<1, -1>(acc, cf, X, c);
+    if (p.j < D.nr - 1) acc = add_flux19<1, 1>(acc, cf, X, c + plane);
+    if (p.i > 0) acc = add_flux19<0, -1>(acc, cf, X, c);
+    if (p.i < D.nth - 1) acc = add_flux19<0, 1>(acc, cf, X, c + D.nph);
+    acc = add_flux19<2, -1>(acc, cf, X, c);
+    acc = add_flux19<2, 1>(acc, cf, X, p.k + 1 < D.nph ? c + 1 : c + 1 - D.nph);
+    return acc;
 }
 
 // b_c - (A x)_c from the 19 assembled coefficients a[n * N + c] (row_off order).

@@ -36,15 +36,14 @@ int vblocks(i64 work) {
     return (int)(b < 1 ? 1 : b);
 }
 
-// Work items (threads) of the batched level operations; 7-point colour passes
-// and restrictions and every prolongation work on groups of four longitude
-// cells when nph is a multiple of 4, vector operations on groups of four.
+// Work items (threads) of the batched level operations; 7-point colour passes,
+// restrictions and prolongations work on groups of four longitude cells when
+// nph is a multiple of 4, vector operations on groups of four elements.
 i64 gs_items(const Dims& D, int stencil) {
-    return (i64)D.nr * D.nth * (stencil == 7 && vec4(D) ? D.nph / 4 : D.nph / 2);
+    if (stencil == 19) return (i64)D.nr * ((D.nth + 1) / 2) * (D.nph / 2);   // rows of the colour only
+    return (i64)D.nr * D.nth * (vec4(D) ? D.nph / 4 : D.nph / 2);
 }
-i64 restrict_items(const Dims& D, const Dims& Dc, int stencil) {
-    return stencil == 7 && vec4(D) ? (i64)Dc.nr * Dc.nth * (D.nph / 4) : Dc.n();
-}
+i64 restrict_items(const Dims& D, const Dims& Dc) { return vec4(D) ? (i64)Dc.nr * Dc.nth * (D.nph / 4) : Dc.n(); }
 i64 prolong_items(const Dims& D) { return vec4(D) ? D.n() / 4 : D.n(); }
 i64 vector_items(i64 n) { return (n + 3) / 4; }
 
@@ -311,7 +310,7 @@ void build_iteration(Plan* pl) {
             t.y = h->L[l + 1].r;
             t.z = h->L[l + 1].e;
             t.shell = (int)s;
-            P.add(t, vblocks(restrict_items(h->L[l].D, h->L[l + 1].D, h->stencil)));
+            P.add(t, vblocks(restrict_items(h->L[l].D, h->L[l + 1].D)));
         }
         }
     }

@@ -50,28 +50,31 @@ struct XLinAcc {   // by linear index (Cell7)
 template <int S, typename T, typename CF, bool CG>
 __device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* x, const T* b, int colour,
                                                 i64 first, i64 stride) {
-    XAcc<T, CG> X{x, D};
     const int hk = D.nph >> 1;
-    const i64 work = (i64)D.nr * D.nth * hk;
-    for (i64 t = first; t < work; t += stride) {
-        int kk, i, j;
-        decode_half(D, t, kk, i, j);
-        int k;
-        if (S == 7) {
-            k = 2 * kk + ((colour + i + j) & 1);
-        } else {
-            if (((i + j) & 1) != (colour & 1)) continue;
-            k = 2 * kk + (((colour >> 1) + j) & 1);
-        }
-        if constexpr (S == 7) {   // the 7-point fast form (same arithmetic as the batched passes)
+    if constexpr (S == 7) {   // the 7-point fast form (same arithmetic as the batched passes)
+        const i64 work = (i64)D.nr * D.nth * hk;
+        for (i64 t = first; t < work; t += stride) {
+            int kk, i, j;
+            decode_half(D, t, kk, i, j);
             Cell7<T> q;
-            q.load(cf, D, j, i, k, XLinAcc<T, CG>{x});
+            q.load(cf, D, j, i, 2 * kk + ((colour + i + j) & 1), XLinAcc<T, CG>{x});
             x[q.c] = q.gs(ldv<T, CG>(b + q.c));
-        } else {
-            const C3 c{j, i, k};
-            const i64 id = cidx(D, c);
-            const T r = ldv<T, CG>(b + id) - apply_cell<S, T>(cf, X, D, c);
-            x[id] = ldv<T, CG>(x + id) + r / diag_cell<S, T>(cf, D, c);
+        }
+    } else {   // rows with (i + j) = colour mod 2 only; the neighbourhood in registers
+        const int nth2 = (D.nth + 1) >> 1;
+        const i64 work = (i64)D.nr * nth2 * hk;
+        for (i64 t = first; t < work; t += stride) {
+            const unsigned row = D.dhk.div((unsigned)t);
+            const unsigned jj = D.dth2.div(row);
+            const int kk = (int)((unsigned)t - row * (unsigned)hk);
+            const int j = (int)jj, i = 2 * (int)(row - jj * (unsigned)nth2) + ((colour ^ j) & 1);
+            if (i >= D.nth) continue;
+            const C3 p{j, i, 2 * kk + (((colour >> 1) + j) & 1)};
+            const int c = cidx(D, p);
+            Nbr19<T> X;
+            X.load(XLinAcc<T, CG>{x}, D, c, p);
+            const T r = ldv<T, CG>(b + c) - apply19<T>(cf, X, D, c, p);
+            x[c] = X.v[0] + r / diag_cell<S, T>(cf, D, p);
         }
     }
 }
@@ -80,7 +83,6 @@ __device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* 
 template <int S, typename T, typename CF, bool CG>
 __device__ __forceinline__ void restrict_range(const CF& cf, const Dims& D, const T* x, const T* b, const Dims& Dc,
                                                int cz, int ce, int cx, T* rc, T* ec_zero, i64 first, i64 stride) {
-    XAcc<T, CG> X{x, D};
     for (i64 t = first; t < Dc.n(); t += stride) {
         const C3 C = decode(Dc, t);
         T s = 0;
@@ -93,7 +95,10 @@ __device__ __forceinline__ void restrict_range(const CF& cf, const Dims& D, cons
                         q.load(cf, D, c.j, c.i, c.k, XLinAcc<T, CG>{x});
                         s += q.resid(ldv<T, CG>(b + q.c));
                     } else {
-                        s += ldv<T, CG>(b + cidx(D, c)) - apply_cell<S, T>(cf, X, D, c);
+                        const int id = cidx(D, c);
+                        Nbr19<T> X;
+                        X.load(XLinAcc<T, CG>{x}, D, id, c);
+                        s += ldv<T, CG>(b + id) - apply19<T>(cf, X, D, id, c);
                     }
                 }
         rc[t] = s;

@@ -196,6 +196,10 @@ ITER_GRIDS = {
     # the smallest longitude ring (nph = 4; the coarse levels reach nph = 2)
     "sphere_nph4": W.grid_desc(6, 4, 4),
     "triaxial_nph4": W.grid_desc(4, 4, 4, mapping=2, flattening=0.1, e2=0.05),
+    # 19 points: odd colatitude count (rows of one parity one longer), and
+    # a longitude count that is not a multiple of 4 (scalar forms)
+    "triaxial_odd_nth": W.grid_desc(6, 9, 12, mapping=2, flattening=0.1, e2=0.05),
+    "oblate_nph10": W.grid_desc(4, 6, 10, r_out=1 / 0.6, mapping=1, flattening=0.1),
 }
 
 
