@@ -227,6 +227,12 @@ typedef struct {
     long long cache_hits;           /* hierarchies reused */
     long long cached_hierarchies;   /* idle hierarchies held */
     size_t bytes_reserved;          /* device bytes reserved for admitted requests */
+    /* host seconds the stepping thread spent, by phase */
+    double t_start;                 /* prologues of newly admitted requests */
+    double t_plan;                  /* rebuilding the batched step after arrivals / retirements */
+    double t_step;                  /* batched outer iterations (launch, device time, stop test) */
+    double t_retire;                /* epilogues and result copies of finished requests */
+    long long plan_rebuilds;        /* times the batched step was rebuilt */
 } mg_serve_stats_t;
 mg_status mg_serve_default_opts(mg_serve_opts* opts);
 /* Start a server (threads and a stream on `device`).  Free with mg_serve_destroy. */

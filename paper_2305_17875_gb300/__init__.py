@@ -66,7 +66,9 @@ class mg_serve_opts(C.Structure):
 class mg_serve_stats_t(C.Structure):
     _fields_ = [("queued", C.c_longlong), ("active", C.c_longlong), ("steps", C.c_longlong),
                 ("retired", C.c_longlong), ("cache_hits", C.c_longlong),
-                ("cached_hierarchies", C.c_longlong), ("bytes_reserved", C.c_size_t)]
+                ("cached_hierarchies", C.c_longlong), ("bytes_reserved", C.c_size_t),
+                ("t_start", C.c_double), ("t_plan", C.c_double), ("t_step", C.c_double),
+                ("t_retire", C.c_double), ("plan_rebuilds", C.c_longlong)]
 
 
 class mg_level_info(C.Structure):

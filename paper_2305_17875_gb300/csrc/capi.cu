@@ -36,6 +36,29 @@ LevelView Level::view(int stencil) const {
     return v;
 }
 
+cudaMemPool_t lib_pool(int device) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64) device = 0;
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            cudaDeviceGetDefaultMemPool(&p, device);
+        } else {
+            unsigned long long keep = ~0ull;   // keep freed blocks for the next hierarchy
+            cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pools[device] = p;
+    }
+    return pools[device];
+}
+
 }  // namespace mgs
 
 #define CK(call)                                                                           \
@@ -103,7 +126,7 @@ int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
 
 void* dalloc(mg_handle* h, size_t bytes) {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, lib_pool(h->device), h->stream) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -117,8 +140,8 @@ void* dalloc(mg_handle* h, size_t bytes) {
 struct TmpDev {
     void* p = nullptr;
     cudaStream_t s;
-    TmpDev(size_t bytes, cudaStream_t st) : s(st) {
-        if (cudaMallocAsync(&p, bytes ? bytes : 16, s) != cudaSuccess) {
+    TmpDev(size_t bytes, cudaStream_t st, int device) : s(st) {
+        if (cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, lib_pool(device), s) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
         }
@@ -158,8 +181,7 @@ mg_status device_sum(mg_handle* h, const double* a, const double* w, i64 n, int 
 // inverse of the bordered matrix [A 1; 1^T 0].
 void free_handle(mg_handle* h) {
     if (!h) return;
-    for (void* p : h->dev_allocs) cudaFree(p);
-    if (h->hscal) cudaFreeHost(h->hscal);
+    for (void* p : h->dev_allocs) cudaFreeAsync(p, h->stream);
     if (h->hf) cudaFreeHost(h->hf);
     if (h->hx) cudaFreeHost(h->hx);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -268,7 +290,6 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     CK(cudaEventRecord(h->ev_in, h->user_stream));
     CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
     stream = h->stream;
-    CK(cudaMallocHost((void**)&h->hscal, sizeof(double) * SC_COUNT));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
 
@@ -407,8 +428,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     if (!(h->binv = (double*)dalloc(h, sizeof(double) * nc * nc))) return MG_ENOMEM;
     {
         const size_t m = (size_t)nc + 1;
-        TmpDev tA(sizeof(double) * nc * nc, stream);
-        TmpDev tw(sizeof(double) * (m * m + m) + sizeof(int) * (2 * m + 1), stream);
+        TmpDev tA(sizeof(double) * nc * nc, stream, h->device);
+        TmpDev tw(sizeof(double) * (m * m + m) + sizeof(int) * (2 * m + 1), stream, h->device);
         if (!tA.p || !tw.p) return MG_ENOMEM;
         double* dA = (double*)tA.p;
         double* work = (double*)tw.p;
@@ -465,6 +486,26 @@ bool has_prec(const mg_handle* h, int prec) {
 }
 
 }  // namespace
+
+namespace mgs {
+
+void destroy_handle_after(mg_handle* h, cudaStream_t last) {
+    if (!h) return;
+    if (last && last != h->stream) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(e, last);
+            cudaStreamWaitEvent(h->stream, e, 0);
+            cudaEventDestroy(e);
+        } else {
+            cudaGetLastError();
+            cudaStreamSynchronize(last);
+        }
+    }
+    free_handle(h);
+}
+
+}  // namespace mgs
 
 namespace mgs {
 
@@ -725,7 +766,10 @@ mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_han
 
 void mg_destroy(mg_handle* h) {
     if (!h) return;
-    cudaStreamSynchronize(h->stream);
+    // the handle's buffers may have been used on other streams (batches, the
+    // caller's stream): wait for the device, then free
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
     free_handle(h);
 }
 

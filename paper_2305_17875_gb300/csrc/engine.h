@@ -29,6 +29,11 @@ struct Level {
 
 void set_error(const std::string& m);
 
+// The library's device memory pool (one per device, stream-ordered, freed
+// blocks kept for reuse): hierarchies and request buffers come from it, so
+// building and dropping hierarchies does not synchronise the device.
+cudaMemPool_t lib_pool(int device);
+
 }  // namespace mgs
 
 struct mg_handle {
@@ -47,7 +52,7 @@ struct mg_handle {
     double* b64 = nullptr;            // volume-integrated right side (fine)
     double* part = nullptr;           // reduction partials (kRedBlocks)
     double* scal = nullptr;           // device scalars
-    double* hscal = nullptr;          // pinned host mirror of scal
+    double hscal[mgs::SC_COUNT] = {}; // host copy of scal (set-up reductions)
     double* binv = nullptr;           // coarsest bordered inverse block (n x n)
     int ncoarse = 0;
     double sumJ = 0.0;
@@ -103,10 +108,16 @@ struct SolveState {             // one shell's outer-iteration bookkeeping
 };
 // A plan launches on its lead handle's private stream, or on ``stream`` for
 // its whole life when one is given (callers whose handles come and go).
-mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stream = nullptr);
-mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n);
+// ``iteration`` = false skips the outer-iteration program (plans used only
+// for prologues / epilogues).
+mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stream = nullptr, bool iteration = true);
+mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n, bool iteration = true);
 void plan_destroy(Plan* pl);
 mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps);
+
+// Free a handle whose last device work was queued on `last` (or on its own
+// stream when null) without waiting for it: the frees are stream-ordered.
+void destroy_handle_after(mg_handle* h, cudaStream_t last);
 mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const double* tol, SolveState* S);
 int plan_check(Plan* pl, SolveState* S);
 mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph);

@@ -13,6 +13,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <list>
@@ -41,7 +42,6 @@ struct Request {
     mg_opts opts{};
     double tol = 0.0;
     std::vector<double> f;          // RHS (host copy taken at submit)
-    std::vector<double> x;          // result (host)
     mg_report rep{};
     mg_status status = MG_OK;
     int state = RQ_QUEUED;
@@ -50,6 +50,8 @@ struct Request {
     double* d_f = nullptr;
     double* d_x = nullptr;
     size_t bytes = 0;               // reserved footprint
+    size_t x_bytes = 0;             // the part of it held by d_x until the poll
+    cudaEvent_t ready = nullptr;    // recorded after the epilogue wrote d_x
     SolveState S;
     std::string key;
 };
@@ -69,7 +71,8 @@ struct mg_server {
     mg_serve_opts o{};
     int device = 0;
     cudaStream_t stream = nullptr;  // every batched step, prologue and epilogue runs here
-    std::mutex mu;
+    cudaStream_t io = nullptr;      // result copies of mg_serve_poll
+    std::mutex mu, io_mu;
     std::condition_variable cv_setup, cv_step, cv_done;
     std::deque<Request*> pending;
     std::vector<Request*> ready;
@@ -82,7 +85,8 @@ struct mg_server {
     std::list<std::pair<std::string, mg_handle*>> cache;
     size_t cache_used = 0;
     // statistics
-    long long steps = 0, retired = 0, cache_hits = 0;
+    long long steps = 0, retired = 0, cache_hits = 0, plan_rebuilds = 0;
+    double t_start = 0, t_plan = 0, t_step = 0, t_retire = 0;
     std::vector<std::thread> workers;
     std::thread stepper;
     mg_status fault = MG_OK;        // a CUDA error stops the server
@@ -123,7 +127,7 @@ void release_handle(mg_server* sv, Request* r) {
         }
     }
     r->h = nullptr;
-    for (mg_handle* h : evict) mg_destroy(h);
+    for (mg_handle* h : evict) destroy_handle_after(h, sv->stream);   // last used on the server stream
 }
 
 void worker_loop(mg_server* sv) {
@@ -152,8 +156,9 @@ void worker_loop(mg_server* sv) {
         cudaStream_t hs = nullptr;
         if (st == MG_OK) {
             hs = r->h->stream;
-            if (cudaMallocAsync((void**)&r->d_f, sizeof(double) * n, hs) != cudaSuccess ||
-                cudaMallocAsync((void**)&r->d_x, sizeof(double) * n, hs) != cudaSuccess) {
+            cudaMemPool_t pool = lib_pool(sv->device);
+            if (cudaMallocFromPoolAsync((void**)&r->d_f, sizeof(double) * n, pool, hs) != cudaSuccess ||
+                cudaMallocFromPoolAsync((void**)&r->d_x, sizeof(double) * n, pool, hs) != cudaSuccess) {
                 cudaGetLastError();
                 st = MG_ENOMEM;
             }
@@ -163,6 +168,15 @@ void worker_loop(mg_server* sv) {
              cudaMemsetAsync(r->d_x, 0, sizeof(double) * n, hs) != cudaSuccess ||
              cudaStreamSynchronize(hs) != cudaSuccess)) {
             st = MG_ECUDA;
+        }
+        if (st != MG_OK) {   // give back what was taken, then report the failure
+            if (hs) {
+                if (r->d_f) cudaFreeAsync(r->d_f, hs);
+                if (r->d_x) cudaFreeAsync(r->d_x, hs);
+                cudaStreamSynchronize(hs);
+            }
+            r->d_f = r->d_x = nullptr;
+            if (r->h) release_handle(sv, r);
         }
         std::lock_guard<std::mutex> lk(sv->mu);
         if (st != MG_OK) {
@@ -185,6 +199,11 @@ void worker_loop(mg_server* sv) {
     }
 }
 
+// Finished requests: their epilogues (gauge, copy into the request's x) are
+// queued on the server stream behind an event, and the requests are marked
+// done at once; the poll that collects a result waits for its event and
+// copies x out.  Slots, hierarchies and the right side are released here;
+// the 8 bytes per cell of x stay reserved until the poll.
 void retire(mg_server* sv, const std::vector<Request*>& done, Plan** finish_plan) {
     if (done.empty()) return;
     std::vector<mg_handle*> hs;
@@ -193,36 +212,30 @@ void retire(mg_server* sv, const std::vector<Request*>& done, Plan** finish_plan
         hs.push_back(r->h);
         xs.push_back(r->d_x);
     }
-    mg_status st = *finish_plan ? plan_reset(*finish_plan, hs.data(), (int)hs.size())
-                                : plan_create(hs.data(), (int)hs.size(), finish_plan, sv->stream);
+    mg_status st = *finish_plan ? plan_reset(*finish_plan, hs.data(), (int)hs.size(), false)
+                                : plan_create(hs.data(), (int)hs.size(), finish_plan, sv->stream, false);
     if (st == MG_OK) st = plan_finish(*finish_plan, xs.data());
-    for (Request* r : done) {
-        const size_t n = r->f.size();
-        r->x.resize(n);
-        if (st == MG_OK && cudaMemcpyAsync(r->x.data(), r->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                                           sv->stream) != cudaSuccess)
-            st = MG_ECUDA;
-    }
-    if (cudaStreamSynchronize(sv->stream) != cudaSuccess && st == MG_OK) st = MG_ECUDA;
     const double t = now_s();
     for (Request* r : done) {
         SolveState& q = r->S;
         q.R.iters = q.it;
         q.R.seconds = t - r->t_submit;   // latency, submit to result
         q.R.model_bytes = model_bytes_per_iteration(r->h) * q.it;
+        if (st == MG_OK && (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventRecord(r->ready, sv->stream) != cudaSuccess))
+            st = MG_ECUDA;
         q.R.status = st != MG_OK ? st : q.st;
         r->rep = q.R;
         r->status = (mg_status)q.R.status;
         cudaFreeAsync(r->d_f, sv->stream);
-        cudaFreeAsync(r->d_x, sv->stream);
-        r->d_f = r->d_x = nullptr;
+        r->d_f = nullptr;
         release_handle(sv, r);
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     for (Request* r : done) {
         r->state = RQ_DONE;
         sv->slots_in_use -= 1;
-        sv->bytes_reserved -= r->bytes;
+        sv->bytes_reserved -= r->bytes - r->x_bytes;
         sv->retired += 1;
     }
     sv->cv_done.notify_all();
@@ -237,6 +250,8 @@ void stepper_loop(mg_server* sv) {
     std::vector<Request*> active;
     bool changed = true;
     int steps_since_reset = 0;
+    int graph_after = 2;   // steps of an unchanged batch before it is captured as a graph
+    if (const char* v = std::getenv("MG_SERVE_GRAPH_AFTER")) graph_after = std::atoi(v);
     auto fail = [&](mg_status st) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->fault = st;
@@ -252,6 +267,7 @@ void stepper_loop(mg_server* sv) {
             if (sv->stop) break;
             fresh.swap(sv->ready);
         }
+        double t0 = now_s();
         if (!fresh.empty()) {   // prologue for the newcomers, then they join
             std::vector<mg_handle*> hs;
             std::vector<const double*> fs;
@@ -264,8 +280,8 @@ void stepper_loop(mg_server* sv) {
                 tols.push_back(r->tol);
             }
             std::vector<SolveState> S(fresh.size());
-            mg_status st = start_plan ? plan_reset(start_plan, hs.data(), (int)hs.size())
-                                      : plan_create(hs.data(), (int)hs.size(), &start_plan, sv->stream);
+            mg_status st = start_plan ? plan_reset(start_plan, hs.data(), (int)hs.size(), false)
+                                      : plan_create(hs.data(), (int)hs.size(), &start_plan, sv->stream, false);
             if (st == MG_OK) st = plan_start(start_plan, fs.data(), xs.data(), tols.data(), S.data());
             if (st != MG_OK) {
                 fail(st);
@@ -278,6 +294,7 @@ void stepper_loop(mg_server* sv) {
             }
             changed = true;
         }
+        double t1 = now_s();
         if (active.empty()) continue;
         if (changed) {
             std::vector<mg_handle*> hs;
@@ -290,7 +307,10 @@ void stepper_loop(mg_server* sv) {
             }
             changed = false;
             steps_since_reset = 0;
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->plan_rebuilds += 1;
         }
+        double t2 = now_s();
         std::vector<SolveState> S(active.size());
         for (size_t i = 0; i < active.size(); ++i) S[i] = active[i]->S;
         const int nact = plan_check(step_plan, S.data());
@@ -300,7 +320,7 @@ void stepper_loop(mg_server* sv) {
             (S[i].done ? done : still).push_back(active[i]);
         }
         if (nact > 0) {
-            const mg_status st = plan_iterate(step_plan, S.data(), steps_since_reset >= 1);
+            const mg_status st = plan_iterate(step_plan, S.data(), steps_since_reset >= graph_after);
             if (st != MG_OK) {
                 fail(st);
                 break;
@@ -311,10 +331,19 @@ void stepper_loop(mg_server* sv) {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->steps += 1;
         }
+        double t3 = now_s();
         if (!done.empty()) {
             retire(sv, done, &finish_plan);
             active.swap(still);
             changed = true;
+        }
+        double t4 = now_s();
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->t_start += t1 - t0;
+            sv->t_plan += t2 - t1;
+            sv->t_step += t3 - t2;
+            sv->t_retire += t4 - t3;
         }
     }
     plan_destroy(start_plan);
@@ -361,7 +390,9 @@ mg_status mg_serve_create(const mg_serve_opts* opts, mg_server** out) {
     if (o.max_bytes == 0) o.max_bytes = (size_t)(0.8 * (double)free_b);
     if (o.cache_bytes == 0) o.cache_bytes = o.max_bytes / 4;
     sv->o = o;
-    if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->io, cudaStreamNonBlocking) != cudaSuccess) {
+        if (sv->stream) cudaStreamDestroy(sv->stream);
         delete sv;
         set_error("serve: stream creation failed");
         return MG_ECUDA;
@@ -391,6 +422,7 @@ mg_status mg_serve_submit(mg_server* sv, const mg_grid_desc* grid, const mg_opts
     const size_t n = (size_t)grid->nr * grid->nth * grid->nph;
     r->f.assign(f_host, f_host + n);
     r->bytes = fp + 2 * sizeof(double) * n;
+    r->x_bytes = sizeof(double) * n;
     r->key = key_of(*grid, o);
     r->t_submit = now_s();
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -408,18 +440,39 @@ mg_status mg_serve_submit(mg_server* sv, const mg_grid_desc* grid, const mg_opts
 
 mg_status mg_serve_poll(mg_server* sv, uint64_t ticket, double* x_host, mg_report* rep) {
     if (!sv) return MG_EINVAL;
-    std::lock_guard<std::mutex> lk(sv->mu);
-    auto it = sv->all.find(ticket);
-    if (it == sv->all.end()) {
-        set_error("serve: unknown ticket");
-        return MG_EINVAL;
+    Request* r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->all.find(ticket);
+        if (it == sv->all.end()) {
+            set_error("serve: unknown ticket");
+            return MG_EINVAL;
+        }
+        r = it->second;
+        if (r->state != RQ_DONE) return sv->fault != MG_OK ? sv->fault : MG_EAGAIN;
+        sv->all.erase(it);
     }
-    Request* r = it->second;
-    if (r->state != RQ_DONE) return sv->fault != MG_OK ? sv->fault : MG_EAGAIN;
-    if (x_host && !r->x.empty()) std::memcpy(x_host, r->x.data(), sizeof(double) * r->x.size());
-    if (rep) *rep = r->rep;
-    const mg_status st = r->status;
-    sv->all.erase(it);
+    mg_status st = r->status;
+    {
+        std::lock_guard<std::mutex> lk(sv->io_mu);
+        if (r->ready && cudaEventSynchronize(r->ready) != cudaSuccess) st = MG_ECUDA;
+        if (r->d_x) {
+            if (x_host && st != MG_ECUDA &&
+                (cudaMemcpyAsync(x_host, r->d_x, r->x_bytes, cudaMemcpyDeviceToHost, sv->io) != cudaSuccess ||
+                 cudaStreamSynchronize(sv->io) != cudaSuccess))
+                st = MG_ECUDA;
+            cudaFreeAsync(r->d_x, sv->io);
+        }
+        if (r->ready) cudaEventDestroy(r->ready);
+    }
+    if (rep) {
+        *rep = r->rep;
+        rep->status = st;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (r->d_x) sv->bytes_reserved -= r->x_bytes;
+    }
     delete r;
     return st;
 }
@@ -434,6 +487,11 @@ mg_status mg_serve_stats(mg_server* sv, mg_serve_stats_t* out) {
     out->cache_hits = sv->cache_hits;
     out->bytes_reserved = sv->bytes_reserved;
     out->cached_hierarchies = (long long)sv->cache.size();
+    out->t_start = sv->t_start;
+    out->t_plan = sv->t_plan;
+    out->t_step = sv->t_step;
+    out->t_retire = sv->t_retire;
+    out->plan_rebuilds = sv->plan_rebuilds;
     return MG_OK;
 }
 
@@ -452,11 +510,13 @@ void mg_serve_destroy(mg_server* sv) {
         Request* r = kv.second;
         if (r->d_f) cudaFree(r->d_f);
         if (r->d_x) cudaFree(r->d_x);
+        if (r->ready) cudaEventDestroy(r->ready);
         if (r->h) mg_destroy(r->h);
         delete r;
     }
     for (auto& kv : sv->cache) mg_destroy(kv.second);
     if (sv->stream) cudaStreamDestroy(sv->stream);
+    if (sv->io) cudaStreamDestroy(sv->io);
     delete sv;
 }
 

@@ -498,14 +498,16 @@ cudaError_t grow(P** ptr, size_t* cap, size_t need, bool pinned) {
 
 // Point a plan at a (new) set of handles: rebuild the iteration tables and
 // upload them into the plan's buffers (grown only when too small).
-mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n) {
+mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n, bool iteration) {
     if (n <= 0) return MG_EINVAL;
     for (int s = 0; s < n; ++s)
         if (!hs[s] || hs[s]->prec != hs[0]->prec || hs[s]->device != hs[0]->device) {
             set_error("batch handles must share device and precision");
             return MG_EINVAL;
         }
-    if (pl->stream) CK(cudaStreamSynchronize(pl->stream));
+    // a plan pinned to one stream is only ever used in that stream's order;
+    // otherwise wait until the previous handles' work is done
+    if (pl->stream && !pl->fixed) CK(cudaStreamSynchronize(pl->stream));
     pl->hs.assign(hs, hs + n);
     pl->prec = hs[0]->prec;
     pl->stream = pl->fixed ? pl->fixed : hs[0]->stream;
@@ -518,6 +520,7 @@ mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n) {
     CK(grow(&pl->d_fin, &pl->dfin_cap, (size_t)4 * n, false));
     CK(grow(&pl->h_fin, &pl->hfin_cap, (size_t)4 * n, true));
     pl->iter = Program();
+    if (!iteration) return MG_OK;
     build_iteration(pl);
     std::stable_sort(pl->iter.tails.begin(), pl->iter.tails.end(),
                      [](const TailTask& a, const TailTask& b) { return a.lev[0].v.stencil < b.lev[0].v.stencil; });
@@ -530,16 +533,16 @@ mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n) {
         CK(cudaMemcpyAsync(pl->d_tails, pl->iter.tails.data(), sizeof(TailTask) * pl->iter.tails.size(),
                            cudaMemcpyHostToDevice, pl->stream));
     }
-    CK(cudaStreamSynchronize(pl->stream));
+    if (!pl->fixed) CK(cudaStreamSynchronize(pl->stream));
     return MG_OK;
 }
 
-mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stream) {
+mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stream, bool iteration) {
     *out = nullptr;
     if (n <= 0) return MG_EINVAL;
     Plan* pl = new Plan();
     pl->fixed = stream;
-    const mg_status st = plan_reset(pl, hs, n);
+    const mg_status st = plan_reset(pl, hs, n, iteration);
     if (st != MG_OK) {
         plan_destroy(pl);
         return st;
