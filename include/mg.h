@@ -84,6 +84,11 @@ typedef struct {
     int coarse_max;     /* stop coarsening at <= this many cells, default 512 */
     int max_iters;      /* outer iterations (V-cycles), default 100 */
     int stencil;        /* 0 auto (7 for the sphere, 19 otherwise), 7 or 19 */
+    int autotune;       /* 1 (default): at set-up, time a few launch schedules of one outer
+                           iteration (blocks per SM of the level kernels, the single-launch
+                           coarse tail, one-pass red-black tiles) once per hierarchy shape in
+                           the process and keep the fastest; every schedule gives the same
+                           bits.  0: the default schedule. */
 } mg_opts;
 
 #define MG_HIST 64
@@ -251,6 +256,21 @@ mg_status mg_serve_stats(mg_server* sv, mg_serve_stats_t* out);
 /* Stop the threads, wait for the device, free everything; unfinished
  * requests are dropped. */
 void mg_serve_destroy(mg_server* sv);
+
+/* The launch schedule a handle runs (see mg_opts.autotune).  No counterpart in
+ * the paper: it changes speed, never results. */
+typedef struct {
+    int blocks_per_sm;      /* cap of the level kernels' virtual grids, in blocks of 256 per SM */
+    int tail_level;         /* first level of the single-launch coarse tail, 0 = none */
+    int tail_cluster;       /* CTAs per tail cluster */
+    int one_pass_tiles;     /* 1: 7-point red-black sweeps as one-pass tiles where they fit */
+    int source;             /* 0 default, 1 tuned at this set-up, 2 from the process cache,
+                               3 forced by MG_TAIL / MG_FUSED_RB in the environment */
+    int candidates;         /* schedules timed (source 1) */
+    double ms_per_iteration;/* device time of one outer iteration under the chosen schedule
+                               (source 1 and 2; 0 otherwise) */
+} mg_schedule;
+mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out);
 
 /* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with

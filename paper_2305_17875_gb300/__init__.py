@@ -40,7 +40,13 @@ class mg_grid_desc(C.Structure):
 class mg_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_levels", C.c_int), ("coarsen", C.c_int), ("coarse_max", C.c_int),
-                ("max_iters", C.c_int), ("stencil", C.c_int)]
+                ("max_iters", C.c_int), ("stencil", C.c_int), ("autotune", C.c_int)]
+
+
+class mg_schedule(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int), ("tail_level", C.c_int), ("tail_cluster", C.c_int),
+                ("one_pass_tiles", C.c_int), ("source", C.c_int), ("candidates", C.c_int),
+                ("ms_per_iteration", C.c_double)]
 
 
 class mg_report(C.Structure):
@@ -99,6 +105,7 @@ _SIGS = {
     "mg_profile_enable": ([_vp, _i], _i),
     "mg_profile_read": ([_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], _i),
     "mg_project_rhs_noalloc": ([_vp, _vp, _vp, C.c_longlong, _vp, _vp], _i),
+    "mg_get_schedule": ([_vp, C.POINTER(mg_schedule)], _i),
     "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
     "mg_serve_create": ([C.POINTER(mg_serve_opts), C.POINTER(_vp)], _i),
     "mg_serve_submit": ([_vp, C.POINTER(mg_grid_desc), C.POINTER(mg_opts), _vp, _d,
@@ -290,6 +297,12 @@ def mg_coarse_solve(h: Handle, prec: int, r, e):
 
 def mg_vcycle(h: Handle, prec: int, x, b):
     _check(_lib.mg_vcycle(h.ptr, prec, _ptr(x, _vdtype(prec)), _ptr(b, _vdtype(prec))), "mg_vcycle")
+
+
+def mg_get_schedule(h: Handle) -> dict:
+    sc = mg_schedule()
+    _check(_lib.mg_get_schedule(h.ptr, C.byref(sc)), "mg_get_schedule")
+    return {k: getattr(sc, k) for k, _ in mg_schedule._fields_}
 
 
 PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL = range(6)

@@ -9,6 +9,7 @@
 #include <new>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "engine.h"
@@ -82,10 +83,8 @@ constexpr int kMaxCoarse = 2048;   // largest coarsest level (dense bordered inv
 // Semi-coarsening: a direction halves only if its mean diagonal coefficient is
 // at least this fraction of the strongest coarsenable direction's.
 constexpr double kSemiRatio = 0.7;
-// Levels at or below this many cells (never the fine level) can run as one
-// launch: the coarse tail, one cluster of 8 CTAs x 512 threads (opt-in with
-// MG_TAIL=1: on the 128 x 128 x 256 sphere it measured slower than graph-
-// launched per-level kernels, 11.1 vs 9.7 ms per solve).
+// Coarse-tail threshold when MG_TAIL=1 forces the tail without a cell count
+// (MG_TAIL_CELLS); the tuner tries 16384.
 constexpr i64 kTailCells = 65536;
 
 bool finite(double v) { return std::isfinite(v); }
@@ -116,6 +115,7 @@ std::string check_opts(const mg_opts* o) {
     if (o->coarse_max < 1) return "coarse_max must be >= 1";
     if (o->max_iters < 0) return "max_iters must be >= 0";
     if (o->stencil != 0 && o->stencil != 7 && o->stencil != 19) return "stencil must be 0, 7 or 19";
+    if (o->autotune != 0 && o->autotune != 1) return "autotune must be 0 or 1";
     return "";
 }
 
@@ -275,6 +275,130 @@ mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
     return MG_OK;
 }
 
+// Coarse tail over the deepest run of levels of at most `cells` cells, one
+// thread-block cluster of `cluster` CTAs per shell; none when the run is
+// shorter than two levels or clusters cannot be co-resident.
+mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
+    h->tail_level = 0;
+    if (cells <= 0 || h->opts.smoother != MG_SMOOTH_GS) return MG_OK;
+    const int nl = (int)h->L.size();
+    int t = nl;
+    while (t - 1 >= 1 && h->L[t - 1].D.n() <= cells) --t;
+    if (nl - t < 2 || nl - t > kMaxTail || tail_max_clusters(cluster, h->stencil, h->prec) <= 0) return MG_OK;
+    TailTask task{};
+    task.nlev = nl - t;
+    task.nu1 = h->opts.nu1;
+    task.nu2 = h->opts.nu2;
+    task.binv = h->binv;
+    task.ncoarse = h->ncoarse;
+    for (int l = t; l < nl; ++l) task.lev[l - t] = TailLevel{h->L[l].view(h->stencil), h->L[l].e, h->L[l].r};
+    if (!h->tail_dev && !(h->tail_dev = (TailTask*)dalloc(h, sizeof(TailTask)))) return MG_ENOMEM;
+    CK(cudaMemcpyAsync(h->tail_dev, &task, sizeof(TailTask), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->tail_host = task;
+    h->tail_level = t;
+    h->tail_cluster = cluster;
+    return MG_OK;
+}
+
+// ---- schedule tuner.  Candidates: blocks per SM of the level kernels (8, 16,
+// 32), the coarse tail below 16384 cells, one-pass red-black tiles; chosen by
+// coordinate descent on the device time of one outer iteration of this
+// handle, and remembered per hierarchy shape for the rest of the process.
+struct Schedule {
+    int vb_cap = 16;
+    i64 tail_cells = 0;
+    bool fused = false;
+};
+
+std::string shape_key(const mg_handle* h) {
+    std::string k = std::to_string(h->prec) + "/" + std::to_string(h->stencil) + "/" +
+                    std::to_string(h->opts.smoother) + "/" + std::to_string(h->opts.nu1) + "/" +
+                    std::to_string(h->opts.nu2);
+    for (const Level& lv : h->L)
+        k += "|" + std::to_string(lv.D.nr) + "x" + std::to_string(lv.D.nth) + "x" + std::to_string(lv.D.nph);
+    return k;
+}
+
+bool can_fuse(const mg_handle* h) {
+    if (h->stencil != 7 || h->opts.smoother != MG_SMOOTH_GS) return false;
+    for (const Level& lv : h->L)
+        if (rb7_fits(lv.D)) return true;
+    return false;
+}
+
+mg_status apply_schedule(mg_handle* h, const Schedule& sc) {
+    h->vb_cap = sc.vb_cap;
+    h->fused_rb = sc.fused && can_fuse(h);
+    return configure_tail(h, sc.tail_cells, 8);
+}
+
+mg_status time_schedule(mg_handle* h, const Schedule& sc, double* ms) {
+    CKS(apply_schedule(h, sc));
+    Plan* pl = nullptr;
+    CKS(plan_create(&h, 1, &pl));
+    const mg_status st = plan_time(pl, 2, 5, ms);
+    plan_destroy(pl);
+    return st;
+}
+
+mg_status autotune(mg_handle* h) {
+    static std::mutex mu;
+    static std::unordered_map<std::string, std::pair<Schedule, double>> cache;
+    const std::string key = shape_key(h);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            CKS(apply_schedule(h, it->second.first));
+            h->sched_source = 2;
+            h->sched_ms = it->second.second;
+            return MG_OK;
+        }
+    }
+    // finite data for the timing runs (the iterates are discarded)
+    const i64 N = h->L[0].D.n();
+    CK(cudaMemsetAsync(h->x64, 0, sizeof(double) * N, h->stream));
+    CK(cudaMemsetAsync(h->b64, 0, sizeof(double) * N, h->stream));
+    if (h->prec != PREC64) CK(cudaMemsetAsync(h->L[0].r, 0, sizeof(float) * N, h->stream));
+    Schedule best;
+    double best_ms = 0.0;
+    int tried = 1;
+    CKS(time_schedule(h, best, &best_ms));
+    auto consider = [&](const Schedule& sc) -> mg_status {
+        double ms = 0.0;
+        CKS(time_schedule(h, sc, &ms));
+        ++tried;
+        if (ms < 0.98 * best_ms) {   // a clear win only: timings carry noise
+            best = sc;
+            best_ms = ms;
+        }
+        return MG_OK;
+    };
+    for (int cap : {8, 32}) {
+        Schedule sc = best;
+        sc.vb_cap = cap;
+        CKS(consider(sc));
+    }
+    if (h->opts.smoother == MG_SMOOTH_GS) {
+        Schedule sc = best;
+        sc.tail_cells = 16384;
+        CKS(consider(sc));
+    }
+    if (can_fuse(h)) {
+        Schedule sc = best;
+        sc.fused = true;
+        CKS(consider(sc));
+    }
+    CKS(apply_schedule(h, best));
+    h->sched_source = 1;
+    h->sched_candidates = tried;
+    h->sched_ms = best_ms;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {best, best_ms};
+    return MG_OK;
+}
+
 mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t stream, mg_handle* h) {
     h->grid = *g;
     h->opts = *o;
@@ -282,7 +406,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     h->prec = o->precision;
     h->user_stream = stream;
     h->use_graph = std::getenv("MG_NO_GRAPH") == nullptr;
-    h->fused_rb = std::getenv("MG_FUSED_RB") != nullptr;   // one-pass tile sweeps: opt-in
+    h->fused_rb = std::getenv("MG_FUSED_RB") != nullptr;   // one-pass tile sweeps: forced
     CK(cudaGetDevice(&h->device));
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
@@ -449,31 +573,23 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         }
     }
 
-    // --- coarse tail: the deepest run of levels small enough for one cluster
-    const int nl = (int)h->L.size();
-    int t = nl;
-    i64 tail_cells = kTailCells;
-    if (const char* v = std::getenv("MG_TAIL_CELLS")) tail_cells = std::atoll(v);
-    if (const char* v = std::getenv("MG_TAIL_CLUSTER")) h->tail_cluster = std::max(1, std::min(8, std::atoi(v)));
-    while (t - 1 >= 1 && h->L[t - 1].D.n() <= tail_cells) --t;
-    const bool want_tail = std::getenv("MG_TAIL") != nullptr && o->smoother == MG_SMOOTH_GS &&
-                           nl - t >= 2 && nl - t <= kMaxTail &&
-                           tail_max_clusters(h->tail_cluster, h->stencil, h->prec) > 0;
-    if (want_tail) {
-        TailTask task{};
-        task.nlev = nl - t;
-        task.nu1 = o->nu1;
-        task.nu2 = o->nu2;
-        task.binv = h->binv;
-        task.ncoarse = nc;
-        for (int l = t; l < nl; ++l) task.lev[l - t] = TailLevel{h->L[l].view(h->stencil), h->L[l].e, h->L[l].r};
-        if (!(h->tail_dev = (TailTask*)dalloc(h, sizeof(TailTask)))) return MG_ENOMEM;
-        CK(cudaMemcpyAsync(h->tail_dev, &task, sizeof(TailTask), cudaMemcpyHostToDevice, stream));
-        h->tail_host = task;
-        h->tail_level = t;
-    }
     CK(cudaStreamSynchronize(stream));
     CK(cudaGetLastError());
+
+    // --- launch schedule: forced by the environment, tuned, or the default
+    const bool env_sched = std::getenv("MG_TAIL") || std::getenv("MG_FUSED_RB");
+    if (env_sched) {
+        h->sched_source = 3;
+        if (std::getenv("MG_TAIL")) {
+            i64 cells = kTailCells;
+            int cluster = 8;
+            if (const char* v = std::getenv("MG_TAIL_CELLS")) cells = std::atoll(v);
+            if (const char* v = std::getenv("MG_TAIL_CLUSTER")) cluster = std::max(1, std::min(8, std::atoi(v)));
+            CKS(configure_tail(h, cells, cluster));
+        }
+    } else if (o->autotune) {
+        CKS(autotune(h));
+    }
     return MG_OK;
 }
 
@@ -706,6 +822,19 @@ mg_status mg_default_opts(mg_opts* o) {
     o->coarse_max = 512;
     o->max_iters = 100;
     o->stencil = 0;
+    o->autotune = 1;
+    return MG_OK;
+}
+
+mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out) {
+    if (!h || !out) return MG_EINVAL;
+    out->blocks_per_sm = h->vb_cap;
+    out->tail_level = h->tail_level;
+    out->tail_cluster = h->tail_cluster;
+    out->one_pass_tiles = h->fused_rb ? 1 : 0;
+    out->source = h->sched_source;
+    out->candidates = h->sched_candidates;
+    out->ms_per_iteration = h->sched_ms;
     return MG_OK;
 }
 

@@ -73,7 +73,11 @@ struct mg_handle {
     std::vector<cudaEvent_t> prof_pool;
     // outer iterations run as captured graphs (solver.cu)
     bool use_graph = true;
-    bool fused_rb = false;            // one-pass red-black tile sweeps (opt-in, MG_FUSED_RB=1)
+    bool fused_rb = false;            // one-pass red-black tile sweeps (schedule choice)
+    int vb_cap = 16;                  // blocks per SM of the level kernels' virtual grids
+    int sched_source = 0;             // mg_schedule.source
+    int sched_candidates = 0;
+    double sched_ms = 0.0;
     mgs::BTask* one_task = nullptr;   // task table of stand-alone one-pass sweeps
     int tail_level = 0;               // first level of the single-launch coarse tail (0: none)
     int tail_cluster = 8;             // CTAs per tail cluster
@@ -121,6 +125,10 @@ void destroy_handle_after(mg_handle* h, cudaStream_t last);
 mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const double* tol, SolveState* S);
 int plan_check(Plan* pl, SolveState* S);
 mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph);
+// Device time of one outer iteration of every shell of the plan (graph
+// launched, all shells active): `warm` untimed iterations, then the mean of
+// `reps`.  The iterates are not meaningful afterwards.
+mg_status plan_time(Plan* pl, int warm, int reps, double* ms);
 mg_status plan_finish(Plan* pl, double* const* x);
 mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind);
 double model_bytes_per_iteration(const mg_handle* h);

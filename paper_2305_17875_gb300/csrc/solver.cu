@@ -28,11 +28,12 @@ namespace {
         if (s_ != MG_OK) return s_; \
     } while (0)
 
-// Virtual grid of a task: one thread per work item up to 16 blocks per SM,
-// grid-stride beyond.
-int vblocks(i64 work) {
+// Virtual grid of a task: one thread per work item up to the handle's cap of
+// blocks per SM (a schedule choice), grid-stride beyond.
+int vblocks(const mg_handle* h, i64 work) {
     i64 b = (work + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    const i64 cap = 152LL * (h ? h->vb_cap : 16);
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -188,7 +189,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
                 t.shell = (int)s;
-                P.add(t, vblocks(gs_items(h->L[level].D, h->stencil)));
+                P.add(t, vblocks(h, gs_items(h->L[level].D, h->stencil)));
             }
         }
         if (any_jacobi) {
@@ -205,7 +206,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 level_bufs(h, prec, level, &t.x, &t.b);
                 t.y = h->L[level].t;
                 t.shell = (int)s;
-                P.add(t, vblocks(h->L[level].D.n()));
+                P.add(t, vblocks(h, h->L[level].D.n()));
             }
             }
             P.begin(BOP_COPY);
@@ -220,7 +221,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 t.b = h->L[level].t;
                 t.n = h->L[level].D.n() * (i64)(vbytes(prec) / 4);
                 t.shell = (int)s;
-                P.add(t, vblocks(vector_items(t.n)));
+                P.add(t, vblocks(h, vector_items(t.n)));
             }
         }
     }
@@ -237,7 +238,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
             t.b = h->L[level].t;
             t.n = h->L[level].D.n() * (i64)(vbytes(prec) / 4);
             t.shell = (int)s;
-            P.add(t, vblocks(vector_items(t.n)));
+            P.add(t, vblocks(h, vector_items(t.n)));
         }
     }
 }
@@ -290,7 +291,7 @@ void build_iteration(Plan* pl) {
             t.x = h->L[0].e;
             t.n = h->L[0].D.n();
             t.shell = (int)s;
-            P.add(t, vblocks(vector_items(t.n)));
+            P.add(t, vblocks(h, vector_items(t.n)));
         }
     }
     // down leg
@@ -310,7 +311,7 @@ void build_iteration(Plan* pl) {
             t.y = h->L[l + 1].r;
             t.z = h->L[l + 1].e;
             t.shell = (int)s;
-            P.add(t, vblocks(restrict_items(h->L[l].D, h->L[l + 1].D)));
+            P.add(t, vblocks(h, restrict_items(h->L[l].D, h->L[l + 1].D)));
         }
         }
     }
@@ -363,7 +364,7 @@ void build_iteration(Plan* pl) {
             level_bufs(h, prec, l, &t.x, &t.b);
             t.b = h->L[l + 1].e;
             t.shell = (int)s;
-            P.add(t, vblocks(prolong_items(h->L[l].D)));
+            P.add(t, vblocks(h, prolong_items(h->L[l].D)));
         }
         add_smooth(P, pl, l, pl->hs[0]->opts.nu2);
     }
@@ -379,7 +380,7 @@ void build_iteration(Plan* pl) {
             t.scal = h->scal;
             t.n = h->L[0].D.n();
             t.shell = (int)s;
-            P.add(t, vblocks(vector_items(t.n)));
+            P.add(t, vblocks(h, vector_items(t.n)));
         }
     }
     add_residual(P, pl);
@@ -563,7 +564,7 @@ mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const d
         t.b = x[i];
         t.n = 2 * pl->hs[i]->L[0].D.n();
         t.shell = i;
-        pro.add(t, vblocks(vector_items(t.n)));
+        pro.add(t, vblocks(pl->hs[i], vector_items(t.n)));
     }
     pro.begin(BOP_SUM);
     for (int i = 0; i < n; ++i) {
@@ -709,6 +710,25 @@ mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph) {
     return MG_OK;
 }
 
+mg_status plan_time(Plan* pl, int warm, int reps, double* ms) {
+    const int n = (int)pl->hs.size();
+    std::vector<SolveState> S(n);
+    for (int i = 0; i < n; ++i) pl->h_active[i] = 1;
+    mg_handle* h0 = lead(pl);
+    for (int r = 0; r < warm; ++r) CKS(plan_iterate(pl, S.data(), true));
+    CK(cudaEventRecord(h0->ev0, pl->stream));
+    for (int r = 0; r < reps; ++r) {
+        for (int i = 0; i < n; ++i) pl->h_active[i] = 1;
+        CKS(plan_iterate(pl, S.data(), true));
+    }
+    CK(cudaEventRecord(h0->ev1, pl->stream));
+    CK(cudaEventSynchronize(h0->ev1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h0->ev0, h0->ev1));
+    *ms = (double)t / (reps > 0 ? reps : 1);
+    return MG_OK;
+}
+
 // Epilogue for every shell of the plan: remove the J-weighted mean, x out.
 mg_status plan_finish(Plan* pl, double* const* x) {
     const int n = (int)pl->hs.size();
@@ -745,7 +765,7 @@ mg_status plan_finish(Plan* pl, double* const* x) {
         t.aux = h->sumJ;
         t.n = h->L[0].D.n();
         t.shell = i;
-        epi.add(t, vblocks(t.n));
+        epi.add(t, vblocks(pl->hs[i], t.n));
     }
     epi.begin(BOP_COPY);
     for (int i = 0; i < n; ++i) {
@@ -754,7 +774,7 @@ mg_status plan_finish(Plan* pl, double* const* x) {
         t.b = pl->hs[i]->x64;
         t.n = 2 * pl->hs[i]->L[0].D.n();
         t.shell = i;
-        epi.add(t, vblocks(vector_items(t.n)));
+        epi.add(t, vblocks(pl->hs[i], vector_items(t.n)));
     }
     CKS(upload_call(pl, epi));
     CKS(run_program(pl, epi, pl->d_call, nullptr));

@@ -276,14 +276,25 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
     w = W.single(wl, scale)
     fd = to_dev(w["f"], torch.float64)
     out = {}
-    for name, env in [("default", {}), ("tail", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192"}),
-                      ("tail_big", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4"}),
-                      ("fused", {"MG_FUSED_RB": "1"}), ("no_graph", {"MG_NO_GRAPH": "1"})]:
+    for name, env, tune in [("default", {}, 0), ("tuned", {}, 1), ("tuned_again", {}, 1),
+                            ("tail", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192"}, 1),
+                            ("tail_big", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4"}, 1),
+                            ("fused", {"MG_FUSED_RB": "1"}, 1), ("no_graph", {"MG_NO_GRAPH": "1"}, 0)]:
         for k in ("MG_TAIL", "MG_TAIL_CELLS", "MG_TAIL_CLUSTER", "MG_FUSED_RB", "MG_NO_GRAPH"):
             monkeypatch.delenv(k, raising=False)
         for k, v in env.items():
             monkeypatch.setenv(k, v)
-        h = lib.mg_setup(w["grid"], dict(precision=prec))
+        h = lib.mg_setup(w["grid"], dict(precision=prec, autotune=tune))
+        sc = lib.mg_get_schedule(h)
+        if env.get("MG_TAIL") or env.get("MG_FUSED_RB"):
+            assert sc["source"] == 3
+        elif tune:
+            assert sc["source"] in (1, 2) and sc["ms_per_iteration"] > 0
+            assert sc["blocks_per_sm"] in (8, 16, 32)
+        else:
+            assert sc["source"] == 0 and sc["blocks_per_sm"] == 16 and sc["tail_level"] == 0
+        if name == "tuned_again":
+            assert sc["source"] == 2           # same hierarchy shape: from the process cache
         xd = torch.zeros_like(fd)
         rep = lib.mg_solve(h, fd, xd, tol=1e-10)
         out[name] = (to_np(xd), rep["iters"])
