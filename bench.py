@@ -304,8 +304,13 @@ def run_ours(args, rank, world, local_rank):
     g, f = w["grid"], w["f"]
     N = g["nr"] * g["nth"] * g["nph"]
     prec = PREC[args.precision]
+    sopts = dict(precision=prec)
+    if "max_levels" in w:
+        sopts["max_levels"] = w["max_levels"]
+    if w.get("coarsen") == "full":
+        sopts["coarsen"] = 1
     t_setup = time.perf_counter()
-    h = mgs.mg_setup(g, dict(precision=prec))
+    h = mgs.mg_setup(g, sopts)
     t_setup = time.perf_counter() - t_setup
     fd = torch.from_numpy(f).cuda()
     xd = torch.zeros_like(fd)
@@ -377,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
     # plain FP64 multigrid on the same workload (the speedup reference)
     compare = None
     if not args.no_compare and prec != 0:
-        h64 = mgs.mg_setup(g, dict(precision=0))
+        h64 = mgs.mg_setup(g, dict(sopts, precision=0))
         for _ in range(1):
             xd.zero_()
             mgs.mg_solve(h64, fd, xd, tol=TOL)

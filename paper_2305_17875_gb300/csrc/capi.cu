@@ -860,6 +860,7 @@ size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
 mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_handle** out) {
     if (!out) return MG_EINVAL;
     *out = nullptr;
+    cudaGetLastError();   // an earlier failed call of this thread is not set-up's to report
     mg_opts d;
     if (!o) {
         mg_default_opts(&d);
