@@ -54,6 +54,7 @@ struct Request {
     cudaEvent_t ready = nullptr;    // recorded after the epilogue wrote d_x
     SolveState S;
     std::string key;
+    std::string err;                // why the request failed (mg_last_error of its poll)
 };
 
 std::string key_of(const mg_grid_desc& g, const mg_opts& o) {
@@ -90,6 +91,7 @@ struct mg_server {
     std::vector<std::thread> workers;
     std::thread stepper;
     mg_status fault = MG_OK;        // a CUDA error stops the server
+    std::string fault_msg;
 };
 
 namespace {
@@ -170,6 +172,8 @@ void worker_loop(mg_server* sv) {
             st = MG_ECUDA;
         }
         if (st != MG_OK) {   // give back what was taken, then report the failure
+            r->err = std::string("set-up: ") + mg_last_error();
+            if (st == MG_ECUDA) r->err += std::string(" / ") + cudaGetErrorString(cudaGetLastError());
             if (hs) {
                 if (r->d_f) cudaFreeAsync(r->d_f, hs);
                 if (r->d_x) cudaFreeAsync(r->d_x, hs);
@@ -222,8 +226,12 @@ void retire(mg_server* sv, const std::vector<Request*>& done, Plan** finish_plan
         q.R.seconds = t - r->t_submit;   // latency, submit to result
         q.R.model_bytes = model_bytes_per_iteration(r->h) * q.it;
         if (st == MG_OK && (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
-                            cudaEventRecord(r->ready, sv->stream) != cudaSuccess))
+                            cudaEventRecord(r->ready, sv->stream) != cudaSuccess)) {
             st = MG_ECUDA;
+            r->err = std::string("epilogue event: ") + cudaGetErrorString(cudaGetLastError());
+        } else if (st != MG_OK && r->err.empty()) {
+            r->err = std::string("epilogue: ") + mg_last_error();
+        }
         q.R.status = st != MG_OK ? st : q.st;
         r->rep = q.R;
         r->status = (mg_status)q.R.status;
@@ -253,8 +261,10 @@ void stepper_loop(mg_server* sv) {
     int graph_after = 2;   // steps of an unchanged batch before it is captured as a graph
     if (const char* v = std::getenv("MG_SERVE_GRAPH_AFTER")) graph_after = std::atoi(v);
     auto fail = [&](mg_status st) {
+        const std::string why = mg_last_error();
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->fault = st;
+        sv->fault_msg = why;
         sv->stop = true;
         sv->cv_setup.notify_all();
         sv->cv_done.notify_all();
@@ -449,13 +459,22 @@ mg_status mg_serve_poll(mg_server* sv, uint64_t ticket, double* x_host, mg_repor
             return MG_EINVAL;
         }
         r = it->second;
-        if (r->state != RQ_DONE) return sv->fault != MG_OK ? sv->fault : MG_EAGAIN;
+        if (r->state != RQ_DONE) {
+            if (sv->fault != MG_OK) set_error("serve: stopped: " + sv->fault_msg);
+            return sv->fault != MG_OK ? sv->fault : MG_EAGAIN;
+        }
         sv->all.erase(it);
     }
     mg_status st = r->status;
     {
         std::lock_guard<std::mutex> lk(sv->io_mu);
-        if (r->ready && cudaEventSynchronize(r->ready) != cudaSuccess) st = MG_ECUDA;
+        if (r->ready) {
+            const cudaError_t e = cudaEventSynchronize(r->ready);
+            if (e != cudaSuccess) {
+                st = MG_ECUDA;
+                r->err = std::string("result event: ") + cudaGetErrorString(e);
+            }
+        }
         if (r->d_x) {
             if (x_host && st != MG_ECUDA &&
                 (cudaMemcpyAsync(x_host, r->d_x, r->x_bytes, cudaMemcpyDeviceToHost, sv->io) != cudaSuccess ||
@@ -469,6 +488,7 @@ mg_status mg_serve_poll(mg_server* sv, uint64_t ticket, double* x_host, mg_repor
         *rep = r->rep;
         rep->status = st;
     }
+    if (st != MG_OK && st != MG_ENOCONV) set_error("serve: " + r->err);
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (r->d_x) sv->bytes_reserved -= r->x_bytes;
