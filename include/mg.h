@@ -244,7 +244,10 @@ mg_status mg_serve_default_opts(mg_serve_opts* opts);
 mg_status mg_serve_create(const mg_serve_opts* opts, mg_server** out);
 /* Queue one solve: grid and options as in mg_setup (opts may be NULL), f_host
  * the pointwise right side (nr*nth*nph doubles, copied before the call
- * returns), tolerance as in mg_solve.  *ticket identifies the request. */
+ * returns), tolerance as in mg_solve.  *ticket identifies the request.  The
+ * server builds hierarchies with the default launch schedule (opts->autotune
+ * is not honoured: schedule timings taken while other requests run would
+ * measure the load); results are the same bits either way. */
 mg_status mg_serve_submit(mg_server* sv, const mg_grid_desc* grid, const mg_opts* opts, const double* f_host,
                           double tol, uint64_t* ticket);
 /* MG_EAGAIN while the request is queued or iterating; otherwise its final
