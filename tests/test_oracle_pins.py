@@ -372,3 +372,115 @@ def test_two_cell_longitude_ring_is_rejected():
     with pytest.raises(ValueError):
         grid.Shell(8, 8, 6 + 1)
     assert grid.Shell(8, 8, 4).n == 256
+
+
+# ------------------------------------------------------------------ Section 3.6 steps (Eqs. PC_6, PC_7)
+from oracle import pc  # noqa: E402
+import workloads as W  # noqa: E402
+
+PC_GRIDS = {
+    "sphere_stretched": (W.grid_desc(8, 8, 16, stretch=1.0), 7),
+    "oblate": (W.grid_desc(6, 8, 12, r_out=1 / 0.6, mapping=1, flattening=0.1), 19),
+    "triaxial": (W.grid_desc(8, 10, 16, mapping=2, flattening=0.1, e2=0.05, stretch=1.5), 19),
+}
+
+
+def _face_centres(sh, d):
+    fj, fi, fk = np.meshgrid(*[np.arange(s) for s in pc.face_shapes(sh)[d]], indexing="ij")
+    e = np.eye(3, dtype=int)
+    t = [a for a in range(3) if a != d]
+    acc = 0.0
+    for a in (0, 1):
+        for b in (0, 1):
+            o = a * e[t[0]] + b * e[t[1]]
+            acc = acc + grid.vertex(sh, fi + o[0], fj + o[1], fk + o[2])
+    return acc / 4.0
+
+
+@pytest.mark.parametrize("name", list(PC_GRIDS))
+def test_uniform_flow_is_discretely_divergence_free(name):
+    """Geometric conservation: the face C of Section 3.2 balance exactly, so a
+    uniform Cartesian velocity has zero flux balance in every interior cell."""
+    g, _ = PC_GRIDS[name]
+    sh = grid.shell(g)
+    fm = grid.face_metrics(sh, with_C=True)
+    u = [np.broadcast_to(np.array([1.0, 0.5, -0.3]), s + (3,)).copy() for s in pc.face_shapes(sh)]
+    D = pc.divergence(sh, fm, u)[1:-1, 1:-1, :]
+    scale = max(np.abs(pc.contravariant_flux(sh, fm, u, d)).max() for d in range(3))
+    assert np.abs(D).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("name", ["sphere_stretched", "oblate"])
+def test_rigid_rotation_is_discretely_divergence_free(name):
+    """Rotation about the polar axis is tangential to every wall of an
+    axisymmetric shell and solenoidal: its discrete divergence vanishes in all
+    cells, walls included."""
+    g, _ = PC_GRIDS[name]
+    sh = grid.shell(g)
+    fm = grid.face_metrics(sh, with_C=True)
+    u = []
+    for d in range(3):
+        X = _face_centres(sh, d)
+        u.append(np.stack([np.zeros(X.shape[:-1]), -X[..., 2], X[..., 1]], axis=-1))
+    scale = max(np.abs(pc.contravariant_flux(sh, fm, u, d)).max() for d in range(3))
+    assert np.abs(pc.divergence(sh, fm, u)).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("name", list(PC_GRIDS))
+def test_correction_removes_exactly_the_operator_flux(name):
+    """D(U) - D(U corrected by x) equals A x for the assembled operator of
+    Eqs. PC_8 / PC_term1-3 (7 or 19 points): the correction's face flux is the
+    operator's face flux."""
+    g, st = PC_GRIDS[name]
+    sh = grid.shell(g)
+    fm = grid.face_metrics(sh, with_C=True)
+    rng = np.random.default_rng(3)
+    u = [rng.standard_normal(s + (3,)) for s in pc.face_shapes(sh)]
+    x = rng.standard_normal(sh.n)
+    Ax = operator.assemble(sh, fm, st) @ x
+    lhs = (pc.divergence(sh, fm, u) - pc.divergence(sh, fm, pc.project(sh, fm, x, u, st))).ravel()
+    np.testing.assert_allclose(lhs, Ax, rtol=0, atol=1e-13 * np.abs(Ax).max())
+
+
+@pytest.mark.parametrize("name", list(PC_GRIDS))
+def test_corrected_velocity_is_divergence_free(name):
+    """The pressure-correction step: f = D(U***)/|J^{-1}|, solve for x = h dP,
+    correct; the new field's divergence is the solver's residual."""
+    g, st = PC_GRIDS[name]
+    sh = grid.shell(g)
+    fm = grid.face_metrics(sh, with_C=True)
+    rng = np.random.default_rng(4)
+    u = [rng.standard_normal(s + (3,)) for s in pc.face_shapes(sh)]
+    hier, fm2 = mg.setup(sh, st)
+    x, info = mg.solve(sh, pc.rhs(sh, fm, u).ravel(), tol=1e-12, hier=hier, fm=fm2, max_iters=400)
+    assert info["converged"]
+    D0 = pc.divergence(sh, fm, u)
+    D1 = pc.divergence(sh, fm, pc.project(sh, fm, x, u, st))
+    assert np.linalg.norm(D1) <= 2e-12 * np.linalg.norm(D0)
+
+
+def test_planted_correction_mistakes_are_caught():
+    """A transposed C, a dropped 1/|J^{-1}| or the cell instead of the face
+    determinant breaks the flux identity; a C column for the flux breaks
+    geometric conservation."""
+    g, st = PC_GRIDS["triaxial"]
+    sh = grid.shell(g)
+    fm = grid.face_metrics(sh, with_C=True)
+    rng = np.random.default_rng(5)
+    u = [rng.standard_normal(s + (3,)) for s in pc.face_shapes(sh)]
+    x = rng.standard_normal(sh.n)
+    Ax = operator.assemble(sh, fm, st) @ x
+
+    def gap(fmx):
+        lhs = (pc.divergence(sh, fm, u) - pc.divergence(sh, fm, pc.project(sh, fmx, x, u, st))).ravel()
+        return np.abs(lhs - Ax).max() / np.abs(Ax).max()
+
+    assert gap(fm) < 1e-13
+    transposed = dict(fm, **{f"C{d}": np.swapaxes(fm[f"C{d}"], -1, -2) for d in range(3)})
+    assert gap(transposed) > 1e-3
+    no_det = dict(fm, **{f"det{d}": np.ones_like(fm[f"det{d}"]) for d in range(3)})
+    assert gap(no_det) > 1e-3
+    uu = [np.broadcast_to(np.array([1.0, 0.5, -0.3]), s + (3,)).copy() for s in pc.face_shapes(sh)]
+    cols = dict(fm, **{f"C{d}": np.swapaxes(fm[f"C{d}"], -1, -2) for d in range(3)})
+    D = pc.divergence(sh, cols, uu)[1:-1, 1:-1, :]
+    assert np.abs(D).max() > 1e-6 * max(np.abs(pc.contravariant_flux(sh, fm, uu, d)).max() for d in range(3))
