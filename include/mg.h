@@ -276,6 +276,34 @@ typedef struct {
 mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out);
 
 /* ---------------------------------------------------------------------------
+ * The steps either side of the solve in the pressure correction (Section 3.6)
+ * for a staggered intermediate velocity.
+ *
+ * u_face: device array of 9 * nr*nth*nph doubles (owned by the caller): the
+ * Cartesian components (x1, x2, x3) of u*** at the centre of every cell's
+ * three LOWER faces, block 3 d + a = component a on the face normal to d
+ * (d in zeta = colatitude, eta = radius, xi = longitude order), each block
+ * [nr][nth][nph] like the face metric.  Wall faces carry no flux: the entries
+ * of the lower wall faces (zeta faces at i = 0, eta faces at j = 0) are not
+ * read and are left unchanged; upper wall faces are not stored.
+ * The face C of Section 3.2 (Eq. skewness) is computed on the first call of
+ * either function on a handle (30 extra arrays of nr*nth*nph doubles, freed
+ * with the handle).  Work is queued on the handle's stream order (the
+ * caller's stream of mg_setup / mg_set_stream); neither call synchronises.
+ * ------------------------------------------------------------------------- */
+/* Right side of Eq. PC_6: f = D(U) / |J^{-1}| per cell, where U_d = sum_a C_da
+ * u_a is the contravariant flux through a d-face and D(U) the cell's flux
+ * balance.  mg_solve(h, f, x) then returns x = h dP of Eq. PC_6.  f: device,
+ * nr*nth*nph doubles. */
+mg_status mg_pc_rhs(mg_handle* h, const double* u_face, double* f);
+/* Correction of Eq. PC_7 on the faces: at every interior face
+ * u_a -= (1/|J^{-1}|_face) sum_p C_pa g_p, with g the gradient of the
+ * operator's face flux (Eqs. PC_term1-3; the face-normal difference only for
+ * the 7-point operator) of x = h dP from mg_solve.  The corrected field's
+ * flux balance equals the solver's residual b - A x. */
+mg_status mg_pc_correct(mg_handle* h, const double* x, double* u_face);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with
  * CUDA events on the handle's stream (a few events per V-cycle) and
  * accumulates their device time.  Slots: 0 = fine-level smoothing launches,

@@ -106,6 +106,8 @@ _SIGS = {
     "mg_profile_read": ([_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], _i),
     "mg_project_rhs_noalloc": ([_vp, _vp, _vp, C.c_longlong, _vp, _vp], _i),
     "mg_get_schedule": ([_vp, C.POINTER(mg_schedule)], _i),
+    "mg_pc_rhs": ([_vp, _vp, _vp], _i),
+    "mg_pc_correct": ([_vp, _vp, _vp], _i),
     "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
     "mg_serve_create": ([C.POINTER(mg_serve_opts), C.POINTER(_vp)], _i),
     "mg_serve_submit": ([_vp, C.POINTER(mg_grid_desc), C.POINTER(mg_opts), _vp, _d,
@@ -297,6 +299,16 @@ def mg_coarse_solve(h: Handle, prec: int, r, e):
 
 def mg_vcycle(h: Handle, prec: int, x, b):
     _check(_lib.mg_vcycle(h.ptr, prec, _ptr(x, _vdtype(prec)), _ptr(b, _vdtype(prec))), "mg_vcycle")
+
+
+def mg_pc_rhs(h: Handle, u_face, f):
+    """Right side of Eq. PC_6 from the staggered velocity u_face (9 * N doubles)."""
+    _check(_lib.mg_pc_rhs(h.ptr, _ptr(u_face, "float64"), _ptr(f, "float64")), "mg_pc_rhs")
+
+
+def mg_pc_correct(h: Handle, x, u_face):
+    """Correction of Eq. PC_7 of u_face (in place) by x = h dP."""
+    _check(_lib.mg_pc_correct(h.ptr, _ptr(x, "float64"), _ptr(u_face, "float64")), "mg_pc_correct")
 
 
 def mg_get_schedule(h: Handle) -> dict:

@@ -451,6 +451,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     CK(up(sph, &T.sph));
     T.ax1 = g->mapping >= MG_MAP_OBLATE ? 1.0 - g->flattening : 1.0;
     T.ax2 = g->mapping == MG_MAP_TRIAXIAL ? 1.0 + g->e2 : 1.0;
+    h->mtab = T;
 
     Level L0;
     L0.D = Dims{nr, nth, nph};
@@ -604,6 +605,8 @@ bool has_prec(const mg_handle* h, int prec) {
 }  // namespace
 
 namespace mgs {
+
+void* handle_alloc(mg_handle* h, size_t bytes) { return dalloc(h, bytes); }
 
 void destroy_handle_after(mg_handle* h, cudaStream_t last) {
     if (!h) return;

@@ -65,6 +65,9 @@ struct mg_handle {
         cudaEvent_t a, b;
         int n;
     };
+    mgs::MetricTables mtab{};         // vertex tables of the fine grid (device)
+    double* pcC[27] = {};             // face C of the pressure-correction steps (on first use)
+    double* pcInv[3] = {};            // 1 / |J^{-1}| of the faces
     bool prof_on = false;
     double prof_ms[MG_PROF_SLOTS] = {};
     long long prof_n[MG_PROF_SLOTS] = {};
@@ -118,6 +121,9 @@ mg_status plan_create(mg_handle* const* hs, int n, Plan** out, cudaStream_t stre
 mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n, bool iteration = true);
 void plan_destroy(Plan* pl);
 mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const double* tol, mg_report* reps);
+
+// Device memory owned by the handle (freed with it); null when out of memory.
+void* handle_alloc(mg_handle* h, size_t bytes);
 
 // Free a handle whose last device work was queued on `last` (or on its own
 // stream when null) without waiting for it: the frees are stream-ordered.

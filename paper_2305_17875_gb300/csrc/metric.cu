@@ -1,6 +1,7 @@
 // metric.cu - set-up kernels: face metric of Section 3.2, coarse-level
 // aggregation, precision casts and the dense coarsest operator.  FP64 throughout.
 #include "mg_kernels.h"
+#include "pc.h"
 
 namespace mgs {
 
@@ -93,6 +94,34 @@ __global__ void k_face_metric(MetricTables t, Dims D, int stencil, double* g0,
             det_sum += face_metric(t, 2, vx, row);
         }
         J[c] = det_sum / 6.0;
+    }
+}
+
+// C and 1/|J^{-1}| of every cell's three lower faces: with a_p = col_{p+1} x
+// col_{p+2} (the cofactor columns of J^{-1}) and det = col_0 . a_0, the
+// inverse has rows a_p / det, so C row p = |det| a_p / det = sign(det) a_p.
+struct CArrays {
+    double* C[27];
+    double* inv[3];
+};
+__global__ void k_face_C(MetricTables t, Dims D, CArrays out) {
+    const i64 n = D.n();
+    for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x) {
+        const C3 cc = decode(D, c);
+        for (int d = 0; d < 3; ++d) {
+            const int v[3] = {cc.i, cc.j, cc.k};
+            V3 col[3];
+            face_columns(t, d, v, col);
+            const V3 a[3] = {cross(col[1], col[2]), cross(col[2], col[0]), cross(col[0], col[1])};
+            const double det = dot(col[0], a[0]);
+            const double sg = det < 0.0 ? -1.0 : 1.0;
+            for (int p = 0; p < 3; ++p) {
+                out.C[9 * d + 3 * p + 0][c] = sg * a[p].x;
+                out.C[9 * d + 3 * p + 1][c] = sg * a[p].y;
+                out.C[9 * d + 3 * p + 2][c] = sg * a[p].z;
+            }
+            out.inv[d][c] = 1.0 / fabs(det);
+        }
     }
 }
 
@@ -299,6 +328,15 @@ cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double
 cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s) {
     if (lv.stencil == 19) k_assemble<19><<<grid_for(lv.D.n(), 128), 128, 0, s>>>(lv.c64, lv.D, a);
     else k_assemble<7><<<grid_for(lv.D.n(), 256), 256, 0, s>>>(lv.c64, lv.D, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_C(const MetricTables& t, Dims D, double* const C[27], double* const inv_det[3],
+                          cudaStream_t s) {
+    CArrays a;
+    for (int q = 0; q < 27; ++q) a.C[q] = C[q];
+    for (int d = 0; d < 3; ++d) a.inv[d] = inv_det[d];
+    k_face_C<<<grid_for(D.n(), 128), 128, 0, s>>>(t, D, a);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,16 @@
+// pc.h - the steps either side of the pressure solve (Section 3.6): internal
+// interface between set-up (metric.cu) and the step kernels (pc.cu).
+#pragma once
+
+#include "mg_kernels.h"
+
+namespace mgs {
+
+// C of every cell's three lower faces (Section 3.2, Eq. skewness: C_pa =
+// |J^{-1}| dzeta_p/dx_a of the face), 27 arrays at index 9 d + 3 p + a (face
+// normal d and row p in zeta, eta, xi order, Cartesian column a), and
+// 1 / |J^{-1}| of the face, 3 arrays.
+cudaError_t launch_face_C(const MetricTables& t, Dims D, double* const C[27], double* const inv_det[3],
+                          cudaStream_t s);
+
+}  // namespace mgs
