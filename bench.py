@@ -379,6 +379,32 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N,
            "ms_per_step": statistics.mean(e2e_ms)}
 
+    # the steps either side of the solve in the pressure correction
+    # (Section 3.6): right side of Eq. PC_6 and correction of Eq. PC_7 from a
+    # random staggered velocity, device time per call
+    pc_step = None
+    if world == 1:
+        u = torch.randn(9 * N, dtype=torch.float64, device="cuda")
+        fpc = torch.empty(N, dtype=torch.float64, device="cuda")
+        mgs.mg_pc_rhs(h, u, fpc)                       # first call builds the face C
+        def _ev_time(fn, reps=5):
+            flush.fill_(3.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+        t_rhs = _ev_time(lambda: mgs.mg_pc_rhs(h, u, fpc))
+        t_cor = _ev_time(lambda: mgs.mg_pc_correct(h, xd, u))
+        b_rhs, b_cor = 160.0 * N, (8 + 216 + 24 + 144) * N
+        pc_step = {"rhs_ms": t_rhs, "correct_ms": t_cor,
+                   "rhs_alg_GBps": b_rhs / (t_rhs * 1e-3) / 1e9, "correct_alg_GBps": b_cor / (t_cor * 1e-3) / 1e9,
+                   "step_ms": t_rhs + ms_step + t_cor,
+                   "note": "right side + solve + correction of one pressure-correction step"}
+        del u, fpc
+
     # plain FP64 multigrid on the same workload (the speedup reference)
     compare = None
     if not args.no_compare and prec != 0:
@@ -402,7 +428,7 @@ def run_ours(args, rank, world, local_rank):
         "config": config_of(args, g, rep, stencil),
         "rel_res": rep["rel_res"], "iters": rep["iters"],
         "roofline": roof, "kernels": kernels,
-        "setup_s": t_setup, "schedule": mgs.mg_get_schedule(h),
+        "setup_s": t_setup, "schedule": mgs.mg_get_schedule(h), "pc_step": pc_step,
         "e2e": e2e,
         "gpu_launches": int(sum(r["launches"] for r in reps)),
         "clocks": clk, "fp64_mg": compare, "wall_s": wall,
