@@ -17,6 +17,11 @@ Every function is plain numpy / scipy in float64 and follows the paper:
                   restated plainly so every GPU step has a CPU twin).
 * ``direct``    - bordered sparse direct solve of the same system (tiny grids).
 * ``mms``       - manufactured solutions with closed-form Laplacians (pins only).
+* ``pc``        - the steps either side of the solve: right side of Eq. PC_6 and
+                  the correction of Eq. PC_7 on a staggered velocity (Section 3.6).
+* ``tridiag``   - the Thomas algorithm and its periodic variant (Section 3.5,
+                  Eqs. FIBRE_TA1-TA2, FIBRE_TAP1-TAP8); ``mg`` uses it for the
+                  radial-line Gauss-Seidel smoother.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
 multigrid convergence factor, which the paper does not give

@@ -16,7 +16,13 @@ own cell-centred design, written out plainly so every GPU step has a CPU twin:
   mirror at walls, wrap in longitude;
 * smoothers: multicolour Gauss-Seidel (7-point: red/black by (i+j+k) mod 2;
   19-point: four colours ((i+j) mod 2) + 2((j+k) mod 2), swept 0..3), or
-  weighted Jacobi (omega 6/7 for 7-point, 4/5 for 19-point), diagonal = diag(A);
+  weighted Jacobi (omega 6/7 for 7-point, 4/5 for 19-point), diagonal = diag(A),
+  or radial-line Gauss-Seidel: every radial line (fixed colatitude and
+  longitude index) is one block, solved exactly with the Thomas algorithm of
+  Section 3.5 (``tridiag.thomas``) on its tridiagonal part of A; lines are
+  coloured so that no two lines of a colour are coupled (7-point: zebra by
+  (i+k) mod 2; 19-point: four colours (i mod 2) + 2 (k mod 2)), swept in
+  colour order;
 * coarsest level: dense bordered solve [A 1; 1^T 0][e; lam] = [r; 0];
 * V(nu1, nu2) cycle, iterated from x0 until ||b - A x||_2 / ||b||_2 <= tol;
 * gauge: the J-weighted mean of x is removed at the end (discrete volume
@@ -30,9 +36,10 @@ import scipy.sparse as sp
 
 from .grid import shell, face_metrics
 from .operator import assemble
+from .tridiag import thomas
 
 SEMI, FULL = 0, 1
-GS, JACOBI = 0, 1
+GS, JACOBI, LINE = 0, 1, 2
 SEMI_RATIO = 0.7
 
 
@@ -46,6 +53,7 @@ class Level:
     factors: tuple = None  # (c_zeta, c_eta, c_xi) to the next level, or None
     colours: list = field(default_factory=list)
     colour_rows: list = field(default_factory=list)   # A restricted to each colour's rows
+    lines: list = None     # per line colour: (cells [nr][m], rows of A, lower, diag, upper)
 
     @property
     def n(self):
@@ -59,6 +67,37 @@ def colour_of(shape, stencil):
     if stencil == 7:
         return ((i + j + k) & 1).ravel()
     return (((i + j) & 1) + 2 * ((j + k) & 1)).ravel()
+
+
+def line_colour_of(shape, stencil):
+    """Colour of the radial line through every cell, [j][i][k] order."""
+    nr, nth, nph = shape
+    j, i, k = np.meshgrid(np.arange(nr), np.arange(nth), np.arange(nph), indexing="ij")
+    if stencil == 7:
+        return ((i + k) & 1).ravel()
+    return ((i & 1) + 2 * (k & 1)).ravel()
+
+
+def line_systems(lv):
+    """For each line colour: the cells of its radial lines as an [nr][m] array
+    (m lines, j on axis 0), the rows of A for those cells, and the tridiagonal
+    part of A on each line: lower[j] = A(c_j, c_{j-1}), diag[j] = A(c_j, c_j),
+    upper[j] = A(c_j, c_{j+1}) (zero past the walls)."""
+    if lv.lines is None:
+        nr = lv.shape[0]
+        col = line_colour_of(lv.shape, lv.stencil)
+        A = lv.A.tocsr()
+        lv.lines = []
+        for c in range(2 if lv.stencil == 7 else 4):
+            cells = np.nonzero(col == c)[0].reshape(nr, -1)
+            diag = np.asarray(A[cells.ravel(), cells.ravel()]).reshape(cells.shape)
+            lower = np.zeros(cells.shape)
+            upper = np.zeros(cells.shape)
+            if nr > 1:
+                lower[1:] = np.asarray(A[cells[1:].ravel(), cells[:-1].ravel()]).reshape(nr - 1, -1)
+                upper[:-1] = np.asarray(A[cells[:-1].ravel(), cells[1:].ravel()]).reshape(nr - 1, -1)
+            lv.lines.append((cells, A[cells.ravel()], lower, diag, upper))
+    return lv.lines
 
 
 def make_level(shape, fm, stencil):
@@ -175,6 +214,11 @@ def smooth(lv, x, b, sweeps, kind=GS):
         for _ in range(sweeps):
             for idx, rows in zip(lv.colours, lv.colour_rows):
                 x[idx] += (b[idx] - rows @ x) / lv.D[idx]
+    elif kind == LINE:
+        for _ in range(sweeps):
+            for cells, rows, lower, diag, upper in line_systems(lv):
+                r = (b[cells.ravel()] - rows @ x).reshape(cells.shape)
+                x[cells.ravel()] += thomas(lower, diag, upper, r).ravel()
     else:
         w = 6.0 / 7.0 if lv.stencil == 7 else 4.0 / 5.0
         for _ in range(sweeps):
