@@ -55,7 +55,7 @@ enum { MG_MAP_SPHERE = 0, MG_MAP_OBLATE = 1, MG_MAP_TRIAXIAL = 2 };
 enum { MG_PREC_FP64 = 0,        /* plain FP64 multigrid */
        MG_PREC_FP32_IR = 1,     /* FP32 V-cycles inside FP64 iterative refinement */
        MG_PREC_FP16C_IR = 2 };  /* FP16 coefficients, FP32 arithmetic, inside FP64 IR */
-enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1 };
+enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1, MG_SMOOTH_LINE = 2 };
 enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
 
 /* Grid and mapping (Section 2 mapping; Section 3.7 Eq. stretching).
@@ -77,7 +77,12 @@ typedef struct {
 /* Solver options; mg_default_opts fills the defaults noted here. */
 typedef struct {
     int precision;      /* MG_PREC_*, default MG_PREC_FP32_IR */
-    int smoother;       /* MG_SMOOTH_*, default GS (multicolour Gauss-Seidel) */
+    int smoother;       /* MG_SMOOTH_*, default GS (multicolour Gauss-Seidel); LINE =
+                           radial-line Gauss-Seidel (every radial line solved exactly by
+                           the Thomas algorithm of Section 3.5; lines coloured (i+k) mod 2
+                           for 7 points, (i mod 2) + 2 (k mod 2) for 19 points; at most
+                           512 radial cells, 256 for precision 0; the coarse tail and the
+                           one-pass red-black tiles apply to GS only) */
     int nu1, nu2;       /* pre/post sweeps, default 2, 2 */
     int max_levels;     /* default 16 */
     int coarsen;        /* MG_COARSEN_*, default SEMI */
@@ -182,8 +187,12 @@ mg_status mg_apply(mg_handle* h, int level, int prec, const void* x_dev, void* y
 
 /* `sweeps` smoothing sweeps on A_l x = b in place: multicolour Gauss-Seidel
  * (kind 0; 7-point: red then black by (i+j+k) mod 2; 19-point: colours
- * ((i+j) mod 2) + 2((j+k) mod 2) in order 0..3) or weighted Jacobi (kind 1,
- * omega 6/7 for 7-point, 4/5 for 19-point).  The diagonal is that of A_l. */
+ * ((i+j) mod 2) + 2((j+k) mod 2) in order 0..3), weighted Jacobi (kind 1,
+ * omega 6/7 for 7-point, 4/5 for 19-point; the diagonal is that of A_l) or
+ * radial-line Gauss-Seidel (kind 2: x_L += A_LL^{-1} (b - A_l x)_L line by
+ * line, A_LL the tridiagonal part of A_l on the line; line colours as for
+ * MG_SMOOTH_LINE, in order).  Kind 2 on a handle set up with another
+ * smoother first factors the line blocks of every level (allocates). */
 mg_status mg_smooth(mg_handle* h, int level, int prec, void* x_dev, const void* b_dev,
                     int sweeps, int kind);
 
@@ -302,6 +311,43 @@ mg_status mg_pc_rhs(mg_handle* h, const double* u_face, double* f);
  * the 7-point operator) of x = h dP from mg_solve.  The corrected field's
  * flux balance equals the solver's residual b - A x. */
 mg_status mg_pc_correct(mg_handle* h, const double* x, double* u_face);
+
+/* ---------------------------------------------------------------------------
+ * Batched tridiagonal line solves: the Thomas algorithm of Section 3.5
+ * (Eqs. FIBRE_TA1, FIBRE_TA2: forward elimination, back substitution) and its
+ * periodic variant (Eqs. FIBRE_TAP1 to FIBRE_TAP8), in FP64, one GPU thread
+ * per line, for the implicit sweeps along one grid direction.
+ *
+ * Row m of a line is a_m psi_{m-1} + b_m psi_m + c_m psi_{m+1} = g_m.  A plain
+ * line ignores a_0 and c_{n-1}; a periodic line (the longitude direction)
+ * uses them as the corners (a_0 multiplies psi_{n-1}, c_{n-1} multiplies
+ * psi_0).  No pivoting: the forward sweep must meet no zero pivot (the
+ * diagonally dominant systems of the implicit sweeps do not); a zero pivot
+ * gives inf / NaN in x and no error status.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n;                 /* unknowns per line: >= 1, >= 3 for periodic lines */
+    int n1, n2;            /* the lines are (l1, l2), 0 <= l1 < n1, 0 <= l2 < n2 */
+    long long sm, s1, s2;  /* strides in elements: entry m of line (l1, l2) sits at
+                              l1*s1 + l2*s2 + m*sm of a, b, c, g and x.  Lines along
+                              axis 0, 1, 2 of a C-contiguous [d0][d1][d2] array:
+                              (n,n1,n2,sm,s1,s2) = (d0,d1,d2,d1*d2,d2,1),
+                              (d1,d0,d2,d2,d1*d2,1), (d2,d0,d1,1,d1*d2,d2).  Lines
+                              adjacent in memory (s2 = 1) give coalesced access. */
+} mg_lines;
+/* Bytes of the device work array mg_thomas needs: (n - 1) * n1 * n2 doubles
+ * for plain lines (at least one row), 2 (n - 1) n1 n2 for periodic ones; 0 for
+ * an invalid geometry. */
+size_t mg_thomas_work_bytes(const mg_lines* lines, int periodic);
+/* Solve every line.  a, b, c, g, x, work: device arrays owned by the caller
+ * (work of mg_thomas_work_bytes bytes, contents on return unspecified); x may
+ * be the same array as g (solved in place), otherwise no array may overlap
+ * another.  Queued on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream), not synchronised.  MG_EINVAL for a bad geometry, a null array
+ * (unless n1 * n2 = 0) or x / work aliasing a coefficient; MG_ECUDA if the
+ * launch fails. */
+mg_status mg_thomas(const mg_lines* lines, const double* a, const double* b, const double* c,
+                    const double* g, double* x, double* work, int periodic, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with

@@ -27,6 +27,7 @@ STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_EN
           5: "MG_EDIVERGED", 6: "MG_ETIMEOUT", 7: "MG_EAGAIN", 8: "MG_ECUDA"}
 PREC_FP64, PREC_FP32_IR, PREC_FP16C_IR = 0, 1, 2
 MG_HIST = 64
+MG_SMOOTH_GS, MG_SMOOTH_JACOBI, MG_SMOOTH_LINE = range(3)
 
 
 class mg_grid_desc(C.Structure):
@@ -41,6 +42,11 @@ class mg_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_levels", C.c_int), ("coarsen", C.c_int), ("coarse_max", C.c_int),
                 ("max_iters", C.c_int), ("stencil", C.c_int), ("autotune", C.c_int)]
+
+
+class mg_lines(C.Structure):
+    _fields_ = [("n", C.c_int), ("n1", C.c_int), ("n2", C.c_int),
+                ("sm", C.c_longlong), ("s1", C.c_longlong), ("s2", C.c_longlong)]
 
 
 class mg_schedule(C.Structure):
@@ -108,6 +114,8 @@ _SIGS = {
     "mg_get_schedule": ([_vp, C.POINTER(mg_schedule)], _i),
     "mg_pc_rhs": ([_vp, _vp, _vp], _i),
     "mg_pc_correct": ([_vp, _vp, _vp], _i),
+    "mg_thomas_work_bytes": ([C.POINTER(mg_lines), _i], C.c_size_t),
+    "mg_thomas": ([C.POINTER(mg_lines), _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
     "mg_serve_create": ([C.POINTER(mg_serve_opts), C.POINTER(_vp)], _i),
     "mg_serve_submit": ([_vp, C.POINTER(mg_grid_desc), C.POINTER(mg_opts), _vp, _d,
@@ -309,6 +317,38 @@ def mg_pc_rhs(h: Handle, u_face, f):
 def mg_pc_correct(h: Handle, x, u_face):
     """Correction of Eq. PC_7 of u_face (in place) by x = h dP."""
     _check(_lib.mg_pc_correct(h.ptr, _ptr(x, "float64"), _ptr(u_face, "float64")), "mg_pc_correct")
+
+
+def lines_along(shape, axis) -> dict:
+    """mg_lines fields for the lines along ``axis`` of a C-contiguous 3-d array."""
+    d0, d1, d2 = shape
+    return [dict(n=d0, n1=d1, n2=d2, sm=d1 * d2, s1=d2, s2=1),
+            dict(n=d1, n1=d0, n2=d2, sm=d2, s1=d1 * d2, s2=1),
+            dict(n=d2, n1=d0, n2=d1, sm=1, s1=d1 * d2, s2=d2)][axis]
+
+
+def _lines(d) -> mg_lines:
+    L = mg_lines()
+    for k, _ in mg_lines._fields_:
+        setattr(L, k, int(d[k]))
+    return L
+
+
+def mg_thomas_work_bytes(lines: dict, periodic=False) -> int:
+    return int(_lib.mg_thomas_work_bytes(C.byref(_lines(lines)), int(bool(periodic))))
+
+
+def mg_thomas(lines: dict, a, b, c, g, x, periodic=False, work=None, stream=None):
+    """Tridiagonal solves of Section 3.5 along every line of ``lines``
+    (mg_lines fields); device float64 tensors; ``work`` is allocated when None."""
+    L = _lines(lines)
+    if work is None:
+        import torch
+        nbytes = _lib.mg_thomas_work_bytes(C.byref(L), int(bool(periodic)))
+        work = torch.empty(max(nbytes // 8, 1), dtype=torch.float64, device=x.device)
+    _check(_lib.mg_thomas(C.byref(L), _ptr(a, "float64"), _ptr(b, "float64"), _ptr(c, "float64"),
+                          _ptr(g, "float64"), _ptr(x, "float64"), _ptr(work, "float64"),
+                          int(bool(periodic)), _stream(stream)), "mg_thomas")
 
 
 def mg_get_schedule(h: Handle) -> dict:

@@ -11,6 +11,7 @@
 #include <cstdlib>
 
 #include "mg_kernels.h"
+#include "line_smooth.cuh"
 
 namespace mgs {
 
@@ -578,6 +579,8 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         // with twice the registers); 7 points: groups when nph is a multiple of 4
         if (S == 7 && vec4(tk.v.D)) gs_pass7v<T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
         else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
+    } else if constexpr (OP == BOP_LINE) {
+        line_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
     } else if constexpr (OP == BOP_JACOBI) {
         jacobi_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (T*)tk.y, (const T*)tk.b, first, stride);
     } else if constexpr (OP == BOP_RESTRICT) {
@@ -968,6 +971,7 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
     switch (op) {
         STENCIL_OP(BOP_GS)
         STENCIL_OP(BOP_JACOBI)
+        STENCIL_OP(BOP_LINE)
         STENCIL_OP(BOP_RESTRICT)
         STENCIL_OP(BOP_RESID)
         PLAIN_OP(BOP_PROLONG)

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "line_smooth.cuh"
 
 using namespace mgs;
 
@@ -108,7 +109,7 @@ std::string check_grid(const mg_grid_desc* g) {
 std::string check_opts(const mg_opts* o) {
     if (!o) return "opts is NULL";
     if (o->precision < 0 || o->precision > 2) return "precision must be 0, 1 or 2";
-    if (o->smoother < 0 || o->smoother > 1) return "smoother must be 0 or 1";
+    if (o->smoother < 0 || o->smoother > 2) return "smoother must be 0, 1 or 2";
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 > 64) return "bad nu1/nu2";
     if (o->max_levels < 1 || o->max_levels > 32) return "max_levels must be in 1..32";
     if (o->coarsen < 0 || o->coarsen > 1) return "coarsen must be 0 or 1";
@@ -223,6 +224,36 @@ bool fastdiv_ok(const Dims& D) {
         }
     }
     return true;
+}
+
+// Radial-line factors of every level in the value type of `prec`, made on
+// first use (set-up of a radial-line handle, or mg_smooth with kind 2).
+mg_status ensure_line_factors(mg_handle* h, int prec) {
+    const int cls = prec == PREC64 ? 0 : 1;
+    const int kc = cls == 0 ? LineRows<double>::kC : LineRows<float>::kC;
+    if (line_chunks(h->L[0].D.nr, kc) > 16) {
+        set_error("radial-line smoother: at most " + std::to_string(16 * kc) + " radial cells in this precision");
+        return MG_EINVAL;
+    }
+    bool missing = false;
+    for (const Level& lv : h->L) missing = missing || !lv.lf[cls];
+    if (!missing) return MG_OK;
+    TmpDev tb(sizeof(unsigned), h->stream, h->device);
+    if (!tb.p) return MG_ENOMEM;
+    CK(cudaMemsetAsync(tb.p, 0, sizeof(unsigned), h->stream));
+    for (Level& lv : h->L) {
+        if (lv.lf[cls]) continue;
+        if (!(lv.lf[cls] = dalloc(h, 3 * (size_t)(cls == 0 ? 8 : 4) * lv.D.n()))) return MG_ENOMEM;
+        CK(launch_line_factors(lv.view(h->stencil), prec, lv.lf[cls], (unsigned*)tb.p, h->stream));
+    }
+    unsigned hb = 0;
+    CK(cudaMemcpyAsync(&hb, tb.p, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hb) {
+        set_error("a radial-line block of the operator has a zero pivot");
+        return MG_EINVAL;
+    }
+    return MG_OK;
 }
 
 // The outer loop converts between FP64 and FP32 on the integer pipes; check
@@ -548,6 +579,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         }
     }
 
+    if (o->smoother == MG_SMOOTH_LINE) CKS(ensure_line_factors(h, h->prec));
+
     // --- coarsest level: dense operator -> bordered inverse (device, FP64)
     const int nc = h->ncoarse;
     if (!(h->binv = (double*)dalloc(h, sizeof(double) * nc * nc))) return MG_ENOMEM;
@@ -714,6 +747,12 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
         const int ncol = h->stencil == 7 ? 2 : 4;
         for (int s = 0; s < sweeps; ++s)
             for (int c = 0; c < ncol; ++c, ++n) CK(launch_gs_colour(v, prec, x, b, c, h->stream));
+    } else if (kind == MG_SMOOTH_LINE) {
+        CKS(ensure_line_factors(h, prec));
+        const int ncol = h->stencil == 7 ? 2 : 4;
+        const void* fac = lv.lf[prec == PREC64 ? 0 : 1];
+        for (int s = 0; s < sweeps; ++s)
+            for (int c = 0; c < ncol; ++c, ++n) CK(launch_line_colour(v, prec, x, b, fac, c, h->stream));
     } else {
         const size_t bytes = value_bytes(prec) * lv.D.n();
         for (int s = 0; s < sweeps; ++s, ++n) {
@@ -771,7 +810,8 @@ mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
 double model_bytes_per_iteration(const mg_handle* h) {
     const int nc = h->stencil == 19 ? 9 : 3;
     const double vb = (double)value_bytes(h->prec), cb = (double)coef_bytes(h->prec);
-    const int ncol = h->opts.smoother == MG_SMOOTH_GS ? (h->stencil == 7 ? 2 : 4) : 1;
+    const int ncol = h->opts.smoother != MG_SMOOTH_JACOBI ? (h->stencil == 7 ? 2 : 4) : 1;
+    const double fac_bytes = h->opts.smoother == MG_SMOOTH_LINE ? 3 * vb : 0.0;   // line factors
     double total = 0.0;
     for (size_t l = 0; l < h->L.size(); ++l) {
         const double n = (double)h->L[l].D.n();
@@ -780,7 +820,7 @@ double model_bytes_per_iteration(const mg_handle* h) {
             break;
         }
         const double nc_cells = (double)h->L[l + 1].D.n();
-        const double sweep = n * (2 * vb + vb + nc * cb) * ncol;   // each colour pass reads the arrays
+        const double sweep = n * (2 * vb + vb + nc * cb + fac_bytes) * ncol;   // each colour pass reads the arrays
         total += (h->opts.nu1 + h->opts.nu2) * sweep;
         total += n * (vb + vb + nc * cb) + 2.0 * nc_cells * vb;     // residual + restriction
         total += n * 2 * vb + nc_cells * vb;                         // prolongation + correction
@@ -857,7 +897,8 @@ size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
     const double coarse = n * (nc * (8 + (o->precision == PREC64 ? 0 : cb)) + 24);
     const double rows = n * 8 * (nc == 9 ? 19 : 1);   // assembled fine rows
     const double fixed = n * 16 /*J, b*/ + rows + 8.0 * kMaxCoarse * kMaxCoarse + (1 << 20);
-    return (size_t)(fine + coarse + fixed);
+    const double lines = o->smoother == MG_SMOOTH_LINE ? 2 * n * 3 * value_bytes(o->precision) : 0.0;
+    return (size_t)(fine + coarse + fixed + lines);
 }
 
 mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_handle** out) {
@@ -962,7 +1003,7 @@ mg_status mg_apply(mg_handle* h, int level, int prec, const void* x, void* y) {
 
 mg_status mg_smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
     LEVEL_CHECK(h, level, prec);
-    if (!x || !b || sweeps < 0 || kind < 0 || kind > 1) return MG_EINVAL;
+    if (!x || !b || sweeps < 0 || kind < 0 || kind > 2) return MG_EINVAL;
     StreamJoin join(h);
     return smooth(h, level, prec, x, b, sweeps, kind);
 }

@@ -24,6 +24,7 @@ struct Level {
     void* e = nullptr;   // correction / iterate
     void* r = nullptr;   // right side on this level
     void* t = nullptr;   // scratch (Jacobi)
+    void* lf[2] = {};    // radial-line factors, double / float (3 n values), made on first use
     LevelView view(int stencil) const;
 };
 

@@ -1,0 +1,228 @@
+// lines.cu - batched tridiagonal line solves (Section 3.5): the Thomas
+// algorithm (Eqs. FIBRE_TA1, FIBRE_TA2) and its periodic variant (Eqs.
+// FIBRE_TAP1 to FIBRE_TAP8), one thread per line.
+//
+// Row m of a line reads a_m psi_{m-1} + b_m psi_m + c_m psi_{m+1} = g_m; a
+// periodic line closes the ring (a_0 couples psi_{n-1}, c_{n-1} couples
+// psi_0).  Element m of line (l1, l2) sits at l1 s1 + l2 s2 + m sm in every
+// array, so the radial, colatitude and longitude lines of an [nr][nth][nph]
+// field are all solved in place of the field.  Consecutive threads take
+// consecutive l2: lines adjacent in memory (s2 = 1) give coalesced loads;
+// for contiguous lines (sm = 1) each thread reads its line in runs of kU
+// elements, one or two sectors per array at a time.
+//
+// The sweep is the normalised form of the paper's forward elimination:
+// cp_m = c_m / (b_m - a_m cp_{m-1}), dp_m = (g_m - a_m dp_{m-1}) / (same), so
+// back substitution psi_m = dp_m - cp_m psi_{m+1} needs only cp and dp (dp is
+// kept in x, cp in the work array, laid out [m][line] so that its accesses
+// are coalesced whatever the line layout).  Same elimination, same pivots as
+// the paper's b'_m = b_m - a_m c_{m-1} / b'_{m-1}; one reciprocal per row.
+//
+// Periodic lines (Eqs. TAP2 to TAP8): psi1 and psi2 solve the leading
+// (n-1)-block with right sides g and (-a_0, 0, .., 0, -c_{n-2}); both share
+// cp.  The paper finds psi1_0 and psi2_0 by back substitution before Eq. TAP8
+// gives psi_{n-1}; here they are summed during the forward sweep instead
+// (back substitution from the top gives psi_0 = sum_m dp_m prod_{k<m} (-cp_k)),
+// so psi_{n-1} is known when the sweep ends and a single back substitution
+// of dp1 + dp2 psi_{n-1} gives psi = psi1 + psi2 psi_{n-1} (Eq. TAP4).
+//
+// FP64 arithmetic is the scarce resource here (one reciprocal and five
+// multiply-adds per row), so the reciprocal is Newton-Raphson iteration
+// r <- r + r (1 - v r) from the hardware's single-precision approximate
+// reciprocal (relative error below 2^-22, squared by each step: two steps
+// reach double precision, within an ulp of 1/v); values whose seed would
+// leave the single-precision range take an IEEE division instead.
+#include <algorithm>
+#include <string>
+
+#include "engine.h"
+
+namespace mgs {
+namespace {
+
+constexpr int kLT = 128;   // threads per block
+constexpr int kU = 8;      // rows loaded ahead per thread
+
+struct LineGeom {
+    int n;
+    i64 n1, n2, nl;
+    i64 sm, s1, s2;
+};
+
+__device__ __forceinline__ double rcp64(double v) {
+    const int e = (__double2hiint(v) >> 20) & 0x7ff;   // biased exponent
+    if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / v;
+    float s;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(__double2float_rn(v)));
+    double r = (double)s;
+    r = __fma_rn(r, __fma_rn(-v, r, 1.0), r);
+    return __fma_rn(r, __fma_rn(-v, r, 1.0), r);
+}
+
+__device__ __forceinline__ i64 line_base(const LineGeom& L, i64 line) {
+    const i64 l1 = line / L.n2;
+    return l1 * L.s1 + (line - l1 * L.n2) * L.s2;
+}
+
+// Plain lines.  x may alias g (g_m is read before x_m is written).
+__global__ void __launch_bounds__(kLT) k_thomas(LineGeom L, const double* __restrict__ a,
+                                                 const double* __restrict__ b,
+                                                 const double* __restrict__ c, const double* g,
+                                                 double* x, double* __restrict__ w) {
+    const i64 line = blockIdx.x * (i64)kLT + threadIdx.x;
+    if (line >= L.nl) return;
+    const i64 base = line_base(L, line);
+    const int n = L.n;
+    double cp = 0.0, dp = 0.0;
+    for (int m0 = 0; m0 < n; m0 += kU) {
+        const int cnt = min(kU, n - m0);
+        double ra[kU], rb[kU], rc[kU], rg[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (u < cnt) {
+                const i64 o = base + (i64)(m0 + u) * L.sm;
+                const int m = m0 + u;
+                ra[u] = m > 0 ? a[o] : 0.0;
+                rb[u] = b[o];
+                rc[u] = m < n - 1 ? c[o] : 0.0;
+                rg[u] = g[o];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (u < cnt) {
+                const int m = m0 + u;
+                const double r = rcp64(__fma_rn(-ra[u], cp, rb[u]));
+                cp = rc[u] * r;
+                dp = __dmul_rn(__fma_rn(-ra[u], dp, rg[u]), r);
+                x[base + (i64)m * L.sm] = dp;
+                if (m < n - 1) w[(i64)m * L.nl + line] = cp;
+            }
+        }
+    }
+    // back substitution; x_{n-1} = dp_{n-1} is already in place
+    double psi = dp;
+    for (int m = n - 2; m >= 0; --m) {
+        const i64 o = base + (i64)m * L.sm;
+        psi = __fma_rn(-w[(i64)m * L.nl + line], psi, x[o]);
+        x[o] = psi;
+    }
+}
+
+// Periodic lines (n >= 3).  w holds cp in [0, n-2) and dp2 in [n-1, 2n-2)
+// blocks of nl entries.  x may alias g.
+__global__ void __launch_bounds__(kLT) k_thomas_periodic(LineGeom L, const double* __restrict__ a,
+                                                          const double* __restrict__ b,
+                                                          const double* __restrict__ c,
+                                                          const double* g, double* x,
+                                                          double* __restrict__ w) {
+    const i64 line = blockIdx.x * (i64)kLT + threadIdx.x;
+    if (line >= L.nl) return;
+    const i64 base = line_base(L, line);
+    const int n = L.n, nc = n - 1;      // nc rows in the leading block A_c
+    double* wcp = w;
+    double* wd2 = w + (i64)nc * L.nl;
+    double cp = 0.0, d1 = 0.0, d2 = 0.0;
+    double prod = 1.0, s1 = 0.0, s2 = 0.0;   // prod_{k<m} (-cp_k); sums giving psi1_0, psi2_0
+    for (int m0 = 0; m0 < nc; m0 += kU) {
+        const int cnt = min(kU, nc - m0);
+        double ra[kU], rb[kU], rc[kU], rg[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (u < cnt) {
+                const i64 o = base + (i64)(m0 + u) * L.sm;
+                ra[u] = a[o];
+                rb[u] = b[o];
+                rc[u] = c[o];
+                rg[u] = g[o];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (u < cnt) {
+                const int m = m0 + u;
+                const double am = m > 0 ? ra[u] : 0.0;            // a_0 is a corner, not in A_c
+                const double em = (m == 0 ? -ra[u] : 0.0) + (m == nc - 1 ? -rc[u] : 0.0);
+                const double r = rcp64(__fma_rn(-am, cp, rb[u]));
+                cp = m < nc - 1 ? rc[u] * r : 0.0;
+                d1 = __dmul_rn(__fma_rn(-am, d1, rg[u]), r);
+                d2 = __dmul_rn(__fma_rn(-am, d2, em), r);
+                s1 = __fma_rn(prod, d1, s1);
+                s2 = __fma_rn(prod, d2, s2);
+                prod = -prod * cp;
+                x[base + (i64)m * L.sm] = d1;
+                wd2[(i64)m * L.nl + line] = d2;
+                if (m < nc - 1) wcp[(i64)m * L.nl + line] = cp;
+            }
+        }
+    }
+    // Eq. TAP8 with psi1_{n-2} = dp1_{n-2}, psi2_{n-2} = dp2_{n-2}
+    const i64 ol = base + (i64)nc * L.sm;
+    const double al = a[ol], bl = b[ol], cl = c[ol], gl = g[ol];
+    const double num = __fma_rn(-al, d1, __fma_rn(-cl, s1, gl));
+    const double den = __fma_rn(al, d2, __fma_rn(cl, s2, bl));
+    const double last = num / den;
+    x[ol] = last;
+    // one back substitution of dp1 + dp2 last
+    double psi = __fma_rn(d2, last, d1);
+    x[base + (i64)(nc - 1) * L.sm] = psi;
+    for (int m = nc - 2; m >= 0; --m) {
+        const i64 o = base + (i64)m * L.sm;
+        const double dm = __fma_rn(wd2[(i64)m * L.nl + line], last, x[o]);
+        psi = __fma_rn(-wcp[(i64)m * L.nl + line], psi, dm);
+        x[o] = psi;
+    }
+}
+
+bool geom_of(const mg_lines* in, int periodic, LineGeom* L) {
+    if (!in || in->n < 1 || (periodic && in->n < 3) || in->n1 < 0 || in->n2 < 0) return false;
+    L->n = in->n;
+    L->n1 = in->n1;
+    L->n2 = in->n2;
+    L->nl = (i64)in->n1 * in->n2;
+    L->sm = in->sm;
+    L->s1 = in->s1;
+    L->s2 = in->s2;
+    return true;
+}
+
+}  // namespace
+}  // namespace mgs
+
+using namespace mgs;
+
+extern "C" size_t mg_thomas_work_bytes(const mg_lines* lines, int periodic) {
+    LineGeom L;
+    if (!geom_of(lines, periodic, &L)) return 0;
+    const i64 rows = periodic ? 2 * (i64)(L.n - 1) : (i64)std::max(L.n - 1, 1);
+    return (size_t)(rows * L.nl) * sizeof(double);
+}
+
+extern "C" mg_status mg_thomas(const mg_lines* lines, const double* a, const double* b, const double* c,
+                               const double* g, double* x, double* work, int periodic, void* stream) {
+    LineGeom L;
+    if (!geom_of(lines, periodic, &L)) {
+        set_error(periodic ? "mg_thomas: periodic lines need n >= 3 and n1, n2 >= 0"
+                           : "mg_thomas: lines need n >= 1 and n1, n2 >= 0");
+        return MG_EINVAL;
+    }
+    if (L.nl == 0) return MG_OK;
+    if (!a || !b || !c || !g || !x || !work) {
+        set_error("mg_thomas: null array");
+        return MG_EINVAL;
+    }
+    if (x == a || x == b || x == c || work == x || work == g) {
+        set_error("mg_thomas: x and work may not alias the coefficients (x may alias g)");
+        return MG_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((L.nl + kLT - 1) / kLT);
+    if (periodic) k_thomas_periodic<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
+    else k_thomas<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("mg_thomas: ") + cudaGetErrorString(e));
+        return MG_ECUDA;
+    }
+    return MG_OK;
+}

@@ -208,6 +208,36 @@ __global__ void k_assemble(CoefF64 cf, Dims D, double* a) {
     }
 }
 
+// Factorisation of the radial-line blocks A_LL (tridiagonal: the operator's
+// couplings at radial offsets -1, 0, +1, found by applying the operator to
+// unit vectors) for the radial-line smoother: Thomas elimination in FP64
+// along every line, stored as alpha = -a_j / b'_j, beta = 1 / b'_j,
+// gamma = -c_j / b'_j (three arrays of n cells, value type T).  A zero or
+// non-finite pivot counts in *bad.
+template <int S, typename T>
+__global__ void k_line_factors(CoefF64 cf, Dims D, T* fac, unsigned* bad) {
+    const i64 N = D.n();
+    const i64 lines = (i64)D.nth * D.nph;
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < lines; t += (i64)gridDim.x * blockDim.x) {
+        const int i = (int)(t / D.nph), k = (int)(t % D.nph);
+        double cprev = 0.0;
+        for (int j = 0; j < D.nr; ++j) {
+            const C3 p{j, i, k};
+            const i64 c = cidx(D, p);
+            const double lo = j > 0 ? apply_cell<S, double>(cf, UnitX{c - D.nth * D.nph, D}, D, p) : 0.0;
+            const double dd = apply_cell<S, double>(cf, UnitX{c, D}, D, p);
+            const double up = j + 1 < D.nr ? apply_cell<S, double>(cf, UnitX{c + D.nth * D.nph, D}, D, p) : 0.0;
+            const double ib = 1.0 / (dd - lo * cprev);
+            cprev = up * ib;
+            const double al = -lo * ib;
+            if (!isfinite(ib) || !isfinite(al) || !isfinite(cprev)) atomicAdd(bad, 1u);
+            fac[c] = (T)al;
+            fac[N + c] = (T)ib;
+            fac[2 * N + c] = (T)(-cprev);
+        }
+    }
+}
+
 // ---- in-place Gauss-Jordan inversion with partial pivoting (FP64), for the
 // bordered coarsest matrix [A 1; 1^T 0] of order m.  Step k: the pivot row
 // (largest |M[r][k]|, r >= k) is swapped into row k, row k is scaled, and
@@ -328,6 +358,19 @@ cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double
 cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s) {
     if (lv.stencil == 19) k_assemble<19><<<grid_for(lv.D.n(), 128), 128, 0, s>>>(lv.c64, lv.D, a);
     else k_assemble<7><<<grid_for(lv.D.n(), 256), 256, 0, s>>>(lv.c64, lv.D, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsigned* bad, cudaStream_t s) {
+    const i64 lines = (i64)lv.D.nth * lv.D.nph;
+    const int nb = grid_for(lines, 128);
+    if (prec == PREC64) {
+        if (lv.stencil == 19) k_line_factors<19, double><<<nb, 128, 0, s>>>(lv.c64, lv.D, (double*)fac, bad);
+        else k_line_factors<7, double><<<nb, 128, 0, s>>>(lv.c64, lv.D, (double*)fac, bad);
+    } else {
+        if (lv.stencil == 19) k_line_factors<19, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
+        else k_line_factors<7, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
+    }
     return cudaGetLastError();
 }
 

@@ -37,6 +37,10 @@ cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s)
 cudaError_t launch_cast32(const double* src, float* dst, i64 n, cudaStream_t s);
 cudaError_t launch_cast16(const double* src, __half* dst, i64 n, float inv_scale, cudaStream_t s);
 cudaError_t launch_dense_operator(const LevelView& lv, double* A, cudaStream_t s);
+// Factors of the radial-line blocks of a level for the radial-line smoother:
+// 3 x n values of the cycle's type (double for PREC64, float otherwise);
+// *bad (zeroed by the caller) counts zero or non-finite pivots.
+cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsigned* bad, cudaStream_t s);
 // Leading n x n block of [A 1; 1^T 0]^{-1} (A: n x n row-major) by Gauss-Jordan
 // elimination on the device.  work: (n+1)^2 doubles, col: n+1 doubles, piv and
 // perm: n+1 ints each, *bad (zeroed by the caller) set on a zero pivot.
@@ -72,6 +76,9 @@ cudaError_t launch_gs_colour(const LevelView& lv, int prec, void* x, const void*
                              cudaStream_t s);
 cudaError_t launch_jacobi(const LevelView& lv, int prec, const void* x, void* xo, const void* b,
                           cudaStream_t s);
+// One colour of the radial-line Gauss-Seidel sweep (fac from launch_line_factors).
+cudaError_t launch_line_colour(const LevelView& lv, int prec, void* x, const void* b, const void* fac,
+                               int colour, cudaStream_t s);
 cudaError_t launch_restrict_residual(const LevelView& lv, Dims Dc, int prec, const void* x,
                                      const void* b, void* rc, void* ec_zero, cudaStream_t s);
 cudaError_t launch_prolong_add(const LevelView& lv, Dims Dc, int prec, const void* ec, void* x,
@@ -116,7 +123,8 @@ enum {
     BOP_SHIFT,        // x -= scal[SC_SUMJX] / aux
     BOP_FINALIZE,     // scal[slot] = sum of n partials z; y (if set) gets a copy
     BOP_COARSE,       // x = binv b, n rows
-    BOP_RB7           // one red-black sweep of the 7-point operator, x -> y (tiles)
+    BOP_RB7,          // one red-black sweep of the 7-point operator, x -> y (tiles)
+    BOP_LINE          // radial-line Gauss-Seidel colour pass: x, b, z = line factors
 };
 // Tiles of the one-pass red-black sweep (colatitude x radius x longitude).
 constexpr int kRbJ = 8, kRbI = 8, kRbK = 64;

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "line_smooth.cuh"
 
 namespace mgs {
 
@@ -47,6 +48,11 @@ i64 gs_items(const Dims& D, int stencil) {
 i64 restrict_items(const Dims& D, const Dims& Dc) { return vec4(D) ? (i64)Dc.nr * Dc.nth * (D.nph / 4) : Dc.n(); }
 i64 prolong_items(const Dims& D) { return vec4(D) ? D.n() / 4 : D.n(); }
 i64 vector_items(i64 n) { return (n + 3) / 4; }
+// radial-line colour passes: W threads per line (one per chunk of rows)
+i64 line_items(const Dims& D, int stencil, int prec) {
+    const int kc = prec == PREC64 ? LineRows<double>::kC : LineRows<float>::kC;
+    return line_count(D, stencil, 0) * line_chunks(D.nr, kc);
+}
 
 // one launch of a level operation over some tasks
 struct Launch {
@@ -146,11 +152,12 @@ bool fused_level(const mg_handle* h, int level) {
 
 void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
     const int prec = pl->prec;
-    int maxc = 0;
+    int maxc = 0, maxl = 0;
     bool any_jacobi = false, any_fused = false;
     for (mg_handle* h : pl->hs) {
         if (level >= top_of(h)) continue;
         if (h->opts.smoother == MG_SMOOTH_JACOBI) any_jacobi = true;
+        else if (h->opts.smoother == MG_SMOOTH_LINE) maxl = std::max(maxl, h->stencil == 7 ? 2 : 4);
         else if (fused_level(h, level)) any_fused = true;
         else maxc = std::max(maxc, h->stencil == 7 ? 2 : 4);
     }
@@ -190,6 +197,24 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 level_bufs(h, prec, level, &t.x, &t.b);
                 t.shell = (int)s;
                 P.add(t, vblocks(h, gs_items(h->L[level].D, h->stencil)));
+            }
+        }
+        for (int c = 0; c < maxl; ++c)
+            for (int st : {7, 19}) {
+            Launch& L = P.begin(BOP_LINE, c, st);
+            if (level == 0) {
+                L.prof = MG_PROF_SMOOTH0;
+                L.prof_n = 1;
+            }
+            for (size_t s = 0; s < pl->hs.size(); ++s) {
+                mg_handle* h = pl->hs[s];
+                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_LINE || h->stencil != st) continue;
+                if (c >= (h->stencil == 7 ? 2 : 4)) continue;
+                BTask t = task_of(h, level);
+                level_bufs(h, prec, level, &t.x, &t.b);
+                t.z = h->L[level].lf[prec == PREC64 ? 0 : 1];
+                t.shell = (int)s;
+                P.add(t, vblocks(h, line_items(h->L[level].D, h->stencil, prec)));
             }
         }
         if (any_jacobi) {

@@ -5,6 +5,7 @@
 #include <cooperative_groups.h>
 
 #include "mg_kernels.h"
+#include "line_smooth.cuh"
 
 namespace mgs {
 
@@ -181,6 +182,13 @@ __global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* _
                                      (i64)gridDim.x * blockDim.x);
 }
 
+// One colour of the radial-line Gauss-Seidel sweep (line_smooth.cuh).
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_line(CF cf, Dims D, T* x, const T* __restrict__ b,
+                                                    const T* __restrict__ fac, int colour) {
+    line_pass<S, T>(cf, D, x, b, fac, colour, blockIdx.x, gridDim.x);
+}
+
 // Weighted Jacobi, out of place: xo = x + omega (b - A x) / diag(A).
 template <int S, typename T, typename CF>
 __global__ void __launch_bounds__(kThreads) k_jacobi(CF cf, Dims D, const T* __restrict__ x, T* __restrict__ xo,
@@ -310,6 +318,16 @@ cudaError_t launch_gs_colour(const LevelView& lv, int prec, void* x, const void*
                              cudaStream_t s) {
     const int nb = blocks_for((i64)lv.D.nr * lv.D.nth * (lv.D.nph / 2));
     MG_DISPATCH(lv, prec, (k_gs<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, colour)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_colour(const LevelView& lv, int prec, void* x, const void* b, const void* fac,
+                               int colour, cudaStream_t s) {
+    const int kc = prec == PREC64 ? LineRows<double>::kC : LineRows<float>::kC;
+    const i64 lines = line_count(lv.D, lv.stencil, colour);
+    const int nb = blocks_for(lines * line_chunks(lv.D.nr, kc));
+    MG_DISPATCH(lv, prec, (k_line<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, (const T*)fac,
+                                                                colour)));
     return cudaGetLastError();
 }
 
