@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-grid DOF/s to 1e-10 rel. residual, FP32-refined vs FP64 MG; HBM GB/s; p99 ms"
 UNIT = "DOF/s"
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
+SMOOTHER = {"gs": 0, "jacobi": 1, "line": 2}
 PREC_NAME = {0: "plain FP64 multigrid", 1: "FP32 V-cycles inside FP64 refinement",
              2: "FP16-coefficient FP32 V-cycles inside FP64 refinement"}
 L2_FLUSH_BYTES = 256 << 20
@@ -47,6 +48,8 @@ def parse():
                                                          "(small cases for profiling; not a bench line)")
     p.add_argument("--precision", default="fp32", choices=list(PREC))
     p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--smoother", default="gs", choices=list(SMOOTHER),
+                   help="gs: multicolour Gauss-Seidel; jacobi; line: radial-line Gauss-Seidel")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--requests", type=int, default=600, help="serve_stream: requests to submit")
@@ -90,7 +93,7 @@ def ncu_traffic(workload, precision, slot):
     return e.get("dram_bytes_per_launch")
 
 
-def algorithmic_bytes(slot, stencil, prec, n_fine, n_next):
+def algorithmic_bytes(slot, stencil, prec, n_fine, n_next, smoother=0):
     """Minimum HBM bytes one launch of the slot's kernel must move (each array
     it needs read or written once; neighbour re-reads served on chip)."""
     vb = 8 if prec == 0 else 4
@@ -102,7 +105,8 @@ def algorithmic_bytes(slot, stencil, prec, n_fine, n_next):
         # one colour pass: all of x (neighbours), b and the updated cells' x
         # for 1/ncol of the cells, every coefficient an updated cell touches
         coef = ncomp * cb * N if stencil == 7 else 18 * cb * N / ncol
-        return vb * N + 2 * vb * N / ncol + coef
+        line = 3 * vb * N / ncol if smoother == 2 else 0.0   # the line factors of the updated cells
+        return vb * N + 2 * vb * N / ncol + coef + line
     if slot == "residual":
         # x, b, the FP64 operator rows (7-point: the three face arrays and the
         # stored centre; 19-point: the 19 assembled coefficients), FP32 r out
@@ -176,14 +180,14 @@ class Clocks:
 def _oracle_solve_job(args):
     """Runs in a spawned process with single-threaded BLAS: one oracle solve of
     the sample grid; returns (cells, seconds of the solve, iterations)."""
-    g, tol = args
+    g, tol, kind = args
     import numpy as np
     import workloads as W
     from oracle import mg as omg
     f = W.rhs_modes(g, seed=0)
     hier, fm = omg.setup(g, 7 if g["mapping"] == 0 else 19)
     t0 = time.perf_counter()
-    x, info = omg.solve(g, f.ravel(), tol=tol, hier=hier, fm=fm, max_iters=200)
+    x, info = omg.solve(g, f.ravel(), tol=tol, hier=hier, fm=fm, max_iters=200, kind=kind)
     dt = time.perf_counter() - t0
     return g["nr"] * g["nth"] * g["nph"], dt, info["iters"]
 
@@ -194,7 +198,7 @@ def sample_grid(g, factor=2):
     return s
 
 
-def cpu_baseline(g, tol, repeats=1):
+def cpu_baseline(g, tol, repeats=1, kind=0):
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in env_keys}
     for k in env_keys:
@@ -202,7 +206,7 @@ def cpu_baseline(g, tol, repeats=1):
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(1) as pool:
-            res = pool.map(_oracle_solve_job, [(sample_grid(g), tol)] * repeats)
+            res = pool.map(_oracle_solve_job, [(sample_grid(g), tol, kind)] * repeats)
     finally:
         for k, v in old.items():
             if v is None:
@@ -235,9 +239,9 @@ def run_reference(args, rank, world):
     s = sample_grid(g)
     with ctx.Pool(1) as pool:
         for _ in range(args.warmup):
-            pool.map(_oracle_solve_job, [(s, args.tol)])
+            pool.map(_oracle_solve_job, [(s, args.tol, SMOOTHER[args.smoother])])
         t0 = time.perf_counter()
-        res = [pool.map(_oracle_solve_job, [(s, args.tol)])[0] for _ in range(args.steps)]
+        res = [pool.map(_oracle_solve_job, [(s, args.tol, SMOOTHER[args.smoother])])[0] for _ in range(args.steps)]
         wall = time.perf_counter() - t0
     cells = res[0][0]
     ms = [r[1] * 1e3 for r in res]
@@ -262,7 +266,8 @@ def config_of(args, g, rep, stencil):
     c = {"workload": name, "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
          "mapping": ["sphere", "oblate", "triaxial"][g["mapping"]], "stretch": g["stretch"],
          "flattening": g["flattening"], "tol": args.tol, "precision": PREC_NAME[PREC[args.precision]],
-         "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{args.gpus}"}
+         "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{args.gpus}",
+         "smoother": getattr(args, "smoother", "gs")}
     if rep is not None:
         c.update(stencil=stencil, levels=rep["levels"], iters=rep["iters"])
     return c
@@ -304,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
     g, f = w["grid"], w["f"]
     N = g["nr"] * g["nth"] * g["nph"]
     prec = PREC[args.precision]
-    sopts = dict(precision=prec)
+    sopts = dict(precision=prec, smoother=SMOOTHER[args.smoother])
     if "max_levels" in w:
         sopts["max_levels"] = w["max_levels"]
     if w.get("coarsen") == "full":
@@ -351,17 +356,19 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel (largest device time in the timed region)
     name, (tot_ms, nl) = max(((k, v) for k, v in prof.items() if k != "tail"), key=lambda kv: kv[1][0])
     per_launch_ms = tot_ms / max(nl, 1)
-    abytes = algorithmic_bytes(name, stencil, prec, N, n_next)
+    abytes = algorithmic_bytes(name, stencil, prec, N, n_next, sopts["smoother"])
     peak, peak_kind = peaks()
     achieved = abytes / (per_launch_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
-            "traffic": ncu_traffic(args.workload, args.precision, name),
+            "traffic": ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
+                                   args.precision, name),
             "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": per_launch_ms,
             "share_of_step": tot_ms / sum(ms)}
     kernels = {k: {"ms_total": v[0], "launches": v[1],
                    "avg_ms": v[0] / max(v[1], 1),
-                   "alg_GBps": algorithmic_bytes(k, stencil, prec, N, n_next) / (v[0] / max(v[1], 1) * 1e-3) / 1e9
+                   "alg_GBps": algorithmic_bytes(k, stencil, prec, N, n_next, sopts["smoother"]) /
+                   (v[0] / max(v[1], 1) * 1e-3) / 1e9
                    if v[1] and k != "tail" else None} for k, v in prof.items()}
 
     # end to end through the public host-buffer call (pinned host memory)
@@ -405,6 +412,30 @@ def run_ours(args, rank, world, local_rank):
                    "note": "right side + solve + correction of one pressure-correction step"}
         del u, fpc
 
+    # the line solves of Section 3.5 on this grid's field: every radial line
+    # (plain Thomas) and every longitude line (periodic Thomas) of random
+    # diagonally dominant systems, FP64; algorithmic bytes = a, b, c, g read
+    # and x written once (40 B per unknown)
+    line_solves = None
+    if world == 1:
+        shape = (g["nr"], g["nth"], g["nph"])
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        la = -torch.rand(shape, generator=gen, device="cuda", dtype=torch.float64)
+        lc = -torch.rand(shape, generator=gen, device="cuda", dtype=torch.float64)
+        lb = 2.2 + torch.rand(shape, generator=gen, device="cuda", dtype=torch.float64)
+        lg = torch.randn(shape, generator=gen, device="cuda", dtype=torch.float64)
+        lx = torch.empty_like(lg)
+        lw = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+        line_solves = {}
+        for key, axis, per in (("radial", 0, False), ("longitude_periodic", 2, True)):
+            L = mgs.lines_along(shape, axis)
+            mgs.mg_thomas(L, la, lb, lc, lg, lx, periodic=per, work=lw)
+            t = _ev_time(lambda: mgs.mg_thomas(L, la, lb, lc, lg, lx, periodic=per, work=lw))
+            gbs = 40.0 * N / (t * 1e-3) / 1e9
+            line_solves[key] = {"ms": t, "alg_GBps": gbs, "frac": gbs / peaks()[0],
+                                "lines": L["n1"] * L["n2"], "n": L["n"]}
+        del la, lb, lc, lg, lx, lw
+
     # plain FP64 multigrid on the same workload (the speedup reference)
     compare = None
     if not args.no_compare and prec != 0:
@@ -429,12 +460,13 @@ def run_ours(args, rank, world, local_rank):
         "rel_res": rep["rel_res"], "iters": rep["iters"],
         "roofline": roof, "kernels": kernels,
         "setup_s": t_setup, "schedule": mgs.mg_get_schedule(h), "pc_step": pc_step,
+        "line_solves": line_solves,
         "e2e": e2e,
         "gpu_launches": int(sum(r["launches"] for r in reps)),
         "clocks": clk, "fp64_mg": compare, "wall_s": wall,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, TOL)
+        line["cpu_baseline"] = cpu_baseline(g, TOL, kind=sopts["smoother"])
     print(json.dumps(line), flush=True)
 
 

@@ -81,8 +81,8 @@ typedef struct {
                            radial-line Gauss-Seidel (every radial line solved exactly by
                            the Thomas algorithm of Section 3.5; lines coloured (i+k) mod 2
                            for 7 points, (i mod 2) + 2 (k mod 2) for 19 points; at most
-                           512 radial cells, 256 for precision 0; the coarse tail and the
-                           one-pass red-black tiles apply to GS only) */
+                           256 radial cells; the coarse tail and the one-pass red-black
+                           tiles apply to GS only) */
     int nu1, nu2;       /* pre/post sweeps, default 2, 2 */
     int max_levels;     /* default 16 */
     int coarsen;        /* MG_COARSEN_*, default SEMI */

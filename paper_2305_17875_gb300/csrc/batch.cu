@@ -629,6 +629,7 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
 // CTAs per SM.
 template <int P, int OP, int S>
 constexpr int min_ctas() {
+    if (OP == BOP_LINE) return 2;          // two chunks of 16 rows per thread: fits 128 registers
     if (P == PREC64 || (OP != BOP_GS && OP != BOP_RESTRICT)) return 1;
     if (OP == BOP_GS) return 4;
     if (S == 19) return 2;                 // the 19-point restriction groups hold ~100 values per thread

@@ -30,11 +30,7 @@ namespace mgs {
 
 template <typename T>
 struct LineRows {
-    static constexpr int kC = 32;   // rows of a chunk held in registers
-};
-template <>
-struct LineRows<double> {
-    static constexpr int kC = 16;
+    static constexpr int kC = 16;   // rows of a chunk held in registers
 };
 
 // Chunks per line: the smallest power of two W with W * kC >= nr (W <= 16

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* _
 
 // One colour of the radial-line Gauss-Seidel sweep (line_smooth.cuh).
 template <int S, typename T, typename CF>
-__global__ void __launch_bounds__(kThreads) k_line(CF cf, Dims D, T* x, const T* __restrict__ b,
+__global__ void __launch_bounds__(kThreads, 2) k_line(CF cf, Dims D, T* x, const T* __restrict__ b,
                                                     const T* __restrict__ fac, int colour) {
     line_pass<S, T>(cf, D, x, b, fac, colour, blockIdx.x, gridDim.x);
 }

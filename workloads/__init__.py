@@ -99,6 +99,10 @@ SINGLE = {
                               precision="fp32"),
     "single_oblate_256": dict(grid=grid_desc(256, r_out=1 / 0.6, mapping=1, flattening=0.1),
                               rhs=("modes", 0), tol=1e-10, precision="fp32"),
+    # a thin shell (radius ratio 1.05, tanh clustering 2): radial coupling
+    # dominates by ~10^3; the case the radial-line smoother is for
+    "single_thin_128": dict(grid=grid_desc(128, r_out=1.05, stretch=2.0), rhs=("modes", 0), tol=1e-10,
+                            precision="fp32"),
 }
 
 
