@@ -22,6 +22,8 @@ Every function is plain numpy / scipy in float64 and follows the paper:
 * ``tridiag``   - the Thomas algorithm and its periodic variant (Section 3.5,
                   Eqs. FIBRE_TA1-TA2, FIBRE_TAP1-TAP8); ``mg`` uses it for the
                   radial-line Gauss-Seidel smoother.
+* ``adi``       - the ADI-CN implicit viscous sweeps of Section 3.4 (Eqs.
+                  solve_2 to solve_4) on a cell-centred field.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
 multigrid convergence factor, which the paper does not give

@@ -178,3 +178,138 @@ def test_line_smoother_handles_a_thin_shell():
         h = info["hist"]
         rho[kind] = (h[-1] / h[0]) ** (1.0 / info["iters"])
     assert rho[mg.GS] > 0.9 and rho[mg.LINE] < 0.15, rho
+
+
+# ---------------------------------------------------------------- ADI-CN sweeps (Section 3.4)
+from oracle import adi, operator  # noqa: E402
+
+ADI_GRIDS = {
+    "sphere_stretched": dict(mapping=0, stretch=2.0),
+    "triaxial": dict(mapping=2, flattening=0.1, e2=0.05, stretch=1.0),
+}
+
+
+def _adi_grid(name, shape=(6, 8, 12)):
+    sh = grid.Shell(*shape, **ADI_GRIDS[name])
+    return sh, grid.face_metrics(sh)
+
+
+@pytest.mark.parametrize("name", list(ADI_GRIDS))
+def test_diagonal_terms_sum_to_the_seven_point_operator(name):
+    """With zero-flux walls, L_zeta + L_eta + L_xi is the 7-point conservative
+    operator (Eq. PC_term1 in each direction) assembled independently."""
+    sh, fm = _adi_grid(name)
+    u = np.random.default_rng(1).standard_normal(sh.n)
+    bc = adi.walls((adi.FLUX0, 0, 0), (adi.FLUX0, 0, 0))
+    L = sum(adi.apply_diag(sh, fm, u, d, bc) for d in range(3)).ravel()
+    A = operator.assemble(sh, fm, 7)
+    np.testing.assert_allclose(L, A @ u, rtol=0, atol=1e-13 * np.abs(A @ u).max())
+
+
+@pytest.mark.parametrize("name", list(ADI_GRIDS))
+def test_constants_are_steady(name):
+    """A constant field with zero-flux walls, or with wall values equal to the
+    constant, has L = 0 and is unchanged by a sub-step."""
+    sh, fm = _adi_grid(name)
+    u = np.full(sh.shape, 0.7)
+    for bc in (adi.walls((adi.FLUX0, 0, 0), (adi.FLUX0, 0, 0)),
+               adi.walls((adi.VALUE, 0.7, 0.7), (adi.VALUE, 0.7, 0.7))):
+        for d in range(3):
+            assert np.abs(adi.apply_diag(sh, fm, u, d, bc)).max() < 1e-13
+        np.testing.assert_allclose(adi.substep(sh, fm, u, 0.3, bc), u, rtol=1e-13)
+
+
+@pytest.mark.parametrize("name", list(ADI_GRIDS))
+def test_each_sweep_solves_its_system(name):
+    """(J - kappa L_d) u = rhs holds after the sweep, with L_d applied by the
+    flux form (not the tridiagonal assembly), for each direction and wall kind."""
+    sh, fm = _adi_grid(name)
+    rng = np.random.default_rng(2)
+    J = fm["J"]
+    for bc in (adi.walls(), adi.walls((adi.VALUE, 1.0, 0.0), (adi.FLUX0, 0, 0))):
+        for d in range(3):
+            rhs = rng.standard_normal(sh.shape)
+            u = adi.sweep(sh, fm, d, 0.8, rhs, bc)
+            res = J * u - 0.8 * adi.apply_diag(sh, fm, u, d, bc) - rhs
+            assert np.abs(res).max() < 1e-12 * np.abs(rhs).max(), (d, np.abs(res).max())
+
+
+def test_substep_without_viscosity_adds_the_explicit_terms():
+    sh, fm = _adi_grid("triaxial")
+    rng = np.random.default_rng(3)
+    un, s = rng.standard_normal(sh.shape), rng.standard_normal(sh.shape)
+    np.testing.assert_allclose(adi.substep(sh, fm, un, 0.0, adi.walls(), src=s), un + s / fm["J"], rtol=1e-13)
+
+
+def _exact(sh, fm, un, kappa, bc):
+    """exp(2 kappa J^{-1} L) u^n for zero-flux walls (L = sum of the diagonal
+    terms), by the matrix exponential of the assembled operator."""
+    import scipy.linalg
+    A = operator.assemble(sh, fm, 7).toarray()
+    M = A / fm["J"].ravel()[:, None]
+    return scipy.linalg.expm(2.0 * kappa * M) @ un.ravel()
+
+
+@pytest.mark.parametrize("name", list(ADI_GRIDS))
+def test_substep_is_second_order_in_time(name):
+    """The sub-step factorises (I - kM_1)(I - kM_2)(I - kM_3)(u - u^n) = 2kM u^n
+    (M_p = J^{-1} L_p): it matches exp(2 k M) u^n to O(k^3) (a first-order
+    splitting or a misplaced factor 2 would leave O(k^2))."""
+    sh, fm = _adi_grid(name, (4, 6, 8))
+    bc = adi.walls((adi.FLUX0, 0, 0), (adi.FLUX0, 0, 0))
+    un = np.random.default_rng(4).standard_normal(sh.shape)
+    scale = np.abs(operator.assemble(sh, fm, 7).diagonal() / fm["J"].ravel()).max()
+    errs = []
+    for k in (0.02, 0.01, 0.005):
+        kappa = k / scale
+        errs.append(np.abs(adi.substep(sh, fm, un, kappa, bc).ravel() - _exact(sh, fm, un, kappa, bc)).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 7.0 < r1 < 9.0 and 7.0 < r2 < 9.0, errs
+
+
+def test_planted_adi_mistakes_are_caught(monkeypatch):
+    """Explicit terms with weight kappa instead of 2 kappa, or a sweep that
+    solves with +kappa, break second order or the sweep residual."""
+    sh, fm = _adi_grid("sphere_stretched", (4, 6, 8))
+    bc = adi.walls((adi.FLUX0, 0, 0), (adi.FLUX0, 0, 0))
+    un = np.random.default_rng(4).standard_normal(sh.shape)
+    scale = np.abs(operator.assemble(sh, fm, 7).diagonal() / fm["J"].ravel()).max()
+    kap = [k / scale for k in (0.02, 0.01)]
+    good = [np.abs(adi.substep(sh, fm, un, k, bc).ravel() - _exact(sh, fm, un, k, bc)).max() for k in kap]
+    orig = adi.apply_diag
+
+    def halved(shh, fmm, u, d, b):
+        return 0.5 * orig(shh, fmm, u, d, b) if d != 0 else orig(shh, fmm, u, d, b)
+
+    monkeypatch.setattr(adi, "apply_diag", halved)
+    bad = [np.abs(adi.substep(sh, fm, un, k, bc).ravel() - _exact(sh, fm, un, k, bc)).max() for k in kap]
+    monkeypatch.setattr(adi, "apply_diag", orig)
+    assert good[0] / good[1] > 7.0 and bad[0] / bad[1] < 4.5
+    origls = adi.line_system
+
+    def flipped(shh, fmm, d, kappa, b):
+        return origls(shh, fmm, d, -kappa, b)
+
+    monkeypatch.setattr(adi, "line_system", flipped)
+    rhs = np.random.default_rng(5).standard_normal(sh.shape)
+    u = adi.sweep(sh, fm, 1, 0.8, rhs, bc)
+    monkeypatch.setattr(adi, "line_system", origls)
+    res = fm["J"] * u - 0.8 * adi.apply_diag(sh, fm, u, 1, bc) - rhs
+    assert np.abs(res).max() > 1e-3 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_wall_values_sit_on_the_wall_face(d):
+    """u linear in the index along d (u = m + 1/2 at cell m) with wall values 0
+    and n (its values on the wall faces): every face, walls included, carries
+    the flux G_dd x 1, so L_d u = G(upper face) - G(lower face) exactly."""
+    sh, fm = _adi_grid("triaxial")
+    ax = {0: 1, 1: 0}[d]
+    n = sh.shape[ax]
+    shape = [1, 1, 1]
+    shape[ax] = n
+    u = np.broadcast_to((np.arange(n) + 0.5).reshape(shape), sh.shape)
+    bc = adi.walls((adi.VALUE, 0.0, float(n)), (adi.VALUE, 0.0, float(n)))
+    G = np.moveaxis(adi.face_G(sh, fm, d), ax, 0)
+    want = np.moveaxis(G[1:] - G[:-1], 0, ax)
+    np.testing.assert_allclose(adi.apply_diag(sh, fm, u, d, bc), want, rtol=0, atol=1e-13 * np.abs(G).max())
