@@ -436,6 +436,31 @@ def run_ours(args, rank, world, local_rank):
                                 "lines": L["n1"] * L["n2"], "n": L["n"]}
         del la, lb, lc, lg, lx, lw
 
+    # one ADI-CN sub-step of Section 3.4 (three implicit sweeps, Eqs.
+    # solve_2-solve_4) on this grid: diffusion number kappa G / J up to 10,
+    # no-slip walls; algorithmic bytes 136 per cell (u^n, s, J, three G read
+    # and u written in the first sweep; u, u^n, J, one G read and u written in
+    # each of the other two)
+    adi_step = None
+    if world == 1:
+        Jd = torch.empty(N, dtype=torch.float64, device="cuda")
+        mgs.mg_get_metric(h, 0, 9, Jd)
+        uo = torch.empty(N, dtype=torch.float64, device="cuda")
+        gmax = 0.0
+        for comp in (0, 4, 8):
+            mgs.mg_get_metric(h, 0, comp, uo)
+            gmax = max(gmax, uo.abs().max().item())
+        kappa = 10.0 * Jd.min().item() / gmax
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        un = torch.randn(N, generator=gen, device="cuda", dtype=torch.float64)
+        src = 0.01 * torch.randn(N, generator=gen, device="cuda", dtype=torch.float64) * Jd
+        mgs.mg_adi_substep(h, kappa, un, uo, src=src)
+        t = _ev_time(lambda: mgs.mg_adi_substep(h, kappa, un, uo, src=src))
+        gbs = 136.0 * N / (t * 1e-3) / 1e9
+        adi_step = {"ms": t, "alg_GBps": gbs, "frac": gbs / peaks()[0], "kappa": kappa,
+                    "note": "three FP64 line-solve sweeps (2 plain, 1 periodic), no-slip walls"}
+        del Jd, un, src, uo
+
     # plain FP64 multigrid on the same workload (the speedup reference)
     compare = None
     if not args.no_compare and prec != 0:
@@ -460,7 +485,7 @@ def run_ours(args, rank, world, local_rank):
         "rel_res": rep["rel_res"], "iters": rep["iters"],
         "roofline": roof, "kernels": kernels,
         "setup_s": t_setup, "schedule": mgs.mg_get_schedule(h), "pc_step": pc_step,
-        "line_solves": line_solves,
+        "line_solves": line_solves, "adi_substep": adi_step,
         "e2e": e2e,
         "gpu_launches": int(sum(r["launches"] for r in reps)),
         "clocks": clk, "fp64_mg": compare, "wall_s": wall,

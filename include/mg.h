@@ -350,6 +350,38 @@ mg_status mg_thomas(const mg_lines* lines, const double* a, const double* b, con
                     const double* g, double* x, double* work, int periodic, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The ADI-CN implicit viscous sweeps of Section 3.4 (Eqs. solve_2, solve_3,
+ * solve_4) for one cell-centred field (a velocity component or the
+ * temperature) on the handle's fine grid, FP64.  With kappa = (h/2)
+ * sqrt(Pr/Ra) (h the RKW3 sub-step) and L_p the diagonal viscous term of
+ * direction p (Eq. PC_term1 in flux form, the operator's G_pp faces):
+ *   (J - kappa L_zeta) u*   = J u^n + src + kappa L_zeta u^n + 2 kappa (L_eta + L_xi) u^n
+ *   (J - kappa L_eta)  u**  = J u*  - kappa L_eta u^n
+ *   (J - kappa L_xi)   u*** = J u** - kappa L_xi u^n          (periodic longitude)
+ * J = |J^{-1}| of the cell; src the caller's explicit terms (beta h times
+ * advection, cross diffusion, pressure and buoyancy), volume integrated like
+ * J u.  Each sweep is one tridiagonal system per grid line (Thomas; periodic
+ * Thomas in longitude), formed on the fly from the face metric.
+ * ------------------------------------------------------------------------- */
+enum { MG_WALL_FLUX0 = 0, MG_WALL_VALUE = 1 };
+typedef struct {
+    int radius;              /* MG_WALL_FLUX0 (zero flux) or MG_WALL_VALUE at the walls j = 0, j = nr */
+    int colatitude;          /* the same at the walls i = 0, i = nth */
+    double v_r_in, v_r_out;  /* MG_WALL_VALUE: the value on the wall face (half a cell from the
+                                centre; face flux 2 G_pp (u_w - u_c) outward) */
+    double v_th0, v_th1;
+} mg_walls;
+/* One sub-step: u = u*** from u^n.  un, src (may be NULL = 0) and u are
+ * device arrays of nr*nth*nph doubles, [nr][nth][nph], owned by the caller; u
+ * may not alias un or src.  walls NULL = no-slip (value 0 on all four walls).
+ * The first call on a handle computes G_pp of the wall faces and allocates
+ * 2 nr*nth*nph doubles of line work (freed with the handle).  Queued on the
+ * handle's stream order, not synchronised.  MG_EINVAL for null or aliased
+ * arrays, kappa < 0 or not finite, a bad wall kind or value. */
+mg_status mg_adi_substep(mg_handle* h, double kappa, const mg_walls* walls, const double* un,
+                         const double* src, double* u);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with
  * CUDA events on the handle's stream (a few events per V-cycle) and
  * accumulates their device time.  Slots: 0 = fine-level smoothing launches,

@@ -49,6 +49,11 @@ class mg_lines(C.Structure):
                 ("sm", C.c_longlong), ("s1", C.c_longlong), ("s2", C.c_longlong)]
 
 
+class mg_walls(C.Structure):
+    _fields_ = [("radius", C.c_int), ("colatitude", C.c_int), ("v_r_in", C.c_double), ("v_r_out", C.c_double),
+                ("v_th0", C.c_double), ("v_th1", C.c_double)]
+
+
 class mg_schedule(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("tail_level", C.c_int), ("tail_cluster", C.c_int),
                 ("one_pass_tiles", C.c_int), ("source", C.c_int), ("candidates", C.c_int),
@@ -114,6 +119,7 @@ _SIGS = {
     "mg_get_schedule": ([_vp, C.POINTER(mg_schedule)], _i),
     "mg_pc_rhs": ([_vp, _vp, _vp], _i),
     "mg_pc_correct": ([_vp, _vp, _vp], _i),
+    "mg_adi_substep": ([_vp, _d, C.POINTER(mg_walls), _vp, _vp, _vp], _i),
     "mg_thomas_work_bytes": ([C.POINTER(mg_lines), _i], C.c_size_t),
     "mg_thomas": ([C.POINTER(mg_lines), _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
@@ -349,6 +355,22 @@ def mg_thomas(lines: dict, a, b, c, g, x, periodic=False, work=None, stream=None
     _check(_lib.mg_thomas(C.byref(L), _ptr(a, "float64"), _ptr(b, "float64"), _ptr(c, "float64"),
                           _ptr(g, "float64"), _ptr(x, "float64"), _ptr(work, "float64"),
                           int(bool(periodic)), _stream(stream)), "mg_thomas")
+
+
+MG_WALL_FLUX0, MG_WALL_VALUE = 0, 1
+
+
+def mg_adi_substep(h: Handle, kappa, un, u, src=None, walls=None):
+    """ADI-CN sub-step of Section 3.4 (Eqs. solve_2 to solve_4): u = u*** from
+    un.  walls: dict of mg_walls fields, or None for no-slip."""
+    wp = None
+    if walls is not None:
+        w = mg_walls()
+        for k, v in walls.items():
+            setattr(w, k, v)
+        wp = C.byref(w)
+    _check(_lib.mg_adi_substep(h.ptr, float(kappa), wp, _ptr(un, "float64"), _ptr(src, "float64"),
+                               _ptr(u, "float64")), "mg_adi_substep")
 
 
 def mg_get_schedule(h: Handle) -> dict:

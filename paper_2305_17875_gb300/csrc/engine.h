@@ -69,6 +69,8 @@ struct mg_handle {
     mgs::MetricTables mtab{};         // vertex tables of the fine grid (device)
     double* pcC[27] = {};             // face C of the pressure-correction steps (on first use)
     double* pcInv[3] = {};            // 1 / |J^{-1}| of the faces
+    double* wallG[4] = {};            // G_dd on the wall planes (implicit sweeps, on first use)
+    double* adi_w = nullptr;          // line-solve work of the implicit sweeps (2 N doubles)
     bool prof_on = false;
     double prof_ms[MG_PROF_SLOTS] = {};
     long long prof_n[MG_PROF_SLOTS] = {};

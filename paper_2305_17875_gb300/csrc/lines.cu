@@ -27,15 +27,13 @@
 // of dp1 + dp2 psi_{n-1} gives psi = psi1 + psi2 psi_{n-1} (Eq. TAP4).
 //
 // FP64 arithmetic is the scarce resource here (one reciprocal and five
-// multiply-adds per row), so the reciprocal is Newton-Raphson iteration
-// r <- r + r (1 - v r) from the hardware's single-precision approximate
-// reciprocal (relative error below 2^-22, squared by each step: two steps
-// reach double precision, within an ulp of 1/v); values whose seed would
-// leave the single-precision range take an IEEE division instead.
+// multiply-adds per row), so the reciprocal is rcp64 (fp64.cuh: two Newton
+// steps from the single-precision approximate reciprocal).
 #include <algorithm>
 #include <string>
 
 #include "engine.h"
+#include "fp64.cuh"
 
 namespace mgs {
 namespace {
@@ -48,16 +46,6 @@ struct LineGeom {
     i64 n1, n2, nl;
     i64 sm, s1, s2;
 };
-
-__device__ __forceinline__ double rcp64(double v) {
-    const int e = (__double2hiint(v) >> 20) & 0x7ff;   // biased exponent
-    if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / v;
-    float s;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(__double2float_rn(v)));
-    double r = (double)s;
-    r = __fma_rn(r, __fma_rn(-v, r, 1.0), r);
-    return __fma_rn(r, __fma_rn(-v, r, 1.0), r);
-}
 
 __device__ __forceinline__ i64 line_base(const LineGeom& L, i64 line) {
     const i64 l1 = line / L.n2;

@@ -97,6 +97,32 @@ __global__ void k_face_metric(MetricTables t, Dims D, int stencil, double* g0,
     }
 }
 
+// G_dd on the four wall planes (Section 3.2 steps 1-5 at the wall faces):
+// radius walls j = 0 and j = nr ([nth][nph] each), colatitude walls i = 0 and
+// i = nth ([nr][nph] each).
+__global__ void k_wall_G(MetricTables t, Dims D, double* r_lo, double* r_hi, double* th_lo, double* th_hi) {
+    const i64 nr_w = (i64)D.nth * D.nph, nt_w = (i64)D.nr * D.nph;
+    double row[3];
+    for (i64 q = blockIdx.x * (i64)blockDim.x + threadIdx.x; q < nr_w + nt_w; q += (i64)gridDim.x * blockDim.x) {
+        if (q < nr_w) {
+            const int i = (int)(q / D.nph), k = (int)(q % D.nph);
+            const int vl[3] = {i, 0, k}, vh[3] = {i, D.nr, k};
+            face_metric(t, 1, vl, row);
+            r_lo[q] = row[1];
+            face_metric(t, 1, vh, row);
+            r_hi[q] = row[1];
+        } else {
+            const i64 p = q - nr_w;
+            const int j = (int)(p / D.nph), k = (int)(p % D.nph);
+            const int vl[3] = {0, j, k}, vh[3] = {D.nth, j, k};
+            face_metric(t, 0, vl, row);
+            th_lo[p] = row[0];
+            face_metric(t, 0, vh, row);
+            th_hi[p] = row[0];
+        }
+    }
+}
+
 // C and 1/|J^{-1}| of every cell's three lower faces: with a_p = col_{p+1} x
 // col_{p+2} (the cofactor columns of J^{-1}) and det = col_0 . a_0, the
 // inverse has rows a_p / det, so C row p = |det| a_p / det = sign(det) a_p.
@@ -371,6 +397,12 @@ cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsign
         if (lv.stencil == 19) k_line_factors<19, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
         else k_line_factors<7, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_G(const MetricTables& t, Dims D, double* const g[4], cudaStream_t s) {
+    const i64 n = (i64)D.nth * D.nph + (i64)D.nr * D.nph;
+    k_wall_G<<<grid_for(n, 128), 128, 0, s>>>(t, D, g[0], g[1], g[2], g[3]);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
-// pc.h - the steps either side of the pressure solve (Section 3.6): internal
-// interface between set-up (metric.cu) and the step kernels (pc.cu).
+// pc.h - the steps either side of the pressure solve (Section 3.6) and the
+// implicit viscous sweeps (Section 3.4): internal interface between set-up
+// (metric.cu) and the step kernels (pc.cu, adi.cu).
 #pragma once
 
 #include "mg_kernels.h"
@@ -12,5 +13,9 @@ namespace mgs {
 // 1 / |J^{-1}| of the face, 3 arrays.
 cudaError_t launch_face_C(const MetricTables& t, Dims D, double* const C[27], double* const inv_det[3],
                           cudaStream_t s);
+
+// G_dd on the wall planes: g[0], g[1] the radius walls j = 0 and j = nr
+// ([nth][nph]), g[2], g[3] the colatitude walls i = 0 and i = nth ([nr][nph]).
+cudaError_t launch_wall_G(const MetricTables& t, Dims D, double* const g[4], cudaStream_t s);
 
 }  // namespace mgs
