@@ -23,7 +23,6 @@
 #include <string>
 
 #include "engine.h"
-#include "fp64.cuh"
 #include "pc.h"
 
 namespace mgs {
@@ -52,21 +51,21 @@ template <int P>
 __device__ __forceinline__ void face_fluxes(const AdiArgs& A, const double* x, i64 c, int j, int i, int k,
                                             double& flo, double& fhi) {
     const Dims& D = A.D;
-    const double xc = x[c];
+    const double xc = __ldg(x + c);
     if constexpr (P == 2) {
         const i64 km = k == 0 ? c + D.nph - 1 : c - 1;
         const i64 kp = k == D.nph - 1 ? c - D.nph + 1 : c + 1;
-        flo = A.G[2][c] * (xc - x[km]);
-        fhi = A.G[2][kp] * (x[kp] - xc);
+        flo = __ldg(A.G[2] + c) * (xc - __ldg(x + km));
+        fhi = __ldg(A.G[2] + kp) * (__ldg(x + kp) - xc);
     } else {
         const int m = P == 0 ? i : j;
         const int n = P == 0 ? D.nth : D.nr;
         const i64 st = P == 0 ? (i64)D.nph : (i64)D.nth * D.nph;
         const i64 wi = P == 0 ? (i64)j * D.nph + k : (i64)i * D.nph + k;
-        if (m > 0) flo = A.G[P][c] * (xc - x[c - st]);
-        else flo = A.wall[P] ? 2.0 * A.wg[P][0][wi] * (xc - A.wv[P][0]) : 0.0;
-        if (m < n - 1) fhi = A.G[P][c + st] * (x[c + st] - xc);
-        else fhi = A.wall[P] ? 2.0 * A.wg[P][1][wi] * (A.wv[P][1] - xc) : 0.0;
+        if (m > 0) flo = __ldg(A.G[P] + c) * (xc - __ldg(x + c - st));
+        else flo = A.wall[P] ? 2.0 * __ldg(A.wg[P][0] + wi) * (xc - A.wv[P][0]) : 0.0;
+        if (m < n - 1) fhi = __ldg(A.G[P] + c + st) * (__ldg(x + c + st) - xc);
+        else fhi = A.wall[P] ? 2.0 * __ldg(A.wg[P][1] + wi) * (A.wv[P][1] - xc) : 0.0;
     }
 }
 
@@ -88,8 +87,8 @@ __device__ __forceinline__ void adi_row(const AdiArgs& A, i64 c, int j, int i, i
     double gw = 0.0;   // right-side term of the wall values
     if constexpr (P == 2) {
         const i64 kp = k == D.nph - 1 ? c - D.nph + 1 : c + 1;
-        glo = A.G[2][c];
-        ghi = A.G[2][kp];
+        glo = __ldg(A.G[2] + c);
+        ghi = __ldg(A.G[2] + kp);
         a = -kap * glo;
         cc = -kap * ghi;
     } else {
@@ -98,27 +97,27 @@ __device__ __forceinline__ void adi_row(const AdiArgs& A, i64 c, int j, int i, i
         const i64 st = P == 0 ? (i64)D.nph : (i64)D.nth * D.nph;
         const i64 wi = P == 0 ? (i64)j * D.nph + k : (i64)i * D.nph + k;
         if (m > 0) {
-            glo = A.G[P][c];
+            glo = __ldg(A.G[P] + c);
             a = -kap * glo;
         } else {
             a = 0.0;
-            glo = A.wall[P] ? 2.0 * A.wg[P][0][wi] : 0.0;
+            glo = A.wall[P] ? 2.0 * __ldg(A.wg[P][0] + wi) : 0.0;
             gw = __fma_rn(glo, A.wv[P][0], gw);
         }
         if (m < n - 1) {
-            ghi = A.G[P][c + st];
+            ghi = __ldg(A.G[P] + c + st);
             cc = -kap * ghi;
         } else {
             cc = 0.0;
-            ghi = A.wall[P] ? 2.0 * A.wg[P][1][wi] : 0.0;
+            ghi = A.wall[P] ? 2.0 * __ldg(A.wg[P][1] + wi) : 0.0;
             gw = __fma_rn(ghi, A.wv[P][1], gw);
         }
     }
-    const double Jc = A.J[c];
+    const double Jc = __ldg(A.J + c);
     b = __fma_rn(kap, glo + ghi, Jc);
     if constexpr (P == 0) {
-        double r = Jc * A.un[c];
-        if (A.src) r += A.src[c];
+        double r = Jc * __ldg(A.un + c);
+        if (A.src) r += __ldg(A.src + c);
         const double l0 = diag_term<0>(A, A.un, c, j, i, k);
         const double l12 = diag_term<1>(A, A.un, c, j, i, k) + diag_term<2>(A, A.un, c, j, i, k);
         r = __fma_rn(kap, l0, r);
@@ -163,12 +162,13 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
     };
     if constexpr (P < 2) {
         double cp = 0.0, dp = 0.0;
+#pragma unroll 4
         for (int m = 0; m < n; ++m) {
             int jj, ii, kk;
             const i64 c = at(m, jj, ii, kk);
             double a, b, cc, g;
             adi_row<P>(A, c, jj, ii, kk, a, b, cc, g);
-            const double r = rcp64(__fma_rn(-a, cp, b));
+            const double r = 1.0 / __fma_rn(-a, cp, b);
             cp = cc * r;
             dp = __dmul_rn(__fma_rn(-a, dp, g), r);
             u[c] = dp;
@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
         double* wcp = A.w;
         double* wd2 = A.w + (i64)nc * nl;
         double cp = 0.0, d1 = 0.0, d2 = 0.0, prod = 1.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll 4
         for (int m = 0; m < nc; ++m) {
             int jj, ii, kk;
             const i64 c = at(m, jj, ii, kk);
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
             adi_row<2>(A, c, jj, ii, kk, a, b, cc, g);
             const double am = m > 0 ? a : 0.0;
             const double em = (m == 0 ? -a : 0.0) + (m == nc - 1 ? -cc : 0.0);
-            const double r = rcp64(__fma_rn(-am, cp, b));
+            const double r = 1.0 / __fma_rn(-am, cp, b);
             cp = m < nc - 1 ? cc * r : 0.0;
             d1 = __dmul_rn(__fma_rn(-am, d1, g), r);
             d2 = __dmul_rn(__fma_rn(-am, d2, em), r);

@@ -368,7 +368,15 @@ mg_status time_schedule(mg_handle* h, const Schedule& sc, double* ms) {
     CKS(apply_schedule(h, sc));
     Plan* pl = nullptr;
     CKS(plan_create(&h, 1, &pl));
-    const mg_status st = plan_time(pl, 2, 5, ms);
+    // the least of three short runs: clock ramps and other tenants of the
+    // GPU only ever slow a run down
+    mg_status st = MG_OK;
+    *ms = 0.0;
+    for (int r = 0; r < 3 && st == MG_OK; ++r) {
+        double t = 0.0;
+        st = plan_time(pl, r == 0 ? 2 : 1, 4, &t);
+        if (st == MG_OK && (r == 0 || t < *ms)) *ms = t;
+    }
     plan_destroy(pl);
     return st;
 }
@@ -397,8 +405,10 @@ mg_status autotune(mg_handle* h) {
     int tried = 1;
     CKS(time_schedule(h, best, &best_ms));
     auto consider = [&](const Schedule& sc) -> mg_status {
-        double ms = 0.0;
+        double ms = 0.0, again = 0.0;
         CKS(time_schedule(h, sc, &ms));
+        CKS(time_schedule(h, best, &again));   // the incumbent timed beside it
+        best_ms = std::min(best_ms, again);
         ++tried;
         if (ms < 0.98 * best_ms) {   // a clear win only: timings carry noise
             best = sc;

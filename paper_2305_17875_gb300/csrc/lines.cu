@@ -26,14 +26,13 @@
 // so psi_{n-1} is known when the sweep ends and a single back substitution
 // of dp1 + dp2 psi_{n-1} gives psi = psi1 + psi2 psi_{n-1} (Eq. TAP4).
 //
-// FP64 arithmetic is the scarce resource here (one reciprocal and five
-// multiply-adds per row), so the reciprocal is rcp64 (fp64.cuh: two Newton
-// steps from the single-precision approximate reciprocal).
+// One IEEE division per row (the hardware's double-precision reciprocal
+// approximation plus refinement; a hand-rolled Newton reciprocal from the
+// single-precision one measured slower).
 #include <algorithm>
 #include <string>
 
 #include "engine.h"
-#include "fp64.cuh"
 
 namespace mgs {
 namespace {
@@ -80,7 +79,7 @@ __global__ void __launch_bounds__(kLT) k_thomas(LineGeom L, const double* __rest
         for (int u = 0; u < kU; ++u) {
             if (u < cnt) {
                 const int m = m0 + u;
-                const double r = rcp64(__fma_rn(-ra[u], cp, rb[u]));
+                const double r = 1.0 / __fma_rn(-ra[u], cp, rb[u]);
                 cp = rc[u] * r;
                 dp = __dmul_rn(__fma_rn(-ra[u], dp, rg[u]), r);
                 x[base + (i64)m * L.sm] = dp;
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(kLT) k_thomas_periodic(LineGeom L, const doubl
                 const int m = m0 + u;
                 const double am = m > 0 ? ra[u] : 0.0;            // a_0 is a corner, not in A_c
                 const double em = (m == 0 ? -ra[u] : 0.0) + (m == nc - 1 ? -rc[u] : 0.0);
-                const double r = rcp64(__fma_rn(-am, cp, rb[u]));
+                const double r = 1.0 / __fma_rn(-am, cp, rb[u]);
                 cp = m < nc - 1 ? rc[u] * r : 0.0;
                 d1 = __dmul_rn(__fma_rn(-am, d1, rg[u]), r);
                 d2 = __dmul_rn(__fma_rn(-am, d2, em), r);
