@@ -452,13 +452,20 @@ def run_ours(args, rank, world, local_rank):
             gmax = max(gmax, uo.abs().max().item())
         kappa = 10.0 * Jd.min().item() / gmax
         gen = torch.Generator(device="cuda").manual_seed(5)
-        un = torch.randn(N, generator=gen, device="cuda", dtype=torch.float64)
-        src = 0.01 * torch.randn(N, generator=gen, device="cuda", dtype=torch.float64) * Jd
+        un = [torch.randn(N, generator=gen, device="cuda", dtype=torch.float64) for _ in range(3)]
+        src = [0.01 * torch.randn(N, generator=gen, device="cuda", dtype=torch.float64) * Jd for _ in range(3)]
+        uo = [uo] + [torch.empty_like(uo) for _ in range(2)]
+        mgs.mg_adi_substep(h, kappa, un[0], uo[0], src=src[0])
+        t1 = _ev_time(lambda: mgs.mg_adi_substep(h, kappa, un[0], uo[0], src=src[0]))
         mgs.mg_adi_substep(h, kappa, un, uo, src=src)
-        t = _ev_time(lambda: mgs.mg_adi_substep(h, kappa, un, uo, src=src))
-        gbs = 136.0 * N / (t * 1e-3) / 1e9
-        adi_step = {"ms": t, "alg_GBps": gbs, "frac": gbs / peaks()[0], "kappa": kappa,
-                    "note": "three FP64 line-solve sweeps (2 plain, 1 periodic), no-slip walls"}
+        t3 = _ev_time(lambda: mgs.mg_adi_substep(h, kappa, un, uo, src=src))
+        gbs = 136.0 * N / (t1 * 1e-3) / 1e9
+        gbs3 = 3 * 136.0 * N / (t3 * 1e-3) / 1e9
+        adi_step = {"ms": t1, "alg_GBps": gbs, "frac": gbs / peaks()[0],
+                    "ms_3_fields": t3, "alg_GBps_3_fields": gbs3, "frac_3_fields": gbs3 / peaks()[0],
+                    "kappa": kappa,
+                    "note": "three FP64 line-solve sweeps (2 plain, 1 periodic), no-slip walls; one field, "
+                            "and the three velocity components in one call"}
         del Jd, un, src, uo
 
     # plain FP64 multigrid on the same workload (the speedup reference)

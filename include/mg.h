@@ -371,15 +371,19 @@ typedef struct {
                                 centre; face flux 2 G_pp (u_w - u_c) outward) */
     double v_th0, v_th1;
 } mg_walls;
-/* One sub-step: u = u*** from u^n.  un, src (may be NULL = 0) and u are
- * device arrays of nr*nth*nph doubles, [nr][nth][nph], owned by the caller; u
- * may not alias un or src.  walls NULL = no-slip (value 0 on all four walls).
+/* One sub-step of `nfields` fields with the same kappa: u[f] = u*** from
+ * un[f].  un[f], src[f] and u[f] are device arrays of nr*nth*nph doubles,
+ * [nr][nth][nph], owned by the caller; src may be NULL (no explicit terms), as
+ * may any src[f]; no u[f] may alias another array.  walls: NULL = no-slip
+ * (value 0 on all four walls), else nfields entries whose kinds agree (the
+ * fields share the matrices: one division per row serves up to four fields,
+ * as the three velocity components of a sub-step); values may differ.
  * The first call on a handle computes G_pp of the wall faces and allocates
  * 2 nr*nth*nph doubles of line work (freed with the handle).  Queued on the
  * handle's stream order, not synchronised.  MG_EINVAL for null or aliased
- * arrays, kappa < 0 or not finite, a bad wall kind or value. */
-mg_status mg_adi_substep(mg_handle* h, double kappa, const mg_walls* walls, const double* un,
-                         const double* src, double* u);
+ * arrays, nfields < 1, kappa < 0 or not finite, a bad wall kind or value. */
+mg_status mg_adi_substep(mg_handle* h, double kappa, int nfields, const mg_walls* walls,
+                         const double* const* un, const double* const* src, double* const* u);
 
 /* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with

@@ -119,7 +119,7 @@ _SIGS = {
     "mg_get_schedule": ([_vp, C.POINTER(mg_schedule)], _i),
     "mg_pc_rhs": ([_vp, _vp, _vp], _i),
     "mg_pc_correct": ([_vp, _vp, _vp], _i),
-    "mg_adi_substep": ([_vp, _d, C.POINTER(mg_walls), _vp, _vp, _vp], _i),
+    "mg_adi_substep": ([_vp, _d, _i, C.POINTER(mg_walls), _vp, _vp, _vp], _i),
     "mg_thomas_work_bytes": ([C.POINTER(mg_lines), _i], C.c_size_t),
     "mg_thomas": ([C.POINTER(mg_lines), _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
@@ -362,15 +362,25 @@ MG_WALL_FLUX0, MG_WALL_VALUE = 0, 1
 
 def mg_adi_substep(h: Handle, kappa, un, u, src=None, walls=None):
     """ADI-CN sub-step of Section 3.4 (Eqs. solve_2 to solve_4): u = u*** from
-    un.  walls: dict of mg_walls fields, or None for no-slip."""
+    un.  un, u (and src) are one device tensor or equal-length lists of them
+    (fields sharing kappa and wall kinds); walls: None for no-slip, a dict of
+    mg_walls fields, or one dict per field."""
+    many = isinstance(un, (list, tuple))
+    uns, us = (list(un), list(u)) if many else ([un], [u])
+    n = len(uns)
+    srcs = (list(src) if many else [src]) if src is not None else None
     wp = None
     if walls is not None:
-        w = mg_walls()
-        for k, v in walls.items():
-            setattr(w, k, v)
-        wp = C.byref(w)
-    _check(_lib.mg_adi_substep(h.ptr, float(kappa), wp, _ptr(un, "float64"), _ptr(src, "float64"),
-                               _ptr(u, "float64")), "mg_adi_substep")
+        wl = walls if isinstance(walls, (list, tuple)) else [walls] * n
+        W = (mg_walls * n)()
+        for f, d in enumerate(wl):
+            for k, v in d.items():
+                setattr(W[f], k, v)
+        wp = W
+    UN = (C.c_void_p * n)(*[_ptr(t, "float64") for t in uns])
+    U = (C.c_void_p * n)(*[_ptr(t, "float64") for t in us])
+    S = (C.c_void_p * n)(*[_ptr(t, "float64") for t in srcs]) if srcs is not None else None
+    _check(_lib.mg_adi_substep(h.ptr, float(kappa), n, wp, UN, S, U), "mg_adi_substep")
 
 
 def mg_get_schedule(h: Handle) -> dict:

@@ -11,6 +11,9 @@
 // of its tridiagonal system from the face metric (G_pp of the row's two faces,
 // J) and the stencil of u^n, then eliminates as it goes (normalised Thomas,
 // cp kept in a work array laid out [row][line]) and back-substitutes into u.
+// Up to four fields with the same kappa and wall kinds (the three velocity
+// components) share the matrix: one division per row serves all of them, and
+// their independent recurrences fill the FP64 pipeline of a thread.
 // Colatitude and radius lines are adjacent in memory along longitude, so
 // their loads coalesce; longitude lines are contiguous (one thread walks a
 // run of consecutive cells).  Right sides read only the line's own cell of
@@ -19,6 +22,7 @@
 // Walls: zero flux, or a value held on the wall face half a cell from the
 // centre, whose face flux is 2 G_pp(wall face) (u_w - u_c) outward; G_pp of
 // the wall faces comes from the face metric (k_wall_G).
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -29,29 +33,33 @@ namespace mgs {
 namespace {
 
 constexpr int kAT = 128;
+constexpr int kMaxF = 4;    // fields per launch (the three velocity components share one matrix)
+
+unsigned adi_blocks(i64 lines) { return (unsigned)((lines + kAT - 1) / kAT); }
 
 struct AdiArgs {
     Dims D;
     const double* G[3];     // G_pp on the lower p-face of every cell (0 on lower walls)
     const double* J;
-    const double* un;
-    const double* src;      // may be null
-    double* u;              // result; input of the eta and xi sweeps
+    const double* un[kMaxF];
+    const double* src[kMaxF];   // may be null
+    double* u[kMaxF];           // result; input of the eta and xi sweeps
     double* w;              // 2 N doubles of line-solve work
     double kappa;
     int wall[2];            // per direction 0 (colatitude), 1 (radius): 1 = value, 0 = zero flux
-    double wv[2][2];        // wall values [direction][lower, upper]
+    double wv[kMaxF][2][2]; // wall values [field][direction][lower, upper]
     const double* wg[2][2]; // wall-face G_pp [direction][lower, upper]: colatitude [nr][nph], radius [nth][nph]
 };
 
 // Fluxes of direction p through the lower and upper faces of cell (j, i, k)
-// for the field x: interior faces G (x_up - x_down); value walls
+// for field f of u^n: interior faces G (x_up - x_down); value walls
 // 2 G_w (x_c - x_w) (lower) and 2 G_w (x_w - x_c) (upper); zero-flux walls 0.
 template <int P>
-__device__ __forceinline__ void face_fluxes(const AdiArgs& A, const double* x, i64 c, int j, int i, int k,
-                                            double& flo, double& fhi) {
+__device__ __forceinline__ double diag_term(const AdiArgs& A, int f, i64 c, int j, int i, int k) {
     const Dims& D = A.D;
+    const double* x = A.un[f];
     const double xc = __ldg(x + c);
+    double flo, fhi;
     if constexpr (P == 2) {
         const i64 km = k == 0 ? c + D.nph - 1 : c - 1;
         const i64 kp = k == D.nph - 1 ? c - D.nph + 1 : c + 1;
@@ -63,28 +71,23 @@ __device__ __forceinline__ void face_fluxes(const AdiArgs& A, const double* x, i
         const i64 st = P == 0 ? (i64)D.nph : (i64)D.nth * D.nph;
         const i64 wi = P == 0 ? (i64)j * D.nph + k : (i64)i * D.nph + k;
         if (m > 0) flo = __ldg(A.G[P] + c) * (xc - __ldg(x + c - st));
-        else flo = A.wall[P] ? 2.0 * __ldg(A.wg[P][0] + wi) * (xc - A.wv[P][0]) : 0.0;
+        else flo = A.wall[P] ? 2.0 * __ldg(A.wg[P][0] + wi) * (xc - A.wv[f][P][0]) : 0.0;
         if (m < n - 1) fhi = __ldg(A.G[P] + c + st) * (__ldg(x + c + st) - xc);
-        else fhi = A.wall[P] ? 2.0 * __ldg(A.wg[P][1] + wi) * (A.wv[P][1] - xc) : 0.0;
+        else fhi = A.wall[P] ? 2.0 * __ldg(A.wg[P][1] + wi) * (A.wv[f][P][1] - xc) : 0.0;
     }
-}
-
-template <int P>
-__device__ __forceinline__ double diag_term(const AdiArgs& A, const double* x, i64 c, int j, int i, int k) {
-    double flo, fhi;
-    face_fluxes<P>(A, x, c, j, i, k, flo, fhi);
     return fhi - flo;
 }
 
-// Row of the sweep along direction P at cell (j, i, k): a (lower neighbour),
-// b, cc (upper neighbour), g (right side).
-template <int P>
+// Row of the sweep along direction P at cell (j, i, k): the matrix entries a
+// (lower neighbour), b, cc (upper neighbour), shared by the fields, and the
+// right side g[f] of each field.
+template <int P, int NF>
 __device__ __forceinline__ void adi_row(const AdiArgs& A, i64 c, int j, int i, int k, double& a, double& b,
-                                        double& cc, double& g) {
+                                        double& cc, double g[NF]) {
     const Dims& D = A.D;
     const double kap = A.kappa;
-    double glo, ghi;   // face coefficients of the implicit part
-    double gw = 0.0;   // right-side term of the wall values
+    double glo, ghi;          // face coefficients of the implicit part
+    double gwl = 0.0, gwh = 0.0;   // wall-face coefficients of value walls
     if constexpr (P == 2) {
         const i64 kp = k == D.nph - 1 ? c - D.nph + 1 : c + 1;
         glo = __ldg(A.G[2] + c);
@@ -102,7 +105,7 @@ __device__ __forceinline__ void adi_row(const AdiArgs& A, i64 c, int j, int i, i
         } else {
             a = 0.0;
             glo = A.wall[P] ? 2.0 * __ldg(A.wg[P][0] + wi) : 0.0;
-            gw = __fma_rn(glo, A.wv[P][0], gw);
+            gwl = glo;
         }
         if (m < n - 1) {
             ghi = __ldg(A.G[P] + c + st);
@@ -110,26 +113,31 @@ __device__ __forceinline__ void adi_row(const AdiArgs& A, i64 c, int j, int i, i
         } else {
             cc = 0.0;
             ghi = A.wall[P] ? 2.0 * __ldg(A.wg[P][1] + wi) : 0.0;
-            gw = __fma_rn(ghi, A.wv[P][1], gw);
+            gwh = ghi;
         }
     }
     const double Jc = __ldg(A.J + c);
     b = __fma_rn(kap, glo + ghi, Jc);
-    if constexpr (P == 0) {
-        double r = Jc * __ldg(A.un + c);
-        if (A.src) r += __ldg(A.src + c);
-        const double l0 = diag_term<0>(A, A.un, c, j, i, k);
-        const double l12 = diag_term<1>(A, A.un, c, j, i, k) + diag_term<2>(A, A.un, c, j, i, k);
-        r = __fma_rn(kap, l0, r);
-        r = __fma_rn(2.0 * kap, l12, r);
-        g = __fma_rn(kap, gw, r);
-    } else {
-        const double l = diag_term<P>(A, A.un, c, j, i, k);
-        g = __fma_rn(kap, gw, __fma_rn(-kap, l, Jc * A.u[c]));
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        double gw = 0.0;   // right-side term of the wall values
+        if constexpr (P < 2) gw = __fma_rn(gwh, A.wv[f][P][1], gwl * A.wv[f][P][0]);
+        if constexpr (P == 0) {
+            double r = Jc * __ldg(A.un[f] + c);
+            if (A.src[f]) r += __ldg(A.src[f] + c);
+            const double l0 = diag_term<0>(A, f, c, j, i, k);
+            const double l12 = diag_term<1>(A, f, c, j, i, k) + diag_term<2>(A, f, c, j, i, k);
+            r = __fma_rn(kap, l0, r);
+            r = __fma_rn(2.0 * kap, l12, r);
+            g[f] = __fma_rn(kap, gw, r);
+        } else {
+            const double l = diag_term<P>(A, f, c, j, i, k);
+            g[f] = __fma_rn(kap, gw, __fma_rn(-kap, l, Jc * A.u[f][c]));
+        }
     }
 }
 
-template <int P>
+template <int P, int NF>
 __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
     const Dims& D = A.D;
     const i64 line = blockIdx.x * (i64)kAT + threadIdx.x;
@@ -153,7 +161,6 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
         i = (int)(line - (i64)j * D.nth);
         base = line * D.nph;
     }
-    double* u = A.u;
     auto at = [&](int m, int& jj, int& ii, int& kk) {
         jj = P == 1 ? m : j;
         ii = P == 0 ? m : i;
@@ -161,69 +168,101 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
         return base + (i64)m * sm;
     };
     if constexpr (P < 2) {
-        double cp = 0.0, dp = 0.0;
-#pragma unroll 4
+        double cp = 0.0, dp[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dp[f] = 0.0;
+#pragma unroll 2
         for (int m = 0; m < n; ++m) {
             int jj, ii, kk;
             const i64 c = at(m, jj, ii, kk);
-            double a, b, cc, g;
-            adi_row<P>(A, c, jj, ii, kk, a, b, cc, g);
+            double a, b, cc, g[NF];
+            adi_row<P, NF>(A, c, jj, ii, kk, a, b, cc, g);
             const double r = 1.0 / __fma_rn(-a, cp, b);
             cp = cc * r;
-            dp = __dmul_rn(__fma_rn(-a, dp, g), r);
-            u[c] = dp;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                dp[f] = __dmul_rn(__fma_rn(-a, dp[f], g[f]), r);
+                A.u[f][c] = dp[f];
+            }
             if (m < n - 1) A.w[(i64)m * nl + line] = cp;
         }
-        double psi = dp;
+        double psi[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) psi[f] = dp[f];
         for (int m = n - 2; m >= 0; --m) {
             const i64 c = base + (i64)m * sm;
-            psi = __fma_rn(-A.w[(i64)m * nl + line], psi, u[c]);
-            u[c] = psi;
+            const double cpm = A.w[(i64)m * nl + line];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                psi[f] = __fma_rn(-cpm, psi[f], A.u[f][c]);
+                A.u[f][c] = psi[f];
+            }
         }
     } else {
-        // periodic (Eqs. TAP2-TAP8): psi1, psi2 on the leading block share cp;
+        // periodic (Eqs. TAP2-TAP8): psi1 (one per field) and psi2 (shared:
+        // it depends on the matrix only) on the leading block share cp;
         // psi1_0, psi2_0 summed during the sweep (see lines.cu)
         const int nc = n - 1;
         double* wcp = A.w;
         double* wd2 = A.w + (i64)nc * nl;
-        double cp = 0.0, d1 = 0.0, d2 = 0.0, prod = 1.0, s1 = 0.0, s2 = 0.0;
-#pragma unroll 4
+        double cp = 0.0, d2 = 0.0, prod = 1.0, s2 = 0.0, d1[NF], s1[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) d1[f] = s1[f] = 0.0;
+#pragma unroll 2
         for (int m = 0; m < nc; ++m) {
             int jj, ii, kk;
             const i64 c = at(m, jj, ii, kk);
-            double a, b, cc, g;
-            adi_row<2>(A, c, jj, ii, kk, a, b, cc, g);
+            double a, b, cc, g[NF];
+            adi_row<2, NF>(A, c, jj, ii, kk, a, b, cc, g);
             const double am = m > 0 ? a : 0.0;
             const double em = (m == 0 ? -a : 0.0) + (m == nc - 1 ? -cc : 0.0);
             const double r = 1.0 / __fma_rn(-am, cp, b);
             cp = m < nc - 1 ? cc * r : 0.0;
-            d1 = __dmul_rn(__fma_rn(-am, d1, g), r);
             d2 = __dmul_rn(__fma_rn(-am, d2, em), r);
-            s1 = __fma_rn(prod, d1, s1);
             s2 = __fma_rn(prod, d2, s2);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                d1[f] = __dmul_rn(__fma_rn(-am, d1[f], g[f]), r);
+                s1[f] = __fma_rn(prod, d1[f], s1[f]);
+                A.u[f][c] = d1[f];
+            }
             prod = -prod * cp;
-            u[c] = d1;
             wd2[(i64)m * nl + line] = d2;
             if (m < nc - 1) wcp[(i64)m * nl + line] = cp;
         }
         int jj, ii, kk;
         const i64 cl = at(nc, jj, ii, kk);
-        double al, bl, cl_, gl;
-        adi_row<2>(A, cl, jj, ii, kk, al, bl, cl_, gl);
-        const double last = __fma_rn(-al, d1, __fma_rn(-cl_, s1, gl)) / __fma_rn(al, d2, __fma_rn(cl_, s2, bl));
-        u[cl] = last;
-        double psi = __fma_rn(d2, last, d1);
-        u[base + (i64)(nc - 1) * sm] = psi;
+        double al, bl, cl_, gl[NF];
+        adi_row<2, NF>(A, cl, jj, ii, kk, al, bl, cl_, gl);
+        const double rden = 1.0 / __fma_rn(al, d2, __fma_rn(cl_, s2, bl));
+        double last[NF], psi[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            last[f] = __dmul_rn(__fma_rn(-al, d1[f], __fma_rn(-cl_, s1[f], gl[f])), rden);
+            A.u[f][cl] = last[f];
+            psi[f] = __fma_rn(d2, last[f], d1[f]);
+            A.u[f][base + (i64)(nc - 1) * sm] = psi[f];
+        }
         for (int m = nc - 2; m >= 0; --m) {
             const i64 c = base + (i64)m * sm;
-            const double dm = __fma_rn(wd2[(i64)m * nl + line], last, u[c]);
-            psi = __fma_rn(-wcp[(i64)m * nl + line], psi, dm);
-            u[c] = psi;
+            const double d2m = wd2[(i64)m * nl + line], cpm = wcp[(i64)m * nl + line];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const double dm = __fma_rn(d2m, last[f], A.u[f][c]);
+                psi[f] = __fma_rn(-cpm, psi[f], dm);
+                A.u[f][c] = psi[f];
+            }
         }
     }
 }
 
-unsigned adi_blocks(i64 lines) { return (unsigned)((lines + kAT - 1) / kAT); }
+template <int NF>
+void launch_sweeps(const AdiArgs& A, cudaStream_t s) {
+    const Dims& D = A.D;
+    k_adi<0, NF><<<adi_blocks((i64)D.nr * D.nph), kAT, 0, s>>>(A);
+    k_adi<1, NF><<<adi_blocks((i64)D.nth * D.nph), kAT, 0, s>>>(A);
+    k_adi<2, NF><<<adi_blocks((i64)D.nr * D.nth), kAT, 0, s>>>(A);
+}
 
 mg_status ensure_adi(mg_handle* h) {
     if (h->adi_w) return MG_OK;
@@ -249,21 +288,27 @@ mg_status ensure_adi(mg_handle* h) {
 
 using namespace mgs;
 
-extern "C" mg_status mg_adi_substep(mg_handle* h, double kappa, const mg_walls* walls, const double* un,
-                                    const double* src, double* u) {
-    if (!h || !un || !u || un == u || src == u || !(kappa >= 0.0) || !std::isfinite(kappa)) {
-        set_error("mg_adi_substep: null or aliased array, or kappa not finite and >= 0");
+extern "C" mg_status mg_adi_substep(mg_handle* h, double kappa, int nfields, const mg_walls* walls,
+                                    const double* const* un, const double* const* src, double* const* u) {
+    if (!h || nfields < 1 || !un || !u || !(kappa >= 0.0) || !std::isfinite(kappa)) {
+        set_error("mg_adi_substep: null handle or arrays, nfields < 1, or kappa not finite and >= 0");
         return MG_EINVAL;
     }
-    mg_walls wl{};
-    wl.radius = wl.colatitude = MG_WALL_VALUE;   // no-slip (u = 0) by default
-    if (walls) wl = *walls;
-    const bool ok_kind = (wl.radius == MG_WALL_FLUX0 || wl.radius == MG_WALL_VALUE) &&
-                         (wl.colatitude == MG_WALL_FLUX0 || wl.colatitude == MG_WALL_VALUE);
-    if (!ok_kind || !std::isfinite(wl.v_r_in) || !std::isfinite(wl.v_r_out) || !std::isfinite(wl.v_th0) ||
-        !std::isfinite(wl.v_th1)) {
-        set_error("mg_adi_substep: bad wall kind or value");
-        return MG_EINVAL;
+    for (int f = 0; f < nfields; ++f) {
+        bool bad = !un[f] || !u[f];
+        for (int e = 0; e < nfields && !bad; ++e) bad = u[f] == un[e] || (src && u[f] == src[e]) || (e != f && u[f] == u[e]);
+        const mg_walls* w = walls ? &walls[f] : nullptr;
+        if (w) {
+            bad = bad || !(w->radius == MG_WALL_FLUX0 || w->radius == MG_WALL_VALUE) ||
+                  !(w->colatitude == MG_WALL_FLUX0 || w->colatitude == MG_WALL_VALUE) ||
+                  !std::isfinite(w->v_r_in) || !std::isfinite(w->v_r_out) || !std::isfinite(w->v_th0) ||
+                  !std::isfinite(w->v_th1) || w->radius != walls[0].radius || w->colatitude != walls[0].colatitude;
+        }
+        if (bad) {
+            set_error("mg_adi_substep: field " + std::to_string(f) +
+                      ": null or aliased array, or a bad wall kind or value (kinds must agree across fields)");
+            return MG_EINVAL;
+        }
     }
     if (cudaEventRecord(h->ev_in, h->user_stream) != cudaSuccess ||
         cudaStreamWaitEvent(h->stream, h->ev_in, 0) != cudaSuccess) {
@@ -273,38 +318,49 @@ extern "C" mg_status mg_adi_substep(mg_handle* h, double kappa, const mg_walls* 
     mg_status st = ensure_adi(h);
     if (st != MG_OK) return st;
     const Level& L0 = h->L[0];
-    const Dims& D = L0.D;
     AdiArgs A{};
-    A.D = D;
+    A.D = L0.D;
     A.G[0] = L0.g64[0];
     A.G[1] = L0.g64[4];
     A.G[2] = L0.g64[8];
     A.J = h->J64;
-    A.un = un;
-    A.src = src;
-    A.u = u;
     A.w = h->adi_w;
     A.kappa = kappa;
-    A.wall[0] = wl.colatitude;
-    A.wall[1] = wl.radius;
-    A.wv[0][0] = wl.v_th0;
-    A.wv[0][1] = wl.v_th1;
-    A.wv[1][0] = wl.v_r_in;
-    A.wv[1][1] = wl.v_r_out;
+    A.wall[0] = walls ? walls[0].colatitude : MG_WALL_VALUE;   // no-slip (value 0) by default
+    A.wall[1] = walls ? walls[0].radius : MG_WALL_VALUE;
     A.wg[0][0] = h->wallG[2];
     A.wg[0][1] = h->wallG[3];
     A.wg[1][0] = h->wallG[0];
     A.wg[1][1] = h->wallG[1];
-    k_adi<0><<<adi_blocks((i64)D.nr * D.nph), kAT, 0, h->stream>>>(A);
-    k_adi<1><<<adi_blocks((i64)D.nth * D.nph), kAT, 0, h->stream>>>(A);
-    k_adi<2><<<adi_blocks((i64)D.nr * D.nth), kAT, 0, h->stream>>>(A);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    for (int f0 = 0; f0 < nfields && e == cudaSuccess; f0 += kMaxF) {
+        const int nf = std::min(kMaxF, nfields - f0);
+        for (int q = 0; q < nf; ++q) {
+            const int f = f0 + q;
+            A.un[q] = un[f];
+            A.src[q] = src ? src[f] : nullptr;
+            A.u[q] = u[f];
+            if (walls) {
+                A.wv[q][0][0] = walls[f].v_th0;
+                A.wv[q][0][1] = walls[f].v_th1;
+                A.wv[q][1][0] = walls[f].v_r_in;
+                A.wv[q][1][1] = walls[f].v_r_out;
+            } else {
+                A.wv[q][0][0] = A.wv[q][0][1] = A.wv[q][1][0] = A.wv[q][1][1] = 0.0;
+            }
+        }
+        if (nf == 1) launch_sweeps<1>(A, h->stream);
+        else if (nf == 2) launch_sweeps<2>(A, h->stream);
+        else if (nf == 3) launch_sweeps<3>(A, h->stream);
+        else launch_sweeps<4>(A, h->stream);
+        e = cudaGetLastError();
+        h->launches += 3;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_out, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->user_stream, h->ev_out, 0);
     if (e != cudaSuccess) {
         set_error(std::string("mg_adi_substep: ") + cudaGetErrorString(e));
         return MG_ECUDA;
     }
-    h->launches += 3;
     return MG_OK;
 }

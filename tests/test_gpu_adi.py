@@ -57,6 +57,39 @@ def test_substep_matches_oracle(lib, name, walls):
                                    err_msg=f"kappa {kappa}")
 
 
+@pytest.mark.parametrize("name", list(AGRIDS))
+def test_three_fields_share_the_matrix(lib, name):
+    """Three fields in one call (one launch per sweep, shared rows and
+    divisions) with their own wall values: each equals the oracle's sub-step
+    of that field, and the single-field call gives the same bits."""
+    import torch
+    g = AGRIDS[name]
+    sh = grid.shell(g)
+    fm = grid.face_metrics(sh)
+    h = lib.mg_setup(g, dict(precision=1))
+    rng = np.random.default_rng(51)
+    uns = [rng.standard_normal(sh.shape) for _ in range(3)]
+    srcs = [0.1 * rng.standard_normal(sh.shape) * fm["J"] for _ in range(3)]
+    vals = [(0.0, 0.0, 0.0, 0.0), (0.2, -0.1, 0.05, 0.3), (1.0, 0.0, -0.5, 0.5)]
+    wg = [dict(radius=1, colatitude=1, v_r_in=a, v_r_out=b, v_th0=c, v_th1=d) for a, b, c, d in vals]
+    kappa = 1.0 / (np.abs(fm["G1"][..., 1]).max() / fm["J"].min())
+    outs = [torch.empty(sh.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    lib.mg_adi_substep(h, kappa, [_dev(x) for x in uns], outs, src=[_dev(x) for x in srcs], walls=wg)
+    for f in range(3):
+        a, b, c, d = vals[f]
+        want = adi.substep(sh, fm, uns[f], kappa, adi.walls((adi.VALUE, a, b), (adi.VALUE, c, d)), src=srcs[f])
+        np.testing.assert_allclose(outs[f].cpu().numpy(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+        one = torch.empty_like(outs[f])
+        lib.mg_adi_substep(h, kappa, _dev(uns[f]), one, src=_dev(srcs[f]), walls=wg[f])
+        assert torch.equal(one, outs[f])
+    # five fields: two launches of sweeps (four, then one)
+    five = [torch.empty(sh.shape, dtype=torch.float64, device="cuda") for _ in range(5)]
+    lib.mg_adi_substep(h, kappa, [_dev(uns[f % 3]) for f in range(5)], five)
+    ref = torch.empty_like(five[0])
+    lib.mg_adi_substep(h, kappa, _dev(uns[1]), ref)
+    assert torch.equal(five[4], ref)
+
+
 def test_substep_rejects_bad_arguments(lib):
     import torch
     g = AGRIDS["triaxial"]
@@ -69,6 +102,9 @@ def test_substep_rejects_bad_arguments(lib):
         assert e.value.status == lib.MG_EINVAL
     with pytest.raises(lib.MGError):
         lib.mg_adi_substep(h, 1.0, x, x)       # u aliasing un
+    with pytest.raises(lib.MGError):          # wall kinds differ between fields
+        lib.mg_adi_substep(h, 1.0, [x, x.clone()], [x.clone(), x.clone()],
+                           walls=[dict(radius=1, colatitude=1), dict(radius=0, colatitude=1)])
 
 
 def test_bench_size_properties(lib):
