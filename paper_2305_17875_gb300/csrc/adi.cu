@@ -137,8 +137,101 @@ __device__ __forceinline__ void adi_row(const AdiArgs& A, i64 c, int j, int i, i
     }
 }
 
+// Colatitude and radius sweeps: two threads per line (adjacent lanes) eliminate
+// from both ends towards the middle row p = n / 2 (a twisted factorisation:
+// top-down x_m = dp_m - cp_m x_{m+1} above, bottom-up x_m = ep_m - ap_m x_{m-1}
+// below), exchange their last pivots by a lane shuffle, both solve row p, and
+// substitute outwards; the sequential chain is half the line, the thread
+// count twice the line count.
+template <int P, int NF>
+__global__ void __launch_bounds__(kAT) k_adi2(AdiArgs A) {
+    static_assert(P < 2, "two-way sweeps are for the walled directions");
+    const Dims& D = A.D;
+    const i64 nl = P == 0 ? (i64)D.nr * D.nph : (i64)D.nth * D.nph;
+    const i64 line = (blockIdx.x * (i64)kAT + threadIdx.x) >> 1;
+    const int side = threadIdx.x & 1;   // 0: rows 0 .. p-1 downwards; 1: rows n-1 .. p+1 upwards
+    const bool live = line < nl;        // both lanes of a pair share it; every lane reaches the shuffles
+    const int n = P == 0 ? D.nth : D.nr;
+    const int p = n >> 1;
+    const i64 sm = P == 0 ? (i64)D.nph : (i64)D.nth * D.nph;
+    int j = 0, i = 0, k = 0;
+    i64 base = 0;
+    if (live) {
+        if (P == 0) {
+            j = (int)(line / D.nph);
+            k = (int)(line - (i64)j * D.nph);
+            base = (i64)j * D.nth * D.nph + k;
+        } else {
+            i = (int)(line / D.nph);
+            k = (int)(line - (i64)i * D.nph);
+            base = (i64)i * D.nph + k;
+        }
+    }
+    auto at = [&](int m, int& jj, int& ii, int& kk) {
+        jj = P == 1 ? m : j;
+        ii = P == 0 ? m : i;
+        kk = k;
+        return base + (i64)m * sm;
+    };
+    // elimination towards row p: q = cp (top) or ap (bottom), d[f] = dp or ep
+    double q = 0.0, d[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) d[f] = 0.0;
+    const int cnt = live ? (side == 0 ? p : n - 1 - p) : 0;
+#pragma unroll 2
+    for (int t = 0; t < cnt; ++t) {
+        const int m = side == 0 ? t : n - 1 - t;
+        int jj, ii, kk;
+        const i64 c = at(m, jj, ii, kk);
+        double a, b, cc, g[NF];
+        adi_row<P, NF>(A, c, jj, ii, kk, a, b, cc, g);
+        const double toward = side == 0 ? a : cc;   // coupling to the row already eliminated
+        const double away = side == 0 ? cc : a;     // coupling to the next row
+        const double r = 1.0 / __fma_rn(-toward, q, b);
+        q = away * r;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            d[f] = __dmul_rn(__fma_rn(-toward, d[f], g[f]), r);
+            A.u[f][c] = d[f];
+        }
+        A.w[(i64)m * nl + line] = q;
+    }
+    // the partner's last pivot
+    const double qo = __shfl_xor_sync(0xffffffffu, q, 1);
+    double dother[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dother[f] = __shfl_xor_sync(0xffffffffu, d[f], 1);
+    if (!live) return;
+    const double qt = side == 0 ? q : qo, qb = side == 0 ? qo : q;   // cp_{p-1}, ap_{p+1}
+    int jj, ii, kk;
+    const i64 cpv = at(p, jj, ii, kk);
+    double a, b, cc, g[NF];
+    adi_row<P, NF>(A, cpv, jj, ii, kk, a, b, cc, g);
+    const double r = 1.0 / __fma_rn(-cc, qb, __fma_rn(-a, qt, b));
+    double x[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const double dt = side == 0 ? d[f] : dother[f], db = side == 0 ? dother[f] : d[f];
+        x[f] = __dmul_rn(__fma_rn(-cc, db, __fma_rn(-a, dt, g[f])), r);
+        if (side == 0) A.u[f][cpv] = x[f];
+    }
+    // substitute outwards from row p
+    for (int t = cnt - 1; t >= 0; --t) {
+        const int m = side == 0 ? t : n - 1 - t;
+        const i64 c = base + (i64)m * sm;
+        const double qm = A.w[(i64)m * nl + line];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            x[f] = __fma_rn(-qm, x[f], A.u[f][c]);
+            A.u[f][c] = x[f];
+        }
+    }
+}
+
+// Longitude sweep (periodic), one thread per line.
 template <int P, int NF>
 __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
+    static_assert(P == 2, "one-thread sweeps are for the periodic direction");
     const Dims& D = A.D;
     const i64 line = blockIdx.x * (i64)kAT + threadIdx.x;
     // lines: colatitude (j, k), radius (i, k), longitude (j, i)
@@ -167,38 +260,7 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
         kk = P == 2 ? m : k;
         return base + (i64)m * sm;
     };
-    if constexpr (P < 2) {
-        double cp = 0.0, dp[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) dp[f] = 0.0;
-#pragma unroll 2
-        for (int m = 0; m < n; ++m) {
-            int jj, ii, kk;
-            const i64 c = at(m, jj, ii, kk);
-            double a, b, cc, g[NF];
-            adi_row<P, NF>(A, c, jj, ii, kk, a, b, cc, g);
-            const double r = 1.0 / __fma_rn(-a, cp, b);
-            cp = cc * r;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                dp[f] = __dmul_rn(__fma_rn(-a, dp[f], g[f]), r);
-                A.u[f][c] = dp[f];
-            }
-            if (m < n - 1) A.w[(i64)m * nl + line] = cp;
-        }
-        double psi[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) psi[f] = dp[f];
-        for (int m = n - 2; m >= 0; --m) {
-            const i64 c = base + (i64)m * sm;
-            const double cpm = A.w[(i64)m * nl + line];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                psi[f] = __fma_rn(-cpm, psi[f], A.u[f][c]);
-                A.u[f][c] = psi[f];
-            }
-        }
-    } else {
+    {
         // periodic (Eqs. TAP2-TAP8): psi1 (one per field) and psi2 (shared:
         // it depends on the matrix only) on the leading block share cp;
         // psi1_0, psi2_0 summed during the sweep (see lines.cu)
@@ -259,8 +321,8 @@ __global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
 template <int NF>
 void launch_sweeps(const AdiArgs& A, cudaStream_t s) {
     const Dims& D = A.D;
-    k_adi<0, NF><<<adi_blocks((i64)D.nr * D.nph), kAT, 0, s>>>(A);
-    k_adi<1, NF><<<adi_blocks((i64)D.nth * D.nph), kAT, 0, s>>>(A);
+    k_adi2<0, NF><<<adi_blocks(2 * (i64)D.nr * D.nph), kAT, 0, s>>>(A);
+    k_adi2<1, NF><<<adi_blocks(2 * (i64)D.nth * D.nph), kAT, 0, s>>>(A);
     k_adi<2, NF><<<adi_blocks((i64)D.nr * D.nth), kAT, 0, s>>>(A);
 }
 
