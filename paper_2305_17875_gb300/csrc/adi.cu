@@ -7,16 +7,17 @@
 //   sweep zeta:  (J - kappa L_zeta) u*   = J u^n + s + kappa L_zeta u^n + 2 kappa (L_eta + L_xi) u^n
 //   sweep eta:   (J - kappa L_eta)  u**  = J u* - kappa L_eta u^n
 //   sweep xi:    (J - kappa L_xi)   u*** = J u** - kappa L_xi u^n     (periodic)
-// One launch per sweep, one thread per grid line: the thread forms each row
+// One launch per sweep, two threads per grid line: a thread forms each row
 // of its tridiagonal system from the face metric (G_pp of the row's two faces,
 // J) and the stencil of u^n, then eliminates as it goes (normalised Thomas,
 // cp kept in a work array laid out [row][line]) and back-substitutes into u.
 // Up to four fields with the same kappa and wall kinds (the three velocity
 // components) share the matrix: one division per row serves all of them, and
 // their independent recurrences fill the FP64 pipeline of a thread.
-// Colatitude and radius lines are adjacent in memory along longitude, so
-// their loads coalesce; longitude lines are contiguous (one thread walks a
-// run of consecutive cells).  Right sides read only the line's own cell of
+// Two threads per line eliminate from both ends to the middle row (a twisted
+// factorisation; see k_adi2).  Colatitude and radius lines are adjacent in
+// memory along longitude, so their loads coalesce; longitude lines are
+// contiguous (a thread walks a run of consecutive cells).  Right sides read only the line's own cell of
 // the previous sweep's result, so every sweep works in place on u.
 //
 // Walls: zero flux, or a value held on the wall face half a cell from the
@@ -196,17 +197,22 @@ __global__ void __launch_bounds__(kAT) k_adi2(AdiArgs A) {
         }
         A.w[(i64)m * nl + line] = q;
     }
+    // row p, read by both lanes before either writes it (__syncwarp below
+    // orders those reads before the write)
+    int jj, ii, kk;
+    const i64 cpv = at(p, jj, ii, kk);
+    double a = 0.0, b = 1.0, cc = 0.0, g[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) g[f] = 0.0;
+    if (live) adi_row<P, NF>(A, cpv, jj, ii, kk, a, b, cc, g);
     // the partner's last pivot
     const double qo = __shfl_xor_sync(0xffffffffu, q, 1);
     double dother[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) dother[f] = __shfl_xor_sync(0xffffffffu, d[f], 1);
+    __syncwarp();
     if (!live) return;
     const double qt = side == 0 ? q : qo, qb = side == 0 ? qo : q;   // cp_{p-1}, ap_{p+1}
-    int jj, ii, kk;
-    const i64 cpv = at(p, jj, ii, kk);
-    double a, b, cc, g[NF];
-    adi_row<P, NF>(A, cpv, jj, ii, kk, a, b, cc, g);
     const double r = 1.0 / __fma_rn(-cc, qb, __fma_rn(-a, qt, b));
     double x[NF];
 #pragma unroll
@@ -228,93 +234,121 @@ __global__ void __launch_bounds__(kAT) k_adi2(AdiArgs A) {
     }
 }
 
-// Longitude sweep (periodic), one thread per line.
-template <int P, int NF>
-__global__ void __launch_bounds__(kAT) k_adi(AdiArgs A) {
-    static_assert(P == 2, "one-thread sweeps are for the periodic direction");
+// Longitude sweep (periodic, Eqs. TAP2-TAP8), two threads per line: the
+// leading block A_c (rows 0 .. n-2, corners taken out) is solved by the
+// twisted elimination for every field's right side and for the corner column
+// (-a_0, 0, .., 0, -c_{n-2}) together (psi1 per field, psi2 shared); the lanes
+// swap their end values psi_0 and psi_{n-2}, form psi_{n-1} (Eq. TAP8) and
+// add psi2 psi_{n-1} to their own rows (Eq. TAP4).
+template <int NF>
+__global__ void __launch_bounds__(kAT) k_adi2p(AdiArgs A) {
     const Dims& D = A.D;
-    const i64 line = blockIdx.x * (i64)kAT + threadIdx.x;
-    // lines: colatitude (j, k), radius (i, k), longitude (j, i)
-    const i64 nl = P == 0 ? (i64)D.nr * D.nph : (P == 1 ? (i64)D.nth * D.nph : (i64)D.nr * D.nth);
-    if (line >= nl) return;
-    const int n = P == 0 ? D.nth : (P == 1 ? D.nr : D.nph);
-    const i64 sm = P == 0 ? (i64)D.nph : (P == 1 ? (i64)D.nth * D.nph : 1);
-    int j = 0, i = 0, k = 0;
-    i64 base;
-    if (P == 0) {
-        j = (int)(line / D.nph);
-        k = (int)(line - (i64)j * D.nph);
-        base = (i64)j * D.nth * D.nph + k;
-    } else if (P == 1) {
-        i = (int)(line / D.nph);
-        k = (int)(line - (i64)i * D.nph);
-        base = (i64)i * D.nph + k;
-    } else {
+    const i64 nl = (i64)D.nr * D.nth;
+    const i64 line = (blockIdx.x * (i64)kAT + threadIdx.x) >> 1;
+    const int side = threadIdx.x & 1;   // 0: rows 0 .. p-1 downwards; 1: rows n-2 .. p+1 upwards
+    const bool live = line < nl;
+    const int n = D.nph, nc = n - 1, p = nc >> 1;
+    int j = 0, i = 0;
+    i64 base = 0;
+    if (live) {
         j = (int)(line / D.nth);
         i = (int)(line - (i64)j * D.nth);
         base = line * D.nph;
     }
-    auto at = [&](int m, int& jj, int& ii, int& kk) {
-        jj = P == 1 ? m : j;
-        ii = P == 0 ? m : i;
-        kk = P == 2 ? m : k;
-        return base + (i64)m * sm;
+    double* wq = A.w;                    // pivot ratios of A_c
+    double* w2 = A.w + (i64)nc * nl;     // corner column: eliminated, then psi2
+    // row m of A_c (corner entries out) and the corner column's entry
+    auto row = [&](int m, double& am, double& b, double& cm, double& em, double g[NF]) {
+        double a, cc;
+        adi_row<2, NF>(A, base + m, j, i, m, a, b, cc, g);
+        am = m > 0 ? a : 0.0;
+        cm = m < nc - 1 ? cc : 0.0;
+        em = (m == 0 ? -a : 0.0) + (m == nc - 1 ? -cc : 0.0);
     };
-    {
-        // periodic (Eqs. TAP2-TAP8): psi1 (one per field) and psi2 (shared:
-        // it depends on the matrix only) on the leading block share cp;
-        // psi1_0, psi2_0 summed during the sweep (see lines.cu)
-        const int nc = n - 1;
-        double* wcp = A.w;
-        double* wd2 = A.w + (i64)nc * nl;
-        double cp = 0.0, d2 = 0.0, prod = 1.0, s2 = 0.0, d1[NF], s1[NF];
+    double q = 0.0, d2 = 0.0, d[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) d1[f] = s1[f] = 0.0;
+    for (int f = 0; f < NF; ++f) d[f] = 0.0;
+    const int cnt = live ? (side == 0 ? p : nc - 1 - p) : 0;
 #pragma unroll 2
-        for (int m = 0; m < nc; ++m) {
-            int jj, ii, kk;
-            const i64 c = at(m, jj, ii, kk);
-            double a, b, cc, g[NF];
-            adi_row<2, NF>(A, c, jj, ii, kk, a, b, cc, g);
-            const double am = m > 0 ? a : 0.0;
-            const double em = (m == 0 ? -a : 0.0) + (m == nc - 1 ? -cc : 0.0);
-            const double r = 1.0 / __fma_rn(-am, cp, b);
-            cp = m < nc - 1 ? cc * r : 0.0;
-            d2 = __dmul_rn(__fma_rn(-am, d2, em), r);
-            s2 = __fma_rn(prod, d2, s2);
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                d1[f] = __dmul_rn(__fma_rn(-am, d1[f], g[f]), r);
-                s1[f] = __fma_rn(prod, d1[f], s1[f]);
-                A.u[f][c] = d1[f];
-            }
-            prod = -prod * cp;
-            wd2[(i64)m * nl + line] = d2;
-            if (m < nc - 1) wcp[(i64)m * nl + line] = cp;
-        }
-        int jj, ii, kk;
-        const i64 cl = at(nc, jj, ii, kk);
-        double al, bl, cl_, gl[NF];
-        adi_row<2, NF>(A, cl, jj, ii, kk, al, bl, cl_, gl);
-        const double rden = 1.0 / __fma_rn(al, d2, __fma_rn(cl_, s2, bl));
-        double last[NF], psi[NF];
+    for (int t = 0; t < cnt; ++t) {
+        const int m = side == 0 ? t : nc - 1 - t;
+        double am, b, cm, em, g[NF];
+        row(m, am, b, cm, em, g);
+        const double toward = side == 0 ? am : cm, away = side == 0 ? cm : am;
+        const double r = 1.0 / __fma_rn(-toward, q, b);
+        q = away * r;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            last[f] = __dmul_rn(__fma_rn(-al, d1[f], __fma_rn(-cl_, s1[f], gl[f])), rden);
-            A.u[f][cl] = last[f];
-            psi[f] = __fma_rn(d2, last[f], d1[f]);
-            A.u[f][base + (i64)(nc - 1) * sm] = psi[f];
+            d[f] = __dmul_rn(__fma_rn(-toward, d[f], g[f]), r);
+            A.u[f][base + m] = d[f];
         }
-        for (int m = nc - 2; m >= 0; --m) {
-            const i64 c = base + (i64)m * sm;
-            const double d2m = wd2[(i64)m * nl + line], cpm = wcp[(i64)m * nl + line];
+        d2 = __dmul_rn(__fma_rn(-toward, d2, em), r);
+        wq[(i64)m * nl + line] = q;
+        w2[(i64)m * nl + line] = d2;
+    }
+    // rows p and n-1, read by both lanes before either writes them
+    double ap = 0.0, bp = 1.0, cp = 0.0, ep = 0.0, gp[NF], al = 0.0, bl = 1.0, cl = 0.0, gl[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const double dm = __fma_rn(d2m, last[f], A.u[f][c]);
-                psi[f] = __fma_rn(-cpm, psi[f], dm);
-                A.u[f][c] = psi[f];
-            }
+    for (int f = 0; f < NF; ++f) gp[f] = gl[f] = 0.0;
+    if (live) {
+        row(p, ap, bp, cp, ep, gp);
+        adi_row<2, NF>(A, base + nc, j, i, nc, al, bl, cl, gl);
+    }
+    const double qo = __shfl_xor_sync(0xffffffffu, q, 1);
+    const double d2o = __shfl_xor_sync(0xffffffffu, d2, 1);
+    double dother[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dother[f] = __shfl_xor_sync(0xffffffffu, d[f], 1);
+    __syncwarp();
+    const double qt = side == 0 ? q : qo, qb = side == 0 ? qo : q;
+    const double rp = 1.0 / __fma_rn(-cp, qb, __fma_rn(-ap, qt, bp));
+    double x[NF], x2;
+    x2 = __dmul_rn(__fma_rn(-cp, side == 0 ? d2o : d2, __fma_rn(-ap, side == 0 ? d2 : d2o, ep)), rp);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const double dt = side == 0 ? d[f] : dother[f], db = side == 0 ? dother[f] : d[f];
+        x[f] = __dmul_rn(__fma_rn(-cp, db, __fma_rn(-ap, dt, gp[f])), rp);
+        if (live && side == 0) A.u[f][base + p] = x[f];
+    }
+    if (live && side == 0) w2[(i64)p * nl + line] = x2;
+    // substitute outwards: psi1 into u, psi2 into w2
+    for (int t = cnt - 1; t >= 0; --t) {
+        const int m = side == 0 ? t : nc - 1 - t;
+        const i64 c = base + m;
+        const double qm = wq[(i64)m * nl + line];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            x[f] = __fma_rn(-qm, x[f], A.u[f][c]);
+            A.u[f][c] = x[f];
         }
+        x2 = __fma_rn(-qm, x2, w2[(i64)m * nl + line]);
+        w2[(i64)m * nl + line] = x2;
+    }
+    // the lanes end at psi_0 (top) and psi_{n-2} (bottom; psi_p when it has no rows)
+    const double x2o = __shfl_xor_sync(0xffffffffu, x2, 1);
+    double xo[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) xo[f] = __shfl_xor_sync(0xffffffffu, x[f], 1);
+    if (!live) return;
+    const double s20 = side == 0 ? x2 : x2o, s2e = side == 0 ? x2o : x2;
+    const double rden = 1.0 / __fma_rn(al, s2e, __fma_rn(cl, s20, bl));
+    double last[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const double s10 = side == 0 ? x[f] : xo[f], s1e = side == 0 ? xo[f] : x[f];
+        last[f] = __dmul_rn(__fma_rn(-al, s1e, __fma_rn(-cl, s10, gl[f])), rden);
+    }
+    // Eq. TAP4 on the lane's rows: top 0 .. p, bottom p+1 .. n-2; row n-1 = psi_{n-1}
+    const int m0 = side == 0 ? 0 : p + 1, m1 = side == 0 ? p : nc - 1;
+    for (int m = m0; m <= m1; ++m) {
+        const i64 c = base + m;
+        const double s2 = w2[(i64)m * nl + line];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) A.u[f][c] = __fma_rn(s2, last[f], A.u[f][c]);
+    }
+    if (side == 0) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) A.u[f][base + nc] = last[f];
     }
 }
 
@@ -323,7 +357,7 @@ void launch_sweeps(const AdiArgs& A, cudaStream_t s) {
     const Dims& D = A.D;
     k_adi2<0, NF><<<adi_blocks(2 * (i64)D.nr * D.nph), kAT, 0, s>>>(A);
     k_adi2<1, NF><<<adi_blocks(2 * (i64)D.nth * D.nph), kAT, 0, s>>>(A);
-    k_adi<2, NF><<<adi_blocks((i64)D.nr * D.nth), kAT, 0, s>>>(A);
+    k_adi2p<NF><<<adi_blocks(2 * (i64)D.nr * D.nth), kAT, 0, s>>>(A);
 }
 
 mg_status ensure_adi(mg_handle* h) {
