@@ -1,6 +1,6 @@
 // lines.cu - batched tridiagonal line solves (Section 3.5): the Thomas
 // algorithm (Eqs. FIBRE_TA1, FIBRE_TA2) and its periodic variant (Eqs.
-// FIBRE_TAP1 to FIBRE_TAP8), one thread per line.
+// FIBRE_TAP1 to FIBRE_TAP8).
 //
 // Row m of a line reads a_m psi_{m-1} + b_m psi_m + c_m psi_{m+1} = g_m; a
 // periodic line closes the ring (a_0 couples psi_{n-1}, c_{n-1} couples
@@ -11,12 +11,14 @@
 // for contiguous lines (sm = 1) each thread reads its line in runs of kU
 // elements, one or two sectors per array at a time.
 //
-// The sweep is the normalised form of the paper's forward elimination:
-// cp_m = c_m / (b_m - a_m cp_{m-1}), dp_m = (g_m - a_m dp_{m-1}) / (same), so
-// back substitution psi_m = dp_m - cp_m psi_{m+1} needs only cp and dp (dp is
-// kept in x, cp in the work array, laid out [m][line] so that its accesses
-// are coalesced whatever the line layout).  Same elimination, same pivots as
-// the paper's b'_m = b_m - a_m c_{m-1} / b'_{m-1}; one reciprocal per row.
+// Plain lines take two threads each (a twisted factorisation, k_thomas2),
+// except many contiguous ones; periodic lines one thread each.  The sweep is the normalised form of the
+// paper's forward elimination: cp_m = c_m / (b_m - a_m cp_{m-1}),
+// dp_m = (g_m - a_m dp_{m-1}) / (same), so back substitution
+// psi_m = dp_m - cp_m psi_{m+1} needs only cp and dp (dp is kept in x, cp in
+// the work array, laid out [m][line] so that its accesses are coalesced
+// whatever the line layout).  Same elimination, same pivots as the paper's
+// b'_m = b_m - a_m c_{m-1} / b'_{m-1}.
 //
 // Periodic lines (Eqs. TAP2 to TAP8): psi1 and psi2 solve the leading
 // (n-1)-block with right sides g and (-a_0, 0, .., 0, -c_{n-2}); both share
@@ -51,7 +53,8 @@ __device__ __forceinline__ i64 line_base(const LineGeom& L, i64 line) {
     return l1 * L.s1 + (line - l1 * L.n2) * L.s2;
 }
 
-// Plain lines.  x may alias g (g_m is read before x_m is written).
+// Plain lines, one thread per line.  x may alias g (g_m is read before x_m is
+// written).
 __global__ void __launch_bounds__(kLT) k_thomas(LineGeom L, const double* __restrict__ a,
                                                  const double* __restrict__ b,
                                                  const double* __restrict__ c, const double* g,
@@ -93,6 +96,77 @@ __global__ void __launch_bounds__(kLT) k_thomas(LineGeom L, const double* __rest
         const i64 o = base + (i64)m * L.sm;
         psi = __fma_rn(-w[(i64)m * L.nl + line], psi, x[o]);
         x[o] = psi;
+    }
+}
+
+// Plain lines, two threads per line (adjacent lanes): the top lane eliminates
+// rows 0 .. p-1 downwards (x_m = dp_m - cp_m x_{m+1}), the bottom lane rows
+// n-1 .. p+1 upwards (x_m = ep_m - ap_m x_{m-1}), p = n / 2; they swap their
+// last pivots by a lane shuffle, both solve row p, and substitute outwards (a
+// twisted factorisation: half the sequential chain, twice the threads).  The
+// work array holds cp at rows 0 .. p-1 and ap at rows p .. n-2 (row m - 1
+// for m > p).  x may alias g: every row is read before it is written, row p
+// by both lanes before the barrier and written after it.
+__global__ void __launch_bounds__(kLT) k_thomas2(LineGeom L, const double* __restrict__ a,
+                                                  const double* __restrict__ b,
+                                                  const double* __restrict__ c, const double* g,
+                                                  double* x, double* __restrict__ w) {
+    const i64 line = (blockIdx.x * (i64)kLT + threadIdx.x) >> 1;
+    const int side = threadIdx.x & 1;
+    const bool live = line < L.nl;
+    const i64 base = live ? line_base(L, line) : 0;
+    const int n = L.n, p = n >> 1;
+    const int cnt = live ? (side == 0 ? p : n - 1 - p) : 0;
+    auto wrow = [&](int m) { return (i64)(m > p ? m - 1 : m) * L.nl + line; };
+    double q = 0.0, d = 0.0;
+    for (int t0 = 0; t0 < cnt; t0 += kU) {
+        const int k = min(kU, cnt - t0);
+        double rt[kU], rb[kU], ra[kU], rg[kU];   // toward, diagonal, away, right side
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (u < k) {
+                const int m = side == 0 ? t0 + u : n - 1 - t0 - u;
+                const i64 o = base + (i64)m * L.sm;
+                const double am = m > 0 ? a[o] : 0.0, cm = m < n - 1 ? c[o] : 0.0;
+                rt[u] = side == 0 ? am : cm;
+                ra[u] = side == 0 ? cm : am;
+                rb[u] = b[o];
+                rg[u] = g[o];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (u < k) {
+                const int m = side == 0 ? t0 + u : n - 1 - t0 - u;
+                const double r = 1.0 / __fma_rn(-rt[u], q, rb[u]);
+                q = ra[u] * r;
+                d = __dmul_rn(__fma_rn(-rt[u], d, rg[u]), r);
+                x[base + (i64)m * L.sm] = d;
+                w[wrow(m)] = q;
+            }
+        }
+    }
+    double ap = 0.0, bp = 1.0, cp = 0.0, gp = 0.0;
+    const i64 op = base + (i64)p * L.sm;
+    if (live) {
+        ap = p > 0 ? a[op] : 0.0;
+        cp = p < n - 1 ? c[op] : 0.0;
+        bp = b[op];
+        gp = g[op];
+    }
+    const double qo = __shfl_xor_sync(0xffffffffu, q, 1);
+    const double dother = __shfl_xor_sync(0xffffffffu, d, 1);
+    __syncwarp();
+    if (!live) return;
+    const double qt = side == 0 ? q : qo, qb = side == 0 ? qo : q;
+    const double dt = side == 0 ? d : dother, db = side == 0 ? dother : d;
+    double xv = __fma_rn(-cp, db, __fma_rn(-ap, dt, gp)) / __fma_rn(-cp, qb, __fma_rn(-ap, qt, bp));
+    if (side == 0) x[op] = xv;
+    for (int t = cnt - 1; t >= 0; --t) {
+        const int m = side == 0 ? t : n - 1 - t;
+        const i64 o = base + (i64)m * L.sm;
+        xv = __fma_rn(-w[wrow(m)], xv, x[o]);
+        x[o] = xv;
     }
 }
 
@@ -205,6 +279,11 @@ extern "C" mg_status mg_thomas(const mg_lines* lines, const double* a, const dou
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned blocks = (unsigned)((L.nl + kLT - 1) / kLT);
     if (periodic) k_thomas_periodic<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
+    // two threads per line unless the lines are contiguous and numerous (then
+    // two lanes streaming far-apart runs of one line cost more than the
+    // shorter chain gains: 1.34 vs 1.10 ms for 65536 lines of 512)
+    else if (L.sm != 1 || L.nl < 32768)
+        k_thomas2<<<(unsigned)((2 * L.nl + kLT - 1) / kLT), kLT, 0, s>>>(L, a, b, c, g, x, work);
     else k_thomas<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
