@@ -11,8 +11,8 @@
 // for contiguous lines (sm = 1) each thread reads its line in runs of kU
 // elements, one or two sectors per array at a time.
 //
-// Plain lines take two threads each (a twisted factorisation, k_thomas2),
-// except many contiguous ones; periodic lines one thread each.  The sweep is the normalised form of the
+// Lines take two threads each (a twisted factorisation, k_thomas2 and
+// k_thomas2p), except many contiguous ones (one thread each).  The sweep is the normalised form of the
 // paper's forward elimination: cp_m = c_m / (b_m - a_m cp_{m-1}),
 // dp_m = (g_m - a_m dp_{m-1}) / (same), so back substitution
 // psi_m = dp_m - cp_m psi_{m+1} needs only cp and dp (dp is kept in x, cp in
@@ -235,6 +235,92 @@ __global__ void __launch_bounds__(kLT) k_thomas_periodic(LineGeom L, const doubl
     }
 }
 
+// Periodic lines, two threads per line: the leading block A_c (rows 0 .. n-2,
+// corners out) is solved by the twisted elimination for g and for the corner
+// column (-a_0, 0, .., 0, -c_{n-2}) together (psi1, psi2); the lanes swap
+// their end values psi_0 and psi_{n-2}, form psi_{n-1} (Eq. TAP8) and add
+// psi2 psi_{n-1} to their own rows (Eq. TAP4).  w: pivot ratios in rows
+// [0, n-1) (row p unused), psi2 in rows [n-1, 2n-2).  x may alias g.
+__global__ void __launch_bounds__(kLT) k_thomas2p(LineGeom L, const double* __restrict__ a,
+                                                   const double* __restrict__ b,
+                                                   const double* __restrict__ c, const double* g,
+                                                   double* x, double* __restrict__ w) {
+    const i64 line = (blockIdx.x * (i64)kLT + threadIdx.x) >> 1;
+    const int side = threadIdx.x & 1;
+    const bool live = line < L.nl;
+    const i64 base = live ? line_base(L, line) : 0;
+    const int n = L.n, nc = n - 1, p = nc >> 1;
+    double* wq = w;
+    double* w2 = w + (i64)nc * L.nl;
+    auto row = [&](int m, double& am, double& bm, double& cm, double& em, double& gm) {
+        const i64 o = base + (i64)m * L.sm;
+        const double aa = a[o], cc = c[o];
+        am = m > 0 ? aa : 0.0;
+        cm = m < nc - 1 ? cc : 0.0;
+        em = (m == 0 ? -aa : 0.0) + (m == nc - 1 ? -cc : 0.0);
+        bm = b[o];
+        gm = g[o];
+    };
+    double q = 0.0, d = 0.0, d2 = 0.0;
+    const int cnt = live ? (side == 0 ? p : nc - 1 - p) : 0;
+    for (int t = 0; t < cnt; ++t) {
+        const int m = side == 0 ? t : nc - 1 - t;
+        double am, bm, cm, em, gm;
+        row(m, am, bm, cm, em, gm);
+        const double toward = side == 0 ? am : cm, away = side == 0 ? cm : am;
+        const double r = 1.0 / __fma_rn(-toward, q, bm);
+        q = away * r;
+        d = __dmul_rn(__fma_rn(-toward, d, gm), r);
+        d2 = __dmul_rn(__fma_rn(-toward, d2, em), r);
+        x[base + (i64)m * L.sm] = d;
+        wq[(i64)m * L.nl + line] = q;
+        w2[(i64)m * L.nl + line] = d2;
+    }
+    // rows p and n-1, read by both lanes before either writes them
+    double ap = 0.0, bp = 1.0, cp = 0.0, ep = 0.0, gp = 0.0, al = 0.0, bl = 1.0, cl = 0.0, gl = 0.0;
+    const i64 ol = base + (i64)nc * L.sm;
+    if (live) {
+        row(p, ap, bp, cp, ep, gp);
+        al = a[ol];
+        bl = b[ol];
+        cl = c[ol];
+        gl = g[ol];
+    }
+    const double qo = __shfl_xor_sync(0xffffffffu, q, 1);
+    const double dO = __shfl_xor_sync(0xffffffffu, d, 1);
+    const double d2o = __shfl_xor_sync(0xffffffffu, d2, 1);
+    __syncwarp();
+    const double qt = side == 0 ? q : qo, qb = side == 0 ? qo : q;
+    const double rp = 1.0 / __fma_rn(-cp, qb, __fma_rn(-ap, qt, bp));
+    double xv = __dmul_rn(__fma_rn(-cp, side == 0 ? dO : d, __fma_rn(-ap, side == 0 ? d : dO, gp)), rp);
+    double x2 = __dmul_rn(__fma_rn(-cp, side == 0 ? d2o : d2, __fma_rn(-ap, side == 0 ? d2 : d2o, ep)), rp);
+    if (live && side == 0) {
+        x[base + (i64)p * L.sm] = xv;
+        w2[(i64)p * L.nl + line] = x2;
+    }
+    for (int t = cnt - 1; t >= 0; --t) {
+        const int m = side == 0 ? t : nc - 1 - t;
+        const i64 o = base + (i64)m * L.sm;
+        const double qm = wq[(i64)m * L.nl + line];
+        xv = __fma_rn(-qm, xv, x[o]);
+        x[o] = xv;
+        x2 = __fma_rn(-qm, x2, w2[(i64)m * L.nl + line]);
+        w2[(i64)m * L.nl + line] = x2;
+    }
+    const double xo = __shfl_xor_sync(0xffffffffu, xv, 1);
+    const double x2o = __shfl_xor_sync(0xffffffffu, x2, 1);
+    if (!live) return;
+    const double s10 = side == 0 ? xv : xo, s1e = side == 0 ? xo : xv;
+    const double s20 = side == 0 ? x2 : x2o, s2e = side == 0 ? x2o : x2;
+    const double last = __fma_rn(-al, s1e, __fma_rn(-cl, s10, gl)) / __fma_rn(al, s2e, __fma_rn(cl, s20, bl));
+    const int m0 = side == 0 ? 0 : p + 1, m1 = side == 0 ? p : nc - 1;
+    for (int m = m0; m <= m1; ++m) {
+        const i64 o = base + (i64)m * L.sm;
+        x[o] = __fma_rn(w2[(i64)m * L.nl + line], last, x[o]);
+    }
+    if (side == 0) x[ol] = last;
+}
+
 bool geom_of(const mg_lines* in, int periodic, LineGeom* L) {
     if (!in || in->n < 1 || (periodic && in->n < 3) || in->n1 < 0 || in->n2 < 0) return false;
     L->n = in->n;
@@ -278,11 +364,17 @@ extern "C" mg_status mg_thomas(const mg_lines* lines, const double* a, const dou
     }
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned blocks = (unsigned)((L.nl + kLT - 1) / kLT);
-    if (periodic) k_thomas_periodic<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
+    // two threads per line where the shorter chain pays (measured): plain
+    // lines unless contiguous and numerous; periodic lines (whose twisted form
+    // adds a pass) only when contiguous and few
+    const bool two = L.sm != 1 || L.nl < 32768;
+    if (periodic && L.sm == 1 && L.nl < 32768)
+        k_thomas2p<<<(unsigned)((2 * L.nl + kLT - 1) / kLT), kLT, 0, s>>>(L, a, b, c, g, x, work);
+    else if (periodic) k_thomas_periodic<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
     // two threads per line unless the lines are contiguous and numerous (then
     // two lanes streaming far-apart runs of one line cost more than the
     // shorter chain gains: 1.34 vs 1.10 ms for 65536 lines of 512)
-    else if (L.sm != 1 || L.nl < 32768)
+    else if (two)
         k_thomas2<<<(unsigned)((2 * L.nl + kLT - 1) / kLT), kLT, 0, s>>>(L, a, b, c, g, x, work);
     else k_thomas<<<blocks, kLT, 0, s>>>(L, a, b, c, g, x, work);
     const cudaError_t e = cudaGetLastError();
