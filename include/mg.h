@@ -277,7 +277,8 @@ typedef struct {
     int tail_cluster;       /* CTAs per tail cluster */
     int one_pass_tiles;     /* 1: 7-point red-black sweeps as one-pass tiles where they fit */
     int source;             /* 0 default, 1 tuned at this set-up, 2 from the process cache,
-                               3 forced by MG_TAIL / MG_FUSED_RB in the environment */
+                               3 forced by MG_TAIL / MG_FUSED_RB / MG_VB_CAP in the
+                               environment (MG_VB_CAP = blocks per SM) */
     int candidates;         /* schedules timed (source 1) */
     double ms_per_iteration;/* device time of one outer iteration under the chosen schedule
                                (source 1 and 2; 0 otherwise) */

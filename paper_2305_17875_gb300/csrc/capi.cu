@@ -621,9 +621,10 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     CK(cudaGetLastError());
 
     // --- launch schedule: forced by the environment, tuned, or the default
-    const bool env_sched = std::getenv("MG_TAIL") || std::getenv("MG_FUSED_RB");
+    const bool env_sched = std::getenv("MG_TAIL") || std::getenv("MG_FUSED_RB") || std::getenv("MG_VB_CAP");
     if (env_sched) {
         h->sched_source = 3;
+        if (const char* v = std::getenv("MG_VB_CAP")) h->vb_cap = std::max(1, std::min(64, std::atoi(v)));
         if (std::getenv("MG_TAIL")) {
             i64 cells = kTailCells;
             int cluster = 8;
