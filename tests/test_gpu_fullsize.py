@@ -1,8 +1,9 @@
 """Full-size solves, in the launch configuration the benchmark times, checked
 against the oracle on sampled cells.
 
-The grids are the 128 x 128 x 256 stretched sphere (7-point) and the
-256 x 256 x 512 oblate shell (19-point).  The oracle cannot solve them, so
+The grids are the 128 x 128 x 256 stretched sphere (7-point), the
+256 x 256 x 512 oblate shell (19-point) and the 128 x 128 x 256 thin shell
+(radius 1 to 1.05), with point and radial-line Gauss-Seidel.  The oracle cannot solve them, so
 the check is on properties it can evaluate one cell at a time:
 
 * the relative residual ||b - A x|| / ||b|| estimated from 32768 random cells,
@@ -24,7 +25,8 @@ from oracle import grid, operator
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("single_sphere_128", 1), ("single_oblate_256", 1), ("single_oblate_256", 2)]
+CASES = [("single_sphere_128", 1, 0), ("single_oblate_256", 1, 0), ("single_oblate_256", 2, 0),
+         ("single_sphere_128", 1, 2), ("single_thin_128", 1, 2), ("single_thin_128", 1, 0)]
 
 
 def _volumes(g):
@@ -47,14 +49,14 @@ def _workload(name):
     return _W[name]
 
 
-@pytest.mark.parametrize("wl,prec", CASES)
-def test_full_size_solve_sampled_against_oracle(lib, wl, prec):
+@pytest.mark.parametrize("wl,prec,smoother", CASES)
+def test_full_size_solve_sampled_against_oracle(lib, wl, prec, smoother):
     import torch
     w = _workload(wl)
     g, f = w["grid"], w["f"]
     sh = grid.shell(g)
     stencil = 7 if g["mapping"] == 0 else 19
-    h = lib.mg_setup(g, dict(precision=prec))
+    h = lib.mg_setup(g, dict(precision=prec, smoother=smoother))
     fd = torch.from_numpy(f).to("cuda:0")
     xd = torch.zeros_like(fd)
     rep = lib.mg_solve(h, fd, xd, tol=1e-10)
