@@ -20,6 +20,8 @@ AGRIDS = {
     "sphere_stretched_ragged": W.grid_desc(10, 12, 20, stretch=2.0),
     "triaxial": W.grid_desc(8, 7, 12, mapping=2, flattening=0.1, e2=0.05, stretch=1.0),
     "oblate_nph4": W.grid_desc(6, 6, 4, r_out=1 / 0.6, mapping=1, flattening=0.1),
+    # odd line lengths in radius and colatitude, six longitudes
+    "sphere_odd": W.grid_desc(9, 5, 6, stretch=1.0),
 }
 WALLS = {
     "no_slip": (None, adi.walls()),

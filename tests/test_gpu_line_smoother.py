@@ -163,6 +163,23 @@ def test_batched_line_solves_equal_lone_solves(lib):
         assert torch.equal(x, xl)
 
 
+def test_mixed_smoothers_in_one_batch(lib):
+    """Point and radial-line Gauss-Seidel handles solved together (one launch
+    per level operation for each smoother): each equals its lone solve."""
+    import torch
+    shells = [W.grid_desc(16, stretch=2.0), W.grid_desc(12, 8, 16, mapping=2, flattening=0.05, e2=0.05),
+              W.grid_desc(16, 16, 32, r_out=1.05, stretch=2.0), W.grid_desc(8, stretch=1.0)]
+    smoothers = [0, LINE, LINE, 0]
+    fs = [_dev(W.rhs_modes(g, seed=60 + s), 0) for s, g in enumerate(shells)]
+    hs = [lib.mg_setup(g, dict(precision=1, smoother=sm)) for g, sm in zip(shells, smoothers)]
+    xs = [torch.zeros_like(f) for f in fs]
+    reps = lib.mg_solve_batch(hs, fs, xs, [1e-10] * len(hs))
+    for g, sm, f, x, rep in zip(shells, smoothers, fs, xs, reps):
+        xl = torch.zeros_like(f)
+        rl = lib.mg_solve(lib.mg_setup(g, dict(precision=1, smoother=sm)), f, xl, tol=1e-10)
+        assert rep["iters"] == rl["iters"] and torch.equal(x, xl)
+
+
 def test_too_many_radial_cells_is_rejected(lib):
     with pytest.raises(lib.MGError) as e:
         lib.mg_setup(W.grid_desc(520, 4, 8), dict(precision=1, smoother=LINE))

@@ -137,6 +137,20 @@ def test_hierarchy_reuse(lib):
     assert np.array_equal(r2[t2][0], xl)
 
 
+def test_served_line_smoother_requests(lib):
+    """Requests asking for the radial-line smoother are served like any other
+    and give the lone-solve bits."""
+    g = W.grid_desc(16, 16, 32, r_out=1.05, stretch=2.0)
+    f = W.rhs_modes(g, seed=9)
+    sv = lib.mg_serve_create(max_slots=2)
+    t = lib.mg_serve_submit(sv, g, f, 1e-10, opts=dict(smoother=2))
+    r = _drain(lib, sv, [t], [f.shape])
+    sv.close()
+    assert r[t][1] == "MG_OK"
+    xl, rl = _lone(lib, g, f, 1e-10, dict(smoother=2))
+    assert r[t][2]["iters"] == rl["iters"] and np.array_equal(r[t][0], xl)
+
+
 def test_serve_errors(lib):
     sv = lib.mg_serve_create()
     g = W.grid_desc(8)
