@@ -358,7 +358,7 @@ extern "C" mg_status mg_thomas(const mg_lines* lines, const double* a, const dou
         set_error("mg_thomas: null array");
         return MG_EINVAL;
     }
-    if (x == a || x == b || x == c || work == x || work == g) {
+    if (x == a || x == b || x == c || work == x || work == g || work == a || work == b || work == c) {
         set_error("mg_thomas: x and work may not alias the coefficients (x may alias g)");
         return MG_EINVAL;
     }

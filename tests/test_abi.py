@@ -61,3 +61,28 @@ def test_host_side_validation_without_gpu(so):
     assert e.value.status == mgs.MG_EINVAL
     o = mgs.default_opts()
     assert (o.precision, o.nu1, o.nu2, o.smoother) == (1, 2, 2, 0)
+
+
+def test_line_solve_and_adi_validation_without_gpu(so):
+    """Geometry and argument checks of mg_thomas / mg_adi_substep happen on
+    the host, before any device work."""
+    import paper_2305_17875_gb300 as mgs
+    L = dict(n=5, n1=3, n2=4, sm=12, s1=4, s2=1)
+    assert mgs.mg_thomas_work_bytes(L) == 8 * 4 * 12
+    assert mgs.mg_thomas_work_bytes(L, periodic=True) == 8 * 2 * 4 * 12
+    assert mgs.mg_thomas_work_bytes(dict(L, n=2), periodic=True) == 0
+    assert mgs.mg_thomas_work_bytes(dict(L, n=0)) == 0
+    assert mgs.mg_thomas_work_bytes(dict(L, n1=-1)) == 0
+    assert mgs.lines_along((2, 3, 4), 0) == dict(n=2, n1=3, n2=4, sm=12, s1=4, s2=1)
+    assert mgs.lines_along((2, 3, 4), 2) == dict(n=4, n1=2, n2=3, sm=1, s1=12, s2=4)
+    dummy = 4096   # never dereferenced: the checks fail first
+    for geom, per in ((dict(L, n=2), True), (dict(L, n=0), False)):
+        with pytest.raises(mgs.MGError) as e:
+            mgs.mg_thomas(geom, dummy, dummy + 8, dummy + 16, dummy + 24, dummy + 32, periodic=per, work=dummy + 40,
+                          stream=0)
+        assert e.value.status == mgs.MG_EINVAL
+    with pytest.raises(mgs.MGError) as e:       # x aliasing a coefficient
+        mgs.mg_thomas(L, dummy, dummy + 8, dummy + 16, dummy + 24, dummy, work=dummy + 40, stream=0)
+    assert e.value.status == mgs.MG_EINVAL
+    st = mgs._lib.mg_adi_substep(None, 1.0, 1, None, None, None, None)
+    assert st == mgs.MG_EINVAL
