@@ -228,7 +228,7 @@ def cell_volume(sh, fm):
             + d2 + np.roll(d2, -1, axis=2)) / 6.0
 
 
-# ---------------------------------------------------------------- analytic (pins only)
+# ---------------------------------------------------------------- analytic metric
 def analytic_jacobian(sh: Shell, iv, jv, kv):
     """Exact dx_a/dzeta_p at fractional computational point (iv, jv, kv)."""
     fl, e2 = _scales(sh)
@@ -270,6 +270,16 @@ def analytic_face_metrics(sh):
         adet, G, _ = metric_from_jacobian(M)
         out[f"G{d}"] = G[..., d, :]
         out[f"det{d}"] = adet
+    return out
+
+
+def face_metrics_analytic(sh):
+    """The metric with exact derivatives at the face centres instead of the
+    differences of Section 3.2 step 1 (steps 2 to 5 unchanged): G rows and
+    |J^{-1}| of every face, and the cell |J^{-1}| as the mean of the six face
+    determinants (step 3), in the layout of ``face_metrics``."""
+    out = analytic_face_metrics(sh)
+    out["J"] = cell_volume(sh, out)
     return out
 
 
