@@ -56,6 +56,7 @@ enum { MG_PREC_FP64 = 0,        /* plain FP64 multigrid */
        MG_PREC_FP32_IR = 1,     /* FP32 V-cycles inside FP64 iterative refinement */
        MG_PREC_FP16C_IR = 2 };  /* FP16 coefficients, FP32 arithmetic, inside FP64 IR */
 enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1, MG_SMOOTH_LINE = 2 };
+enum { MG_METRIC_DISCRETE = 0, MG_METRIC_ANALYTIC = 1 };
 enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
 
 /* Grid and mapping (Section 2 mapping; Section 3.7 Eq. stretching).
@@ -94,6 +95,11 @@ typedef struct {
                            coarse tail, one-pass red-black tiles) once per hierarchy shape in
                            the process and keep the fastest; every schedule gives the same
                            bits.  0: the default schedule. */
+    int metric;         /* MG_METRIC_DISCRETE (default): the face metric of Section 3.2 from
+                           vertex differences (step 1); MG_METRIC_ANALYTIC: exact derivatives of
+                           the mapping at the face centres, steps 2-5 unchanged (an O(h^2)
+                           different operator).  The pressure-correction steps and the ADI
+                           sweeps need the discrete metric (MG_EINVAL otherwise). */
 } mg_opts;
 
 #define MG_HIST 64

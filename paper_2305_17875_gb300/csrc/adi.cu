@@ -406,6 +406,10 @@ extern "C" mg_status mg_adi_substep(mg_handle* h, double kappa, int nfields, con
             return MG_EINVAL;
         }
     }
+    if (h->opts.metric != MG_METRIC_DISCRETE) {
+        set_error("mg_adi_substep: the implicit sweeps need the discrete metric of Section 3.2");
+        return MG_EINVAL;
+    }
     if (cudaEventRecord(h->ev_in, h->user_stream) != cudaSuccess ||
         cudaStreamWaitEvent(h->stream, h->ev_in, 0) != cudaSuccess) {
         set_error("stream join failed");

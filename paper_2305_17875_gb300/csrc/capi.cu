@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "pc.h"
 #include "line_smooth.cuh"
 
 using namespace mgs;
@@ -117,6 +118,7 @@ std::string check_opts(const mg_opts* o) {
     if (o->max_iters < 0) return "max_iters must be >= 0";
     if (o->stencil != 0 && o->stencil != 7 && o->stencil != 19) return "stencil must be 0, 7 or 19";
     if (o->autotune != 0 && o->autotune != 1) return "autotune must be 0 or 1";
+    if (o->metric != MG_METRIC_DISCRETE && o->metric != MG_METRIC_ANALYTIC) return "metric must be 0 or 1";
     return "";
 }
 
@@ -158,6 +160,13 @@ struct TmpDev {
 double stretch_unit(double jv, int n, double rx) {
     const double t = jv / n - 0.5;
     return rx == 0.0 ? t : std::tanh(rx * t) / (2.0 * std::tanh(rx / 2.0));
+}
+
+// Its derivative with respect to the index (the analytic metric option).
+double d_stretch_unit(double jv, int n, double rx) {
+    if (rx == 0.0) return 1.0 / n;
+    const double c = std::cosh(rx * (jv / n - 0.5));
+    return rx / (n * c * c * 2.0 * std::tanh(rx / 2.0));
 }
 
 int ncomp(int stencil) { return stencil == 19 ? 9 : 3; }
@@ -505,7 +514,44 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     if (!(h->part = (double*)dalloc(h, sizeof(double) * kRedBlocks))) return MG_ENOMEM;
     if (!(h->scal = (double*)dalloc(h, sizeof(double) * SC_COUNT))) return MG_ENOMEM;
     if (!(h->one_task = (BTask*)dalloc(h, sizeof(BTask)))) return MG_ENOMEM;
-    CK(launch_face_metric(T, L0.D, h->stencil, L0.g64, h->J64, stream));
+    if (o->metric == MG_METRIC_ANALYTIC) {
+        // exact derivatives at the face centres: tables at half-index resolution
+        std::vector<double> ar(2 * nr + 1), adr(2 * nr + 1), act(2 * nth + 1), ast(2 * nth + 1),
+            acp(2 * nph + 1), asp(2 * nph + 1);
+        for (int t = 0; t <= 2 * nr; ++t) {
+            ar[t] = g->r_in + (g->r_out - g->r_in) * (stretch_unit(0.5 * t, nr, g->stretch) + 0.5);
+            adr[t] = (g->r_out - g->r_in) * d_stretch_unit(0.5 * t, nr, g->stretch);
+        }
+        for (int t = 0; t <= 2 * nth; ++t) {
+            const double th = g->th0 + (g->th1 - g->th0) * (0.5 * t) / nth;
+            act[t] = std::cos(th);
+            ast[t] = std::sin(th);
+        }
+        for (int t = 0; t <= 2 * nph; ++t) {
+            const double ph = 2.0 * M_PI * (0.5 * t) / nph;
+            acp[t] = std::cos(ph);
+            asp[t] = std::sin(ph);
+        }
+        const size_t ab = sizeof(double) * (2 * ar.size() + 2 * act.size() + 2 * acp.size());
+        double* at = (double*)dalloc(h, ab);
+        if (!at) return MG_ENOMEM;
+        p = at;
+        AnalyticTables AT{};
+        CK(up(ar, &AT.rho));
+        CK(up(adr, &AT.drho));
+        CK(up(act, &AT.cth));
+        CK(up(ast, &AT.sth));
+        CK(up(acp, &AT.cph));
+        CK(up(asp, &AT.sph));
+        AT.dth = (g->th1 - g->th0) / nth;
+        AT.dph = 2.0 * M_PI / nph;
+        AT.ax1 = T.ax1;
+        AT.ax2 = T.ax2;
+        CK(launch_face_metric_analytic(AT, L0.D, h->stencil, L0.g64, h->J64, stream));
+        CK(cudaStreamSynchronize(stream));   // the host tables leave scope
+    } else {
+        CK(launch_face_metric(T, L0.D, h->stencil, L0.g64, h->J64, stream));
+    }
     {
         const i64 rows = h->stencil == 19 ? 19 : 1;
         if (!(L0.a64 = (double*)dalloc(h, sizeof(double) * rows * N))) return MG_ENOMEM;
@@ -877,6 +923,7 @@ mg_status mg_default_opts(mg_opts* o) {
     o->max_iters = 100;
     o->stencil = 0;
     o->autotune = 1;
+    o->metric = MG_METRIC_DISCRETE;
     return MG_OK;
 }
 

@@ -51,9 +51,7 @@ __device__ void face_columns(const MetricTables& t, int d, const int v[3], V3 co
 // det = col_0 . a_0 and J = cof^T / det, so
 //   G_pq = |det| sum_a J_pa J_qa = (a_p . a_q) / |det|.
 // Returns |det| and writes row d of G.
-__device__ double face_metric(const MetricTables& t, int d, const int v[3], double row[3]) {
-    V3 col[3];
-    face_columns(t, d, v, col);
+__device__ double g_from_columns(const V3 col[3], int d, double row[3]) {
     const V3 a0 = cross(col[1], col[2]);
     const V3 a1 = cross(col[2], col[0]);
     const V3 a2 = cross(col[0], col[1]);
@@ -63,6 +61,28 @@ __device__ double face_metric(const MetricTables& t, int d, const int v[3], doub
     row[1] = dot(ad, a1) / adet;
     row[2] = dot(ad, a2) / adet;
     return adet;
+}
+
+__device__ double face_metric(const MetricTables& t, int d, const int v[3], double row[3]) {
+    V3 col[3];
+    face_columns(t, d, v, col);
+    return g_from_columns(col, d, row);
+}
+
+// The analytic option: the columns dx/dzeta_p exactly at the face centre
+// from the mapping (x1 = ax1 r cos th, x2 = ax2 r sin th cos ph,
+// x3 = r sin th sin ph) and the derivatives of r(eta), th(zeta), ph(xi);
+// steps 2 to 5 as above.  Tables at half-index resolution: entry t is the
+// value at index t / 2 (faces at even t, cell centres at odd t).
+__device__ double face_metric_analytic(const AnalyticTables& t, int d, int i, int j, int k, double row[3]) {
+    const int tr = 2 * j + (d == 1 ? 0 : 1), tt = 2 * i + (d == 0 ? 0 : 1), tp = 2 * k + (d == 2 ? 0 : 1);
+    const double r = t.rho[tr], dr = t.drho[tr];
+    const double ct = t.cth[tt], st = t.sth[tt], cp = t.cph[tp], sp = t.sph[tp];
+    V3 col[3];
+    col[0] = {-t.ax1 * r * st * t.dth, t.ax2 * r * ct * cp * t.dth, r * ct * sp * t.dth};
+    col[1] = {t.ax1 * ct * dr, t.ax2 * st * cp * dr, st * sp * dr};
+    col[2] = {0.0, -t.ax2 * r * st * sp * t.dph, r * st * cp * t.dph};
+    return g_from_columns(col, d, row);
 }
 
 __global__ void k_face_metric(MetricTables t, Dims D, int stencil, double* g0,
@@ -120,6 +140,31 @@ __global__ void k_wall_G(MetricTables t, Dims D, double* r_lo, double* r_hi, dou
             face_metric(t, 0, vh, row);
             th_hi[p] = row[0];
         }
+    }
+}
+
+// The face metric of the analytic option, stored like k_face_metric's.
+__global__ void k_face_metric_analytic(AnalyticTables t, Dims D, int stencil, double* g0, double* g1, double* g2,
+                                       double* g3, double* g4, double* g5, double* g6, double* g7, double* g8,
+                                       double* J) {
+    const i64 n = D.n();
+    double* g[9] = {g0, g1, g2, g3, g4, g5, g6, g7, g8};
+    for (i64 c = blockIdx.x * (i64)blockDim.x + threadIdx.x; c < n; c += (i64)gridDim.x * blockDim.x) {
+        const C3 cc = decode(D, c);
+        const int k = cc.k, i = cc.i, j = cc.j;
+        double row[3], det_sum = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            det_sum += face_metric_analytic(t, d, i, j, k, row);
+            const bool wall = (d == 0 && i == 0) || (d == 1 && j == 0);
+            for (int q = 0; q < 3; ++q) {
+                double* dst = g[3 * d + q];
+                if (dst && (stencil == 19 || q == d)) dst[c] = wall ? 0.0 : row[q];
+            }
+        }
+        det_sum += face_metric_analytic(t, 0, i + 1, j, k, row);
+        det_sum += face_metric_analytic(t, 1, i, j + 1, k, row);
+        det_sum += face_metric_analytic(t, 2, i, j, k + 1, row);
+        J[c] = det_sum / 6.0;
     }
 }
 
@@ -397,6 +442,13 @@ cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsign
         if (lv.stencil == 19) k_line_factors<19, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
         else k_line_factors<7, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_metric_analytic(const AnalyticTables& t, Dims D, int stencil, double* const g[9],
+                                        double* J, cudaStream_t s) {
+    k_face_metric_analytic<<<grid_for(D.n(), 128), 128, 0, s>>>(t, D, stencil, g[0], g[1], g[2], g[3], g[4],
+                                                                 g[5], g[6], g[7], g[8], J);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,10 @@ mg_status finish(mg_handle* h, const char* what) {
 }
 
 mg_status start(mg_handle* h) {
+    if (h->opts.metric != MG_METRIC_DISCRETE) {
+        set_error("the pressure-correction steps need the discrete metric of Section 3.2");
+        return MG_EINVAL;
+    }
     if (cudaEventRecord(h->ev_in, h->user_stream) != cudaSuccess ||
         cudaStreamWaitEvent(h->stream, h->ev_in, 0) != cudaSuccess) {
         set_error("stream join failed");

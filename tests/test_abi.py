@@ -59,6 +59,9 @@ def test_host_side_validation_without_gpu(so):
     with pytest.raises(mgs.MGError) as e:
         mgs.mg_setup(g, dict(precision=7), stream=0)
     assert e.value.status == mgs.MG_EINVAL
+    with pytest.raises(mgs.MGError) as e:
+        mgs.mg_setup(g, dict(metric=2), stream=0)
+    assert e.value.status == mgs.MG_EINVAL
     o = mgs.default_opts()
     assert (o.precision, o.nu1, o.nu2, o.smoother) == (1, 2, 2, 0)
 

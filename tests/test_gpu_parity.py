@@ -369,3 +369,43 @@ def test_fused_red_black_sweep_matches_oracle(lib, name, prec, sweeps, path, mon
     ref = omg.smooth(lv, to_np(to_dev(x0, vtype(prec))), to_np(bd), sweeps, omg.GS)
     tol = {0: 1e-12, 1: 1e-5, 2: 3e-3}[prec]
     np.testing.assert_allclose(to_np(xd), ref, rtol=0, atol=tol * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ analytic metric option
+@pytest.mark.parametrize("name", ["sphere_stretched_ragged", "triaxial_stretched"])
+def test_analytic_metric_matches_oracle(lib, name):
+    """metric = analytic: the face rows and cell volumes against the oracle's
+    exact-derivative metric (FP64, 1e-12), and a solve against the oracle's
+    solve on that metric."""
+    torch, dev = torch_dev()
+    g = GRIDS[name]
+    sh = grid.shell(g)
+    fm = grid.face_metrics_analytic(sh)
+    h = lib.mg_setup(g, dict(precision=1, metric=1))
+    nr, nth, nph = sh.shape
+    G0 = fm["G0"][:, :nth, :, :].copy()
+    G0[:, 0] = 0
+    G1 = fm["G1"][:nr].copy()
+    G1[0] = 0
+    rows = [G0, G1, fm["G2"]]
+    buf = torch.empty(sh.n, dtype=torch.float64, device=dev)
+    for d in range(3):
+        for q in range(3):
+            if stencil_of(g) == 7 and q != d:
+                continue
+            lib.mg_get_metric(h, 0, 3 * d + q, buf)
+            np.testing.assert_allclose(to_np(buf), rows[d][..., q].ravel(), rtol=0,
+                                       atol=1e-12 * np.abs(rows[d][..., d]).max())
+    lib.mg_get_metric(h, 0, 9, buf)
+    np.testing.assert_allclose(to_np(buf), fm["J"].ravel(), rtol=1e-12)
+    f = W.rhs_modes(g, seed=3)
+    fd = to_dev(f, torch.float64)
+    xd = torch.zeros_like(fd)
+    rep = lib.mg_solve(h, fd, xd, tol=1e-12)
+    xo, info = omg.solve(g, f.ravel(), tol=1e-12, fm=fm, max_iters=400)
+    assert rep["rel_res"] <= 1e-12 and info["converged"]
+    err = np.abs(to_np(xd) - xo).max() / np.abs(xo).max()
+    assert err <= 1e-9, err
+    # the steps around the solve need the discrete metric
+    with pytest.raises(lib.MGError):
+        lib.mg_pc_rhs(h, torch.zeros(9 * sh.n, dtype=torch.float64, device=dev), buf)
