@@ -392,6 +392,13 @@ typedef struct {
 mg_status mg_adi_substep(mg_handle* h, double kappa, int nfields, const mg_walls* walls,
                          const double* const* un, const double* const* src, double* const* u);
 
+/* Bytes the library's device memory pool has handed out and not taken back
+ * on `device` (hierarchies, request buffers, work arrays of live handles and
+ * servers); freed blocks kept for reuse are not counted.  Test hook: with
+ * MG_TEST_FAIL_ALLOC_AFTER=n in the environment, every set-up fails its
+ * (n+1)-th device allocation with MG_ENOMEM (releasing what it took). */
+size_t mg_device_bytes_in_use(int device);
+
 /* ---------------------------------------------------------------------------
  * Kernel timing.  While enabled, the solve brackets chosen launch groups with
  * CUDA events on the handle's stream (a few events per V-cycle) and

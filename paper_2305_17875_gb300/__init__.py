@@ -121,6 +121,7 @@ _SIGS = {
     "mg_pc_rhs": ([_vp, _vp, _vp], _i),
     "mg_pc_correct": ([_vp, _vp, _vp], _i),
     "mg_adi_substep": ([_vp, _d, _i, C.POINTER(mg_walls), _vp, _vp, _vp], _i),
+    "mg_device_bytes_in_use": ([_i], C.c_size_t),
     "mg_thomas_work_bytes": ([C.POINTER(mg_lines), _i], C.c_size_t),
     "mg_thomas": ([C.POINTER(mg_lines), _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "mg_serve_default_opts": ([C.POINTER(mg_serve_opts)], _i),
@@ -359,6 +360,10 @@ def mg_thomas(lines: dict, a, b, c, g, x, periodic=False, work=None, stream=None
 
 
 MG_WALL_FLUX0, MG_WALL_VALUE = 0, 1
+
+
+def mg_device_bytes_in_use(device: int = 0) -> int:
+    return int(_lib.mg_device_bytes_in_use(int(device)))
 
 
 def mg_adi_substep(h: Handle, kappa, un, u, src=None, walls=None):

@@ -129,6 +129,7 @@ int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
 
 void* dalloc(mg_handle* h, size_t bytes) {
     void* p = nullptr;
+    if (h->fail_alloc_after >= 0 && h->allocs_done++ >= h->fail_alloc_after) return nullptr;
     if (cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, lib_pool(h->device), h->stream) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -452,6 +453,7 @@ mg_status autotune(mg_handle* h) {
 mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t stream, mg_handle* h) {
     h->grid = *g;
     h->opts = *o;
+    if (const char* v = std::getenv("MG_TEST_FAIL_ALLOC_AFTER")) h->fail_alloc_after = std::atoll(v);
     h->stencil = stencil_of(g, o);
     h->prec = o->precision;
     h->user_stream = stream;
@@ -925,6 +927,15 @@ mg_status mg_default_opts(mg_opts* o) {
     o->autotune = 1;
     o->metric = MG_METRIC_DISCRETE;
     return MG_OK;
+}
+
+size_t mg_device_bytes_in_use(int device) {
+    size_t used = 0;
+    cudaMemPool_t p = lib_pool(device);
+    unsigned long long v = 0;   // the attribute is a 64-bit count
+    if (p && cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &v) == cudaSuccess) used = (size_t)v;
+    else cudaGetLastError();
+    return used;
 }
 
 mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out) {

@@ -58,6 +58,8 @@ struct mg_handle {
     int ncoarse = 0;
     double sumJ = 0.0;
     size_t bytes = 0;
+    long long fail_alloc_after = -1;  // test hook (MG_TEST_FAIL_ALLOC_AFTER): fail set-up allocations from this one on
+    long long allocs_done = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches = 0;           // kernels launched by the current solve
     // kernel timing (mg_profile_enable)

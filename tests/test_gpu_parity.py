@@ -409,3 +409,32 @@ def test_analytic_metric_matches_oracle(lib, name):
     # the steps around the solve need the discrete metric
     with pytest.raises(lib.MGError):
         lib.mg_pc_rhs(h, torch.zeros(9 * sh.n, dtype=torch.float64, device=dev), buf)
+
+
+def test_setup_allocation_failures_release_everything(lib, monkeypatch):
+    """A set-up whose n-th device allocation fails returns MG_ENOMEM and gives
+    back every byte it took, for every n (fault injected on the host)."""
+    import gc
+    import torch
+    g = GRIDS["triaxial_stretched"]
+    gc.collect()
+    torch.cuda.synchronize()
+    base = lib.mg_device_bytes_in_use(0)
+    n, failures = 0, 0
+    while True:
+        monkeypatch.setenv("MG_TEST_FAIL_ALLOC_AFTER", str(n))
+        try:
+            h = lib.mg_setup(g, dict(precision=1, autotune=0))
+        except lib.MGError as e:
+            assert e.status == lib.MG_ENOMEM
+            torch.cuda.synchronize()          # the frees are stream ordered
+            assert lib.mg_device_bytes_in_use(0) == base
+            failures += 1
+            n += 1
+            continue
+        h.close()
+        break
+    monkeypatch.delenv("MG_TEST_FAIL_ALLOC_AFTER")
+    gc.collect()
+    torch.cuda.synchronize()
+    assert failures > 10 and lib.mg_device_bytes_in_use(0) == base
