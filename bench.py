@@ -280,6 +280,28 @@ def config_of(args, g, rep, stencil):
     return c
 
 
+# ----------------------------------------------------------------- ranks
+def sync_ranks():
+    """Barrier across the ranks of a distributed run (no-op otherwise)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(value):
+    """The largest value over the job's ranks after a barrier (the job is as
+    slow as its slowest rank); the value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- our arm
 def time_solves(mgs, h, fd, xd, steps, flush, torch):
     ms, reps = [], []
@@ -349,11 +371,7 @@ def run_ours(args, rank, world, local_rank):
              ("restrict0", mgs.PROF_RESTRICT0), ("prolong0", mgs.PROF_PROLONG0),
              ("update", mgs.PROF_UPDATE), ("tail", mgs.PROF_TAIL))}
     mgs.mg_profile_enable(h, False)
-    ms_step = statistics.mean(ms)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(statistics.mean(ms))
     rep = reps[-1]
     info0 = mgs.mg_get_level_info(h, 0)
     info1 = mgs.mg_get_level_info(h, 1) if info0["levels"] > 1 else info0
@@ -546,6 +564,7 @@ def run_batch(args, rank, world, local_rank):
         batch_once(hs)
     clocks = Clocks(local_rank)
     torch.cuda.synchronize()
+    sync_ranks()
     clocks.start()
     mgs.mg_profile_enable(hs[0], True)
     runs = [batch_once(hs) for _ in range(args.steps)]
@@ -553,7 +572,7 @@ def run_batch(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = [r[0] for r in runs]
     reps = runs[-1][1]
-    ms_step = statistics.mean(ms)
+    ms_step = max_over_ranks(statistics.mean(ms))
     # the same shells one after another
     seq = 0.0
     for h, f, x in zip(hs, fds, xds):
@@ -618,6 +637,7 @@ def run_serve(args, rank, world, local_rank):
     while mgs.mg_serve_poll(sv, t, None) is None:
         time.sleep(0.001)
     tickets, out = [], {}
+    sync_ranks()
     t0 = time.perf_counter()
     nxt = 0
     while len(out) < len(reqs):
@@ -633,7 +653,7 @@ def run_serve(args, rank, world, local_rank):
             if res is not None:
                 out[q] = res[1]
         time.sleep(0.0005)
-    wall = time.perf_counter() - t0
+    wall = max_over_ranks(time.perf_counter() - t0)
     stats = mgs.mg_serve_stats(sv)
     sv.close()
     lat = np.array([out[q]["seconds"] * 1e3 for q in range(len(reqs))])
