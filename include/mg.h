@@ -124,8 +124,12 @@ const char* mg_version(void);
 const char* mg_last_error(void);
 mg_status mg_default_opts(mg_opts* opts);
 
-/* Device memory a handle for this grid and these options would hold (bytes),
- * or 0 if the description is invalid. */
+/* Device memory a handle for this grid and these options would hold after
+ * mg_setup (bytes; an upper estimate), or 0 if the description is invalid.
+ * Arrays made on first use are not included: the face C of the
+ * pressure-correction steps (30 nr*nth*nph doubles), the ADI line work and
+ * wall metric (about 2 nr*nth*nph doubles), radial-line factors requested by
+ * mg_smooth on a handle set up with another smoother. */
 size_t mg_footprint_bytes(const mg_grid_desc* grid, const mg_opts* opts);
 
 /* Build a handle: face metrics of Section 3.2 on the device (FP64), the
