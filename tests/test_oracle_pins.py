@@ -508,3 +508,18 @@ def test_analytic_metric_keeps_the_operator_invariants():
     scale = abs(A).sum(axis=1).max()
     assert np.abs(A @ one).max() < 1e-13 * scale
     assert np.abs(A.T @ one).max() < 1e-13 * scale
+
+
+@pytest.mark.parametrize("name", ["oblate"])
+def test_axisymmetric_mapping_has_no_longitude_cross_metric(name):
+    """An axisymmetric map (the oblate shell) keeps the longitude direction
+    orthogonal to the meridional plane face by face in the discrete metric of
+    Section 3.2 too (the edge sums of step 1 are symmetric about the face's
+    mid-longitude): G_r,phi and G_th,phi vanish to rounding, while G_r,th
+    does not."""
+    sh = sh_of(16, **MAPS[name])
+    fm = grid.face_metrics(sh)
+    scale = max(np.abs(fm[f"G{d}"][..., d]).max() for d in range(3))
+    for arr, q in (("G0", 2), ("G1", 2), ("G2", 0), ("G2", 1)):
+        assert np.abs(fm[arr][..., q]).max() < 1e-14 * scale, (arr, q)
+    assert np.abs(fm["G0"][..., 1]).max() > 1e-3 * scale
