@@ -67,7 +67,7 @@ __device__ __forceinline__ void gs_pass(const CF& cf, const Dims& D, T* x, const
             const C3 p{j, i, 2 * kk + (((colour >> 1) + j) & 1)};
             const int c = cidx(D, p);
             Nbr19<T> X;
-            X.load(XLin<T>{x}, D, c, p);
+            X.load(XLin<T>{x}, D, c, p, !cf.has(2));
             const T r = b[c] - apply19<T>(cf, X, D, c, p);
             x[c] = X.v[0] + r / diag_cell<S, T>(cf, D, p);
         }
@@ -239,7 +239,9 @@ struct Group19 {
     T lo[9], hi[9];      // longitude k0 - 1 and k0 + 4 of the rows with dj == 0 or di == 0
     bool ju, iu;
     int plane;
-    __device__ __forceinline__ void load(const T* x, const Dims& D, int j, int i, int k0) {
+    // axi: no longitude cross terms, so the off-centre rows need no cells
+    // beyond the group in longitude
+    __device__ __forceinline__ void load(const T* x, const Dims& D, int j, int i, int k0, bool axi) {
         plane = D.nth * D.nph;
         c0 = (j * D.nth + i) * D.nph + k0;
         rb = c0 - k0;
@@ -255,9 +257,11 @@ struct Group19 {
             for (int b = 0; b < 3; ++b) {
                 const int r = a * 3 + b, o = oj[a] + oi[b];
                 ld4(x + c0 + o, R[r]);
-                if (a == 1 || b == 1) {
+                if ((a == 1 && b == 1) || (!axi && (a == 1 || b == 1))) {
                     lo[r] = x[rb + o + km];
                     hi[r] = x[rb + o + kw];
+                } else {
+                    lo[r] = hi[r] = (T)0;
                 }
             }
     }
@@ -278,13 +282,13 @@ struct Group19 {
 // acc + sgn F for the d-face of cell m of the group; G[q][m] is component
 // 3d + q of the face's metric row.
 template <int d, int side, int m, typename T>
-__device__ __forceinline__ T face19g(T acc, const Group19<T>& g, const T G[3][4]) {
+__device__ __forceinline__ T face19g(T acc, const Group19<T>& g, const T G[3][4], bool axi) {
     constexpr int sL = side < 0 ? -1 : 0, sU = side < 0 ? 0 : 1;
     const T sgn = (T)side;
     acc = fma(sgn * G[d][m], g.template atd<m, d, sU, d, 0>() - g.template atd<m, d, sL, d, 0>(), acc);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        if (q == d) continue;
+        if (q == d || (axi && (q == 2 || d == 2))) continue;   // absent longitude cross terms
         T plus, minus;
         if (q == 0) {
             plus = g.template atd<m, d, sL, 0, 1>() + g.template atd<m, d, sU, 0, 1>();
@@ -302,11 +306,18 @@ __device__ __forceinline__ T face19g(T acc, const Group19<T>& g, const T G[3][4]
 }
 
 template <int d, int side, int MASK, typename T>
-__device__ __forceinline__ void face19g_all(T acc[4], const Group19<T>& g, const T G[3][4]) {
-    if (MASK & 1) acc[0] = face19g<d, side, 0>(acc[0], g, G);
-    if (MASK & 2) acc[1] = face19g<d, side, 1>(acc[1], g, G);
-    if (MASK & 4) acc[2] = face19g<d, side, 2>(acc[2], g, G);
-    if (MASK & 8) acc[3] = face19g<d, side, 3>(acc[3], g, G);
+__device__ __forceinline__ void face19g_all(T acc[4], const Group19<T>& g, const T G[3][4], bool axi) {
+    if (MASK & 1) acc[0] = face19g<d, side, 0>(acc[0], g, G, axi);
+    if (MASK & 2) acc[1] = face19g<d, side, 1>(acc[1], g, G, axi);
+    if (MASK & 4) acc[2] = face19g<d, side, 2>(acc[2], g, G, axi);
+    if (MASK & 8) acc[3] = face19g<d, side, 3>(acc[3], g, G, axi);
+}
+
+// component a of four consecutive cells, zero when the component is absent
+template <typename T, typename CF>
+__device__ __forceinline__ void load4_or0(const CF& cf, int a, int idx, T v[4]) {
+    if (cf.has(a)) cf.load4(a, idx, v);
+    else v[0] = v[1] = v[2] = v[3] = (T)0;
 }
 
 // (A x) of the group's cells in MASK (bit m), in apply19's face order.  Lower
@@ -316,31 +327,32 @@ template <int MASK, typename T, typename CF>
 __device__ __forceinline__ void apply19_group(const CF& cf, const Dims& D, const Group19<T>& g, int j, int i,
                                               T acc[4]) {
     T G[3][4];
+    const bool axi = !cf.has(2);
     for (int m = 0; m < 4; ++m) acc[m] = (T)0;
     if (j > 0) {
-        for (int q = 0; q < 3; ++q) cf.load4(3 + q, g.c0, G[q]);
-        face19g_all<1, -1, MASK>(acc, g, G);
+        for (int q = 0; q < 3; ++q) load4_or0<T>(cf, 3 + q, g.c0, G[q]);
+        face19g_all<1, -1, MASK>(acc, g, G, axi);
     }
     if (g.ju) {
-        for (int q = 0; q < 3; ++q) cf.load4(3 + q, g.c0 + g.plane, G[q]);
-        face19g_all<1, 1, MASK>(acc, g, G);
+        for (int q = 0; q < 3; ++q) load4_or0<T>(cf, 3 + q, g.c0 + g.plane, G[q]);
+        face19g_all<1, 1, MASK>(acc, g, G, axi);
     }
     if (i > 0) {
-        for (int q = 0; q < 3; ++q) cf.load4(q, g.c0, G[q]);
-        face19g_all<0, -1, MASK>(acc, g, G);
+        for (int q = 0; q < 3; ++q) load4_or0<T>(cf, q, g.c0, G[q]);
+        face19g_all<0, -1, MASK>(acc, g, G, axi);
     }
     if (g.iu) {
-        for (int q = 0; q < 3; ++q) cf.load4(q, g.c0 + D.nph, G[q]);
-        face19g_all<0, 1, MASK>(acc, g, G);
+        for (int q = 0; q < 3; ++q) load4_or0<T>(cf, q, g.c0 + D.nph, G[q]);
+        face19g_all<0, 1, MASK>(acc, g, G, axi);
     }
-    for (int q = 0; q < 3; ++q) cf.load4(6 + q, g.c0, G[q]);
-    face19g_all<2, -1, MASK>(acc, g, G);
+    for (int q = 0; q < 3; ++q) load4_or0<T>(cf, 6 + q, g.c0, G[q]);
+    face19g_all<2, -1, MASK>(acc, g, G, axi);
     // upper longitude faces: the next cell's lower face
     for (int q = 0; q < 3; ++q) {
-        const T nxt = (T)cf(6 + q, g.rb + g.kw);
+        const T nxt = cf.has(6 + q) ? (T)cf(6 + q, g.rb + g.kw) : (T)0;
         G[q][0] = G[q][1], G[q][1] = G[q][2], G[q][2] = G[q][3], G[q][3] = nxt;
     }
-    face19g_all<2, 1, MASK>(acc, g, G);
+    face19g_all<2, 1, MASK>(acc, g, G, axi);
 }
 
 // 19-point residual + children-sum restriction over groups (as restrict_pass7v).
@@ -359,7 +371,7 @@ __device__ __forceinline__ void restrict_pass19v(const CF& cf, const Dims& D, co
             for (int di = 0; di < cz; ++di) {
                 const int j = ce * (int)J + dj, i = cz * I + di;
                 Group19<T> g;
-                g.load(x, D, j, i, 4 * q);
+                g.load(x, D, j, i, 4 * q, !cf.has(2));
                 T B[4], ax[4];
                 ldg4(b + g.c0, B);
                 apply19_group<15>(cf, D, g, j, i, ax);
@@ -416,7 +428,7 @@ __device__ __forceinline__ void restrict_pass(const CF& cf, const Dims& D, const
                     } else {
                         const int id = cidx(D, c);
                         Nbr19<T> X;
-                        X.load(XLin<T>{x}, D, id, c);
+                        X.load(XLin<T>{x}, D, id, c, !cf.has(2));
                         s += b[id] - apply19<T>(cf, X, D, id, c);
                     }
                 }

@@ -171,7 +171,14 @@ double d_stretch_unit(double jv, int n, double rx) {
 }
 
 int ncomp(int stencil) { return stencil == 19 ? 9 : 3; }
-bool stored(int stencil, int a) { return stencil == 19 || a == 0 || a == 4 || a == 8; }
+// Metric components kept per level: the diagonal for 7 points; all nine for
+// 19 points, except on an axisymmetric mapping, whose longitude cross
+// components (zeta-xi, eta-xi, xi-zeta, xi-eta) vanish to rounding face by face
+// and are dropped (the operator is then the 11-point one they leave).
+bool stored(const mg_handle* h, int a) {
+    if (h->stencil == 7) return a == 0 || a == 4 || a == 8;
+    return !h->axi || (a != 2 && a != 5 && a != 6 && a != 7);
+}
 
 mg_status read_scalars(mg_handle* h, int count) {
     CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
@@ -455,6 +462,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     h->opts = *o;
     if (const char* v = std::getenv("MG_TEST_FAIL_ALLOC_AFTER")) h->fail_alloc_after = std::atoll(v);
     h->stencil = stencil_of(g, o);
+    h->axi = h->stencil == 19 && g->mapping != MG_MAP_TRIAXIAL && std::getenv("MG_FULL19") == nullptr;
     h->prec = o->precision;
     h->user_stream = stream;
     h->use_graph = std::getenv("MG_NO_GRAPH") == nullptr;
@@ -509,7 +517,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     L0.D = Dims{nr, nth, nph};
     const i64 N = L0.D.n();
     for (int a = 0; a < 9; ++a)
-        if (stored(h->stencil, a) && !(L0.g64[a] = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
+        if (stored(h, a) && !(L0.g64[a] = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
     if (!(h->J64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
     if (!(h->b64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
     if (!(h->x64 = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
@@ -577,7 +585,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         Level c;
         c.D = Dims{fine.D.nr / fine.ce, fine.D.nth / fine.cz, fine.D.nph / fine.cx};
         for (int a = 0; a < 9; ++a)
-            if (stored(h->stencil, a) && !(c.g64[a] = (double*)dalloc(h, sizeof(double) * c.D.n())))
+            if (stored(h, a) && !(c.g64[a] = (double*)dalloc(h, sizeof(double) * c.D.n())))
                 return MG_ENOMEM;
         CK(launch_coarsen_faces(fine.view(h->stencil), c.D, c.g64, stream));
         h->L.push_back(c);
@@ -601,7 +609,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     for (Level& lv : h->L) {
         const i64 n = lv.D.n();
         for (int a = 0; a < 9; ++a) {
-            if (!stored(h->stencil, a)) continue;
+            if (!stored(h, a)) continue;
             if (h->prec == PREC32) {
                 if (!(lv.g32[a] = (float*)dalloc(h, sizeof(float) * n))) return MG_ENOMEM;
                 CK(launch_cast32(lv.g64[a], lv.g32[a], n, stream));

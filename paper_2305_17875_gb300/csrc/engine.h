@@ -41,6 +41,7 @@ struct mg_handle {
     mg_grid_desc grid{};
     mg_opts opts{};
     int stencil = 7;
+    bool axi = false;                 // 19 points on an axisymmetric mapping: longitude cross terms dropped
     int prec = 1;                     // PREC64 / PREC32 / PREC16
     cudaStream_t stream = nullptr;        // private work stream of the handle
     cudaStream_t user_stream = nullptr;   // caller's stream; joined by events

@@ -59,7 +59,7 @@ __device__ __forceinline__ T line_residual(const CF& cf, const Dims& D, const T*
         const C3 p{j, i, k};
         const int c = cidx(D, p);
         Nbr19<T> X;
-        X.load(XLin<T>{x}, D, c, p);
+        X.load(XLin<T>{x}, D, c, p, !cf.has(2));
         return b[c] - apply19<T>(cf, X, D, c, p);
     }
 }

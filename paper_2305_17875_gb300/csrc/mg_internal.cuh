@@ -104,8 +104,12 @@ __device__ __forceinline__ C3 shift(C3 c, int s, const Dims& D) {
 }
 
 // ---------------------------------------------------------------- coefficients
+// A metric component whose array is absent (null) is zero: the cross terms
+// of the 7-point operator, and on an axisymmetric mapping the longitude cross
+// terms of the 19-point one (zero to rounding there).
 struct CoefF64 {
     const double* g[9];
+    __device__ __forceinline__ bool has(int a) const { return g[a] != nullptr; }
     __device__ __forceinline__ double operator()(int a, i64 idx) const { return __ldg(g[a] + idx); }
     // four consecutive cells from idx (a multiple of 4)
     __device__ __forceinline__ void load4(int a, int idx, double v[4]) const {
@@ -116,6 +120,7 @@ struct CoefF64 {
 };
 struct CoefF32 {
     const float* g[9];
+    __device__ __forceinline__ bool has(int a) const { return g[a] != nullptr; }
     __device__ __forceinline__ float operator()(int a, i64 idx) const { return __ldg(g[a] + idx); }
     __device__ __forceinline__ void load4(int a, int idx, float v[4]) const {
         const float4 p = __ldg(reinterpret_cast<const float4*>(g[a] + idx));
@@ -127,6 +132,7 @@ struct CoefF32 {
 struct CoefF16 {
     const __half* g[9];
     float s[9];
+    __device__ __forceinline__ bool has(int a) const { return g[a] != nullptr; }
     __device__ __forceinline__ float operator()(int a, i64 idx) const {
         return __half2float(__ldg(g[a] + idx)) * s[a];
     }
@@ -165,9 +171,9 @@ __device__ __forceinline__ T add_flux(T acc, T sgn, const CF& cf, const XA& X, c
     const i64 u = cidx(D, U);
     acc = fma(sgn * (T)cf(4 * d, u), X(U) - X(L), acc);   // 4 d = 3 d + d
     if (S == 19) {
-        if (d != 0) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 0, u), cross_diff<d, 0, T>(X, D, L, U), acc);
-        if (d != 1) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 1, u), cross_diff<d, 1, T>(X, D, L, U), acc);
-        if (d != 2) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 2, u), cross_diff<d, 2, T>(X, D, L, U), acc);
+        if (d != 0 && cf.has(3 * d + 0)) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 0, u), cross_diff<d, 0, T>(X, D, L, U), acc);
+        if (d != 1 && cf.has(3 * d + 1)) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 1, u), cross_diff<d, 1, T>(X, D, L, U), acc);
+        if (d != 2 && cf.has(3 * d + 2)) acc = fma(sgn * (T)0.25 * (T)cf(3 * d + 2, u), cross_diff<d, 2, T>(X, D, L, U), acc);
     }
     return acc;
 }
@@ -213,16 +219,20 @@ __device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
             T w = 0;
             if (hasEu) w += (T)cf(3, eu);     // eta faces, column zeta
             if (hasEl) w -= (T)cf(3, self);
-            w += (T)cf(6, xu);                 // xi faces, column zeta
-            w -= (T)cf(6, self);
+            if (cf.has(6)) {
+                w += (T)cf(6, xu);             // xi faces, column zeta
+                w -= (T)cf(6, self);
+            }
             dg = fma((T)0.25 * sz, w, dg);
         }
         if (se != (T)0) {
             T w = 0;
             if (hasZu) w += (T)cf(1, zu);     // zeta faces, column eta
             if (hasZl) w -= (T)cf(1, self);
-            w += (T)cf(7, xu);                 // xi faces, column eta
-            w -= (T)cf(7, self);
+            if (cf.has(7)) {
+                w += (T)cf(7, xu);             // xi faces, column eta
+                w -= (T)cf(7, self);
+            }
             dg = fma((T)0.25 * se, w, dg);
         }
     }
@@ -342,14 +352,20 @@ __host__ __device__ constexpr int row_index(int dj, int di, int dk) {
 template <typename T>
 struct Nbr19 {
     T v[19];
+    // axi: the longitude cross terms are absent, so the eight edges with a
+    // longitude offset and a radial or colatitude offset are not read (zero)
     template <typename XL>
-    __device__ __forceinline__ void load(const XL& X, const Dims& D, int c, C3 p) {
+    __device__ __forceinline__ void load(const XL& X, const Dims& D, int c, C3 p, bool axi) {
         const int plane = D.nth * D.nph;
         const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
         const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
         const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
 #pragma unroll
-        for (int n = 0; n < 19; ++n) v[n] = X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
+        for (int n = 0; n < 19; ++n) {
+            const bool phi_edge = row_off(n, 2) != 0 && (row_off(n, 0) != 0 || row_off(n, 1) != 0);
+            v[n] = (axi && phi_edge) ? (T)0
+                                     : X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
+        }
     }
     // value at offset a along paper direction da and b along direction db
     // (directions 0 zeta -> i, 1 eta -> j, 2 xi -> k)
@@ -371,7 +387,7 @@ __device__ __forceinline__ T add_flux19(T acc, const CF& cf, const Nbr19<T>& X, 
     acc = fma(sgn * (T)cf(4 * d, u), X.template at<d, sU, d, 0>() - X.template at<d, sL, d, 0>(), acc);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        if (q == d) continue;
+        if (q == d || !cf.has(3 * d + q)) continue;
         T plus, minus;
         if (q == 0) {
             plus = X.template at<d, sL, 0, 1>() + X.template at<d, sU, 0, 1>();

@@ -73,7 +73,7 @@ __device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* 
             const C3 p{j, i, 2 * kk + (((colour >> 1) + j) & 1)};
             const int c = cidx(D, p);
             Nbr19<T> X;
-            X.load(XLinAcc<T, CG>{x}, D, c, p);
+            X.load(XLinAcc<T, CG>{x}, D, c, p, !cf.has(2));
             const T r = ldv<T, CG>(b + c) - apply19<T>(cf, X, D, c, p);
             x[c] = X.v[0] + r / diag_cell<S, T>(cf, D, p);
         }
@@ -98,7 +98,7 @@ __device__ __forceinline__ void restrict_range(const CF& cf, const Dims& D, cons
                     } else {
                         const int id = cidx(D, c);
                         Nbr19<T> X;
-                        X.load(XLinAcc<T, CG>{x}, D, id, c);
+                        X.load(XLinAcc<T, CG>{x}, D, id, c, !cf.has(2));
                         s += ldv<T, CG>(b + id) - apply19<T>(cf, X, D, id, c);
                     }
                 }
