@@ -627,7 +627,8 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
                 q.load(tk.v.c64, tk.v.D, cc.j, cc.i, cc.k, XLin<double>{(const double*)tk.x});
                 r = q.resid_rows(__ldcs(b + c), __ldcs(tk.a64 + c));
             } else {
-                r = resid_rows19(tk.a64, N, (const double*)tk.x, tk.v.D, (int)c, cc, __ldcs(b + c));
+                r = resid_rows19(tk.a64, N, (const double*)tk.x, tk.v.D, (int)c, cc, __ldcs(b + c),
+                                 tk.v.c64.has(2) ? 19 : 11);
             }
             if (r32) r32[c] = narrow_rn(r) * scale32;
             acc = fma(r, r, acc);

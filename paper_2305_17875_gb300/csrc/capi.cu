@@ -563,7 +563,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         CK(launch_face_metric(T, L0.D, h->stencil, L0.g64, h->J64, stream));
     }
     {
-        const i64 rows = h->stencil == 19 ? 19 : 1;
+        const i64 rows = assembled_rows(L0.view(h->stencil));
         if (!(L0.a64 = (double*)dalloc(h, sizeof(double) * rows * N))) return MG_ENOMEM;
         CK(launch_assemble_rows(L0.view(h->stencil), L0.a64, stream));
     }

@@ -258,7 +258,7 @@ __global__ void k_dense(CoefF64 cf, Dims D, double* A) {
 // neighbour that coincides with an earlier one (a longitude ring of two cells)
 // keeps its coefficient on the earlier entry and stores 0.
 template <int S>
-__global__ void k_assemble(CoefF64 cf, Dims D, double* a) {
+__global__ void k_assemble(CoefF64 cf, Dims D, double* a, int nrows) {
     const i64 N = D.n();
     for (i64 cl = blockIdx.x * (i64)blockDim.x + threadIdx.x; cl < N; cl += (i64)gridDim.x * blockDim.x) {
         const C3 p = decode(D, cl);
@@ -267,7 +267,7 @@ __global__ void k_assemble(CoefF64 cf, Dims D, double* a) {
             continue;
         }
         i64 t[19];
-        for (int n = 0; n < 19; ++n) {
+        for (int n = 0; n < nrows; ++n) {
             const int j = p.j + row_off(n, 0), i = p.i + row_off(n, 1);
             int k = p.k + row_off(n, 2);
             k = k < 0 ? k + D.nph : (k >= D.nph ? k - D.nph : k);
@@ -427,8 +427,9 @@ cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double
 }
 
 cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s) {
-    if (lv.stencil == 19) k_assemble<19><<<grid_for(lv.D.n(), 128), 128, 0, s>>>(lv.c64, lv.D, a);
-    else k_assemble<7><<<grid_for(lv.D.n(), 256), 256, 0, s>>>(lv.c64, lv.D, a);
+    if (lv.stencil == 19)
+        k_assemble<19><<<grid_for(lv.D.n(), 128), 128, 0, s>>>(lv.c64, lv.D, a, assembled_rows(lv));
+    else k_assemble<7><<<grid_for(lv.D.n(), 256), 256, 0, s>>>(lv.c64, lv.D, a, 1);
     return cudaGetLastError();
 }
 

@@ -419,9 +419,10 @@ __device__ __forceinline__ T apply19(const CF& cf, const Nbr19<T>& X, const Dims
     return acc;
 }
 
-// b_c - (A x)_c from the 19 assembled coefficients a[n * N + c] (row_off order).
+// b_c - (A x)_c from the assembled coefficients a[n * N + c] (row_off order;
+// nrows = 19, or 11 when the longitude edges 11..18 are absent).
 __device__ __forceinline__ double resid_rows19(const double* __restrict__ a, i64 N, const double* __restrict__ x,
-                                               const Dims& D, int c, C3 p, double b) {
+                                               const Dims& D, int c, C3 p, double b, int nrows) {
     const int plane = D.nth * D.nph;
     const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
     const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
@@ -429,6 +430,7 @@ __device__ __forceinline__ double resid_rows19(const double* __restrict__ a, i64
     double r = b;
 #pragma unroll
     for (int n = 0; n < 19; ++n) {
+        if (n >= nrows) break;
         const int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
         r = fma(-__ldcs(a + n * N + c), __ldg(x + c + o), r);
     }

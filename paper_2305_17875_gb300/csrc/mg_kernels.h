@@ -32,7 +32,12 @@ cudaError_t launch_face_metric(const MetricTables& t, Dims D, int stencil, doubl
                                double* J, cudaStream_t s);
 cudaError_t launch_coarsen_faces(const LevelView& fine, Dims Dc, double* const gc[9], cudaStream_t s);
 // Assembled FP64 rows of a level (row_off order): 19 x n doubles for the
-// 19-point operator, n (the centre coefficient) for the 7-point one.
+// 19-point operator (11 x n without the longitude cross terms: the entries
+// 11..18 are the longitude edges), n (the centre coefficient) for the
+// 7-point one.
+inline int assembled_rows(const LevelView& lv) {
+    return lv.stencil == 7 ? 1 : (lv.c64.g[2] ? 19 : 11);
+}
 cudaError_t launch_assemble_rows(const LevelView& lv, double* a, cudaStream_t s);
 cudaError_t launch_cast32(const double* src, float* dst, i64 n, cudaStream_t s);
 cudaError_t launch_cast16(const double* src, __half* dst, i64 n, float inv_scale, cudaStream_t s);
