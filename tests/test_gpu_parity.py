@@ -438,3 +438,29 @@ def test_setup_allocation_failures_release_everything(lib, monkeypatch):
     gc.collect()
     torch.cuda.synchronize()
     assert failures > 10 and lib.mg_device_bytes_in_use(0) == base
+
+
+def test_axisymmetric_operator_matches_the_full_19_point_one(lib, monkeypatch):
+    """The oblate shell's operator without the longitude cross terms (zero to
+    rounding) and with all nine components (MG_FULL19) give the same solve to
+    rounding, and the component arrays the former drops read back as zero."""
+    import torch
+    g = GRIDS["oblate"]
+    n = grid.shell(g).n
+    f = W.rhs_modes(g, seed=12)
+    xs = {}
+    for full in (False, True):
+        if full:
+            monkeypatch.setenv("MG_FULL19", "1")
+        h = lib.mg_setup(g, dict(precision=0))
+        fd = to_dev(f, torch.float64)
+        xd = torch.zeros_like(fd)
+        lib.mg_solve(h, fd, xd, tol=1e-13)
+        xs[full] = to_np(xd)
+        buf = torch.empty(n, dtype=torch.float64, device="cuda")
+        lib.mg_get_metric(h, 0, 5, buf)          # eta-face row, xi column
+        if not full:
+            assert not buf.any()
+        h.close()
+    monkeypatch.delenv("MG_FULL19")
+    np.testing.assert_allclose(xs[False], xs[True], rtol=0, atol=1e-11 * np.abs(xs[True]).max())
