@@ -7,18 +7,21 @@
 //   sweep zeta:  (J - kappa L_zeta) u*   = J u^n + s + kappa L_zeta u^n + 2 kappa (L_eta + L_xi) u^n
 //   sweep eta:   (J - kappa L_eta)  u**  = J u* - kappa L_eta u^n
 //   sweep xi:    (J - kappa L_xi)   u*** = J u** - kappa L_xi u^n     (periodic)
-// One launch per sweep, two threads per grid line: a thread forms each row
-// of its tridiagonal system from the face metric (G_pp of the row's two faces,
-// J) and the stencil of u^n, then eliminates as it goes (normalised Thomas,
-// cp kept in a work array laid out [row][line]) and back-substitutes into u.
-// Up to four fields with the same kappa and wall kinds (the three velocity
-// components) share the matrix: one division per row serves all of them, and
-// their independent recurrences fill the FP64 pipeline of a thread.
-// Two threads per line eliminate from both ends to the middle row (a twisted
-// factorisation; see k_adi2).  Colatitude and radius lines are adjacent in
-// memory along longitude, so their loads coalesce; longitude lines are
-// contiguous (a thread walks a run of consecutive cells).  Right sides read only the line's own cell of
-// the previous sweep's result, so every sweep works in place on u.
+// One launch per sweep, two threads per grid line (adjacent lanes): each
+// forms the rows of its half of the line's tridiagonal system from the face
+// metric (G_pp of the row's two faces, J) and the stencil of u^n, and
+// eliminates towards the middle row as it goes (a twisted factorisation:
+// normalised Thomas from both ends, pivot ratios in a work array laid out
+// [row][line]); the lanes swap their last pivots by a shuffle, solve the
+// middle row and substitute outwards into u.  Periodic longitude lines carry
+// the corner column as an extra right side (Eqs. TAP2-TAP8).  Up to four
+// fields with the same kappa and wall kinds (the three velocity components)
+// share the matrix: one division per row serves all of them, and their
+// independent recurrences fill a thread's FP64 pipeline.  Colatitude and
+// radius lines are adjacent in memory along longitude, so their loads
+// coalesce; longitude lines are contiguous (a thread walks a run of
+// consecutive cells).  Right sides read only the line's own cell of the
+// previous sweep's result, so every sweep works in place on u.
 //
 // Walls: zero flux, or a value held on the wall face half a cell from the
 // centre, whose face flux is 2 G_pp(wall face) (u_w - u_c) outward; G_pp of
