@@ -433,7 +433,7 @@ mg_status autotune(mg_handle* h) {
         }
         return MG_OK;
     };
-    for (int cap : {8, 32}) {
+    for (int cap : {4, 8, 32}) {   // 4: one wave of the level kernels at four resident CTAs per SM
         Schedule sc = best;
         sc.vb_cap = cap;
         CKS(consider(sc));
