@@ -9,7 +9,8 @@ from it.
 Every function is plain numpy / scipy in float64 and follows the paper:
 
 * ``grid``      - mapping (Section 2), radial clustering (Eq. stretching) and the
-                  five-step face metric (Section 3.2, Eqs. jacobi/skewness).
+                  five-step face metric (Section 3.2, Eqs. jacobi/skewness), also
+                  with exact derivatives at the face centres (the analytic option).
 * ``operator``  - the conservative discretisation of d_p(G_pq d_q phi)
                   (Section 3.3, Eqs. PC_8, PC_term1-3), assembled as a sparse matrix.
 * ``mg``        - geometric multigrid on that operator (the paper's own solver is
