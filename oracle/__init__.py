@@ -10,7 +10,9 @@ Every function is plain numpy / scipy in float64 and follows the paper:
 
 * ``grid``      - mapping (Section 2), radial clustering (Eq. stretching) and the
                   five-step face metric (Section 3.2, Eqs. jacobi/skewness), also
-                  with exact derivatives at the face centres (the analytic option).
+                  with exact derivatives at the face centres (the analytic option);
+                  sectors between colatitude walls, or the full sphere with the
+                  shell cut of Sections 3.5 and 3.7 (``full_sphere``).
 * ``operator``  - the conservative discretisation of d_p(G_pq d_q phi)
                   (Section 3.3, Eqs. PC_8, PC_term1-3), assembled as a sparse matrix.
 * ``mg``        - geometric multigrid on that operator (the paper's own solver is
@@ -25,18 +27,23 @@ Every function is plain numpy / scipy in float64 and follows the paper:
                   radial-line Gauss-Seidel smoother.
 * ``adi``       - the ADI-CN implicit viscous sweeps of Section 3.4 (Eqs.
                   solve_2 to solve_4) on a cell-centred field.
+* ``smg``       - semi-coarsening multigrid with zebra plane relaxation (the
+                  solver class of Section 3.6): coarsening along zeta only, the
+                  (eta, xi) planes solved exactly or by a 2-D cycle of eta
+                  semi-coarsening and periodic-Thomas xi-line relaxation.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
-multigrid convergence factor, which the paper does not give
-(parity unpinned: convergence factor only; the converged answer is pinned by
-the direct solve).
+multigrid convergence factors (``mg`` and ``smg``), which the paper does not
+give (parity unpinned: convergence factor only; the converged answer is pinned
+by the direct solve).
 """
 
-from .grid import Shell, shell, face_metrics, cell_volume, vertex, analytic_face_metrics
+from .grid import (Shell, shell, full_sphere, face_metrics, cell_volume, vertex,
+                   analytic_face_metrics)
 from .operator import assemble, apply_rows
-from . import mg, direct
+from . import mg, direct, smg
 
 __all__ = [
-    "Shell", "shell", "face_metrics", "cell_volume", "vertex", "analytic_face_metrics",
-    "assemble", "apply_rows", "mg", "direct",
+    "Shell", "shell", "full_sphere", "face_metrics", "cell_volume", "vertex",
+    "analytic_face_metrics", "assemble", "apply_rows", "mg", "direct", "smg",
 ]

@@ -14,6 +14,16 @@ Readings where the paper is silent:
   the axes permuted;
 * ghost vertices one plane outside the domain (needed by the normal
   derivative at wall faces) come from evaluating the analytic mapping there.
+
+Full sphere with the shell cut (Section 3.5 "Handling shell cut", Section
+3.7): with ``cut`` the colatitude runs over [0, pi] and a zeta grid line
+continues through either pole into the line at longitude k + nph/2.  The
+mapping evaluated at theta < 0 or theta > pi is already the point across the
+pole (sin changes sign where cos(phi + pi) = -cos(phi)), so the vertex
+stencil needs no special case.  Readings (the paper gives no pole metric):
+* the zeta faces at theta = 0 and theta = pi have all four corners on the
+  polar axis, hence zero area; the determinant of Section 3.2 vanishes there
+  and the face carries no flux: its G row, C and determinant are zero.
 """
 from __future__ import annotations
 
@@ -37,6 +47,7 @@ class Shell:
     flattening: float = 0.0    # x1 scaled by (1 - flattening)
     e2: float = 0.0            # x2 scaled by (1 + e2)
     stretch: float = 0.0       # rx_2 of Eq. stretching; 0 = uniform
+    cut: bool = False          # full sphere, zeta lines joined through the poles
 
     def __post_init__(self):
         # Section 3.2's normal derivative at a longitude face differences the
@@ -44,6 +55,8 @@ class Shell:
         # circle both are the same plane and the face determinant is zero.
         if self.nph < 4 or self.nph % 2:
             raise ValueError("nph must be even and >= 4")
+        if self.cut and (self.th0 != 0.0 or self.th1 != np.pi):
+            raise ValueError("the shell cut needs the full colatitude range [0, pi]")
 
     @property
     def shape(self):
@@ -55,6 +68,11 @@ class Shell:
 
     def as_dict(self):
         return asdict(self)
+
+
+def full_sphere(nr, nth, nph, **kw) -> Shell:
+    """A shell over the whole sphere, theta in [0, pi], with the shell cut."""
+    return Shell(nr, nth, nph, th0=0.0, th1=np.pi, cut=True, **kw)
 
 
 def shell(d) -> Shell:
@@ -189,6 +207,16 @@ def _face_index_grids(sh: Shell, d: int, jslice=None):
     return ii, jj, kk
 
 
+def _zero_pole_faces(sh: Shell, out: dict):
+    """Zero-area zeta faces at the poles of a cut shell: no flux, no area."""
+    if not sh.cut:
+        return
+    for key in ("G0", "det0", "C0"):
+        if key in out:
+            out[key][:, 0] = 0.0
+            out[key][:, sh.nth] = 0.0
+
+
 def face_metrics(sh, chunk_cells: int = 1 << 20, with_C: bool = False):
     """The five-step metric of Section 3.2 on every face of the grid.
 
@@ -207,7 +235,8 @@ def face_metrics(sh, chunk_cells: int = 1 << 20, with_C: bool = False):
         for j0 in range(0, nj, step):
             ii, jj, kk = _face_index_grids(sh, d, slice(j0, min(nj, j0 + step)))
             M = face_jacobian(sh, d, ii, jj, kk)
-            adet, G, C = metric_from_jacobian(M)
+            with np.errstate(divide="ignore", invalid="ignore"):   # pole faces, zeroed below
+                adet, G, C = metric_from_jacobian(M)
             Gs.append(G[..., d, :])
             dets.append(adet)
             if with_C:
@@ -216,6 +245,7 @@ def face_metrics(sh, chunk_cells: int = 1 << 20, with_C: bool = False):
         out[f"det{d}"] = np.concatenate(dets, axis=0)
         if with_C:
             out[f"C{d}"] = np.concatenate(Cs, axis=0)
+    _zero_pole_faces(sh, out)
     out["J"] = cell_volume(sh, out)
     return out
 
@@ -267,9 +297,11 @@ def analytic_face_metrics(sh):
             if a != d:
                 c[a] = c[a] + 0.5
         M = analytic_jacobian(sh, c[0], c[1], c[2])
-        adet, G, _ = metric_from_jacobian(M)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            adet, G, _ = metric_from_jacobian(M)
         out[f"G{d}"] = G[..., d, :]
         out[f"det{d}"] = adet
+    _zero_pole_faces(sh, out)
     return out
 
 
@@ -313,6 +345,9 @@ def cell_volume_at(sh, cells):
         if d == 2:
             hi[2] = np.mod(hi[2], sh.nph)
         for corner in (lo, hi):
-            adet, _, _ = metric_from_jacobian(face_jacobian(sh, d, *corner))
+            with np.errstate(divide="ignore", invalid="ignore"):
+                adet, _, _ = metric_from_jacobian(face_jacobian(sh, d, *corner))
+            if d == 0 and sh.cut:
+                adet = np.where((corner[0] == 0) | (corner[0] == sh.nth), 0.0, adet)
             total += adet
     return total / 6.0

@@ -13,7 +13,9 @@ own cell-centred design, written out plainly so every GPU step has a CPU twin:
   strongest are halved (semi-coarsening toward isotropy, the idea behind SMG);
 * restriction: sum over children (b is volume integrated);
 * prolongation: cell-centred trilinear (3/4, 1/4 per halved direction),
-  mirror at walls, wrap in longitude;
+  mirror at walls, wrap in longitude; on the full sphere with the shell cut
+  the colatitude partner beyond a pole is the coarse cell of the same row at
+  longitude k + nph/2 (interpolation across the polar axis);
 * smoothers: multicolour Gauss-Seidel (7-point: red/black by (i+j+k) mod 2;
   19-point: four colours ((i+j) mod 2) + 2((j+k) mod 2), swept 0..3), or
   weighted Jacobi (omega 6/7 for 7-point, 4/5 for 19-point), diagonal = diag(A),
@@ -54,6 +56,7 @@ class Level:
     colours: list = field(default_factory=list)
     colour_rows: list = field(default_factory=list)   # A restricted to each colour's rows
     lines: list = None     # per line colour: (cells [nr][m], rows of A, lower, diag, upper)
+    cut: bool = False      # full sphere: zeta lines joined through the poles
 
     @property
     def n(self):
@@ -100,9 +103,9 @@ def line_systems(lv):
     return lv.lines
 
 
-def make_level(shape, fm, stencil):
-    lv = Level(shape=tuple(shape), fm=fm, stencil=stencil)
-    lv.A = assemble(None, fm, stencil=stencil, shape=lv.shape)
+def make_level(shape, fm, stencil, cut=False):
+    lv = Level(shape=tuple(shape), fm=fm, stencil=stencil, cut=cut)
+    lv.A = assemble(None, fm, stencil=stencil, shape=lv.shape, cut=cut)
     lv.D = lv.A.diagonal().copy()
     col = colour_of(lv.shape, stencil)
     ncol = 2 if stencil == 7 else 4
@@ -152,15 +155,16 @@ def coarsen_faces(shape, fm, c):
     return (ncr, nct, ncp), {"G0": G0, "G1": G1, "G2": G2}
 
 
-def build_hierarchy(fine_shape, fm, stencil=19, policy=SEMI, max_levels=16, coarse_max=512):
-    levels = [make_level(fine_shape, fm, stencil)]
+def build_hierarchy(fine_shape, fm, stencil=19, policy=SEMI, max_levels=16, coarse_max=512,
+                    cut=False):
+    levels = [make_level(fine_shape, fm, stencil, cut)]
     while len(levels) < max_levels and levels[-1].n > coarse_max:
         c = plan_factors(levels[-1].shape, levels[-1].fm, policy)
         if c is None:
             break
         levels[-1].factors = c
         shp, cfm = coarsen_faces(levels[-1].shape, levels[-1].fm, c)
-        levels.append(make_level(shp, cfm, stencil))
+        levels.append(make_level(shp, cfm, stencil, cut))
     return levels
 
 
@@ -190,15 +194,45 @@ def _prolong_1d(nc, c, periodic):
     return sp.coo_matrix((vals, (rows, cols)), shape=(2 * nc, nc)).tocsr()
 
 
-def transfer_matrices(fine_shape, c):
+def _prolong_sphere_plane(nct, ncp, cz, cx):
+    """Prolongation on one (theta, phi) plane of a cut shell, [i][k] order: as
+    the Kronecker product of the 1-D rules, except that a colatitude partner
+    beyond a pole is the coarse cell of the same row at longitude + ncp/2."""
+    nth, nph = nct * cz, ncp * cx
+    rows, cols, vals = [], [], []
+    for i in range(nth):
+        if cz == 1:
+            th = [(i, 1.0, 0)]
+        else:
+            C, s = divmod(i, 2)
+            nb = C - 1 if s == 0 else C + 1
+            th = [(C, 0.75, 0), (nb, 0.25, 0) if 0 <= nb < nct else (C, 0.25, ncp // 2)]
+        for k in range(nph):
+            if cx == 1:
+                ph = [(k, 1.0)]
+            else:
+                C, s = divmod(k, 2)
+                ph = [(C, 0.75), (((C - 1) if s == 0 else (C + 1)) % ncp, 0.25)]
+            for ic, wt, turn in th:
+                for kc, wp in ph:
+                    rows.append(i * nph + k)
+                    cols.append(ic * ncp + (kc + turn) % ncp)
+                    vals.append(wt * wp)
+    return sp.coo_matrix((vals, (rows, cols)), shape=(nth * nph, nct * ncp)).tocsr()
+
+
+def transfer_matrices(fine_shape, c, cut=False):
     """(R, P): children sum and trilinear prolongation between a level and the
     next one, as Kronecker products over the [j][i][k] axes."""
     nr, nth, nph = fine_shape
     cz, ce, cx = c
     R = sp.kron(_restrict_1d(nr // ce, ce),
                 sp.kron(_restrict_1d(nth // cz, cz), _restrict_1d(nph // cx, cx))).tocsr()
-    P = sp.kron(_prolong_1d(nr // ce, ce, False),
-                sp.kron(_prolong_1d(nth // cz, cz, False), _prolong_1d(nph // cx, cx, True))).tocsr()
+    if cut:
+        plane = _prolong_sphere_plane(nth // cz, nph // cx, cz, cx)
+    else:
+        plane = sp.kron(_prolong_1d(nth // cz, cz, False), _prolong_1d(nph // cx, cx, True))
+    P = sp.kron(_prolong_1d(nr // ce, ce, False), plane).tocsr()
     return R, P
 
 
@@ -240,7 +274,7 @@ def coarse_solve(lv, r):
 class Hierarchy:
     def __init__(self, levels):
         self.levels = levels
-        self.transfers = [transfer_matrices(lv.shape, lv.factors) if lv.factors else None
+        self.transfers = [transfer_matrices(lv.shape, lv.factors, lv.cut) if lv.factors else None
                           for lv in levels]
 
     def vcycle(self, l, x, b, nu1=2, nu2=2, kind=GS):
@@ -281,7 +315,7 @@ def setup(sh, stencil=None, policy=SEMI, max_levels=16, coarse_max=512, fm=None)
         stencil = default_stencil(sh)
     if fm is None:
         fm = face_metrics(sh)
-    levels = build_hierarchy(sh.shape, fm, stencil, policy, max_levels, coarse_max)
+    levels = build_hierarchy(sh.shape, fm, stencil, policy, max_levels, coarse_max, sh.cut)
     return Hierarchy(levels), fm
 
 

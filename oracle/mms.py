@@ -11,7 +11,11 @@ paper's discrete metric:
 * ``bump``    - p = sin^2(pi rho_hat) sin^2(pi theta_hat) sin(2 phi): its whole
   gradient vanishes on the walls, so the wall flux is zero for any metric;
 * ``conductive`` - p = a / r + b (Eq. conductive profile), exactly harmonic on
-  the sphere; used in interior cells only (its wall flux is not zero).
+  the sphere; used in interior cells only (its wall flux is not zero);
+* ``polar``   - p = sin^2(pi rho_hat) (cos theta + sin theta cos phi
+  + sin^2 theta sin 2 phi): degree-one and degree-two surface harmonics, smooth
+  through both poles (for the full sphere with the shell cut), whole gradient
+  zero on the radial walls.
 
 rho_hat = (rho - r_in)/(r_out - r_in), theta_hat = (theta - th0)/(th1 - th0).
 """
@@ -44,6 +48,9 @@ def _lambdas(kind, fl, e2, r_in, r_out, th0, th1):
         p = sy.sin(sy.pi * rh) ** 2 * sy.sin(sy.pi * thh) ** 2 * sy.sin(2 * ph)
     elif kind == "conductive":
         p = 1 / rho + sy.Rational(1, 3)
+    elif kind == "polar":
+        p = sy.sin(sy.pi * rh) ** 2 * (sy.cos(th) + sy.sin(th) * sy.cos(ph)
+                                       + sy.sin(th) ** 2 * sy.sin(2 * ph))
     else:
         raise ValueError(kind)
     grad = [sy.diff(p, v) for v in u]

@@ -17,6 +17,13 @@ correction are not stated):
   mirror ghost x_ghost = x_adjacent (zero normal derivative);
 * the 7-point stencil (orthogonal mappings) keeps only the G_pp terms.
 These choices make A 1 = 0 and 1^T A = 0 exactly.
+
+Full sphere with the shell cut (Sections 3.5 and 3.7): a zeta line leaving
+the grid through a pole re-enters at the same colatitude row, longitude
+k + nph/2, so the cell one beyond row 0 (or row nth - 1) is that row's cell
+across the pole.  The pole faces have zero area (no flux, see ``grid``); the
+cut therefore enters only through the tangential differences of the cross
+terms, where it replaces the mirror ghost.
 """
 from __future__ import annotations
 
@@ -33,13 +40,18 @@ def _flat(sh_shape, i, j, k):
     return (j * nth + i) * nph + k
 
 
-def _shift(idx, q, s, n):
-    """Neighbour index along direction q (paper order, 0-based): wrap in xi,
-    mirror-clamp at the radial and colatitude walls."""
+def _shift(idx, q, s, n, cut=False):
+    """Neighbour index along direction q (paper order, 0-based; |s| = 1):
+    wrap in xi, mirror-clamp at the radial and colatitude walls, or across a
+    pole of the shell cut (same zeta row, longitude + nph/2)."""
     out = list(idx)
     v = idx[q] + s
     if PERIODIC[q]:
         v = np.mod(v, n[q])
+    elif q == 0 and cut:
+        across = (v < 0) | (v > n[0] - 1)
+        out[2] = np.where(across, np.mod(idx[2] + n[2] // 2, n[2]), idx[2])
+        v = np.clip(v, 0, n[q] - 1)
     else:
         v = np.clip(v, 0, n[q] - 1)
     out[q] = v
@@ -57,7 +69,7 @@ def _face_row(fm, d, L, n):
     return G[j, i, np.mod(k + 1, n[2])]
 
 
-def _face_terms(d, L, U, g, n, stencil):
+def _face_terms(d, L, U, g, n, stencil, cut=False):
     """(column cells, weights) whose weighted sum is the flux through the face."""
     terms = [(U, g[..., d]), (L, -g[..., d])]
     if stencil == 19:
@@ -65,16 +77,18 @@ def _face_terms(d, L, U, g, n, stencil):
             if q == d:
                 continue
             w = 0.25 * g[..., q]
-            terms += [(_shift(L, q, +1, n), w), (_shift(U, q, +1, n), w),
-                      (_shift(L, q, -1, n), -w), (_shift(U, q, -1, n), -w)]
+            terms += [(_shift(L, q, +1, n, cut), w), (_shift(U, q, +1, n, cut), w),
+                      (_shift(L, q, -1, n, cut), -w), (_shift(U, q, -1, n, cut), -w)]
     return terms
 
 
-def assemble(sh, fm, stencil: int = 19, shape=None):
+def assemble(sh, fm, stencil: int = 19, shape=None, cut=None):
     """Sparse A (CSR, N x N, cells ordered [j][i][k]) from the face G rows ``fm``.
 
-    ``shape`` = (nr, nth, nph) defaults to the shell's; coarse multigrid levels
-    pass their own shape with aggregated face rows."""
+    ``shape`` = (nr, nth, nph) and ``cut`` default to the shell's; coarse
+    multigrid levels pass their own shape with aggregated face rows."""
+    if cut is None:
+        cut = shell(sh).cut if sh is not None else False
     if shape is None:
         shape = shell(sh).shape
     nr, nth, nph = shape
@@ -92,7 +106,7 @@ def assemble(sh, fm, stencil: int = 19, shape=None):
         g = _face_row(fm, d, L, n)
         fL = _flat(shape, *L)
         fU = _flat(shape, *U)
-        for cell, w in _face_terms(d, L, U, g, n, stencil):
+        for cell, w in _face_terms(d, L, U, g, n, stencil, cut):
             fc = _flat(shape, *cell)
             rows += [fL, fU]
             cols += [fc, fc]
@@ -132,10 +146,11 @@ def apply_rows(sh, x, cells, stencil: int = 19):
             # face corner vertex: plane U_d along d, L's indices elsewhere
             corner = list(Ls)
             corner[d] = Us[d] if not PERIODIC[d] else np.mod(Ls[d] + 1, n[d])
-            _, G, _ = metric_from_jacobian(face_jacobian(sh, d, *corner))
+            with np.errstate(divide="ignore", invalid="ignore"):   # pole faces: masked
+                _, G, _ = metric_from_jacobian(face_jacobian(sh, d, *corner))
             g = G[..., d, :]
             F = np.zeros(i.shape)
-            for cell, w in _face_terms(d, Ls, Us, g, n, stencil):
+            for cell, w in _face_terms(d, Ls, Us, g, n, stencil, sh.cut):
                 F = F + w * xr[cell[1], cell[0], cell[2]]
             out += np.where(inside, side * F, 0.0)
     return out

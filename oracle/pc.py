@@ -19,7 +19,8 @@ Readings where the paper is silent:
 * The correction uses at each face the gradient of the operator's flux
   (Eqs. PC_term1-3): the normal difference, and for the 19-point operator the
   averaged tangential differences (mirror ghosts at walls, wrap in
-  longitude); the 7-point operator keeps the normal difference only.  Then
+  longitude, across the pole on the full sphere with the shell cut); the
+  7-point operator keeps the normal difference only.  Then
   U_d(new) = U_d - F_d(h dP) face by face, with F_d the operator's face
   flux, so D(U_new) = D(U***) - A (h dP): the corrected field's divergence is
   the solver's residual.
@@ -99,6 +100,9 @@ def face_gradient(sh, x, d, stencil):
             v[q] = np.mod(c[q] + s, n[q])
         else:
             v[q] = np.clip(c[q] + s, 0, n[q] - 1)
+            if q == 0 and sh.cut:               # across a pole: same row, longitude + nph/2
+                across = (c[0] + s < 0) | (c[0] + s > n[0] - 1)
+                v[2] = np.where(across, np.mod(c[2] + n[2] // 2, n[2]), c[2])
         return tuple(v)
 
     g = np.zeros(face_shapes(sh)[d] + (3,))
@@ -117,6 +121,7 @@ def project(sh, fm, x, u, stencil):
     out = []
     for d in range(3):
         g = face_gradient(sh, x, d, stencil)
-        corr = np.einsum("...ja,...j->...a", fm[f"C{d}"], g) / fm[f"det{d}"][..., None]
+        with np.errstate(divide="ignore", invalid="ignore"):     # zero-area pole faces: masked
+            corr = np.einsum("...ja,...j->...a", fm[f"C{d}"], g) / fm[f"det{d}"][..., None]
         out.append(np.where(_interior(sh, d)[..., None], u[d] - corr, u[d]))
     return out

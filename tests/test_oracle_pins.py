@@ -350,12 +350,12 @@ def test_planted_operator_mistakes_are_caught(monkeypatch):
     good = _interior_truncation(sh, "bump", 19)
     orig = operator._face_terms
 
-    def flipped_cross(d, L, U, g, n, stencil):   # wrong sign on the cross terms
-        t = orig(d, L, U, g, n, stencil)
+    def flipped_cross(d, L, U, g, n, stencil, cut=False):   # wrong sign on the cross terms
+        t = orig(d, L, U, g, n, stencil, cut)
         return t[:2] + [(c, -w) for c, w in t[2:]]
 
-    def swapped_component(d, L, U, g, n, stencil):  # G_pq taken from the wrong column
-        return orig(d, L, U, g[..., ::-1], n, stencil)
+    def swapped_component(d, L, U, g, n, stencil, cut=False):  # G_pq from the wrong column
+        return orig(d, L, U, g[..., ::-1], n, stencil, cut)
 
     for bad in (flipped_cross, swapped_component):
         monkeypatch.setattr(operator, "_face_terms", bad)
