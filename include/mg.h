@@ -64,7 +64,7 @@ enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
  * tanh clustering of Eq. stretching with factor `stretch` (0 = uniform),
  * colatitude th0 + (th1 - th0) i / nth and longitude 2 pi k / nph, mapped to
  * x1 = (1 - flattening) r cos th, x2 = (1 + e2) r sin th cos ph,
- * x3 = r sin th sin ph.  Requirements: nr, nth >= 1; nph >= 2 and even;
+ * x3 = r sin th sin ph.  Requirements: nr, nth >= 1; nph >= 4 and even;
  * 0 < th0 < th1 < pi; 0 < r_in < r_out. */
 typedef struct {
     int nr, nth, nph;
