@@ -64,8 +64,13 @@ enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
  * tanh clustering of Eq. stretching with factor `stretch` (0 = uniform),
  * colatitude th0 + (th1 - th0) i / nth and longitude 2 pi k / nph, mapped to
  * x1 = (1 - flattening) r cos th, x2 = (1 + e2) r sin th cos ph,
- * x3 = r sin th sin ph.  Requirements: nr, nth >= 1; nph >= 2 and even;
- * 0 < th0 < th1 < pi; 0 < r_in < r_out. */
+ * x3 = r sin th sin ph.  Requirements: nr, nth >= 1; nph >= 4 and even;
+ * 0 < r_in < r_out; 0 < th0 < th1 < pi between zero-flux colatitude walls,
+ * or, with cut = 1, the full sphere th0 = 0, th1 = pi (the shell cut of
+ * Sections 3.5 and 3.7: a colatitude line continues through either pole into
+ * the line at longitude k + nph/2; the zeta faces on the polar axis have zero
+ * area and carry no flux).  The shell cut is built for the 7-point operator
+ * (the sphere mapping); other stencils return MG_EINVAL with it. */
 typedef struct {
     int nr, nth, nph;
     double r_in, r_out;
@@ -73,6 +78,7 @@ typedef struct {
     int mapping;              /* MG_MAP_* */
     double flattening, e2;
     double stretch;
+    int cut;                  /* 0: colatitude walls; 1: full sphere with the shell cut */
 } mg_grid_desc;
 
 /* Solver options; mg_default_opts fills the defaults noted here. */

@@ -36,7 +36,7 @@ class mg_grid_desc(C.Structure):
                 ("r_in", C.c_double), ("r_out", C.c_double),
                 ("th0", C.c_double), ("th1", C.c_double),
                 ("mapping", C.c_int), ("flattening", C.c_double), ("e2", C.c_double),
-                ("stretch", C.c_double)]
+                ("stretch", C.c_double), ("cut", C.c_int)]
 
 
 class mg_opts(C.Structure):

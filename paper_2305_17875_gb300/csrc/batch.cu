@@ -606,7 +606,13 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
             restrict_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
                                 (T*)tk.y, (T*)tk.z, first, stride);
     } else if constexpr (OP == BOP_PROLONG) {
-        if (vec4(tk.v.D))
+        if (tk.v.D.cut)
+            for (i64 c = first; c < tk.v.D.n(); c += stride) {
+                T* x = (T*)tk.x;
+                x[c] = x[c] + prolong_cut_cell<T>(tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b,
+                                                  decode(tk.v.D, c), [](const T* p) { return *p; });
+            }
+        else if (vec4(tk.v.D))
             prolong_pass_v<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
         else
             prolong_pass<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);

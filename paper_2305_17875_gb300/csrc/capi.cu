@@ -98,8 +98,12 @@ std::string check_grid(const mg_grid_desc* g) {
     if ((long long)g->nr * g->nth * g->nph > (1LL << 31)) return "grid too large";
     if (!(finite(g->r_in) && finite(g->r_out) && g->r_in > 0 && g->r_out > g->r_in))
         return "need 0 < r_in < r_out";
-    if (!(finite(g->th0) && finite(g->th1) && g->th0 > 0 && g->th1 > g->th0 && g->th1 < M_PI))
+    if (g->cut != 0 && g->cut != 1) return "cut must be 0 or 1";
+    if (g->cut) {
+        if (!(g->th0 == 0.0 && g->th1 == M_PI)) return "the shell cut needs th0 = 0 and th1 = pi";
+    } else if (!(finite(g->th0) && finite(g->th1) && g->th0 > 0 && g->th1 > g->th0 && g->th1 < M_PI)) {
         return "need 0 < th0 < th1 < pi";
+    }
     if (g->mapping < 0 || g->mapping > 2) return "mapping must be 0, 1 or 2";
     if (!(finite(g->flattening) && g->flattening > -1 && g->flattening < 1)) return "need |flattening| < 1";
     if (!(finite(g->e2) && g->e2 > -1)) return "need e2 > -1";
@@ -125,6 +129,12 @@ std::string check_opts(const mg_opts* o) {
 int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
     if (o->stencil) return o->stencil;
     return g->mapping == MG_MAP_SPHERE ? 7 : 19;
+}
+
+// Combinations of a valid grid and valid options that are not built.
+std::string check_pair(const mg_grid_desc* g, const mg_opts* o) {
+    if (g->cut && stencil_of(g, o) != 7) return "the shell cut is built for the 7-point operator only";
+    return "";
 }
 
 void* dalloc(mg_handle* h, size_t bytes) {
@@ -515,6 +525,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
 
     Level L0;
     L0.D = Dims{nr, nth, nph};
+    L0.D.cut = g->cut;
     const i64 N = L0.D.n();
     for (int a = 0; a < 9; ++a)
         if (stored(h, a) && !(L0.g64[a] = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
@@ -584,6 +595,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         fine.cx = f[2];
         Level c;
         c.D = Dims{fine.D.nr / fine.ce, fine.D.nth / fine.cz, fine.D.nph / fine.cx};
+        c.D.cut = fine.D.cut;
         for (int a = 0; a < 9; ++a)
             if (stored(h, a) && !(c.g64[a] = (double*)dalloc(h, sizeof(double) * c.D.n())))
                 return MG_ENOMEM;
@@ -964,7 +976,7 @@ size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
         mg_default_opts(&d);
         o = &d;
     }
-    if (!check_grid(g).empty() || !check_opts(o).empty()) return 0;
+    if (!check_grid(g).empty() || !check_opts(o).empty() || !check_pair(g, o).empty()) return 0;
     const double n = (double)g->nr * g->nth * g->nph;
     const int nc = stencil_of(g, o) == 19 ? 9 : 3;
     const double cb = (double)coef_bytes(o->precision);
@@ -989,6 +1001,7 @@ mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_han
     }
     std::string why = check_grid(g);
     if (why.empty()) why = check_opts(o);
+    if (why.empty()) why = check_pair(g, o);
     if (!why.empty()) {
         set_error(why);
         return MG_EINVAL;

@@ -135,10 +135,11 @@ __global__ void k_wall_G(MetricTables t, Dims D, double* r_lo, double* r_hi, dou
             const i64 p = q - nr_w;
             const int j = (int)(p / D.nph), k = (int)(p % D.nph);
             const int vl[3] = {0, j, k}, vh[3] = {D.nth, j, k};
+            // on the full sphere these faces lie on the polar axis: zero area, no flux
             face_metric(t, 0, vl, row);
-            th_lo[p] = row[0];
+            th_lo[p] = D.cut ? 0.0 : row[0];
             face_metric(t, 0, vh, row);
-            th_hi[p] = row[0];
+            th_hi[p] = D.cut ? 0.0 : row[0];
         }
     }
 }

@@ -131,6 +131,12 @@ __device__ __forceinline__ void lin1d(int f, int c, int nc, bool periodic, int i
 template <typename T, bool CG>
 __device__ __forceinline__ void prolong_range(const Dims& D, const Dims& Dc, int cz, int ce, int cx, const T* ec,
                                               T* x, i64 first, i64 stride) {
+    if (D.cut) {   // full sphere: colatitude partners across the poles
+        for (i64 c = first; c < D.n(); c += stride)
+            x[c] = ldv<T, CG>(x + c) +
+                   prolong_cut_cell<T>(Dc, cz, ce, cx, ec, decode(D, c), [](const T* p) { return ldv<T, CG>(p); });
+        return;
+    }
     for (i64 c = first; c < D.n(); c += stride) {
         const C3 f = decode(D, c);
         int ij[2], ii[2], ik[2];
