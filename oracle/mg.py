@@ -25,6 +25,16 @@ own cell-centred design, written out plainly so every GPU step has a CPU twin:
   coloured so that no two lines of a colour are coupled (7-point: zebra by
   (i+k) mod 2; 19-point: four colours (i mod 2) + 2 (k mod 2)), swept in
   colour order;
+  or longitude-line Gauss-Seidel: every longitude line (fixed radius and
+  colatitude index, periodic) is one block, solved with the periodic Thomas
+  algorithm of Section 3.5 (``tridiag.thomas_periodic``) on the cyclic
+  tridiagonal part of A on the line (couplings inside the line beyond it,
+  the shell cut's, taken from the current iterate); colours 7-point
+  (i+j) mod 2, 19-point (i mod 2) + 2 (j mod 2); a level with fewer than
+  four longitudes is swept by point Gauss-Seidel instead;
+  or alternating lines: one radial-line sweep, then one longitude-line sweep,
+  per smoothing step (radial clustering and thin shells make the radial
+  couplings strong, the poles the longitude ones);
 * coarsest level: dense bordered solve [A 1; 1^T 0][e; lam] = [r; 0];
 * V(nu1, nu2) cycle, iterated from x0 until ||b - A x||_2 / ||b||_2 <= tol;
 * gauge: the J-weighted mean of x is removed at the end (discrete volume
@@ -38,10 +48,10 @@ import scipy.sparse as sp
 
 from .grid import shell, face_metrics
 from .operator import assemble
-from .tridiag import thomas
+from .tridiag import thomas, thomas_periodic
 
 SEMI, FULL = 0, 1
-GS, JACOBI, LINE = 0, 1, 2
+GS, JACOBI, LINE, XLINE, ALT = 0, 1, 2, 3, 4
 SEMI_RATIO = 0.7
 
 
@@ -56,6 +66,7 @@ class Level:
     colours: list = field(default_factory=list)
     colour_rows: list = field(default_factory=list)   # A restricted to each colour's rows
     lines: list = None     # per line colour: (cells [nr][m], rows of A, lower, diag, upper)
+    xlines: list = None    # per longitude-line colour: (cells [nph][m], rows of A, a, b, c)
     cut: bool = False      # full sphere: zeta lines joined through the poles
 
     @property
@@ -101,6 +112,40 @@ def line_systems(lv):
                 upper[:-1] = np.asarray(A[cells[:-1].ravel(), cells[1:].ravel()]).reshape(nr - 1, -1)
             lv.lines.append((cells, A[cells.ravel()], lower, diag, upper))
     return lv.lines
+
+
+def xline_colour_of(shape, stencil):
+    """Colour of the longitude line through every cell, [j][i][k] order."""
+    nr, nth, nph = shape
+    j, i, k = np.meshgrid(np.arange(nr), np.arange(nth), np.arange(nph), indexing="ij")
+    if stencil == 7:
+        return ((i + j) & 1).ravel()
+    return ((i & 1) + 2 * (j & 1)).ravel()
+
+
+def xline_systems(lv):
+    """For each longitude-line colour: the cells of its lines as an [nph][m]
+    array (m lines, k on axis 0), the rows of A for those cells, and the
+    cyclic tridiagonal part of A on each line: a[k] = A(c_k, c_{k-1}),
+    b[k] = A(c_k, c_k), c[k] = A(c_k, c_{k+1}), indices wrapping."""
+    if lv.xlines is None:
+        nph = lv.shape[2]
+        col = xline_colour_of(lv.shape, lv.stencil)
+        A = lv.A.tocsr()
+        lv.xlines = []
+        for c in range(2 if lv.stencil == 7 else 4):
+            sel = np.nonzero(col == c)[0]
+            if sel.size == 0:
+                continue
+            cells = sel.reshape(-1, nph).T                       # [nph][m]
+            flat = cells.ravel()
+            km = np.roll(cells, 1, axis=0).ravel()
+            kp = np.roll(cells, -1, axis=0).ravel()
+            a = np.asarray(A[flat, km]).reshape(cells.shape)
+            b = np.asarray(A[flat, flat]).reshape(cells.shape)
+            cc = np.asarray(A[flat, kp]).reshape(cells.shape)
+            lv.xlines.append((cells, A[flat], a, b, cc))
+    return lv.xlines
 
 
 def make_level(shape, fm, stencil, cut=False):
@@ -248,11 +293,19 @@ def smooth(lv, x, b, sweeps, kind=GS):
         for _ in range(sweeps):
             for idx, rows in zip(lv.colours, lv.colour_rows):
                 x[idx] += (b[idx] - rows @ x) / lv.D[idx]
-    elif kind == LINE:
+    elif kind in (LINE, XLINE, ALT):
         for _ in range(sweeps):
-            for cells, rows, lower, diag, upper in line_systems(lv):
-                r = (b[cells.ravel()] - rows @ x).reshape(cells.shape)
-                x[cells.ravel()] += thomas(lower, diag, upper, r).ravel()
+            if kind in (LINE, ALT):
+                for cells, rows, lower, diag, upper in line_systems(lv):
+                    r = (b[cells.ravel()] - rows @ x).reshape(cells.shape)
+                    x[cells.ravel()] += thomas(lower, diag, upper, r).ravel()
+            if kind in (XLINE, ALT):
+                if lv.shape[2] < 4:
+                    x = smooth(lv, x, b, 1, GS)
+                    continue
+                for cells, rows, a, bb, c in xline_systems(lv):
+                    r = (b[cells.ravel()] - rows @ x).reshape(cells.shape)
+                    x[cells.ravel()] += thomas_periodic(a, bb, c, r).ravel()
     else:
         w = 6.0 / 7.0 if lv.stencil == 7 else 4.0 / 5.0
         for _ in range(sweeps):

@@ -180,6 +180,80 @@ def test_line_smoother_handles_a_thin_shell():
     assert rho[mg.GS] > 0.9 and rho[mg.LINE] < 0.15, rho
 
 
+# ---------------------------------------------------------------- longitude-line smoother
+@pytest.mark.parametrize("name", list(LINE_GRIDS))
+def test_longitude_line_blocks_are_cyclic_tridiagonal_and_colours_uncoupled(name):
+    sh, fm, lv = _level(name)
+    Ad = lv.A.toarray()
+    col = mg.xline_colour_of(lv.shape, lv.stencil)
+    line = np.arange(lv.n) // sh.nph                  # (j, i) of every cell
+    n = sh.nph
+    for cells, _, a, b, c in mg.xline_systems(lv):
+        for l in range(cells.shape[1]):
+            L = cells[:, l]
+            B = Ad[np.ix_(L, L)]
+            band = np.eye(n, dtype=bool) | np.eye(n, k=1, dtype=bool) | np.eye(n, k=-1, dtype=bool)
+            band[0, n - 1] = band[n - 1, 0] = True
+            assert not B[~band].any()
+            np.testing.assert_array_equal(np.diag(B), b[:, l])
+            np.testing.assert_array_equal([B[k, (k - 1) % n] for k in range(n)], a[:, l])
+            np.testing.assert_array_equal([B[k, (k + 1) % n] for k in range(n)], c[:, l])
+    r, cc = lv.A.nonzero()
+    assert not ((col[r] == col[cc]) & (line[r] != line[cc])).any()
+
+
+@pytest.mark.parametrize("name", list(LINE_GRIDS))
+def test_longitude_line_sweep_is_block_gauss_seidel(name):
+    sh, fm, lv = _level(name)
+    rng = np.random.default_rng(16)
+    b, _ = mg.prepare_rhs(fm["J"], rng.standard_normal(sh.n))
+    x0 = rng.standard_normal(sh.n)
+    Ad = lv.A.toarray()
+    y = x0.copy()
+    for cells, *_ in mg.xline_systems(lv):
+        for l in range(cells.shape[1]):
+            L = cells[:, l]
+            y[L] += np.linalg.solve(Ad[np.ix_(L, L)], b[L] - Ad[L] @ y)
+        rr = b[cells.ravel()] - Ad[cells.ravel()] @ y
+        assert np.abs(rr).max() <= 1e-12 * np.abs(b).max()
+    x = mg.smooth(lv, x0, b, 1, mg.XLINE)
+    np.testing.assert_allclose(x, y, rtol=0, atol=1e-13 * np.abs(y).max())
+    # alternating: the radial sweep, then the longitude sweep
+    z = mg.smooth(lv, mg.smooth(lv, x0, b, 1, mg.LINE), b, 1, mg.XLINE)
+    np.testing.assert_allclose(mg.smooth(lv, x0, b, 1, mg.ALT), z, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("kind", ["XLINE", "ALT"])
+def test_longitude_line_smoothed_multigrid_matches_direct_solve(kind):
+    kw, st = LINE_GRIDS["triaxial_19"]
+    for sh in (grid.Shell(8, 8, 16, **kw), grid.full_sphere(8, 8, 16, **kw)):
+        fm = grid.face_metrics(sh)
+        f = np.random.default_rng(17).standard_normal(sh.n)
+        x, info = mg.solve(sh, f, tol=1e-12, kind=getattr(mg, kind), fm=fm)
+        assert info["converged"]
+        lv = mg.make_level(sh.shape, fm, st, sh.cut)
+        b, _ = mg.prepare_rhs(fm["J"], f)
+        xd, _ = direct.bordered_solve(lv.A, b, fm["J"].ravel())
+        np.testing.assert_allclose(x, xd, rtol=0, atol=1e-10 * np.abs(xd).max())
+
+
+def test_alternating_lines_handle_the_poles_and_a_thin_shell():
+    """The full sphere (longitude coupling grows like 1/sin^2(theta) toward
+    the poles) defeats point and radial-line smoothing; alternating radial and
+    longitude lines keep their rate there and on the thin stretched shell."""
+    f_iters = {}
+    for name, sh in (("sphere", grid.full_sphere(16, 16, 32)),
+                     ("thin", grid.Shell(16, 16, 32, r_out=1.05, stretch=2.0))):
+        f = np.random.default_rng(3).standard_normal(sh.n)
+        hier, fm = mg.setup(sh, 7)
+        for kind in (mg.GS, mg.LINE, mg.ALT):
+            _, info = mg.solve(sh, f, tol=1e-10, hier=hier, fm=fm, kind=kind, max_iters=60)
+            f_iters[name, kind] = info["iters"]
+    assert f_iters["sphere", mg.ALT] <= 10 and f_iters["thin", mg.ALT] <= 6, f_iters
+    assert f_iters["sphere", mg.GS] >= 3 * f_iters["sphere", mg.ALT], f_iters
+    assert f_iters["sphere", mg.LINE] >= 3 * f_iters["sphere", mg.ALT], f_iters
+
+
 # ---------------------------------------------------------------- ADI-CN sweeps (Section 3.4)
 from oracle import adi, operator  # noqa: E402
 
