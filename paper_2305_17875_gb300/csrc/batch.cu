@@ -12,6 +12,7 @@
 
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
+#include "xline_smooth.cuh"
 
 namespace mgs {
 
@@ -593,6 +594,8 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
     } else if constexpr (OP == BOP_LINE) {
         line_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
+    } else if constexpr (OP == BOP_XLINE) {
+        xline_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour, first, stride);
     } else if constexpr (OP == BOP_JACOBI) {
         jacobi_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (T*)tk.y, (const T*)tk.b, first, stride);
     } else if constexpr (OP == BOP_RESTRICT) {
@@ -992,6 +995,7 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
         STENCIL_OP(BOP_GS)
         STENCIL_OP(BOP_JACOBI)
         STENCIL_OP(BOP_LINE)
+        STENCIL_OP(BOP_XLINE)
         STENCIL_OP(BOP_RESTRICT)
         STENCIL_OP(BOP_RESID)
         PLAIN_OP(BOP_PROLONG)

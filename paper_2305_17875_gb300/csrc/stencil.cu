@@ -6,6 +6,7 @@
 
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
+#include "xline_smooth.cuh"
 
 namespace mgs {
 
@@ -195,6 +196,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_line(CF cf, Dims D, T* x, const
     line_pass<S, T>(cf, D, x, b, fac, colour, blockIdx.x, gridDim.x);
 }
 
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_xline(CF cf, Dims D, T* x, const T* __restrict__ b,
+                                                     const T* __restrict__ fac, T* work, int colour) {
+    xline_pass<S, T>(cf, D, x, b, fac, work, colour, blockIdx.x * (i64)blockDim.x + threadIdx.x,
+                     (i64)gridDim.x * blockDim.x);
+}
+
 // Weighted Jacobi, out of place: xo = x + omega (b - A x) / diag(A).
 template <int S, typename T, typename CF>
 __global__ void __launch_bounds__(kThreads) k_jacobi(CF cf, Dims D, const T* __restrict__ x, T* __restrict__ xo,
@@ -334,6 +342,14 @@ cudaError_t launch_line_colour(const LevelView& lv, int prec, void* x, const voi
     const int nb = blocks_for(lines * line_chunks(lv.D.nr, kc));
     MG_DISPATCH(lv, prec, (k_line<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, (const T*)fac,
                                                                 colour)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xline_colour(const LevelView& lv, int prec, void* x, const void* b, const void* fac,
+                                void* work, int colour, cudaStream_t s) {
+    const int nb = blocks_for(xline_items(lv.D, lv.stencil));
+    MG_DISPATCH(lv, prec, (k_xline<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, (const T*)fac,
+                                                                 (T*)work, colour)));
     return cudaGetLastError();
 }
 
