@@ -107,6 +107,10 @@ SINGLE = {
     # dominates by ~10^3; the case the radial-line smoother is for
     "single_thin_128": dict(grid=grid_desc(128, r_out=1.05, stretch=2.0), rhs=("modes", 0), tol=1e-10,
                             precision="fp32"),
+    # the whole sphere with the shell cut (theta in [0, pi]): the paper's own
+    # domain; longitude coupling grows like 1/sin^2(theta) toward the poles
+    "single_full_sphere_128": dict(grid=grid_desc(128, stretch=2.0, cut=True), rhs=("modes", 0), tol=1e-10,
+                                   precision="fp32"),
 }
 
 
