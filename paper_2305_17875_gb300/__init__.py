@@ -159,6 +159,9 @@ def _stream(stream):
 
 
 def _ptr(t, dtype=None):
+    """Device buffer: a C-contiguous CUDA tensor of ``dtype`` (or a raw device
+    address as an int).  Host memory is refused here: the kernels would read
+    it as device memory."""
     if t is None:
         return None
     if hasattr(t, "data_ptr"):
@@ -166,10 +169,32 @@ def _ptr(t, dtype=None):
             raise ValueError("tensor must be C-contiguous")
         if dtype is not None and str(t.dtype) != f"torch.{dtype}":
             raise TypeError(f"expected {dtype}, got {t.dtype}")
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor (device buffer), got a host tensor")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        raise ValueError("expected a CUDA tensor (device buffer), got a numpy array")
+    return int(t)
+
+
+def _hptr(t):
+    """Host buffer of float64: a C-contiguous numpy array or CPU tensor (or a
+    raw host address as an int)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be C-contiguous")
+        if str(t.dtype) != "torch.float64":
+            raise TypeError(f"expected float64, got {t.dtype}")
+        if t.is_cuda:
+            raise ValueError("expected a host buffer, got a CUDA tensor")
         return t.data_ptr()
     if isinstance(t, np.ndarray):
         if not t.flags["C_CONTIGUOUS"]:
             raise ValueError("array must be C-contiguous")
+        if t.dtype != np.float64:
+            raise TypeError(f"expected float64, got {t.dtype}")
         return t.ctypes.data
     return int(t)
 
@@ -258,7 +283,7 @@ def mg_solve(h: Handle, f, x, tol=1e-10, allow=(MG_OK,)):
 def mg_solve_host(h: Handle, f, x, tol=1e-10, allow=(MG_OK,)):
     """Solve from host arrays (numpy or pinned torch CPU tensors); x in place."""
     rep = mg_report()
-    st = _lib.mg_solve_host(h.ptr, _ptr(f), _ptr(x), float(tol), C.byref(rep))
+    st = _lib.mg_solve_host(h.ptr, _hptr(f), _hptr(x), float(tol), C.byref(rep))
     _check(st, "mg_solve_host", allow)
     return rep.as_dict()
 
@@ -453,7 +478,7 @@ def mg_serve_submit(sv: Server, grid, f, tol=1e-10, opts=None) -> int:
 def mg_serve_poll(sv: Server, ticket: int, x=None):
     """None while the request runs; else (status name, report dict)."""
     rep = mg_report()
-    st = _lib.mg_serve_poll(sv.ptr, C.c_uint64(ticket), _ptr(x), C.byref(rep))
+    st = _lib.mg_serve_poll(sv.ptr, C.c_uint64(ticket), _hptr(x), C.byref(rep))
     if st == MG_EAGAIN:
         return None
     if st not in (MG_OK, MG_ENOCONV):

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -97,3 +98,26 @@ def test_line_solve_and_adi_validation_without_gpu(so):
     assert e.value.status == mgs.MG_EINVAL
     st = mgs._lib.mg_adi_substep(None, 1.0, 1, None, None, None, None)
     assert st == mgs.MG_EINVAL
+
+
+def test_buffers_are_checked_for_their_memory_kind(so):
+    """Device arguments refuse host memory (numpy arrays, CPU tensors) before
+    any call: the kernels would read it as device memory.  Host arguments
+    refuse CUDA tensors and other dtypes."""
+    import torch
+    import paper_2305_17875_gb300 as mgs
+    host_t = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        mgs._ptr(host_t, "float64")
+    with pytest.raises(ValueError):
+        mgs._ptr(np.zeros(4), "float64")
+    with pytest.raises(TypeError):
+        mgs._ptr(torch.zeros(4, dtype=torch.float32), "float64")
+    assert mgs._ptr(1234, "float64") == 1234              # raw device address
+    assert mgs._hptr(host_t) == host_t.data_ptr()
+    a = np.zeros(4)
+    assert mgs._hptr(a) == a.ctypes.data
+    with pytest.raises(TypeError):
+        mgs._hptr(np.zeros(4, dtype=np.float32))
+    with pytest.raises(ValueError):
+        mgs._hptr(np.zeros((4, 4))[:, 0])
