@@ -595,7 +595,10 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
     } else if constexpr (OP == BOP_LINE) {
         line_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
     } else if constexpr (OP == BOP_XLINE) {
-        xline_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour, first, stride);
+        if (tk.n)   // chunked: W threads per line (uniform per task, so per block)
+            xline_pass_chunked<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
+        else
+            xline_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour, first, stride);
     } else if constexpr (OP == BOP_JACOBI) {
         jacobi_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (T*)tk.y, (const T*)tk.b, first, stride);
     } else if constexpr (OP == BOP_RESTRICT) {

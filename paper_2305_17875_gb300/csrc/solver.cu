@@ -4,6 +4,7 @@
 // the batch of one.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -240,9 +241,14 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                         if (narrow) {
                             P.add(t, vblocks(h, gs_items(h->L[level].D, h->stencil)));
                         } else {
+                            // MG_XLINE_CHUNKS=1: W threads per line where the lines fit
+                            const Dims& D = h->L[level].D;
+                            const int kc = prec == PREC64 ? LineRows<double>::kC : LineRows<float>::kC;
+                            const int W = std::getenv("MG_XLINE_CHUNKS") ? xline_chunks(D.nph, kc) : 0;
                             t.z = h->L[level].xf[prec == PREC64 ? 0 : 1];
                             t.y = h->L[level].t;
-                            P.add(t, vblocks(h, xline_items(h->L[level].D, h->stencil)));
+                            t.n = W > 0 ? 1 : 0;
+                            P.add(t, vblocks(h, xline_items(D, h->stencil) * (W > 0 ? W : 1)));
                         }
                     }
                 }

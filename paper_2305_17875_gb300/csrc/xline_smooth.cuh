@@ -85,4 +85,107 @@ __device__ __forceinline__ void xline_pass(const CF& cf, const Dims& D, T* x, co
     }
 }
 
+// Chunks of the leading block's rows per line for the chunked pass: W threads
+// per line (a power of two, at most 16), each holding at most kC rows in
+// registers; 0 when the lines are too long for it.
+__host__ __device__ inline int xline_chunks(int nph, int kC) {
+    const int w = line_chunks(nph - 1, kC);
+    return w <= 16 ? w : 0;
+}
+
+// The same colour pass with W threads per line (blockDim.x = 256, every
+// thread of the block takes part; virtual blocks lb, lb + nblocks, ...): each
+// thread runs the recurrences of T_c on its chunk of rows from a zero start,
+// the chunks' affine maps are composed through shared memory as in the
+// radial-line pass, then the periodic closure (psi1_0 and psi1_{n-2} through
+// shared memory, d_{n-1} by the line's last thread) and the correction.
+template <int S, typename T, typename CF>
+__device__ __forceinline__ void xline_pass_chunked(const CF& cf, const Dims& D, T* x, const T* b, const T* fac,
+                                                   int colour, int lb, int nblocks) {
+    constexpr int kC = LineRows<T>::kC;
+    __shared__ T sP[256], sQ[256], s0[256], s1[256], sD[256];
+    const i64 N = D.n();
+    const T* alpha = fac;
+    const T* beta = fac + N;
+    const T* gamma = fac + 2 * N;
+    const T* psi2 = fac + 3 * N;
+    const int n = D.nph, m = n - 1;                 // rows of the leading block
+    const int W = line_chunks(m, kC);
+    const int LB = 256 / W;
+    const int w = threadIdx.x / LB, l = threadIdx.x - w * LB;
+    const int rows = (m + W - 1) / W;
+    const int k0 = min(w * rows, m), nk = min(k0 + rows, m) - k0;
+    const i64 lines = xline_items(D, S);
+    const i64 groups = (lines + LB - 1) / LB;
+    for (i64 g = lb; g < groups; g += nblocks) {
+        const i64 t = g * LB + l;
+        int j = 0, i = 0;
+        const bool valid = t < lines && xline_of(D, S, colour, t, j, i);
+        const int cnt = valid ? nk : 0;             // rows this thread works on
+        const int c0 = (j * D.nth + i) * D.nph;
+        const int cl = c0 + n - 1;
+        T d[kC], P[kC];
+        T q = 0, p = 1;
+#pragma unroll
+        for (int u = 0; u < kC; ++u) {
+            if (u < cnt) {
+                const int k = k0 + u;
+                const T r = line_residual<S, T>(cf, D, x, b, j, i, k);
+                const T a = alpha[c0 + k];
+                q = fma(a, q, beta[c0 + k] * r);
+                p = p * a;
+                d[u] = q;
+                P[u] = p;
+            }
+        }
+        T rl = 0;
+        if (valid && w == W - 1) rl = line_residual<S, T>(cf, D, x, b, j, i, n - 1);
+        sP[threadIdx.x] = p;
+        sQ[threadIdx.x] = q;
+        __syncthreads();
+        T in = 0;
+        for (int v = 0; v < w; ++v) in = fma(sP[v * LB + l], in, sQ[v * LB + l]);
+        __syncthreads();
+        q = 0;
+        p = 1;
+        T last = 0;   // the backward value of the chunk's last row
+#pragma unroll
+        for (int u = kC - 1; u >= 0; --u) {
+            if (u < cnt) {
+                const T gm = gamma[c0 + k0 + u];
+                q = fma(gm, q, fma(P[u], in, d[u]));
+                p = p * gm;
+                d[u] = q;
+                P[u] = p;
+                if (u == cnt - 1) last = q;
+            }
+        }
+        sP[threadIdx.x] = p;
+        sQ[threadIdx.x] = q;
+        __syncthreads();
+        in = 0;
+        for (int v = W - 1; v > w; --v) in = fma(sP[v * LB + l], in, sQ[v * LB + l]);
+        // psi1 of the first and the last row of the leading block; the chunk
+        // holding the last row has only empty chunks after it (in = 0), so
+        // its backward value there is final
+        if (cnt > 0 && k0 == 0) s0[l] = fma(P[0], in, d[0]);
+        if (cnt > 0 && k0 + cnt == m) s1[l] = last;
+        __syncthreads();
+        if (valid && w == W - 1) {
+            const T dl = (rl - alpha[cl] * s0[l] - gamma[cl] * s1[l]) * beta[cl];
+            sD[l] = dl;
+            x[cl] = x[cl] + dl;
+        }
+        __syncthreads();
+        const T dl = sD[l];
+#pragma unroll
+        for (int u = 0; u < kC; ++u) {
+            if (u < cnt) {
+                const int c = c0 + k0 + u;
+                x[c] = x[c] + fma(psi2[c], dl, fma(P[u], in, d[u]));
+            }
+        }
+    }
+}
+
 }  // namespace mgs

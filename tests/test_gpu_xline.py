@@ -79,12 +79,16 @@ def test_line_sweeps_match_oracle(lib, name, prec, kind):
                                    err_msg=f"level {l} shape {lv.shape}")
 
 
+@pytest.mark.parametrize("chunks", [False, True])
 @pytest.mark.parametrize("kind", [XLINE, ALT])
 @pytest.mark.parametrize("name", list(XGRIDS))
-def test_fp64_iterates_match_oracle(lib, name, kind):
-    """Plain FP64 multigrid through the batched engine with the line smoothers:
+def test_fp64_iterates_match_oracle(lib, name, kind, chunks, monkeypatch):
+    """Plain FP64 multigrid through the batched engine with the line smoothers
+    (one thread per line, or MG_XLINE_CHUNKS=1: several threads per line):
     iterates and residual histories after 1 and 3 V-cycles."""
     import torch
+    if chunks:
+        monkeypatch.setenv("MG_XLINE_CHUNKS", "1")
     g = XGRIDS[name]
     n = grid.shell(g).n
     f = np.random.default_rng(42).standard_normal(n)
