@@ -171,6 +171,43 @@ def test_full_sphere_correction_is_divergence_free(name):
     assert np.linalg.norm(D1) <= 1e-11 * np.linalg.norm(D0)
 
 
+def test_full_sphere_zeta_sweep_is_the_merged_cut_system():
+    """Section 3.5 merges the zeta line at longitude k with the line at
+    k + nph/2 (run backwards) into one system of twice the length.  With the
+    zero-area pole faces the merged system's couplings across the poles are
+    zero: solving it whole gives the implicit zeta sweep of the two lines,
+    and any wall value at the poles has no effect."""
+    from oracle import adi, tridiag
+    sh = sphere_of(6, **MAPS["sphere"])
+    fm = grid.face_metrics(sh)
+    rng = np.random.default_rng(9)
+    rhs = rng.standard_normal(sh.shape)
+    kappa = 0.3 * fm["J"].min() / np.abs(fm["G1"][..., 1]).max()
+    got = adi.sweep(sh, fm, 0, kappa, rhs, adi.walls(colatitude=(adi.VALUE, 5.0, -3.0)))
+    got0 = adi.sweep(sh, fm, 0, kappa, rhs, adi.walls(colatitude=(adi.FLUX0, 0.0, 0.0)))
+    np.testing.assert_array_equal(got, got0)
+    a, b, c, w = adi.line_system(sh, fm, 0, kappa, adi.walls())
+    n, h = sh.nth, sh.nph // 2
+    for j in range(sh.nr):
+        for k in range(h):
+            # merged line: line k + h from the south pole up to the north pole,
+            # across it, then line k down to the south pole
+            idx = [(i, k + h) for i in range(n - 1, -1, -1)] + [(i, k) for i in range(n)]
+            A = np.zeros(2 * n)
+            B = np.zeros(2 * n)
+            Cc = np.zeros(2 * n)
+            g = np.zeros(2 * n)
+            for m, (i, kk) in enumerate(idx):
+                # reversed part: lower and upper neighbours swap
+                lo, up = (c[i, j, kk], a[i, j, kk]) if m < n else (a[i, j, kk], c[i, j, kk])
+                A[m], B[m], Cc[m], g[m] = lo, b[i, j, kk], up, rhs[j, i, kk]
+            # the joint between the two halves is the pole face: zero coupling
+            assert A[n] == 0.0 and Cc[n - 1] == 0.0
+            x = tridiag.thomas(A, B, Cc, g)
+            want = np.array([got[j, i, kk] for (i, kk) in idx])
+            np.testing.assert_allclose(x, want, rtol=0, atol=1e-13 * np.abs(want).max())
+
+
 # ---------------------------------------------------------------- multigrid on the cut
 def _prolongation_defect(nr, nth, nph):
     """Largest error of P on a coarse field linear in the colatitude measured
