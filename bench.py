@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-grid DOF/s to 1e-10 rel. residual, FP32-refined vs FP64 MG; HBM GB/s; p99 ms"
 UNIT = "DOF/s"
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
-SMOOTHER = {"gs": 0, "jacobi": 1, "line": 2}
+SMOOTHER = {"gs": 0, "jacobi": 1, "line": 2, "xline": 3, "alt": 4}
 PREC_NAME = {0: "plain FP64 multigrid", 1: "FP32 V-cycles inside FP64 refinement",
              2: "FP16-coefficient FP32 V-cycles inside FP64 refinement"}
 L2_FLUSH_BYTES = 256 << 20
@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=list(PREC))
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--smoother", default="gs", choices=list(SMOOTHER),
-                   help="gs: multicolour Gauss-Seidel; jacobi; line: radial-line Gauss-Seidel")
+                   help="gs: multicolour Gauss-Seidel; jacobi; line: radial-line Gauss-Seidel; "
+                        "xline: longitude-line Gauss-Seidel; alt: radial then longitude lines")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--requests", type=int, default=600, help="serve_stream: requests to submit")
@@ -115,8 +116,12 @@ def algorithmic_bytes(slot, stencil, prec, n_fine, n_next, smoother=0, axi=False
         # for 1/ncol of the cells, every coefficient an updated cell touches
         # (its lower faces' rows and the upper faces' rows of its neighbours)
         coef = ncomp * cb * N if stencil == 7 else (10 if axi else 18) * cb * N / ncol
-        line = 3 * vb * N / ncol if smoother == 2 else 0.0   # the line factors of the updated cells
-        return vb * N + 2 * vb * N / ncol + coef + line
+        base = vb * N + 2 * vb * N / ncol + coef
+        radial = 3 * vb * N / ncol          # radial-line factors of the updated cells
+        longitude = 4 * vb * N / ncol       # longitude-line factors (alpha, beta, gamma, psi2)
+        if smoother == 4:                   # as many radial as longitude passes: their mean
+            return base + (radial + longitude) / 2
+        return base + (radial if smoother == 2 else longitude if smoother == 3 else 0.0)
     if slot == "residual":
         # x, b, the FP64 operator rows (7-point: the three face arrays and the
         # stored centre; 19-point: the 19 assembled coefficients), FP32 r out

@@ -55,7 +55,7 @@ enum { MG_MAP_SPHERE = 0, MG_MAP_OBLATE = 1, MG_MAP_TRIAXIAL = 2 };
 enum { MG_PREC_FP64 = 0,        /* plain FP64 multigrid */
        MG_PREC_FP32_IR = 1,     /* FP32 V-cycles inside FP64 iterative refinement */
        MG_PREC_FP16C_IR = 2 };  /* FP16 coefficients, FP32 arithmetic, inside FP64 IR */
-enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1, MG_SMOOTH_LINE = 2 };
+enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1, MG_SMOOTH_LINE = 2, MG_SMOOTH_XLINE = 3, MG_SMOOTH_ALT = 4 };
 enum { MG_METRIC_DISCRETE = 0, MG_METRIC_ANALYTIC = 1 };
 enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
 
@@ -65,7 +65,12 @@ enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
  * colatitude th0 + (th1 - th0) i / nth and longitude 2 pi k / nph, mapped to
  * x1 = (1 - flattening) r cos th, x2 = (1 + e2) r sin th cos ph,
  * x3 = r sin th sin ph.  Requirements: nr, nth >= 1; nph >= 4 and even;
- * 0 < th0 < th1 < pi; 0 < r_in < r_out. */
+ * 0 < r_in < r_out; 0 < th0 < th1 < pi between zero-flux colatitude walls,
+ * or, with cut = 1, the full sphere th0 = 0, th1 = pi (the shell cut of
+ * Sections 3.5 and 3.7: a colatitude line continues through either pole into
+ * the line at longitude k + nph/2; the zeta faces on the polar axis have zero
+ * area and carry no flux).  The shell cut is built for the 7-point operator
+ * (the sphere mapping); other stencils return MG_EINVAL with it. */
 typedef struct {
     int nr, nth, nph;
     double r_in, r_out;
@@ -73,6 +78,7 @@ typedef struct {
     int mapping;              /* MG_MAP_* */
     double flattening, e2;
     double stretch;
+    int cut;                  /* 0: colatitude walls; 1: full sphere with the shell cut */
 } mg_grid_desc;
 
 /* Solver options; mg_default_opts fills the defaults noted here. */
@@ -83,7 +89,13 @@ typedef struct {
                            the Thomas algorithm of Section 3.5; lines coloured (i+k) mod 2
                            for 7 points, (i mod 2) + 2 (k mod 2) for 19 points; at most
                            256 radial cells; the coarse tail and the one-pass red-black
-                           tiles apply to GS only) */
+                           tiles apply to GS only); XLINE = longitude-line Gauss-Seidel
+                           (every longitude line solved by the periodic Thomas algorithm
+                           of Section 3.5 on the cyclic tridiagonal part of the operator
+                           on it; lines coloured (i+j) mod 2 for 7 points, (i mod 2) +
+                           2 (j mod 2) for 19 points; a level with fewer than four
+                           longitudes takes a point sweep instead); ALT = one LINE sweep
+                           then one XLINE sweep per smoothing step */
     int nu1, nu2;       /* pre/post sweeps, default 2, 2 */
     int max_levels;     /* default 16 */
     int coarsen;        /* MG_COARSEN_*, default SEMI */
@@ -201,8 +213,10 @@ mg_status mg_apply(mg_handle* h, int level, int prec, const void* x_dev, void* y
  * omega 6/7 for 7-point, 4/5 for 19-point; the diagonal is that of A_l) or
  * radial-line Gauss-Seidel (kind 2: x_L += A_LL^{-1} (b - A_l x)_L line by
  * line, A_LL the tridiagonal part of A_l on the line; line colours as for
- * MG_SMOOTH_LINE, in order).  Kind 2 on a handle set up with another
- * smoother first factors the line blocks of every level (allocates). */
+ * MG_SMOOTH_LINE, in order), longitude-line Gauss-Seidel (kind 3, as
+ * MG_SMOOTH_XLINE; uses the level's scratch array) or both (kind 4, radial
+ * then longitude lines per sweep).  Kinds 2 to 4 on a handle set up with
+ * another smoother first factor the line blocks of every level (allocates). */
 mg_status mg_smooth(mg_handle* h, int level, int prec, void* x_dev, const void* b_dev,
                     int sweeps, int kind);
 

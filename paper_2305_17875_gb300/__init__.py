@@ -27,7 +27,7 @@ STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_EN
           5: "MG_EDIVERGED", 6: "MG_ETIMEOUT", 7: "MG_EAGAIN", 8: "MG_ECUDA"}
 PREC_FP64, PREC_FP32_IR, PREC_FP16C_IR = 0, 1, 2
 MG_HIST = 64
-MG_SMOOTH_GS, MG_SMOOTH_JACOBI, MG_SMOOTH_LINE = range(3)
+MG_SMOOTH_GS, MG_SMOOTH_JACOBI, MG_SMOOTH_LINE, MG_SMOOTH_XLINE, MG_SMOOTH_ALT = range(5)
 MG_METRIC_DISCRETE, MG_METRIC_ANALYTIC = range(2)
 
 
@@ -36,7 +36,7 @@ class mg_grid_desc(C.Structure):
                 ("r_in", C.c_double), ("r_out", C.c_double),
                 ("th0", C.c_double), ("th1", C.c_double),
                 ("mapping", C.c_int), ("flattening", C.c_double), ("e2", C.c_double),
-                ("stretch", C.c_double)]
+                ("stretch", C.c_double), ("cut", C.c_int)]
 
 
 class mg_opts(C.Structure):

@@ -12,6 +12,7 @@
 
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
+#include "xline_smooth.cuh"
 
 namespace mgs {
 
@@ -593,6 +594,11 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
     } else if constexpr (OP == BOP_LINE) {
         line_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
+    } else if constexpr (OP == BOP_XLINE) {
+        if (tk.n)   // chunked: W threads per line (uniform per task, so per block)
+            xline_pass_chunked<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
+        else
+            xline_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour, first, stride);
     } else if constexpr (OP == BOP_JACOBI) {
         jacobi_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (T*)tk.y, (const T*)tk.b, first, stride);
     } else if constexpr (OP == BOP_RESTRICT) {
@@ -606,7 +612,13 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
             restrict_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
                                 (T*)tk.y, (T*)tk.z, first, stride);
     } else if constexpr (OP == BOP_PROLONG) {
-        if (vec4(tk.v.D))
+        if (tk.v.D.cut)
+            for (i64 c = first; c < tk.v.D.n(); c += stride) {
+                T* x = (T*)tk.x;
+                x[c] = x[c] + prolong_cut_cell<T>(tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b,
+                                                  decode(tk.v.D, c), [](const T* p) { return *p; });
+            }
+        else if (vec4(tk.v.D))
             prolong_pass_v<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
         else
             prolong_pass<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
@@ -986,6 +998,7 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
         STENCIL_OP(BOP_GS)
         STENCIL_OP(BOP_JACOBI)
         STENCIL_OP(BOP_LINE)
+        STENCIL_OP(BOP_XLINE)
         STENCIL_OP(BOP_RESTRICT)
         STENCIL_OP(BOP_RESID)
         PLAIN_OP(BOP_PROLONG)

@@ -98,8 +98,12 @@ std::string check_grid(const mg_grid_desc* g) {
     if ((long long)g->nr * g->nth * g->nph > (1LL << 31)) return "grid too large";
     if (!(finite(g->r_in) && finite(g->r_out) && g->r_in > 0 && g->r_out > g->r_in))
         return "need 0 < r_in < r_out";
-    if (!(finite(g->th0) && finite(g->th1) && g->th0 > 0 && g->th1 > g->th0 && g->th1 < M_PI))
+    if (g->cut != 0 && g->cut != 1) return "cut must be 0 or 1";
+    if (g->cut) {
+        if (!(g->th0 == 0.0 && g->th1 == M_PI)) return "the shell cut needs th0 = 0 and th1 = pi";
+    } else if (!(finite(g->th0) && finite(g->th1) && g->th0 > 0 && g->th1 > g->th0 && g->th1 < M_PI)) {
         return "need 0 < th0 < th1 < pi";
+    }
     if (g->mapping < 0 || g->mapping > 2) return "mapping must be 0, 1 or 2";
     if (!(finite(g->flattening) && g->flattening > -1 && g->flattening < 1)) return "need |flattening| < 1";
     if (!(finite(g->e2) && g->e2 > -1)) return "need e2 > -1";
@@ -110,7 +114,7 @@ std::string check_grid(const mg_grid_desc* g) {
 std::string check_opts(const mg_opts* o) {
     if (!o) return "opts is NULL";
     if (o->precision < 0 || o->precision > 2) return "precision must be 0, 1 or 2";
-    if (o->smoother < 0 || o->smoother > 2) return "smoother must be 0, 1 or 2";
+    if (o->smoother < 0 || o->smoother > 4) return "smoother must be 0 .. 4";
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 > 64) return "bad nu1/nu2";
     if (o->max_levels < 1 || o->max_levels > 32) return "max_levels must be in 1..32";
     if (o->coarsen < 0 || o->coarsen > 1) return "coarsen must be 0 or 1";
@@ -125,6 +129,12 @@ std::string check_opts(const mg_opts* o) {
 int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
     if (o->stencil) return o->stencil;
     return g->mapping == MG_MAP_SPHERE ? 7 : 19;
+}
+
+// Combinations of a valid grid and valid options that are not built.
+std::string check_pair(const mg_grid_desc* g, const mg_opts* o) {
+    if (g->cut && stencil_of(g, o) != 7) return "the shell cut is built for the 7-point operator only";
+    return "";
 }
 
 void* dalloc(mg_handle* h, size_t bytes) {
@@ -268,6 +278,31 @@ mg_status ensure_line_factors(mg_handle* h, int prec) {
     CK(cudaStreamSynchronize(h->stream));
     if (hb) {
         set_error("a radial-line block of the operator has a zero pivot");
+        return MG_EINVAL;
+    }
+    return MG_OK;
+}
+
+// Longitude-line factors of every level with at least four longitudes, in
+// the value type of `prec`, made on first use.
+mg_status ensure_xline_factors(mg_handle* h, int prec) {
+    const int cls = prec == PREC64 ? 0 : 1;
+    bool missing = false;
+    for (const Level& lv : h->L) missing = missing || (lv.D.nph >= 4 && !lv.xf[cls]);
+    if (!missing) return MG_OK;
+    TmpDev tb(sizeof(unsigned), h->stream, h->device);
+    if (!tb.p) return MG_ENOMEM;
+    CK(cudaMemsetAsync(tb.p, 0, sizeof(unsigned), h->stream));
+    for (Level& lv : h->L) {
+        if (lv.xf[cls] || lv.D.nph < 4) continue;
+        if (!(lv.xf[cls] = dalloc(h, 4 * (size_t)(cls == 0 ? 8 : 4) * lv.D.n()))) return MG_ENOMEM;
+        CK(launch_xline_factors(lv.view(h->stencil), prec, lv.xf[cls], (unsigned*)tb.p, h->stream));
+    }
+    unsigned hb = 0;
+    CK(cudaMemcpyAsync(&hb, tb.p, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hb) {
+        set_error("a longitude-line block of the operator has a zero pivot");
         return MG_EINVAL;
     }
     return MG_OK;
@@ -515,6 +550,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
 
     Level L0;
     L0.D = Dims{nr, nth, nph};
+    L0.D.cut = g->cut;
     const i64 N = L0.D.n();
     for (int a = 0; a < 9; ++a)
         if (stored(h, a) && !(L0.g64[a] = (double*)dalloc(h, sizeof(double) * N))) return MG_ENOMEM;
@@ -584,6 +620,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         fine.cx = f[2];
         Level c;
         c.D = Dims{fine.D.nr / fine.ce, fine.D.nth / fine.cz, fine.D.nph / fine.cx};
+        c.D.cut = fine.D.cut;
         for (int a = 0; a < 9; ++a)
             if (stored(h, a) && !(c.g64[a] = (double*)dalloc(h, sizeof(double) * c.D.n())))
                 return MG_ENOMEM;
@@ -645,7 +682,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         }
     }
 
-    if (o->smoother == MG_SMOOTH_LINE) CKS(ensure_line_factors(h, h->prec));
+    if (radial_lines(o->smoother)) CKS(ensure_line_factors(h, h->prec));
+    if (longitude_lines(o->smoother)) CKS(ensure_xline_factors(h, h->prec));
 
     // --- coarsest level: dense operator -> bordered inverse (device, FP64)
     const int nc = h->ncoarse;
@@ -814,12 +852,25 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
         const int ncol = h->stencil == 7 ? 2 : 4;
         for (int s = 0; s < sweeps; ++s)
             for (int c = 0; c < ncol; ++c, ++n) CK(launch_gs_colour(v, prec, x, b, c, h->stream));
-    } else if (kind == MG_SMOOTH_LINE) {
-        CKS(ensure_line_factors(h, prec));
+    } else if (kind == MG_SMOOTH_LINE || kind == MG_SMOOTH_XLINE || kind == MG_SMOOTH_ALT) {
+        // radial lines, longitude lines, or both in that order per sweep; a
+        // level narrower than four longitudes takes a point sweep for the
+        // longitude lines
         const int ncol = h->stencil == 7 ? 2 : 4;
-        const void* fac = lv.lf[prec == PREC64 ? 0 : 1];
-        for (int s = 0; s < sweeps; ++s)
-            for (int c = 0; c < ncol; ++c, ++n) CK(launch_line_colour(v, prec, x, b, fac, c, h->stream));
+        const int cls = prec == PREC64 ? 0 : 1;
+        if (radial_lines(kind)) CKS(ensure_line_factors(h, prec));
+        if (longitude_lines(kind)) CKS(ensure_xline_factors(h, prec));
+        for (int s = 0; s < sweeps; ++s) {
+            if (radial_lines(kind))
+                for (int c = 0; c < ncol; ++c, ++n) CK(launch_line_colour(v, prec, x, b, lv.lf[cls], c, h->stream));
+            if (!longitude_lines(kind)) continue;
+            if (lv.D.nph < 4) {
+                for (int c = 0; c < ncol; ++c, ++n) CK(launch_gs_colour(v, prec, x, b, c, h->stream));
+                continue;
+            }
+            for (int c = 0; c < ncol; ++c, ++n)
+                CK(launch_xline_colour(v, prec, x, b, lv.xf[cls], lv.t, c, h->stream));
+        }
     } else {
         const size_t bytes = value_bytes(prec) * lv.D.n();
         for (int s = 0; s < sweeps; ++s, ++n) {
@@ -878,7 +929,10 @@ double model_bytes_per_iteration(const mg_handle* h) {
     const int nc = h->stencil == 19 ? 9 : 3;
     const double vb = (double)value_bytes(h->prec), cb = (double)coef_bytes(h->prec);
     const int ncol = h->opts.smoother != MG_SMOOTH_JACOBI ? (h->stencil == 7 ? 2 : 4) : 1;
-    const double fac_bytes = h->opts.smoother == MG_SMOOTH_LINE ? 3 * vb : 0.0;   // line factors
+    // line factors (radial 3, longitude 4 values per cell; the longitude pass
+    // also writes and reads its scratch)
+    const double fac_bytes = (radial_lines(h->opts.smoother) ? 3 * vb : 0.0) +
+                             (longitude_lines(h->opts.smoother) ? 6 * vb : 0.0);
     double total = 0.0;
     for (size_t l = 0; l < h->L.size(); ++l) {
         const double n = (double)h->L[l].D.n();
@@ -964,7 +1018,7 @@ size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
         mg_default_opts(&d);
         o = &d;
     }
-    if (!check_grid(g).empty() || !check_opts(o).empty()) return 0;
+    if (!check_grid(g).empty() || !check_opts(o).empty() || !check_pair(g, o).empty()) return 0;
     const double n = (double)g->nr * g->nth * g->nph;
     const int nc = stencil_of(g, o) == 19 ? 9 : 3;
     const double cb = (double)coef_bytes(o->precision);
@@ -974,7 +1028,8 @@ size_t mg_footprint_bytes(const mg_grid_desc* g, const mg_opts* o) {
     const double coarse = n * (nc * (8 + (o->precision == PREC64 ? 0 : cb)) + 24);
     const double rows = n * 8 * (nc == 9 ? 19 : 1);   // assembled fine rows
     const double fixed = n * 16 /*J, b*/ + rows + 8.0 * kMaxCoarse * kMaxCoarse + (1 << 20);
-    const double lines = o->smoother == MG_SMOOTH_LINE ? 2 * n * 3 * value_bytes(o->precision) : 0.0;
+    const double lines = (radial_lines(o->smoother) ? 2 * n * 3 * value_bytes(o->precision) : 0.0) +
+                         (longitude_lines(o->smoother) ? 2 * n * 4 * value_bytes(o->precision) : 0.0);
     return (size_t)(fine + coarse + fixed + lines);
 }
 
@@ -989,6 +1044,7 @@ mg_status mg_setup(const mg_grid_desc* g, const mg_opts* o, void* stream, mg_han
     }
     std::string why = check_grid(g);
     if (why.empty()) why = check_opts(o);
+    if (why.empty()) why = check_pair(g, o);
     if (!why.empty()) {
         set_error(why);
         return MG_EINVAL;
@@ -1080,7 +1136,7 @@ mg_status mg_apply(mg_handle* h, int level, int prec, const void* x, void* y) {
 
 mg_status mg_smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
     LEVEL_CHECK(h, level, prec);
-    if (!x || !b || sweeps < 0 || kind < 0 || kind > 2) return MG_EINVAL;
+    if (!x || !b || sweeps < 0 || kind < 0 || kind > 4) return MG_EINVAL;
     StreamJoin join(h);
     return smooth(h, level, prec, x, b, sweeps, kind);
 }

@@ -25,6 +25,7 @@ struct Level {
     void* r = nullptr;   // right side on this level
     void* t = nullptr;   // scratch (Jacobi)
     void* lf[2] = {};    // radial-line factors, double / float (3 n values), made on first use
+    void* xf[2] = {};    // longitude-line factors, double / float (4 n values), made on first use
     LevelView view(int stencil) const;
 };
 
@@ -144,4 +145,7 @@ mg_status plan_time(Plan* pl, int warm, int reps, double* ms);
 mg_status plan_finish(Plan* pl, double* const* x);
 mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind);
 double model_bytes_per_iteration(const mg_handle* h);
+// smoothers that sweep radial lines / longitude lines (the alternating one both)
+inline bool radial_lines(int smoother) { return smoother == MG_SMOOTH_LINE || smoother == MG_SMOOTH_ALT; }
+inline bool longitude_lines(int smoother) { return smoother == MG_SMOOTH_XLINE || smoother == MG_SMOOTH_ALT; }
 }  // namespace mgs

@@ -135,10 +135,11 @@ __global__ void k_wall_G(MetricTables t, Dims D, double* r_lo, double* r_hi, dou
             const i64 p = q - nr_w;
             const int j = (int)(p / D.nph), k = (int)(p % D.nph);
             const int vl[3] = {0, j, k}, vh[3] = {D.nth, j, k};
+            // on the full sphere these faces lie on the polar axis: zero area, no flux
             face_metric(t, 0, vl, row);
-            th_lo[p] = row[0];
+            th_lo[p] = D.cut ? 0.0 : row[0];
             face_metric(t, 0, vh, row);
-            th_hi[p] = row[0];
+            th_hi[p] = D.cut ? 0.0 : row[0];
         }
     }
 }
@@ -309,6 +310,70 @@ __global__ void k_line_factors(CoefF64 cf, Dims D, T* fac, unsigned* bad) {
     }
 }
 
+// Factors of the longitude-line blocks (the cyclic tridiagonal part of the
+// operator on every line of fixed j and i: couplings at longitude offsets
+// -1, 0, +1, found by applying the operator to unit vectors) for the
+// longitude-line smoother, in the layout of xline_smooth.cuh: the normalised
+// Thomas elimination of the leading block T_c (alpha, beta, gamma), psi2 =
+// T_c^{-1} (-a_0, 0, .., 0, -c_{n-2}), and in the last cell's slot c_{n-1},
+// 1 / (b_{n-1} + c_{n-1} psi2_0 + a_{n-1} psi2_{n-2}) and a_{n-1}.  FP64
+// elimination; the backward pass of psi2 reads the stored (type T) factors,
+// as the smoother does.  Needs nph >= 4.  A zero or non-finite pivot counts
+// in *bad.
+template <int S, typename T>
+__global__ void k_xline_factors(CoefF64 cf, Dims D, T* fac, unsigned* bad) {
+    const i64 N = D.n();
+    const i64 lines = (i64)D.nr * D.nth;
+    const int n = D.nph;
+    T* alpha = fac;
+    T* beta = fac + N;
+    T* gamma = fac + 2 * N;
+    T* psi2 = fac + 3 * N;
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < lines; t += (i64)gridDim.x * blockDim.x) {
+        const int j = (int)(t / D.nth), i = (int)(t % D.nth);
+        const i64 c0 = (i64)(j * D.nth + i) * n;
+        auto coupling = [&](int k, int m) {   // A(c_k, c_m)
+            const C3 p{j, i, k};
+            return apply_cell<S, double>(cf, UnitX{c0 + m, D}, D, p);
+        };
+        bool ok = true;
+        // forward elimination of T_c; psi2's forward recurrence alongside
+        double cprev = 0.0, q = 0.0;
+        for (int k = 0; k < n - 1; ++k) {
+            const double lo = k > 0 ? coupling(k, k - 1) : 0.0;
+            const double dd = coupling(k, k);
+            const double up = k < n - 2 ? coupling(k, k + 1) : 0.0;
+            const double ib = 1.0 / (dd - lo * cprev);
+            const double a = -lo * ib;
+            cprev = up * ib;
+            double e = 0.0;                               // right side of psi2
+            if (k == 0) e -= coupling(0, n - 1);
+            if (k == n - 2) e -= coupling(n - 2, n - 1);
+            q = fma(a, q, ib * e);
+            ok = ok && isfinite(ib) && isfinite(a) && isfinite(cprev);
+            alpha[c0 + k] = (T)a;
+            beta[c0 + k] = (T)ib;
+            gamma[c0 + k] = (T)(-cprev);
+            psi2[c0 + k] = (T)q;                          // forward value, finished below
+        }
+        double e = 0.0, p2_first = 0.0, p2_last = 0.0;
+        for (int k = n - 2; k >= 0; --k) {
+            e = fma((double)gamma[c0 + k], e, (double)psi2[c0 + k]);
+            psi2[c0 + k] = (T)e;
+            if (k == n - 2) p2_last = e;
+            if (k == 0) p2_first = e;
+        }
+        const double an = coupling(n - 1, n - 2), cn = coupling(n - 1, 0), bn = coupling(n - 1, n - 1);
+        const double inv = 1.0 / (bn + cn * p2_first + an * p2_last);
+        ok = ok && isfinite(inv);
+        alpha[c0 + n - 1] = (T)cn;
+        beta[c0 + n - 1] = (T)inv;
+        gamma[c0 + n - 1] = (T)an;
+        psi2[c0 + n - 1] = (T)0;
+        if (!ok) atomicAdd(bad, 1u);
+    }
+}
+
 // ---- in-place Gauss-Jordan inversion with partial pivoting (FP64), for the
 // bordered coarsest matrix [A 1; 1^T 0] of order m.  Step k: the pivot row
 // (largest |M[r][k]|, r >= k) is swapped into row k, row k is scaled, and
@@ -442,6 +507,19 @@ cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsign
     } else {
         if (lv.stencil == 19) k_line_factors<19, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
         else k_line_factors<7, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xline_factors(const LevelView& lv, int prec, void* fac, unsigned* bad, cudaStream_t s) {
+    const i64 lines = (i64)lv.D.nr * lv.D.nth;
+    const int nb = grid_for(lines, 128);
+    if (prec == PREC64) {
+        if (lv.stencil == 19) k_xline_factors<19, double><<<nb, 128, 0, s>>>(lv.c64, lv.D, (double*)fac, bad);
+        else k_xline_factors<7, double><<<nb, 128, 0, s>>>(lv.c64, lv.D, (double*)fac, bad);
+    } else {
+        if (lv.stencil == 19) k_xline_factors<19, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
+        else k_xline_factors<7, float><<<nb, 128, 0, s>>>(lv.c64, lv.D, (float*)fac, bad);
     }
     return cudaGetLastError();
 }

@@ -43,6 +43,7 @@ struct FastDiv {
 struct Dims {
     int nr = 0, nth = 0, nph = 0;
     FastDiv dph, dth, dhk, dq, dth2;   // by nph, nth, nph / 2, nph / 4, (nth + 1) / 2
+    int cut = 0;                       // full sphere: colatitude lines joined through the poles
     __host__ __device__ Dims() {}
     __host__ __device__ Dims(int r, int t, int p)
         : nr(r), nth(t), nph(p), dph((unsigned)p), dth((unsigned)t), dhk((unsigned)(p >= 2 ? p / 2 : 1)),
@@ -101,6 +102,54 @@ __device__ __forceinline__ C3 shift(C3 c, int s, const Dims& D) {
         c.k = v < 0 ? v + D.nph : (v >= D.nph ? v - D.nph : v);
     }
     return c;
+}
+
+// Prolongation of one fine cell on the full sphere (shell cut): cell-centred
+// trilinear weights (3/4, 1/4 per halved direction; mirror at the radius
+// walls, wrap in longitude) where the colatitude partner of a fine cell in the
+// first or last coarse row lies across the pole: the coarse cell of the same
+// row at longitude K + nph_c / 2.  Returns the weighted sum of ec, read
+// through ld (a functor taking the element's address).
+template <typename T, typename LD>
+__device__ __forceinline__ T prolong_cut_cell(const Dims& Dc, int cz, int ce, int cx, const T* ec, C3 f, LD ld) {
+    int ij[2], ii[2], ik[2];
+    float wj[2], wi[2], wk[2];
+    bool turn = false;   // the second colatitude partner is across the pole
+    auto lin = [](int v, int c, int nc, int mode, int idx[2], float w[2], bool* across) {
+        // mode 0 mirror, 1 periodic, 2 cut
+        if (c == 1) {
+            idx[0] = idx[1] = v;
+            w[0] = 1.0f;
+            w[1] = 0.0f;
+            return;
+        }
+        const int C = v >> 1;
+        int nb = (v & 1) ? C + 1 : C - 1;
+        if (mode == 1) {
+            nb = nb < 0 ? nb + nc : (nb >= nc ? nb - nc : nb);
+        } else if (nb < 0 || nb >= nc) {
+            if (mode == 2) *across = true;
+            nb = C;
+        }
+        idx[0] = C;
+        idx[1] = nb;
+        w[0] = 0.75f;
+        w[1] = 0.25f;
+    };
+    bool dummy = false;
+    lin(f.j, ce, Dc.nr, 0, ij, wj, &dummy);
+    lin(f.i, cz, Dc.nth, 2, ii, wi, &turn);
+    lin(f.k, cx, Dc.nph, 1, ik, wk, &dummy);
+    const int half = Dc.nph >> 1;
+    T s = 0;
+    for (int a = 0; a < ce; ++a)
+        for (int bb = 0; bb < cz; ++bb)
+            for (int e = 0; e < cx; ++e) {
+                int k = ik[e];
+                if (turn && bb == 1) k = k + half >= Dc.nph ? k + half - Dc.nph : k + half;
+                s = fma((T)wj[a] * (T)wi[bb] * (T)wk[e], ld(ec + cidx(Dc, ij[a], ii[bb], k)), s);
+            }
+    return s;
 }
 
 // ---------------------------------------------------------------- coefficients

@@ -46,6 +46,9 @@ cudaError_t launch_dense_operator(const LevelView& lv, double* A, cudaStream_t s
 // 3 x n values of the cycle's type (double for PREC64, float otherwise);
 // *bad (zeroed by the caller) counts zero or non-finite pivots.
 cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsigned* bad, cudaStream_t s);
+// Longitude-line factors (4 n values of the precision class of prec; layout of
+// xline_smooth.cuh); the level needs nph >= 4.
+cudaError_t launch_xline_factors(const LevelView& lv, int prec, void* fac, unsigned* bad, cudaStream_t s);
 // Leading n x n block of [A 1; 1^T 0]^{-1} (A: n x n row-major) by Gauss-Jordan
 // elimination on the device.  work: (n+1)^2 doubles, col: n+1 doubles, piv and
 // perm: n+1 ints each, *bad (zeroed by the caller) set on a zero pivot.
@@ -81,6 +84,10 @@ cudaError_t launch_gs_colour(const LevelView& lv, int prec, void* x, const void*
                              cudaStream_t s);
 cudaError_t launch_jacobi(const LevelView& lv, int prec, const void* x, void* xo, const void* b,
                           cudaStream_t s);
+// One colour of the longitude-line Gauss-Seidel sweep (fac from
+// launch_xline_factors; work: n values of scratch).
+cudaError_t launch_xline_colour(const LevelView& lv, int prec, void* x, const void* b, const void* fac,
+                                void* work, int colour, cudaStream_t s);
 // One colour of the radial-line Gauss-Seidel sweep (fac from launch_line_factors).
 cudaError_t launch_line_colour(const LevelView& lv, int prec, void* x, const void* b, const void* fac,
                                int colour, cudaStream_t s);
@@ -129,7 +136,8 @@ enum {
     BOP_FINALIZE,     // scal[slot] = sum of n partials z; y (if set) gets a copy
     BOP_COARSE,       // x = binv b, n rows
     BOP_RB7,          // one red-black sweep of the 7-point operator, x -> y (tiles)
-    BOP_LINE          // radial-line Gauss-Seidel colour pass: x, b, z = line factors
+    BOP_LINE,         // radial-line Gauss-Seidel colour pass: x, b, z = line factors
+    BOP_XLINE         // longitude-line Gauss-Seidel colour pass: x, b, z = factors, y = scratch
 };
 // Tiles of the one-pass red-black sweep (colatitude x radius x longitude).
 constexpr int kRbJ = 8, kRbI = 8, kRbK = 64;

@@ -4,12 +4,13 @@
 // the batch of one.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "engine.h"
-#include "line_smooth.cuh"
+#include "xline_smooth.cuh"
 
 namespace mgs {
 
@@ -152,14 +153,17 @@ bool fused_level(const mg_handle* h, int level) {
 
 void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
     const int prec = pl->prec;
-    int maxc = 0, maxl = 0;
+    int maxc = 0, maxl = 0, maxx = 0;
     bool any_jacobi = false, any_fused = false;
     for (mg_handle* h : pl->hs) {
         if (level >= top_of(h)) continue;
+        const int nc = h->stencil == 7 ? 2 : 4;
         if (h->opts.smoother == MG_SMOOTH_JACOBI) any_jacobi = true;
-        else if (h->opts.smoother == MG_SMOOTH_LINE) maxl = std::max(maxl, h->stencil == 7 ? 2 : 4);
-        else if (fused_level(h, level)) any_fused = true;
-        else maxc = std::max(maxc, h->stencil == 7 ? 2 : 4);
+        else if (radial_lines(h->opts.smoother) || longitude_lines(h->opts.smoother)) {
+            if (radial_lines(h->opts.smoother)) maxl = std::max(maxl, nc);
+            if (longitude_lines(h->opts.smoother)) maxx = std::max(maxx, nc);
+        } else if (fused_level(h, level)) any_fused = true;
+        else maxc = std::max(maxc, nc);
     }
     for (int sw = 0; sw < sweeps; ++sw) {
         if (any_fused) {   // ping-pong between the level iterate and its scratch
@@ -208,7 +212,7 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
             }
             for (size_t s = 0; s < pl->hs.size(); ++s) {
                 mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_LINE || h->stencil != st) continue;
+                if (level >= top_of(h) || !radial_lines(h->opts.smoother) || h->stencil != st) continue;
                 if (c >= (h->stencil == 7 ? 2 : 4)) continue;
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
@@ -217,6 +221,37 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
                 P.add(t, vblocks(h, line_items(h->L[level].D, h->stencil, prec)));
             }
         }
+        // longitude lines after the radial ones (the alternating smoother);
+        // levels narrower than four longitudes take a point colour instead
+        for (int c = 0; c < maxx; ++c)
+            for (int st : {7, 19})
+                for (int narrow = 0; narrow < 2; ++narrow) {
+                    Launch& L = P.begin(narrow ? BOP_GS : BOP_XLINE, c, st);
+                    if (level == 0) {
+                        L.prof = MG_PROF_SMOOTH0;
+                        L.prof_n = 1;
+                    }
+                    for (size_t s = 0; s < pl->hs.size(); ++s) {
+                        mg_handle* h = pl->hs[s];
+                        if (level >= top_of(h) || !longitude_lines(h->opts.smoother) || h->stencil != st) continue;
+                        if (c >= (h->stencil == 7 ? 2 : 4) || (h->L[level].D.nph < 4) != (narrow == 1)) continue;
+                        BTask t = task_of(h, level);
+                        level_bufs(h, prec, level, &t.x, &t.b);
+                        t.shell = (int)s;
+                        if (narrow) {
+                            P.add(t, vblocks(h, gs_items(h->L[level].D, h->stencil)));
+                        } else {
+                            // MG_XLINE_CHUNKS=1: W threads per line where the lines fit
+                            const Dims& D = h->L[level].D;
+                            const int kc = prec == PREC64 ? LineRows<double>::kC : LineRows<float>::kC;
+                            const int W = std::getenv("MG_XLINE_CHUNKS") ? xline_chunks(D.nph, kc) : 0;
+                            t.z = h->L[level].xf[prec == PREC64 ? 0 : 1];
+                            t.y = h->L[level].t;
+                            t.n = W > 0 ? 1 : 0;
+                            P.add(t, vblocks(h, xline_items(D, h->stencil) * (W > 0 ? W : 1)));
+                        }
+                    }
+                }
         if (any_jacobi) {
             for (int st : {7, 19}) {
             Launch& L = P.begin(BOP_JACOBI, 0, st);

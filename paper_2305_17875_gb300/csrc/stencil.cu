@@ -6,6 +6,7 @@
 
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
+#include "xline_smooth.cuh"
 
 namespace mgs {
 
@@ -131,6 +132,12 @@ __device__ __forceinline__ void lin1d(int f, int c, int nc, bool periodic, int i
 template <typename T, bool CG>
 __device__ __forceinline__ void prolong_range(const Dims& D, const Dims& Dc, int cz, int ce, int cx, const T* ec,
                                               T* x, i64 first, i64 stride) {
+    if (D.cut) {   // full sphere: colatitude partners across the poles
+        for (i64 c = first; c < D.n(); c += stride)
+            x[c] = ldv<T, CG>(x + c) +
+                   prolong_cut_cell<T>(Dc, cz, ce, cx, ec, decode(D, c), [](const T* p) { return ldv<T, CG>(p); });
+        return;
+    }
     for (i64 c = first; c < D.n(); c += stride) {
         const C3 f = decode(D, c);
         int ij[2], ii[2], ik[2];
@@ -187,6 +194,13 @@ template <int S, typename T, typename CF>
 __global__ void __launch_bounds__(kThreads, 2) k_line(CF cf, Dims D, T* x, const T* __restrict__ b,
                                                     const T* __restrict__ fac, int colour) {
     line_pass<S, T>(cf, D, x, b, fac, colour, blockIdx.x, gridDim.x);
+}
+
+template <int S, typename T, typename CF>
+__global__ void __launch_bounds__(kThreads) k_xline(CF cf, Dims D, T* x, const T* __restrict__ b,
+                                                     const T* __restrict__ fac, T* work, int colour) {
+    xline_pass<S, T>(cf, D, x, b, fac, work, colour, blockIdx.x * (i64)blockDim.x + threadIdx.x,
+                     (i64)gridDim.x * blockDim.x);
 }
 
 // Weighted Jacobi, out of place: xo = x + omega (b - A x) / diag(A).
@@ -328,6 +342,14 @@ cudaError_t launch_line_colour(const LevelView& lv, int prec, void* x, const voi
     const int nb = blocks_for(lines * line_chunks(lv.D.nr, kc));
     MG_DISPATCH(lv, prec, (k_line<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, (const T*)fac,
                                                                 colour)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xline_colour(const LevelView& lv, int prec, void* x, const void* b, const void* fac,
+                                void* work, int colour, cudaStream_t s) {
+    const int nb = blocks_for(xline_items(lv.D, lv.stencil));
+    MG_DISPATCH(lv, prec, (k_xline<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, (const T*)fac,
+                                                                 (T*)work, colour)));
     return cudaGetLastError();
 }
 

@@ -54,6 +54,14 @@ def test_host_side_validation_without_gpu(so):
     assert mgs.mg_footprint_bytes(dict(g, nph=2)) == 0            # degenerate longitude faces
     assert mgs.mg_footprint_bytes(dict(g, r_out=0.5)) == 0        # r_out < r_in
     assert mgs.mg_footprint_bytes(dict(g, th1=3.5)) == 0          # beyond the pole
+    import math
+    sphere = dict(g, th0=0.0, th1=math.pi, cut=1)                      # full sphere, shell cut
+    assert mgs.mg_footprint_bytes(sphere) > 0
+    assert mgs.mg_footprint_bytes(dict(sphere, cut=2)) == 0
+    assert mgs.mg_footprint_bytes(dict(g, cut=1)) == 0               # cut needs [0, pi]
+    assert mgs.mg_footprint_bytes(dict(sphere, th0=0.0, cut=0)) == 0  # walls need th0 > 0
+    assert mgs.mg_footprint_bytes(dict(sphere, mapping=1, flattening=0.1)) == 0   # 19 points
+    assert mgs.mg_footprint_bytes(sphere, dict(stencil=19)) == 0
     with pytest.raises(mgs.MGError) as e:
         mgs.mg_setup(dict(g, nph=15), stream=0)
     assert e.value.status == mgs.MG_EINVAL

@@ -33,12 +33,16 @@ PI = math.pi
 
 
 def grid_desc(nr, nth=None, nph=None, r_in=1.0, r_out=2.0, th0=PI / 6, th1=5 * PI / 6,
-              mapping=0, flattening=0.0, e2=0.0, stretch=0.0):
+              mapping=0, flattening=0.0, e2=0.0, stretch=0.0, cut=False):
+    """Grid description dict (the C field names).  ``cut`` makes it the full
+    sphere with the shell cut (th0 = 0, th1 = pi)."""
     nth = nr if nth is None else nth
     nph = 2 * nr if nph is None else nph
+    if cut:
+        th0, th1 = 0.0, PI
     return dict(nr=int(nr), nth=int(nth), nph=int(nph), r_in=float(r_in), r_out=float(r_out),
                 th0=float(th0), th1=float(th1), mapping=int(mapping),
-                flattening=float(flattening), e2=float(e2), stretch=float(stretch))
+                flattening=float(flattening), e2=float(e2), stretch=float(stretch), cut=int(bool(cut)))
 
 
 def _centres(g):
@@ -103,6 +107,10 @@ SINGLE = {
     # dominates by ~10^3; the case the radial-line smoother is for
     "single_thin_128": dict(grid=grid_desc(128, r_out=1.05, stretch=2.0), rhs=("modes", 0), tol=1e-10,
                             precision="fp32"),
+    # the whole sphere with the shell cut (theta in [0, pi]): the paper's own
+    # domain; longitude coupling grows like 1/sin^2(theta) toward the poles
+    "single_full_sphere_128": dict(grid=grid_desc(128, stretch=2.0, cut=True), rhs=("modes", 0), tol=1e-10,
+                                   precision="fp32"),
 }
 
 
