@@ -53,6 +53,7 @@ def parse():
                         "xline: longitude-line Gauss-Seidel; alt: radial then longitude lines")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-c3", action="store_true", help="skip the 256 x 256 x 512 oblate-shell leg")
     p.add_argument("--requests", type=int, default=600, help="serve_stream: requests to submit")
     p.add_argument("--rate", type=float, default=200.0, help="serve_stream: Poisson arrival rate (1/s)")
     return p.parse_args()
@@ -101,41 +102,56 @@ def ncu_traffic(workload, precision, slot):
     return e.get("dram_bytes_per_launch") * scale
 
 
-def algorithmic_bytes(slot, stencil, prec, n_fine, n_next, smoother=0, axi=False):
-    """Minimum HBM bytes one launch of the slot's kernel must move (each array
-    it needs read or written once; neighbour re-reads served on chip).  axi:
-    a 19-point operator on an axisymmetric mapping, which keeps 5 of the 9
-    metric components (the longitude cross terms vanish)."""
+def coef_components(stencil, axi):
+    """Metric arrays the operator stores: 3 for 7 points, 9 for 19 points, 5
+    for 19 points on an axisymmetric mapping (the longitude cross terms
+    vanish there and are not stored)."""
+    return (5 if axi else 9) if stencil == 19 else 3
+
+
+def sweep_bytes_per_cell(stencil, prec, smoother=0, axi=False, ncomp=None):
+    """Minimum HBM bytes of one whole smoothing sweep (all colours) per cell:
+    x read and written, b read, every stored coefficient array read once;
+    line smoothers add their factor arrays (radial 3, longitude 4 values per
+    cell; the alternating smoother's sweeps are radial and longitude in
+    turn: their mean)."""
     vb = 8 if prec == 0 else 4
     cb = {0: 8, 1: 4, 2: 2}[prec]
-    ncomp = (5 if axi else 9) if stencil == 19 else 3
-    ncol = 4 if stencil == 19 else 2
+    nc = coef_components(stencil, axi) if ncomp is None else ncomp
+    base = 3 * vb + nc * cb
+    fac = {2: 3 * vb, 3: 4 * vb, 4: 3.5 * vb}.get(smoother, 0.0)
+    return base + fac
+
+
+def algorithmic_bytes(slot, stencil, prec, n_fine, n_next, smoother=0, axi=False, passes_per_sweep=None,
+                      ncomp=None):
+    """Minimum HBM bytes one launch of the slot's kernel must move: each array
+    it needs read or written once, neighbour re-reads served on chip.  A
+    colour pass is charged 1/C of a whole sweep (C = 2 colours for 7 points, 4
+    for 19 points); a one-pass sweep (all colours in one launch,
+    passes_per_sweep = 1) the whole sweep.  ncomp overrides the stored
+    coefficient count (9 for 19 points: the count of the survey's table)."""
+    vb = 8 if prec == 0 else 4
+    cb = {0: 8, 1: 4, 2: 2}[prec]
+    nc = coef_components(stencil, axi) if ncomp is None else ncomp
     N = float(n_fine)
     if slot == "smooth0":
-        # one colour pass: all of x (neighbours), b and the updated cells' x
-        # for 1/ncol of the cells, every coefficient an updated cell touches
-        # (its lower faces' rows and the upper faces' rows of its neighbours)
-        coef = ncomp * cb * N if stencil == 7 else (10 if axi else 18) * cb * N / ncol
-        base = vb * N + 2 * vb * N / ncol + coef
-        radial = 3 * vb * N / ncol          # radial-line factors of the updated cells
-        longitude = 4 * vb * N / ncol       # longitude-line factors (alpha, beta, gamma, psi2)
-        if smoother == 4:                   # as many radial as longitude passes: their mean
-            return base + (radial + longitude) / 2
-        return base + (radial if smoother == 2 else longitude if smoother == 3 else 0.0)
+        ncol = 4 if stencil == 19 else 2
+        if smoother == 1:
+            ncol = 1                        # weighted Jacobi: one pass per sweep
+        per = ncol if passes_per_sweep is None else passes_per_sweep
+        return sweep_bytes_per_cell(stencil, prec, smoother, axi, nc) * N / per
     if slot == "residual":
-        # x, b, the FP64 operator rows (7-point: the three face arrays and the
-        # stored centre; 19-point: the 19 assembled coefficients), FP32 r out
-        rows = 8 * (ncomp + 1) if stencil == 7 else 8 * (11 if axi else 19)
-        return N * (8 + 8 + rows + (0 if prec == 0 else 4))
+        # x64, b64, the FP64 face coefficients, the FP32 residual out
+        return N * (8 + 8 + 8 * nc + (0 if prec == 0 else 4))
     if slot == "restrict0":
-        return N * (2 * vb + ncomp * cb) + 2 * vb * n_next
+        # x, b, coefficients of every fine cell; the coarse right side out
+        return N * (2 * vb + nc * cb) + vb * n_next
     if slot == "prolong0":
         return 2 * vb * N + vb * n_next
     if slot == "update":
-        return 20 * N
-    if slot == "tail":
-        return float("nan")     # many small levels; no single per-launch byte count
-    raise KeyError(slot)
+        return 20 * N                       # e32 read, x64 read and written
+    return float("nan")                     # many small launches; no single per-launch count
 
 
 # ----------------------------------------------------------------- clocks
@@ -338,6 +354,139 @@ def time_solves(mgs, h, fd, xd, steps, flush, torch):
 
 
 TOL = 1e-10
+SLOT_NAMES = (("smooth0", 0), ("residual", 1), ("restrict0", 2), ("prolong0", 3), ("update", 4), ("tail", 5),
+              ("other", 6))
+
+
+def profile_solves(mgs, h, fd, xd, steps, flush, torch, stencil, prec, N, n_next, smoother, axi, one_pass):
+    """A separate profiled run of the same solves (every launch of the outer
+    iterations bracketed by events, so it runs a little slower than the
+    headline): device time per slot and per level, and the roofline of the
+    level-0 kernel with the largest device time."""
+    mgs.mg_profile_enable(h, True)
+    ms, _ = time_solves(mgs, h, fd, xd, steps, flush, torch)
+    slots = {name: mgs.mg_profile_read(h, slot) for name, slot in SLOT_NAMES}
+    levels = {}
+    for l in range(1, mgs.PROF_SLOTS - mgs.PROF_LEVEL_BASE):
+        t, n = mgs.mg_profile_read(h, mgs.PROF_LEVEL_BASE + l)
+        if n:
+            levels[l] = {"ms_per_solve": t / steps, "launches_per_solve": n / steps}
+    mgs.mg_profile_enable(h, False)
+    kernels = {}
+    for k, (t, n) in slots.items():
+        avg = t / max(n, 1)
+        ab = algorithmic_bytes(k, stencil, prec, N, n_next, smoother, axi,
+                               passes_per_sweep=1 if (k == "smooth0" and one_pass) else None)
+        kernels[k] = {"ms_per_solve": t / steps, "launches_per_solve": n / steps, "avg_ms": avg if n else None,
+                      "alg_GBps": ab / (avg * 1e-3) / 1e9 if n and ab == ab else None}
+    attributed = sum(v["ms_per_solve"] for v in kernels.values()) + sum(v["ms_per_solve"] for v in levels.values())
+    return {"profiled_ms_per_solve": statistics.mean(ms), "attributed_ms_per_solve": attributed,
+            "kernels": kernels, "levels": levels}, slots
+
+
+def roofline_of(name, slots, steps, stencil, prec, N, n_next, smoother, axi, one_pass, traffic):
+    tot_ms, nl = slots[name]
+    per_launch_ms = tot_ms / max(nl, 1)
+    pps = 1 if (name == "smooth0" and one_pass) else None
+    abytes = algorithmic_bytes(name, stencil, prec, N, n_next, smoother, axi, passes_per_sweep=pps)
+    peak, peak_kind = peaks()
+    achieved = abytes / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+            "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": per_launch_ms,
+            "cells": N, "sweep_bytes_per_cell": sweep_bytes_per_cell(stencil, prec, smoother, axi)
+            if name == "smooth0" else None,
+            "launches_per_sweep": (1 if one_pass else (1 if smoother == 1 else (4 if stencil == 19 else 2)))
+            if name == "smooth0" else None}
+    if stencil == 19 and axi:
+        # the survey's table counts nine coefficient arrays for 19 points
+        sb = algorithmic_bytes(name, stencil, prec, N, n_next, smoother, axi, passes_per_sweep=pps, ncomp=9)
+        roof["frac_nine_component_model"] = sb / (per_launch_ms * 1e-3) / 1e9 / peak
+    return roof
+
+
+def single_leg(args, mgs, torch, workload, scale, prec, smoother, steps, warmup, flush, traffic_key=None):
+    """Set-up, warm-up and `steps` timed solves (profiling off) of one single
+    workload, then a profiled run of the same solves for the kernel
+    breakdown.  Returns the leg's record, the handle and its device buffers."""
+    import workloads as W
+    w = W.single(workload, scale)
+    g, f = w["grid"], w["f"]
+    N = g["nr"] * g["nth"] * g["nph"]
+    sopts = dict(precision=prec, smoother=smoother)
+    if "max_levels" in w:
+        sopts["max_levels"] = w["max_levels"]
+    if w.get("coarsen") == "full":
+        sopts["coarsen"] = 1
+    t_setup = time.perf_counter()
+    h = mgs.mg_setup(g, sopts)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    fd = torch.from_numpy(f).cuda()
+    xd = torch.zeros_like(fd)
+    for _ in range(warmup):
+        xd.zero_()
+        mgs.mg_solve(h, fd, xd, tol=TOL)
+    torch.cuda.synchronize()
+    ms, reps = time_solves(mgs, h, fd, xd, steps, flush, torch)
+    rep = reps[-1]
+    info0 = mgs.mg_get_level_info(h, 0)
+    info1 = mgs.mg_get_level_info(h, 1) if info0["levels"] > 1 else info0
+    n_next = info1["nr"] * info1["nth"] * info1["nph"]
+    stencil = rep["stencil"]
+    axi = stencil == 19 and g["mapping"] != 2
+    sched = mgs.mg_get_schedule(h)
+    one_pass = bool(sched.get("one_pass_tiles", 0)) and smoother == 0
+    prof, slots = profile_solves(mgs, h, fd, xd, max(2, min(steps, 10)), flush, torch, stencil, prec, N, n_next,
+                                 smoother, axi, one_pass)
+    name = max(((k, v) for k, v in slots.items() if k in ("smooth0", "residual", "restrict0", "prolong0", "update")),
+               key=lambda kv: kv[1][0])[0]
+    pname = [k for k, v in PREC.items() if v == prec][0]
+    roof = roofline_of(name, slots, steps, stencil, prec, N, n_next, smoother, axi, one_pass,
+                       ncu_traffic(traffic_key or workload, pname, name))
+    roof["share_of_step"] = slots[name][0] / max(sum(v[0] for v in slots.values()), 1e-30)
+    leg = {"workload": workload if scale == 1 else f"{workload}/{scale}", "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
+           "value": N / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
+           "p99_ms": float(__import__("numpy").percentile(ms, 99)), "iters": rep["iters"], "rel_res": rep["rel_res"],
+           "levels": rep["levels"], "stencil": stencil, "setup_s": t_setup, "schedule": sched,
+           "roofline": roof, "profile": prof, "gpu_launches": int(sum(r["launches"] for r in reps)), "ms": ms}
+    return leg, h, g, f, fd, xd, rep
+
+
+def fp64_compare(args, mgs, torch, g, sopts, fd, xd, flush, world, ms_step, steps):
+    """Plain FP64 multigrid on the same workload: the speedup reference."""
+    N = g["nr"] * g["nth"] * g["nph"]
+    h64 = mgs.mg_setup(g, dict(sopts, precision=0))
+    xd.zero_()
+    mgs.mg_solve(h64, fd, xd, tol=TOL)
+    ms64, reps64 = time_solves(mgs, h64, fd, xd, steps, flush, torch)
+    v64 = world * N / (statistics.mean(ms64) / 1e3)
+    h64.close()
+    return {"value": v64, "ms_per_step": statistics.mean(ms64), "iters": reps64[-1]["iters"],
+            "speedup": statistics.mean(ms64) / ms_step}
+
+
+def c3_leg(args, mgs, torch, flush, world):
+    """The 256 x 256 x 512 oblate shell (19 points): FP32 cycles, FP16
+    coefficients, and plain FP64 multigrid, each to the bench tolerance."""
+    steps = max(3, min(args.steps, 8))
+    out = {}
+    for pname in ("fp32", "fp16"):
+        leg, h, g, f, fd, xd, rep = single_leg(args, mgs, torch, "single_oblate_256", 1, PREC[pname], 0, steps,
+                                               max(1, min(args.warmup, 2)), flush)
+        leg.pop("ms")
+        if pname == "fp32":
+            out.update(leg)
+            if not args.no_compare:
+                out["fp64_mg"] = fp64_compare(args, mgs, torch, g, dict(precision=0), fd, xd, flush, world,
+                                              leg["ms_per_step"], max(2, steps // 3))
+        else:
+            out["fp16_coefficients"] = {k: leg[k] for k in ("value", "ms_per_step", "iters", "rel_res", "roofline",
+                                                            "setup_s")}
+        h.close()
+        del fd, xd
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -352,31 +501,33 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
+    prec = PREC[args.precision]
+    smoother = SMOOTHER[args.smoother]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     w = W.single(args.workload, args.scale)
     g, f = w["grid"], w["f"]
     N = g["nr"] * g["nth"] * g["nph"]
-    prec = PREC[args.precision]
-    sopts = dict(precision=prec, smoother=SMOOTHER[args.smoother])
+    sopts = dict(precision=prec, smoother=smoother)
     if "max_levels" in w:
         sopts["max_levels"] = w["max_levels"]
     if w.get("coarsen") == "full":
         sopts["coarsen"] = 1
     t_setup = time.perf_counter()
     h = mgs.mg_setup(g, sopts)
+    torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     fd = torch.from_numpy(f).cuda()
     xd = torch.zeros_like(fd)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         xd.zero_()
         mgs.mg_solve(h, fd, xd, tol=TOL)
 
+    # the headline: timed with profiling off
     clocks = Clocks(local_rank)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    mgs.mg_profile_enable(h, True)
     t0 = time.perf_counter()
     ms, reps = time_solves(mgs, h, fd, xd, args.steps, flush, torch)
     torch.cuda.synchronize()
@@ -384,36 +535,25 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    prof = {name: mgs.mg_profile_read(h, slot) for name, slot in
-            (("smooth0", mgs.PROF_SMOOTH0), ("residual", mgs.PROF_RESIDUAL),
-             ("restrict0", mgs.PROF_RESTRICT0), ("prolong0", mgs.PROF_PROLONG0),
-             ("update", mgs.PROF_UPDATE), ("tail", mgs.PROF_TAIL))}
-    mgs.mg_profile_enable(h, False)
     ms_step = max_over_ranks(statistics.mean(ms))
     rep = reps[-1]
     info0 = mgs.mg_get_level_info(h, 0)
     info1 = mgs.mg_get_level_info(h, 1) if info0["levels"] > 1 else info0
     n_next = info1["nr"] * info1["nth"] * info1["nph"]
     stencil = rep["stencil"]
-
-    # roofline of the dominant kernel (largest device time in the timed region)
-    name, (tot_ms, nl) = max(((k, v) for k, v in prof.items() if k != "tail"), key=lambda kv: kv[1][0])
-    per_launch_ms = tot_ms / max(nl, 1)
     axi = stencil == 19 and g["mapping"] != 2
-    abytes = algorithmic_bytes(name, stencil, prec, N, n_next, sopts["smoother"], axi)
-    peak, peak_kind = peaks()
-    achieved = abytes / (per_launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind,
-            "traffic": ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
-                                   args.precision, name),
-            "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": per_launch_ms,
-            "share_of_step": tot_ms / sum(ms)}
-    kernels = {k: {"ms_total": v[0], "launches": v[1],
-                   "avg_ms": v[0] / max(v[1], 1),
-                   "alg_GBps": algorithmic_bytes(k, stencil, prec, N, n_next, sopts["smoother"], axi) /
-                   (v[0] / max(v[1], 1) * 1e-3) / 1e9
-                   if v[1] and k != "tail" else None} for k, v in prof.items()}
+    sched = mgs.mg_get_schedule(h)
+    one_pass = bool(sched.get("one_pass_tiles", 0)) and smoother == 0
+
+    # kernel breakdown: a separate profiled run of the same solves
+    prof, slots = profile_solves(mgs, h, fd, xd, max(2, min(args.steps, 10)), flush, torch, stencil, prec, N,
+                                 n_next, smoother, axi, one_pass)
+    name = max(((k, v) for k, v in slots.items() if k in ("smooth0", "residual", "restrict0", "prolong0", "update")),
+               key=lambda kv: kv[1][0])[0]
+    roof = roofline_of(name, slots, args.steps, stencil, prec, N, n_next, smoother, axi, one_pass,
+                       ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
+                                   args.precision, name))
+    roof["share_of_step"] = slots[name][0] / max(sum(v[0] for v in slots.values()), 1e-30)
 
     # end to end through the public host-buffer call (pinned host memory)
     fh = torch.from_numpy(f.copy()).pin_memory()
@@ -515,15 +655,16 @@ def run_ours(args, rank, world, local_rank):
     # plain FP64 multigrid on the same workload (the speedup reference)
     compare = None
     if not args.no_compare and prec != 0:
-        h64 = mgs.mg_setup(g, dict(sopts, precision=0))
-        for _ in range(1):
-            xd.zero_()
-            mgs.mg_solve(h64, fd, xd, tol=TOL)
-        ms64, reps64 = time_solves(mgs, h64, fd, xd, max(3, args.steps // 3), flush, torch)
-        v64 = world * N / (statistics.mean(ms64) / 1e3)
-        compare = {"value": v64, "ms_per_step": statistics.mean(ms64), "iters": reps64[-1]["iters"],
-                   "speedup": (world * N / (ms_step / 1e3)) / v64}
-        h64.close()
+        compare = fp64_compare(args, mgs, torch, g, sopts, fd, xd, flush, world, ms_step, max(3, args.steps // 3))
+    h.close()
+    del fd, xd
+    torch.cuda.empty_cache()
+
+    # the 19-point oblate shell (C3) in the same line, when the headline is the
+    # default workload
+    c3 = None
+    if world == 1 and args.workload == "single_sphere_128" and args.scale == 1 and not args.no_c3:
+        c3 = c3_leg(args, mgs, torch, flush, world)
 
     if rank != 0:
         return
@@ -534,12 +675,12 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
         "config": config_of(args, g, rep, stencil),
         "rel_res": rep["rel_res"], "iters": rep["iters"],
-        "roofline": roof, "kernels": kernels,
-        "setup_s": t_setup, "schedule": mgs.mg_get_schedule(h), "pc_step": pc_step,
+        "roofline": roof, "profile": prof,
+        "setup_s": t_setup, "schedule": sched, "pc_step": pc_step,
         "line_solves": line_solves, "adi_substep": adi_step,
         "e2e": e2e,
         "gpu_launches": int(sum(r["launches"] for r in reps)),
-        "clocks": clk, "fp64_mg": compare, "wall_s": wall,
+        "clocks": clk, "fp64_mg": compare, "wall_s": wall, "c3": c3,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, TOL, kind=sopts["smoother"])

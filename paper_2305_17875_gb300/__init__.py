@@ -420,7 +420,8 @@ def mg_get_schedule(h: Handle) -> dict:
     return {k: getattr(sc, k) for k, _ in mg_schedule._fields_}
 
 
-PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL = range(6)
+PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL, PROF_OTHER = range(7)
+PROF_LEVEL_BASE, PROF_SLOTS = 8, 24   # slot PROF_LEVEL_BASE + l: level l's operations (1 <= l < 16)
 
 
 def mg_profile_enable(h: Handle, on: bool = True):

@@ -61,6 +61,7 @@ struct Launch {
     int stencil = 0;               // stencil shared by the tasks of stencil operations
     int t0 = 0, nt = 0, total = 0;
     int prof = -1, prof_n = 0;     // profiling slot around this launch
+    int level = -1;                // level of a level operation (timing attribution)
     int tail_stencil = 0;          // >0: a coarse-tail launch of this stencil
 };
 
@@ -151,7 +152,7 @@ bool fused_level(const mg_handle* h, int level) {
     return h->fused_rb && h->stencil == 7 && h->opts.smoother == MG_SMOOTH_GS && rb7_fits(h->L[level].D);
 }
 
-void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
+void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
     const int prec = pl->prec;
     int maxc = 0, maxl = 0, maxx = 0;
     bool any_jacobi = false, any_fused = false;
@@ -303,6 +304,12 @@ void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
     }
 }
 
+void add_smooth(Program& P, Plan* pl, int level, int sweeps) {
+    const size_t first_launch = P.launches.size();
+    add_smooth_launches(P, pl, level, sweeps);
+    for (size_t i = first_launch; i < P.launches.size(); ++i) P.launches[i].level = level;
+}
+
 // Outer FP64 residual and its norm for every shell.
 void add_residual(Program& P, Plan* pl) {
     for (int st : {7, 19}) {
@@ -359,6 +366,7 @@ void build_iteration(Plan* pl) {
         add_smooth(P, pl, l, pl->hs[0]->opts.nu1);
         for (int st : {7, 19}) {
         Launch& L = P.begin(BOP_RESTRICT, 0, st);
+        L.level = l;
         if (l == 0) {
             L.prof = MG_PROF_RESTRICT0;
             L.prof_n = 1;
@@ -413,6 +421,7 @@ void build_iteration(Plan* pl) {
     // up leg
     for (int l = depth - 1; l >= 0; --l) {
         Launch& L = P.begin(BOP_PROLONG);
+        L.level = l;
         if (l == 0) {
             L.prof = MG_PROF_PROLONG0;
             L.prof_n = 1;
@@ -450,7 +459,12 @@ void build_iteration(Plan* pl) {
 mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const int* active) {
     mg_handle* h0 = lead(pl);
     for (const Launch& L : P.launches) {
-        if (L.prof >= 0) prof_begin(h0, L.prof);
+        // every launch is timed in some slot: the named fine-level ones, the
+        // coarser levels' operations by level, the rest together
+        const int slot = L.prof >= 0   ? L.prof
+                         : L.level > 0 ? MG_PROF_LEVEL_BASE + std::min(L.level, MG_PROF_SLOTS - 1 - MG_PROF_LEVEL_BASE)
+                                       : MG_PROF_OTHER;
+        prof_begin(h0, slot);
         if (L.tail_stencil) {
             int first = 0, n = 0;
             for (size_t i = 0; i < P.tails.size(); ++i) {
@@ -464,7 +478,7 @@ mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const in
             CK(launch_batch(d_tasks + L.t0, L.nt, L.total, active, L.op, L.colour, L.stencil, pl->prec,
                             pl->stream));
         }
-        if (L.prof >= 0) prof_end(h0, L.prof, L.prof_n);
+        prof_end(h0, slot, L.prof >= 0 ? L.prof_n : 1);
         h0->launches += 1;
     }
     return MG_OK;

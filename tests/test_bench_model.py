@@ -1,6 +1,8 @@
 """Host logic of bench.py: the algorithmic byte model behind the roofline
-fraction (each array a launch needs moved once), checked against the counts
-written out by hand, and the half-size traffic scaling."""
+fraction, checked against the survey's per-sweep table written out by hand
+(a whole smoothing sweep moves x twice, b once and every stored coefficient
+array once; a colour pass is charged 1/C of a sweep), and the half-size
+traffic scaling."""
 import json
 import os
 
@@ -12,36 +14,47 @@ N2 = 128 * 128 * 256          # the 128 x 128 x 256 bench grid
 N2C = 64 * 128 * 256          # its first coarse level (radius halved)
 
 
-def test_seven_point_colour_pass_bytes():
-    # x read (4 B) + b and x of the updated half (2 x 4 B / 2) + three G arrays (12 B)
-    assert bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C) == pytest.approx(N2 * (4 + 4 + 12))
-    assert bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C) == pytest.approx(83.886080e6)
+def test_sweep_bytes_follow_the_table():
+    # x read + written, b read, coefficients: 7 points FP32 4+4+4+12
+    assert bench.sweep_bytes_per_cell(7, 1) == 24
+    assert bench.sweep_bytes_per_cell(19, 1, ncomp=9) == 48        # 4+4+4+36
+    assert bench.sweep_bytes_per_cell(19, 2, ncomp=9) == 30        # FP16 coefficients 4+4+4+18
+    assert bench.sweep_bytes_per_cell(7, 0) == 48                  # FP64
+    assert bench.sweep_bytes_per_cell(19, 0, ncomp=9) == 96
+    # the axisymmetric operator stores five arrays
+    assert bench.sweep_bytes_per_cell(19, 1, axi=True) == 32
+    assert bench.sweep_bytes_per_cell(19, 2, axi=True) == 22
 
 
-def test_nineteen_point_colour_pass_bytes():
-    # 18 coefficients of the updated quarter, or 10 with the axisymmetric operator
-    full = bench.algorithmic_bytes("smooth0", 19, 1, N2, N2C)
-    axi = bench.algorithmic_bytes("smooth0", 19, 1, N2, N2C, axi=True)
-    assert full == pytest.approx(N2 * (4 + 2 + 18))
-    assert axi == pytest.approx(N2 * (4 + 2 + 10))
+def test_colour_pass_is_a_fraction_of_the_sweep():
+    # 7 points: two colour passes per sweep, 12 B per cell each
+    assert bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C) == pytest.approx(12 * N2)
+    assert bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C) == pytest.approx(50.331648e6)
+    # a one-pass sweep is charged the whole sweep
+    assert bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C, passes_per_sweep=1) == pytest.approx(24 * N2)
+    # 19 points: four colour passes
+    assert bench.algorithmic_bytes("smooth0", 19, 1, N2, N2C) == pytest.approx(12 * N2)
+    assert bench.algorithmic_bytes("smooth0", 19, 1, N2, N2C, axi=True) == pytest.approx(8 * N2)
+    assert bench.algorithmic_bytes("smooth0", 19, 2, N2, N2C, axi=True) == pytest.approx(5.5 * N2)
 
 
-def test_line_pass_adds_the_factors_of_the_updated_cells():
+def test_line_pass_adds_the_factors():
     base = bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C)
     line = bench.algorithmic_bytes("smooth0", 7, 1, N2, N2C, smoother=2)
     assert line - base == pytest.approx(3 * 4 * N2 / 2)
 
 
 def test_outer_residual_bytes():
-    # x 8 + b 8 + FP64 rows + r32 4: 7-point rows = 3 faces + centre
-    assert bench.algorithmic_bytes("residual", 7, 1, N2, N2C) == pytest.approx(N2 * (8 + 8 + 32 + 4))
-    assert bench.algorithmic_bytes("residual", 19, 1, N2, N2C) == pytest.approx(N2 * (8 + 8 + 152 + 4))
-    assert bench.algorithmic_bytes("residual", 19, 1, N2, N2C, axi=True) == pytest.approx(N2 * (8 + 8 + 88 + 4))
-    assert bench.algorithmic_bytes("residual", 7, 0, N2, N2C) == pytest.approx(N2 * (8 + 8 + 32))
+    # x64 8 + b64 8 + FP64 coefficients + r32 4
+    assert bench.algorithmic_bytes("residual", 7, 1, N2, N2C) == pytest.approx(N2 * (8 + 8 + 24 + 4))
+    assert bench.algorithmic_bytes("residual", 19, 1, N2, N2C) == pytest.approx(N2 * (8 + 8 + 72 + 4))
+    assert bench.algorithmic_bytes("residual", 19, 1, N2, N2C, axi=True) == pytest.approx(N2 * (8 + 8 + 40 + 4))
+    assert bench.algorithmic_bytes("residual", 7, 0, N2, N2C) == pytest.approx(N2 * (8 + 8 + 24))
 
 
 def test_transfer_and_update_bytes():
-    assert bench.algorithmic_bytes("restrict0", 7, 1, N2, N2C) == pytest.approx(N2 * (8 + 12) + 8 * N2C)
+    # residual + restriction: x, b, coefficients, coarse right side (20.5 B per fine cell at FP32)
+    assert bench.algorithmic_bytes("restrict0", 7, 1, N2, N2C) == pytest.approx(N2 * (8 + 12) + 4 * N2C)
     assert bench.algorithmic_bytes("prolong0", 7, 1, N2, N2C) == pytest.approx(8 * N2 + 4 * N2C)
     assert bench.algorithmic_bytes("update", 7, 1, N2, N2C) == pytest.approx(20 * N2)
 
