@@ -299,13 +299,21 @@ typedef struct {
     int blocks_per_sm;      /* cap of the level kernels' virtual grids, in blocks of 256 per SM */
     int tail_level;         /* first level of the single-launch coarse tail, 0 = none */
     int tail_cluster;       /* CTAs per tail cluster */
-    int one_pass_tiles;     /* 1: 7-point red-black sweeps as one-pass tiles where they fit */
+    int one_pass_tiles;     /* 1: Gauss-Seidel sweeps as one launch per sweep (all colours,
+                               shared-memory plane tiles) on every level a tile fits */
     int source;             /* 0 default, 1 tuned at this set-up, 2 from the process cache,
-                               3 forced by MG_TAIL / MG_FUSED_RB / MG_VB_CAP in the
-                               environment (MG_VB_CAP = blocks per SM) */
+                               3 forced by MG_TAIL / MG_FUSED_RB / MG_VB_CAP / MG_TILE in the
+                               environment (MG_VB_CAP = blocks per SM; MG_TILE = "cells,planes,kmax[,min_cells]";
+                               MG_FUSED_RB alone sweeps every level a tile fits in one pass) */
     int candidates;         /* schedules timed (source 1) */
     double ms_per_iteration;/* device time of one outer iteration under the chosen schedule
                                (source 1 and 2; 0 otherwise) */
+    int tile_cells;         /* one-pass tiles: target cells per plane (colatitude rows x longitudes) */
+    int tile_planes;        /* one-pass tiles: radius planes per chunk (0: chosen per level) */
+    int tile_kmax;          /* one-pass tiles: widest tile in longitudes (whole rows up to it) */
+    long long tile_min_cells; /* one-pass tiles: levels with fewer cells keep the colour passes */
+    int tile0[3];           /* the fine level's tile (colatitude rows, radius planes, longitudes);
+                               zeros when the fine level is swept by colour passes */
 } mg_schedule;
 mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out);
 

@@ -58,7 +58,8 @@ class mg_walls(C.Structure):
 class mg_schedule(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("tail_level", C.c_int), ("tail_cluster", C.c_int),
                 ("one_pass_tiles", C.c_int), ("source", C.c_int), ("candidates", C.c_int),
-                ("ms_per_iteration", C.c_double)]
+                ("ms_per_iteration", C.c_double), ("tile_cells", C.c_int), ("tile_planes", C.c_int),
+                ("tile_kmax", C.c_int), ("tile_min_cells", C.c_longlong), ("tile0", C.c_int * 3)]
 
 
 class mg_report(C.Structure):
@@ -417,7 +418,9 @@ def mg_adi_substep(h: Handle, kappa, un, u, src=None, walls=None):
 def mg_get_schedule(h: Handle) -> dict:
     sc = mg_schedule()
     _check(_lib.mg_get_schedule(h.ptr, C.byref(sc)), "mg_get_schedule")
-    return {k: getattr(sc, k) for k, _ in mg_schedule._fields_}
+    out = {k: getattr(sc, k) for k, _ in mg_schedule._fields_}
+    out["tile0"] = list(sc.tile0)
+    return out
 
 
 PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL, PROF_OTHER = range(7)

@@ -777,154 +777,6 @@ __global__ void __launch_bounds__(kBT, min_ctas<P, OP, S>()) k_batch(const BTask
 }
 
 
-// ---- one red-black sweep of the 7-point operator per launch (overlapped tiles)
-//
-// A CTA owns a tile of kRbJ x kRbI x kRbK cells.  It stages the old iterate on
-// the tile plus a 2-cell ring in shared memory, updates the red cells of the
-// tile plus a 1-cell ring in place (red cells read only black neighbours),
-// then the black cells of the tile in place (they read only red neighbours,
-// now new), and writes the tile to the output array.  The ring work is
-// repeated by the neighbouring tiles; the input array is never written, so
-// the result is the sequential sweep "all red, then all black".
-// Ring entries outside the radial / colatitude walls are clamped copies that
-// only ever meet zero wall coefficients; longitude wraps.
-constexpr int kRgJ = kRbJ + 4, kRgI = kRbI + 4, kRgK = kRbK + 4;
-constexpr int kRB7 = 512;   // threads per tile
-
-template <typename T, typename CF>
-struct Faces7b {
-    T el, eu, zl, zu, xl, xu;
-    __device__ __forceinline__ void load(const CF& cf, const Dims& D, int j, int i, int k) {
-        const int c = cidx(D, j, i, k);
-        const int plane = D.nth * D.nph;
-        el = (T)cf(4, c);
-        eu = j + 1 < D.nr ? (T)cf(4, c + plane) : (T)0;
-        zl = (T)cf(0, c);
-        zu = i + 1 < D.nth ? (T)cf(0, c + D.nph) : (T)0;
-        xl = (T)cf(8, c);
-        xu = (T)cf(8, c - k + (k + 1 == D.nph ? 0 : k + 1));
-    }
-    // x_c + (b - A x)_c / A_cc from the six neighbour values
-    __device__ __forceinline__ T update(T b, T xc, T xel, T xeu, T xzl, T xzu, T xxl, T xxu) const {
-        const T ax = ax7(xc, xel, xeu, xzl, xzu, xxl, xxu, el, eu, zl, zu, xl, xu);
-        const T dg = -(el + eu + zl + zu + xl + xu);
-        return xc + (b - ax) / dg;
-    }
-};
-
-__device__ __forceinline__ int wrap_k(const Dims& D, int k) {   // k >= -nph
-    const int kp = k + D.nph;
-    return kp - D.nph * (int)D.dph.div((unsigned)kp);
-}
-__device__ __forceinline__ int clamp_to(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
-
-template <typename T, typename CF>
-__device__ void rb7_tile(const BTask& tk, const CF& cf, int lb, T* sx) {
-    const Dims& D = tk.v.D;
-    const int ntk = (D.nph + kRbK - 1) / kRbK, nti = (D.nth + kRbI - 1) / kRbI;
-    const int tkk = lb % ntk, tii = (lb / ntk) % nti, tjj = lb / (ntk * nti);
-    const int j0 = tjj * kRbJ, i0 = tii * kRbI, k0 = tkk * kRbK;
-    const T* __restrict__ x = (const T*)tk.x;
-    const T* __restrict__ b = (const T*)tk.b;
-    T* __restrict__ out = (T*)tk.y;
-    auto S = [&](int jj, int ii, int kk) -> T& { return sx[(jj * kRgI + ii) * kRgK + kk]; };
-
-    // 1. old iterate on tile + 2-cell ring, copied asynchronously (all issued, then one wait)
-    for (int w = threadIdx.x; w < kRgJ * kRgI * kRgK; w += kRB7) {
-        const int jj = w / (kRgI * kRgK), rem = w - jj * (kRgI * kRgK);
-        const int ii = rem / kRgK, kk = rem - ii * kRgK;
-        const int j = clamp_to(j0 - 2 + jj, D.nr), i = clamp_to(i0 - 2 + ii, D.nth);
-        const int k = wrap_k(D, k0 - 2 + kk);
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(sx + w);
-        const T* g = x + cidx(D, j, i, k);
-        if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g));
-        else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g));
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-
-    // 2. red cells ((i + j + k) even) of tile + 1-cell ring, in place
-    constexpr int NJ = kRbJ + 2, NI = kRbI + 2, NK2 = (kRbK + 2) / 2;
-#pragma unroll 2
-    for (int w = threadIdx.x; w < NJ * NI * NK2; w += kRB7) {
-        const int jj = w / (NI * NK2), rem = w - jj * (NI * NK2);
-        const int ii = rem / NK2, m = rem - ii * NK2;
-        const int j = j0 - 1 + jj, i = i0 - 1 + ii;
-        if (j < 0 || j >= D.nr || i < 0 || i >= D.nth) continue;
-        const int kk = 2 * m + ((j + i + k0 - 1) & 1);        // first red in the row
-        const int kw = wrap_k(D, k0 - 1 + kk);
-        Faces7b<T, CF> F;
-        F.load(cf, D, j, i, kw);
-        const int a = jj + 1, c = ii + 1, e = kk + 1;         // region coordinates
-        S(a, c, e) = F.update(b[cidx(D, j, i, kw)], S(a, c, e), S(a - 1, c, e), S(a + 1, c, e), S(a, c - 1, e),
-                              S(a, c + 1, e), S(a, c, e - 1), S(a, c, e + 1));
-    }
-    __syncthreads();
-
-    // 3. black cells of the tile, in place
-    constexpr int BK2 = kRbK / 2;
-#pragma unroll 2
-    for (int w = threadIdx.x; w < kRbJ * kRbI * BK2; w += kRB7) {
-        const int jj = w / (kRbI * BK2), rem = w - jj * (kRbI * BK2);
-        const int ii = rem / BK2, m = rem - ii * BK2;
-        const int j = j0 + jj, i = i0 + ii;
-        const int kk = 2 * m + (((j + i + k0) & 1) ^ 1);      // first black in the row
-        const int k = k0 + kk;
-        if (j >= D.nr || i >= D.nth || k >= D.nph) continue;
-        Faces7b<T, CF> F;
-        F.load(cf, D, j, i, k);
-        const int a = jj + 2, c = ii + 2, e = kk + 2;
-        S(a, c, e) = F.update(b[cidx(D, j, i, k)], S(a, c, e), S(a - 1, c, e), S(a + 1, c, e), S(a, c - 1, e),
-                              S(a, c + 1, e), S(a, c, e - 1), S(a, c, e + 1));
-    }
-    __syncthreads();
-
-    // 4. the tile out, coalesced along longitude
-#pragma unroll 4
-    for (int w = threadIdx.x; w < kRbJ * kRbI * kRbK; w += kRB7) {
-        const int jj = w / (kRbI * kRbK), rem = w - jj * (kRbI * kRbK);
-        const int ii = rem / kRbK, kk = rem - ii * kRbK;
-        const int j = j0 + jj, i = i0 + ii, k = k0 + kk;
-        if (j >= D.nr || i >= D.nth || k >= D.nph) continue;
-        out[cidx(D, j, i, k)] = S(jj + 2, ii + 2, kk + 2);
-    }
-}
-
-template <int P>
-__global__ void __launch_bounds__(kRB7) k_rb7(const BTask* __restrict__ tasks, int ntasks, int total,
-                                              const int* __restrict__ active, int early_trigger) {
-    typedef typename Prec<P>::T T;
-    extern __shared__ __align__(16) unsigned char dyn[];
-    T* sx = reinterpret_cast<T*>(dyn);
-    __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];
-    __shared__ int tk_index;
-    const BTask& tk = *reinterpret_cast<const BTask*>(tk_raw);
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    if (early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = ntasks - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(&tasks[mid].block0) <= vb) lo = mid;
-                else hi = mid - 1;
-            }
-            tk_index = lo;
-        }
-        __syncthreads();
-        {
-            const unsigned* src = reinterpret_cast<const unsigned*>(tasks + tk_index);
-            unsigned* dst = reinterpret_cast<unsigned*>(tk_raw);
-            for (int w = threadIdx.x; w < (int)(sizeof(BTask) / 4); w += kRB7) dst[w] = __ldg(src + w);
-        }
-        __syncthreads();
-        if (!active || active[tk.shell]) rb7_tile<T>(tk, Prec<P>::cf(tk.v), vb - tk.block0, sx);
-        __syncthreads();
-    }
-    if (!early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-
 // Self-check of narrow_rn and scaled_widen against the hardware conversions on
 // a million bit patterns: splitmix64 draws with exponents around the FP32
 // range (normal, subnormal and overflowing results), rounding ties of both
@@ -1017,30 +869,6 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
 #undef PLAIN_OP
 }
 
-template <int P>
-static cudaError_t rb7_launch(const BTask* tasks, int ntasks, int total, const int* active, cudaStream_t s) {
-    typedef typename Prec<P>::T T;
-    const size_t smem = sizeof(T) * kRgJ * kRgI * kRgK;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_rb7<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int early = total <= 152 * 2 ? 1 : 0;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(total, 1, 1);
-    cfg.blockDim = dim3(kRB7, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attrs[1];
-    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attrs[0].val.programmaticStreamSerializationAllowed = use_pdl() ? 1 : 0;
-    cfg.attrs = attrs;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_rb7<P>, tasks, ntasks, total, active, early);
-}
-
 cudaError_t launch_convert_check(unsigned* bad, cudaStream_t s) {
     k_convert_check<<<512, 256, 0, s>>>(1 << 20, bad);
     return cudaGetLastError();
@@ -1050,13 +878,6 @@ cudaError_t launch_batch(const BTask* tasks, int ntasks, int total_blocks, const
                          int stencil, int prec, cudaStream_t s) {
     if (ntasks <= 0 || total_blocks <= 0) return cudaSuccess;
     cudaError_t e;
-    if (op == BOP_RB7) {
-        if (prec == PREC64) e = rb7_launch<PREC64>(tasks, ntasks, total_blocks, active, s);
-        else if (prec == PREC32) e = rb7_launch<PREC32>(tasks, ntasks, total_blocks, active, s);
-        else e = rb7_launch<PREC16>(tasks, ntasks, total_blocks, active, s);
-        if (e != cudaSuccess) return e;
-        return cudaGetLastError();
-    }
     if (prec == PREC64) e = batch_dispatch<PREC64>(tasks, ntasks, total_blocks, active, op, colour, stencil, s);
     else if (prec == PREC32) e = batch_dispatch<PREC32>(tasks, ntasks, total_blocks, active, op, colour, stencil, s);
     else e = batch_dispatch<PREC16>(tasks, ntasks, total_blocks, active, op, colour, stencil, s);

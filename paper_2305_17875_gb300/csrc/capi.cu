@@ -391,7 +391,11 @@ mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
 struct Schedule {
     int vb_cap = 16;
     i64 tail_cells = 0;
-    bool fused = false;
+    bool fused = false;       // one-pass sweeps
+    int tile_cells = 2048;    // one-pass tiles: target cells per plane
+    int tile_tj = 0;          // one-pass tiles: planes per chunk (0: per level)
+    int tile_kmax = 256;      // one-pass tiles: widest tile in longitudes
+    i64 tile_min = 1 << 20;   // one-pass tiles: smallest level (cells) swept in one pass
 };
 
 std::string shape_key(const mg_handle* h) {
@@ -403,16 +407,31 @@ std::string shape_key(const mg_handle* h) {
     return k;
 }
 
-bool can_fuse(const mg_handle* h) {
-    if (h->stencil != 7 || h->opts.smoother != MG_SMOOTH_GS) return false;
-    for (const Level& lv : h->L)
-        if (rb7_fits(lv.D)) return true;
-    return false;
+void set_tiles(mg_handle* h, bool on, int cells, int tj, int kmax, i64 min_cells) {
+    h->one_pass = on;
+    h->sweep_cells = cells;
+    h->sweep_tj = tj;
+    h->sweep_kmax = kmax;
+    h->sweep_min_cells = min_cells;
+}
+
+// One-pass sweeps apply to Gauss-Seidel handles with a level a tile fits.
+bool can_fuse(mg_handle* h, const Schedule& sc) {
+    if (h->opts.smoother != MG_SMOOTH_GS) return false;
+    const bool was = h->one_pass;
+    const int c = h->sweep_cells, tj = h->sweep_tj, km = h->sweep_kmax;
+    const i64 mc = h->sweep_min_cells;
+    set_tiles(h, true, sc.tile_cells, sc.tile_tj, sc.tile_kmax, sc.tile_min);
+    bool any = false;
+    int tile[3];
+    for (int l = 0; l < (int)h->L.size() && !any; ++l) any = sweep_tile_for(h, l, tile);
+    set_tiles(h, was, c, tj, km, mc);
+    return any;
 }
 
 mg_status apply_schedule(mg_handle* h, const Schedule& sc) {
     h->vb_cap = sc.vb_cap;
-    h->fused_rb = sc.fused && can_fuse(h);
+    set_tiles(h, sc.fused && can_fuse(h, sc), sc.tile_cells, sc.tile_tj, sc.tile_kmax, sc.tile_min);
     return configure_tail(h, sc.tail_cells, 8);
 }
 
@@ -478,10 +497,31 @@ mg_status autotune(mg_handle* h) {
         sc.tail_cells = 16384;
         CKS(consider(sc));
     }
-    if (can_fuse(h)) {
-        Schedule sc = best;
-        sc.fused = true;
-        CKS(consider(sc));
+    {   // one-pass sweeps on the large levels: two plane areas, then the
+        // chunk depth, the smallest level swept in one pass and the tile width
+        for (int cells : {2048, 3072}) {
+            Schedule sc = best;
+            sc.fused = true;
+            sc.tile_cells = cells;
+            if (can_fuse(h, sc)) CKS(consider(sc));
+        }
+        if (best.fused) {
+            for (int tj : {8, 32}) {
+                Schedule t = best;
+                t.tile_tj = tj;
+                CKS(consider(t));
+            }
+            for (i64 mc : {(i64)1 << 18, (i64)1 << 22}) {
+                Schedule t = best;
+                t.tile_min = mc;
+                if (can_fuse(h, t)) CKS(consider(t));
+            }
+            if (h->stencil == 7) {
+                Schedule t = best;
+                t.tile_kmax = 128;
+                CKS(consider(t));
+            }
+        }
     }
     CKS(apply_schedule(h, best));
     h->sched_source = 1;
@@ -501,7 +541,17 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     h->prec = o->precision;
     h->user_stream = stream;
     h->use_graph = std::getenv("MG_NO_GRAPH") == nullptr;
-    h->fused_rb = std::getenv("MG_FUSED_RB") != nullptr;   // one-pass tile sweeps: forced
+    h->one_pass = std::getenv("MG_FUSED_RB") != nullptr;   // one-pass sweeps: forced
+    if (h->one_pass) h->sweep_min_cells = 0;   // forced: every level a tile fits
+    if (const char* v = std::getenv("MG_TILE")) {   // "cells,planes,kmax[,min_cells]"
+        int c = 2048, tj = 0, km = 256;
+        long long mc = h->sweep_min_cells;
+        std::sscanf(v, "%d,%d,%d,%lld", &c, &tj, &km, &mc);
+        h->sweep_cells = std::max(1, c);
+        h->sweep_tj = std::max(0, tj);
+        h->sweep_kmax = std::max(4, km);
+        h->sweep_min_cells = std::max(0LL, mc);
+    }
     CK(cudaGetDevice(&h->device));
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
@@ -560,6 +610,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     if (!(h->part = (double*)dalloc(h, sizeof(double) * kRedBlocks))) return MG_ENOMEM;
     if (!(h->scal = (double*)dalloc(h, sizeof(double) * SC_COUNT))) return MG_ENOMEM;
     if (!(h->one_task = (BTask*)dalloc(h, sizeof(BTask)))) return MG_ENOMEM;
+    if (!(h->one_map = dalloc(h, 128))) return MG_ENOMEM;
     if (o->metric == MG_METRIC_ANALYTIC) {
         // exact derivatives at the face centres: tables at half-index resolution
         std::vector<double> ar(2 * nr + 1), adr(2 * nr + 1), act(2 * nth + 1), ast(2 * nth + 1),
@@ -715,7 +766,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     CK(cudaGetLastError());
 
     // --- launch schedule: forced by the environment, tuned, or the default
-    const bool env_sched = std::getenv("MG_TAIL") || std::getenv("MG_FUSED_RB") || std::getenv("MG_VB_CAP");
+    const bool env_sched =
+        std::getenv("MG_TAIL") || std::getenv("MG_FUSED_RB") || std::getenv("MG_VB_CAP") || std::getenv("MG_TILE");
     if (env_sched) {
         h->sched_source = 3;
         if (const char* v = std::getenv("MG_VB_CAP")) h->vb_cap = std::max(1, std::min(64, std::atoi(v)));
@@ -825,14 +877,47 @@ void prof_collect(mg_handle* h) {
     h->prof_pending.clear();
 }
 
+bool sweep_tile_for(const mg_handle* h, int level, int tile[3]) {
+    if (!h->one_pass || h->opts.smoother != MG_SMOOTH_GS || level < 0 || level >= (int)h->L.size()) return false;
+    const Dims& D = h->L[level].D;
+    if (D.n() < h->sweep_min_cells) return false;
+    // longitudes: whole rows up to the widest tile, else the largest
+    // power-of-two divisor of nph up to 128
+    // (19 points: at most 128, the buffers hold four halo rows either side)
+    const int kmax = h->stencil == 19 ? std::min(h->sweep_kmax, 128) : h->sweep_kmax;
+    int tk = D.nph;
+    if (tk > kmax) {
+        tk = 0;
+        for (int c = 128; c >= 8 && !tk; c >>= 1)
+            if (D.nph % c == 0 && c <= kmax) tk = c;
+        if (!tk) return false;
+    }
+    // rows: the plane area, at least four rows (the halo is 2 or 4 rows)
+    const int ti = std::max(4, std::min(D.nth, h->sweep_cells / tk));
+    int tj = h->sweep_tj;
+    if (tj <= 0) {   // deep chunks, while the level still has two tiles per SM
+        tj = 32;
+        for (;;) {
+            const int t3[3] = {ti, tj, tk};
+            if (tj <= 4 || sweep_units(D, t3) >= 2 * 152) break;
+            tj >>= 1;
+        }
+    }
+    tile[0] = ti;
+    tile[1] = tj;
+    tile[2] = tk;
+    return sweep_tile_ok(D, h->stencil, h->prec, tile);
+}
+
 mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
     Level& lv = h->L[level];
     const LevelView v = lv.view(h->stencil);
     if (sweeps == 0) return MG_OK;
     if (level == 0) prof_begin(h, MG_PROF_SMOOTH0);
     int n = 0;
-    if (kind == MG_SMOOTH_GS && h->fused_rb && h->stencil == 7 && rb7_fits(lv.D)) {
-        // one-pass red-black sweeps ping-pong between x and the level's scratch
+    int tile[3];
+    if (kind == MG_SMOOTH_GS && prec == h->prec && sweep_tile_for(h, level, tile)) {
+        // one-pass sweeps ping-pong between x and the level's scratch
         void* bufs[2] = {x, lv.t};
         for (int s = 0; s < sweeps; ++s, ++n) {
             BTask t{};
@@ -841,9 +926,16 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
             t.y = bufs[(s + 1) & 1];
             t.b = b;
             t.block0 = 0;
-            t.nblocks = rb7_tiles(lv.D);
+            t.nblocks = sweep_units(lv.D, tile);
+            for (int a = 0; a < 3; ++a) t.tile[a] = tile[a];
+            t.tmap = h->one_map;
+            alignas(64) unsigned char map[128];
+            CK(encode_sweep_map(map, t.x, lv.D, h->stencil, prec, tile));
+            // pageable sources: both copies are staged before the calls return
+            CK(cudaMemcpyAsync(h->one_map, map, sizeof(map), cudaMemcpyHostToDevice, h->stream));
             CK(cudaMemcpyAsync(h->one_task, &t, sizeof(BTask), cudaMemcpyHostToDevice, h->stream));
-            CK(launch_batch(h->one_task, 1, t.nblocks, nullptr, BOP_RB7, 0, 7, prec, h->stream));
+            CK(launch_sweep(h->one_task, 1, t.nblocks, nullptr, h->stencil, h->axi, prec,
+                            sweep_smem_bytes(h->stencil, prec, lv.D, tile), h->stream));
         }
         if (sweeps & 1) {
             CK(cudaMemcpyAsync(x, lv.t, value_bytes(prec) * lv.D.n(), cudaMemcpyDeviceToDevice, h->stream));
@@ -1005,7 +1097,14 @@ mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out) {
     out->blocks_per_sm = h->vb_cap;
     out->tail_level = h->tail_level;
     out->tail_cluster = h->tail_cluster;
-    out->one_pass_tiles = h->fused_rb ? 1 : 0;
+    out->one_pass_tiles = h->one_pass ? 1 : 0;
+    out->tile_cells = h->sweep_cells;
+    out->tile_planes = h->sweep_tj;
+    out->tile_kmax = h->sweep_kmax;
+    out->tile_min_cells = h->sweep_min_cells;
+    int tile[3] = {0, 0, 0};
+    if (!sweep_tile_for(h, 0, tile)) tile[0] = tile[1] = tile[2] = 0;
+    for (int a = 0; a < 3; ++a) out->tile0[a] = tile[a];
     out->source = h->sched_source;
     out->candidates = h->sched_candidates;
     out->ms_per_iteration = h->sched_ms;

@@ -83,12 +83,17 @@ struct mg_handle {
     std::vector<cudaEvent_t> prof_pool;
     // outer iterations run as captured graphs (solver.cu)
     bool use_graph = true;
-    bool fused_rb = false;            // one-pass red-black tile sweeps (schedule choice)
+    bool one_pass = false;            // one-pass multicolour sweeps where a tile fits (schedule choice)
+    int sweep_cells = 2048;           // one-pass tiles: target cells per plane (rows x longitudes)
+    int sweep_tj = 0;                 // one-pass tiles: radius planes per chunk (0: per level)
+    int sweep_kmax = 256;             // one-pass tiles: widest tile in longitudes (whole rows up to it)
+    long long sweep_min_cells = 1 << 20;   // one-pass tiles: only on levels of at least this many cells
     int vb_cap = 16;                  // blocks per SM of the level kernels' virtual grids
     int sched_source = 0;             // mg_schedule.source
     int sched_candidates = 0;
     double sched_ms = 0.0;
     mgs::BTask* one_task = nullptr;   // task table of stand-alone one-pass sweeps
+    void* one_map = nullptr;          // tensor map of a stand-alone one-pass sweep (128 bytes)
     int tail_level = 0;               // first level of the single-launch coarse tail (0: none)
     int tail_cluster = 8;             // CTAs per tail cluster
     mgs::TailTask* tail_dev = nullptr;
@@ -145,6 +150,10 @@ mg_status plan_time(Plan* pl, int warm, int reps, double* ms);
 mg_status plan_finish(Plan* pl, double* const* x);
 mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind);
 double model_bytes_per_iteration(const mg_handle* h);
+// The one-pass sweep tile of a level under the handle's schedule (colatitude
+// rows, radius planes per chunk, longitudes); false when the level is
+// smoothed by colour passes.
+bool sweep_tile_for(const mg_handle* h, int level, int tile[3]);
 // smoothers that sweep radial lines / longitude lines (the alternating one both)
 inline bool radial_lines(int smoother) { return smoother == MG_SMOOTH_LINE || smoother == MG_SMOOTH_ALT; }
 inline bool longitude_lines(int smoother) { return smoother == MG_SMOOTH_XLINE || smoother == MG_SMOOTH_ALT; }

@@ -240,52 +240,77 @@ __device__ __forceinline__ T apply_cell(const CF& cf, const XA& X, const Dims& D
     return acc;
 }
 
-// Exact diagonal A_cc of the operator above.  Besides -sum of the six G_dd, a
-// cross term reaches x_c itself when a tangential neighbour is mirrored onto c
-// at a wall: +G_dq/4 at an upper face and -G_dq/4 at a lower face when c is
-// on the top wall in q, with opposite signs on the bottom wall.
-template <int S, typename T, typename CF>
-__device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
+// The coefficient rows of one cell's six faces as the formulas below read
+// them: face 0 = the cell's own (lower-face) rows, 1 / 2 / 3 = the rows of the
+// next cell along radius / colatitude / longitude (the cell's upper faces).
+// CellRows reads them from the coefficient arrays; the one-pass sweeps hand
+// over rows already loaded into registers through the same interface, so the
+// arithmetic is one piece of code.
+template <typename CF>
+struct CellRows {
+    const CF& cf;
+    i64 self, eu, zu, xu;
+    __device__ __forceinline__ bool has(int a) const { return cf.has(a); }
+    template <int F>
+    __device__ __forceinline__ auto at(int a) const {
+        return cf(a, F == 0 ? self : (F == 1 ? eu : (F == 2 ? zu : xu)));
+    }
+};
+template <typename CF>
+__device__ __forceinline__ CellRows<CF> cell_rows(const CF& cf, const Dims& D, C3 c) {
     const i64 self = cidx(D, c);
+    return CellRows<CF>{cf, self, c.j < D.nr - 1 ? cidx(D, c.j + 1, c.i, c.k) : self,
+                        c.i < D.nth - 1 ? cidx(D, c.j, c.i + 1, c.k) : self,
+                        cidx(D, c.j, c.i, c.k + 1 == D.nph ? 0 : c.k + 1)};
+}
+
+template <int S, typename T, typename R>
+__device__ __forceinline__ T diag_cell_r(const R& cr, const Dims& D, C3 c) {
     T dg = 0;
     // lower/upper coefficient rows of the six faces (upper = neighbour's lower row)
     const bool hasEl = c.j > 0, hasEu = c.j < D.nr - 1;
     const bool hasZl = c.i > 0, hasZu = c.i < D.nth - 1;
-    const i64 eu = hasEu ? cidx(D, c.j + 1, c.i, c.k) : self;
-    const i64 zu = hasZu ? cidx(D, c.j, c.i + 1, c.k) : self;
-    const i64 xu = cidx(D, c.j, c.i, c.k + 1 == D.nph ? 0 : c.k + 1);
-    if (hasEl) dg -= (T)cf(4, self);
-    if (hasEu) dg -= (T)cf(4, eu);
-    if (hasZl) dg -= (T)cf(0, self);
-    if (hasZu) dg -= (T)cf(0, zu);
-    dg -= (T)cf(8, self);
-    dg -= (T)cf(8, xu);
+    if (hasEl) dg -= (T)cr.template at<0>(4);
+    if (hasEu) dg -= (T)cr.template at<1>(4);
+    if (hasZl) dg -= (T)cr.template at<0>(0);
+    if (hasZu) dg -= (T)cr.template at<2>(0);
+    dg -= (T)cr.template at<0>(8);
+    dg -= (T)cr.template at<3>(8);
     if (S == 19) {
         // mirrored-onto-self weight along q: +1 at the top wall, -1 at the bottom
         const T sz = (T)((c.i == D.nth - 1) - (c.i == 0));   // q = zeta
         const T se = (T)((c.j == D.nr - 1) - (c.j == 0));    // q = eta
         if (sz != (T)0) {
             T w = 0;
-            if (hasEu) w += (T)cf(3, eu);     // eta faces, column zeta
-            if (hasEl) w -= (T)cf(3, self);
-            if (cf.has(6)) {
-                w += (T)cf(6, xu);             // xi faces, column zeta
-                w -= (T)cf(6, self);
+            if (hasEu) w += (T)cr.template at<1>(3);     // eta faces, column zeta
+            if (hasEl) w -= (T)cr.template at<0>(3);
+            if (cr.has(6)) {
+                w += (T)cr.template at<3>(6);             // xi faces, column zeta
+                w -= (T)cr.template at<0>(6);
             }
             dg = fma((T)0.25 * sz, w, dg);
         }
         if (se != (T)0) {
             T w = 0;
-            if (hasZu) w += (T)cf(1, zu);     // zeta faces, column eta
-            if (hasZl) w -= (T)cf(1, self);
-            if (cf.has(7)) {
-                w += (T)cf(7, xu);             // xi faces, column eta
-                w -= (T)cf(7, self);
+            if (hasZu) w += (T)cr.template at<2>(1);     // zeta faces, column eta
+            if (hasZl) w -= (T)cr.template at<0>(1);
+            if (cr.has(7)) {
+                w += (T)cr.template at<3>(7);             // xi faces, column eta
+                w -= (T)cr.template at<0>(7);
             }
             dg = fma((T)0.25 * se, w, dg);
         }
     }
     return dg;
+}
+
+// Exact diagonal A_cc of the operator above.  Besides -sum of the six G_dd, a
+// cross term reaches x_c itself when a tangential neighbour is mirrored onto c
+// at a wall: +G_dq/4 at an upper face and -G_dq/4 at a lower face when c is
+// on the top wall in q, with opposite signs on the bottom wall.
+template <int S, typename T, typename CF>
+__device__ __forceinline__ T diag_cell(const CF& cf, const Dims& D, C3 c) {
+    return diag_cell_r<S, T>(cell_rows(cf, D, c), D, c);
 }
 
 // ---------------------------------------------------------------- 7-point fast path
@@ -428,15 +453,16 @@ struct Nbr19 {
 };
 
 // acc + sgn F for the lower (side -1) or upper (side +1) d-face of the cell,
-// from registers: the arithmetic of add_flux step by step (same bits).
-template <int d, int side, typename T, typename CF>
-__device__ __forceinline__ T add_flux19(T acc, const CF& cf, const Nbr19<T>& X, int u) {
+// from registers: the arithmetic of add_flux step by step (same bits).  F is
+// the face's row in the cell's rows (0 for a lower face).
+template <int d, int side, int F, typename T, typename R>
+__device__ __forceinline__ T add_flux19(T acc, const R& cr, const Nbr19<T>& X) {
     constexpr int sL = side < 0 ? -1 : 0, sU = side < 0 ? 0 : 1;
     const T sgn = (T)side;
-    acc = fma(sgn * (T)cf(4 * d, u), X.template at<d, sU, d, 0>() - X.template at<d, sL, d, 0>(), acc);
+    acc = fma(sgn * (T)cr.template at<F>(4 * d), X.template at<d, sU, d, 0>() - X.template at<d, sL, d, 0>(), acc);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        if (q == d || !cf.has(3 * d + q)) continue;
+        if (q == d || !cr.has(3 * d + q)) continue;
         T plus, minus;
         if (q == 0) {
             plus = X.template at<d, sL, 0, 1>() + X.template at<d, sU, 0, 1>();
@@ -448,24 +474,30 @@ __device__ __forceinline__ T add_flux19(T acc, const CF& cf, const Nbr19<T>& X, 
             plus = X.template at<d, sL, 2, 1>() + X.template at<d, sU, 2, 1>();
             minus = X.template at<d, sL, 2, -1>() + X.template at<d, sU, 2, -1>();
         }
-        acc = fma(sgn * (T)0.25 * (T)cf(3 * d + q, u), plus - minus, acc);
+        acc = fma(sgn * (T)0.25 * (T)cr.template at<F>(3 * d + q), plus - minus, acc);
     }
     return acc;
 }
 
-// (A x)_c of the 19-point operator from the loaded neighbourhood; equal bit
-// for bit to apply_cell<19>.
+// (A x)_c of the 19-point operator from the loaded neighbourhood and the
+// cell's face rows; equal bit for bit to apply_cell<19>.
+template <typename T, typename R>
+__device__ __forceinline__ T apply19_r(const R& cr, const Nbr19<T>& X, const Dims& D, C3 p) {
+    T acc = 0;
+    if (p.j > 0) acc = add_flux19<1, -1, 0>(acc, cr, X);
+    if (p.j < D.nr - 1) acc = add_flux19<1, 1, 1>(acc, cr, X);
+    if (p.i > 0) acc = add_flux19<0, -1, 0>(acc, cr, X);
+    if (p.i < D.nth - 1) acc = add_flux19<0, 1, 2>(acc, cr, X);
+    acc = add_flux19<2, -1, 0>(acc, cr, X);
+    acc = add_flux19<2, 1, 3>(acc, cr, X);
+    return acc;
+}
+
 template <typename T, typename CF>
 __device__ __forceinline__ T apply19(const CF& cf, const Nbr19<T>& X, const Dims& D, int c, C3 p) {
     const int plane = D.nth * D.nph;
-    T acc = 0;
-    if (p.j > 0) acc = add_flux19<1, -1>(acc, cf, X, c);
-    if (p.j < D.nr - 1) acc = add_flux19<1, 1>(acc, cf, X, c + plane);
-    if (p.i > 0) acc = add_flux19<0, -1>(acc, cf, X, c);
-    if (p.i < D.nth - 1) acc = add_flux19<0, 1>(acc, cf, X, c + D.nph);
-    acc = add_flux19<2, -1>(acc, cf, X, c);
-    acc = add_flux19<2, 1>(acc, cf, X, p.k + 1 < D.nph ? c + 1 : c + 1 - D.nph);
-    return acc;
+    const CellRows<CF> cr{cf, c, c + plane, c + D.nph, p.k + 1 < D.nph ? c + 1 : c + 1 - D.nph};
+    return apply19_r<T>(cr, X, D, p);
 }
 
 // b_c - (A x)_c from the assembled coefficients a[n * N + c] (row_off order;

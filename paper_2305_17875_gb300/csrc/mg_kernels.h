@@ -135,16 +135,10 @@ enum {
     BOP_SHIFT,        // x -= scal[SC_SUMJX] / aux
     BOP_FINALIZE,     // scal[slot] = sum of n partials z; y (if set) gets a copy
     BOP_COARSE,       // x = binv b, n rows
-    BOP_RB7,          // one red-black sweep of the 7-point operator, x -> y (tiles)
+    BOP_SWEEP,        // one whole multicolour sweep, x -> y (sweep.cu; launched by launch_sweep)
     BOP_LINE,         // radial-line Gauss-Seidel colour pass: x, b, z = line factors
     BOP_XLINE         // longitude-line Gauss-Seidel colour pass: x, b, z = factors, y = scratch
 };
-// Tiles of the one-pass red-black sweep (colatitude x radius x longitude).
-constexpr int kRbJ = 8, kRbI = 8, kRbK = 64;
-inline int rb7_tiles(const Dims& D) {
-    return ((D.nr + kRbJ - 1) / kRbJ) * ((D.nth + kRbI - 1) / kRbI) * ((D.nph + kRbK - 1) / kRbK);
-}
-inline bool rb7_fits(const Dims& D) { return D.nph >= kRbK; }
 struct BTask {
     LevelView v;       // level of the task (dims, factors, coefficients, stencil)
     Dims Dc;           // next-coarser level (restriction / prolongation)
@@ -163,8 +157,28 @@ struct BTask {
     int block0;        // first virtual block of the task in its launch
     int nblocks;       // virtual blocks (work mapping of a stand-alone launch)
     int shell;         // index of the active flag
+    int tile[3];       // one-pass sweep: colatitude rows, radius planes, longitudes of a tile
+    const void* tmap;  // one-pass sweep: tensor map of x (device, 64-byte aligned)
 };
 static_assert(sizeof(BTask) % 4 == 0, "BTask is staged in shared memory word by word");
+// ---- one-pass multicolour sweeps (sweep.cu).  A tile is tile[0] colatitude
+// rows x tile[2] longitudes (tile[2] == nph: whole rows) x a chunk of tile[1]
+// radius planes; the iterate x of a task is staged through a tensor map made
+// by encode_sweep_map (128 bytes, 64-byte aligned).
+bool sweep_tile_ok(const Dims& D, int stencil, int prec, const int tile[3]);
+size_t sweep_smem_bytes(int stencil, int prec, const Dims& D, const int tile[3]);
+int sweep_units(const Dims& D, const int tile[3]);
+cudaError_t encode_sweep_map(void* map, const void* x, const Dims& D, int stencil, int prec, const int tile[3]);
+// All tasks of one launch share stencil, precision and axi; smem = the
+// largest sweep_smem_bytes of its tasks.
+// axi: 19 points without the longitude cross terms (the handle's stored
+// components); every task of the launch shares it.
+cudaError_t launch_sweep(const BTask* tasks, int ntasks, int total, const int* active, int stencil, bool axi,
+                         int prec, size_t smem, cudaStream_t s);
+// The fault word of the sweeps (a plane copy that did not land in time);
+// clear resets it.
+cudaError_t sweep_fault_read(unsigned* out, bool clear);
+
 // Checks the integer-pipe FP64 <-> FP32 conversions (narrow_rn, scaled_widen)
 // against the hardware ones; *bad (zeroed by the caller) counts mismatches.
 cudaError_t launch_convert_check(unsigned* bad, cudaStream_t s);

@@ -63,12 +63,25 @@ struct Launch {
     int prof = -1, prof_n = 0;     // profiling slot around this launch
     int level = -1;                // level of a level operation (timing attribution)
     int tail_stencil = 0;          // >0: a coarse-tail launch of this stencil
+    size_t smem = 0;               // one-pass sweep launches: dynamic shared memory
+    bool axi = false;              // one-pass sweep launches: 19 points without longitude cross terms
+};
+
+// Tensor map of a one-pass sweep task's input iterate (made when the plan's
+// tables are uploaded).
+struct MapReq {
+    int task;
+    const void* x;
+    Dims D;
+    int stencil, prec;
+    int tile[3];
 };
 
 struct Program {
     std::vector<BTask> tasks;
     std::vector<Launch> launches;
     std::vector<TailTask> tails;   // tail tasks (7-point first, then 19-point)
+    std::vector<MapReq> maps;      // tensor maps of the one-pass sweep tasks
 
     Launch& begin(int op, int colour = 0, int stencil = 0) {
         Launch L;
@@ -109,6 +122,8 @@ struct Plan {
     size_t iter_cap = 0;
     TailTask* d_tails = nullptr;
     size_t tails_cap = 0;
+    unsigned char* d_maps = nullptr;   // tensor maps of the iteration's sweep tasks (128 bytes each)
+    size_t maps_cap = 0;
     int* d_active = nullptr;      // per-shell flags
     int* h_active = nullptr;      // pinned
     double* d_fin = nullptr;      // per shell: [sum J f, ||b||^2, ||r||^2, sum J x]
@@ -146,10 +161,11 @@ void level_bufs(const mg_handle* h, int prec, int level, void** x, const void** 
 
 int top_of(const mg_handle* h) { return h->tail_level > 0 ? h->tail_level : (int)h->L.size() - 1; }
 
-// One-pass red-black sweeps apply to 7-point Gauss-Seidel levels wide enough
-// for the longitude tiles.
+// Levels smoothed by one-pass sweeps (the schedule's choice, where the tile
+// fits the level).
 bool fused_level(const mg_handle* h, int level) {
-    return h->fused_rb && h->stencil == 7 && h->opts.smoother == MG_SMOOTH_GS && rb7_fits(h->L[level].D);
+    int tile[3];
+    return sweep_tile_for(h, level, tile);
 }
 
 void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
@@ -167,26 +183,37 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
         else maxc = std::max(maxc, nc);
     }
     for (int sw = 0; sw < sweeps; ++sw) {
-        if (any_fused) {   // ping-pong between the level iterate and its scratch
-            Launch& L = P.begin(BOP_RB7, 0, 7);
-            if (level == 0) {
-                L.prof = MG_PROF_SMOOTH0;
-                L.prof_n = 1;
+        if (any_fused)   // ping-pong between the level iterate and its scratch
+            for (int kind = 0; kind < 3; ++kind) {   // 7 points; 19 axisymmetric; 19 full
+                const int st = kind == 0 ? 7 : 19;
+                const bool axi = kind == 1;
+                Launch& L = P.begin(BOP_SWEEP, 0, st);
+                L.axi = axi;
+                if (level == 0) {
+                    L.prof = MG_PROF_SMOOTH0;
+                    L.prof_n = 1;
+                }
+                for (size_t s = 0; s < pl->hs.size(); ++s) {
+                    mg_handle* h = pl->hs[s];
+                    int tile[3];
+                    if (level >= top_of(h) || h->stencil != st || (st == 19 && h->axi != axi) ||
+                        !sweep_tile_for(h, level, tile))
+                        continue;
+                    const Dims& D = h->L[level].D;
+                    BTask t = task_of(h, level);
+                    void* xb;
+                    const void* bb;
+                    level_bufs(h, prec, level, &xb, &bb);
+                    t.x = (sw & 1) ? h->L[level].t : xb;
+                    t.y = (sw & 1) ? xb : h->L[level].t;
+                    t.b = bb;
+                    t.shell = (int)s;
+                    for (int a = 0; a < 3; ++a) t.tile[a] = tile[a];
+                    P.maps.push_back(MapReq{(int)P.tasks.size(), t.x, D, st, prec, {tile[0], tile[1], tile[2]}});
+                    L.smem = std::max(L.smem, sweep_smem_bytes(st, prec, D, tile));
+                    P.add(t, sweep_units(D, tile));
+                }
             }
-            for (size_t s = 0; s < pl->hs.size(); ++s) {
-                mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || !fused_level(h, level)) continue;
-                BTask t = task_of(h, level);
-                void* xb;
-                const void* bb;
-                level_bufs(h, prec, level, &xb, &bb);
-                t.x = (sw & 1) ? h->L[level].t : xb;
-                t.y = (sw & 1) ? xb : h->L[level].t;
-                t.b = bb;
-                t.shell = (int)s;
-                P.add(t, rb7_tiles(h->L[level].D));
-            }
-        }
         for (int c = 0; c < maxc; ++c)
             for (int st : {7, 19}) {
             Launch& L = P.begin(BOP_GS, c, st);
@@ -474,6 +501,8 @@ mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const in
                 ++n;
             }
             CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream));
+        } else if (L.op == BOP_SWEEP) {
+            CK(launch_sweep(d_tasks + L.t0, L.nt, L.total, active, L.stencil, L.axi, pl->prec, L.smem, pl->stream));
         } else {
             CK(launch_batch(d_tasks + L.t0, L.nt, L.total, active, L.op, L.colour, L.stencil, pl->prec,
                             pl->stream));
@@ -545,6 +574,7 @@ void plan_destroy(Plan* pl) {
     if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
     if (pl->d_iter) cudaFree(pl->d_iter);
     if (pl->d_tails) cudaFree(pl->d_tails);
+    if (pl->d_maps) cudaFree(pl->d_maps);
     if (pl->d_active) cudaFree(pl->d_active);
     if (pl->d_fin) cudaFree(pl->d_fin);
     if (pl->d_call) cudaFree(pl->d_call);
@@ -599,6 +629,19 @@ mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n, bool iteration) {
     build_iteration(pl);
     std::stable_sort(pl->iter.tails.begin(), pl->iter.tails.end(),
                      [](const TailTask& a, const TailTask& b) { return a.lev[0].v.stencil < b.lev[0].v.stencil; });
+    if (!pl->iter.maps.empty()) {
+        const size_t nb = 128 * pl->iter.maps.size();
+        CK(grow(&pl->d_maps, &pl->maps_cap, nb, false));
+        // host images of the maps (CUtensorMap is 128 bytes, 64-byte aligned)
+        std::vector<unsigned long long> img(nb / 8);
+        for (size_t m = 0; m < pl->iter.maps.size(); ++m) {
+            const MapReq& q = pl->iter.maps[m];
+            CK(encode_sweep_map(&img[16 * m], q.x, q.D, q.stencil, q.prec, q.tile));
+            pl->iter.tasks[q.task].tmap = pl->d_maps + 128 * m;
+        }
+        CK(cudaMemcpyAsync(pl->d_maps, img.data(), nb, cudaMemcpyHostToDevice, pl->stream));
+        CK(cudaStreamSynchronize(pl->stream));   // img is pageable and local
+    }
     CK(grow(&pl->d_iter, &pl->iter_cap, pl->iter.tasks.size() + 1, false));
     if (!pl->iter.tasks.empty())
         CK(cudaMemcpyAsync(pl->d_iter, pl->iter.tasks.data(), sizeof(BTask) * pl->iter.tasks.size(),

@@ -272,8 +272,9 @@ def test_solve_matches_oracle(lib, wl, scale, prec, opts, path, monkeypatch):
 @pytest.mark.parametrize("wl,scale,prec", [("single_sphere_128", 4, 1), ("single_sphere_128", 4, 0),
                                              ("single_oblate_256", 8, 1), ("single_sphere_32", 1, 2)])
 def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypatch):
-    """The coarse tail, the one-pass red-black tiles and the per-level launches
-    share the per-cell arithmetic, so every schedule gives the same bits."""
+    """The coarse tail, the one-pass sweeps (several tile shapes) and the
+    per-level launches share the per-cell arithmetic, so every schedule gives
+    the same bits."""
     torch, dev = torch_dev()
     w = W.single(wl, scale)
     fd = to_dev(w["f"], torch.float64)
@@ -281,8 +282,11 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
     for name, env, tune in [("default", {}, 0), ("tuned", {}, 1), ("tuned_again", {}, 1),
                             ("tail", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192"}, 1),
                             ("tail_big", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4"}, 1),
-                            ("fused", {"MG_FUSED_RB": "1"}, 1), ("no_graph", {"MG_NO_GRAPH": "1"}, 0)]:
-        for k in ("MG_TAIL", "MG_TAIL_CELLS", "MG_TAIL_CLUSTER", "MG_FUSED_RB", "MG_NO_GRAPH"):
+                            ("fused", {"MG_FUSED_RB": "1"}, 1),
+                            ("fused_narrow", {"MG_FUSED_RB": "1", "MG_TILE": "256,3,32"}, 1),
+                            ("fused_tail", {"MG_FUSED_RB": "1", "MG_TILE": "1024,2,256", "MG_TAIL": "1"}, 1),
+                            ("no_graph", {"MG_NO_GRAPH": "1"}, 0)]:
+        for k in ("MG_TAIL", "MG_TAIL_CELLS", "MG_TAIL_CLUSTER", "MG_FUSED_RB", "MG_NO_GRAPH", "MG_TILE"):
             monkeypatch.delenv(k, raising=False)
         for k, v in env.items():
             monkeypatch.setenv(k, v)
@@ -343,8 +347,8 @@ def test_max_iters_reports_noconv(lib):
 
 
 FUSED_GRIDS = {
-    # nph >= 64 takes the one-pass red-black kernel (8 x 8 x 64 tiles); partial
-    # tiles in every direction, and a grid whose longitude ring wraps onto itself
+    # with MG_FUSED_RB=1 every level a tile fits takes the one-pass sweep;
+    # ragged last tiles in colatitude and radius
     "fused_ragged": W.grid_desc(6, 20, 96),
     "fused_stretched": W.grid_desc(12, 20, 72, stretch=2.0),
     "fused_exact_tiles": W.grid_desc(8, 16, 64),
