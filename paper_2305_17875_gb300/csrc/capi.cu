@@ -742,12 +742,12 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     {
         const size_t m = (size_t)nc + 1;
         TmpDev tA(sizeof(double) * nc * nc, stream, h->device);
-        TmpDev tw(sizeof(double) * (m * m + m) + sizeof(int) * (2 * m + 1), stream, h->device);
+        TmpDev tw(sizeof(double) * (m * m + kGjScratch) + sizeof(int) * (2 * m + 1), stream, h->device);
         if (!tA.p || !tw.p) return MG_ENOMEM;
         double* dA = (double*)tA.p;
         double* work = (double*)tw.p;
         double* col = work + m * m;
-        int* piv = (int*)(col + m);
+        int* piv = (int*)(col + kGjScratch);
         int* perm = piv + m;
         int* bad = perm + m;
         CK(cudaMemsetAsync(bad, 0, sizeof(int), stream));
@@ -757,7 +757,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         if (hbad) {
-            set_error("coarsest bordered operator is singular");
+            set_error(hbad == 2 ? "coarsest inverse: a grid barrier gave up waiting"
+                                : "coarsest bordered operator is singular");
             return MG_EINVAL;
         }
     }

@@ -375,10 +375,8 @@ __global__ void k_xline_factors(CoefF64 cf, Dims D, T* fac, unsigned* bad) {
 }
 
 // ---- in-place Gauss-Jordan inversion with partial pivoting (FP64), for the
-// bordered coarsest matrix [A 1; 1^T 0] of order m.  Step k: the pivot row
-// (largest |M[r][k]|, r >= k) is swapped into row k, row k is scaled, and
-// every other row eliminated; the row swaps are undone on the columns at the
-// end.  A zero pivot (singular matrix) sets *bad.
+// bordered coarsest matrix [A 1; 1^T 0] of order m.  A zero pivot (singular
+// matrix) sets *bad.
 __global__ void k_bordered(const double* __restrict__ A, int n, double* __restrict__ M) {
     const int m = n + 1;
     for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < (i64)m * m; t += (i64)gridDim.x * blockDim.x) {
@@ -387,78 +385,163 @@ __global__ void k_bordered(const double* __restrict__ A, int n, double* __restri
     }
 }
 
-__global__ void __launch_bounds__(1024) k_gj_pivot(double* M, int m, int k, double* col, int* piv, int* bad) {
-    __shared__ double bv[32];
-    __shared__ int bi[32];
-    __shared__ int p_sh;
-    double best = -1.0;
-    int arg = k;
-    for (int r = k + threadIdx.x; r < m; r += blockDim.x) {
-        const double v = fabs(M[(i64)r * m + k]);
-        if (v > best) best = v, arg = r;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, arg, o);
-        if (ov > best || (ov == best && oi < arg)) best = ov, arg = oi;
-    }
-    if ((threadIdx.x & 31) == 0) bv[threadIdx.x >> 5] = best, bi[threadIdx.x >> 5] = arg;
+// One launch for the whole inversion: a cooperative grid (every CTA
+// co-resident) in which CTA b owns rows b, b + G, ...; pivot rows are never
+// moved (implicit partial pivoting), so the in-place result M satisfies
+// inverse[i][j] = M[piv[i]][ipiv[j]] with ipiv the inverse permutation.
+// Step k: every CTA reduces the candidates (|M[r][k]|, r) the CTAs published
+// for column k (the largest |.| over unused rows, ties to the lower row) to
+// the pivot row p, copies row p, scales it by 1 / M[p][k] (M[p][k] becomes
+// 1 / M[p][k]) and eliminates column k from its own rows r != p
+// (M[r][c] -= M[r][k] * row_p[c], M[r][k] = -M[r][k] / M[p][k]), publishing
+// its candidates for column k + 1 on the way; the owner of p writes the scaled
+// row after the step's barrier (the other CTAs read the unscaled one during
+// the step).  One grid barrier per column.  Barrier waits are bounded: a wait
+// that gives up sets *bad = 2 and the CTA leaves.
+struct GjShared {
+    double row[kMaxGj];     // the pivot row (scaled)
+    double f[kMaxGj];       // multipliers M[r][k] of this CTA's rows
+    double cv[32];          // block reductions
+    int ci[32];
+    int piv[kMaxGj];
+    unsigned char used[kMaxGj];
+};
+
+__device__ bool gj_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int* bad) {
+    __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = -1.0;
-        int a = k;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            if (bv[w] > b || (bv[w] == b && bi[w] < a)) b = bv[w], a = bi[w];
-        if (!(b > 0.0)) *bad = 1;
-        p_sh = a;
-        piv[k] = a;
-    }
-    __syncthreads();
-    const int p = p_sh;
-    if (p != k)
-        for (int c = threadIdx.x; c < m; c += blockDim.x) {
-            const double a = M[(i64)k * m + c];
-            M[(i64)k * m + c] = M[(i64)p * m + c];
-            M[(i64)p * m + c] = a;
+        ok = 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd((unsigned*)gen, 1u);
+        } else {
+            for (int it = 0; it < (1 << 22) && *gen == g; ++it)
+                if (it > 64) __nanosleep(64);
+            if (*gen == g) {
+                ok = 0;
+                atomicExch(bad, 2);
+            }
         }
-    __syncthreads();
-    const double d = M[(i64)k * m + k];
-    const double inv = d != 0.0 ? 1.0 / d : 0.0;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) col[r] = r == k ? 0.0 : M[(i64)r * m + k];
-    __syncthreads();
-    for (int c = threadIdx.x; c < m; c += blockDim.x)
-        M[(i64)k * m + c] = c == k ? inv : M[(i64)k * m + c] * inv;
-}
-
-__global__ void k_gj_elim(double* __restrict__ M, int m, int k, const double* __restrict__ col) {
-    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < (i64)m * m; t += (i64)gridDim.x * blockDim.x) {
-        const int r = (int)(t / m), c = (int)(t % m);
-        if (r == k) continue;
-        const double f = col[r];
-        const double v = c == k ? 0.0 : M[t];
-        M[t] = fma(-f, M[(i64)k * m + c], v);
+        __threadfence();
     }
+    __syncthreads();
+    return ok != 0;
 }
 
-// Undo the row swaps on the columns, last swap first: perm[c] = the column of
-// M that ends at position c.  One thread (O(m)).
-__global__ void k_gj_perm(const int* __restrict__ piv, int m, int* __restrict__ perm) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int c = 0; c < m; ++c) perm[c] = c;
-    for (int k = m - 1; k >= 0; --k) {
-        const int a = perm[k];
-        perm[k] = perm[piv[k]];
-        perm[piv[k]] = a;
+// Largest (|v|, row) over the block's threads, ties to the lower row; the
+// result in thread 0.
+__device__ void gj_reduce(double& v, int& r, GjShared& sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, o);
+        const int orr = __shfl_down_sync(0xffffffffu, r, o);
+        if (ov > v || (ov == v && orr < r)) v = ov, r = orr;
     }
+    if ((threadIdx.x & 31) == 0) sh.cv[threadIdx.x >> 5] = v, sh.ci[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sh.cv[w] > v || (sh.cv[w] == v && sh.ci[w] < r)) v = sh.cv[w], r = sh.ci[w];
+    __syncthreads();
 }
 
-// binv = leading n x n block of the unscrambled inverse.
-__global__ void k_gj_finish(const double* __restrict__ M, int m, const int* __restrict__ perm,
-                            double* __restrict__ binv) {
+__global__ void __launch_bounds__(256) k_gj_coop(double* __restrict__ M, int m, double* cand_v, int* cand_r,
+                                                  unsigned* bar, int* piv_out, int* ipiv_out, int* bad) {
+    __shared__ GjShared sh;
+    const int G = gridDim.x, b = blockIdx.x;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) sh.used[r] = 0;
+    {   // candidates for column 0
+        double v = -1.0;
+        int rr = m;
+        for (int r = b + (int)threadIdx.x * G; r < m; r += (int)blockDim.x * G) {
+            const double a = fabs(M[(i64)r * m]);
+            if (a > v || (a == v && r < rr)) v = a, rr = r;
+        }
+        gj_reduce(v, rr, sh);
+        if (threadIdx.x == 0) {
+            cand_v[b] = v;
+            cand_r[b] = rr;
+        }
+    }
+    if (!gj_barrier(bar, bar + 1, G, bad)) return;
+    int pending = -1;   // a scaled pivot row of this CTA not yet written
+    for (int k = 0; k < m; ++k) {
+        const int buf = (k & 1) * G;
+        if (pending >= 0) {   // the previous step's pivot row, scaled
+            for (int c = threadIdx.x; c < m; c += blockDim.x) M[(i64)pending * m + c] = sh.row[c];
+            pending = -1;
+            __syncthreads();
+        }
+        // the pivot: every CTA reduces the same candidates the same way
+        double v = -1.0;
+        int p = m;
+        for (int q = threadIdx.x; q < G; q += blockDim.x) {
+            const double cv = __ldcg(cand_v + buf + q);
+            const int cr = __ldcg(cand_r + buf + q);
+            if (cv > v || (cv == v && cr < p)) v = cv, p = cr;
+        }
+        gj_reduce(v, p, sh);
+        if (threadIdx.x == 0) {
+            sh.ci[0] = p;
+            if (!(v > 0.0) || p >= m) atomicExch(bad, 1);
+        }
+        __syncthreads();
+        p = sh.ci[0];
+        if (p >= m) return;   // singular (flagged): every CTA leaves here
+        // the pivot row, scaled
+        const double inv = 1.0 / __ldcg(M + (i64)p * m + k);
+        for (int c = threadIdx.x; c < m; c += blockDim.x)
+            sh.row[c] = c == k ? inv : __ldcg(M + (i64)p * m + c) * inv;
+        if (threadIdx.x == 0) {
+            sh.used[p] = 1;
+            sh.piv[k] = p;
+        }
+        __syncthreads();
+        // the multipliers first: column k is overwritten below
+        for (int r = b + (int)threadIdx.x * G; r < m; r += (int)blockDim.x * G) sh.f[(r - b) / G] = M[(i64)r * m + k];
+        __syncthreads();
+        // eliminate column k from this CTA's rows; candidates for column k + 1
+        double bv = -1.0;
+        int br = m;
+        for (int r = b; r < m; r += G) {
+            if (r == p) continue;
+            const double f = sh.f[(r - b) / G];
+            for (int c = threadIdx.x; c < m; c += blockDim.x) {
+                const double nv = c == k ? -f * inv : fma(-f, sh.row[c], M[(i64)r * m + c]);
+                M[(i64)r * m + c] = nv;
+                if (c == k + 1 && !sh.used[r]) {
+                    const double a = fabs(nv);
+                    if (a > bv || (a == bv && r < br)) bv = a, br = r;
+                }
+            }
+        }
+        if (p % G == b) pending = p;
+        gj_reduce(bv, br, sh);
+        if (threadIdx.x == 0) {
+            cand_v[((k + 1) & 1) * G + b] = bv;
+            cand_r[((k + 1) & 1) * G + b] = br;
+        }
+        if (!gj_barrier(bar, bar + 1, G, bad)) return;
+    }
+    if (pending >= 0)
+        for (int c = threadIdx.x; c < m; c += blockDim.x) M[(i64)pending * m + c] = sh.row[c];
+    if (b == 0)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            piv_out[k] = sh.piv[k];
+            ipiv_out[sh.piv[k]] = k;
+        }
+}
+
+// binv = leading n x n block of the inverse: binv[i][j] = M[piv[i]][ipiv[j]].
+__global__ void k_gj_finish(const double* __restrict__ M, int m, const int* __restrict__ piv,
+                            const int* __restrict__ ipiv, double* __restrict__ binv) {
     const int n = m - 1;
     for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < (i64)n * n; t += (i64)gridDim.x * blockDim.x) {
         const int r = (int)(t / n), c = (int)(t % n);
-        binv[t] = M[(i64)r * m + perm[c]];
+        binv[t] = M[(i64)piv[r] * m + ipiv[c]];
     }
 }
 
@@ -480,14 +563,29 @@ cudaError_t launch_face_metric(const MetricTables& t, Dims D, int stencil, doubl
 cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double* col, int* piv, int* perm,
                                    int* bad, double* binv, cudaStream_t s) {
     const int m = n + 1;
+    if (m > kMaxGj) return cudaErrorInvalidValue;
     const i64 mm = (i64)m * m;
     k_bordered<<<grid_for(mm, 256), 256, 0, s>>>(A, n, work);
-    for (int k = 0; k < m; ++k) {
-        k_gj_pivot<<<1, 1024, 0, s>>>(work, m, k, col, piv, bad);
-        k_gj_elim<<<grid_for(mm, 256), 256, 0, s>>>(work, m, k, col);
-    }
-    k_gj_perm<<<1, 1, 0, s>>>(piv, m, perm);
-    k_gj_finish<<<grid_for((i64)n * n, 256), 256, 0, s>>>(work, m, perm, binv);
+    // a cooperative grid of one CTA per SM (at most one per row); col holds
+    // the barrier words and the double-buffered candidates
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gj_coop, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || per < 1) return cudaErrorNotSupported;
+    int G = std::min(std::min(sms, m), kGjMaxCtas);
+    unsigned* bar = reinterpret_cast<unsigned*>(col);                 // count, generation
+    double* cand_v = col + 1;                                          // 2 G values
+    int* cand_r = reinterpret_cast<int*>(col + 1 + 2 * G);             // 2 G rows
+    e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    int mv = m;
+    void* args[] = {&work, &mv, &cand_v, &cand_r, &bar, &piv, &perm, &bad};
+    e = cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3(G), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    k_gj_finish<<<grid_for((i64)n * n, 256), 256, 0, s>>>(work, m, piv, perm, binv);
     return cudaGetLastError();
 }
 

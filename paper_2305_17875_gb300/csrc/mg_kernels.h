@@ -50,8 +50,13 @@ cudaError_t launch_line_factors(const LevelView& lv, int prec, void* fac, unsign
 // xline_smooth.cuh); the level needs nph >= 4.
 cudaError_t launch_xline_factors(const LevelView& lv, int prec, void* fac, unsigned* bad, cudaStream_t s);
 // Leading n x n block of [A 1; 1^T 0]^{-1} (A: n x n row-major) by Gauss-Jordan
-// elimination on the device.  work: (n+1)^2 doubles, col: n+1 doubles, piv and
-// perm: n+1 ints each, *bad (zeroed by the caller) set on a zero pivot.
+// elimination on the device, one cooperative launch (n + 1 <= kMaxGj).
+// work: (n+1)^2 doubles, col: kGjScratch doubles (barrier words and pivot
+// candidates), piv and perm: n+1 ints each, *bad (zeroed by the caller) set
+// on a zero pivot (1) or a grid barrier that gave up waiting (2).
+constexpr int kMaxGj = 2049;
+constexpr int kGjMaxCtas = 256;
+constexpr int kGjScratch = 1 + 3 * kGjMaxCtas;
 cudaError_t launch_bordered_inverse(const double* A, int n, double* work, double* col, int* piv, int* perm,
                                    int* bad, double* binv, cudaStream_t s);
 

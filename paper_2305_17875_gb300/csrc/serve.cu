@@ -90,6 +90,12 @@ struct mg_server {
     double t_start = 0, t_plan = 0, t_step = 0, t_retire = 0;
     std::vector<std::thread> workers;
     std::thread stepper;
+    // evicted hierarchies wait here for their last use (an event on the
+    // server stream) and are freed by the reaper thread, off the stepping path
+    std::deque<std::pair<mg_handle*, cudaEvent_t>> reap;
+    std::condition_variable cv_reap;
+    bool reap_stop = false;
+    std::thread reaper;
     mg_status fault = MG_OK;        // a CUDA error stops the server
     std::string fault_msg;
 };
@@ -129,7 +135,49 @@ void release_handle(mg_server* sv, Request* r) {
         }
     }
     r->h = nullptr;
-    for (mg_handle* h : evict) destroy_handle_after(h, sv->stream);   // last used on the server stream
+    if (evict.empty()) return;
+    // last used on the server stream: freed by the reaper once that work is done
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(e, sv->stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (e) cudaEventDestroy(e);
+        for (mg_handle* h : evict) destroy_handle_after(h, sv->stream);
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (size_t i = 0; i < evict.size(); ++i) {
+            cudaEvent_t ei = e;
+            if (i > 0 && (cudaEventCreateWithFlags(&ei, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventRecord(ei, sv->stream) != cudaSuccess)) {
+                cudaGetLastError();
+                ei = nullptr;
+            }
+            sv->reap.emplace_back(evict[i], ei);
+        }
+    }
+    sv->cv_reap.notify_one();
+}
+
+void reaper_loop(mg_server* sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        std::pair<mg_handle*, cudaEvent_t> item;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_reap.wait(lk, [&] { return sv->reap_stop || !sv->reap.empty(); });
+            if (sv->reap.empty()) break;   // stopping and drained
+            item = sv->reap.front();
+            sv->reap.pop_front();
+        }
+        if (item.second) {
+            cudaEventSynchronize(item.second);
+            cudaEventDestroy(item.second);
+            destroy_handle_after(item.first, nullptr);
+        } else {
+            destroy_handle_after(item.first, sv->stream);
+        }
+    }
 }
 
 void worker_loop(mg_server* sv) {
@@ -409,6 +457,7 @@ mg_status mg_serve_create(const mg_serve_opts* opts, mg_server** out) {
     }
     for (int t = 0; t < o.setup_threads; ++t) sv->workers.emplace_back(worker_loop, sv);
     sv->stepper = std::thread(stepper_loop, sv);
+    sv->reaper = std::thread(reaper_loop, sv);
     *out = sv;
     return MG_OK;
 }
@@ -529,6 +578,12 @@ void mg_serve_destroy(mg_server* sv) {
     sv->cv_step.notify_all();
     for (auto& t : sv->workers) t.join();
     if (sv->stepper.joinable()) sv->stepper.join();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->reap_stop = true;
+    }
+    sv->cv_reap.notify_all();
+    if (sv->reaper.joinable()) sv->reaper.join();   // frees what it still holds, then stops
     cudaDeviceSynchronize();
     for (auto& kv : sv->all) {
         Request* r = kv.second;
