@@ -246,6 +246,66 @@ def test_colours_are_independent_sets():
             assert np.all(sub.row == sub.col)
 
 
+def test_gauss_seidel_sweep_is_block_gauss_seidel_in_colour_order():
+    """One multicolour Gauss-Seidel sweep is block Gauss-Seidel over the colour
+    sets taken in order 0, 1 (7 points) or 0, 1, 2, 3 (19 points): with
+    d_c = y_c - x_c the change of colour c, the final residual on colour c is
+    exactly -sum over the later colours c' of A[c, c'] d_c' (the residual of
+    colour c is zero right after its own update).  A swapped colour order, a
+    skipped colour or a wrong diagonal breaks this identity."""
+    rng = np.random.default_rng(11)
+    for stencil, name in ((7, "sphere_stretched"), (19, "triaxial_stretched"), (19, "oblate")):
+        sh = grid.Shell(4, 6, 8, **MAPS[name])
+        lv = mg.make_level(sh.shape, grid.face_metrics(sh), stencil)
+        x0 = rng.standard_normal(lv.n)
+        b = rng.standard_normal(lv.n)
+        _check_block_gauss_seidel(lv, x0, b, stencil, name)
+
+
+def _colour_sets(shape, stencil):
+    """The colour sets of the survey's ordering, from the cell indices:
+    (i + j + k) mod 2 for 7 points, ((i + j) mod 2) + 2 ((j + k) mod 2) for 19."""
+    j, i, k = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    col = ((i + j + k) % 2 if stencil == 7 else (i + j) % 2 + 2 * ((j + k) % 2)).ravel()
+    return [np.nonzero(col == c)[0] for c in range(2 if stencil == 7 else 4)]
+
+
+def _check_block_gauss_seidel(lv, x0, b, stencil, name):
+    y = mg.smooth(lv, x0, b, 1, mg.GS)
+    r = b - lv.A @ y
+    scale = np.abs(lv.A).max() * np.abs(y).max()
+    sets = _colour_sets(lv.shape, stencil)
+    for c, idx in enumerate(sets):
+        want = np.zeros(len(idx))
+        for later in sets[c + 1:]:
+            want -= lv.A[idx][:, later] @ (y[later] - x0[later])
+        np.testing.assert_allclose(r[idx], want, rtol=0, atol=1e-12 * scale, err_msg=f"{name} colour {c}")
+        if c < len(sets) - 1:
+            assert np.abs(r[idx]).max() > 1e-3 * scale       # not an already-converged colour
+    assert np.abs(r[sets[-1]]).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("stencil,factor", [(7, -5.0 / 7.0), (19, -3.0 / 5.0)])
+def test_weighted_jacobi_damps_the_checkerboard_by_one_minus_two_omega(stencil, factor):
+    """On the constant-coefficient operator (G_pp = 1, no cross terms) the
+    checkerboard (-1)^(i+j+k) is an eigenvector at cells away from the walls
+    with D^-1 A e = 2 e, so one weighted-Jacobi step multiplies it by
+    1 - 2 omega: -5/7 for omega = 6/7 (7 points), -3/5 for omega = 4/5
+    (19 points)."""
+    nr, nth, nph = 6, 6, 8
+    fm = {"G0": np.zeros((nr, nth + 1, nph, 3)), "G1": np.zeros((nr + 1, nth, nph, 3)),
+          "G2": np.zeros((nr, nth, nph, 3)), "J": np.ones((nr, nth, nph))}
+    fm["G0"][..., 0] = 1.0
+    fm["G1"][..., 1] = 1.0
+    fm["G2"][..., 2] = 1.0
+    lv = mg.make_level((nr, nth, nph), fm, stencil)
+    j, i, k = np.meshgrid(np.arange(nr), np.arange(nth), np.arange(nph), indexing="ij")
+    e = ((-1.0) ** (i + j + k)).ravel()
+    y = mg.smooth(lv, e, np.zeros(lv.n), 1, mg.JACOBI).reshape(nr, nth, nph)
+    inner = (slice(1, nr - 1), slice(1, nth - 1), slice(None))
+    np.testing.assert_allclose(y[inner], factor * e.reshape(nr, nth, nph)[inner], rtol=0, atol=1e-14)
+
+
 def test_plan_factors_policies():
     sh = sh_of(16, **MAPS["sphere"])
     fm = grid.face_metrics(sh)
@@ -457,6 +517,22 @@ def test_corrected_velocity_is_divergence_free(name):
     D0 = pc.divergence(sh, fm, u)
     D1 = pc.divergence(sh, fm, pc.project(sh, fm, x, u, st))
     assert np.linalg.norm(D1) <= 2e-12 * np.linalg.norm(D0)
+
+
+def test_planted_smoother_mistakes_are_caught():
+    """A reversed colour order and a wrong diagonal each break a smoother pin."""
+    rng = np.random.default_rng(12)
+    sh = grid.Shell(4, 6, 8, **MAPS["triaxial_stretched"])
+    fm = grid.face_metrics(sh)
+    x0, b = rng.standard_normal(sh.n), rng.standard_normal(sh.n)
+    lv = mg.make_level(sh.shape, fm, 19)
+    lv.colours, lv.colour_rows = lv.colours[::-1], lv.colour_rows[::-1]
+    with pytest.raises(AssertionError):
+        _check_block_gauss_seidel(lv, x0, b, 19, "reversed order")
+    lv = mg.make_level(sh.shape, fm, 19)
+    lv.D = lv.D * 1.1
+    with pytest.raises(AssertionError):
+        _check_block_gauss_seidel(lv, x0, b, 19, "wrong diagonal")
 
 
 def test_planted_correction_mistakes_are_caught():
