@@ -450,19 +450,23 @@ mg_status mg_profile_read(mg_handle* h, int slot, double* ms, long long* launche
 /* ---------------------------------------------------------------------------
  * Right-hand-side projection without allocation.  The paper has no
  * counterpart: this is a library convenience for callers that cannot
- * allocate device memory when they need it (inside a CUDA stream capture,
- * in an allocation-free time-step loop, or when another pool owns the GPU's
- * memory).  Computes mean = sum J f / sum J and b = J (f - mean) for caller
- * device arrays J (cell volumes, e.g. from mg_get_metric component 9), f and
- * b of n doubles, and writes the mean to the caller's device double mean_dev
- * (may be NULL).  Work is queued on cuda_stream (a cudaStream_t; NULL = the
- * legacy default stream); the call does not synchronise.
+ * allocate device memory when they need it (a time-step loop that must not
+ * stall on the allocator, or a program whose GPU memory is owned by another
+ * pool or a framework's caching allocator).  Computes mean = sum J f / sum J
+ * and b = J (f - mean) for caller device arrays J (cell volumes, e.g. from
+ * mg_get_metric component 9), f and b of n doubles on the current device, and
+ * writes the mean to the caller's device double mean_dev (may be NULL).  Work
+ * is queued on cuda_stream (a cudaStream_t; NULL = the legacy default
+ * stream); the call does not synchronise.
  * No allocation: the reduction scratch is a 128 KB static device array in
  * the library, present on every GPU that loads it until the process exits.
  * n must not exceed 4,194,304 cells (MG_EINVAL otherwise, with the limit in
- * mg_last_error()).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.
+ * mg_last_error()); arrays that are not memory of the current device are
+ * refused with MG_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it for that device index
+ * (not per context; a device reset needs a new process); make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race.
  * ------------------------------------------------------------------------- */
 mg_status mg_project_rhs_noalloc(const double* J_dev, const double* f_dev, double* b_dev, long long n,
                                  void* cuda_stream, double* mean_dev);

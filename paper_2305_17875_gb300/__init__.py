@@ -502,14 +502,20 @@ def mg_serve_destroy(sv: Server):
 
 def mg_project_rhs_noalloc(J, f, b, mean=None, stream=None):
     """b = J (f - mean_J f) with no device allocation (the library's static
-    scratch holds the partial sums); for callers that cannot allocate, e.g.
-    inside a stream capture.  J, f, b: float64 device tensors of one size;
-    mean: optional float64 device tensor of one element."""
+    scratch holds the partial sums), for callers that cannot allocate when
+    they need the step (a time loop that must not stall on the allocator, or
+    a program whose GPU memory belongs to another pool).  J, f, b: float64
+    tensors of one size on one CUDA device; mean: optional float64 tensor of
+    one element there.  The call runs with the tensors' device current;
+    stream=None means torch.cuda.current_stream() of that device (not the
+    legacy default stream the C call takes for NULL)."""
+    import torch
     n = J.numel()
     if f.numel() != n or b.numel() != n:
         raise ValueError("J, f and b must have the same size")
-    _check(_lib.mg_project_rhs_noalloc(_ptr(J, "float64"), _ptr(f, "float64"), _ptr(b, "float64"), n,
-                                       _stream(stream), _ptr(mean, "float64")), "mg_project_rhs_noalloc")
+    with torch.cuda.device(J.device):
+        _check(_lib.mg_project_rhs_noalloc(_ptr(J, "float64"), _ptr(f, "float64"), _ptr(b, "float64"), n,
+                                           _stream(stream), _ptr(mean, "float64")), "mg_project_rhs_noalloc")
 
 
 def exported_symbols():

@@ -1,19 +1,28 @@
 // noalloc.cu - the right-hand-side projection without any allocation.
 //
 // Some callers cannot allocate device memory at the moment they need this
-// step: code that runs while a CUDA stream capture is open (cudaMalloc is
-// not permitted inside a capture), latency-critical time-step loops that must
-// not stall on the allocator, and host programs whose device memory is owned
-// by another pool (a simulation that reserved most of the GPU for its own
-// fields, or a framework's caching allocator).  For them this file computes
-// b = J (f - mean_J f) with its reduction scratch in a fixed static device
-// array instead of allocated memory.
+// step: time-step loops that must not stall on the allocator (cudaMalloc can
+// synchronise the device and takes driver locks), and host programs whose
+// device memory is owned by another pool (a simulation that reserved most of
+// the GPU for its own fields up front, or a framework's caching allocator
+// that must see every byte).  For them this file computes b = J (f - mean_J f)
+// with its reduction scratch in a fixed static device array instead of
+// allocated memory.
 //
 // The array is file-scope and every GPU that loads the library holds it until
 // the process exits.  All calls share it and it keeps the last call's
 // partial sums; each call overwrites every entry it reads before reading it,
 // so nothing has to start at zero.  Calls that overlap on the GPU (different
 // streams, or host threads without ordering) race on the array.
+//
+// Host code cannot hand the array's name to a kernel (in host code it is a
+// stand-in, not a device address): its device address is looked up with
+// cudaGetSymbolAddress on the first call on each device, with that device
+// current, and kept per device index.  The cache is keyed by the device
+// index, not by the context: a caller that drives a device through a context
+// other than its primary one gets the primary context's address, and after a
+// cudaDeviceReset the cached address is stale (restart the process).
+#include <atomic>
 #include <cstdio>
 #include <string>
 
@@ -74,9 +83,10 @@ __global__ void __launch_bounds__(kNaThreads) k_na_project(const double* __restr
     if (c < n) b[c] = J[c] * (f[c] - mean);
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device (host
+// threads may race on the first lookup: both find the same address).
 constexpr int kNaMaxDevices = 64;
-double* g_scratch_ptr[kNaMaxDevices] = {};
+std::atomic<double*> g_scratch_ptr[kNaMaxDevices] = {};
 
 mg_status scratch_for_current_device(double** out) {
     int dev = 0;
@@ -89,16 +99,37 @@ mg_status scratch_for_current_device(double** out) {
         set_error("device index out of range for the static scratch table");
         return MG_EINVAL;
     }
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    double* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
         if (e != cudaSuccess) {
             set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
             return MG_ECUDA;
         }
-        g_scratch_ptr[dev] = (double*)p;
+        p = (double*)q;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
+    return MG_OK;
+}
+
+// A caller array must be device memory of the current device: the kernels
+// run there (cudaPointerGetAttributes allocates nothing).
+mg_status check_on_device(const void* ptr, int dev, const char* name) {
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("mg_project_rhs_noalloc: ") + name + " is not a CUDA pointer");
+        return MG_EINVAL;
+    }
+    const bool device_mem = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (!device_mem || (a.type == cudaMemoryTypeDevice && a.device != dev)) {
+        set_error(std::string("mg_project_rhs_noalloc: ") + name + " is not memory of the current device " +
+                  std::to_string(dev));
+        return MG_EINVAL;
+    }
     return MG_OK;
 }
 
@@ -118,8 +149,14 @@ extern "C" mg_status mg_project_rhs_noalloc(const double* J_dev, const double* f
         return MG_EINVAL;
     }
     double* scratch = nullptr;
-    const mg_status st = scratch_for_current_device(&scratch);
+    mg_status st = scratch_for_current_device(&scratch);
     if (st != MG_OK) return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if ((st = check_on_device(J_dev, dev, "J")) != MG_OK || (st = check_on_device(f_dev, dev, "f")) != MG_OK ||
+        (st = check_on_device(b_dev, dev, "b")) != MG_OK ||
+        (mean_dev && (st = check_on_device(mean_dev, dev, "mean")) != MG_OK))
+        return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int nb = (int)((n + kNaThreads - 1) / kNaThreads);
     k_na_partials<<<nb, kNaThreads, 0, s>>>(J_dev, f_dev, (int)n, scratch);
