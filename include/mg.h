@@ -55,7 +55,8 @@ enum { MG_MAP_SPHERE = 0, MG_MAP_OBLATE = 1, MG_MAP_TRIAXIAL = 2 };
 enum { MG_PREC_FP64 = 0,        /* plain FP64 multigrid */
        MG_PREC_FP32_IR = 1,     /* FP32 V-cycles inside FP64 iterative refinement */
        MG_PREC_FP16C_IR = 2 };  /* FP16 coefficients, FP32 arithmetic, inside FP64 IR */
-enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1, MG_SMOOTH_LINE = 2, MG_SMOOTH_XLINE = 3, MG_SMOOTH_ALT = 4 };
+enum { MG_SMOOTH_GS = 0, MG_SMOOTH_JACOBI = 1, MG_SMOOTH_LINE = 2, MG_SMOOTH_XLINE = 3, MG_SMOOTH_ALT = 4,
+       MG_SMOOTH_PLANE = 5 };
 enum { MG_METRIC_DISCRETE = 0, MG_METRIC_ANALYTIC = 1 };
 enum { MG_COARSEN_SEMI = 0, MG_COARSEN_FULL = 1 };
 
@@ -95,7 +96,18 @@ typedef struct {
                            on it; lines coloured (i+j) mod 2 for 7 points, (i mod 2) +
                            2 (j mod 2) for 19 points; a level with fewer than four
                            longitudes takes a point sweep instead); ALT = one LINE sweep
-                           then one XLINE sweep per smoothing step */
+                           then one XLINE sweep per smoothing step; PLANE = the
+                           semi-coarsening multigrid of Section 3.6: the hierarchy halves
+                           the colatitude only (down to one plane, which the dense
+                           bordered solve takes, so it must hold at most 2048 cells),
+                           and the smoother is zebra plane relaxation (every (radius,
+                           longitude) plane of fixed colatitude row one block, even rows
+                           first), each plane solved by plane_cycles V(1,1) cycles of a
+                           2-D multigrid (radius halved down to one row, coarse plane
+                           operators R B P, zebra longitude lines by the periodic
+                           Thomas algorithm of Section 3.5).  7-point operator only,
+                           nr a power of two; the coarse-level and coarsening options
+                           (max_levels, coarsen, coarse_max) are not used */
     int nu1, nu2;       /* pre/post sweeps, default 2, 2 */
     int max_levels;     /* default 16 */
     int coarsen;        /* MG_COARSEN_*, default SEMI */
@@ -112,6 +124,7 @@ typedef struct {
                            the mapping at the face centres, steps 2-5 unchanged (an O(h^2)
                            different operator).  The pressure-correction steps and the ADI
                            sweeps need the discrete metric (MG_EINVAL otherwise). */
+    int plane_cycles;   /* PLANE smoother: 2-D cycles per plane solve, default 1 */
 } mg_opts;
 
 #define MG_HIST 64

@@ -27,7 +27,7 @@ STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_EN
           5: "MG_EDIVERGED", 6: "MG_ETIMEOUT", 7: "MG_EAGAIN", 8: "MG_ECUDA"}
 PREC_FP64, PREC_FP32_IR, PREC_FP16C_IR = 0, 1, 2
 MG_HIST = 64
-MG_SMOOTH_GS, MG_SMOOTH_JACOBI, MG_SMOOTH_LINE, MG_SMOOTH_XLINE, MG_SMOOTH_ALT = range(5)
+MG_SMOOTH_GS, MG_SMOOTH_JACOBI, MG_SMOOTH_LINE, MG_SMOOTH_XLINE, MG_SMOOTH_ALT, MG_SMOOTH_PLANE = range(6)
 MG_METRIC_DISCRETE, MG_METRIC_ANALYTIC = range(2)
 
 
@@ -42,7 +42,8 @@ class mg_grid_desc(C.Structure):
 class mg_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_levels", C.c_int), ("coarsen", C.c_int), ("coarse_max", C.c_int),
-                ("max_iters", C.c_int), ("stencil", C.c_int), ("autotune", C.c_int), ("metric", C.c_int)]
+                ("max_iters", C.c_int), ("stencil", C.c_int), ("autotune", C.c_int), ("metric", C.c_int),
+                ("plane_cycles", C.c_int)]
 
 
 class mg_lines(C.Structure):

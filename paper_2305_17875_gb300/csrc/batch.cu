@@ -13,6 +13,7 @@
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
 #include "xline_smooth.cuh"
+#include "plane_smooth.cuh"
 
 namespace mgs {
 
@@ -599,6 +600,22 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
             xline_pass_chunked<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
         else
             xline_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour, first, stride);
+    } else if constexpr (OP == BOP_PRES) {
+        plane_res3d<T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, (T*)tk.y, (T*)tk.z, colour, first, stride);
+    } else if constexpr (OP == BOP_PRELAX || OP == BOP_PRESTRICT) {
+        // the plane operator of a 2-D level: FP64 arrays for the FP64 cycle, FP32 copies otherwise
+        const T* const* pc = (const T* const*)(P == PREC64 ? (const void* const*)tk.v.c64.g
+                                                           : (const void* const*)tk.v.c32.g);
+        if constexpr (OP == BOP_PRELAX)
+            plane_relax<T>(pc, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour & 1, colour >> 1,
+                           first, stride);
+        else
+            plane_restrict<T>(pc, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, (T*)tk.y, (T*)tk.z, colour, first,
+                              stride);
+    } else if constexpr (OP == BOP_PPROLONG) {
+        plane_prolong<T>(tk.v.D, (T*)tk.x, tk.Dc, (const T*)tk.b, colour, first, stride);
+    } else if constexpr (OP == BOP_PUPDATE) {
+        plane_update<T>(tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
     } else if constexpr (OP == BOP_JACOBI) {
         jacobi_pass<S, T>(cf, tk.v.D, (const T*)tk.x, (T*)tk.y, (const T*)tk.b, first, stride);
     } else if constexpr (OP == BOP_RESTRICT) {
@@ -862,6 +879,11 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
         PLAIN_OP(BOP_SHIFT)
         PLAIN_OP(BOP_FINALIZE)
         PLAIN_OP(BOP_COARSE)
+        PLAIN_OP(BOP_PRES)
+        PLAIN_OP(BOP_PRELAX)
+        PLAIN_OP(BOP_PRESTRICT)
+        PLAIN_OP(BOP_PPROLONG)
+        PLAIN_OP(BOP_PUPDATE)
         default:
             return cudaErrorInvalidValue;
     }

@@ -15,6 +15,7 @@
 #include "engine.h"
 #include "pc.h"
 #include "line_smooth.cuh"
+#include "plane_smooth.cuh"
 
 using namespace mgs;
 
@@ -114,7 +115,9 @@ std::string check_grid(const mg_grid_desc* g) {
 std::string check_opts(const mg_opts* o) {
     if (!o) return "opts is NULL";
     if (o->precision < 0 || o->precision > 2) return "precision must be 0, 1 or 2";
-    if (o->smoother < 0 || o->smoother > 4) return "smoother must be 0 .. 4";
+    if (o->smoother < 0 || o->smoother > 5) return "smoother must be 0 .. 5";
+    if (o->smoother == MG_SMOOTH_PLANE && (o->plane_cycles < 1 || o->plane_cycles > 64))
+        return "plane_cycles must be in 1..64";
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 > 64) return "bad nu1/nu2";
     if (o->max_levels < 1 || o->max_levels > 32) return "max_levels must be in 1..32";
     if (o->coarsen < 0 || o->coarsen > 1) return "coarsen must be 0 or 1";
@@ -134,6 +137,16 @@ int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
 // Combinations of a valid grid and valid options that are not built.
 std::string check_pair(const mg_grid_desc* g, const mg_opts* o) {
     if (g->cut && stencil_of(g, o) != 7) return "the shell cut is built for the 7-point operator only";
+    if (o->smoother == MG_SMOOTH_PLANE) {
+        if (stencil_of(g, o) != 7) return "plane relaxation is built for the 7-point operator only";
+        if (g->nr & (g->nr - 1)) return "plane relaxation needs nr a power of two (the plane cycles end on one row)";
+        long long nth = g->nth;
+        while (nth % 2 == 0 && nth > 1) nth /= 2;   // the colatitude-only hierarchy ends here
+        if ((long long)g->nr * nth * g->nph > kMaxCoarse)
+            return "plane relaxation: the coarsest level (" + std::to_string(g->nr) + " x " + std::to_string(nth) +
+                   " x " + std::to_string(g->nph) + ") exceeds the dense bordered solve (" +
+                   std::to_string(kMaxCoarse) + " cells)";
+    }
     return "";
 }
 
@@ -308,6 +321,56 @@ mg_status ensure_xline_factors(mg_handle* h, int prec) {
     return MG_OK;
 }
 
+// Plane hierarchies of every level above the coarsest (the semi-coarsening
+// multigrid's smoother): the plane operator of the level (FP64), its radius
+// coarsening R B P down to one row, the cycle-precision copies, the
+// longitude-line factors and the work arrays of every 2-D level.
+mg_status build_planes(mg_handle* h) {
+    const bool f32 = h->prec != PREC64;
+    const size_t vb = f32 ? sizeof(float) : sizeof(double);
+    TmpDev tb(sizeof(unsigned), h->stream, h->device);
+    if (!tb.p) return MG_ENOMEM;
+    CK(cudaMemsetAsync(tb.p, 0, sizeof(unsigned), h->stream));
+    for (size_t l = 0; l + 1 < h->L.size(); ++l) {
+        Level& lv = h->L[l];
+        lv.planes.clear();
+        Dims D = lv.D;
+        for (int m = 0;; ++m) {
+            PlaneLevel P;
+            P.D = D;
+            const i64 n = D.n();
+            for (int o = 0; o < 9; ++o) {
+                if (!(P.c64[o] = (double*)dalloc(h, sizeof(double) * n))) return MG_ENOMEM;
+                if (f32 && !(P.c32[o] = (float*)dalloc(h, sizeof(float) * n))) return MG_ENOMEM;
+            }
+            if (!(P.fac = dalloc(h, 4 * vb * n)) || !(P.e = dalloc(h, vb * n)) || !(P.r = dalloc(h, vb * n)) ||
+                !(P.w = dalloc(h, vb * n)))
+                return MG_ENOMEM;
+            if (m == 0) {
+                CK(launch_plane_op0(lv.view(h->stencil), P.c64, h->stream));
+            } else {
+                const PlaneLevel& F = lv.planes.back();
+                CK(launch_plane_coarsen(F.c64, F.D, D, P.c64, h->stream));
+            }
+            if (f32)
+                for (int o = 0; o < 9; ++o) CK(launch_cast32(P.c64[o], P.c32[o], n, h->stream));
+            CK(launch_plane_factors(P.c64, D, h->prec, P.fac, (unsigned*)tb.p, h->stream));
+            lv.planes.push_back(P);
+            if (D.nr % 2 || D.nr < 2) break;   // one row: the plane cycles end here
+            D = Dims{D.nr / 2, D.nth, D.nph};
+            D.cut = lv.D.cut;
+        }
+    }
+    unsigned hb = 0;
+    CK(cudaMemcpyAsync(&hb, tb.p, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hb) {
+        set_error("a longitude line of a plane operator has a zero pivot");
+        return MG_EINVAL;
+    }
+    return MG_OK;
+}
+
 // The outer loop converts between FP64 and FP32 on the integer pipes; check
 // those conversions against the hardware ones once per device and process.
 mg_status conversion_check(mg_handle* h) {
@@ -331,6 +394,12 @@ mg_status conversion_check(mg_handle* h) {
 
 // Longest-first plan of the next level: which directions halve.
 mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
+    if (h->opts.smoother == MG_SMOOTH_PLANE) {   // semi-coarsening: the colatitude only, down to one plane
+        *ok = lv.D.nth % 2 == 0 && lv.D.nth > 1;
+        f[0] = *ok ? 2 : 1;
+        f[1] = f[2] = 1;
+        return MG_OK;
+    }
     const int n[3] = {lv.D.nth, lv.D.nr, lv.D.nph};
     bool can[3];
     for (int d = 0; d < 3; ++d) can[d] = n[d] % 2 == 0 && n[d] >= 4 && (d != 2 || n[d] % 4 == 0);
@@ -660,7 +729,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     h->L.push_back(L0);
 
     // --- hierarchy by face-metric aggregation
-    while ((int)h->L.size() < o->max_levels && h->L.back().D.n() > o->coarse_max) {
+    const bool plane = o->smoother == MG_SMOOTH_PLANE;   // coarsens to one plane whatever the size
+    while (plane || ((int)h->L.size() < o->max_levels && h->L.back().D.n() > o->coarse_max)) {
         int f[3];
         bool ok;
         CKS(plan_next(h, h->L.back(), f, &ok));
@@ -735,6 +805,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
 
     if (radial_lines(o->smoother)) CKS(ensure_line_factors(h, h->prec));
     if (longitude_lines(o->smoother)) CKS(ensure_xline_factors(h, h->prec));
+    if (o->smoother == MG_SMOOTH_PLANE) CKS(build_planes(h));
 
     // --- coarsest level: dense operator -> bordered inverse (device, FP64)
     const int nc = h->ncoarse;
@@ -878,6 +949,73 @@ void prof_collect(mg_handle* h) {
     h->prof_pending.clear();
 }
 
+void plane_sweep_steps(const mg_handle* h, int level, void* x, const void* b, std::vector<PlaneStep>& out) {
+    const Level& lv = h->L[level];
+    const std::vector<PlaneLevel>& P = lv.planes;
+    const int M = (int)P.size() - 1;
+    auto vb = [](i64 work) {
+        i64 n = (work + 255) / 256;
+        return (int)std::max<i64>(1, std::min<i64>(n, 152 * 16));
+    };
+    auto two_d = [&](int m) {   // a task over 2-D level m
+        BTask t{};
+        t.v.D = P[m].D;
+        t.v.stencil = 7;
+        for (int o = 0; o < 9; ++o) {
+            t.v.c64.g[o] = P[m].c64[o];
+            t.v.c32.g[o] = P[m].c32[o];
+        }
+        t.x = P[m].e;
+        t.b = P[m].r;
+        t.z = P[m].fac;
+        t.y = P[m].w;
+        return t;
+    };
+    auto relax = [&](int m, int p, int q) {
+        const Dims& D = P[m].D;
+        const i64 lines = (i64)((D.nth + 1 - p) >> 1) * ((D.nr + 1 - q) >> 1);
+        if (lines > 0) out.push_back(PlaneStep{BOP_PRELAX, p + 2 * q, two_d(m), vb(lines)});
+    };
+    for (int p = 0; p < 2; ++p) {
+        if (plane_cells(lv.D, p) == 0) continue;
+        {   // the 3-D residual on the planes of parity p, e of 2-D level 0 zeroed
+            BTask t{};
+            t.v = lv.view(h->stencil);
+            t.x = x;
+            t.b = b;
+            t.y = P[0].r;
+            t.z = P[0].e;
+            out.push_back(PlaneStep{BOP_PRES, p, t, vb(plane_cells(lv.D, p))});
+        }
+        for (int c = 0; c < h->opts.plane_cycles; ++c) {
+            for (int m = 0; m < M; ++m) {
+                relax(m, p, 0);
+                relax(m, p, 1);
+                BTask t = two_d(m);
+                t.Dc = P[m + 1].D;
+                t.y = P[m + 1].r;
+                t.z = P[m + 1].e;
+                out.push_back(PlaneStep{BOP_PRESTRICT, p, t, vb(plane_cells(P[m + 1].D, p))});
+            }
+            relax(M, p, 0);   // one row from zero: the exact solve
+            relax(M, p, 1);   // (no rows of odd index on one row)
+            for (int m = M - 1; m >= 0; --m) {
+                BTask t = two_d(m);
+                t.Dc = P[m + 1].D;
+                t.b = P[m + 1].e;
+                out.push_back(PlaneStep{BOP_PPROLONG, p, t, vb(plane_cells(P[m].D, p))});
+                relax(m, p, 0);
+                relax(m, p, 1);
+            }
+        }
+        BTask t{};
+        t.v.D = lv.D;
+        t.x = x;
+        t.b = P[0].e;
+        out.push_back(PlaneStep{BOP_PUPDATE, p, t, vb(plane_cells(lv.D, p))});
+    }
+}
+
 bool sweep_tile_for(const mg_handle* h, int level, int tile[3]) {
     if (!h->one_pass || h->opts.smoother != MG_SMOOTH_GS || level < 0 || level >= (int)h->L.size()) return false;
     const Dims& D = h->L[level].D;
@@ -941,6 +1079,25 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
         if (sweeps & 1) {
             CK(cudaMemcpyAsync(x, lv.t, value_bytes(prec) * lv.D.n(), cudaMemcpyDeviceToDevice, h->stream));
         }
+    } else if (kind == MG_SMOOTH_PLANE) {
+        std::vector<PlaneStep> st;
+        plane_sweep_steps(h, level, x, b, st);
+        if (st.size() > h->plane_tasks_cap) {
+            if (!(h->plane_tasks = (BTask*)dalloc(h, sizeof(BTask) * st.size()))) return MG_ENOMEM;
+            h->plane_tasks_cap = st.size();
+        }
+        std::vector<BTask> tasks(st.size());
+        for (size_t i = 0; i < st.size(); ++i) {
+            tasks[i] = st[i].t;
+            tasks[i].block0 = 0;
+            tasks[i].nblocks = st[i].nblocks;
+        }
+        CK(cudaMemcpyAsync(h->plane_tasks, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice,
+                           h->stream));
+        for (int sw = 0; sw < sweeps; ++sw)
+            for (size_t i = 0; i < st.size(); ++i, ++n)
+                CK(launch_batch(h->plane_tasks + i, 1, st[i].nblocks, nullptr, st[i].op, st[i].colour, 7, prec,
+                                h->stream));
     } else if (kind == MG_SMOOTH_GS) {
         const int ncol = h->stencil == 7 ? 2 : 4;
         for (int s = 0; s < sweeps; ++s)
@@ -1081,6 +1238,7 @@ mg_status mg_default_opts(mg_opts* o) {
     o->stencil = 0;
     o->autotune = 1;
     o->metric = MG_METRIC_DISCRETE;
+    o->plane_cycles = 1;
     return MG_OK;
 }
 
@@ -1236,7 +1394,12 @@ mg_status mg_apply(mg_handle* h, int level, int prec, const void* x, void* y) {
 
 mg_status mg_smooth(mg_handle* h, int level, int prec, void* x, const void* b, int sweeps, int kind) {
     LEVEL_CHECK(h, level, prec);
-    if (!x || !b || sweeps < 0 || kind < 0 || kind > 4) return MG_EINVAL;
+    if (!x || !b || sweeps < 0 || kind < 0 || kind > 5) return MG_EINVAL;
+    if (kind == MG_SMOOTH_PLANE && (h->opts.smoother != MG_SMOOTH_PLANE || prec != h->prec ||
+                                    level + 1 >= (int)h->L.size())) {
+        set_error("plane relaxation: a handle set up with the PLANE smoother, its own precision, a level above the coarsest");
+        return MG_EINVAL;
+    }
     StreamJoin join(h);
     return smooth(h, level, prec, x, b, sweeps, kind);
 }

@@ -12,6 +12,18 @@ namespace mgs {
 
 struct Plan;
 
+// One 2-D level of the plane hierarchy of a 3-D level (all its planes at
+// once): nr >> m rows in the 3-D layout.
+struct PlaneLevel {
+    Dims D{};
+    double* c64[9] = {};   // plane operator (set-up, plain FP64 cycles)
+    float* c32[9] = {};    // FP32 copy (FP32 and FP16-coefficient cycles)
+    void* fac = nullptr;   // longitude-line factors, 4 n values of the cycle's type
+    void* e = nullptr;     // correction, right side, line scratch (cycle's type)
+    void* r = nullptr;
+    void* w = nullptr;
+};
+
 struct Level {
     Dims D{};
     int cz = 0, ce = 0, cx = 0;       // halving factors to the next level
@@ -26,6 +38,7 @@ struct Level {
     void* t = nullptr;   // scratch (Jacobi)
     void* lf[2] = {};    // radial-line factors, double / float (3 n values), made on first use
     void* xf[2] = {};    // longitude-line factors, double / float (4 n values), made on first use
+    std::vector<PlaneLevel> planes;   // plane hierarchy (semi-coarsening multigrid), made at set-up
     LevelView view(int stencil) const;
 };
 
@@ -94,6 +107,8 @@ struct mg_handle {
     double sched_ms = 0.0;
     mgs::BTask* one_task = nullptr;   // task table of stand-alone one-pass sweeps
     void* one_map = nullptr;          // tensor map of a stand-alone one-pass sweep (128 bytes)
+    mgs::BTask* plane_tasks = nullptr;    // task table of stand-alone plane relaxations
+    size_t plane_tasks_cap = 0;
     int tail_level = 0;               // first level of the single-launch coarse tail (0: none)
     int tail_cluster = 8;             // CTAs per tail cluster
     mgs::TailTask* tail_dev = nullptr;
@@ -156,5 +171,13 @@ double model_bytes_per_iteration(const mg_handle* h);
 bool sweep_tile_for(const mg_handle* h, int level, int tile[3]);
 // smoothers that sweep radial lines / longitude lines (the alternating one both)
 inline bool radial_lines(int smoother) { return smoother == MG_SMOOTH_LINE || smoother == MG_SMOOTH_ALT; }
+// One sweep of zebra plane relaxation of level `level` (x, b in the cycle's
+// type): the launches in order, each one task over the planes of one parity.
+struct PlaneStep {
+    int op, colour;
+    BTask t;
+    int nblocks;
+};
+void plane_sweep_steps(const mg_handle* h, int level, void* x, const void* b, std::vector<PlaneStep>& out);
 inline bool longitude_lines(int smoother) { return smoother == MG_SMOOTH_XLINE || smoother == MG_SMOOTH_ALT; }
 }  // namespace mgs

@@ -142,7 +142,14 @@ enum {
     BOP_COARSE,       // x = binv b, n rows
     BOP_SWEEP,        // one whole multicolour sweep, x -> y (sweep.cu; launched by launch_sweep)
     BOP_LINE,         // radial-line Gauss-Seidel colour pass: x, b, z = line factors
-    BOP_XLINE         // longitude-line Gauss-Seidel colour pass: x, b, z = factors, y = scratch
+    BOP_XLINE,        // longitude-line Gauss-Seidel colour pass: x, b, z = factors, y = scratch
+    // plane relaxation of the semi-coarsening multigrid (plane_smooth.cuh);
+    // colour = plane parity p (+ 2 q for the row parity q of BOP_PRELAX)
+    BOP_PRES,         // y = b - A x (7-point, 3-D level) on the planes, z (2-D e) zeroed
+    BOP_PRELAX,       // zebra longitude lines of a 2-D level: x = e, b = r, z = factors, y = scratch
+    BOP_PRESTRICT,    // y = R (b - B x) on the next 2-D level (dims Dc), z = its e zeroed
+    BOP_PPROLONG,     // x += P b (b = the next 2-D level's e, dims Dc)
+    BOP_PUPDATE       // x += b on the planes (3-D level)
 };
 struct BTask {
     LevelView v;       // level of the task (dims, factors, coefficients, stencil)
@@ -183,6 +190,17 @@ cudaError_t launch_sweep(const BTask* tasks, int ntasks, int total, const int* a
 // The fault word of the sweeps (a plane copy that did not land in time);
 // clear resets it.
 cudaError_t sweep_fault_read(unsigned* out, bool clear);
+
+// ---- plane hierarchies of the semi-coarsening multigrid (smg.cu).  A 2-D
+// level uses the 3-D layout with nr >> m rows; its plane operator is nine
+// arrays in the order of plane_smooth.cuh's offsets.
+cudaError_t launch_plane_op0(const LevelView& lv, double* const out[9], cudaStream_t s);
+cudaError_t launch_plane_coarsen(const double* const fine[9], const Dims& D, const Dims& Dc, double* const out[9],
+                                 cudaStream_t s);
+// Periodic longitude-line factors (4 n values of the cycle's type of prec);
+// *bad (zeroed by the caller) counts zero or non-finite pivots.
+cudaError_t launch_plane_factors(const double* const c[9], const Dims& D, int prec, void* fac, unsigned* bad,
+                                 cudaStream_t s);
 
 // Checks the integer-pipe FP64 <-> FP32 conversions (narrow_rn, scaled_widen)
 // against the hardware ones; *bad (zeroed by the caller) counts mismatches.

@@ -59,10 +59,10 @@ struct Request {
 
 std::string key_of(const mg_grid_desc& g, const mg_opts& o) {
     char buf[512];
-    std::snprintf(buf, sizeof(buf), "%d %d %d %.17g %.17g %.17g %.17g %d %.17g %.17g %.17g %d | %d %d %d %d %d %d %d %d %d %d",
+    std::snprintf(buf, sizeof(buf), "%d %d %d %.17g %.17g %.17g %.17g %d %.17g %.17g %.17g %d | %d %d %d %d %d %d %d %d %d %d %d",
                   g.nr, g.nth, g.nph, g.r_in, g.r_out, g.th0, g.th1, g.mapping, g.flattening, g.e2, g.stretch, g.cut,
                   o.precision, o.smoother, o.nu1, o.nu2, o.max_levels, o.coarsen, o.coarse_max, o.max_iters,
-                  o.stencil, o.metric);
+                  o.stencil, o.metric, o.plane_cycles);
     return buf;
 }
 

@@ -312,6 +312,27 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
                 P.add(t, vblocks(h, vector_items(t.n)));
             }
         }
+        // zebra plane relaxation (semi-coarsening multigrid): each handle's
+        // launches in order (plane hierarchies differ from handle to handle)
+        for (size_t s = 0; s < pl->hs.size(); ++s) {
+            mg_handle* h = pl->hs[s];
+            if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_PLANE) continue;
+            void* xb;
+            const void* bb;
+            level_bufs(h, prec, level, &xb, &bb);
+            std::vector<PlaneStep> st;
+            plane_sweep_steps(h, level, xb, bb, st);
+            for (const PlaneStep& q : st) {
+                Launch& L = P.begin(q.op, q.colour, 7);
+                if (level == 0) {
+                    L.prof = MG_PROF_SMOOTH0;
+                    L.prof_n = 1;
+                }
+                BTask t = q.t;
+                t.shell = (int)s;
+                P.add(t, q.nblocks);
+            }
+        }
     }
     if (any_fused && (sweeps & 1)) {   // an odd count ends in the scratch: copy back
         P.begin(BOP_COPY);
