@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-grid DOF/s to 1e-10 rel. residual, FP32-refined vs FP64 MG; HBM GB/s; p99 ms"
 UNIT = "DOF/s"
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2}
-SMOOTHER = {"gs": 0, "jacobi": 1, "line": 2, "xline": 3, "alt": 4}
+SMOOTHER = {"gs": 0, "jacobi": 1, "line": 2, "xline": 3, "alt": 4, "plane": 5}
 PREC_NAME = {0: "plain FP64 multigrid", 1: "FP32 V-cycles inside FP64 refinement",
              2: "FP16-coefficient FP32 V-cycles inside FP64 refinement"}
 L2_FLUSH_BYTES = 256 << 20
@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--smoother", default="gs", choices=list(SMOOTHER),
                    help="gs: multicolour Gauss-Seidel; jacobi; line: radial-line Gauss-Seidel; "
-                        "xline: longitude-line Gauss-Seidel; alt: radial then longitude lines")
+                        "xline: longitude-line Gauss-Seidel; alt: radial then longitude lines; "
+                        "plane: semi-coarsening multigrid with zebra plane relaxation, V(1,1)")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 multigrid leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-c3", action="store_true", help="skip the 256 x 256 x 512 oblate-shell leg")
@@ -509,6 +510,8 @@ def run_ours(args, rank, world, local_rank):
     g, f = w["grid"], w["f"]
     N = g["nr"] * g["nth"] * g["nph"]
     sopts = dict(precision=prec, smoother=smoother)
+    if smoother == SMOOTHER["plane"]:
+        sopts.update(nu1=1, nu2=1)          # the semi-coarsening multigrid's V(1,1)
     if "max_levels" in w:
         sopts["max_levels"] = w["max_levels"]
     if w.get("coarsen") == "full":

@@ -607,8 +607,8 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         const T* const* pc = (const T* const*)(P == PREC64 ? (const void* const*)tk.v.c64.g
                                                            : (const void* const*)tk.v.c32.g);
         if constexpr (OP == BOP_PRELAX)
-            plane_relax<T>(pc, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, (T*)tk.y, colour & 1, colour >> 1,
-                           first, stride);
+            plane_relax_warp<T>(pc, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour & 1, colour >> 1, first,
+                                stride);
         else
             plane_restrict<T>(pc, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, (T*)tk.y, (T*)tk.z, colour, first,
                               stride);

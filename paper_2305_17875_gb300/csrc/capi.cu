@@ -140,12 +140,7 @@ std::string check_pair(const mg_grid_desc* g, const mg_opts* o) {
     if (o->smoother == MG_SMOOTH_PLANE) {
         if (stencil_of(g, o) != 7) return "plane relaxation is built for the 7-point operator only";
         if (g->nr & (g->nr - 1)) return "plane relaxation needs nr a power of two (the plane cycles end on one row)";
-        long long nth = g->nth;
-        while (nth % 2 == 0 && nth > 1) nth /= 2;   // the colatitude-only hierarchy ends here
-        if ((long long)g->nr * nth * g->nph > kMaxCoarse)
-            return "plane relaxation: the coarsest level (" + std::to_string(g->nr) + " x " + std::to_string(nth) +
-                   " x " + std::to_string(g->nph) + ") exceeds the dense bordered solve (" +
-                   std::to_string(kMaxCoarse) + " cells)";
+        if (g->nph > 512) return "plane relaxation: at most 512 longitudes (a warp solves a line in chunks of 16)";
     }
     return "";
 }
@@ -331,7 +326,7 @@ mg_status build_planes(mg_handle* h) {
     TmpDev tb(sizeof(unsigned), h->stream, h->device);
     if (!tb.p) return MG_ENOMEM;
     CK(cudaMemsetAsync(tb.p, 0, sizeof(unsigned), h->stream));
-    for (size_t l = 0; l + 1 < h->L.size(); ++l) {
+    for (size_t l = 0; l < (size_t)h->plane_levels; ++l) {
         Level& lv = h->L[l];
         lv.planes.clear();
         Dims D = lv.D;
@@ -394,10 +389,24 @@ mg_status conversion_check(mg_handle* h) {
 
 // Longest-first plan of the next level: which directions halve.
 mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
-    if (h->opts.smoother == MG_SMOOTH_PLANE) {   // semi-coarsening: the colatitude only, down to one plane
-        *ok = lv.D.nth % 2 == 0 && lv.D.nth > 1;
-        f[0] = *ok ? 2 : 1;
-        f[1] = f[2] = 1;
+    if (h->opts.smoother == MG_SMOOTH_PLANE && h->plane_levels == 0) {
+        // semi-coarsening: the colatitude only, down to one plane (or an odd
+        // row count), which the dense bordered solve takes when it fits; a
+        // larger one hands over to the policy below (plane_levels set)
+        if (lv.D.nth % 2 == 0 && lv.D.nth > 1) {
+            *ok = true;
+            f[0] = 2;
+            f[1] = f[2] = 1;
+            return MG_OK;
+        }
+        f[0] = f[1] = f[2] = 1;
+        *ok = false;
+        if (lv.D.n() <= kMaxCoarse) return MG_OK;
+        h->plane_levels = (int)h->L.size() - 1 + (lv.D.nth >= 2 ? 1 : 0);
+    }
+    if (h->opts.smoother == MG_SMOOTH_PLANE && lv.D.n() <= h->opts.coarse_max) {
+        *ok = false;
+        f[0] = f[1] = f[2] = 1;
         return MG_OK;
     }
     const int n[3] = {lv.D.nth, lv.D.nr, lv.D.nph};
@@ -730,7 +739,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
 
     // --- hierarchy by face-metric aggregation
     const bool plane = o->smoother == MG_SMOOTH_PLANE;   // coarsens to one plane whatever the size
-    while (plane || ((int)h->L.size() < o->max_levels && h->L.back().D.n() > o->coarse_max)) {
+    while ((plane && h->plane_levels == 0) ||
+           ((int)h->L.size() < o->max_levels && h->L.back().D.n() > o->coarse_max)) {
         int f[3];
         bool ok;
         CKS(plan_next(h, h->L.back(), f, &ok));
@@ -748,6 +758,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         CK(launch_coarsen_faces(fine.view(h->stencil), c.D, c.g64, stream));
         h->L.push_back(c);
     }
+    if (plane && h->plane_levels == 0) h->plane_levels = (int)h->L.size() - 1;   // every level above the coarsest
     for (const Level& lv : h->L)
         if (!fastdiv_ok(lv.D)) {
             set_error("index divisor self-check failed");
@@ -974,7 +985,7 @@ void plane_sweep_steps(const mg_handle* h, int level, void* x, const void* b, st
     auto relax = [&](int m, int p, int q) {
         const Dims& D = P[m].D;
         const i64 lines = (i64)((D.nth + 1 - p) >> 1) * ((D.nr + 1 - q) >> 1);
-        if (lines > 0) out.push_back(PlaneStep{BOP_PRELAX, p + 2 * q, two_d(m), vb(lines)});
+        if (lines > 0) out.push_back(PlaneStep{BOP_PRELAX, p + 2 * q, two_d(m), vb(32 * lines)});   // a warp per line
     };
     for (int p = 0; p < 2; ++p) {
         if (plane_cells(lv.D, p) == 0) continue;
@@ -1136,7 +1147,7 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
 // V(nu1, nu2) on A_0 x0 = b0; coarse levels use the handle's e / r arrays.
 mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
     const int nl = (int)h->L.size();
-    const int kind = h->opts.smoother;
+    (void)0;
     h->launches += 1;
     if (nl == 1) {
         CK(launch_coarse_solve(h->binv, h->ncoarse, prec, b0, x0, h->stream));
@@ -1147,7 +1158,7 @@ mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
     for (int l = 0; l < top; ++l) {
         void* x = l == 0 ? x0 : h->L[l].e;
         const void* b = l == 0 ? b0 : h->L[l].r;
-        CKS(smooth(h, l, prec, x, b, h->opts.nu1, kind));
+        CKS(smooth(h, l, prec, x, b, h->opts.nu1, level_smoother(h, l)));
         if (l == 0) prof_begin(h, MG_PROF_RESTRICT0);
         CK(launch_restrict_residual(h->L[l].view(h->stencil), h->L[l + 1].D, prec, x, b, h->L[l + 1].r,
                                     h->L[l + 1].e, h->stream));
@@ -1168,7 +1179,7 @@ mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
         CK(launch_prolong_add(h->L[l].view(h->stencil), h->L[l + 1].D, prec, h->L[l + 1].e, x, h->stream));
         if (l == 0) prof_end(h, MG_PROF_PROLONG0, 1);
         h->launches += 1;
-        CKS(smooth(h, l, prec, x, b, h->opts.nu2, kind));
+        CKS(smooth(h, l, prec, x, b, h->opts.nu2, level_smoother(h, l)));
     }
     return MG_OK;
 }
@@ -1396,8 +1407,8 @@ mg_status mg_smooth(mg_handle* h, int level, int prec, void* x, const void* b, i
     LEVEL_CHECK(h, level, prec);
     if (!x || !b || sweeps < 0 || kind < 0 || kind > 5) return MG_EINVAL;
     if (kind == MG_SMOOTH_PLANE && (h->opts.smoother != MG_SMOOTH_PLANE || prec != h->prec ||
-                                    level + 1 >= (int)h->L.size())) {
-        set_error("plane relaxation: a handle set up with the PLANE smoother, its own precision, a level above the coarsest");
+                                    level >= h->plane_levels)) {
+        set_error("plane relaxation: a handle set up with the PLANE smoother, its own precision, a level relaxed by planes");
         return MG_EINVAL;
     }
     StreamJoin join(h);

@@ -96,6 +96,7 @@ struct mg_handle {
     std::vector<cudaEvent_t> prof_pool;
     // outer iterations run as captured graphs (solver.cu)
     bool use_graph = true;
+    int plane_levels = 0;             // PLANE smoother: leading levels relaxed by planes (the rest: GS)
     bool one_pass = false;            // one-pass multicolour sweeps where a tile fits (schedule choice)
     int sweep_cells = 2048;           // one-pass tiles: target cells per plane (rows x longitudes)
     int sweep_tj = 0;                 // one-pass tiles: radius planes per chunk (0: per level)
@@ -171,6 +172,14 @@ double model_bytes_per_iteration(const mg_handle* h);
 bool sweep_tile_for(const mg_handle* h, int level, int tile[3]);
 // smoothers that sweep radial lines / longitude lines (the alternating one both)
 inline bool radial_lines(int smoother) { return smoother == MG_SMOOTH_LINE || smoother == MG_SMOOTH_ALT; }
+// The smoother of a level: the handle's, except that a PLANE handle relaxes
+// by planes only its leading levels of two or more planes above the
+// coarsest (the colatitude-only part of its hierarchy); the levels below a
+// coarsest plane too large for the dense solve take point Gauss-Seidel.
+inline int level_smoother(const mg_handle* h, int level) {
+    if (h->opts.smoother != MG_SMOOTH_PLANE) return h->opts.smoother;
+    return level < h->plane_levels ? MG_SMOOTH_PLANE : MG_SMOOTH_GS;
+}
 // One sweep of zebra plane relaxation of level `level` (x, b in the cycle's
 // type): the launches in order, each one task over the planes of one parity.
 struct PlaneStep {

@@ -92,38 +92,104 @@ __device__ __forceinline__ void plane_res3d(const CF& cf, const Dims& D, const T
 }
 
 // One zebra half-sweep of longitude lines: the lines of rows j = q mod 2 of
-// the planes of parity p.  One thread per line; the residual on the fly,
-// forward recurrence into the scratch w, backward, closure, correction (the
-// periodic elimination of xline_smooth.cuh).
+// the planes of parity p, each x_L += T_L^{-1} (r - B x)_L by the periodic
+// elimination of xline_smooth.cuh (factors from set-up).  One warp per line
+// (work items = lines x 32): every lane takes a chunk of at most kPlaneChunk consecutive cells of the
+// line's leading block [0, n - 1), evaluates their residuals, runs both
+// recurrences on its chunk from zero and publishes the chunk's affine map
+// (value leaving = P * value entering + Q); an inclusive warp scan of the maps
+// (shuffles) gives every chunk its entering value, as the chunked radial- and
+// longitude-line passes do through shared memory.  The recurrences of the
+// sequential elimination, regrouped (equal up to rounding).  n - 1 <= 32 *
+// kPlaneChunk.
+constexpr int kPlaneChunk = 16;
+
 template <typename T>
-__device__ __forceinline__ void plane_relax(const T* const* c, const Dims& D, T* e, const T* r, const T* fac, T* w,
-                                            int p, int q, i64 first, i64 stride) {
+__device__ __forceinline__ void warp_scan_maps(T& P, T& Q, int lane, bool reverse) {
+    // inclusive composition over the lanes in order (reverse: from lane 31 down)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T pp = reverse ? __shfl_down_sync(0xffffffffu, P, o) : __shfl_up_sync(0xffffffffu, P, o);
+        const T qq = reverse ? __shfl_down_sync(0xffffffffu, Q, o) : __shfl_up_sync(0xffffffffu, Q, o);
+        const bool has = reverse ? lane + o < 32 : lane >= o;
+        if (has) {   // (P, Q) after (pp, qq): x -> P (pp x + qq) + Q
+            Q = fma(P, qq, Q);
+            P = P * pp;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void plane_relax_warp(const T* const* c, const Dims& D, T* e, const T* r, const T* fac,
+                                                 int p, int q, i64 first, i64 stride) {
     const i64 N = D.n();
     const T* alpha = fac;
     const T* beta = fac + N;
     const T* gamma = fac + 2 * N;
     const T* psi2 = fac + 3 * N;
-    const int n = D.nph;
+    const int n = D.nph, m = n - 1;                       // the leading block: cells 0 .. n - 2
+    const int lane = threadIdx.x & 31;
+    const int rows = (m + 31) / 32;                        // cells per chunk (<= kPlaneChunk)
+    const int k0 = min(lane * rows, m), nk = min(k0 + rows, m) - k0;
     const int np = (D.nth + 1 - p) >> 1, nq = (D.nr + 1 - q) >> 1;
     const i64 lines = (i64)np * nq;
-    for (i64 t = first; t < lines; t += stride) {
+    for (i64 t = first >> 5; t < lines; t += stride >> 5) {   // uniform per warp
         const int i = 2 * (int)(t % np) + p, j = 2 * (int)(t / np) + q;
         const int c0 = (j * D.nth + i) * D.nph, cl = c0 + n - 1;
-        T fq = 0;
-        for (int k = 0; k < n - 1; ++k) {
-            const T res = r[c0 + k] - plane_apply<T>(c, e, D, j, i, k);
-            fq = fma(alpha[c0 + k], fq, beta[c0 + k] * res);
-            w[c0 + k] = fq;
+        T d[kPlaneChunk], P[kPlaneChunk];
+        // residuals and the forward recurrence on the chunk from zero
+        T fq = 0, fp = 1;
+#pragma unroll
+        for (int u = 0; u < kPlaneChunk; ++u) {
+            if (u < nk) {
+                const int k = k0 + u;
+                const T res = r[c0 + k] - plane_apply<T>(c, e, D, j, i, k);
+                const T a = alpha[c0 + k];
+                fq = fma(a, fq, beta[c0 + k] * res);
+                fp = fp * a;
+                d[u] = fq;
+                P[u] = fp;
+            }
         }
-        const T rl = r[cl] - plane_apply<T>(c, e, D, j, i, n - 1);
-        T be = 0;
-        for (int k = n - 2; k >= 0; --k) {
-            be = fma(gamma[c0 + k], be, w[c0 + k]);
-            w[c0 + k] = be;
+        const T rl = lane == 31 ? r[cl] - plane_apply<T>(c, e, D, j, i, n - 1) : (T)0;
+        // entering value of each chunk: the composed maps of the chunks before it
+        T sp = fp, sq = fq;
+        warp_scan_maps<T>(sp, sq, lane, false);
+        T in = __shfl_up_sync(0xffffffffu, sq, 1);
+        if (lane == 0) in = 0;
+        // backward recurrence on the corrected forward values, from zero
+        T bq = 0, bp = 1, last = 0;
+#pragma unroll
+        for (int u = kPlaneChunk - 1; u >= 0; --u) {
+            if (u < nk) {
+                const T gm = gamma[c0 + k0 + u];
+                bq = fma(gm, bq, fma(P[u], in, d[u]));
+                bp = bp * gm;
+                d[u] = bq;
+                P[u] = bp;
+                if (u == nk - 1) last = bq;
+            }
         }
-        const T dl = (rl - alpha[cl] * w[c0] - gamma[cl] * w[c0 + n - 2]) * beta[cl];
-        for (int k = 0; k < n - 1; ++k) e[c0 + k] = e[c0 + k] + fma(psi2[c0 + k], dl, w[c0 + k]);
-        e[cl] = e[cl] + dl;
+        sp = bp;
+        sq = bq;
+        warp_scan_maps<T>(sp, sq, lane, true);
+        T bin = __shfl_down_sync(0xffffffffu, sq, 1);
+        if (lane == 31) bin = 0;
+        // psi1 at the first and the last cell of the leading block
+        const int first_lane = 0, last_lane = (m - 1) / rows;
+        const T w0 = __shfl_sync(0xffffffffu, nk > 0 ? fma(P[0], bin, d[0]) : (T)0, first_lane);
+        const T wl = __shfl_sync(0xffffffffu, last, last_lane);   // the chunk with the last cell has bin = 0
+        const T rl_all = __shfl_sync(0xffffffffu, rl, 31);
+        const T dl = (rl_all - alpha[cl] * w0 - gamma[cl] * wl) * beta[cl];
+#pragma unroll
+        for (int u = 0; u < kPlaneChunk; ++u) {
+            if (u < nk) {
+                const int cc = c0 + k0 + u;
+                e[cc] = e[cc] + fma(psi2[cc], dl, fma(P[u], bin, d[u]));
+            }
+        }
+        if (lane == 31) e[cl] = e[cl] + dl;
+        __syncwarp();
     }
 }
 

@@ -175,10 +175,10 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
     for (mg_handle* h : pl->hs) {
         if (level >= top_of(h)) continue;
         const int nc = h->stencil == 7 ? 2 : 4;
-        if (h->opts.smoother == MG_SMOOTH_JACOBI) any_jacobi = true;
-        else if (radial_lines(h->opts.smoother) || longitude_lines(h->opts.smoother)) {
-            if (radial_lines(h->opts.smoother)) maxl = std::max(maxl, nc);
-            if (longitude_lines(h->opts.smoother)) maxx = std::max(maxx, nc);
+        if (level_smoother(h, level) == MG_SMOOTH_JACOBI) any_jacobi = true;
+        else if (radial_lines(level_smoother(h, level)) || longitude_lines(level_smoother(h, level))) {
+            if (radial_lines(level_smoother(h, level))) maxl = std::max(maxl, nc);
+            if (longitude_lines(level_smoother(h, level))) maxx = std::max(maxx, nc);
         } else if (fused_level(h, level)) any_fused = true;
         else maxc = std::max(maxc, nc);
     }
@@ -223,7 +223,7 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
             }
             for (size_t s = 0; s < pl->hs.size(); ++s) {
                 mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_GS || h->stencil != st) continue;
+                if (level >= top_of(h) || level_smoother(h, level) != MG_SMOOTH_GS || h->stencil != st) continue;
                 if (fused_level(h, level) || c >= (h->stencil == 7 ? 2 : 4)) continue;
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
@@ -240,7 +240,7 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
             }
             for (size_t s = 0; s < pl->hs.size(); ++s) {
                 mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || !radial_lines(h->opts.smoother) || h->stencil != st) continue;
+                if (level >= top_of(h) || !radial_lines(level_smoother(h, level)) || h->stencil != st) continue;
                 if (c >= (h->stencil == 7 ? 2 : 4)) continue;
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
@@ -261,7 +261,7 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
                     }
                     for (size_t s = 0; s < pl->hs.size(); ++s) {
                         mg_handle* h = pl->hs[s];
-                        if (level >= top_of(h) || !longitude_lines(h->opts.smoother) || h->stencil != st) continue;
+                        if (level >= top_of(h) || !longitude_lines(level_smoother(h, level)) || h->stencil != st) continue;
                         if (c >= (h->stencil == 7 ? 2 : 4) || (h->L[level].D.nph < 4) != (narrow == 1)) continue;
                         BTask t = task_of(h, level);
                         level_bufs(h, prec, level, &t.x, &t.b);
@@ -289,7 +289,7 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
             }
             for (size_t s = 0; s < pl->hs.size(); ++s) {
                 mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_JACOBI || h->stencil != st) continue;
+                if (level >= top_of(h) || level_smoother(h, level) != MG_SMOOTH_JACOBI || h->stencil != st) continue;
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
                 t.y = h->L[level].t;
@@ -300,7 +300,7 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
             P.begin(BOP_COPY);
             for (size_t s = 0; s < pl->hs.size(); ++s) {
                 mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_JACOBI) continue;
+                if (level >= top_of(h) || level_smoother(h, level) != MG_SMOOTH_JACOBI) continue;
                 BTask t{};
                 void* x;
                 const void* b;
@@ -316,7 +316,7 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
         // launches in order (plane hierarchies differ from handle to handle)
         for (size_t s = 0; s < pl->hs.size(); ++s) {
             mg_handle* h = pl->hs[s];
-            if (level >= top_of(h) || h->opts.smoother != MG_SMOOTH_PLANE) continue;
+            if (level >= top_of(h) || level_smoother(h, level) != MG_SMOOTH_PLANE) continue;
             void* xb;
             const void* bb;
             level_bufs(h, prec, level, &xb, &bb);
