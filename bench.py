@@ -72,11 +72,12 @@ def peaks():
 
 
 def kernel_source_hash():
-    """Hash of the sources of the batched level kernels (the ones the roofline
-    reports on)."""
+    """Hash of the sources of the batched level kernels and the one-pass sweep
+    (the ones the roofline reports on), headers included."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_17875_gb300", "csrc")
-    for fn in ("batch.cu", "mg_internal.cuh", "mg_kernels.h"):
+    for fn in ("batch.cu", "sweep.cu", "mg_internal.cuh", "mg_kernels.h", "line_smooth.cuh", "xline_smooth.cuh",
+               "plane_smooth.cuh"):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
