@@ -71,36 +71,43 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the sources of the batched level kernels and the one-pass sweep
-    (the ones the roofline reports on), headers included."""
+BATCH_SOURCES = ("batch.cu", "mg_internal.cuh", "mg_kernels.h", "line_smooth.cuh", "xline_smooth.cuh",
+                 "plane_smooth.cuh")
+SWEEP_SOURCES = ("sweep.cu", "mg_internal.cuh", "mg_kernels.h")
+
+
+def kernel_source_hash(sources=BATCH_SOURCES):
+    """Hash of the source files a kernel is built from (the batched level
+    kernels by default; the one-pass sweeps: SWEEP_SOURCES)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_17875_gb300", "csrc")
-    for fn in ("batch.cu", "sweep.cu", "mg_internal.cuh", "mg_kernels.h", "line_smooth.cuh", "xline_smooth.cuh",
-               "plane_smooth.cuh"):
+    for fn in sources:
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, precision, slot):
+def ncu_traffic(workload, precision, slot, one_pass=False):
     """DRAM bytes per launch of the slot's kernel from the committed ncu
-    summary, or None when absent or taken on different kernel sources."""
+    summary, or None when absent or taken on different kernel sources.  The
+    level-0 smoother's entry is that of the colour passes, or with one_pass
+    that of the one-pass sweep (key suffix /sweep)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    e = d.get(f"{workload}/{precision}/{slot}")
+    suffix = "/sweep" if (one_pass and slot == "smooth0") else ""
+    e = d.get(f"{workload}/{precision}/{slot}{suffix}")
     scale = 1.0
     if not e:
         # a workload too large to capture: its half-size capture (every
         # dimension halved, the same kernels), scaled by the cell count, since
         # a level kernel's traffic per cell does not depend on the grid size
-        e = d.get(f"{workload}/2/{precision}/{slot}")
+        e = d.get(f"{workload}/2/{precision}/{slot}{suffix}")
         scale = 8.0
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(tuple(e.get("sources", BATCH_SOURCES))):
         return None
     return e.get("dram_bytes_per_launch") * scale
 
@@ -446,7 +453,7 @@ def single_leg(args, mgs, torch, workload, scale, prec, smoother, steps, warmup,
                key=lambda kv: kv[1][0])[0]
     pname = [k for k, v in PREC.items() if v == prec][0]
     roof = roofline_of(name, slots, steps, stencil, prec, N, n_next, smoother, axi, one_pass,
-                       ncu_traffic(traffic_key or workload, pname, name))
+                       ncu_traffic(traffic_key or workload, pname, name, one_pass))
     roof["share_of_step"] = slots[name][0] / max(sum(v[0] for v in slots.values()), 1e-30)
     leg = {"workload": workload if scale == 1 else f"{workload}/{scale}", "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
            "value": N / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
@@ -557,7 +564,7 @@ def run_ours(args, rank, world, local_rank):
                key=lambda kv: kv[1][0])[0]
     roof = roofline_of(name, slots, args.steps, stencil, prec, N, n_next, smoother, axi, one_pass,
                        ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
-                                   args.precision, name))
+                                   args.precision, name, one_pass))
     roof["share_of_step"] = slots[name][0] / max(sum(v[0] for v in slots.values()), 1e-30)
 
     # end to end through the public host-buffer call (pinned host memory)

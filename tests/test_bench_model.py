@@ -63,6 +63,6 @@ def test_traffic_lookup_scales_a_half_size_capture():
     path = os.path.join(bench.ROOT, "profiles", "traffic.json")
     d = json.load(open(path))
     e = d.get("single_oblate_256/2/fp32/smooth0")
-    if not e or e.get("source_hash") != bench.kernel_source_hash():
+    if not e or e.get("source_hash") != bench.kernel_source_hash(tuple(e.get("sources", bench.BATCH_SOURCES))):
         pytest.skip("no capture for the current kernel sources")
     assert bench.ncu_traffic("single_oblate_256", "fp32", "smooth0") == pytest.approx(8 * e["dram_bytes_per_launch"])
