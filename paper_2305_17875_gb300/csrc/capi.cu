@@ -577,7 +577,12 @@ mg_status autotune(mg_handle* h) {
     }
     {   // one-pass sweeps on the large levels: two plane areas, then the
         // chunk depth, the smallest level swept in one pass and the tile width
+        // (the 7-point sweep of the FP32 / FP16 cycles takes whole rows and
+        // sizes its tiles itself: only the chunk depth and the smallest level
+        // are candidates there)
+        const bool rb7 = h->stencil == 7 && h->prec != PREC64;
         for (int cells : {2048, 3072}) {
+            if (rb7 && cells != 2048) continue;
             Schedule sc = best;
             sc.fused = true;
             sc.tile_cells = cells;
@@ -594,7 +599,7 @@ mg_status autotune(mg_handle* h) {
                 t.tile_min = mc;
                 if (can_fuse(h, t)) CKS(consider(t));
             }
-            if (h->stencil == 7) {
+            if (h->stencil == 7 && !rb7) {
                 Schedule t = best;
                 t.tile_kmax = 128;
                 CKS(consider(t));
@@ -625,10 +630,11 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         int c = 2048, tj = 0, km = 256;
         long long mc = h->sweep_min_cells;
         std::sscanf(v, "%d,%d,%d,%lld", &c, &tj, &km, &mc);
-        h->sweep_cells = std::max(1, c);
+        h->sweep_cells = std::max(0, c);
         h->sweep_tj = std::max(0, tj);
         h->sweep_kmax = std::max(4, km);
         h->sweep_min_cells = std::max(0LL, mc);
+        h->sweep_tile_env = true;
     }
     CK(cudaGetDevice(&h->device));
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
@@ -688,7 +694,7 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     if (!(h->part = (double*)dalloc(h, sizeof(double) * kRedBlocks))) return MG_ENOMEM;
     if (!(h->scal = (double*)dalloc(h, sizeof(double) * SC_COUNT))) return MG_ENOMEM;
     if (!(h->one_task = (BTask*)dalloc(h, sizeof(BTask)))) return MG_ENOMEM;
-    if (!(h->one_map = dalloc(h, 128))) return MG_ENOMEM;
+    if (!(h->one_map = dalloc(h, 128 * 5))) return MG_ENOMEM;
     if (o->metric == MG_METRIC_ANALYTIC) {
         // exact derivatives at the face centres: tables at half-index resolution
         std::vector<double> ar(2 * nr + 1), adr(2 * nr + 1), act(2 * nth + 1), ast(2 * nth + 1),
@@ -1027,10 +1033,42 @@ void plane_sweep_steps(const mg_handle* h, int level, void* x, const void* b, st
     }
 }
 
+// The 7-point sweep of the FP32 and FP16-coefficient cycles: whole rows, one
+// thread per quad of TI + 2 rows.  The rows and chunk depth minimise the
+// estimate ceil(tiles / 152) (TJ + 3) (TI + 3): one wave of tiles on the SMs,
+// a tile takes TJ + 2 steps and a step costs about its rows plus a fixed
+// part.  MG_TILE fixes the rows (its cells / nph, at least one; cells 0 or
+// rows that do not fit: automatic), a schedule's chunk depth fixes TJ.
+bool rb7_tile_for(const mg_handle* h, const Dims& D, int tile[3]) {
+    const int NQ = D.nph / 4;
+    if (D.nph % 4 != 0 || NQ < 1) return false;
+    const int ti_max = std::min(D.nth, kRB7MaxThreads / NQ - 2);
+    if (ti_max < 1) return false;
+    int lo = 1, hi = ti_max;
+    if (h->sweep_tile_env && h->sweep_cells > 0) lo = hi = std::max(1, std::min(ti_max, h->sweep_cells / D.nph));
+    bool found = false;
+    double best = 0.0;
+    for (int pass = 0; pass < 2 && !found; ++pass, lo = 1, hi = ti_max)   // forced rows that do not fit: automatic
+    for (int ti = lo; ti <= hi; ++ti)
+        for (int tj = 1; tj <= D.nr; ++tj) {
+            if (h->sweep_tj > 0 && tj != std::min(h->sweep_tj, D.nr)) continue;
+            const int t3[3] = {ti, tj, D.nph};
+            if (!sweep_tile_ok(D, 7, h->prec, t3)) continue;
+            const double cost = std::ceil(sweep_units(D, t3) / 152.0) * (tj + 3) * (ti + 3);
+            if (!found || cost < best) {
+                found = true;
+                best = cost;
+                tile[0] = ti, tile[1] = tj, tile[2] = D.nph;
+            }
+        }
+    return found;
+}
+
 bool sweep_tile_for(const mg_handle* h, int level, int tile[3]) {
     if (!h->one_pass || h->opts.smoother != MG_SMOOTH_GS || level < 0 || level >= (int)h->L.size()) return false;
     const Dims& D = h->L[level].D;
     if (D.n() < h->sweep_min_cells) return false;
+    if (h->stencil == 7 && h->prec != PREC64) return !D.cut && rb7_tile_for(h, D, tile);
     // longitudes: whole rows up to the widest tile, else the largest
     // power-of-two divisor of nph up to 128
     // (19 points: at most 128, the buffers hold four halo rows either side)
@@ -1079,13 +1117,15 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
             t.nblocks = sweep_units(lv.D, tile);
             for (int a = 0; a < 3; ++a) t.tile[a] = tile[a];
             t.tmap = h->one_map;
-            alignas(64) unsigned char map[128];
-            CK(encode_sweep_map(map, t.x, lv.D, h->stencil, prec, tile));
+            alignas(64) unsigned char map[128 * 5];
+            CK(encode_sweep_maps(map, t, h->stencil, prec));
             // pageable sources: both copies are staged before the calls return
-            CK(cudaMemcpyAsync(h->one_map, map, sizeof(map), cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(h->one_map, map, 128 * (size_t)sweep_map_count(h->stencil, prec),
+                               cudaMemcpyHostToDevice, h->stream));
             CK(cudaMemcpyAsync(h->one_task, &t, sizeof(BTask), cudaMemcpyHostToDevice, h->stream));
             CK(launch_sweep(h->one_task, 1, t.nblocks, nullptr, h->stencil, h->axi, prec,
-                            sweep_smem_bytes(h->stencil, prec, lv.D, tile), h->stream));
+                            sweep_smem_bytes(h->stencil, prec, lv.D, tile),
+                            sweep_threads(h->stencil, prec, lv.D, tile), h->stream));
         }
         if (sweeps & 1) {
             CK(cudaMemcpyAsync(x, lv.t, value_bytes(prec) * lv.D.n(), cudaMemcpyDeviceToDevice, h->stream));

@@ -102,12 +102,13 @@ struct mg_handle {
     int sweep_tj = 0;                 // one-pass tiles: radius planes per chunk (0: per level)
     int sweep_kmax = 256;             // one-pass tiles: widest tile in longitudes (whole rows up to it)
     long long sweep_min_cells = 1 << 20;   // one-pass tiles: only on levels of at least this many cells
+    bool sweep_tile_env = false;      // MG_TILE given: its plane area also fixes the 7-point sweep's rows
     int vb_cap = 16;                  // blocks per SM of the level kernels' virtual grids
     int sched_source = 0;             // mg_schedule.source
     int sched_candidates = 0;
     double sched_ms = 0.0;
     mgs::BTask* one_task = nullptr;   // task table of stand-alone one-pass sweeps
-    void* one_map = nullptr;          // tensor map of a stand-alone one-pass sweep (128 bytes)
+    void* one_map = nullptr;          // tensor maps of a stand-alone one-pass sweep (up to 5 x 128 bytes)
     mgs::BTask* plane_tasks = nullptr;    // task table of stand-alone plane relaxations
     size_t plane_tasks_cap = 0;
     int tail_level = 0;               // first level of the single-launch coarse tail (0: none)

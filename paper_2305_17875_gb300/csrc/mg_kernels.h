@@ -170,23 +170,31 @@ struct BTask {
     int nblocks;       // virtual blocks (work mapping of a stand-alone launch)
     int shell;         // index of the active flag
     int tile[3];       // one-pass sweep: colatitude rows, radius planes, longitudes of a tile
-    const void* tmap;  // one-pass sweep: tensor map of x (device, 64-byte aligned)
+    const void* tmap;  // one-pass sweep: its tensor maps (device, 64-byte aligned, 128 bytes each)
 };
 static_assert(sizeof(BTask) % 4 == 0, "BTask is staged in shared memory word by word");
 // ---- one-pass multicolour sweeps (sweep.cu).  A tile is tile[0] colatitude
 // rows x tile[2] longitudes (tile[2] == nph: whole rows) x a chunk of tile[1]
-// radius planes; the iterate x of a task is staged through a tensor map made
-// by encode_sweep_map (128 bytes, 64-byte aligned).
+// radius planes.  A task's arrays are staged through sweep_map_count tensor
+// maps (128 bytes each, 64-byte aligned, at tmap) made by encode_sweep_maps
+// from the task's x, b, level view and tile: for the 7-point FP32 / FP16
+// sweep x, b and three coefficient arrays, otherwise x alone.
+// Most compute threads of a 7-point FP32 / FP16 sweep CTA (one per quad of TI
+// + 2 rows; with the copy warp, 19 warps: five per SM sub-partition leave 96
+// registers a thread).
+constexpr int kRB7MaxThreads = 576;
 bool sweep_tile_ok(const Dims& D, int stencil, int prec, const int tile[3]);
 size_t sweep_smem_bytes(int stencil, int prec, const Dims& D, const int tile[3]);
+int sweep_threads(int stencil, int prec, const Dims& D, const int tile[3]);
 int sweep_units(const Dims& D, const int tile[3]);
-cudaError_t encode_sweep_map(void* map, const void* x, const Dims& D, int stencil, int prec, const int tile[3]);
-// All tasks of one launch share stencil, precision and axi; smem = the
-// largest sweep_smem_bytes of its tasks.
+int sweep_map_count(int stencil, int prec);
+cudaError_t encode_sweep_maps(void* maps, const BTask& t, int stencil, int prec);
+// All tasks of one launch share stencil, precision and axi; smem and
+// threads = the largest sweep_smem_bytes and sweep_threads of its tasks.
 // axi: 19 points without the longitude cross terms (the handle's stored
 // components); every task of the launch shares it.
 cudaError_t launch_sweep(const BTask* tasks, int ntasks, int total, const int* active, int stencil, bool axi,
-                         int prec, size_t smem, cudaStream_t s);
+                         int prec, size_t smem, int threads, cudaStream_t s);
 // The fault word of the sweeps (a plane copy that did not land in time);
 // clear resets it.
 cudaError_t sweep_fault_read(unsigned* out, bool clear);

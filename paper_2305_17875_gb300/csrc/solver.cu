@@ -64,17 +64,15 @@ struct Launch {
     int level = -1;                // level of a level operation (timing attribution)
     int tail_stencil = 0;          // >0: a coarse-tail launch of this stencil
     size_t smem = 0;               // one-pass sweep launches: dynamic shared memory
+    int threads = 0;               // one-pass sweep launches: threads per CTA
     bool axi = false;              // one-pass sweep launches: 19 points without longitude cross terms
 };
 
-// Tensor map of a one-pass sweep task's input iterate (made when the plan's
+// Tensor maps of a one-pass sweep task (made from the task when the plan's
 // tables are uploaded).
 struct MapReq {
     int task;
-    const void* x;
-    Dims D;
     int stencil, prec;
-    int tile[3];
 };
 
 struct Program {
@@ -209,8 +207,9 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
                     t.b = bb;
                     t.shell = (int)s;
                     for (int a = 0; a < 3; ++a) t.tile[a] = tile[a];
-                    P.maps.push_back(MapReq{(int)P.tasks.size(), t.x, D, st, prec, {tile[0], tile[1], tile[2]}});
+                    P.maps.push_back(MapReq{(int)P.tasks.size(), st, prec});
                     L.smem = std::max(L.smem, sweep_smem_bytes(st, prec, D, tile));
+                    L.threads = std::max(L.threads, sweep_threads(st, prec, D, tile));
                     P.add(t, sweep_units(D, tile));
                 }
             }
@@ -523,7 +522,8 @@ mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const in
             }
             CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream));
         } else if (L.op == BOP_SWEEP) {
-            CK(launch_sweep(d_tasks + L.t0, L.nt, L.total, active, L.stencil, L.axi, pl->prec, L.smem, pl->stream));
+            CK(launch_sweep(d_tasks + L.t0, L.nt, L.total, active, L.stencil, L.axi, pl->prec, L.smem, L.threads,
+                            pl->stream));
         } else {
             CK(launch_batch(d_tasks + L.t0, L.nt, L.total, active, L.op, L.colour, L.stencil, pl->prec,
                             pl->stream));
@@ -651,14 +651,18 @@ mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n, bool iteration) {
     std::stable_sort(pl->iter.tails.begin(), pl->iter.tails.end(),
                      [](const TailTask& a, const TailTask& b) { return a.lev[0].v.stencil < b.lev[0].v.stencil; });
     if (!pl->iter.maps.empty()) {
-        const size_t nb = 128 * pl->iter.maps.size();
+        size_t count = 0;
+        for (const MapReq& q : pl->iter.maps) count += sweep_map_count(q.stencil, q.prec);
+        const size_t nb = 128 * count;
         CK(grow(&pl->d_maps, &pl->maps_cap, nb, false));
         // host images of the maps (CUtensorMap is 128 bytes, 64-byte aligned)
         std::vector<unsigned long long> img(nb / 8);
-        for (size_t m = 0; m < pl->iter.maps.size(); ++m) {
-            const MapReq& q = pl->iter.maps[m];
-            CK(encode_sweep_map(&img[16 * m], q.x, q.D, q.stencil, q.prec, q.tile));
-            pl->iter.tasks[q.task].tmap = pl->d_maps + 128 * m;
+        size_t at = 0;
+        for (const MapReq& q : pl->iter.maps) {
+            BTask& t = pl->iter.tasks[q.task];
+            CK(encode_sweep_maps(&img[16 * at], t, q.stencil, q.prec));
+            t.tmap = pl->d_maps + 128 * at;
+            at += sweep_map_count(q.stencil, q.prec);
         }
         CK(cudaMemcpyAsync(pl->d_maps, img.data(), nb, cudaMemcpyHostToDevice, pl->stream));
         CK(cudaStreamSynchronize(pl->stream));   // img is pageable and local

@@ -35,6 +35,10 @@
 // ends with MG_ENAN instead of hanging.
 #include <cuda.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "mg_kernels.h"
 
 namespace mgs {
@@ -75,6 +79,9 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sptr(bar)), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sptr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     unsigned ok;
@@ -542,16 +549,36 @@ bool sweep_pdl() {
     return on;
 }
 
+// Resident CTAs per SM of a sweep kernel at (threads, dynamic shared memory):
+// the kernel's shared-memory limit is raised and the runtime asked once per
+// configuration (the query costs host time on every eager launch otherwise).
+// Serialised: launches come from several host threads.
+template <typename K>
+cudaError_t sweep_per_sm(K kernel, int threads, size_t smem, int* per_sm) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, std::pair<int, size_t>>, int> known;
+    static std::map<const void*, size_t> smem_attr;
+    const void* key = reinterpret_cast<const void*>(kernel);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find({key, {threads, smem}});
+    if (it != known.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
+    if (smem > smem_attr[key]) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_attr[key] = smem;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, smem);
+    if (e == cudaSuccess) known[{key, {threads, smem}}] = *per_sm;
+    return e;
+}
+
 template <int S, int P, bool AXI>
 cudaError_t sweep_launch(const BTask* tasks, int ntasks, int total, const int* active, size_t smem, cudaStream_t s) {
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<S, P, AXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = smem;
-    }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<S, P, AXI>, kSW, smem);
+    cudaError_t e = sweep_per_sm(k_sweep<S, P, AXI>, kSW, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = std::min(total, 152 * per_sm);   // persistent beyond one wave
@@ -586,12 +613,436 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+
+// ---- the 7-point red-black sweep on whole longitude rows (FP32 iterate;
+// FP32 or FP16 coefficients).
+//
+// A CTA owns TI colatitude rows i0 .. i0 + TI - 1 and a chunk of TJ radius
+// planes, one thread per quad (four consecutive longitudes) of the rows
+// i0 - 1 .. i0 + TI: the two rows outside the tile carry red updates only,
+// which the black cells of the tile's edge rows read.  Every plane of x (rows
+// i0 - 2 .. i0 + TI + 1), of b and of the three lower-face coefficient arrays
+// (rows i0 - 1 .. i0 + TI + 1) arrives as five bulk tensor copies on one
+// mbarrier, in a ring of four slots that a copy warp keeps filled: it reuses a
+// slot once every compute warp has released the plane in it (a second
+// mbarrier per slot), so copies never wait on the compute warps' steps and the
+// compute warps meet only among themselves (a named barrier) once per step.
+//
+// Step s updates the red cells of plane s and the black cells of plane s - 1;
+// in a quad both are the positions P, P + 2 with P = (i + s) mod 2.  A thread
+// holds its quad on planes s - 2 .. s + 1 in registers (the radius
+// neighbours never pass through shared memory), reads the colatitude and
+// longitude neighbours of its red cells from the copied plane (old values:
+// black cells of plane s are updated only in step s + 1) and those of its
+// black cells from a small double-buffered array where every thread leaves
+// its two new red values of the plane (written in step s - 1), and stores the
+// finished quad of plane s - 1 with one 16-byte store.  The red ring rows and
+// the red planes j0 - 1 and jend repeat work of the neighbouring tiles from
+// the old iterate, so no tile waits for another; the sweep is out of place.
+//
+// The arithmetic is Cell7::gs with the colour passes' neighbour values
+// (mirror at the radius and colatitude walls, longitude wrap), so a sweep
+// gives the bits of its two colour passes.
+constexpr int kRB7Max = kRB7MaxThreads + 32;   // threads: up to nine rows of 64 quads, and the copy warp
+constexpr int kRB7Slots = 4;   // plane slots of the copy ring
+
+struct RB7Layout {
+    unsigned xoff, boff, eoff, zoff, loff;   // the five arrays within a slot
+    unsigned slot;                           // bytes of one slot (multiple of 128)
+    unsigned tx;                             // bytes the five copies of a plane deliver
+    unsigned roff, boff_bars, total;         // red-value array, mbarriers, whole layout
+};
+
+__host__ __device__ inline unsigned rb7_up128(unsigned v) { return (v + 127u) & ~127u; }
+
+__host__ __device__ inline RB7Layout rb7_layout(int TI, int nph, int cbytes) {
+    RB7Layout L;
+    const unsigned xb = (unsigned)((TI + 4) * nph * 4), bb = (unsigned)((TI + 3) * nph * 4);
+    const unsigned cb = (unsigned)((TI + 3) * nph * cbytes);
+    L.xoff = 0;
+    L.boff = rb7_up128(xb);
+    L.eoff = L.boff + rb7_up128(bb);
+    L.zoff = L.eoff + rb7_up128(cb);
+    L.loff = L.zoff + rb7_up128(cb);
+    L.slot = L.loff + rb7_up128(cb);
+    L.tx = xb + bb + 3 * cb;
+    L.roff = kRB7Slots * L.slot;
+    L.boff_bars = L.roff + rb7_up128((unsigned)(2 * (TI + 2) * (nph / 4) * 8));
+    L.total = L.boff_bars + 16 * kRB7Slots + 16;   // full and empty barriers, the abort flag
+    return L;
+}
+
+template <typename CT>
+struct RB7Coef;
+template <>
+struct RB7Coef<float> {
+    static constexpr int kBytes = 4;
+    __device__ static float scale(const LevelView& v, int a) { return 1.0f; }
+    __device__ static const void* array(const LevelView& v, int a) { return v.c32.g[a]; }
+    __device__ static void quad(const float* row, int k0, float, float (&v)[4]) {
+        const float4 p = *reinterpret_cast<const float4*>(row + k0);
+        v[0] = p.x, v[1] = p.y, v[2] = p.z, v[3] = p.w;
+    }
+    __device__ static float one(const float* row, int k, float) { return row[k]; }
+};
+// FP16 storage: the value is the half times the component's power-of-two
+// scale, as CoefF16 reads it
+template <>
+struct RB7Coef<__half> {
+    static constexpr int kBytes = 2;
+    __device__ static float scale(const LevelView& v, int a) { return v.c16.s[a]; }
+    __device__ static const void* array(const LevelView& v, int a) { return v.c16.g[a]; }
+    __device__ static void quad(const __half* row, int k0, float s, float (&v)[4]) {
+        const uint2 p = *reinterpret_cast<const uint2*>(row + k0);
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&p.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&p.y));
+        v[0] = lo.x * s, v[1] = lo.y * s, v[2] = hi.x * s, v[3] = hi.y * s;
+    }
+    __device__ static float one(const __half* row, int k, float s) { return __half2float(row[k]) * s; }
+};
+
+__device__ __forceinline__ void lds4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+
+// Coefficients of the quad's cells on one plane, as Cell7::load reads them:
+// b, the lower radius / colatitude / longitude faces, the upper colatitude
+// face (the next row's lower one, zero on the wall row) and the upper
+// longitude face of the last cell (the next quad's first lower one).
+struct RB7Plane {
+    float B[4], EL[4], ZL[4], ZU[4], XL[4];
+    float XLn;
+};
+
+// Red cells P, P + 2 of plane s.  X0 = the quad on plane s, XM1 = on plane
+// s - 1 (black there: old), X1 = on plane s + 1 (old); XIM / XIP = the rows
+// i -/+ 1 of plane s (old); xadj = the longitude neighbour outside the quad
+// (k0 - 1 for P = 0, k0 + 4 for P = 1); EU = the lower radius faces of plane
+// s + 1 (zero above the last plane).
+template <int P>
+__device__ __forceinline__ void rb7_red(const RB7Plane& c, const float (&EU)[4], const float (&X0)[4],
+                                        const float (&XM1)[4], const float (&X1)[4], const float (&XIM)[4],
+                                        const float (&XIP)[4], float xadj, bool jl, bool ju, bool il, bool iu,
+                                        float (&rn)[2]) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int m = P + 2 * e;
+        Cell7<float> q;
+        q.xc = X0[m];
+        q.xjm = jl ? XM1[m] : q.xc;
+        q.xjp = ju ? X1[m] : q.xc;
+        q.xim = il ? XIM[m] : q.xc;
+        q.xip = iu ? XIP[m] : q.xc;
+        q.xkm = m == 0 ? xadj : X0[m == 0 ? 0 : m - 1];
+        q.xkp = m == 3 ? xadj : X0[m == 3 ? 3 : m + 1];
+        q.el = c.EL[m], q.eu = EU[m], q.zl = c.ZL[m], q.zu = c.ZU[m], q.xl = c.XL[m];
+        q.xu = m == 3 ? c.XLn : c.XL[m == 3 ? 3 : m + 1];
+        rn[e] = q.gs(c.B[m]);
+    }
+}
+
+// Black cells P, P + 2 of plane s - 1.  XM1 = the quad on plane s - 1 (black
+// cells old, red ones new), XM2 = the new red values of plane s - 2 at P, P + 2,
+// rn = the new red values of plane s at P, P + 2; rim / rip = the new red values
+// of the rows i -/+ 1 on plane s - 1 at P, P + 2; radj = the red longitude
+// neighbour outside the quad; c = plane s - 1's coefficients; EU = plane s's
+// lower radius faces (zero when plane s does not exist).
+template <int P>
+__device__ __forceinline__ void rb7_black(const RB7Plane& c, const float (&EU)[4], const float (&XM1)[4],
+                                          const float (&XM2)[2], const float (&rn)[2], float2 rim, float2 rip,
+                                          float radj, bool jl, bool ju, bool il, bool iu, float (&bn)[2]) {
+    const float RIM[2] = {rim.x, rim.y}, RIP[2] = {rip.x, rip.y};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int m = P + 2 * e;
+        Cell7<float> q;
+        q.xc = XM1[m];
+        q.xjm = jl ? XM2[e] : q.xc;
+        q.xjp = ju ? rn[e] : q.xc;
+        q.xim = il ? RIM[e] : q.xc;
+        q.xip = iu ? RIP[e] : q.xc;
+        q.xkm = m == 0 ? radj : XM1[m == 0 ? 0 : m - 1];
+        q.xkp = m == 3 ? radj : XM1[m == 3 ? 3 : m + 1];
+        q.el = c.EL[m], q.eu = EU[m], q.zl = c.ZL[m], q.zu = c.ZU[m], q.xl = c.XL[m];
+        q.xu = m == 3 ? c.XLn : c.XL[m == 3 ? 3 : m + 1];
+        bn[e] = q.gs(c.B[m]);
+    }
+}
+
+// The finished quad of plane s - 1: the black cells P, P + 2 new (bn), the red
+// ones from XM1.
+__device__ __forceinline__ void rb7_store(float* dst, int P, const float (&bn)[2], const float (&XM1)[4]) {
+    *reinterpret_cast<float4*>(dst) = P ? make_float4(XM1[0], bn[0], XM1[2], bn[1])
+                                        : make_float4(bn[0], XM1[1], bn[1], XM1[3]);
+}
+
+template <typename CT>
+__device__ __forceinline__ void rb7_tile(const BTask& tk, int lb, unsigned char* smem) {
+    const Dims D = tk.v.D;
+    const int nph = D.nph, NQ = nph >> 2;
+    const int TI = tk.tile[0], TJ = tk.tile[1];
+    const int nI = (D.nth + TI - 1) / TI;
+    const int it = lb % nI, jc = lb / nI;
+    const int i0 = it * TI, iend = min(i0 + TI, D.nth);
+    const int j0 = jc * TJ, jend = min(j0 + TJ, D.nr);
+    const int plo = max(j0 - 2, 0), phi = min(jend + 1, D.nr - 1);
+    const RB7Layout Ly = rb7_layout(TI, nph, RB7Coef<CT>::kBytes);
+    const float sel = RB7Coef<CT>::scale(tk.v, 4), szl = RB7Coef<CT>::scale(tk.v, 0),
+                sxl = RB7Coef<CT>::scale(tk.v, 8);
+    const unsigned char* maps = (const unsigned char*)tk.tmap;   // x, b, el, zl, xl (128 bytes each)
+    float* out = (float*)tk.y;
+    float2* R = reinterpret_cast<float2*>(smem + Ly.roff);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + Ly.boff_bars);   // a plane's copies landed
+    uint64_t* empty = full + kRB7Slots;                                  // every compute warp is done with it
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kRB7Slots);
+    auto slot = [&](int p) { return smem + (size_t)((p - plo) % kRB7Slots) * Ly.slot; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncw = (int)(blockDim.x >> 5) - 1;   // compute warps; the last warp copies
+    const int s0 = max(j0 - 1, 0);
+
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < kRB7Slots; ++w) {
+            mbar_init(&full[w], 1);
+            mbar_init(&empty[w], ncw);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == ncw) {
+        // the copy warp: plane p into slot (p - plo) mod 4 once the compute
+        // warps have released the plane four before it
+        if (lane == 0) {
+            for (int m = 0; m < 5; ++m) tmap_acquire(maps + 128 * m);
+            int end = plo;   // planes plo .. end - 1 copied
+            for (int p = plo; p <= phi && !*abort_flag; ++p) {
+                const int w = (p - plo) % kRB7Slots, k = (p - plo) / kRB7Slots;
+                if (k > 0 && !mbar_wait(&empty[w], (unsigned)((k - 1) & 1))) break;
+                unsigned char* sl = smem + (size_t)w * Ly.slot;
+                mbar_expect_tx(&full[w], Ly.tx);
+                tma_load_3d(sl + Ly.xoff, maps, 0, i0 - 2, p, &full[w]);
+                tma_load_3d(sl + Ly.boff, maps + 128, 0, i0 - 1, p, &full[w]);
+                tma_load_3d(sl + Ly.eoff, maps + 256, 0, i0 - 1, p, &full[w]);
+                tma_load_3d(sl + Ly.zoff, maps + 384, 0, i0 - 1, p, &full[w]);
+                tma_load_3d(sl + Ly.loff, maps + 512, 0, i0 - 1, p, &full[w]);
+                end = p + 1;
+            }
+            // the compute warps stopped early (a copy that did not land): the
+            // copies in flight still write the slots; wait for them (bounded)
+            if (*abort_flag)
+                for (int p = max(plo, end - kRB7Slots); p < end; ++p)   // the last copy into each slot
+                    mbar_wait(&full[(p - plo) % kRB7Slots], (unsigned)(((p - plo) / kRB7Slots) & 1));
+        }
+    } else {
+        // this thread's quad: unit row r (colatitude i0 - 1 + r), quad q
+        const int u = threadIdx.x;
+        const int r = u / NQ, q = u - r * NQ;
+        const int i = i0 - 1 + r;
+        const bool valid = u < (TI + 2) * NQ && i >= 0 && i <= iend && i < D.nth;
+        const bool interior = valid && i >= i0 && i < iend;
+        const int k0 = 4 * q;
+        const bool il = i > 0, iu = i + 1 < D.nth;
+        const int xr = (r + 1) * nph;                 // own row in the x buffers
+        const int cr = r * nph;                       // own row in the b and coefficient buffers
+        const int km = k0 == 0 ? nph - 1 : k0 - 1;    // longitude neighbours outside the quad
+        const int kp = k0 + 4 == nph ? 0 : k0 + 4;
+        const int qm = q == 0 ? NQ - 1 : q - 1, qp = q + 1 == NQ ? 0 : q + 1;
+        const unsigned nct = (unsigned)(ncw * 32);
+        auto sync_compute = [&]() { asm volatile("bar.sync 1, %0;\n" ::"r"(nct) : "memory"); };
+        auto release = [&](int p) {   // this warp has read plane p for the last time
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[(p - plo) % kRB7Slots]);
+        };
+        int waited = plo - 1;
+        auto wait_upto = [&](int need) {
+            bool ok = true;
+            while (waited < need && ok) {
+                const int p = waited + 1;
+                ok = mbar_wait(&full[(p - plo) % kRB7Slots], (unsigned)(((p - plo) / kRB7Slots) & 1));
+                if (ok) waited = p;
+            }
+            if (!ok) *abort_flag = 1;
+            return ok;
+        };
+
+        // state at the first step s0: the quad on planes s0 - 1 and s0 (old)
+        float xm2[2] = {0.f, 0.f}, xm1[4] = {0.f, 0.f, 0.f, 0.f}, x0[4] = {0.f, 0.f, 0.f, 0.f};
+        RB7Plane kc;   // coefficients of plane s - 1 (its black cells are updated in step s)
+        for (int m = 0; m < 4; ++m) kc.B[m] = kc.EL[m] = kc.ZL[m] = kc.ZU[m] = kc.XL[m] = 0.f;
+        kc.XLn = 0.f;
+        if (wait_upto(min(s0, phi)) && valid) {
+            if (s0 > 0) lds4(reinterpret_cast<const float*>(slot(s0 - 1) + Ly.xoff) + xr + k0, xm1);
+            lds4(reinterpret_cast<const float*>(slot(s0) + Ly.xoff) + xr + k0, x0);
+        }
+        if (s0 > plo) release(plo);
+        sync_compute();
+
+        for (int s = s0; s <= jend && !*abort_flag; ++s) {
+            const bool ok = wait_upto(min(s + 1, phi));
+            const bool red = s < D.nr;          // plane s exists
+            const bool ju = s + 1 < D.nr;       // plane s + 1 exists
+            const bool blk = interior && s - 1 >= j0;
+            const int P = (i + s) & 1;
+            float rn[2] = {0.f, 0.f};
+            RB7Plane c;
+            float EU[4] = {0.f, 0.f, 0.f, 0.f};   // lower radius faces of plane s + 1
+            float ELs[4] = {0.f, 0.f, 0.f, 0.f};  // lower radius faces of plane s (black's upper faces)
+            if (ok && valid && red) {
+                const unsigned char* sl = slot(s);
+                const float* X = reinterpret_cast<const float*>(sl + Ly.xoff);
+                const CT* EL = reinterpret_cast<const CT*>(sl + Ly.eoff);
+                const CT* ZL = reinterpret_cast<const CT*>(sl + Ly.zoff);
+                const CT* XL = reinterpret_cast<const CT*>(sl + Ly.loff);
+                lds4(reinterpret_cast<const float*>(sl + Ly.boff) + cr + k0, c.B);
+                RB7Coef<CT>::quad(EL + cr, k0, sel, c.EL);
+                RB7Coef<CT>::quad(ZL + cr, k0, szl, c.ZL);
+                if (iu) RB7Coef<CT>::quad(ZL + cr + nph, k0, szl, c.ZU);
+                else c.ZU[0] = c.ZU[1] = c.ZU[2] = c.ZU[3] = 0.f;
+                RB7Coef<CT>::quad(XL + cr, k0, sxl, c.XL);
+                c.XLn = RB7Coef<CT>::one(XL + cr, kp, sxl);
+                for (int m = 0; m < 4; ++m) ELs[m] = c.EL[m];
+                float X1[4] = {0.f, 0.f, 0.f, 0.f}, XIM[4], XIP[4];
+                if (ju) {
+                    const unsigned char* sl1 = slot(s + 1);
+                    lds4(reinterpret_cast<const float*>(sl1 + Ly.xoff) + xr + k0, X1);
+                    RB7Coef<CT>::quad(reinterpret_cast<const CT*>(sl1 + Ly.eoff) + cr, k0, sel, EU);
+                }
+                lds4(X + xr - nph + k0, XIM);
+                lds4(X + xr + nph + k0, XIP);
+                const float xadj = X[xr + (P == 0 ? km : kp)];
+                if (P == 0) rb7_red<0>(c, EU, x0, xm1, X1, XIM, XIP, xadj, s > 0, ju, il, iu, rn);
+                else rb7_red<1>(c, EU, x0, xm1, X1, XIM, XIP, xadj, s > 0, ju, il, iu, rn);
+                R[(s & 1) * (TI + 2) * NQ + r * NQ + q] = make_float2(rn[0], rn[1]);
+                if (blk) {
+                    const float2* Rp = R + ((s - 1) & 1) * (TI + 2) * NQ;
+                    const float2 rim = il ? Rp[(r - 1) * NQ + q] : make_float2(0.f, 0.f);
+                    const float2 rip = iu ? Rp[(r + 1) * NQ + q] : make_float2(0.f, 0.f);
+                    const float radj = P == 0 ? Rp[r * NQ + qm].y : Rp[r * NQ + qp].x;
+                    float bn[2];
+                    if (P == 0) rb7_black<0>(kc, ELs, xm1, xm2, rn, rim, rip, radj, s - 1 > 0, true, il, iu, bn);
+                    else rb7_black<1>(kc, ELs, xm1, xm2, rn, rim, rip, radj, s - 1 > 0, true, il, iu, bn);
+                    rb7_store(out + ((i64)(s - 1) * D.nth + i) * nph + k0, P, bn, xm1);
+                }
+                // shift: plane s - 1's red values become the next step's plane
+                // s - 2 values, plane s (red new, black old) the next plane
+                // s - 1, plane s + 1 the next plane s; plane s's coefficients
+                // the next step's black ones (selects, not indexing by P: the
+                // arrays stay in registers)
+                xm2[0] = P ? xm1[0] : xm1[1];
+                xm2[1] = P ? xm1[2] : xm1[3];
+                xm1[0] = P ? x0[0] : rn[0];
+                xm1[1] = P ? rn[0] : x0[1];
+                xm1[2] = P ? x0[2] : rn[1];
+                xm1[3] = P ? rn[1] : x0[3];
+                x0[0] = X1[0], x0[1] = X1[1], x0[2] = X1[2], x0[3] = X1[3];
+                kc = c;
+            } else if (ok && blk) {
+                // the last plane's black cells (s == nr: no plane above them)
+                const float2* Rp = R + ((s - 1) & 1) * (TI + 2) * NQ;
+                const float2 rim = il ? Rp[(r - 1) * NQ + q] : make_float2(0.f, 0.f);
+                const float2 rip = iu ? Rp[(r + 1) * NQ + q] : make_float2(0.f, 0.f);
+                const float radj = P == 0 ? Rp[r * NQ + qm].y : Rp[r * NQ + qp].x;
+                float bn[2];
+                if (P == 0) rb7_black<0>(kc, ELs, xm1, xm2, rn, rim, rip, radj, s - 1 > 0, false, il, iu, bn);
+                else rb7_black<1>(kc, ELs, xm1, xm2, rn, rim, rip, radj, s - 1 > 0, false, il, iu, bn);
+                rb7_store(out + ((i64)(s - 1) * D.nth + i) * nph + k0, P, bn, xm1);
+            }
+            if (ok && s <= phi) release(s);   // plane s is not read again
+            sync_compute();                   // the red values of plane s are in R
+        }
+        if (*abort_flag) {
+            const float nan = __int_as_float(0x7fc00000);
+            const int per = (iend - i0) * nph;
+            for (int p = j0; p < jend; ++p)
+                for (int t = threadIdx.x; t < per; t += (int)nct) out[((i64)p * D.nth + i0) * nph + t] = nan;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (*abort_flag) atomicOr(&g_sweep_fault, 1u);
+        for (int w = 0; w < kRB7Slots; ++w) {
+            mbar_inval(&full[w]);
+            mbar_inval(&empty[w]);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(kRB7Max, 1) k_rb7(const BTask* __restrict__ tasks, int ntasks, int total,
+                                                    const int* __restrict__ active, int early_trigger) {
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];
+    __shared__ int tk_index;
+    const BTask& tk = *reinterpret_cast<const BTask*>(tk_raw);
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = ntasks - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&tasks[mid].block0) <= vb) lo = mid;
+                else hi = mid - 1;
+            }
+            tk_index = lo;
+        }
+        __syncthreads();
+        {
+            const unsigned* src = reinterpret_cast<const unsigned*>(tasks + tk_index);
+            unsigned* dst = reinterpret_cast<unsigned*>(tk_raw);
+            for (int w = threadIdx.x; w < (int)(sizeof(BTask) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
+        }
+        __syncthreads();
+        if (!active || active[tk.shell]) {
+            const BTask t = tk;   // register copy: the stages write shared memory
+            rb7_tile<CT>(t, vb - t.block0, dyn);
+        }
+        __syncthreads();
+    }
+    if (!early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename CT>
+cudaError_t rb7_launch(const BTask* tasks, int ntasks, int total, const int* active, size_t smem, int threads,
+                       cudaStream_t s) {
+    if (threads < 32 || threads > kRB7Max) return cudaErrorInvalidConfiguration;
+    int per_sm = 0;
+    cudaError_t e = sweep_per_sm(k_rb7<CT>, threads, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(total, 152 * per_sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[0].val.programmaticStreamSerializationAllowed = sweep_pdl() ? 1 : 0;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_rb7<CT>, tasks, ntasks, total, active, grid >= total ? 1 : 0);
+}
+
+bool rb7_path(int stencil, int prec) { return stencil == 7 && prec != PREC64; }
+
 }  // namespace
 
 bool sweep_tile_ok(const Dims& D, int stencil, int prec, const int tile[3]) {
     const int vb = prec == PREC64 ? 8 : 4;
     const int TI = tile[0], TJ = tile[1], TK = tile[2];
     if (TI < 1 || TJ < 1 || TK < 1 || D.cut) return false;
+    if (rb7_path(stencil, prec)) {
+        // whole rows of quads; every copy's rows a multiple of 16 bytes and at
+        // most 256 elements wide; one thread per quad of TI + 2 rows
+        const int cbytes = prec == PREC16 ? 2 : 4;
+        if (TK != D.nph || D.nph % 4 != 0 || (D.nph * cbytes) % 16 != 0 || D.nph > 256) return false;
+        if ((TI + 2) * (D.nph / 4) > kRB7MaxThreads || TI + 4 > 256) return false;
+        return sweep_smem_bytes(stencil, prec, D, tile) <= 227 * 1024;
+    }
     if ((D.nph * vb) % 16 != 0) return false;                  // row stride of the map
     if (D.nph % TK != 0 || (TK * vb) % 16 != 0) return false;  // whole 16-byte stores
     const bool full = TK == D.nph;
@@ -611,6 +1062,7 @@ bool sweep_tile_ok(const Dims& D, int stencil, int prec, const int tile[3]) {
 }
 
 size_t sweep_smem_bytes(int stencil, int prec, const Dims& D, const int tile[3]) {
+    if (rb7_path(stencil, prec)) return rb7_layout(tile[0], D.nph, prec == PREC16 ? 2 : 4).total;
     const int vb = prec == PREC64 ? 8 : 4;
     const bool full = tile[2] == D.nph;
     const size_t cols = full ? D.nph : tile[2] + 2 * halo_cols(stencil, vb);
@@ -623,32 +1075,66 @@ int sweep_units(const Dims& D, const int tile[3]) {
     return ((D.nr + tile[1] - 1) / tile[1]) * ((D.nth + tile[0] - 1) / tile[0]) * (D.nph / tile[2]);
 }
 
-cudaError_t encode_sweep_map(void* map, const void* x, const Dims& D, int stencil, int prec, const int tile[3]) {
+int sweep_threads(int stencil, int prec, const Dims& D, const int tile[3]) {
+    if (!rb7_path(stencil, prec)) return kSW;
+    return ((tile[0] + 2) * (D.nph / 4) + 31) / 32 * 32 + 32;   // the quads' warps and the copy warp
+}
+
+int sweep_map_count(int stencil, int prec) { return rb7_path(stencil, prec) ? 5 : 1; }
+
+namespace {
+
+// One 3-D map (longitude, colatitude, radius) of an [nr][nth][nph] array with
+// boxes of whole rows: `rows` rows, one plane.
+cudaError_t encode_rows(void* map, const void* base, const Dims& D, CUtensorMapDataType dt, int ebytes, int cols,
+                        int rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    const int vb = prec == PREC64 ? 8 : 4;
-    const bool full = tile[2] == D.nph;
     const cuuint64_t dims[3] = {(cuuint64_t)D.nph, (cuuint64_t)D.nth, (cuuint64_t)D.nr};
-    const cuuint64_t strides[2] = {(cuuint64_t)D.nph * vb, (cuuint64_t)D.nph * D.nth * vb};
-    const cuuint32_t box[3] = {(cuuint32_t)(full ? D.nph : tile[2] + 2 * halo_cols(stencil, vb)),
-                               (cuuint32_t)(tile[0] + 2 * halo_rows(stencil)), 1u};
+    const cuuint64_t strides[2] = {(cuuint64_t)D.nph * ebytes, (cuuint64_t)D.nph * D.nth * ebytes};
+    const cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)rows, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map),
-                          vb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                          const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+}  // namespace
+
+cudaError_t encode_sweep_maps(void* maps, const BTask& t, int stencil, int prec) {
+    const Dims& D = t.v.D;
+    unsigned char* m = static_cast<unsigned char*>(maps);
+    if (rb7_path(stencil, prec)) {
+        // x (rows i0 - 2 .. i0 + TI + 1), b and the lower radius, colatitude and
+        // longitude faces (rows i0 - 1 .. i0 + TI + 1)
+        const int TI = t.tile[0];
+        const bool h = prec == PREC16;
+        const CUtensorMapDataType ct = h ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        const int cb = h ? 2 : 4;
+        const void* c[3] = {h ? (const void*)t.v.c16.g[4] : (const void*)t.v.c32.g[4],
+                            h ? (const void*)t.v.c16.g[0] : (const void*)t.v.c32.g[0],
+                            h ? (const void*)t.v.c16.g[8] : (const void*)t.v.c32.g[8]};
+        cudaError_t e = encode_rows(m, t.x, D, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, D.nph, TI + 4);
+        if (e == cudaSuccess) e = encode_rows(m + 128, t.b, D, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, D.nph, TI + 3);
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = encode_rows(m + 256 + 128 * a, c[a], D, ct, cb, D.nph, TI + 3);
+        return e;
+    }
+    const int vb = prec == PREC64 ? 8 : 4;
+    const bool full = t.tile[2] == D.nph;
+    return encode_rows(m, t.x, D, vb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, vb,
+                       full ? D.nph : t.tile[2] + 2 * halo_cols(stencil, vb), t.tile[0] + 2 * halo_rows(stencil));
+}
+
 cudaError_t launch_sweep(const BTask* tasks, int ntasks, int total, const int* active, int stencil, bool axi,
-                         int prec, size_t smem, cudaStream_t s) {
+                         int prec, size_t smem, int threads, cudaStream_t s) {
     if (ntasks <= 0 || total <= 0) return cudaSuccess;
     cudaError_t e;
-    if (stencil == 7) {
-        if (prec == PREC64) e = sweep_launch<7, PREC64, false>(tasks, ntasks, total, active, smem, s);
-        else if (prec == PREC32) e = sweep_launch<7, PREC32, false>(tasks, ntasks, total, active, smem, s);
-        else e = sweep_launch<7, PREC16, false>(tasks, ntasks, total, active, smem, s);
+    if (rb7_path(stencil, prec)) {
+        if (prec == PREC16) e = rb7_launch<__half>(tasks, ntasks, total, active, smem, threads, s);
+        else e = rb7_launch<float>(tasks, ntasks, total, active, smem, threads, s);
+    } else if (stencil == 7) {   // FP64 (FP32 / FP16 take the red-black kernel above)
+        e = sweep_launch<7, PREC64, false>(tasks, ntasks, total, active, smem, s);
     } else if (axi) {
         if (prec == PREC64) e = sweep_launch<19, PREC64, true>(tasks, ntasks, total, active, smem, s);
         else if (prec == PREC32) e = sweep_launch<19, PREC32, true>(tasks, ntasks, total, active, smem, s);

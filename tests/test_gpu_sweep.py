@@ -8,7 +8,11 @@ orders are red/black by (i + j + k) mod 2 for 7 points and the four colours
 through MG_TILE ("cells,planes,kmax"): whole longitude rows, tiles narrower
 than the grid (both longitude seams), chunks of one to three planes, ragged
 last tiles in every direction; grids with odd counts, stretched radii, the
-axisymmetric 19-point operator and the full one.
+axisymmetric 19-point operator and the full one.  The 7-point sweep of the
+FP32 and FP16-coefficient cycles (whole rows, one thread per four
+longitudes, x, b and the face coefficients staged by bulk copies) takes its
+rows from the plane area (cells / nph, at least one) and the chunk depth
+from MG_TILE.
 """
 import numpy as np
 import pytest
@@ -82,7 +86,10 @@ def test_one_pass_sweep_matches_oracle(lib, name, prec, tile, monkeypatch):
     b = rng.standard_normal(lv.n) * np.abs(lv.D)
     for sweeps in (1, 2, 3):
         x, sc = _sweep(lib, g, prec, x0, b, sweeps, TILES[tile], monkeypatch)
-        assert sc["one_pass_tiles"] == 1 and sc["tile0"][0] > 0, sc
+        assert sc["one_pass_tiles"] == 1, sc
+        # the 7-point FP32 / FP16 sweep takes whole rows of at most 256
+        # longitudes; wider grids keep the colour passes
+        assert sc["tile0"][0] > 0 or (st == 7 and prec != 0 and g["nph"] > 256), sc
         ref = omg.smooth(lv, _np(_dev(x0, prec)), _np(_dev(b, prec)), sweeps, omg.GS)
         np.testing.assert_allclose(x, ref, rtol=0, atol=TOL[prec] * np.abs(ref).max(),
                                    err_msg=f"{sweeps} sweeps, tile {sc['tile0']}")
@@ -118,3 +125,23 @@ def test_one_pass_sweep_covers_the_bench_shapes(lib, monkeypatch):
         sc = lib.mg_get_schedule(h)
         assert sc["one_pass_tiles"] == 1 and min(sc["tile0"]) > 0, (wl, sc)
         h.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_red_black_sweep_at_full_size_is_the_colour_passes(lib, prec, monkeypatch):
+    """The 128 x 128 x 256 sphere's two finest levels in the automatic tile
+    shape (the one the solves use): one-pass sweeps bit for bit the colour
+    passes, and the tile is whole rows."""
+    g = W.single("single_sphere_128", 1)["grid"]
+    rng = np.random.default_rng(11)
+    for level in (0, 1):
+        h = lib.mg_setup(g, dict(precision=1))
+        info = lib.mg_get_level_info(h, level)
+        h.close()
+        n = info["nr"] * info["nth"] * info["nph"]
+        x0, b = rng.standard_normal(n), rng.standard_normal(n)
+        a, sc = _sweep(lib, g, prec, x0, b, 2, None, monkeypatch, True, level)
+        c, _ = _sweep(lib, g, prec, x0, b, 2, None, monkeypatch, False, level)
+        if level == 0:
+            assert sc["tile0"][2] == g["nph"] and sc["tile0"][0] >= 1, sc
+        assert np.array_equal(a, c), f"level {level}"
