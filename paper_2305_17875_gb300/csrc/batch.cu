@@ -43,9 +43,12 @@ struct Prec<PREC16> {
 };
 
 // multicolour Gauss-Seidel colour pass (same cells and arithmetic as stencil.cu)
+// poles (19 points on the full sphere): the first and last rows of x as they
+// were before the pass (BOP_POLES), read for the cells across the pole: cells
+// of one colour couple across the pole, and a colour is updated as one step.
 template <int S, typename T, typename CF>
 __device__ __forceinline__ void gs_pass(const CF& cf, const Dims& D, T* x, const T* b, int colour, i64 first,
-                                        i64 stride) {
+                                        i64 stride, const T* poles = nullptr) {
     const int hk = D.nph >> 1;
     if constexpr (S == 7) {
         const i64 work = (i64)D.nr * D.nth * hk;
@@ -69,7 +72,7 @@ __device__ __forceinline__ void gs_pass(const CF& cf, const Dims& D, T* x, const
             const C3 p{j, i, 2 * kk + (((colour >> 1) + j) & 1)};
             const int c = cidx(D, p);
             Nbr19<T> X;
-            X.load(XLin<T>{x}, D, c, p, !cf.has(2));
+            X.load(XLin<T>{x}, D, c, p, !cf.has(2), poles);
             const T r = b[c] - apply19<T>(cf, X, D, c, p);
             x[c] = X.v[0] + r / diag_cell<S, T>(cf, D, p);
         }
@@ -592,7 +595,7 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         // 19 points: the scalar form (a group would load four cells to update two
         // with twice the registers); 7 points: groups when nph is a multiple of 4
         if (S == 7 && vec4(tk.v.D)) gs_pass7v<T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
-        else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
+        else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride, (const T*)tk.z);
     } else if constexpr (OP == BOP_LINE) {
         line_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
     } else if constexpr (OP == BOP_XLINE) {
@@ -622,7 +625,7 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         if (S == 7 && vec4(tk.v.D))
             restrict_pass7v<T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
                                (T*)tk.y, (T*)tk.z, first, stride);
-        else if (S == 19 && vec4(tk.v.D))
+        else if (S == 19 && vec4(tk.v.D) && !tk.v.D.cut)   // (the groups know no pole partners)
             restrict_pass19v<T>(cf, tk.v.D, (const T*)tk.x, (const T*)tk.b, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx,
                                 (T*)tk.y, (T*)tk.z, first, stride);
         else
@@ -729,6 +732,18 @@ __global__ void __launch_bounds__(kBT, min_ctas<P, OP, S>()) k_batch(const BTask
                 st4(x + 4 * g, X);
             }
             for (i64 c = 4 * n4 + first; c < tk.n; c += stride) x[c] += scaled_widen(e[c], k);
+        } else if constexpr (OP == BOP_POLES) {   // rows 0 and nth - 1 of x -> z [side][j][k]
+            typedef typename Prec<P>::T T;
+            const Dims& D = tk.v.D;
+            const T* x = (const T*)tk.x;
+            T* z = (T*)tk.z;
+            const i64 per = (i64)D.nr * D.nph;
+            for (i64 e = first; e < 2 * per; e += stride) {
+                const int side = e >= per ? 1 : 0;
+                const i64 r = e - side * per;
+                const int j = (int)(r / D.nph), k = (int)(r - (i64)j * D.nph);
+                z[e] = x[((i64)j * D.nth + (side ? D.nth - 1 : 0)) * D.nph + k];
+            }
         } else if constexpr (OP == BOP_ZERO) {
             unsigned* x = (unsigned*)tk.x;
             for (i64 g = first; g < n4; g += stride) reinterpret_cast<uint4*>(x)[g] = make_uint4(0u, 0u, 0u, 0u);
@@ -884,6 +899,7 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
         PLAIN_OP(BOP_PRESTRICT)
         PLAIN_OP(BOP_PPROLONG)
         PLAIN_OP(BOP_PUPDATE)
+        PLAIN_OP(BOP_POLES)
         default:
             return cudaErrorInvalidValue;
     }

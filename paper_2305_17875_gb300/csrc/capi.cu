@@ -136,7 +136,12 @@ int stencil_of(const mg_grid_desc* g, const mg_opts* o) {
 
 // Combinations of a valid grid and valid options that are not built.
 std::string check_pair(const mg_grid_desc* g, const mg_opts* o) {
-    if (g->cut && stencil_of(g, o) != 7) return "the shell cut is built for the 7-point operator only";
+    if (g->cut && stencil_of(g, o) == 19) {
+        if (g->mapping == MG_MAP_TRIAXIAL)
+            return "the shell cut with 19 points is built for axisymmetric mappings (sphere, oblate) only";
+        if (o->smoother != MG_SMOOTH_GS && o->smoother != MG_SMOOTH_JACOBI)
+            return "the shell cut with 19 points is built for the point smoothers (Gauss-Seidel, Jacobi) only";
+    }
     if (o->smoother == MG_SMOOTH_PLANE) {
         if (stencil_of(g, o) != 7) return "plane relaxation is built for the 7-point operator only";
         if (g->nr & (g->nr - 1)) return "plane relaxation needs nr a power of two (the plane cycles end on one row)";
@@ -442,6 +447,7 @@ mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
 mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
     h->tail_level = 0;
     if (cells <= 0 || h->opts.smoother != MG_SMOOTH_GS) return MG_OK;
+    if (h->grid.cut && h->stencil == 19) return MG_OK;   // the tail's passes know no pole copy
     const int nl = (int)h->L.size();
     int t = nl;
     while (t - 1 >= 1 && h->L[t - 1].D.n() <= cells) --t;
@@ -621,6 +627,12 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
     if (const char* v = std::getenv("MG_TEST_FAIL_ALLOC_AFTER")) h->fail_alloc_after = std::atoll(v);
     h->stencil = stencil_of(g, o);
     h->axi = h->stencil == 19 && g->mapping != MG_MAP_TRIAXIAL && std::getenv("MG_FULL19") == nullptr;
+    if (g->cut && h->stencil == 19 && !h->axi) {
+        // the longitude cross terms would couple a cell with itself across the
+        // pole on a two-longitude level, which the cell-wise diagonal ignores
+        set_error("the shell cut with 19 points needs the axisymmetric operator (no longitude cross terms)");
+        return MG_EINVAL;
+    }
     h->prec = o->precision;
     h->user_stream = stream;
     h->use_graph = std::getenv("MG_NO_GRAPH") == nullptr;
@@ -809,6 +821,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
         Level& lv = h->L[l];
         const i64 n = lv.D.n();
         if (!(lv.t = dalloc(h, sizeof(double) * n))) return MG_ENOMEM;
+        if (lv.D.cut && h->stencil == 19 && !(lv.poles = dalloc(h, sizeof(double) * 2 * lv.D.nr * lv.D.nph)))
+            return MG_ENOMEM;
         if (l == 0) {
             if (h->prec != PREC64) {
                 if (!(lv.e = dalloc(h, sizeof(float) * n))) return MG_ENOMEM;
@@ -1151,8 +1165,15 @@ mg_status smooth(mg_handle* h, int level, int prec, void* x, const void* b, int 
                                 h->stream));
     } else if (kind == MG_SMOOTH_GS) {
         const int ncol = h->stencil == 7 ? 2 : 4;
+        const bool poles = h->stencil == 19 && lv.D.cut;   // cells of a colour couple across the pole
         for (int s = 0; s < sweeps; ++s)
-            for (int c = 0; c < ncol; ++c, ++n) CK(launch_gs_colour(v, prec, x, b, c, h->stream));
+            for (int c = 0; c < ncol; ++c, ++n) {
+                if (poles) {
+                    CK(launch_poles(v, prec, x, lv.poles, h->stream));
+                    ++n;
+                }
+                CK(launch_gs_colour(v, prec, x, b, c, h->stream, poles ? lv.poles : nullptr));
+            }
     } else if (kind == MG_SMOOTH_LINE || kind == MG_SMOOTH_XLINE || kind == MG_SMOOTH_ALT) {
         // radial lines, longitude lines, or both in that order per sweep; a
         // level narrower than four longitudes takes a point sweep for the

@@ -36,6 +36,7 @@ struct Level {
     void* e = nullptr;   // correction / iterate
     void* r = nullptr;   // right side on this level
     void* t = nullptr;   // scratch (Jacobi)
+    void* poles = nullptr;   // 19 points on the full sphere: rows 0 and nth - 1 before a colour pass (2 nr nph values)
     void* lf[2] = {};    // radial-line factors, double / float (3 n values), made on first use
     void* xf[2] = {};    // longitude-line factors, double / float (4 n values), made on first use
     std::vector<PlaneLevel> planes;   // plane hierarchy (semi-coarsening multigrid), made at set-up

@@ -256,8 +256,9 @@ __global__ void k_dense(CoefF64 cf, Dims D, double* A) {
 
 // Assembled operator rows of a level (row_off order): coefficient n of cell c is
 // the operator applied to the unit vector of neighbour n, evaluated at c.  A
-// neighbour that coincides with an earlier one (a longitude ring of two cells)
-// keeps its coefficient on the earlier entry and stores 0.
+// neighbour that coincides with an earlier one (a longitude ring of two cells,
+// or a cell across the pole that is also a longitude neighbour) keeps its
+// coefficient on the earlier entry and stores 0.
 template <int S>
 __global__ void k_assemble(CoefF64 cf, Dims D, double* a, int nrows) {
     const i64 N = D.n();
@@ -272,7 +273,11 @@ __global__ void k_assemble(CoefF64 cf, Dims D, double* a, int nrows) {
             const int j = p.j + row_off(n, 0), i = p.i + row_off(n, 1);
             int k = p.k + row_off(n, 2);
             k = k < 0 ? k + D.nph : (k >= D.nph ? k - D.nph : k);
-            t[n] = (j < 0 || j >= D.nr || i < 0 || i >= D.nth) ? -1 : (i64)cidx(D, j, i, k);
+            int cell, pole;
+            if (j >= 0 && j < D.nr && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole))
+                t[n] = cell;   // the cell across the pole
+            else
+                t[n] = (j < 0 || j >= D.nr || i < 0 || i >= D.nth) ? -1 : (i64)cidx(D, j, i, k);
             bool dup = false;
             for (int m = 0; m < n; ++m) dup = dup || (t[n] >= 0 && t[m] == t[n]);
             a[n * N + cl] = (t[n] < 0 || dup) ? 0.0 : apply_cell<19, double>(cf, UnitX{t[n], D}, D, p);

@@ -93,6 +93,10 @@ template <int q>
 __device__ __forceinline__ C3 shift(C3 c, int s, const Dims& D) {
     if (q == 0) {
         int v = c.i + s;
+        if (D.cut && (v < 0 || v >= D.nth)) {   // across a pole: same row, longitude + nph/2
+            const int k = c.k + (D.nph >> 1);
+            c.k = k >= D.nph ? k - D.nph : k;
+        }
         c.i = v < 0 ? 0 : (v >= D.nth ? D.nth - 1 : v);
     } else if (q == 1) {
         int v = c.j + s;
@@ -277,8 +281,10 @@ __device__ __forceinline__ T diag_cell_r(const R& cr, const Dims& D, C3 c) {
     dg -= (T)cr.template at<0>(8);
     dg -= (T)cr.template at<3>(8);
     if (S == 19) {
-        // mirrored-onto-self weight along q: +1 at the top wall, -1 at the bottom
-        const T sz = (T)((c.i == D.nth - 1) - (c.i == 0));   // q = zeta
+        // mirrored-onto-self weight along q: +1 at the top wall, -1 at the
+        // bottom (none in colatitude on the full sphere: the neighbour beyond
+        // a pole row is the cell across the pole)
+        const T sz = D.cut ? (T)0 : (T)((c.i == D.nth - 1) - (c.i == 0));   // q = zeta
         const T se = (T)((c.j == D.nr - 1) - (c.j == 0));    // q = eta
         if (sz != (T)0) {
             T w = 0;
@@ -398,7 +404,8 @@ struct Cell7 {
 // longitude, then the radius-colatitude, radius-longitude and
 // colatitude-longitude edges, each as (-,-), (-,+), (+,-), (+,+).  A neighbour
 // beyond a wall has coefficient 0 (its mirrored contributions sit on the cell
-// it is mirrored onto).  The 7-point row stores only the centre; its six face
+// it is mirrored onto); on the full sphere a neighbour beyond a pole row is
+// the cell across the pole (across_pole) and keeps its own coefficient.  The 7-point row stores only the centre; its six face
 // coefficients are the G arrays themselves.
 __host__ __device__ constexpr int row_off(int n, int axis) {   // axis 0 radius, 1 colatitude, 2 longitude
     if (n == 0) return 0;
@@ -421,24 +428,48 @@ __host__ __device__ constexpr int row_index(int dj, int di, int dk) {
                                             : 15 + 2 * (di > 0) + (dk > 0);
 }
 
+// The cell across a pole of the shell cut for the 19-point neighbour at
+// colatitude offset di of a cell in the first or last row: the same row,
+// radius j + dj (mirrored at the radial walls), longitude k + dk + nph/2.
+// Its place in a pole-row copy laid out [side][j][k] (side 0: row 0, 1: row
+// nth - 1) is returned in *pole.
+__device__ __forceinline__ bool across_pole(const Dims& D, C3 p, int dj, int di, int dk, int* cell, int* pole) {
+    if (!D.cut || di == 0 || (di < 0 && p.i > 0) || (di > 0 && p.i + 1 < D.nth)) return false;
+    const int j = (p.j + dj < 0 || p.j + dj >= D.nr) ? p.j : p.j + dj;
+    int k = p.k + dk + (D.nph >> 1);
+    k = k < 0 ? k + D.nph : (k >= D.nph ? k - D.nph : k);
+    *cell = (j * D.nth + p.i) * D.nph + k;
+    *pole = ((di < 0 ? 0 : 1) * D.nr + j) * D.nph + k;
+    return true;
+}
+
 // x on the 19-point neighbourhood of cell c, with the operator's neighbour
-// rules: mirror (clamp) at the radial and colatitude walls, wrap in longitude.
+// rules: mirror (clamp) at the radial and colatitude walls, wrap in longitude,
+// and on the full sphere the cell across the pole beyond the first and last
+// colatitude rows.
 template <typename T>
 struct Nbr19 {
     T v[19];
     // axi: the longitude cross terms are absent, so the eight edges with a
-    // longitude offset and a radial or colatitude offset are not read (zero)
+    // longitude offset and a radial or colatitude offset are not read (zero).
+    // poles: a copy of the first and last rows of x taken before a colour pass
+    // (the values every cell of the pass must see across the pole), or null.
     template <typename XL>
-    __device__ __forceinline__ void load(const XL& X, const Dims& D, int c, C3 p, bool axi) {
+    __device__ __forceinline__ void load(const XL& X, const Dims& D, int c, C3 p, bool axi,
+                                         const T* poles = nullptr) {
         const int plane = D.nth * D.nph;
         const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
         const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
         const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
+        const bool pole_row = D.cut && (p.i == 0 || p.i + 1 == D.nth);
 #pragma unroll
         for (int n = 0; n < 19; ++n) {
             const bool phi_edge = row_off(n, 2) != 0 && (row_off(n, 0) != 0 || row_off(n, 1) != 0);
-            v[n] = (axi && phi_edge) ? (T)0
-                                     : X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
+            int cell, pole;
+            if (axi && phi_edge) v[n] = (T)0;
+            else if (pole_row && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole))
+                v[n] = poles ? poles[pole] : X(cell);
+            else v[n] = X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
         }
     }
     // value at offset a along paper direction da and b along direction db
@@ -508,11 +539,14 @@ __device__ __forceinline__ double resid_rows19(const double* __restrict__ a, i64
     const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
     const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
     const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
+    const bool pole_row = D.cut && (p.i == 0 || p.i + 1 == D.nth);
     double r = b;
 #pragma unroll
     for (int n = 0; n < 19; ++n) {
         if (n >= nrows) break;
-        const int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
+        int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
+        int cell, pole;
+        if (pole_row && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole)) o = cell - c;
         r = fma(-__ldcs(a + n * N + c), __ldg(x + c + o), r);
     }
     return r;

@@ -85,8 +85,12 @@ cudaError_t launch_finalize(const double* partials, int nparts, int op, double* 
 
 // ---- level operations (stencil.cu); x/b/y are double* for PREC64, float* otherwise
 cudaError_t launch_apply(const LevelView& lv, int prec, const void* x, void* y, cudaStream_t s);
+// poles: for 19 points on the full sphere, the first and last rows of x as the
+// pass starts (launch_poles), else null.
 cudaError_t launch_gs_colour(const LevelView& lv, int prec, void* x, const void* b, int colour,
-                             cudaStream_t s);
+                             cudaStream_t s, const void* poles = nullptr);
+// Rows 0 and nth - 1 of x into poles, laid out [side][j][k] (2 nr nph values).
+cudaError_t launch_poles(const LevelView& lv, int prec, const void* x, void* poles, cudaStream_t s);
 cudaError_t launch_jacobi(const LevelView& lv, int prec, const void* x, void* xo, const void* b,
                           cudaStream_t s);
 // One colour of the longitude-line Gauss-Seidel sweep (fac from
@@ -149,7 +153,8 @@ enum {
     BOP_PRELAX,       // zebra longitude lines of a 2-D level: x = e, b = r, z = factors, y = scratch
     BOP_PRESTRICT,    // y = R (b - B x) on the next 2-D level (dims Dc), z = its e zeroed
     BOP_PPROLONG,     // x += P b (b = the next 2-D level's e, dims Dc)
-    BOP_PUPDATE       // x += b on the planes (3-D level)
+    BOP_PUPDATE,      // x += b on the planes (3-D level)
+    BOP_POLES         // z [side][j][k] = rows 0 and nth - 1 of x (19 points on the full sphere, before a colour pass)
 };
 struct BTask {
     LevelView v;       // level of the task (dims, factors, coefficients, stencil)

@@ -215,6 +215,22 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
             }
         for (int c = 0; c < maxc; ++c)
             for (int st : {7, 19}) {
+            auto colour_pass = [&](const mg_handle* h) {
+                return level < top_of(h) && level_smoother(h, level) == MG_SMOOTH_GS && h->stencil == st &&
+                       !fused_level(h, level) && c < (h->stencil == 7 ? 2 : 4);
+            };
+            if (st == 19) {   // full-sphere levels: their pole rows as the pass starts
+                P.begin(BOP_POLES);
+                for (size_t s = 0; s < pl->hs.size(); ++s) {
+                    mg_handle* h = pl->hs[s];
+                    if (!colour_pass(h) || !h->L[level].D.cut) continue;
+                    BTask t = task_of(h, level);
+                    level_bufs(h, prec, level, &t.x, &t.b);
+                    t.z = h->L[level].poles;
+                    t.shell = (int)s;
+                    P.add(t, vblocks(h, 2LL * h->L[level].D.nr * h->L[level].D.nph));
+                }
+            }
             Launch& L = P.begin(BOP_GS, c, st);
             if (level == 0) {
                 L.prof = MG_PROF_SMOOTH0;
@@ -222,10 +238,10 @@ void add_smooth_launches(Program& P, Plan* pl, int level, int sweeps) {
             }
             for (size_t s = 0; s < pl->hs.size(); ++s) {
                 mg_handle* h = pl->hs[s];
-                if (level >= top_of(h) || level_smoother(h, level) != MG_SMOOTH_GS || h->stencil != st) continue;
-                if (fused_level(h, level) || c >= (h->stencil == 7 ? 2 : 4)) continue;
+                if (!colour_pass(h)) continue;
                 BTask t = task_of(h, level);
                 level_bufs(h, prec, level, &t.x, &t.b);
+                if (st == 19 && h->L[level].D.cut) t.z = h->L[level].poles;
                 t.shell = (int)s;
                 P.add(t, vblocks(h, gs_items(h->L[level].D, h->stencil)));
             }

@@ -49,9 +49,12 @@ struct XLinAcc {   // by linear index (Cell7)
 // for every cell of the colour.  Cells of one colour share no stencil entry, so
 // the pass equals the sequential sweep over that colour.
 // 7-point: colour (i + j + k) mod 2.  19-point: ((i + j) mod 2) + 2 ((j + k) mod 2).
+// On the full sphere the 19-point cells of a colour couple across the pole;
+// poles (the first and last rows as the pass starts) gives them the values
+// of the colour's simultaneous update.
 template <int S, typename T, typename CF, bool CG>
 __device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* x, const T* b, int colour,
-                                                i64 first, i64 stride) {
+                                                i64 first, i64 stride, const T* poles = nullptr) {
     const int hk = D.nph >> 1;
     if constexpr (S == 7) {   // the 7-point fast form (same arithmetic as the batched passes)
         const i64 work = (i64)D.nr * D.nth * hk;
@@ -74,7 +77,7 @@ __device__ __forceinline__ void gs_colour_range(const CF& cf, const Dims& D, T* 
             const C3 p{j, i, 2 * kk + (((colour >> 1) + j) & 1)};
             const int c = cidx(D, p);
             Nbr19<T> X;
-            X.load(XLinAcc<T, CG>{x}, D, c, p, !cf.has(2));
+            X.load(XLinAcc<T, CG>{x}, D, c, p, !cf.has(2), poles);
             const T r = ldv<T, CG>(b + c) - apply19<T>(cf, X, D, c, p);
             x[c] = X.v[0] + r / diag_cell<S, T>(cf, D, p);
         }
@@ -184,9 +187,23 @@ __global__ void __launch_bounds__(kThreads) k_apply(CF cf, Dims D, const T* __re
 }
 
 template <int S, typename T, typename CF>
-__global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* __restrict__ b, int colour) {
+__global__ void __launch_bounds__(kThreads) k_gs(CF cf, Dims D, T* x, const T* __restrict__ b, int colour,
+                                                 const T* __restrict__ poles) {
     gs_colour_range<S, T, CF, false>(cf, D, x, b, colour, blockIdx.x * (i64)blockDim.x + threadIdx.x,
-                                     (i64)gridDim.x * blockDim.x);
+                                     (i64)gridDim.x * blockDim.x, poles);
+}
+
+// Rows 0 and nth - 1 of x into poles [side][j][k] (before a 19-point colour
+// pass on the full sphere).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_poles(Dims D, const T* __restrict__ x, T* __restrict__ poles) {
+    const i64 per = (i64)D.nr * D.nph;
+    GRID_STRIDE(e, 2 * per) {
+        const int side = e >= per ? 1 : 0;
+        const i64 r = e - side * per;
+        const int j = (int)(r / D.nph), k = (int)(r - (i64)j * D.nph);
+        poles[e] = x[((i64)j * D.nth + (side ? D.nth - 1 : 0)) * D.nph + k];
+    }
 }
 
 // One colour of the radial-line Gauss-Seidel sweep (line_smooth.cuh).
@@ -329,9 +346,17 @@ cudaError_t launch_apply(const LevelView& lv, int prec, const void* x, void* y, 
 }
 
 cudaError_t launch_gs_colour(const LevelView& lv, int prec, void* x, const void* b, int colour,
-                             cudaStream_t s) {
+                             cudaStream_t s, const void* poles) {
     const int nb = blocks_for((i64)lv.D.nr * lv.D.nth * (lv.D.nph / 2));
-    MG_DISPATCH(lv, prec, (k_gs<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, colour)));
+    MG_DISPATCH(lv, prec, (k_gs<S, T><<<nb, kThreads, 0, s>>>(cf, lv.D, (T*)x, (const T*)b, colour,
+                                                              (const T*)poles)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poles(const LevelView& lv, int prec, const void* x, void* poles, cudaStream_t s) {
+    const int nb = blocks_for(2LL * lv.D.nr * lv.D.nph);
+    if (prec == PREC64) k_poles<double><<<nb, kThreads, 0, s>>>(lv.D, (const double*)x, (double*)poles);
+    else k_poles<float><<<nb, kThreads, 0, s>>>(lv.D, (const float*)x, (float*)poles);
     return cudaGetLastError();
 }
 

@@ -60,8 +60,10 @@ def test_host_side_validation_without_gpu(so):
     assert mgs.mg_footprint_bytes(dict(sphere, cut=2)) == 0
     assert mgs.mg_footprint_bytes(dict(g, cut=1)) == 0               # cut needs [0, pi]
     assert mgs.mg_footprint_bytes(dict(sphere, th0=0.0, cut=0)) == 0  # walls need th0 > 0
-    assert mgs.mg_footprint_bytes(dict(sphere, mapping=1, flattening=0.1)) == 0   # 19 points
-    assert mgs.mg_footprint_bytes(sphere, dict(stencil=19)) == 0
+    assert mgs.mg_footprint_bytes(dict(sphere, mapping=1, flattening=0.1)) > 0    # 19 points, axisymmetric
+    assert mgs.mg_footprint_bytes(dict(sphere, mapping=2, flattening=0.1, e2=0.05)) == 0   # 19 points, triaxial
+    assert mgs.mg_footprint_bytes(sphere, dict(stencil=19)) > 0
+    assert mgs.mg_footprint_bytes(sphere, dict(stencil=19, smoother=2)) == 0   # 19 points, radial lines
     with pytest.raises(mgs.MGError) as e:
         mgs.mg_setup(dict(g, nph=15), stream=0)
     assert e.value.status == mgs.MG_EINVAL
