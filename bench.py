@@ -426,6 +426,8 @@ def single_leg(args, mgs, torch, workload, scale, prec, smoother, steps, warmup,
     sopts = dict(precision=prec, smoother=smoother)
     if "max_levels" in w:
         sopts["max_levels"] = w["max_levels"]
+    if "max_iters" in w:
+        sopts["max_iters"] = w["max_iters"]
     if w.get("coarsen") == "full":
         sopts["coarsen"] = 1
     t_setup = time.perf_counter()
@@ -522,6 +524,8 @@ def run_ours(args, rank, world, local_rank):
         sopts.update(nu1=1, nu2=1)          # the semi-coarsening multigrid's V(1,1)
     if "max_levels" in w:
         sopts["max_levels"] = w["max_levels"]
+    if "max_iters" in w:
+        sopts["max_iters"] = w["max_iters"]
     if w.get("coarsen") == "full":
         sopts["coarsen"] = 1
     t_setup = time.perf_counter()

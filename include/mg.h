@@ -116,9 +116,11 @@ typedef struct {
     int stencil;        /* 0 auto (7 for the sphere, 19 otherwise), 7 or 19 */
     int autotune;       /* 1 (default): at set-up, time a few launch schedules of one outer
                            iteration (blocks per SM of the level kernels, the single-launch
-                           coarse tail, one-pass red-black tiles) once per hierarchy shape in
-                           the process and keep the fastest; every schedule gives the same
-                           bits.  0: the default schedule. */
+                           coarse tail, one-pass sweeps and their tile shapes) once per
+                           hierarchy shape in the process and keep the fastest; every
+                           schedule gives the same bits.  2: take the schedule tuned earlier
+                           in this process for the same hierarchy shape, else the default;
+                           never times (what the serve loop uses).  0: the default schedule. */
     int metric;         /* MG_METRIC_DISCRETE (default): the face metric of Section 3.2 from
                            vertex differences (step 1); MG_METRIC_ANALYTIC: exact derivatives of
                            the mapping at the face centres, steps 2-5 unchanged (an O(h^2)
@@ -291,9 +293,11 @@ mg_status mg_serve_create(const mg_serve_opts* opts, mg_server** out);
 /* Queue one solve: grid and options as in mg_setup (opts may be NULL), f_host
  * the pointwise right side (nr*nth*nph doubles, copied before the call
  * returns), tolerance as in mg_solve.  *ticket identifies the request.  The
- * server builds hierarchies with the default launch schedule (opts->autotune
- * is not honoured: schedule timings taken while other requests run would
- * measure the load); results are the same bits either way. */
+ * server never times schedules (timings taken while other requests run would
+ * measure the load): a hierarchy takes the schedule tuned earlier in the
+ * process for its shape (mg_setup with autotune = 1, e.g. of representative
+ * shapes before the server starts), else the default (opts->autotune is
+ * read as 2); results are the same bits either way. */
 mg_status mg_serve_submit(mg_server* sv, const mg_grid_desc* grid, const mg_opts* opts, const double* f_host,
                           double tol, uint64_t* ticket);
 /* MG_EAGAIN while the request is queued or iterating; otherwise its final

@@ -124,7 +124,7 @@ std::string check_opts(const mg_opts* o) {
     if (o->coarse_max < 1) return "coarse_max must be >= 1";
     if (o->max_iters < 0) return "max_iters must be >= 0";
     if (o->stencil != 0 && o->stencil != 7 && o->stencil != 19) return "stencil must be 0, 7 or 19";
-    if (o->autotune != 0 && o->autotune != 1) return "autotune must be 0 or 1";
+    if (o->autotune < 0 || o->autotune > 2) return "autotune must be 0, 1 or 2";
     if (o->metric != MG_METRIC_DISCRETE && o->metric != MG_METRIC_ANALYTIC) return "metric must be 0 or 1";
     return "";
 }
@@ -536,20 +536,31 @@ mg_status time_schedule(mg_handle* h, const Schedule& sc, double* ms) {
     return st;
 }
 
-mg_status autotune(mg_handle* h) {
-    static std::mutex mu;
-    static std::unordered_map<std::string, std::pair<Schedule, double>> cache;
-    const std::string key = shape_key(h);
+// Schedules tuned in this process, per hierarchy shape.
+std::mutex g_sched_mu;
+std::unordered_map<std::string, std::pair<Schedule, double>> g_sched_cache;
+
+// The cached schedule of the handle's shape, if any (source 2).
+mg_status cached_schedule(mg_handle* h, bool* found) {
+    std::pair<Schedule, double> hit;
     {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            CKS(apply_schedule(h, it->second.first));
-            h->sched_source = 2;
-            h->sched_ms = it->second.second;
-            return MG_OK;
-        }
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        auto it = g_sched_cache.find(shape_key(h));
+        *found = it != g_sched_cache.end();
+        if (!*found) return MG_OK;
+        hit = it->second;
     }
+    CKS(apply_schedule(h, hit.first));
+    h->sched_source = 2;
+    h->sched_ms = hit.second;
+    return MG_OK;
+}
+
+mg_status autotune(mg_handle* h) {
+    bool found = false;
+    CKS(cached_schedule(h, &found));
+    if (found) return MG_OK;
+    const std::string key = shape_key(h);
     // finite data for the timing runs (the iterates are discarded)
     const i64 N = h->L[0].D.n();
     CK(cudaMemsetAsync(h->x64, 0, sizeof(double) * N, h->stream));
@@ -616,8 +627,8 @@ mg_status autotune(mg_handle* h) {
     h->sched_source = 1;
     h->sched_candidates = tried;
     h->sched_ms = best_ms;
-    std::lock_guard<std::mutex> lk(mu);
-    cache[key] = {best, best_ms};
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched_cache[key] = {best, best_ms};
     return MG_OK;
 }
 
@@ -881,8 +892,11 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
             if (const char* v = std::getenv("MG_TAIL_CLUSTER")) cluster = std::max(1, std::min(8, std::atoi(v)));
             CKS(configure_tail(h, cells, cluster));
         }
-    } else if (o->autotune) {
+    } else if (o->autotune == 1) {
         CKS(autotune(h));
+    } else if (o->autotune == 2) {
+        bool found = false;
+        CKS(cached_schedule(h, &found));
     }
     return MG_OK;
 }

@@ -461,15 +461,23 @@ struct Nbr19 {
         const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
         const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
         const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
-        const bool pole_row = D.cut && (p.i == 0 || p.i + 1 == D.nth);
 #pragma unroll
         for (int n = 0; n < 19; ++n) {
             const bool phi_edge = row_off(n, 2) != 0 && (row_off(n, 0) != 0 || row_off(n, 1) != 0);
+            v[n] = (axi && phi_edge) ? (T)0
+                                     : X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
+        }
+        if (D.cut && (p.i == 0 || p.i + 1 == D.nth)) pole_row(X, D, p, axi, poles);
+    }
+    // the entries across the pole of a first or last row (full sphere), kept
+    // apart from the common path
+    template <typename XL>
+    __device__ __noinline__ void pole_row(const XL& X, const Dims& D, C3 p, bool axi, const T* poles) {
+        for (int n = 3; n < 19; ++n) {
+            const bool phi_edge = row_off(n, 2) != 0 && (row_off(n, 0) != 0 || row_off(n, 1) != 0);
             int cell, pole;
-            if (axi && phi_edge) v[n] = (T)0;
-            else if (pole_row && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole))
+            if (!(axi && phi_edge) && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole))
                 v[n] = poles ? poles[pole] : X(cell);
-            else v[n] = X(c + oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1]);
         }
     }
     // value at offset a along paper direction da and b along direction db
@@ -531,6 +539,24 @@ __device__ __forceinline__ T apply19(const CF& cf, const Nbr19<T>& X, const Dims
     return apply19_r<T>(cr, X, D, p);
 }
 
+// resid_rows19 for a first or last row of the full sphere: the entries
+// beyond the row are the cells across the pole (same multiply-add order).
+static __device__ __noinline__ double resid_rows19_pole(const double* __restrict__ a, i64 N, const double* __restrict__ x,
+                                                        const Dims& D, int c, C3 p, double b, int nrows) {
+    const int plane = D.nth * D.nph;
+    const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
+    const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
+    const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
+    double r = b;
+    for (int n = 0; n < nrows; ++n) {
+        int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
+        int cell, pole;
+        if (across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole)) o = cell - c;
+        r = fma(-__ldcs(a + n * N + c), __ldg(x + c + o), r);
+    }
+    return r;
+}
+
 // b_c - (A x)_c from the assembled coefficients a[n * N + c] (row_off order;
 // nrows = 19, or 11 when the longitude edges 11..18 are absent).
 __device__ __forceinline__ double resid_rows19(const double* __restrict__ a, i64 N, const double* __restrict__ x,
@@ -539,14 +565,12 @@ __device__ __forceinline__ double resid_rows19(const double* __restrict__ a, i64
     const int oj[3] = {p.j > 0 ? -plane : 0, 0, p.j + 1 < D.nr ? plane : 0};
     const int oi[3] = {p.i > 0 ? -D.nph : 0, 0, p.i + 1 < D.nth ? D.nph : 0};
     const int ok[3] = {p.k > 0 ? -1 : D.nph - 1, 0, p.k + 1 < D.nph ? 1 : 1 - D.nph};
-    const bool pole_row = D.cut && (p.i == 0 || p.i + 1 == D.nth);
+    if (D.cut && (p.i == 0 || p.i + 1 == D.nth)) return resid_rows19_pole(a, N, x, D, c, p, b, nrows);
     double r = b;
 #pragma unroll
     for (int n = 0; n < 19; ++n) {
         if (n >= nrows) break;
-        int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
-        int cell, pole;
-        if (pole_row && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole)) o = cell - c;
+        const int o = oj[row_off(n, 0) + 1] + oi[row_off(n, 1) + 1] + ok[row_off(n, 2) + 1];
         r = fma(-__ldcs(a + n * N + c), __ldg(x + c + o), r);
     }
     return r;

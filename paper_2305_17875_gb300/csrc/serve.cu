@@ -477,10 +477,11 @@ mg_status mg_serve_submit(mg_server* sv, const mg_grid_desc* grid, const mg_opts
     if (!r) return MG_ENOMEM;
     r->grid = *grid;
     r->opts = o;
-    // hierarchies of the serve loop keep the default launch schedule: timing
-    // candidate schedules while other requests run on the GPU would measure
-    // the load, not the schedule (results are the same bits either way)
-    r->opts.autotune = 0;
+    // hierarchies of the serve loop never time schedules (timings taken while
+    // other requests run on the GPU would measure the load, not the
+    // schedule): they take the one tuned earlier in the process for their
+    // shape, else the default (results are the same bits either way)
+    r->opts.autotune = 2;
     r->tol = tol;
     const size_t n = (size_t)grid->nr * grid->nth * grid->nph;
     r->f.assign(f_host, f_host + n);

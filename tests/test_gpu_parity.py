@@ -297,7 +297,7 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
     w = W.single(wl, scale)
     fd = to_dev(w["f"], torch.float64)
     out = {}
-    for name, env, tune in [("default", {}, 0), ("tuned", {}, 1), ("tuned_again", {}, 1),
+    for name, env, tune in [("default", {}, 0), ("tuned", {}, 1), ("tuned_again", {}, 1), ("cached", {}, 2),
                             ("tail", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192"}, 1),
                             ("tail_big", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4"}, 1),
                             ("fused", {"MG_FUSED_RB": "1"}, 1),
@@ -314,10 +314,10 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
             assert sc["source"] == 3
         elif tune:
             assert sc["source"] in (1, 2) and sc["ms_per_iteration"] > 0
-            assert sc["blocks_per_sm"] in (8, 16, 32)
+            assert sc["blocks_per_sm"] in (4, 8, 16, 32)
         else:
             assert sc["source"] == 0 and sc["blocks_per_sm"] == 16 and sc["tail_level"] == 0
-        if name == "tuned_again":
+        if name in ("tuned_again", "cached"):
             assert sc["source"] == 2           # same hierarchy shape: from the process cache
         xd = torch.zeros_like(fd)
         rep = lib.mg_solve(h, fd, xd, tol=1e-10)
@@ -326,6 +326,21 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
     for name, (x, it) in out.items():
         assert it == out["default"][1], name
         assert np.array_equal(x, out["default"][0]), name
+
+
+def test_cached_schedules_without_timing(lib):
+    """autotune = 2 (the serve loop's set-up) times nothing: the default
+    schedule for a shape not tuned yet, the tuned one once a set-up with
+    autotune = 1 has cached it."""
+    g = W.grid_desc(12, 10, 24, stretch=1.5)
+    sc0 = lib.mg_get_schedule(lib.mg_setup(g, dict(precision=1, autotune=2)))
+    assert sc0["source"] == 0 and sc0["candidates"] == 0
+    tuned = lib.mg_get_schedule(lib.mg_setup(g, dict(precision=1, autotune=1)))
+    assert tuned["source"] == 1 and tuned["candidates"] > 1
+    again = lib.mg_get_schedule(lib.mg_setup(g, dict(precision=1, autotune=2)))
+    assert again["source"] == 2
+    for k in ("blocks_per_sm", "tail_level", "one_pass_tiles", "tile0"):
+        assert again[k] == tuned[k], k
 
 
 def test_solve_warm_start_and_host_buffers(lib):

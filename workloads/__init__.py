@@ -111,6 +111,10 @@ SINGLE = {
     # domain; longitude coupling grows like 1/sin^2(theta) toward the poles
     "single_full_sphere_128": dict(grid=grid_desc(128, stretch=2.0, cut=True), rhs=("modes", 0), tol=1e-10,
                                    precision="fp32"),
+    # the oblate whole sphere (19 points, the cross terms across the poles;
+    # point smoothing stalls at the poles, so many V-cycles)
+    "single_full_oblate_64": dict(grid=grid_desc(64, r_out=1 / 0.6, mapping=1, flattening=0.1, cut=True),
+                                  rhs=("modes", 0), tol=1e-10, precision="fp32", max_iters=1000),
 }
 
 
