@@ -472,8 +472,9 @@ struct Nbr19 {
     // the entries across the pole of a first or last row (full sphere), kept
     // apart from the common path
     template <typename XL>
-    __device__ __noinline__ void pole_row(const XL& X, const Dims& D, C3 p, bool axi, const T* poles) {
-        for (int n = 3; n < 19; ++n) {
+    __device__ __forceinline__ void pole_row(const XL& X, const Dims& D, C3 p, bool axi, const T* poles) {
+#pragma unroll
+        for (int n = 3; n < 19; ++n) {   // (unrolled: v stays in registers)
             const bool phi_edge = row_off(n, 2) != 0 && (row_off(n, 0) != 0 || row_off(n, 1) != 0);
             int cell, pole;
             if (!(axi && phi_edge) && across_pole(D, p, row_off(n, 0), row_off(n, 1), row_off(n, 2), &cell, &pole))
