@@ -187,6 +187,101 @@ __device__ __forceinline__ void gs_pass7v(const CF& cf, const Dims& D, T* x, con
     }
 }
 
+// 19-point colour pass over groups of four longitudes (nph a multiple of 4,
+// walled grids): a work item is a group of a row of the colour and updates
+// its two cells of the colour (positions P, P + 2, P the colour's longitude
+// parity) from 16-byte loads of the nine (radius, colatitude) rows around it,
+// the two longitudes either side, and the face rows; each cell's neighbourhood
+// and rows are then picked out of those registers and go through the scalar
+// pass's arithmetic (apply19_r, diag_cell_r), so the bits are those of
+// gs_pass.  The group is written back whole (the other two cells unchanged).
+template <typename T, typename CF, bool AXI, int P>
+__device__ __forceinline__ void group19(const CF& cf, const Dims& D, T* x, const T* b, int j, int i, int q) {
+    const int plane = D.nth * D.nph;
+    const int k0 = 4 * q;
+    const int c0 = (j * D.nth + i) * D.nph + k0;
+    const int oj[3] = {j > 0 ? -plane : 0, 0, j + 1 < D.nr ? plane : 0};
+    const int oi[3] = {i > 0 ? -D.nph : 0, 0, i + 1 < D.nth ? D.nph : 0};
+    const int km = k0 == 0 ? c0 + D.nph - 1 : c0 - 1;   // longitude k0 - 1 of the row (wrapped)
+    const int kp = k0 + 4 == D.nph ? c0 - k0 : c0 + 4;   // longitude k0 + 4
+    // x on the nine rows; the longitudes either side where a longitude offset is read
+    T X[3][3][4], E[3][3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int o = oj[a] + oi[e];
+            ld4(x + c0 + o, X[a][e]);
+            const bool edge = (a == 1 && e == 1) || (!AXI && (a == 1 || e == 1));
+            E[a][e][0] = edge ? x[km + o] : (T)0;
+            E[a][e][1] = edge ? x[kp + o] : (T)0;
+        }
+    // face rows: own components, radius-upper 3..5, colatitude-upper 0..2,
+    // longitude-upper 6..8 (the next group's first cell for the last one)
+    T C[9][4], EU[3][4], ZU[3][4], XN[3];
+    const bool ju = j + 1 < D.nr, iu = i + 1 < D.nth;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        if (RegRows<T, AXI>::stored(a)) cf.load4(a, c0, C[a]);
+        else C[a][0] = C[a][1] = C[a][2] = C[a][3] = (T)0;
+    }
+#pragma unroll
+    for (int qq = 0; qq < 3; ++qq) {
+        if (ju && RegRows<T, AXI>::stored(3 + qq)) cf.load4(3 + qq, c0 + plane, EU[qq]);
+        else EU[qq][0] = EU[qq][1] = EU[qq][2] = EU[qq][3] = (T)0;
+        if (iu && RegRows<T, AXI>::stored(qq)) cf.load4(qq, c0 + D.nph, ZU[qq]);
+        else ZU[qq][0] = ZU[qq][1] = ZU[qq][2] = ZU[qq][3] = (T)0;
+        XN[qq] = RegRows<T, AXI>::stored(6 + qq) ? (T)cf(6 + qq, kp) : (T)0;
+    }
+    T B[4];
+    ldg4(b + c0, B);
+    T out[4] = {X[1][1][0], X[1][1][1], X[1][1][2], X[1][1][3]};
+#pragma unroll
+    for (int e2 = 0; e2 < 2; ++e2) {
+        const int m = P + 2 * e2;
+        Nbr19<T> N;
+#pragma unroll
+        for (int n = 0; n < 19; ++n) {
+            const int dj = row_off(n, 0), di = row_off(n, 1), dk = row_off(n, 2);
+            const bool phi_edge = dk != 0 && (dj != 0 || di != 0);
+            const int kk = m + dk;
+            N.v[n] = (AXI && phi_edge) ? (T)0
+                     : (kk < 0 ? E[dj + 1][di + 1][0] : (kk > 3 ? E[dj + 1][di + 1][1] : X[dj + 1][di + 1][kk < 0 ? 0 : (kk > 3 ? 3 : kk)]));
+        }
+        T v[19];
+        v[0] = B[m];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[1 + a] = C[a][m];
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) {
+            v[10 + qq] = EU[qq][m];
+            v[13 + qq] = ZU[qq][m];
+            v[16 + qq] = m < 3 ? C[6 + qq][m < 3 ? m + 1 : 3] : XN[qq];
+        }
+        const RegRows<T, AXI> cr{v};
+        const C3 p3{j, i, k0 + m};
+        const T r = v[0] - apply19_r<T>(cr, N, D, p3);
+        out[m] = N.v[0] + r / diag_cell_r<19, T>(cr, D, p3);
+    }
+    st4(x + c0, out);
+}
+
+template <typename T, typename CF, bool AXI>
+__device__ __forceinline__ void gs_pass19v(const CF& cf, const Dims& D, T* x, const T* b, int colour, i64 first,
+                                           i64 stride) {
+    const int nq = D.nph >> 2, nth2 = (D.nth + 1) >> 1;
+    const i64 work = (i64)D.nr * nth2 * nq;
+    for (i64 t = first; t < work; t += stride) {
+        const unsigned row = D.dq.div((unsigned)t);
+        const unsigned jj = D.dth2.div(row);
+        const int q = (int)((unsigned)t - row * (unsigned)nq);
+        const int j = (int)jj, i = 2 * (int)(row - jj * (unsigned)nth2) + ((colour ^ j) & 1);
+        if (i >= D.nth) continue;
+        if ((((colour >> 1) + j) & 1) == 0) group19<T, CF, AXI, 0>(cf, D, x, b, j, i, q);
+        else group19<T, CF, AXI, 1>(cf, D, x, b, j, i, q);
+    }
+}
+
 // 7-point residual + children-sum restriction over groups of four fine
 // longitude cells in every child row: four coarse cells when longitude is
 // not halved, two when it is.  Sums in the order of the scalar form.
@@ -595,7 +690,10 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
         // 19 points: the scalar form (a group would load four cells to update two
         // with twice the registers); 7 points: groups when nph is a multiple of 4
         if (S == 7 && vec4(tk.v.D)) gs_pass7v<T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
-        else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride, (const T*)tk.z);
+        else if (S == 19 && gs19_groups(tk.v.D)) {
+            if (cf.has(2)) gs_pass19v<T, typename Prec<P>::CF, false>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
+            else gs_pass19v<T, typename Prec<P>::CF, true>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride);
+        } else gs_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, colour, first, stride, (const T*)tk.z);
     } else if constexpr (OP == BOP_LINE) {
         line_pass<S, T>(cf, tk.v.D, (T*)tk.x, (const T*)tk.b, (const T*)tk.z, colour, lb, tk.nblocks);
     } else if constexpr (OP == BOP_XLINE) {
@@ -676,7 +774,7 @@ template <int P, int OP, int S>
 constexpr int min_ctas() {
     if (OP == BOP_LINE) return 2;          // two chunks of 16 rows per thread: fits 128 registers
     if (P == PREC64 || (OP != BOP_GS && OP != BOP_RESTRICT)) return 1;
-    if (OP == BOP_GS) return 4;
+    if (OP == BOP_GS) return S == 19 ? 2 : 4;   // the 19-point groups hold ~100 values per thread
     if (S == 19) return 2;                 // the 19-point restriction groups hold ~100 values per thread
     return P == PREC32 ? 3 : 1;
 }

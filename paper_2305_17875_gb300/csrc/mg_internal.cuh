@@ -55,6 +55,9 @@ struct Dims {
 // vectors of FP32) when nph is a multiple of 4; the batched level operations
 // then work on whole groups.
 __host__ __device__ __forceinline__ bool vec4(const Dims& D) { return (D.nph & 3) == 0; }
+// The 19-point colour passes work on groups of four longitudes on walled grids
+// of vec4 rows (the full sphere's pole rows take the scalar pass).
+__host__ __device__ __forceinline__ bool gs19_groups(const Dims& D) { return vec4(D) && !D.cut; }
 
 struct C3 {
     int j, i, k;
@@ -267,6 +270,25 @@ __device__ __forceinline__ CellRows<CF> cell_rows(const CF& cf, const Dims& D, C
                         c.i < D.nth - 1 ? cidx(D, c.j, c.i + 1, c.k) : self,
                         cidx(D, c.j, c.i, c.k + 1 == D.nph ? 0 : c.k + 1)};
 }
+
+// Face rows of one cell held in registers: v[1 + a] = component a of the
+// cell's own rows, v[10 + q] = component 3 + q of the radius-upper row,
+// v[13 + q] = component q of the colatitude-upper row, v[16 + q] = component
+// 6 + q of the longitude-upper row (v[0] is free: the callers keep b there),
+// read by the formulas below through CellRows' interface.  AXI: the
+// longitude cross components 2, 5, 6, 7 are not stored.
+template <typename T, bool AXI>
+struct RegRows {
+    const T* v;
+    __device__ __forceinline__ static constexpr bool stored(int a) {
+        return !AXI || (a != 2 && a != 5 && a != 6 && a != 7);
+    }
+    __device__ __forceinline__ bool has(int a) const { return stored(a); }
+    template <int F>
+    __device__ __forceinline__ T at(int a) const {
+        return F == 0 ? v[1 + a] : (F == 1 ? v[10 + a - 3] : (F == 2 ? v[13 + a] : v[16 + a - 6]));
+    }
+};
 
 template <int S, typename T, typename R>
 __device__ __forceinline__ T diag_cell_r(const R& cr, const Dims& D, C3 c) {

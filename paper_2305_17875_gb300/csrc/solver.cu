@@ -43,7 +43,8 @@ int vblocks(const mg_handle* h, i64 work) {
 // restrictions and prolongations work on groups of four longitude cells when
 // nph is a multiple of 4, vector operations on groups of four elements.
 i64 gs_items(const Dims& D, int stencil) {
-    if (stencil == 19) return (i64)D.nr * ((D.nth + 1) / 2) * (D.nph / 2);   // rows of the colour only
+    if (stencil == 19)   // rows of the colour only; groups of four longitudes or cells of the colour
+        return (i64)D.nr * ((D.nth + 1) / 2) * (gs19_groups(D) ? D.nph / 4 : D.nph / 2);
     return (i64)D.nr * D.nth * (vec4(D) ? D.nph / 4 : D.nph / 2);
 }
 i64 restrict_items(const Dims& D, const Dims& Dc) { return vec4(D) ? (i64)Dc.nr * Dc.nth * (D.nph / 4) : Dc.n(); }

@@ -224,24 +224,6 @@ __device__ __forceinline__ void stage_cell(const Stage& st, int u, int& i, int& 
 
 __device__ __forceinline__ int wrap_k(const Dims& D, int k) { return k < 0 ? k + D.nph : (k >= D.nph ? k - D.nph : k); }
 
-// Face rows of one cell held in registers (the layout of StageSize<19>:
-// v[1 + a] = component a of the cell's own rows, v[10 + q] = component 3 + q
-// of the radius-upper row, v[13 + q] = component q of the colatitude-upper
-// row, v[16 + q] = component 6 + q of the longitude-upper row), read by the
-// formulas of mg_internal.cuh through CellRows' interface.
-template <typename T, bool AXI>
-struct RegRows {
-    const T* v;
-    __device__ __forceinline__ static constexpr bool stored(int a) {
-        return !AXI || (a != 2 && a != 5 && a != 6 && a != 7);
-    }
-    __device__ __forceinline__ bool has(int a) const { return stored(a); }
-    template <int F>
-    __device__ __forceinline__ T at(int a) const {
-        return F == 0 ? v[1 + a] : (F == 1 ? v[10 + a - 3] : (F == 2 ? v[13 + a] : v[16 + a - 6]));
-    }
-};
-
 // Loads of one stage into registers.
 template <int S, bool AXI, typename T, typename CF>
 __device__ __forceinline__ void stage_load(const CF& cf, const Dims& D, const T* __restrict__ b, const Stage& st,
