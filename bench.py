@@ -456,7 +456,9 @@ def single_leg(args, mgs, torch, workload, scale, prec, smoother, steps, warmup,
     pname = [k for k, v in PREC.items() if v == prec][0]
     roof = roofline_of(name, slots, steps, stencil, prec, N, n_next, smoother, axi, one_pass,
                        ncu_traffic(traffic_key or workload, pname, name, one_pass))
-    roof["share_of_step"] = slots[name][0] / max(sum(v[0] for v in slots.values()), 1e-30)
+    # the kernel's share of all device time of the profiled solves (every
+    # slot and every coarse level): comparable with an ncu launch list
+    roof["share_of_step"] = prof["kernels"][name]["ms_per_solve"] / max(prof["attributed_ms_per_solve"], 1e-30)
     leg = {"workload": workload if scale == 1 else f"{workload}/{scale}", "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
            "value": N / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
            "p99_ms": float(__import__("numpy").percentile(ms, 99)), "iters": rep["iters"], "rel_res": rep["rel_res"],
@@ -569,7 +571,7 @@ def run_ours(args, rank, world, local_rank):
     roof = roofline_of(name, slots, args.steps, stencil, prec, N, n_next, smoother, axi, one_pass,
                        ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
                                    args.precision, name, one_pass))
-    roof["share_of_step"] = slots[name][0] / max(sum(v[0] for v in slots.values()), 1e-30)
+    roof["share_of_step"] = prof["kernels"][name]["ms_per_solve"] / max(prof["attributed_ms_per_solve"], 1e-30)
 
     # end to end through the public host-buffer call (pinned host memory)
     fh = torch.from_numpy(f.copy()).pin_memory()
