@@ -369,8 +369,8 @@ SLOT_NAMES = (("smooth0", 0), ("residual", 1), ("restrict0", 2), ("prolong0", 3)
 
 
 def profile_solves(mgs, h, fd, xd, steps, flush, torch, stencil, prec, N, n_next, smoother, axi, one_pass):
-    """A separate profiled run of the same solves (every launch of the outer
-    iterations bracketed by events, so it runs a little slower than the
+    """A separate profiled run of the same solves (every launch records its
+    own start and end on the GPU's global timer; the launches run as in the
     headline): device time per slot and per level, and the roofline of the
     level-0 kernel with the largest device time."""
     mgs.mg_profile_enable(h, True)
@@ -381,6 +381,7 @@ def profile_solves(mgs, h, fd, xd, steps, flush, torch, stencil, prec, N, n_next
         t, n = mgs.mg_profile_read(h, mgs.PROF_LEVEL_BASE + l)
         if n:
             levels[l] = {"ms_per_solve": t / steps, "launches_per_solve": n / steps}
+    gap_ms, _ = mgs.mg_profile_read(h, mgs.PROF_GAPS)
     mgs.mg_profile_enable(h, False)
     kernels = {}
     for k, (t, n) in slots.items():
@@ -390,7 +391,14 @@ def profile_solves(mgs, h, fd, xd, steps, flush, torch, stencil, prec, N, n_next
         kernels[k] = {"ms_per_solve": t / steps, "launches_per_solve": n / steps, "avg_ms": avg if n else None,
                       "alg_GBps": ab / (avg * 1e-3) / 1e9 if n and ab == ab else None}
     attributed = sum(v["ms_per_solve"] for v in kernels.values()) + sum(v["ms_per_solve"] for v in levels.values())
-    return {"profiled_ms_per_solve": statistics.mean(ms), "attributed_ms_per_solve": attributed,
+    live = statistics.mean(ms)
+    # device time no kernel covers, within a program run (an outer
+    # iteration, the prologue, the epilogue): launch latency between kernels
+    gaps = gap_ms / steps
+    return {"profiled_ms_per_solve": live, "attributed_ms_per_solve": attributed,
+            "launch_gaps_ms_per_solve": gaps,
+            # the rest: between program runs (stop tests, copies, host calls)
+            "between_programs_ms_per_solve": live - attributed - gaps,
             "kernels": kernels, "levels": levels}, slots
 
 
@@ -459,6 +467,7 @@ def single_leg(args, mgs, torch, workload, scale, prec, smoother, steps, warmup,
     # the kernel's share of all device time of the profiled solves (every
     # slot and every coarse level): comparable with an ncu launch list
     roof["share_of_step"] = prof["kernels"][name]["ms_per_solve"] / max(prof["attributed_ms_per_solve"], 1e-30)
+    prof["attributed_over_headline"] = prof["attributed_ms_per_solve"] / statistics.mean(ms)
     leg = {"workload": workload if scale == 1 else f"{workload}/{scale}", "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
            "value": N / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
            "p99_ms": float(__import__("numpy").percentile(ms, 99)), "iters": rep["iters"], "rel_res": rep["rel_res"],
@@ -572,6 +581,7 @@ def run_ours(args, rank, world, local_rank):
                        ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
                                    args.precision, name, one_pass))
     roof["share_of_step"] = prof["kernels"][name]["ms_per_solve"] / max(prof["attributed_ms_per_solve"], 1e-30)
+    prof["attributed_over_headline"] = prof["attributed_ms_per_solve"] / ms_step
 
     # end to end through the public host-buffer call (pinned host memory)
     fh = torch.from_numpy(f.copy()).pin_memory()

@@ -443,10 +443,13 @@ mg_status mg_adi_substep(mg_handle* h, double kappa, int nfields, const mg_walls
 size_t mg_device_bytes_in_use(int device);
 
 /* ---------------------------------------------------------------------------
- * Kernel timing.  While enabled, a solve brackets every launch of its outer
- * iterations with CUDA events on the handle's stream (event records between
- * launches: the timed solve runs somewhat slower than an untimed one) and
- * accumulates device time per slot.  Slots: 0 = fine-level smoothing
+ * Kernel timing.  While enabled, every kernel a solve launches records its
+ * own clock on the GPU's global nanosecond timer: the earliest start of its
+ * thread blocks (after they wait for the previous launch) and the latest end.
+ * Each launch's span is added to its slot, so the slots hold device time of
+ * the kernels proper; launch gaps and host waits between outer iterations
+ * are not in any slot.  The launches run as in an untimed solve (the clocks
+ * add a reset and a read-back per outer iteration).  Slots: 0 = fine-level smoothing
  * launches, 1 = outer FP64 residual, 2 = fine-level residual + restriction,
  * 3 = fine-level prolongation + correction, 4 = outer update, 5 = the
  * single-launch coarse tail of the V-cycle, 6 = everything else (zeroing,
@@ -454,10 +457,10 @@ size_t mg_device_bytes_in_use(int device);
  * smoothing, restriction and prolongation launches of level l (1 <= l < 16;
  * deeper levels share the last slot).  The slots together cover the whole
  * outer iteration.  Stand-alone component calls (mg_smooth, mg_vcycle) time
- * slots 0, 2, 3 and 5 only.
+ * slots 0, 2, 3 and 5 only, with CUDA events around their launches.
  * ------------------------------------------------------------------------- */
 enum { MG_PROF_SMOOTH0 = 0, MG_PROF_RESIDUAL = 1, MG_PROF_RESTRICT0 = 2, MG_PROF_PROLONG0 = 3,
-       MG_PROF_UPDATE = 4, MG_PROF_TAIL = 5, MG_PROF_OTHER = 6, MG_PROF_LEVEL_BASE = 8,
+       MG_PROF_UPDATE = 4, MG_PROF_TAIL = 5, MG_PROF_OTHER = 6, MG_PROF_GAPS = 7, MG_PROF_LEVEL_BASE = 8,
        MG_PROF_SLOTS = 24 };
 /* Enable (on != 0) or disable timing; either way the accumulators reset. */
 mg_status mg_profile_enable(mg_handle* h, int on);

@@ -424,7 +424,7 @@ def mg_get_schedule(h: Handle) -> dict:
     return out
 
 
-PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL, PROF_OTHER = range(7)
+PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TAIL, PROF_OTHER, PROF_GAPS = range(8)
 PROF_LEVEL_BASE, PROF_SLOTS = 8, 24   # slot PROF_LEVEL_BASE + l: level l's operations (1 <= l < 16)
 
 

@@ -781,12 +781,14 @@ constexpr int min_ctas() {
 
 template <int P, int OP, int S>
 __global__ void __launch_bounds__(kBT, min_ctas<P, OP, S>()) k_batch(const BTask* __restrict__ tasks, int ntasks, int total,
-                                                const int* __restrict__ active, int colour, int early_trigger) {
+                                                const int* __restrict__ active, int colour, int early_trigger,
+                                                unsigned long long* stamp) {
     __shared__ double sh[8];
     __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];
     __shared__ int tk_index;
     const BTask& tk = *reinterpret_cast<const BTask*>(tk_raw);
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    stamp_start(stamp);
     if (early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         // the block's task descriptor is staged once in shared memory
@@ -903,6 +905,7 @@ __global__ void __launch_bounds__(kBT, min_ctas<P, OP, S>()) k_batch(const BTask
         }
         __syncthreads();   // the descriptor is rewritten for the next virtual block
     }
+    stamp_end(stamp);
     if (!early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
@@ -952,7 +955,7 @@ bool use_pdl() {
 
 template <int P, int OP, int S>
 static cudaError_t batch_launch(const BTask* tasks, int ntasks, int total, const int* active, int colour,
-                                cudaStream_t s) {
+                                cudaStream_t s, unsigned long long* stamp) {
     const int early = total <= 152 * 8 ? 1 : 0;   // fits one wave at 8 CTAs per SM
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(total, 1, 1);              // one CTA per virtual block
@@ -963,19 +966,19 @@ static cudaError_t batch_launch(const BTask* tasks, int ntasks, int total, const
     attr[0].val.programmaticStreamSerializationAllowed = use_pdl() ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch<P, OP, S>, tasks, ntasks, total, active, colour, early);
+    return cudaLaunchKernelEx(&cfg, k_batch<P, OP, S>, tasks, ntasks, total, active, colour, early, stamp);
 }
 
 template <int P>
 static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, const int* active, int op, int colour,
-                                  int stencil, cudaStream_t s) {
+                                  int stencil, cudaStream_t s, unsigned long long* stamp) {
 #define STENCIL_OP(OPV)                                                                         \
     case OPV:                                                                                   \
-        return stencil == 19 ? batch_launch<P, OPV, 19>(tasks, ntasks, total, active, colour, s) \
-                             : batch_launch<P, OPV, 7>(tasks, ntasks, total, active, colour, s);
+        return stencil == 19 ? batch_launch<P, OPV, 19>(tasks, ntasks, total, active, colour, s, stamp) \
+                             : batch_launch<P, OPV, 7>(tasks, ntasks, total, active, colour, s, stamp);
 #define PLAIN_OP(OPV) \
     case OPV:         \
-        return batch_launch<P, OPV, 0>(tasks, ntasks, total, active, colour, s);
+        return batch_launch<P, OPV, 0>(tasks, ntasks, total, active, colour, s, stamp);
     switch (op) {
         STENCIL_OP(BOP_GS)
         STENCIL_OP(BOP_JACOBI)
@@ -1005,18 +1008,112 @@ static cudaError_t batch_dispatch(const BTask* tasks, int ntasks, int total, con
 #undef PLAIN_OP
 }
 
+namespace {
+__global__ void k_stamp_reset(unsigned long long* st, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        st[2 * i] = ~0ull;
+        st[2 * i + 1] = 0ull;
+    }
+}
+}  // namespace
+
+cudaError_t launch_stamp_reset(unsigned long long* stamps, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_stamp_reset<<<(n + 255) / 256, 256, 0, s>>>(stamps, n);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void __launch_bounds__(256) k_stamp_accum(unsigned long long* st, int n, unsigned long long* acc) {
+    __shared__ unsigned long long lo, hi;
+    if (threadIdx.x == 0) {
+        lo = ~0ull;
+        hi = 0ull;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long a = st[2 * i], b = st[2 * i + 1];
+        if (a != ~0ull && b >= a) {
+            acc[2 * i] += b - a;
+            acc[2 * i + 1] += 1;
+            atomicMin(&lo, a);
+            atomicMax(&hi, b);
+        }
+        st[2 * i] = ~0ull;
+        st[2 * i + 1] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && lo != ~0ull) {
+        acc[2 * n] += hi - lo;
+        acc[2 * n + 1] += 1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_loop_check(LoopShell* S, int n, const double* __restrict__ fin,
+                                                    int* active, int* passes, cudaGraphConditionalHandle cond) {
+    int running = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        LoopShell& q = S[i];
+        if (active[i]) {
+            q.it += 1;
+            q.rr = fin[4 * i + 2];
+        }
+        if (!q.done) {
+            const double rel = sqrt(q.rr) / q.bnorm;
+            if (q.it < kLoopHist) q.hist[q.it] = rel;
+            q.rel = rel;
+            if (!isfinite(rel)) {
+                q.why = LOOP_NAN;
+                q.done = 1;
+            } else if (rel <= q.tol) {
+                q.done = 1;
+            } else {
+                q.best = fmin(q.best, rel);
+                if (rel > 1e3 * q.best) {
+                    q.why = LOOP_DIVERGED;
+                    q.done = 1;
+                } else if (q.it >= q.max_iters) {
+                    q.why = LOOP_NOCONV;
+                    q.done = 1;
+                }
+            }
+        }
+        active[i] = q.done ? 0 : 1;
+        running |= q.done ? 0 : 1;
+    }
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        const int p = passes[0] + 1;
+        passes[0] = p;
+        cudaGraphSetConditional(cond, (running && p < passes[1]) ? 1u : 0u);
+    }
+}
+}  // namespace
+
+cudaError_t launch_stamp_accum(unsigned long long* stamps, int n, unsigned long long* acc, cudaStream_t s) {
+    k_stamp_accum<<<1, 256, 0, s>>>(stamps, n, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_check(LoopShell* S, int n, const double* fin, int* active, int* passes,
+                              cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_loop_check<<<1, 256, 0, s>>>(S, n, fin, active, passes, cond);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_convert_check(unsigned* bad, cudaStream_t s) {
     k_convert_check<<<512, 256, 0, s>>>(1 << 20, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BTask* tasks, int ntasks, int total_blocks, const int* active, int op, int colour,
-                         int stencil, int prec, cudaStream_t s) {
+                         int stencil, int prec, cudaStream_t s, unsigned long long* stamp) {
     if (ntasks <= 0 || total_blocks <= 0) return cudaSuccess;
     cudaError_t e;
-    if (prec == PREC64) e = batch_dispatch<PREC64>(tasks, ntasks, total_blocks, active, op, colour, stencil, s);
-    else if (prec == PREC32) e = batch_dispatch<PREC32>(tasks, ntasks, total_blocks, active, op, colour, stencil, s);
-    else e = batch_dispatch<PREC16>(tasks, ntasks, total_blocks, active, op, colour, stencil, s);
+    if (prec == PREC64) e = batch_dispatch<PREC64>(tasks, ntasks, total_blocks, active, op, colour, stencil, s, stamp);
+    else if (prec == PREC32)
+        e = batch_dispatch<PREC32>(tasks, ntasks, total_blocks, active, op, colour, stencil, s, stamp);
+    else e = batch_dispatch<PREC16>(tasks, ntasks, total_blocks, active, op, colour, stencil, s, stamp);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -234,10 +234,6 @@ void free_handle(mg_handle* h) {
     for (int s = 0; s < MG_PROF_SLOTS; ++s)
         if (h->prof_open[s]) cudaEventDestroy(h->prof_open[s]);
     for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
-    for (auto& p : h->graph_events) {
-        cudaEventDestroy(p.a);
-        cudaEventDestroy(p.b);
-    }
     plan_destroy(h->solo);
     plan_destroy(h->batch);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -946,38 +942,19 @@ static cudaEvent_t prof_event(mg_handle* h) {
     return e;
 }
 
-// Inside a stream capture the events become event-record nodes of the graph
-// (re-recorded at every replay and read after each one).
-static void prof_record(mg_handle* h, cudaEvent_t e) {
-    if (h->capturing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
-    else cudaEventRecord(e, h->stream);
-}
-
 void prof_begin(mg_handle* h, int slot) {
     if (!h->prof_on) return;
     cudaEvent_t e = prof_event(h);
-    prof_record(h, e);
+    cudaEventRecord(e, h->stream);
     h->prof_open[slot] = e;
 }
 
 void prof_end(mg_handle* h, int slot, int nlaunch) {
     if (!h->prof_on || !h->prof_open[slot]) return;
     cudaEvent_t e = prof_event(h);
-    prof_record(h, e);
-    if (h->capturing) h->graph_events.push_back({slot, h->prof_open[slot], e, nlaunch});
-    else h->prof_pending.push_back({slot, h->prof_open[slot], e, nlaunch});
+    cudaEventRecord(e, h->stream);
+    h->prof_pending.push_back({slot, h->prof_open[slot], e, nlaunch});
     h->prof_open[slot] = nullptr;
-}
-
-static void graph_prof_collect(mg_handle* h) {
-    for (auto& p : h->graph_events) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            h->prof_ms[p.slot] += ms;
-            h->prof_n[p.slot] += p.n;
-        }
-        cudaGetLastError();
-    }
 }
 
 void prof_collect(mg_handle* h) {

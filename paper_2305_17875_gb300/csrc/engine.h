@@ -78,7 +78,8 @@ struct mg_handle {
     long long allocs_done = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches = 0;           // kernels launched by the current solve
-    // kernel timing (mg_profile_enable)
+    // kernel timing (mg_profile_enable): events around stand-alone component
+    // calls; a solve's launches record their own clocks (solver.cu)
     struct Pending {
         int slot;
         cudaEvent_t a, b;
@@ -116,8 +117,6 @@ struct mg_handle {
     int tail_cluster = 8;             // CTAs per tail cluster
     mgs::TailTask* tail_dev = nullptr;
     mgs::TailTask tail_host{};
-    bool capturing = false;
-    std::vector<Pending> graph_events;     // event nodes inside the current graph
     mgs::Plan* solo = nullptr;             // the batch-of-one plan of mg_solve
     mgs::Plan* batch = nullptr;            // last mg_solve_batch plan led by this handle
     std::vector<unsigned long long> batch_key;   // serials of the batch plan's handles

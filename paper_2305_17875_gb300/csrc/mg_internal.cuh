@@ -51,6 +51,21 @@ struct Dims {
     __host__ __device__ i64 n() const { return (i64)nr * nth * nph; }
 };
 
+// Launch clock (profiling): stamp[0] = the earliest start of the launch's
+// CTAs (after their grid-dependency wait), stamp[1] = the latest end, on the
+// global nanosecond timer; a null stamp records nothing.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void stamp_start(unsigned long long* stamp) {
+    if (stamp && threadIdx.x == 0) atomicMin(stamp, global_ns());
+}
+__device__ __forceinline__ void stamp_end(unsigned long long* stamp) {
+    if (stamp && threadIdx.x == 0) atomicMax(stamp + 1, global_ns());
+}
+
 // Rows of a level split into groups of four longitude cells (aligned 16-byte
 // vectors of FP32) when nph is a multiple of 4; the batched level operations
 // then work on whole groups.

@@ -125,7 +125,8 @@ struct TailTask {
     const int* active; // per-shell flags of a batch (null: always run)
     int shell;
 };
-cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s);
+cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s,
+                        unsigned long long* stamp = nullptr);
 // Clusters of csize tail CTAs that can be co-resident (0: cluster launch unavailable).
 int tail_max_clusters(int csize, int stencil, int prec);
 
@@ -199,7 +200,7 @@ cudaError_t encode_sweep_maps(void* maps, const BTask& t, int stencil, int prec)
 // axi: 19 points without the longitude cross terms (the handle's stored
 // components); every task of the launch shares it.
 cudaError_t launch_sweep(const BTask* tasks, int ntasks, int total, const int* active, int stencil, bool axi,
-                         int prec, size_t smem, int threads, cudaStream_t s);
+                         int prec, size_t smem, int threads, cudaStream_t s, unsigned long long* stamp = nullptr);
 // The fault word of the sweeps (a plane copy that did not land in time);
 // clear resets it.
 cudaError_t sweep_fault_read(unsigned* out, bool clear);
@@ -219,7 +220,32 @@ cudaError_t launch_plane_factors(const double* const c[9], const Dims& D, int pr
 // against the hardware ones; *bad (zeroed by the caller) counts mismatches.
 cudaError_t launch_convert_check(unsigned* bad, cudaStream_t s);
 // All tasks of one launch share `stencil` (7 or 19) for the stencil ops.
+// stamp (profiling, may be null): the launch clock of stamp_start / stamp_end.
 cudaError_t launch_batch(const BTask* tasks, int ntasks, int total_blocks, const int* active, int op, int colour,
-                         int stencil, int prec, cudaStream_t s);
+                         int stencil, int prec, cudaStream_t s, unsigned long long* stamp = nullptr);
+// n launch clocks to (never started, never ended).
+cudaError_t launch_stamp_reset(unsigned long long* stamps, int n, cudaStream_t s);
+// Adds n launch clocks into acc (per launch: nanoseconds, count; then the
+// span from the first start to the last end, and the number of spans) and
+// resets the clocks.  One CTA.
+cudaError_t launch_stamp_accum(unsigned long long* stamps, int n, unsigned long long* acc, cudaStream_t s);
+
+// One shell's stop test of the outer iteration, kept on the device while the
+// iteration loops there (the test a solve makes between V-cycles, same
+// arithmetic: relative residual sqrt(rr) / ||b||, history, tolerance, growth
+// above 1e3 x the best so far, iteration limit).
+constexpr int kLoopHist = 64;
+enum { LOOP_RUN = 0, LOOP_NAN = 1, LOOP_DIVERGED = 2, LOOP_NOCONV = 3 };
+struct LoopShell {
+    double bnorm, best, tol, rr, rel;
+    int it, max_iters, done, why;   // why: LOOP_* (set with done)
+    double hist[kLoopHist];
+};
+// After an outer iteration: the active shells' iteration count and residual
+// (fin[4 i + 2]), their stop tests, the new active flags; passes[0] counts
+// the calls.  Sets the while node's condition to "some shell still active
+// and fewer than passes[1] calls".  One CTA.
+cudaError_t launch_loop_check(LoopShell* S, int n, const double* fin, int* active, int* passes,
+                              cudaGraphConditionalHandle cond, cudaStream_t s);
 
 }  // namespace mgs

@@ -12,6 +12,8 @@
 #include "engine.h"
 #include "xline_smooth.cuh"
 
+static_assert(mgs::kLoopHist == MG_HIST, "device stop-test history length");
+
 namespace mgs {
 
 namespace {
@@ -133,6 +135,25 @@ struct Plan {
     cudaGraphExec_t gexec = nullptr;
     bool graph_prof = false;
     long long graph_launches = 0;
+    // launch clocks while profiling (two words a launch: first start, last
+    // end): the iteration's own (captured in its graph) and a prologue's or
+    // epilogue's; the host copies are pinned
+    unsigned long long *d_stamp_it = nullptr, *h_stamp_it = nullptr;
+    unsigned long long *d_stamp_call = nullptr, *h_stamp_call = nullptr;
+    size_t stamp_it_cap = 0, stamp_call_cap = 0;
+    // the device-side outer loop: a graph whose while node repeats the
+    // iteration and the stop test of every shell until none is active
+    cudaGraphExec_t lexec = nullptr;
+    bool loop_prof = false;       // built with clocks
+    bool loop_failed = false;     // the runtime refused the graph: host loop
+    long long loop_launches = 0;  // kernels per pass
+    LoopShell* d_loop = nullptr;  // per-shell stop tests
+    LoopShell* h_loop = nullptr;  // pinned
+    int* d_ctl = nullptr;         // [passes made, pass limit]
+    int* h_ctl = nullptr;         // pinned
+    size_t dloop_cap = 0, hloop_cap = 0, dctl_cap = 0, hctl_cap = 0;
+    unsigned long long *d_acc = nullptr, *h_acc = nullptr;   // clocks summed over the passes
+    size_t acc_cap = 0;
 };
 
 namespace {
@@ -520,35 +541,115 @@ void build_iteration(Plan* pl) {
     P.drop_empty();
 }
 
-mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const int* active) {
+// The timing slot of a launch: the named fine-level ones, the coarser
+// levels' operations by level, the rest together.
+int slot_of(const Launch& L) {
+    return L.prof >= 0   ? L.prof
+           : L.level > 0 ? MG_PROF_LEVEL_BASE + std::min(L.level, MG_PROF_SLOTS - 1 - MG_PROF_LEVEL_BASE)
+                         : MG_PROF_OTHER;
+}
+
+// Launch-clock buffers for n launches (device and pinned host), grown on
+// demand; a grown iteration buffer needs a new graph (the old one holds the
+// old address).
+mg_status stamp_buffers(size_t n, unsigned long long** d, unsigned long long** hbuf, size_t* cap) {
+    if (n <= *cap && *d) return MG_OK;
+    if (*d) cudaFree(*d);
+    if (*hbuf) cudaFreeHost(*hbuf);
+    *d = *hbuf = nullptr;
+    *cap = 0;
+    // two words a launch, and two more for the accumulated spans
+    CK(cudaMalloc((void**)d, 2 * sizeof(unsigned long long) * (n + 1)));
+    CK(cudaMallocHost((void**)hbuf, 2 * sizeof(unsigned long long) * (n + 1)));
+    *cap = n;
+    return MG_OK;
+}
+
+// Launches P's kernels in order.  With d_st (profiling), every launch also
+// records its clock (its CTAs' first start after the grid-dependency wait and
+// last end) in d_st + 2 i.  Unlike events between launches, the clocks leave
+// the launches' programmatic overlap as it is.
+mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const int* active,
+                      unsigned long long* d_st = nullptr) {
     mg_handle* h0 = lead(pl);
-    for (const Launch& L : P.launches) {
-        // every launch is timed in some slot: the named fine-level ones, the
-        // coarser levels' operations by level, the rest together
-        const int slot = L.prof >= 0   ? L.prof
-                         : L.level > 0 ? MG_PROF_LEVEL_BASE + std::min(L.level, MG_PROF_SLOTS - 1 - MG_PROF_LEVEL_BASE)
-                                       : MG_PROF_OTHER;
-        prof_begin(h0, slot);
+    const int nl = (int)P.launches.size();
+    for (int i = 0; i < nl; ++i) {
+        const Launch& L = P.launches[i];
+        if (!L.tail_stencil && L.total == 0) continue;   // launches nothing
+        unsigned long long* st = d_st ? d_st + 2 * i : nullptr;
         if (L.tail_stencil) {
             int first = 0, n = 0;
-            for (size_t i = 0; i < P.tails.size(); ++i) {
-                const int st = P.tails[i].lev[0].v.stencil;
-                if (st != L.tail_stencil) continue;
-                if (n == 0) first = (int)i;
+            for (size_t k = 0; k < P.tails.size(); ++k) {
+                const int sten = P.tails[k].lev[0].v.stencil;
+                if (sten != L.tail_stencil) continue;
+                if (n == 0) first = (int)k;
                 ++n;
             }
-            CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream));
+            CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream, st));
         } else if (L.op == BOP_SWEEP) {
             CK(launch_sweep(d_tasks + L.t0, L.nt, L.total, active, L.stencil, L.axi, pl->prec, L.smem, L.threads,
-                            pl->stream));
+                            pl->stream, st));
         } else {
             CK(launch_batch(d_tasks + L.t0, L.nt, L.total, active, L.op, L.colour, L.stencil, pl->prec,
-                            pl->stream));
+                            pl->stream, st));
         }
-        prof_end(h0, slot, L.prof >= 0 ? L.prof_n : 1);
         h0->launches += 1;
     }
     return MG_OK;
+}
+
+// run_program with clocks: reset, the launches, the clocks copied to h_st;
+// stamps_collect reads them once the stream has passed that copy.
+mg_status run_clocked(Plan* pl, const Program& P, const BTask* d_tasks, const int* active,
+                      unsigned long long* d_st, unsigned long long* h_st) {
+    const int nl = (int)P.launches.size();
+    CK(launch_stamp_reset(d_st, nl, pl->stream));
+    lead(pl)->launches += 1;
+    CKS(run_program(pl, P, d_tasks, active, d_st));
+    if (nl > 0)
+        CK(cudaMemcpyAsync(h_st, d_st, 2 * sizeof(unsigned long long) * nl, cudaMemcpyDeviceToHost, pl->stream));
+    return MG_OK;
+}
+
+// Adds the launch clocks of one run of P (read back into h_st) to the slots;
+// the time between its first start and last end that no launch covers goes
+// to the gap slot.
+void stamps_collect(mg_handle* h0, const Program& P, const unsigned long long* h_st) {
+    unsigned long long lo = ~0ull, hi = 0, busy = 0;
+    for (size_t i = 0; i < P.launches.size(); ++i) {
+        const unsigned long long a = h_st[2 * i], b = h_st[2 * i + 1];
+        if (a == ~0ull || b < a) continue;   // the launch ran no CTA
+        const Launch& L = P.launches[i];
+        const int slot = slot_of(L);
+        h0->prof_ms[slot] += (double)(b - a) * 1e-6;
+        h0->prof_n[slot] += L.prof >= 0 ? L.prof_n : 1;
+        busy += b - a;
+        lo = std::min(lo, a);
+        hi = std::max(hi, b);
+    }
+    if (lo != ~0ull && hi - lo >= busy) {
+        h0->prof_ms[MG_PROF_GAPS] += (double)(hi - lo - busy) * 1e-6;
+        h0->prof_n[MG_PROF_GAPS] += 1;
+    }
+}
+
+// The same from clocks accumulated on the device (launch_stamp_accum) over
+// the passes of the device-side loop.
+void acc_collect(mg_handle* h0, const Program& P, const unsigned long long* acc) {
+    const size_t nl = P.launches.size();
+    unsigned long long busy = 0;
+    for (size_t i = 0; i < nl; ++i) {
+        if (!acc[2 * i + 1]) continue;
+        const Launch& L = P.launches[i];
+        const int slot = slot_of(L);
+        h0->prof_ms[slot] += (double)acc[2 * i] * 1e-6;
+        h0->prof_n[slot] += (long long)acc[2 * i + 1] * (L.prof >= 0 ? L.prof_n : 1);
+        busy += acc[2 * i];
+    }
+    if (acc[2 * nl + 1] && acc[2 * nl] >= busy) {
+        h0->prof_ms[MG_PROF_GAPS] += (double)(acc[2 * nl] - busy) * 1e-6;
+        h0->prof_n[MG_PROF_GAPS] += (long long)acc[2 * nl + 1];
+    }
 }
 
 mg_status upload_call(Plan* pl, const Program& P) {
@@ -564,22 +665,38 @@ mg_status upload_call(Plan* pl, const Program& P) {
     return MG_OK;
 }
 
+// The iteration's clock buffer; a new one retires the graph that holds the
+// old address.
+mg_status iter_stamps(Plan* pl) {
+    unsigned long long* before = pl->d_stamp_it;
+    CKS(stamp_buffers(pl->iter.launches.size(), &pl->d_stamp_it, &pl->h_stamp_it, &pl->stamp_it_cap));
+    if (pl->d_stamp_it != before && pl->gexec) {
+        CK(cudaStreamSynchronize(pl->stream));
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
+    }
+    return MG_OK;
+}
+
+// A prologue or epilogue (not captured), clocked while profiling.
+mg_status run_call(Plan* pl, const Program& P) {
+    if (!lead(pl)->prof_on) return run_program(pl, P, pl->d_call, nullptr);
+    CKS(stamp_buffers(P.launches.size(), &pl->d_stamp_call, &pl->h_stamp_call, &pl->stamp_call_cap));
+    return run_clocked(pl, P, pl->d_call, nullptr, pl->d_stamp_call, pl->h_stamp_call);
+}
+
 mg_status build_graph(Plan* pl) {
     mg_handle* h0 = lead(pl);
     if (pl->gexec) {
         cudaGraphExecDestroy(pl->gexec);
         pl->gexec = nullptr;
     }
-    for (auto& p : h0->graph_events) {
-        h0->prof_pool.push_back(p.a);
-        h0->prof_pool.push_back(p.b);
-    }
-    h0->graph_events.clear();
+    const bool prof = h0->prof_on;
+    if (prof) CKS(iter_stamps(pl));
     const long long before = h0->launches;
     CK(cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal));
-    h0->capturing = true;
-    const mg_status st = run_program(pl, pl->iter, pl->d_iter, pl->d_active);
-    h0->capturing = false;
+    const mg_status st = prof ? run_clocked(pl, pl->iter, pl->d_iter, pl->d_active, pl->d_stamp_it, pl->h_stamp_it)
+                              : run_program(pl, pl->iter, pl->d_iter, pl->d_active);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(pl->stream, &g);
     if (st != MG_OK) {
@@ -592,7 +709,7 @@ mg_status build_graph(Plan* pl) {
     const cudaError_t ei = cudaGraphInstantiate(&pl->gexec, g, 0);
     cudaGraphDestroy(g);
     CK(ei);
-    pl->graph_prof = h0->prof_on;
+    pl->graph_prof = prof;
     return MG_OK;
 }
 
@@ -618,6 +735,17 @@ void plan_destroy(Plan* pl) {
     if (pl->d_call) cudaFree(pl->d_call);
     if (pl->h_active) cudaFreeHost(pl->h_active);
     if (pl->h_fin) cudaFreeHost(pl->h_fin);
+    if (pl->d_stamp_it) cudaFree(pl->d_stamp_it);
+    if (pl->h_stamp_it) cudaFreeHost(pl->h_stamp_it);
+    if (pl->d_stamp_call) cudaFree(pl->d_stamp_call);
+    if (pl->h_stamp_call) cudaFreeHost(pl->h_stamp_call);
+    if (pl->lexec) cudaGraphExecDestroy(pl->lexec);
+    if (pl->d_loop) cudaFree(pl->d_loop);
+    if (pl->h_loop) cudaFreeHost(pl->h_loop);
+    if (pl->d_ctl) cudaFree(pl->d_ctl);
+    if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
+    if (pl->d_acc) cudaFree(pl->d_acc);
+    if (pl->h_acc) cudaFreeHost(pl->h_acc);
     delete pl;
 }
 
@@ -658,7 +786,15 @@ mg_status plan_reset(Plan* pl, mg_handle* const* hs, int n, bool iteration) {
         cudaGraphExecDestroy(pl->gexec);
         pl->gexec = nullptr;
     }
+    if (pl->lexec) {
+        cudaGraphExecDestroy(pl->lexec);
+        pl->lexec = nullptr;
+    }
     CK(grow(&pl->d_active, &pl->dact_cap, (size_t)n, false));
+    CK(grow(&pl->d_loop, &pl->dloop_cap, (size_t)n, false));
+    CK(grow(&pl->h_loop, &pl->hloop_cap, (size_t)n, true));
+    CK(grow(&pl->d_ctl, &pl->dctl_cap, (size_t)2, false));
+    CK(grow(&pl->h_ctl, &pl->hctl_cap, (size_t)2, true));
     CK(grow(&pl->h_active, &pl->hact_cap, (size_t)n, true));
     CK(grow(&pl->d_fin, &pl->dfin_cap, (size_t)4 * n, false));
     CK(grow(&pl->h_fin, &pl->hfin_cap, (size_t)4 * n, true));
@@ -777,9 +913,11 @@ mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const d
         pro.add(t, 1);
     }
     add_residual(pro, pl);
+    pro.drop_empty();   // the residual launch of the stencil no shell has
     CKS(upload_call(pl, pro));
-    CKS(run_program(pl, pro, pl->d_call, nullptr));
+    CKS(run_call(pl, pro));
     CKS(read_fin(pl));
+    if (pl->hs[0]->prof_on) stamps_collect(pl->hs[0], pro, pl->h_stamp_call);
     for (int i = 0; i < n; ++i) {
         mg_handle* h = pl->hs[i];
         SolveState& q = S[i];
@@ -843,24 +981,21 @@ mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph) {
     const int n = (int)pl->hs.size();
     mg_handle* h0 = lead(pl);
     CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, pl->stream));
+    const bool prof = h0->prof_on;
     if (use_graph) {
-        if (!pl->gexec || pl->graph_prof != h0->prof_on) CKS(build_graph(pl));
+        if (!pl->gexec || pl->graph_prof != prof) CKS(build_graph(pl));
         CK(cudaGraphLaunch(pl->gexec, pl->stream));
         h0->launches += pl->graph_launches;
     } else {
-        CKS(run_program(pl, pl->iter, pl->d_iter, pl->d_active));
-    }
-    CKS(read_fin(pl));
-    if (use_graph && h0->prof_on) {
-        for (auto& p : h0->graph_events) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                h0->prof_ms[p.slot] += ms;
-                h0->prof_n[p.slot] += p.n;
-            }
-            cudaGetLastError();
+        if (prof) {
+            CKS(iter_stamps(pl));
+            CKS(run_clocked(pl, pl->iter, pl->d_iter, pl->d_active, pl->d_stamp_it, pl->h_stamp_it));
+        } else {
+            CKS(run_program(pl, pl->iter, pl->d_iter, pl->d_active));
         }
     }
+    CKS(read_fin(pl));
+    if (prof) stamps_collect(h0, pl->iter, pl->h_stamp_it);
     for (int i = 0; i < n; ++i)
         if (pl->h_active[i]) {
             S[i].it += 1;
@@ -936,9 +1071,165 @@ mg_status plan_finish(Plan* pl, double* const* x) {
         epi.add(t, vblocks(pl->hs[i], vector_items(t.n)));
     }
     CKS(upload_call(pl, epi));
-    CKS(run_program(pl, epi, pl->d_call, nullptr));
+    CKS(run_call(pl, epi));
+    if (lead(pl)->prof_on) {
+        CK(cudaStreamSynchronize(pl->stream));
+        stamps_collect(lead(pl), epi, pl->h_stamp_call);
+    }
     return MG_OK;
 }
+
+namespace {
+
+// The while-node graph of the device-side loop: one pass = the iteration,
+// the stop tests (which set the node's condition), and with clocks their
+// accumulation.  False with the runtime's error cleared when the graph
+// cannot be made (the caller then loops on the host).
+bool build_loop(Plan* pl) {
+    mg_handle* h0 = lead(pl);
+    if (pl->lexec) {
+        cudaGraphExecDestroy(pl->lexec);
+        pl->lexec = nullptr;
+    }
+    const bool prof = h0->prof_on;
+    const int nl = (int)pl->iter.launches.size();
+    if (prof && (iter_stamps(pl) != MG_OK ||
+                 stamp_buffers((size_t)nl, &pl->d_acc, &pl->h_acc, &pl->acc_cap) != MG_OK)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t top = nullptr;
+    if (cudaGraphCreate(&top, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = false;
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphConditionalHandleCreate(&cond, top, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const long long before = h0->launches;
+        ok = cudaStreamBeginCaptureToGraph(pl->stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            bool run = run_program(pl, pl->iter, pl->d_iter, pl->d_active, prof ? pl->d_stamp_it : nullptr) == MG_OK;
+            run = run && launch_loop_check(pl->d_loop, (int)pl->hs.size(), pl->d_fin, pl->d_active, pl->d_ctl, cond,
+                                           pl->stream) == cudaSuccess;
+            h0->launches += 1;
+            if (prof) {
+                run = run && launch_stamp_accum(pl->d_stamp_it, nl, pl->d_acc, pl->stream) == cudaSuccess;
+                h0->launches += 1;
+            }
+            cudaGraph_t got = nullptr;
+            ok = cudaStreamEndCapture(pl->stream, &got) == cudaSuccess && run;
+        }
+        pl->loop_launches = h0->launches - before;
+        h0->launches = before;
+    }
+    if (ok) ok = cudaGraphInstantiate(&pl->lexec, top, 0) == cudaSuccess;
+    cudaGraphDestroy(top);
+    if (!ok) {
+        if (pl->lexec) cudaGraphExecDestroy(pl->lexec);
+        pl->lexec = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    pl->loop_prof = prof;
+    return true;
+}
+
+// Runs the outer iterations of every still-active shell on the device (the
+// loop graph), then takes the stop tests' results back into S: the same
+// iterates, counts, histories and statuses as the host loop gives.  Sets
+// *unavailable (and returns MG_OK) when the graph cannot be made.
+mg_status plan_loop(Plan* pl, SolveState* S, bool* unavailable) {
+    const int n = (int)pl->hs.size();
+    mg_handle* h0 = lead(pl);
+    const bool prof = h0->prof_on;
+    *unavailable = false;
+    if (!pl->lexec || pl->loop_prof != prof) {
+        if (!build_loop(pl)) {
+            pl->loop_failed = true;
+            *unavailable = true;
+            return MG_OK;
+        }
+    }
+    int most = 0;
+    for (int i = 0; i < n; ++i) {
+        const SolveState& q = S[i];
+        LoopShell& L = pl->h_loop[i];
+        L.bnorm = q.bnorm;
+        L.best = q.best;
+        L.tol = q.tol;
+        L.rr = q.rr;
+        L.rel = q.R.rel_res;
+        L.it = q.it;
+        L.max_iters = pl->hs[i]->opts.max_iters;
+        L.done = q.done ? 1 : 0;
+        L.why = LOOP_RUN;
+        if (!q.done) most = std::max(most, L.max_iters - q.it);
+    }
+    // never binds: every pass moves each active shell one iteration toward
+    // its limit
+    pl->h_ctl[0] = 0;
+    pl->h_ctl[1] = most + 1;
+    cudaStream_t s = pl->stream;
+    CK(cudaMemcpyAsync(pl->d_loop, pl->h_loop, sizeof(LoopShell) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->d_ctl, pl->h_ctl, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    const size_t nl = pl->iter.launches.size();
+    if (prof) {
+        CK(cudaMemsetAsync(pl->d_acc, 0, 2 * sizeof(unsigned long long) * (nl + 1), s));
+        CK(launch_stamp_reset(pl->d_stamp_it, (int)nl, s));
+        h0->launches += 1;
+    }
+    CK(cudaGraphLaunch(pl->lexec, s));
+    CK(cudaMemcpyAsync(pl->h_loop, pl->d_loop, sizeof(LoopShell) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pl->h_ctl, pl->d_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (prof)
+        CK(cudaMemcpyAsync(pl->h_acc, pl->d_acc, 2 * sizeof(unsigned long long) * (nl + 1), cudaMemcpyDeviceToHost,
+                           s));
+    CK(cudaStreamSynchronize(s));
+    h0->launches += (long long)pl->h_ctl[0] * pl->loop_launches;
+    if (prof) acc_collect(h0, pl->iter, pl->h_acc);
+    for (int i = 0; i < n; ++i) {
+        SolveState& q = S[i];
+        if (q.done) continue;
+        const LoopShell& L = pl->h_loop[i];
+        for (int k = q.it + 1; k <= L.it && k < MG_HIST; ++k) q.R.res_hist[k] = L.hist[k];
+        q.it = L.it;
+        q.rr = L.rr;
+        q.best = L.best;
+        q.R.rel_res = L.rel;
+        q.done = true;
+        if (L.why == LOOP_NAN) {
+            q.st = MG_ENAN;
+            set_error("non-finite residual");
+        } else if (L.why == LOOP_DIVERGED) {
+            q.st = MG_EDIVERGED;
+            set_error("residual diverged");
+        } else if (L.why == LOOP_NOCONV) {
+            q.st = MG_ENOCONV;
+            set_error("max_iters reached");
+        } else if (!L.done) {
+            q.st = MG_ENOCONV;
+            set_error("outer loop stopped at its pass limit");
+        }
+    }
+    return MG_OK;
+}
+
+bool host_loop_forced() { return std::getenv("MG_HOST_LOOP") != nullptr; }
+
+}  // namespace
 
 // Solve every shell of the plan; the stop logic per shell is the one of a
 // lone solve, so a shell's iterates do not depend on its batch companions.
@@ -950,7 +1241,16 @@ mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const d
     CK(cudaEventRecord(h0->ev0, s));
     std::vector<SolveState> S(n);
     CKS(plan_start(pl, f, x, tol, S.data()));
-    while (plan_check(pl, S.data()) > 0) CKS(plan_iterate(pl, S.data(), h0->use_graph));
+    int active = plan_check(pl, S.data());
+    if (active > 0 && h0->use_graph && !pl->loop_failed && !host_loop_forced()) {
+        bool unavailable = false;
+        CKS(plan_loop(pl, S.data(), &unavailable));
+        if (!unavailable) active = 0;
+    }
+    while (active > 0) {
+        CKS(plan_iterate(pl, S.data(), h0->use_graph));
+        active = plan_check(pl, S.data());
+    }
     CKS(plan_finish(pl, x));
     CK(cudaEventRecord(h0->ev1, s));
     CK(cudaEventSynchronize(h0->ev1));

@@ -274,11 +274,16 @@ struct CoefOf<PREC16> {
 };
 
 template <int S, typename T, int P>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __restrict__ tasks, int csize) {
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __restrict__ tasks, int csize,
+                                                          unsigned long long* stamp) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const TailTask& tk = tasks[blockIdx.x / csize];
-    if (tk.active && !tk.active[tk.shell]) return;     // uniform over the cluster
+    stamp_start(stamp);
+    if (tk.active && !tk.active[tk.shell]) {           // uniform over the cluster
+        stamp_end(stamp);
+        return;
+    }
     const i64 first = (i64)cl.block_rank() * blockDim.x + threadIdx.x;
     const i64 stride = (i64)csize * blockDim.x;
     const int ncol = S == 7 ? 2 : 4;
@@ -314,6 +319,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __rest
                 cl.sync();
             }
     }
+    stamp_end(stamp);
 }
 
 }  // namespace
@@ -418,7 +424,8 @@ cudaError_t launch_coarse_solve(const double* binv, int n, int prec, const void*
 }
 
 template <int S, typename T, int P>
-static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cudaStream_t s) {
+static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cudaStream_t s,
+                               unsigned long long* stamp) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntasks * csize, 1, 1);
     cfg.blockDim = dim3(kTailThreads, 1, 1);
@@ -431,7 +438,7 @@ static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cud
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tail<S, T, P>, tasks, csize);
+    return cudaLaunchKernelEx(&cfg, k_tail<S, T, P>, tasks, csize, stamp);
 }
 
 template <int S, typename T, int P>
@@ -462,17 +469,18 @@ int tail_max_clusters(int csize, int stencil, int prec) {
     return stencil == 19 ? tail_clusters<19, float, PREC16>(csize) : tail_clusters<7, float, PREC16>(csize);
 }
 
-cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s) {
+cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s,
+                        unsigned long long* stamp) {
     cudaError_t e;
     if (prec == PREC64)
-        e = stencil == 19 ? tail_launch<19, double, PREC64>(tasks, ntasks, csize, s)
-                          : tail_launch<7, double, PREC64>(tasks, ntasks, csize, s);
+        e = stencil == 19 ? tail_launch<19, double, PREC64>(tasks, ntasks, csize, s, stamp)
+                          : tail_launch<7, double, PREC64>(tasks, ntasks, csize, s, stamp);
     else if (prec == PREC32)
-        e = stencil == 19 ? tail_launch<19, float, PREC32>(tasks, ntasks, csize, s)
-                          : tail_launch<7, float, PREC32>(tasks, ntasks, csize, s);
+        e = stencil == 19 ? tail_launch<19, float, PREC32>(tasks, ntasks, csize, s, stamp)
+                          : tail_launch<7, float, PREC32>(tasks, ntasks, csize, s, stamp);
     else
-        e = stencil == 19 ? tail_launch<19, float, PREC16>(tasks, ntasks, csize, s)
-                          : tail_launch<7, float, PREC16>(tasks, ntasks, csize, s);
+        e = stencil == 19 ? tail_launch<19, float, PREC16>(tasks, ntasks, csize, s, stamp)
+                          : tail_launch<7, float, PREC16>(tasks, ntasks, csize, s, stamp);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

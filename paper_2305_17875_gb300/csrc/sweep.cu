@@ -495,13 +495,15 @@ __device__ void sweep_tile(const BTask& tk, const CF& cf_shared, int lb, unsigne
 
 template <int S, int P, bool AXI>
 __global__ void __launch_bounds__(kSW) k_sweep(const BTask* __restrict__ tasks, int ntasks, int total,
-                                               const int* __restrict__ active, int early_trigger) {
+                                               const int* __restrict__ active, int early_trigger,
+        unsigned long long* stamp) {
     typedef typename SPrec<P>::T T;
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];
     __shared__ int tk_index;
     const BTask& tk = *reinterpret_cast<const BTask*>(tk_raw);
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    stamp_start(stamp);
     if (early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -523,6 +525,7 @@ __global__ void __launch_bounds__(kSW) k_sweep(const BTask* __restrict__ tasks, 
         if (!active || active[tk.shell]) sweep_tile<S, AXI, T>(tk, SPrec<P>::cf(tk.v), vb - tk.block0, dyn);
         __syncthreads();
     }
+    stamp_end(stamp);
     if (!early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
@@ -558,7 +561,8 @@ cudaError_t sweep_per_sm(K kernel, int threads, size_t smem, int* per_sm) {
 }
 
 template <int S, int P, bool AXI>
-cudaError_t sweep_launch(const BTask* tasks, int ntasks, int total, const int* active, size_t smem, cudaStream_t s) {
+cudaError_t sweep_launch(const BTask* tasks, int ntasks, int total, const int* active, size_t smem, cudaStream_t s,
+                         unsigned long long* stamp) {
     int per_sm = 0;
     cudaError_t e = sweep_per_sm(k_sweep<S, P, AXI>, kSW, smem, &per_sm);
     if (e != cudaSuccess) return e;
@@ -574,7 +578,7 @@ cudaError_t sweep_launch(const BTask* tasks, int ntasks, int total, const int* a
     attrs[0].val.programmaticStreamSerializationAllowed = sweep_pdl() ? 1 : 0;
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sweep<S, P, AXI>, tasks, ntasks, total, active, grid >= total ? 1 : 0);
+    return cudaLaunchKernelEx(&cfg, k_sweep<S, P, AXI>, tasks, ntasks, total, active, grid >= total ? 1 : 0, stamp);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -954,12 +958,14 @@ __device__ __forceinline__ void rb7_tile(const BTask& tk, int lb, unsigned char*
 
 template <typename CT>
 __global__ void __launch_bounds__(kRB7Max, 1) k_rb7(const BTask* __restrict__ tasks, int ntasks, int total,
-                                                    const int* __restrict__ active, int early_trigger) {
+                                                    const int* __restrict__ active, int early_trigger,
+        unsigned long long* stamp) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(16) unsigned char tk_raw[sizeof(BTask)];
     __shared__ int tk_index;
     const BTask& tk = *reinterpret_cast<const BTask*>(tk_raw);
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    stamp_start(stamp);
     if (early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -984,12 +990,13 @@ __global__ void __launch_bounds__(kRB7Max, 1) k_rb7(const BTask* __restrict__ ta
         }
         __syncthreads();
     }
+    stamp_end(stamp);
     if (!early_trigger) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
 template <typename CT>
 cudaError_t rb7_launch(const BTask* tasks, int ntasks, int total, const int* active, size_t smem, int threads,
-                       cudaStream_t s) {
+                       cudaStream_t s, unsigned long long* stamp) {
     if (threads < 32 || threads > kRB7Max) return cudaErrorInvalidConfiguration;
     int per_sm = 0;
     cudaError_t e = sweep_per_sm(k_rb7<CT>, threads, smem, &per_sm);
@@ -1006,7 +1013,7 @@ cudaError_t rb7_launch(const BTask* tasks, int ntasks, int total, const int* act
     attrs[0].val.programmaticStreamSerializationAllowed = sweep_pdl() ? 1 : 0;
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_rb7<CT>, tasks, ntasks, total, active, grid >= total ? 1 : 0);
+    return cudaLaunchKernelEx(&cfg, k_rb7<CT>, tasks, ntasks, total, active, grid >= total ? 1 : 0, stamp);
 }
 
 bool rb7_path(int stencil, int prec) { return stencil == 7 && prec != PREC64; }
@@ -1109,22 +1116,22 @@ cudaError_t encode_sweep_maps(void* maps, const BTask& t, int stencil, int prec)
 }
 
 cudaError_t launch_sweep(const BTask* tasks, int ntasks, int total, const int* active, int stencil, bool axi,
-                         int prec, size_t smem, int threads, cudaStream_t s) {
+                         int prec, size_t smem, int threads, cudaStream_t s, unsigned long long* stamp) {
     if (ntasks <= 0 || total <= 0) return cudaSuccess;
     cudaError_t e;
     if (rb7_path(stencil, prec)) {
-        if (prec == PREC16) e = rb7_launch<__half>(tasks, ntasks, total, active, smem, threads, s);
-        else e = rb7_launch<float>(tasks, ntasks, total, active, smem, threads, s);
+        if (prec == PREC16) e = rb7_launch<__half>(tasks, ntasks, total, active, smem, threads, s, stamp);
+        else e = rb7_launch<float>(tasks, ntasks, total, active, smem, threads, s, stamp);
     } else if (stencil == 7) {   // FP64 (FP32 / FP16 take the red-black kernel above)
-        e = sweep_launch<7, PREC64, false>(tasks, ntasks, total, active, smem, s);
+        e = sweep_launch<7, PREC64, false>(tasks, ntasks, total, active, smem, s, stamp);
     } else if (axi) {
-        if (prec == PREC64) e = sweep_launch<19, PREC64, true>(tasks, ntasks, total, active, smem, s);
-        else if (prec == PREC32) e = sweep_launch<19, PREC32, true>(tasks, ntasks, total, active, smem, s);
-        else e = sweep_launch<19, PREC16, true>(tasks, ntasks, total, active, smem, s);
+        if (prec == PREC64) e = sweep_launch<19, PREC64, true>(tasks, ntasks, total, active, smem, s, stamp);
+        else if (prec == PREC32) e = sweep_launch<19, PREC32, true>(tasks, ntasks, total, active, smem, s, stamp);
+        else e = sweep_launch<19, PREC16, true>(tasks, ntasks, total, active, smem, s, stamp);
     } else {
-        if (prec == PREC64) e = sweep_launch<19, PREC64, false>(tasks, ntasks, total, active, smem, s);
-        else if (prec == PREC32) e = sweep_launch<19, PREC32, false>(tasks, ntasks, total, active, smem, s);
-        else e = sweep_launch<19, PREC16, false>(tasks, ntasks, total, active, smem, s);
+        if (prec == PREC64) e = sweep_launch<19, PREC64, false>(tasks, ntasks, total, active, smem, s, stamp);
+        else if (prec == PREC32) e = sweep_launch<19, PREC32, false>(tasks, ntasks, total, active, smem, s, stamp);
+        else e = sweep_launch<19, PREC16, false>(tasks, ntasks, total, active, smem, s, stamp);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

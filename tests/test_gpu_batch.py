@@ -101,3 +101,36 @@ def test_batch_argument_errors(lib):
     h64 = lib.mg_setup(g, dict(precision=0))
     with pytest.raises(lib.MGError):
         lib.mg_solve_batch([h, h64], [f, f], [torch.zeros_like(f), torch.zeros_like(f)], [1e-8, 1e-8])
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_device_loop_equals_host_loop(lib, prec, monkeypatch):
+    """The outer loop on the device (a graph whose while node repeats the
+    iteration and the stop tests) against the same loop driven by the host
+    (MG_HOST_LOOP): bitwise the same iterates, counts, residual histories and
+    statuses, for a mixed batch with its own tolerances and for a shell that
+    stops at max_iters."""
+    import torch
+    gs, fs, tols = _mixed_shells()
+    runs = {}
+    for mode in ("device", "host"):
+        if mode == "host":
+            monkeypatch.setenv("MG_HOST_LOOP", "1")
+        else:
+            monkeypatch.delenv("MG_HOST_LOOP", raising=False)
+        hs = [lib.mg_setup(g, dict(precision=prec)) for g in gs]
+        fd = [_dev(f) for f in fs]
+        xs = [torch.zeros_like(f) for f in fd]
+        reps = lib.mg_solve_batch(hs, fd, xs, tols)
+        h2 = lib.mg_setup(gs[3], dict(precision=prec, max_iters=3))
+        x2 = torch.zeros_like(fd[3])
+        r2 = lib.mg_solve(h2, fd[3], x2, tol=1e-14, allow=(lib.MG_ENOCONV,))
+        runs[mode] = ([x.cpu().numpy() for x in xs], reps, x2.cpu().numpy(), r2)
+    (xd, rd, x2d, r2d), (xh, rh, x2h, r2h) = runs["device"], runs["host"]
+    for s in range(len(gs)):
+        for k in ("iters", "status", "rel_res", "res_hist"):
+            assert rd[s][k] == rh[s][k], (s, k)
+        assert np.array_equal(xd[s], xh[s]), s
+    assert r2d["status"] == r2h["status"] == "MG_ENOCONV" and r2d["iters"] == r2h["iters"] == 3
+    assert r2d["res_hist"] == r2h["res_hist"] and np.array_equal(x2d, x2h)
+
