@@ -331,6 +331,8 @@ typedef struct {
     long long tile_min_cells; /* one-pass tiles: levels with fewer cells keep the colour passes */
     int tile0[3];           /* the fine level's tile (colatitude rows, radius planes, longitudes);
                                zeros when the fine level is swept by colour passes */
+    int tail_smem_bytes;    /* > 0: the 7-point tail keeps its levels in the cluster's shared
+                               memory, this many bytes per CTA (MG_TAIL_GLOBAL=1: global memory) */
 } mg_schedule;
 mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out);
 

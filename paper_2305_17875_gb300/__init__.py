@@ -60,7 +60,8 @@ class mg_schedule(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("tail_level", C.c_int), ("tail_cluster", C.c_int),
                 ("one_pass_tiles", C.c_int), ("source", C.c_int), ("candidates", C.c_int),
                 ("ms_per_iteration", C.c_double), ("tile_cells", C.c_int), ("tile_planes", C.c_int),
-                ("tile_kmax", C.c_int), ("tile_min_cells", C.c_longlong), ("tile0", C.c_int * 3)]
+                ("tile_kmax", C.c_int), ("tile_min_cells", C.c_longlong), ("tile0", C.c_int * 3),
+                ("tail_smem_bytes", C.c_int)]
 
 
 class mg_report(C.Structure):

@@ -442,12 +442,14 @@ mg_status plan_next(mg_handle* h, const Level& lv, int f[3], bool* ok) {
 // shorter than two levels or clusters cannot be co-resident.
 mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
     h->tail_level = 0;
+    h->tail_smem = 0;
     if (cells <= 0 || h->opts.smoother != MG_SMOOTH_GS) return MG_OK;
     if (h->grid.cut && h->stencil == 19) return MG_OK;   // the tail's passes know no pole copy
     const int nl = (int)h->L.size();
     int t = nl;
     while (t - 1 >= 1 && h->L[t - 1].D.n() <= cells) --t;
     if (nl - t < 2 || nl - t > kMaxTail || tail_max_clusters(cluster, h->stencil, h->prec) <= 0) return MG_OK;
+    h->tail_smem = 0;
     TailTask task{};
     task.nlev = nl - t;
     task.nu1 = h->opts.nu1;
@@ -461,6 +463,14 @@ mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
     h->tail_host = task;
     h->tail_level = t;
     h->tail_cluster = cluster;
+    // 7 points: every level in the cluster's shared memory when it fits
+    // (MG_TAIL_GLOBAL keeps the global-memory form)
+    if (h->stencil == 7 && !std::getenv("MG_TAIL_GLOBAL")) {
+        TailSmLayout lay;
+        tail_sm_layout(task, cluster, h->prec == PREC64 ? 8 : 4, lay);
+        if (lay.bytes <= kTailSmMaxBytes && tail_max_clusters(cluster, 7, h->prec, lay.bytes) > 0)
+            h->tail_smem = lay.bytes;
+    }
     return MG_OK;
 }
 
@@ -471,6 +481,7 @@ mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
 struct Schedule {
     int vb_cap = 16;
     i64 tail_cells = 0;
+    int tail_cluster = 8;     // CTAs per tail cluster
     bool fused = false;       // one-pass sweeps
     int tile_cells = 2048;    // one-pass tiles: target cells per plane
     int tile_tj = 0;          // one-pass tiles: planes per chunk (0: per level)
@@ -512,7 +523,7 @@ bool can_fuse(mg_handle* h, const Schedule& sc) {
 mg_status apply_schedule(mg_handle* h, const Schedule& sc) {
     h->vb_cap = sc.vb_cap;
     set_tiles(h, sc.fused && can_fuse(h, sc), sc.tile_cells, sc.tile_tj, sc.tile_kmax, sc.tile_min);
-    return configure_tail(h, sc.tail_cells, 8);
+    return configure_tail(h, sc.tail_cells, sc.tail_cluster);
 }
 
 mg_status time_schedule(mg_handle* h, const Schedule& sc, double* ms) {
@@ -587,6 +598,15 @@ mg_status autotune(mg_handle* h) {
         Schedule sc = best;
         sc.tail_cells = 16384;
         CKS(consider(sc));
+        if (best.tail_cells && h->stencil == 7) {
+            // the shared-memory tail: twice the CTAs, then one level more
+            Schedule w = best;
+            w.tail_cluster = 16;
+            CKS(consider(w));
+            Schedule d = best;
+            d.tail_cells = 65536;
+            CKS(consider(d));
+        }
     }
     {   // one-pass sweeps on the large levels: two plane areas, then the
         // chunk depth, the smallest level swept in one pass and the tile width
@@ -885,7 +905,8 @@ mg_status setup_impl(const mg_grid_desc* g, const mg_opts* o, cudaStream_t strea
             i64 cells = kTailCells;
             int cluster = 8;
             if (const char* v = std::getenv("MG_TAIL_CELLS")) cells = std::atoll(v);
-            if (const char* v = std::getenv("MG_TAIL_CLUSTER")) cluster = std::max(1, std::min(8, std::atoi(v)));
+            if (const char* v = std::getenv("MG_TAIL_CLUSTER"))
+                cluster = std::max(1, std::min(kTailMaxCluster, std::atoi(v)));
             CKS(configure_tail(h, cells, cluster));
         }
     } else if (o->autotune == 1) {
@@ -1219,7 +1240,7 @@ mg_status vcycle(mg_handle* h, int prec, void* x0, const void* b0) {
     }
     if (h->tail_level > 0) {
         prof_begin(h, MG_PROF_TAIL);
-        CK(launch_tail(h->tail_dev, 1, h->tail_cluster, h->stencil, prec, h->stream));
+        CK(launch_tail(h->tail_dev, 1, h->tail_cluster, h->stencil, prec, h->stream, nullptr, h->tail_smem));
         prof_end(h, MG_PROF_TAIL, 1);
     } else {
         CK(launch_coarse_solve(h->binv, h->ncoarse, prec, h->L[nl - 1].r, h->L[nl - 1].e, h->stream));
@@ -1319,6 +1340,7 @@ mg_status mg_get_schedule(const mg_handle* h, mg_schedule* out) {
     out->blocks_per_sm = h->vb_cap;
     out->tail_level = h->tail_level;
     out->tail_cluster = h->tail_cluster;
+    out->tail_smem_bytes = h->tail_level > 0 ? (int)h->tail_smem : 0;
     out->one_pass_tiles = h->one_pass ? 1 : 0;
     out->tile_cells = h->sweep_cells;
     out->tile_planes = h->sweep_tj;

@@ -115,6 +115,7 @@ struct mg_handle {
     size_t plane_tasks_cap = 0;
     int tail_level = 0;               // first level of the single-launch coarse tail (0: none)
     int tail_cluster = 8;             // CTAs per tail cluster
+    size_t tail_smem = 0;             // >0: the tail's levels in shared memory (bytes per CTA)
     mgs::TailTask* tail_dev = nullptr;
     mgs::TailTask tail_host{};
     mgs::Plan* solo = nullptr;             // the batch-of-one plan of mg_solve

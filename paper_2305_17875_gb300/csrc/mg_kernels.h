@@ -111,6 +111,7 @@ cudaError_t launch_coarse_solve(const double* binv, int n, int prec, const void*
 // and back in one launch; one thread-block cluster of csize CTAs per task.
 constexpr int kMaxTail = 16;
 constexpr int kTailThreads = 512;
+constexpr int kTailMaxCluster = 16;   // above 8: a non-portable cluster size
 struct TailLevel {
     LevelView v;       // dims, factors to the next level, coefficients
     void* e;           // iterate / correction of the level
@@ -125,10 +126,39 @@ struct TailTask {
     const int* active; // per-shell flags of a batch (null: always run)
     int shell;
 };
+// The 7-point tail can keep every level in the cluster's shared memory: cell
+// c of level l on CTA c >> sh[l] at offset c & (2^sh[l] - 1), five arrays of
+// 2^sh[l] values per level (e, r, the lower-face components 0, 4, 8), level
+// l's first array at byte off[l].
+constexpr int kTailSmThreads = 1024;
+constexpr unsigned kTailSmMaxBytes = 200u * 1024u;
+struct TailSmLayout {
+    int sh[kMaxTail];
+    unsigned off[kMaxTail];
+    unsigned rd_off;     // the coarsest level's r in FP64 (ncoarse values), every CTA a copy
+    unsigned bytes;
+};
+__host__ __device__ inline void tail_sm_layout(const TailTask& tk, int csize, int vbytes, TailSmLayout& L) {
+    unsigned at = 0;
+    for (int l = 0; l < tk.nlev; ++l) {
+        const long long n = (long long)tk.lev[l].v.D.nr * tk.lev[l].v.D.nth * tk.lev[l].v.D.nph;
+        const long long per = (n + csize - 1) / csize;
+        int s = 5;   // at least 32 cells (an even chunk: a colour pass's items split on it)
+        while ((1LL << s) < per) ++s;
+        L.sh[l] = s;
+        L.off[l] = at;
+        at += (5u * (unsigned)vbytes) << s;
+    }
+    L.rd_off = at;
+    at += 8u * (unsigned)tk.ncoarse;
+    L.bytes = at;
+}
+// smem > 0: the shared-memory form with that much dynamic shared memory
+// (7-point only); 0: levels in global memory.
 cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s,
-                        unsigned long long* stamp = nullptr);
+                        unsigned long long* stamp = nullptr, size_t smem = 0);
 // Clusters of csize tail CTAs that can be co-resident (0: cluster launch unavailable).
-int tail_max_clusters(int csize, int stencil, int prec);
+int tail_max_clusters(int csize, int stencil, int prec, size_t smem = 0);
 
 // ---- batched level operations (batch.cu)
 enum {

@@ -471,6 +471,7 @@ void build_iteration(Plan* pl) {
     // bottom: coarse tails (one launch per stencil) and dense coarse solves
     for (int st : {7, 19}) {
         bool any = false;
+        size_t smem = 0;
         for (size_t s = 0; s < pl->hs.size(); ++s) {
             mg_handle* h = pl->hs[s];
             if (h->tail_level <= 0 || h->stencil != st) continue;
@@ -478,6 +479,10 @@ void build_iteration(Plan* pl) {
             tt.active = pl->d_active;
             tt.shell = (int)s;
             P.tails.push_back(tt);
+            // the shared-memory form when every shell's tail has it (the two
+            // forms give the same bits)
+            const size_t own = h->tail_cluster == lead(pl)->tail_cluster ? h->tail_smem : 0;
+            smem = !any ? own : (own && smem ? std::max(smem, own) : 0);
             any = true;
         }
         if (any) {
@@ -485,6 +490,7 @@ void build_iteration(Plan* pl) {
             L.tail_stencil = st;
             L.prof = MG_PROF_TAIL;
             L.prof_n = 1;
+            L.smem = smem;
         }
     }
     P.begin(BOP_COARSE);
@@ -585,7 +591,8 @@ mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const in
                 if (n == 0) first = (int)k;
                 ++n;
             }
-            CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream, st));
+            CK(launch_tail(pl->d_tails + first, n, h0->tail_cluster, L.tail_stencil, pl->prec, pl->stream, st,
+                           L.smem));
         } else if (L.op == BOP_SWEEP) {
             CK(launch_sweep(d_tasks + L.t0, L.nt, L.total, active, L.stencil, L.axi, pl->prec, L.smem, L.threads,
                             pl->stream, st));

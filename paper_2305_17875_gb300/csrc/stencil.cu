@@ -4,6 +4,9 @@
 // and the coarsest-level dense solve.
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
 #include "xline_smooth.cuh"
@@ -322,6 +325,292 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __rest
     stamp_end(stamp);
 }
 
+// ---- the 7-point coarse tail in the cluster's shared memory (layout in
+// tail_sm_layout).  Each CTA works on the cells it holds; a neighbour held by
+// another CTA is read through the cluster's shared-memory window.  Per cell
+// the arithmetic is that of k_tail (Cell7, the same restriction,
+// prolongation and coarse rows), so both forms give the same bits.
+
+// One level array spread over the cluster, read and written through the
+// cluster's shared-memory window (32-bit addresses; a CTA's own cells map to
+// its own shared memory).
+template <typename T>
+struct SmArr {
+    T* p;             // this CTA's chunk
+    unsigned base;    // the same as a shared-memory address
+    int sh;
+    __device__ __forceinline__ unsigned at(int c) const {
+        const unsigned a = base + (unsigned)(c & ((1 << sh) - 1)) * (unsigned)sizeof(T);
+        unsigned r;
+        asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"((unsigned)(c >> sh)));
+        return r;
+    }
+    __device__ __forceinline__ T operator()(int c) const {
+        T v;
+        if constexpr (sizeof(T) == 4)
+            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(at(c)) : "memory");
+        else
+            asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(at(c)) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ void st(int c, T v) const {
+        if constexpr (sizeof(T) == 4)
+            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(at(c)), "f"(v) : "memory");
+        else
+            asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(at(c)), "d"(v) : "memory");
+    }
+};
+// The three 7-point components of a level, as the global readers give them.
+template <typename T>
+struct SmCoef7 {
+    SmArr<T> g0, g4, g8;
+    __device__ __forceinline__ T operator()(int a, i64 idx) const {
+        return a == 0 ? g0((int)idx) : (a == 4 ? g4((int)idx) : g8((int)idx));
+    }
+};
+template <typename T>
+struct SmLevel {
+    SmArr<T> e, r;
+    SmCoef7<T> cf;
+    int lo, hi;   // the cells this CTA holds
+};
+template <typename T>
+__device__ __forceinline__ SmLevel<T> sm_level(unsigned char* dyn, const TailSmLayout& L, const Dims& D, int l,
+                                               int rank) {
+    const int s = L.sh[l];
+    T* b = reinterpret_cast<T*>(dyn + L.off[l]);
+    const int n = 1 << s;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(b);
+    const unsigned w = (unsigned)(n * sizeof(T));
+    SmLevel<T> v;
+    v.e = SmArr<T>{b, a, s};
+    v.r = SmArr<T>{b + n, a + w, s};
+    v.cf = SmCoef7<T>{{b + 2 * n, a + 2 * w, s}, {b + 3 * n, a + 3 * w, s}, {b + 4 * n, a + 4 * w, s}};
+    v.lo = rank << s;
+    v.hi = min((rank + 1) << s, (int)D.n());
+    return v;
+}
+
+// One colour of the pass (gs_colour_range, 7 points): item t is cell 2t or
+// 2t + 1, so the items of the cells a CTA holds are t in [lo / 2, hi / 2).
+template <typename T>
+__device__ __forceinline__ void sm_gs(const SmLevel<T>& V, const Dims D, int colour) {
+    const int work = D.nr * D.nth * (D.nph >> 1);
+    const int t1 = min(V.hi >> 1, work);
+    for (int t = (V.lo >> 1) + threadIdx.x; t < t1; t += blockDim.x) {
+        int kk, i, j;
+        decode_half(D, t, kk, i, j);
+        Cell7<T> q;
+        q.load(V.cf, D, j, i, 2 * kk + ((colour + i + j) & 1), V.e);
+        V.e.st(q.c, q.gs(V.r(q.c)));
+    }
+}
+
+// Residual restricted into the coarse cells this CTA holds (restrict_range,
+// 7 points), their correction zeroed.
+template <typename T>
+__device__ __forceinline__ void sm_restrict(const SmLevel<T>& F, const Dims D, const SmLevel<T>& C,
+                                            const Dims Dc, int cz, int ce, int cx) {
+    for (int t = C.lo + threadIdx.x; t < C.hi; t += blockDim.x) {
+        const C3 P = decode(Dc, t);
+        T s = 0;
+        for (int dj = 0; dj < ce; ++dj)
+            for (int di = 0; di < cz; ++di)
+                for (int dk = 0; dk < cx; ++dk) {
+                    Cell7<T> q;
+                    q.load(F.cf, D, ce * P.j + dj, cz * P.i + di, cx * P.k + dk, F.e);
+                    s += q.resid(F.r(q.c));
+                }
+        C.r.st(t, s);
+        C.e.st(t, (T)0);
+    }
+}
+
+// x += P ec on the fine cells this CTA holds (prolong_range).
+template <typename T>
+__device__ __forceinline__ void sm_prolong(const SmLevel<T>& F, const Dims D, const SmLevel<T>& C,
+                                           const Dims Dc, int cz, int ce, int cx) {
+    for (int c = F.lo + threadIdx.x; c < F.hi; c += blockDim.x) {
+        T* xc = F.e.p + (c - F.lo);   // this CTA's own cell
+        if (D.cut) {
+            // prolong_cut_cell reads through addresses: offsets from a base
+            const T* base = C.e.p;
+            *xc = *xc + prolong_cut_cell<T>(Dc, cz, ce, cx, base, decode(D, c),
+                                            [&](const T* p) { return C.e((int)(p - base)); });
+            continue;
+        }
+        const C3 f = decode(D, c);
+        int ij[2], ii[2], ik[2];
+        float wj[2], wi[2], wk[2];
+        lin1d(f.j, ce, Dc.nr, false, ij, wj);
+        lin1d(f.i, cz, Dc.nth, false, ii, wi);
+        lin1d(f.k, cx, Dc.nph, true, ik, wk);
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a >= ce) break;
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb) {
+                if (bb >= cz) break;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (e >= cx) break;
+                    s = fma((T)wj[a] * (T)wi[bb] * (T)wk[e], C.e(cidx(Dc, ij[a], ii[bb], ik[e])), s);
+                }
+            }
+        }
+        *xc = *xc + s;
+    }
+}
+
+// e = Binv r on the coarsest rows this CTA holds, one warp per row
+// (coarse_range).
+// e = Binv r on the coarsest rows this CTA holds, one warp per row
+// (coarse_range's sums: each lane over m = lane, lane + 32, ..., then the
+// shuffle tree).  rd: the coarsest r converted to FP64 once, in this CTA's
+// shared memory; the lane's loads of a block of eight terms go out together.
+template <typename T>
+__device__ __forceinline__ void sm_coarse(const double* binv, const double* rd, int n, const SmLevel<T>& V) {
+    const int lane = threadIdx.x & 31;
+    const int hi = min(V.hi, n);
+    for (int row = V.lo + (int)(threadIdx.x >> 5); row < hi; row += (int)(blockDim.x >> 5)) {
+        const double* brow = binv + (i64)row * n;
+        double s = 0.0;
+        for (int m0 = lane; m0 < n; m0 += 32 * 8) {
+            double bv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) bv[u] = m0 + 32 * u < n ? __ldg(brow + m0 + 32 * u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (m0 + 32 * u < n) s += bv[u] * rd[m0 + 32 * u];
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) V.e.st(row, (T)s);
+    }
+}
+
+// Threads of a shared-memory tail CTA (FP64 halves them for registers).
+template <typename T>
+constexpr int tail_sm_threads() {
+    return sizeof(T) == 8 ? kTailSmThreads / 2 : kTailSmThreads;
+}
+
+// Asynchronous 4- or 8-byte copy global -> this CTA's shared memory.
+template <typename T>
+__device__ __forceinline__ void cp_async_val(T* sdst, const T* gsrc) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// count values from global to this CTA's shared memory, spread over the
+// CTA's threads: 16-byte copies when both ends are 16-byte aligned, the rest
+// one value at a time.
+template <typename T>
+__device__ __forceinline__ void stage_span(T* sdst, const T* gsrc, int count) {
+    constexpr int V = 16 / (int)sizeof(T);
+    int done = 0;
+    if (((reinterpret_cast<uintptr_t>(gsrc) | reinterpret_cast<uintptr_t>(sdst)) & 15) == 0) {
+        const int nv = count / V;
+        for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(sdst + q * V);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc + q * V) : "memory");
+        }
+        done = nv * V;
+    }
+    for (int q = done + (int)threadIdx.x; q < count; q += blockDim.x) cp_async_val<T>(sdst + q, gsrc + q);
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(tail_sm_threads<T>(), 1) k_tail_sm(const TailTask* __restrict__ tasks, int csize,
+                                                                     unsigned long long* stamp) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ TailSmLayout lay;
+    cg::cluster_group cl = cg::this_cluster();
+    const TailTask& tk = tasks[blockIdx.x / csize];
+    stamp_start(stamp);
+    if (tk.active && !tk.active[tk.shell]) {   // uniform over the cluster
+        stamp_end(stamp);
+        return;
+    }
+    const int rank = (int)cl.block_rank();
+    if (threadIdx.x == 0) tail_sm_layout(tk, csize, (int)sizeof(T), lay);
+    __syncthreads();
+    const int nl = tk.nlev;
+    // stage (copies all in flight at once): the components of every level, e
+    // and r of the first, this CTA's rows of Binv
+    for (int l = 0; l < nl; ++l) {
+        const auto& cf = CoefOf<P>::get(tk.lev[l].v);
+        const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[l].v.D, l, rank);
+        const int cnt = V.hi - V.lo;
+        if (cnt <= 0) continue;
+        if constexpr (P == PREC16) {   // FP16 storage: converted as the global readers do
+            for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) {
+                const int o = c - V.lo;
+                V.cf.g0.p[o] = (T)cf(0, c);
+                V.cf.g4.p[o] = (T)cf(4, c);
+                V.cf.g8.p[o] = (T)cf(8, c);
+            }
+        } else {
+            stage_span<T>(V.cf.g0.p, cf.g[0] + V.lo, cnt);
+            stage_span<T>(V.cf.g4.p, cf.g[4] + V.lo, cnt);
+            stage_span<T>(V.cf.g8.p, cf.g[8] + V.lo, cnt);
+        }
+        if (l == 0) {
+            stage_span<T>(V.e.p, (const T*)tk.lev[0].e + V.lo, cnt);
+            stage_span<T>(V.r.p, (const T*)tk.lev[0].r + V.lo, cnt);
+        }
+    }
+    {   // this CTA's rows of Binv toward L2 for the coarse phase
+        const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[nl - 1].v.D, nl - 1, rank);
+        const int n = tk.ncoarse;
+        const i64 b0 = (i64)V.lo * n, b1 = (i64)min(V.hi, n) * n;
+        for (i64 q = b0 + 16 * (i64)threadIdx.x; q < b1; q += 16 * (i64)blockDim.x)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(tk.binv + q));
+    }
+    cp_async_wait_all();
+    cl.sync();
+    for (int l = 0; l < nl - 1; ++l) {
+        const LevelView& A = tk.lev[l].v;
+        const SmLevel<T> F = sm_level<T>(dyn, lay, A.D, l, rank);
+        for (int sw = 0; sw < tk.nu1; ++sw)
+            for (int c = 0; c < 2; ++c) {
+                sm_gs<T>(F, A.D, c);
+                cl.sync();
+            }
+        const SmLevel<T> C = sm_level<T>(dyn, lay, tk.lev[l + 1].v.D, l + 1, rank);
+        sm_restrict<T>(F, A.D, C, tk.lev[l + 1].v.D, A.cz, A.ce, A.cx);
+        cl.sync();
+    }
+    {
+        const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[nl - 1].v.D, nl - 1, rank);
+        double* rd = reinterpret_cast<double*>(dyn + lay.rd_off);
+        for (int m = threadIdx.x; m < tk.ncoarse; m += blockDim.x) rd[m] = (double)V.r(m);
+        __syncthreads();
+        sm_coarse<T>(tk.binv, rd, tk.ncoarse, V);
+    }
+    cl.sync();
+    for (int l = nl - 2; l >= 0; --l) {
+        const LevelView& A = tk.lev[l].v;
+        const SmLevel<T> F = sm_level<T>(dyn, lay, A.D, l, rank);
+        const SmLevel<T> C = sm_level<T>(dyn, lay, tk.lev[l + 1].v.D, l + 1, rank);
+        sm_prolong<T>(F, A.D, C, tk.lev[l + 1].v.D, A.cz, A.ce, A.cx);
+        cl.sync();
+        for (int sw = 0; sw < tk.nu2; ++sw)
+            for (int c = 0; c < 2; ++c) {
+                sm_gs<T>(F, A.D, c);
+                cl.sync();
+            }
+    }
+    // the top level's correction back to global memory
+    const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[0].v.D, 0, rank);
+    for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) ((T*)tk.lev[0].e)[c] = V.e.p[c - V.lo];
+    stamp_end(stamp);
+}
+
 }  // namespace
 
 // Dispatch on (precision, stencil): T = value type, cf = coefficient reader.
@@ -423,64 +712,108 @@ cudaError_t launch_coarse_solve(const double* binv, int n, int prec, const void*
     return cudaGetLastError();
 }
 
+// The tail kernel of (stencil, precision); the shared-memory form when smem > 0.
 template <int S, typename T, int P>
-static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cudaStream_t s,
-                               unsigned long long* stamp) {
-    cudaLaunchConfig_t cfg = {};
+static void* tail_kernel(size_t smem) {
+    if (S == 7 && smem > 0) return reinterpret_cast<void*>(k_tail_sm<T, P>);
+    return reinterpret_cast<void*>(k_tail<S, T, P>);
+}
+
+static void tail_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int ntasks, int csize, size_t smem,
+                        int sm_threads, cudaStream_t s) {
+    cfg = {};
     cfg.gridDim = dim3(ntasks * csize, 1, 1);
-    cfg.blockDim = dim3(kTailThreads, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.blockDim = dim3(smem > 0 ? sm_threads : kTailThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = csize;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tail<S, T, P>, tasks, csize, stamp);
+}
+
+// Kernel attributes, set once per kernel: the shared-memory form's dynamic
+// shared memory limit; clusters above the portable 8 CTAs.
+static cudaError_t tail_attrs(const void* k, size_t smem, int csize) {
+    static std::mutex mu;
+    static std::map<const void*, size_t> smem_done;
+    static std::map<const void*, bool> wide_done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > smem_done[k]) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmMaxBytes);
+        if (e != cudaSuccess) return e;
+        smem_done[k] = kTailSmMaxBytes;
+    }
+    if (csize > 8 && !wide_done[k]) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        wide_done[k] = true;
+    }
+    return cudaSuccess;
 }
 
 template <int S, typename T, int P>
-static int tail_clusters(int csize) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csize, 1, 1);
-    cfg.blockDim = dim3(kTailThreads, 1, 1);
+static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cudaStream_t s,
+                               unsigned long long* stamp, size_t smem) {
+    if (S != 7) smem = 0;
+    if (smem > kTailSmMaxBytes) return cudaErrorInvalidValue;
+    if (csize < 1 || csize > kTailMaxCluster) return cudaErrorInvalidValue;
+    const void* k = tail_kernel<S, T, P>(smem);
+    const cudaError_t ea = tail_attrs(k, smem, csize);
+    if (ea != cudaSuccess) return ea;
+    cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = csize;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    tail_config(cfg, attr, ntasks, csize, smem, tail_sm_threads<T>(), s);
+    void* args[] = {(void*)&tasks, (void*)&csize, (void*)&stamp};
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+template <int S, typename T, int P>
+static int tail_clusters(int csize, size_t smem) {
+    if (S != 7) smem = 0;
+    if (smem > kTailSmMaxBytes) return 0;
+    if (csize < 1 || csize > kTailMaxCluster) return 0;
+    const void* k = tail_kernel<S, T, P>(smem);
+    if (tail_attrs(k, smem, csize) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    tail_config(cfg, attr, 1, csize, smem, tail_sm_threads<T>(), nullptr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_tail<S, T, P>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-int tail_max_clusters(int csize, int stencil, int prec) {
+int tail_max_clusters(int csize, int stencil, int prec, size_t smem) {
     if (prec == PREC64)
-        return stencil == 19 ? tail_clusters<19, double, PREC64>(csize) : tail_clusters<7, double, PREC64>(csize);
+        return stencil == 19 ? tail_clusters<19, double, PREC64>(csize, smem)
+                             : tail_clusters<7, double, PREC64>(csize, smem);
     if (prec == PREC32)
-        return stencil == 19 ? tail_clusters<19, float, PREC32>(csize) : tail_clusters<7, float, PREC32>(csize);
-    return stencil == 19 ? tail_clusters<19, float, PREC16>(csize) : tail_clusters<7, float, PREC16>(csize);
+        return stencil == 19 ? tail_clusters<19, float, PREC32>(csize, smem)
+                             : tail_clusters<7, float, PREC32>(csize, smem);
+    return stencil == 19 ? tail_clusters<19, float, PREC16>(csize, smem) : tail_clusters<7, float, PREC16>(csize, smem);
 }
 
 cudaError_t launch_tail(const TailTask* tasks, int ntasks, int csize, int stencil, int prec, cudaStream_t s,
-                        unsigned long long* stamp) {
+                        unsigned long long* stamp, size_t smem) {
     cudaError_t e;
     if (prec == PREC64)
-        e = stencil == 19 ? tail_launch<19, double, PREC64>(tasks, ntasks, csize, s, stamp)
-                          : tail_launch<7, double, PREC64>(tasks, ntasks, csize, s, stamp);
+        e = stencil == 19 ? tail_launch<19, double, PREC64>(tasks, ntasks, csize, s, stamp, smem)
+                          : tail_launch<7, double, PREC64>(tasks, ntasks, csize, s, stamp, smem);
     else if (prec == PREC32)
-        e = stencil == 19 ? tail_launch<19, float, PREC32>(tasks, ntasks, csize, s, stamp)
-                          : tail_launch<7, float, PREC32>(tasks, ntasks, csize, s, stamp);
+        e = stencil == 19 ? tail_launch<19, float, PREC32>(tasks, ntasks, csize, s, stamp, smem)
+                          : tail_launch<7, float, PREC32>(tasks, ntasks, csize, s, stamp, smem);
     else
-        e = stencil == 19 ? tail_launch<19, float, PREC16>(tasks, ntasks, csize, s, stamp)
-                          : tail_launch<7, float, PREC16>(tasks, ntasks, csize, s, stamp);
+        e = stencil == 19 ? tail_launch<19, float, PREC16>(tasks, ntasks, csize, s, stamp, smem)
+                          : tail_launch<7, float, PREC16>(tasks, ntasks, csize, s, stamp, smem);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -300,11 +300,15 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
     for name, env, tune in [("default", {}, 0), ("tuned", {}, 1), ("tuned_again", {}, 1), ("cached", {}, 2),
                             ("tail", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192"}, 1),
                             ("tail_big", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4"}, 1),
+                            ("tail_global", {"MG_TAIL": "1", "MG_TAIL_CELLS": "8192", "MG_TAIL_GLOBAL": "1"}, 1),
+                            ("tail_big_global", {"MG_TAIL": "1", "MG_TAIL_CELLS": "65536", "MG_TAIL_CLUSTER": "4",
+                                                 "MG_TAIL_GLOBAL": "1"}, 1),
                             ("fused", {"MG_FUSED_RB": "1"}, 1),
                             ("fused_narrow", {"MG_FUSED_RB": "1", "MG_TILE": "256,3,32"}, 1),
                             ("fused_tail", {"MG_FUSED_RB": "1", "MG_TILE": "1024,2,256", "MG_TAIL": "1"}, 1),
                             ("no_graph", {"MG_NO_GRAPH": "1"}, 0)]:
-        for k in ("MG_TAIL", "MG_TAIL_CELLS", "MG_TAIL_CLUSTER", "MG_FUSED_RB", "MG_NO_GRAPH", "MG_TILE"):
+        for k in ("MG_TAIL", "MG_TAIL_CELLS", "MG_TAIL_CLUSTER", "MG_FUSED_RB", "MG_NO_GRAPH", "MG_TILE",
+                  "MG_TAIL_GLOBAL"):
             monkeypatch.delenv(k, raising=False)
         for k, v in env.items():
             monkeypatch.setenv(k, v)
@@ -319,6 +323,12 @@ def test_schedules_give_bitwise_identical_solves(lib, wl, scale, prec, monkeypat
             assert sc["source"] == 0 and sc["blocks_per_sm"] == 16 and sc["tail_level"] == 0
         if name in ("tuned_again", "cached"):
             assert sc["source"] == 2           # same hierarchy shape: from the process cache
+        if name.endswith("global"):
+            assert sc["tail_smem_bytes"] == 0, name
+        elif name == "tail" and stencil_of(w["grid"]) == 7:
+            # a small 7-point tail lives in the cluster's shared memory (the
+            # big one falls back to global memory where it does not fit)
+            assert sc["tail_level"] > 0 and sc["tail_smem_bytes"] > 0, name
         xd = torch.zeros_like(fd)
         rep = lib.mg_solve(h, fd, xd, tol=1e-10)
         out[name] = (to_np(xd), rep["iters"])
