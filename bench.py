@@ -382,6 +382,13 @@ def profile_solves(mgs, h, fd, xd, steps, flush, torch, stencil, prec, N, n_next
         if n:
             levels[l] = {"ms_per_solve": t / steps, "launches_per_solve": n / steps}
     gap_ms, _ = mgs.mg_profile_read(h, mgs.PROF_GAPS)
+    # cross-check of the clocks: the same solves with CUDA events around
+    # every launch (eager launches, host loop: the events break the launches'
+    # overlap, so these spans include some launch latency)
+    mgs.mg_profile_enable(h, 2)
+    ev_steps = max(2, min(steps, 3))
+    ev_ms, _ = time_solves(mgs, h, fd, xd, ev_steps, flush, torch)
+    ev_slots = {name: mgs.mg_profile_read(h, slot) for name, slot in SLOT_NAMES}
     mgs.mg_profile_enable(h, False)
     kernels = {}
     for k, (t, n) in slots.items():
@@ -395,11 +402,22 @@ def profile_solves(mgs, h, fd, xd, steps, flush, torch, stencil, prec, N, n_next
     # device time no kernel covers, within a program run (an outer
     # iteration, the prologue, the epilogue): launch latency between kernels
     gaps = gap_ms / steps
+    events = {k: {"ms_per_solve": t / ev_steps, "avg_ms": t / n if n else None} for k, (t, n) in ev_slots.items()}
     return {"profiled_ms_per_solve": live, "attributed_ms_per_solve": attributed,
             "launch_gaps_ms_per_solve": gaps,
+            "events_ms_per_solve": statistics.mean(ev_ms), "events": events,
             # the rest: between program runs (stop tests, copies, host calls)
             "between_programs_ms_per_solve": live - attributed - gaps,
             "kernels": kernels, "levels": levels}, slots
+
+
+def add_event_check(roof, prof, name):
+    """The kernel's mean launch time from the CUDA-event pass beside the
+    clocks' (same bytes, the events' duration)."""
+    ev = prof["events"].get(name, {}).get("avg_ms")
+    if ev:
+        roof["avg_launch_ms_events"] = ev
+        roof["frac_events"] = roof["algorithmic_bytes_per_launch"] / (ev * 1e-3) / 1e9 / roof["peak"]
 
 
 def roofline_of(name, slots, steps, stencil, prec, N, n_next, smoother, axi, one_pass, traffic):
@@ -467,6 +485,7 @@ def single_leg(args, mgs, torch, workload, scale, prec, smoother, steps, warmup,
     # the kernel's share of all device time of the profiled solves (every
     # slot and every coarse level): comparable with an ncu launch list
     roof["share_of_step"] = prof["kernels"][name]["ms_per_solve"] / max(prof["attributed_ms_per_solve"], 1e-30)
+    add_event_check(roof, prof, name)
     prof["attributed_over_headline"] = prof["attributed_ms_per_solve"] / statistics.mean(ms)
     leg = {"workload": workload if scale == 1 else f"{workload}/{scale}", "grid": f"{g['nr']}x{g['nth']}x{g['nph']}",
            "value": N / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
@@ -581,6 +600,7 @@ def run_ours(args, rank, world, local_rank):
                        ncu_traffic(args.workload if args.smoother == "gs" else f"{args.workload}/{args.smoother}",
                                    args.precision, name, one_pass))
     roof["share_of_step"] = prof["kernels"][name]["ms_per_solve"] / max(prof["attributed_ms_per_solve"], 1e-30)
+    add_event_check(roof, prof, name)
     prof["attributed_over_headline"] = prof["attributed_ms_per_solve"] / ms_step
 
     # end to end through the public host-buffer call (pinned host memory)

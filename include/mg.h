@@ -445,26 +445,33 @@ mg_status mg_adi_substep(mg_handle* h, double kappa, int nfields, const mg_walls
 size_t mg_device_bytes_in_use(int device);
 
 /* ---------------------------------------------------------------------------
- * Kernel timing.  While enabled, every kernel a solve launches records its
- * own clock on the GPU's global nanosecond timer: the earliest start of its
- * thread blocks (after they wait for the previous launch) and the latest end.
- * Each launch's span is added to its slot, so the slots hold device time of
- * the kernels proper; launch gaps and host waits between outer iterations
- * are not in any slot.  The launches run as in an untimed solve (the clocks
- * add a reset and a read-back per outer iteration).  Slots: 0 = fine-level smoothing
- * launches, 1 = outer FP64 residual, 2 = fine-level residual + restriction,
- * 3 = fine-level prolongation + correction, 4 = outer update, 5 = the
- * single-launch coarse tail of the V-cycle, 6 = everything else (zeroing,
- * reductions, the coarsest solve, copies), MG_PROF_LEVEL_BASE + l = the
+ * Kernel timing.  With mg_profile_enable(h, 1) every kernel a solve launches
+ * records its own clock on the GPU's global nanosecond timer: the earliest
+ * start of its thread blocks (after they wait for the previous launch) and
+ * the latest end.  Each launch's span is added to its slot, so the slots hold
+ * device time of the kernels proper; the launches run as in an untimed solve
+ * (the clocks add a reset, and per outer iteration an accumulation or a
+ * read-back).  With mode 2 every launch is bracketed by CUDA events instead,
+ * the launches run eagerly and the outer loop on the host (a slower solve:
+ * event records between launches; a cross-check of the clocks).  Slots:
+ * 0 = fine-level smoothing launches, 1 = outer FP64 residual, 2 = fine-level
+ * residual + restriction, 3 = fine-level prolongation + correction, 4 = outer
+ * update, 5 = the single-launch coarse tail of the V-cycle, 6 = everything
+ * else (zeroing, reductions, the coarsest solve, copies; the device loop's
+ * stop tests and the clock bookkeeping are in no slot), 7 = with clocks, the
+ * time inside each program
+ * run (prologue, outer iteration, epilogue) between its first start and last
+ * end that no launch covers (launch gaps), MG_PROF_LEVEL_BASE + l = the
  * smoothing, restriction and prolongation launches of level l (1 <= l < 16;
- * deeper levels share the last slot).  The slots together cover the whole
- * outer iteration.  Stand-alone component calls (mg_smooth, mg_vcycle) time
- * slots 0, 2, 3 and 5 only, with CUDA events around their launches.
+ * deeper levels share the last slot).  Stand-alone component calls
+ * (mg_smooth, mg_vcycle) time slots 0, 2, 3 and 5 only, with CUDA events
+ * around their launches in either mode.
  * ------------------------------------------------------------------------- */
 enum { MG_PROF_SMOOTH0 = 0, MG_PROF_RESIDUAL = 1, MG_PROF_RESTRICT0 = 2, MG_PROF_PROLONG0 = 3,
        MG_PROF_UPDATE = 4, MG_PROF_TAIL = 5, MG_PROF_OTHER = 6, MG_PROF_GAPS = 7, MG_PROF_LEVEL_BASE = 8,
        MG_PROF_SLOTS = 24 };
-/* Enable (on != 0) or disable timing; either way the accumulators reset. */
+/* Enable (on = 1 clocks, 2 events) or disable (0) timing; either way the
+ * accumulators reset. */
 mg_status mg_profile_enable(mg_handle* h, int on);
 /* Accumulated device milliseconds and launch count of one slot. */
 mg_status mg_profile_read(mg_handle* h, int slot, double* ms, long long* launches);

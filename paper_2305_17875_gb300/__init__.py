@@ -429,8 +429,10 @@ PROF_SMOOTH0, PROF_RESIDUAL, PROF_RESTRICT0, PROF_PROLONG0, PROF_UPDATE, PROF_TA
 PROF_LEVEL_BASE, PROF_SLOTS = 8, 24   # slot PROF_LEVEL_BASE + l: level l's operations (1 <= l < 16)
 
 
-def mg_profile_enable(h: Handle, on: bool = True):
-    _check(_lib.mg_profile_enable(h.ptr, int(bool(on))), "mg_profile_enable")
+def mg_profile_enable(h: Handle, on=True):
+    """on: True / 1 = launch clocks, 2 = CUDA events around eager launches, False / 0 = off."""
+    mode = int(on) if not isinstance(on, bool) else int(on)
+    _check(_lib.mg_profile_enable(h.ptr, mode), "mg_profile_enable")
 
 
 def mg_profile_read(h: Handle, slot: int):

@@ -1559,10 +1559,11 @@ mg_status mg_solve_host(mg_handle* h, const double* f_host, double* x_host, doub
 }
 
 mg_status mg_profile_enable(mg_handle* h, int on) {
-    if (!h) return MG_EINVAL;
+    if (!h || on < 0 || on > 2) return MG_EINVAL;
     CK(cudaStreamSynchronize(h->stream));
     prof_collect(h);
     h->prof_on = on != 0;
+    h->prof_events = on == 2;
     for (int s = 0; s < MG_PROF_SLOTS; ++s) {
         h->prof_ms[s] = 0.0;
         h->prof_n[s] = 0;

@@ -91,6 +91,7 @@ struct mg_handle {
     double* wallG[4] = {};            // G_dd on the wall planes (implicit sweeps, on first use)
     double* adi_w = nullptr;          // line-solve work of the implicit sweeps (2 N doubles)
     bool prof_on = false;
+    bool prof_events = false;         // mode 2: CUDA events around eager launches
     double prof_ms[MG_PROF_SLOTS] = {};
     long long prof_n[MG_PROF_SLOTS] = {};
     cudaEvent_t prof_open[MG_PROF_SLOTS] = {};

@@ -159,6 +159,9 @@ struct Plan {
 namespace {
 
 mg_handle* lead(Plan* p) { return p->hs[0]; }
+// Kernel timing by launch clocks (mg_profile_enable 1); mode 2 brackets every
+// launch with CUDA events instead, run eagerly.
+bool clocks(const mg_handle* h) { return h->prof_on && !h->prof_events; }
 
 BTask task_of(const mg_handle* h, int level) {
     BTask t{};
@@ -583,6 +586,8 @@ mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const in
         const Launch& L = P.launches[i];
         if (!L.tail_stencil && L.total == 0) continue;   // launches nothing
         unsigned long long* st = d_st ? d_st + 2 * i : nullptr;
+        const int slot = slot_of(L);
+        if (h0->prof_events) prof_begin(h0, slot);
         if (L.tail_stencil) {
             int first = 0, n = 0;
             for (size_t k = 0; k < P.tails.size(); ++k) {
@@ -600,6 +605,7 @@ mg_status run_program(Plan* pl, const Program& P, const BTask* d_tasks, const in
             CK(launch_batch(d_tasks + L.t0, L.nt, L.total, active, L.op, L.colour, L.stencil, pl->prec,
                             pl->stream, st));
         }
+        if (h0->prof_events) prof_end(h0, slot, L.prof >= 0 ? L.prof_n : 1);
         h0->launches += 1;
     }
     return MG_OK;
@@ -687,7 +693,7 @@ mg_status iter_stamps(Plan* pl) {
 
 // A prologue or epilogue (not captured), clocked while profiling.
 mg_status run_call(Plan* pl, const Program& P) {
-    if (!lead(pl)->prof_on) return run_program(pl, P, pl->d_call, nullptr);
+    if (!clocks(lead(pl))) return run_program(pl, P, pl->d_call, nullptr);
     CKS(stamp_buffers(P.launches.size(), &pl->d_stamp_call, &pl->h_stamp_call, &pl->stamp_call_cap));
     return run_clocked(pl, P, pl->d_call, nullptr, pl->d_stamp_call, pl->h_stamp_call);
 }
@@ -698,7 +704,7 @@ mg_status build_graph(Plan* pl) {
         cudaGraphExecDestroy(pl->gexec);
         pl->gexec = nullptr;
     }
-    const bool prof = h0->prof_on;
+    const bool prof = clocks(h0);
     if (prof) CKS(iter_stamps(pl));
     const long long before = h0->launches;
     CK(cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal));
@@ -924,7 +930,7 @@ mg_status plan_start(Plan* pl, const double* const* f, double* const* x, const d
     CKS(upload_call(pl, pro));
     CKS(run_call(pl, pro));
     CKS(read_fin(pl));
-    if (pl->hs[0]->prof_on) stamps_collect(pl->hs[0], pro, pl->h_stamp_call);
+    if (clocks(pl->hs[0])) stamps_collect(pl->hs[0], pro, pl->h_stamp_call);
     for (int i = 0; i < n; ++i) {
         mg_handle* h = pl->hs[i];
         SolveState& q = S[i];
@@ -988,7 +994,7 @@ mg_status plan_iterate(Plan* pl, SolveState* S, bool use_graph) {
     const int n = (int)pl->hs.size();
     mg_handle* h0 = lead(pl);
     CK(cudaMemcpyAsync(pl->d_active, pl->h_active, sizeof(int) * n, cudaMemcpyHostToDevice, pl->stream));
-    const bool prof = h0->prof_on;
+    const bool prof = clocks(h0);
     if (use_graph) {
         if (!pl->gexec || pl->graph_prof != prof) CKS(build_graph(pl));
         CK(cudaGraphLaunch(pl->gexec, pl->stream));
@@ -1079,7 +1085,7 @@ mg_status plan_finish(Plan* pl, double* const* x) {
     }
     CKS(upload_call(pl, epi));
     CKS(run_call(pl, epi));
-    if (lead(pl)->prof_on) {
+    if (clocks(lead(pl))) {
         CK(cudaStreamSynchronize(pl->stream));
         stamps_collect(lead(pl), epi, pl->h_stamp_call);
     }
@@ -1098,7 +1104,7 @@ bool build_loop(Plan* pl) {
         cudaGraphExecDestroy(pl->lexec);
         pl->lexec = nullptr;
     }
-    const bool prof = h0->prof_on;
+    const bool prof = clocks(h0);
     const int nl = (int)pl->iter.launches.size();
     if (prof && (iter_stamps(pl) != MG_OK ||
                  stamp_buffers((size_t)nl, &pl->d_acc, &pl->h_acc, &pl->acc_cap) != MG_OK)) {
@@ -1160,7 +1166,7 @@ bool build_loop(Plan* pl) {
 mg_status plan_loop(Plan* pl, SolveState* S, bool* unavailable) {
     const int n = (int)pl->hs.size();
     mg_handle* h0 = lead(pl);
-    const bool prof = h0->prof_on;
+    const bool prof = clocks(h0);
     *unavailable = false;
     if (!pl->lexec || pl->loop_prof != prof) {
         if (!build_loop(pl)) {
@@ -1249,13 +1255,14 @@ mg_status plan_solve(Plan* pl, const double* const* f, double* const* x, const d
     std::vector<SolveState> S(n);
     CKS(plan_start(pl, f, x, tol, S.data()));
     int active = plan_check(pl, S.data());
-    if (active > 0 && h0->use_graph && !pl->loop_failed && !host_loop_forced()) {
+    const bool graphs = h0->use_graph && !h0->prof_events;
+    if (active > 0 && graphs && !pl->loop_failed && !host_loop_forced()) {
         bool unavailable = false;
         CKS(plan_loop(pl, S.data(), &unavailable));
         if (!unavailable) active = 0;
     }
     while (active > 0) {
-        CKS(plan_iterate(pl, S.data(), h0->use_graph));
+        CKS(plan_iterate(pl, S.data(), graphs));
         active = plan_check(pl, S.data());
     }
     CKS(plan_finish(pl, x));

@@ -369,7 +369,7 @@ def test_solve_warm_start_and_host_buffers(lib):
     np.testing.assert_allclose(xh.ravel(), to_np(xd), atol=1e-9 * np.abs(xh).max())
 
 
-@pytest.mark.parametrize("loop", ["device", "host"])
+@pytest.mark.parametrize("loop", ["device", "host", "events"])
 @pytest.mark.parametrize("wl,scale,prec", [("single_sphere_128", 4, 1), ("single_oblate_256", 8, 2)])
 def test_kernel_clocks_cover_every_launch_and_change_nothing(lib, wl, scale, prec, loop, monkeypatch):
     """Kernel timing on: the solve's iterates are bitwise those of an untimed
@@ -378,7 +378,9 @@ def test_kernel_clocks_cover_every_launch_and_change_nothing(lib, wl, scale, pre
     more than the solve's wall time.  Bookkeeping kernels: with the loop on
     the host, a clock reset per outer iteration and one each for the
     prologue and the epilogue; with the loop on the device, a stop test and a
-    clock accumulation per iteration, and three resets."""
+    clock accumulation per iteration, and three resets.  "events": CUDA
+    events around eager launches instead of clocks (no bookkeeping kernels,
+    no gap slot)."""
     import time
     torch, dev = torch_dev()
     if loop == "host":
@@ -390,7 +392,8 @@ def test_kernel_clocks_cover_every_launch_and_change_nothing(lib, wl, scale, pre
     fd = to_dev(w["f"], torch.float64)
     x0 = torch.zeros_like(fd)
     r0 = lib.mg_solve(h, fd, x0, tol=1e-10)
-    lib.mg_profile_enable(h, True)
+    mode = 2 if loop == "events" else 1
+    lib.mg_profile_enable(h, mode)
     for rep in range(2):             # the second solve replays the clocked graph
         x1 = torch.zeros_like(fd)
         torch.cuda.synchronize()
@@ -399,23 +402,25 @@ def test_kernel_clocks_cover_every_launch_and_change_nothing(lib, wl, scale, pre
         torch.cuda.synchronize()
         wall_ms = (time.perf_counter() - t0) * 1e3
         slots = [lib.mg_profile_read(h, s) for s in range(lib.PROF_SLOTS)]
-        lib.mg_profile_enable(h, True)           # resets the accumulators
+        lib.mg_profile_enable(h, mode)           # resets the accumulators
         assert r1["iters"] == r0["iters"]
         assert torch.equal(x1, x0)
         n = sum(k for s, (_, k) in enumerate(slots) if s != lib.PROF_GAPS)
         it = r1["iters"]
-        book = it + 2 if loop == "host" else 2 * it + 3
+        book = {"host": it + 2, "device": 2 * it + 3, "events": 0}[loop]
         assert n == r1["launches"] - book
         ms = sum(t for t, _ in slots)
         assert 0 < ms <= wall_ms
         assert all(t > 0 for s, (t, k) in enumerate(slots) if k and s != lib.PROF_GAPS)
         assert slots[lib.PROF_GAPS][0] >= 0
+        if loop == "events":
+            assert slots[lib.PROF_GAPS][1] == 0
     lib.mg_profile_enable(h, False)
     x2 = torch.zeros_like(fd)
     r2 = lib.mg_solve(h, fd, x2, tol=1e-10)
     assert r2["launches"] == r0["launches"] and torch.equal(x2, x0)
-    # the device loop's stop test is a kernel of each iteration
-    assert r0["launches"] == n + (it if loop == "device" else 0)
+    # untimed, the device loop's stop test is a kernel of each iteration
+    assert r0["launches"] == n + (0 if loop == "host" else it)
 
 
 def test_nan_rhs_is_reported(lib):
