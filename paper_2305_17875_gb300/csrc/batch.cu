@@ -761,6 +761,7 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
                                  tk.v.c64.has(2) ? 19 : 11);
             }
             if (r32) r32[c] = narrow_rn(r) * scale32;
+            if (tk.e0) ((float*)tk.e0)[c] = 0.0f;   // the next cycle starts from e = 0
             acc = fma(r, r, acc);
         }
         const double s = block_sum_256(acc, sh);

@@ -572,7 +572,10 @@ mg_status autotune(mg_handle* h) {
     const i64 N = h->L[0].D.n();
     CK(cudaMemsetAsync(h->x64, 0, sizeof(double) * N, h->stream));
     CK(cudaMemsetAsync(h->b64, 0, sizeof(double) * N, h->stream));
-    if (h->prec != PREC64) CK(cudaMemsetAsync(h->L[0].r, 0, sizeof(float) * N, h->stream));
+    if (h->prec != PREC64) {
+        CK(cudaMemsetAsync(h->L[0].r, 0, sizeof(float) * N, h->stream));
+        CK(cudaMemsetAsync(h->L[0].e, 0, sizeof(float) * N, h->stream));
+    }
     Schedule best;
     double best_ms = 0.0;
     int tried = 1;
@@ -595,13 +598,15 @@ mg_status autotune(mg_handle* h) {
         CKS(consider(sc));
     }
     if (h->opts.smoother == MG_SMOOTH_GS) {
+        // the 7-point tail keeps its levels in shared memory, where 16 CTAs
+        // halve each phase's work; the other tails take the portable 8
         Schedule sc = best;
         sc.tail_cells = 16384;
+        sc.tail_cluster = h->stencil == 7 ? 16 : 8;
         CKS(consider(sc));
         if (best.tail_cells && h->stencil == 7) {
-            // the shared-memory tail: twice the CTAs, then one level more
-            Schedule w = best;
-            w.tail_cluster = 16;
+            Schedule w = best;   // the other cluster size, then one level more
+            w.tail_cluster = best.tail_cluster == 16 ? 8 : 16;
             CKS(consider(w));
             Schedule d = best;
             d.tail_cells = 65536;

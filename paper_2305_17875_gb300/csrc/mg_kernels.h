@@ -207,6 +207,7 @@ struct BTask {
     int shell;         // index of the active flag
     int tile[3];       // one-pass sweep: colatitude rows, radius planes, longitudes of a tile
     const void* tmap;  // one-pass sweep: its tensor maps (device, 64-byte aligned, 128 bytes each)
+    void* e0;          // outer residual of an FP32 / FP16 cycle: the fine correction, zeroed for the next cycle
 };
 static_assert(sizeof(BTask) % 4 == 0, "BTask is staged in shared memory word by word");
 // ---- one-pass multicolour sweeps (sweep.cu).  A tile is tile[0] colatitude

@@ -412,6 +412,7 @@ void add_residual(Program& P, Plan* pl) {
         t.b = h->b64;
         t.a64 = h->L[0].a64;
         t.y = pl->prec == PREC64 ? nullptr : h->L[0].r;
+        t.e0 = pl->prec == PREC64 ? nullptr : h->L[0].e;   // (the cycle's ZERO, fused here)
         t.z = h->part;
         t.shell = (int)s;
         P.add(t, red_blocks(h->L[0].D.n()));
@@ -438,17 +439,8 @@ void build_iteration(Plan* pl) {
     const int prec = pl->prec;
     int depth = 0;
     for (mg_handle* h : pl->hs) depth = std::max(depth, top_of(h));
-    if (prec != PREC64) {
-        P.begin(BOP_ZERO);
-        for (size_t s = 0; s < pl->hs.size(); ++s) {
-            mg_handle* h = pl->hs[s];
-            BTask t{};
-            t.x = h->L[0].e;
-            t.n = h->L[0].D.n();
-            t.shell = (int)s;
-            P.add(t, vblocks(h, vector_items(t.n)));
-        }
-    }
+    // the fine correction starts at zero: the outer residual that ends the
+    // prologue and every iteration clears it (FP32 / FP16 cycles)
     // down leg
     for (int l = 0; l < depth; ++l) {
         add_smooth(P, pl, l, pl->hs[0]->opts.nu1);

@@ -331,33 +331,33 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __rest
 // the arithmetic is that of k_tail (Cell7, the same restriction,
 // prolongation and coarse rows), so both forms give the same bits.
 
-// One level array spread over the cluster, read and written through the
-// cluster's shared-memory window (32-bit addresses; a CTA's own cells map to
-// its own shared memory).
+// One level array spread over the cluster, read through the cluster's
+// shared-memory window (32-bit addresses) and written by the CTA that holds
+// the cell through its own shared memory.
 template <typename T>
 struct SmArr {
     T* p;             // this CTA's chunk
     unsigned base;    // the same as a shared-memory address
     int sh;
-    __device__ __forceinline__ unsigned at(int c) const {
-        const unsigned a = base + (unsigned)(c & ((1 << sh) - 1)) * (unsigned)sizeof(T);
-        unsigned r;
-        asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"((unsigned)(c >> sh)));
-        return r;
+    int me;           // this CTA's rank
+    __device__ __forceinline__ unsigned off(int c) const {
+        return base + (unsigned)(c & ((1 << sh) - 1)) * (unsigned)sizeof(T);
     }
+    // any cell (a CTA's own cells map to its own shared memory)
     __device__ __forceinline__ T operator()(int c) const {
+        unsigned a;
+        asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(off(c)), "r"((unsigned)(c >> sh)));
         T v;
         if constexpr (sizeof(T) == 4)
-            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(at(c)) : "memory");
+            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
         else
-            asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(at(c)) : "memory");
+            asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
         return v;
     }
+    // a cell this CTA holds
     __device__ __forceinline__ void st(int c, T v) const {
-        if constexpr (sizeof(T) == 4)
-            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(at(c)), "f"(v) : "memory");
-        else
-            asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(at(c)), "d"(v) : "memory");
+        if constexpr (sizeof(T) == 4) asm volatile("st.shared.f32 [%0], %1;" ::"r"(off(c)), "f"(v) : "memory");
+        else asm volatile("st.shared.f64 [%0], %1;" ::"r"(off(c)), "d"(v) : "memory");
     }
 };
 // The three 7-point components of a level, as the global readers give them.
@@ -383,9 +383,10 @@ __device__ __forceinline__ SmLevel<T> sm_level(unsigned char* dyn, const TailSmL
     const unsigned a = (unsigned)__cvta_generic_to_shared(b);
     const unsigned w = (unsigned)(n * sizeof(T));
     SmLevel<T> v;
-    v.e = SmArr<T>{b, a, s};
-    v.r = SmArr<T>{b + n, a + w, s};
-    v.cf = SmCoef7<T>{{b + 2 * n, a + 2 * w, s}, {b + 3 * n, a + 3 * w, s}, {b + 4 * n, a + 4 * w, s}};
+    v.e = SmArr<T>{b, a, s, rank};
+    v.r = SmArr<T>{b + n, a + w, s, rank};
+    v.cf = SmCoef7<T>{{b + 2 * n, a + 2 * w, s, rank}, {b + 3 * n, a + 3 * w, s, rank},
+                      {b + 4 * n, a + 4 * w, s, rank}};
     v.lo = rank << s;
     v.hi = min((rank + 1) << s, (int)D.n());
     return v;
