@@ -152,8 +152,10 @@ def algorithmic_bytes(slot, stencil, prec, n_fine, n_next, smoother=0, axi=False
         per = ncol if passes_per_sweep is None else passes_per_sweep
         return sweep_bytes_per_cell(stencil, prec, smoother, axi, nc) * N / per
     if slot == "residual":
-        # x64, b64, the FP64 face coefficients, the FP32 residual out
-        return N * (8 + 8 + 8 * nc + (0 if prec == 0 else 4))
+        # x64, b64, the FP64 face coefficients; in FP32 / FP16 cycles the
+        # FP32 residual out and the fine FP32 correction cleared for the next
+        # cycle
+        return N * (8 + 8 + 8 * nc + (0 if prec == 0 else 8))
     if slot == "restrict0":
         # x, b, coefficients of every fine cell; the coarse right side out
         return N * (2 * vb + nc * cb) + vb * n_next
