@@ -9,6 +9,7 @@
 // Shells whose active flag is 0 skip their tasks.
 #include <cooperative_groups.h>
 #include <cstdlib>
+#include <type_traits>
 
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
@@ -111,6 +112,87 @@ __device__ __forceinline__ void st2(double* p, double a, double b) {
     *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
+// ---- L2 residency of a level's lines.  A level small enough to stay in L2
+// across its passes (its x, b and coefficients; the coarse levels of a
+// V-cycle are visited by ten launches an iteration) keeps its lines
+// (evict_last); the fine level, which streams through L2 every pass, marks
+// its read-only b and coefficients evict_first so that they do not push the
+// coarse levels out (its x keeps the normal priority: the next pass reads
+// it again).  Hints change where lines live, never values.
+constexpr long long kL2KeepBytes = 48ll << 20;
+__device__ __forceinline__ unsigned long long l2_policy(int kind) {   // 0 first, 1 normal, 2 last
+    unsigned long long p;
+    if (kind == 2) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else if (kind == 1) asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Plain accesses (FP64 cycles)
+struct PlainMem {
+    template <typename T>
+    __device__ __forceinline__ void ld4x(const T* p, T v[4]) const { ld4(p, v); }
+    template <typename T>
+    __device__ __forceinline__ void ld4r(const T* p, T v[4]) const { ldg4(p, v); }
+    template <typename T>
+    __device__ __forceinline__ T ldx(const T* p) const { return *p; }
+    template <typename T>
+    __device__ __forceinline__ void st4x(T* p, const T v[4]) const { st4(p, v); }
+    template <typename T>
+    __device__ __forceinline__ void st2x(T* p, T a, T b) const { st2(p, a, b); }
+    template <typename CF, typename T>
+    __device__ __forceinline__ void cf4(const CF& cf, int a, int idx, T v[4]) const { cf.load4(a, idx, v); }
+    template <typename CF>
+    __device__ __forceinline__ auto cf1(const CF& cf, int a, int idx) const { return cf(a, idx); }
+};
+// FP32 values with L2 priorities: xp for x, rp for b and the coefficients
+struct HintMem {
+    unsigned long long xp, rp;
+    __device__ __forceinline__ void ld4x(const float* p, float v[4]) const {
+        asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p), "l"(xp));
+    }
+    __device__ __forceinline__ void ld4r(const float* p, float v[4]) const {
+        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+            : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p), "l"(rp));
+    }
+    __device__ __forceinline__ float ldx(const float* p) const {
+        float v;
+        asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(xp));
+        return v;
+    }
+    __device__ __forceinline__ void st4x(float* p, const float v[4]) const {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                     "f"(v[2]), "f"(v[3]), "l"(xp)
+                     : "memory");
+    }
+    __device__ __forceinline__ void st2x(float* p, float a, float b) const {
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(a), "f"(b), "l"(xp)
+                     : "memory");
+    }
+    __device__ __forceinline__ void cf4(const CoefF32& cf, int a, int idx, float v[4]) const {
+        ld4r(cf.g[a] + idx, v);
+    }
+    __device__ __forceinline__ float cf1(const CoefF32& cf, int a, int idx) const {
+        float v;
+        asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(cf.g[a] + idx), "l"(rp));
+        return v;
+    }
+    // FP16 storage: the same conversion as CoefF16's readers
+    __device__ __forceinline__ void cf4(const CoefF16& cf, int a, int idx, float v[4]) const {
+        unsigned u0, u1;
+        asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(u0), "=r"(u1) : "l"(cf.g[a] + idx), "l"(rp));
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u0));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u1));
+        v[0] = lo.x * cf.s[a], v[1] = lo.y * cf.s[a], v[2] = hi.x * cf.s[a], v[3] = hi.y * cf.s[a];
+    }
+    __device__ __forceinline__ float cf1(const CoefF16& cf, int a, int idx) const { return cf(a, idx); }
+};
+// The accesses of a level of n cells at vb / cb bytes per value / coefficient.
+__device__ __forceinline__ HintMem level_mem(long long n, int vb, int cb, int ncomp) {
+    const bool keep = n * (2ll * vb + (long long)ncomp * cb) <= kL2KeepBytes;
+    return HintMem{l2_policy(keep ? 2 : 1), l2_policy(keep ? 2 : 0)};
+}
+
 // x, b and the six face coefficients of the four cells (j, i, k0 .. k0 + 3)
 // of a 7-point level; cell(m) gives the Cell7 of cell k0 + m.
 template <typename T>
@@ -118,32 +200,33 @@ struct Group7 {
     int c0;
     T X0[4], Jm[4], Jp[4], Im[4], Ip[4], EL[4], EU[4], ZL[4], ZU[4], XL[4];
     T xkm, xkp, xu3;
-    template <typename CF>
-    __device__ __forceinline__ void load(const CF& cf, const Dims& D, const T* x, int j, int i, int k0) {
+    template <typename CF, typename M = PlainMem>
+    __device__ __forceinline__ void load(const CF& cf, const Dims& D, const T* x, int j, int i, int k0,
+                                         const M& mem = M()) {
         const int plane = D.nth * D.nph;
         c0 = (j * D.nth + i) * D.nph + k0;
         const int rb = c0 - k0;
         const bool jl = j > 0, ju = j + 1 < D.nr, il = i > 0, iu = i + 1 < D.nth;
-        ld4(x + c0, X0);
-        if (jl) ld4(x + c0 - plane, Jm);
+        mem.ld4x(x + c0, X0);
+        if (jl) mem.ld4x(x + c0 - plane, Jm);
         else for (int m = 0; m < 4; ++m) Jm[m] = X0[m];
-        if (ju) ld4(x + c0 + plane, Jp);
+        if (ju) mem.ld4x(x + c0 + plane, Jp);
         else for (int m = 0; m < 4; ++m) Jp[m] = X0[m];
-        if (il) ld4(x + c0 - D.nph, Im);
+        if (il) mem.ld4x(x + c0 - D.nph, Im);
         else for (int m = 0; m < 4; ++m) Im[m] = X0[m];
-        if (iu) ld4(x + c0 + D.nph, Ip);
+        if (iu) mem.ld4x(x + c0 + D.nph, Ip);
         else for (int m = 0; m < 4; ++m) Ip[m] = X0[m];
         const int kw = k0 + 4 == D.nph ? rb : c0 + 4;
-        xkm = x[k0 == 0 ? rb + D.nph - 1 : c0 - 1];
-        xkp = x[kw];
-        cf.load4(4, c0, EL);
-        if (ju) cf.load4(4, c0 + plane, EU);
+        xkm = mem.ldx(x + (k0 == 0 ? rb + D.nph - 1 : c0 - 1));
+        xkp = mem.ldx(x + kw);
+        mem.cf4(cf, 4, c0, EL);
+        if (ju) mem.cf4(cf, 4, c0 + plane, EU);
         else for (int m = 0; m < 4; ++m) EU[m] = (T)0;
-        cf.load4(0, c0, ZL);
-        if (iu) cf.load4(0, c0 + D.nph, ZU);
+        mem.cf4(cf, 0, c0, ZL);
+        if (iu) mem.cf4(cf, 0, c0 + D.nph, ZU);
         else for (int m = 0; m < 4; ++m) ZU[m] = (T)0;
-        cf.load4(8, c0, XL);
-        xu3 = (T)cf(8, kw);
+        mem.cf4(cf, 8, c0, XL);
+        xu3 = (T)mem.cf1(cf, 8, kw);
     }
     __device__ __forceinline__ Cell7<T> cell(int m) const {   // m a compile-time constant after unrolling
         Cell7<T> q;
@@ -164,15 +247,19 @@ __device__ __forceinline__ void gs_pass7v(const CF& cf, const Dims& D, T* x, con
                                           i64 stride) {
     const int nq = D.nph >> 2;
     const i64 work = (i64)D.nr * D.nth * nq;
+    // FP32 values: the level's L2 priorities; FP64 plain
+    typedef typename std::conditional<sizeof(T) == 4, HintMem, PlainMem>::type M;
+    M mem{};
+    if constexpr (sizeof(T) == 4) mem = level_mem(D.n(), 4, sizeof(cf.g[0][0]), 3);
     for (i64 t = first; t < work; t += stride) {
         const unsigned row = D.dq.div((unsigned)t);
         const unsigned jj = D.dth.div(row);
         const int k0 = 4 * (int)((unsigned)t - row * (unsigned)nq);
         const int i = (int)(row - jj * (unsigned)D.nth), j = (int)jj;
         Group7<T> g;
-        g.load(cf, D, x, j, i, k0);
+        g.load(cf, D, x, j, i, k0, mem);
         T B[4];
-        ldg4(b + g.c0, B);
+        mem.ld4r(b + g.c0, B);
         // the group is written back whole (16-byte store, full sectors); the two
         // cells of the other colour keep the values every reader sees this pass
         T out[4] = {g.X0[0], g.X0[1], g.X0[2], g.X0[3]};
@@ -183,7 +270,7 @@ __device__ __forceinline__ void gs_pass7v(const CF& cf, const Dims& D, T* x, con
             out[1] = g.cell(1).gs(B[1]);
             out[3] = g.cell(3).gs(B[3]);
         }
-        st4(x + g.c0, out);
+        mem.st4x(x + g.c0, out);
     }
 }
 
@@ -290,6 +377,14 @@ __device__ __forceinline__ void restrict_pass7v(const CF& cf, const Dims& D, con
                                                 int cz, int ce, int cx, T* rc, T* ec_zero, i64 first, i64 stride) {
     const int nq = D.nph >> 2;
     const i64 work = (i64)Dc.nr * Dc.nth * nq;
+    // FP32 values: the fine level's L2 priorities for its reads, the coarse
+    // level's for the coarse right side and correction written
+    typedef typename std::conditional<sizeof(T) == 4, HintMem, PlainMem>::type M;
+    M fm{}, cm{};
+    if constexpr (sizeof(T) == 4) {
+        fm = level_mem(D.n(), 4, sizeof(cf.g[0][0]), 3);
+        cm = level_mem(Dc.n(), 4, sizeof(cf.g[0][0]), 3);
+    }
     for (i64 t = first; t < work; t += stride) {
         const unsigned row = D.dq.div((unsigned)t);
         const unsigned J = Dc.dth.div(row);
@@ -299,9 +394,9 @@ __device__ __forceinline__ void restrict_pass7v(const CF& cf, const Dims& D, con
         for (int dj = 0; dj < ce; ++dj)
             for (int di = 0; di < cz; ++di) {
                 Group7<T> g;
-                g.load(cf, D, x, ce * (int)J + dj, cz * I + di, 4 * q);
+                g.load(cf, D, x, ce * (int)J + dj, cz * I + di, 4 * q, fm);
                 T B[4];
-                ldg4(b + g.c0, B);
+                fm.ld4r(b + g.c0, B);
                 const T r0 = g.cell(0).resid(B[0]), r1 = g.cell(1).resid(B[1]);
                 const T r2 = g.cell(2).resid(B[2]), r3 = g.cell(3).resid(B[3]);
                 if (cx == 1) {
@@ -315,14 +410,14 @@ __device__ __forceinline__ void restrict_pass7v(const CF& cf, const Dims& D, con
             }
         const int cb = ((int)J * Dc.nth + I) * Dc.nph;
         if (cx == 1) {
-            st4(rc + cb + 4 * q, s);
+            cm.st4x(rc + cb + 4 * q, s);
             if (ec_zero) {
                 const T z[4] = {(T)0, (T)0, (T)0, (T)0};
-                st4(ec_zero + cb + 4 * q, z);
+                cm.st4x(ec_zero + cb + 4 * q, z);
             }
         } else {
-            st2(rc + cb + 2 * q, s[0], s[1]);
-            if (ec_zero) st2(ec_zero + cb + 2 * q, (T)0, (T)0);
+            cm.st2x(rc + cb + 2 * q, s[0], s[1]);
+            if (ec_zero) cm.st2x(ec_zero + cb + 2 * q, (T)0, (T)0);
         }
     }
 }
