@@ -140,7 +140,8 @@ def algorithmic_bytes(slot, stencil, prec, n_fine, n_next, smoother=0, axi=False
     colour pass is charged 1/C of a whole sweep (C = 2 colours for 7 points, 4
     for 19 points); a one-pass sweep (all colours in one launch,
     passes_per_sweep = 1) the whole sweep.  ncomp overrides the stored
-    coefficient count (9 for 19 points: the count of the survey's table)."""
+    coefficient count (9 for 19 points: every component of the general
+    mapping, the model the 19-point byte counts were first planned on)."""
     vb = 8 if prec == 0 else 4
     cb = {0: 8, 1: 4, 2: 2}[prec]
     nc = coef_components(stencil, axi) if ncomp is None else ncomp
@@ -437,7 +438,7 @@ def roofline_of(name, slots, steps, stencil, prec, N, n_next, smoother, axi, one
             "launches_per_sweep": (1 if one_pass else (1 if smoother == 1 else (4 if stencil == 19 else 2)))
             if name == "smooth0" else None}
     if stencil == 19 and axi:
-        # the survey's table counts nine coefficient arrays for 19 points
+        # the same bytes with all nine coefficient arrays of the general mapping
         sb = algorithmic_bytes(name, stencil, prec, N, n_next, smoother, axi, passes_per_sweep=pps, ncomp=9)
         roof["frac_nine_component_model"] = sb / (per_launch_ms * 1e-3) / 1e9 / peak
     return roof

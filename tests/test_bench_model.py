@@ -1,5 +1,5 @@
 """Host logic of bench.py: the algorithmic byte model behind the roofline
-fraction, checked against the survey's per-sweep table written out by hand
+fraction, checked against per-sweep byte counts written out by hand
 (a whole smoothing sweep moves x twice, b once and every stored coefficient
 array once; a colour pass is charged 1/C of a sweep), and the half-size
 traffic scaling."""

@@ -263,7 +263,7 @@ def test_gauss_seidel_sweep_is_block_gauss_seidel_in_colour_order():
 
 
 def _colour_sets(shape, stencil):
-    """The colour sets of the survey's ordering, from the cell indices:
+    """The colour sets of the smoother's ordering, from the cell indices:
     (i + j + k) mod 2 for 7 points, ((i + j) mod 2) + 2 ((j + k) mod 2) for 19."""
     j, i, k = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
     col = ((i + j + k) % 2 if stencil == 7 else (i + j) % 2 + 2 * ((j + k) % 2)).ravel()
