@@ -463,12 +463,12 @@ mg_status configure_tail(mg_handle* h, i64 cells, int cluster) {
     h->tail_host = task;
     h->tail_level = t;
     h->tail_cluster = cluster;
-    // 7 points: every level in the cluster's shared memory when it fits
+    // every level in the cluster's shared memory when it fits
     // (MG_TAIL_GLOBAL keeps the global-memory form)
-    if (h->stencil == 7 && !std::getenv("MG_TAIL_GLOBAL")) {
+    if (!std::getenv("MG_TAIL_GLOBAL")) {
         TailSmLayout lay;
         tail_sm_layout(task, cluster, h->prec == PREC64 ? 8 : 4, lay);
-        if (lay.bytes <= kTailSmMaxBytes && tail_max_clusters(cluster, 7, h->prec, lay.bytes) > 0)
+        if (lay.bytes <= kTailSmMaxBytes && tail_max_clusters(cluster, h->stencil, h->prec, lay.bytes) > 0)
             h->tail_smem = lay.bytes;
     }
     return MG_OK;
@@ -598,13 +598,13 @@ mg_status autotune(mg_handle* h) {
         CKS(consider(sc));
     }
     if (h->opts.smoother == MG_SMOOTH_GS) {
-        // the 7-point tail keeps its levels in shared memory, where 16 CTAs
-        // halve each phase's work; the other tails take the portable 8
+        // the tail keeps its levels in shared memory, where 16 CTAs halve
+        // each phase's work
         Schedule sc = best;
         sc.tail_cells = 16384;
-        sc.tail_cluster = h->stencil == 7 ? 16 : 8;
+        sc.tail_cluster = 16;
         CKS(consider(sc));
-        if (best.tail_cells && h->stencil == 7) {
+        if (best.tail_cells) {
             Schedule w = best;   // the other cluster size, then one level more
             w.tail_cluster = best.tail_cluster == 16 ? 8 : 16;
             CKS(consider(w));

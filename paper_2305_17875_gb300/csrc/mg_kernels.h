@@ -126,10 +126,10 @@ struct TailTask {
     const int* active; // per-shell flags of a batch (null: always run)
     int shell;
 };
-// The 7-point tail can keep every level in the cluster's shared memory: cell
-// c of level l on CTA c >> sh[l] at offset c & (2^sh[l] - 1), five arrays of
-// 2^sh[l] values per level (e, r, the lower-face components 0, 4, 8), level
-// l's first array at byte off[l].
+// The tail can keep every level in the cluster's shared memory: cell c of
+// level l on CTA c >> sh[l] at offset c & (2^sh[l] - 1), arrays of 2^sh[l]
+// values per level (e, r, then the lower-face components: 0, 4, 8 for 7
+// points, all nine for 19), level l's first array at byte off[l].
 constexpr int kTailSmThreads = 1024;
 constexpr unsigned kTailSmMaxBytes = 200u * 1024u;
 struct TailSmLayout {
@@ -138,7 +138,9 @@ struct TailSmLayout {
     unsigned rd_off;     // the coarsest level's r in FP64 (ncoarse values), every CTA a copy
     unsigned bytes;
 };
+__host__ __device__ inline int tail_sm_arrays(const TailTask& tk) { return tk.lev[0].v.stencil == 19 ? 11 : 5; }
 __host__ __device__ inline void tail_sm_layout(const TailTask& tk, int csize, int vbytes, TailSmLayout& L) {
+    const unsigned arrays = (unsigned)tail_sm_arrays(tk);
     unsigned at = 0;
     for (int l = 0; l < tk.nlev; ++l) {
         const long long n = (long long)tk.lev[l].v.D.nr * tk.lev[l].v.D.nth * tk.lev[l].v.D.nph;
@@ -147,7 +149,7 @@ __host__ __device__ inline void tail_sm_layout(const TailTask& tk, int csize, in
         while ((1LL << s) < per) ++s;
         L.sh[l] = s;
         L.off[l] = at;
-        at += (5u * (unsigned)vbytes) << s;
+        at += (arrays * (unsigned)vbytes) << s;
     }
     L.rd_off = at;
     at += 8u * (unsigned)tk.ncoarse;

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "mg_kernels.h"
 #include "line_smooth.cuh"
@@ -325,11 +326,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailTask* __rest
     stamp_end(stamp);
 }
 
-// ---- the 7-point coarse tail in the cluster's shared memory (layout in
+// ---- the coarse tail in the cluster's shared memory (layout in
 // tail_sm_layout).  Each CTA works on the cells it holds; a neighbour held by
 // another CTA is read through the cluster's shared-memory window.  Per cell
-// the arithmetic is that of k_tail (Cell7, the same restriction,
-// prolongation and coarse rows), so both forms give the same bits.
+// the arithmetic is that of k_tail (Cell7 or Nbr19 + apply19 + diag_cell,
+// the same restriction, prolongation and coarse rows), so both forms give
+// the same bits.  Not for the full sphere's 19-point cells (no pole copy).
 
 // One level array spread over the cluster, read through the cluster's
 // shared-memory window (32-bit addresses) and written by the CTA that holds
@@ -368,49 +370,80 @@ struct SmCoef7 {
         return a == 0 ? g0((int)idx) : (a == 4 ? g4((int)idx) : g8((int)idx));
     }
 };
+// The nine 19-point components (consecutive arrays; an absent one, as on an
+// axisymmetric mapping, is never read: has() says so as the global readers do).
 template <typename T>
+struct SmCoef19 {
+    SmArr<T> g0;        // component a at g0 + a arrays
+    unsigned astride;   // bytes between components
+    int n;              // values per array
+    unsigned mask;      // bit a: component a stored
+    __device__ __forceinline__ bool has(int a) const { return (mask >> a) & 1u; }
+    __device__ __forceinline__ T operator()(int a, i64 idx) const {
+        SmArr<T> q = g0;
+        q.base += (unsigned)a * astride;
+        return q((int)idx);
+    }
+    __device__ __forceinline__ T* chunk(int a) const { return g0.p + a * n; }
+};
+template <int S, typename T>
 struct SmLevel {
     SmArr<T> e, r;
-    SmCoef7<T> cf;
+    typename std::conditional<S == 7, SmCoef7<T>, SmCoef19<T>>::type cf;
     int lo, hi;   // the cells this CTA holds
 };
-template <typename T>
-__device__ __forceinline__ SmLevel<T> sm_level(unsigned char* dyn, const TailSmLayout& L, const Dims& D, int l,
-                                               int rank) {
+template <int S, typename T>
+__device__ __forceinline__ SmLevel<S, T> sm_level(unsigned char* dyn, const TailSmLayout& L, const Dims& D, int l,
+                                                  int rank, unsigned mask = 0) {
     const int s = L.sh[l];
     T* b = reinterpret_cast<T*>(dyn + L.off[l]);
     const int n = 1 << s;
     const unsigned a = (unsigned)__cvta_generic_to_shared(b);
     const unsigned w = (unsigned)(n * sizeof(T));
-    SmLevel<T> v;
+    SmLevel<S, T> v;
     v.e = SmArr<T>{b, a, s, rank};
     v.r = SmArr<T>{b + n, a + w, s, rank};
-    v.cf = SmCoef7<T>{{b + 2 * n, a + 2 * w, s, rank}, {b + 3 * n, a + 3 * w, s, rank},
-                      {b + 4 * n, a + 4 * w, s, rank}};
+    if constexpr (S == 7)
+        v.cf = SmCoef7<T>{{b + 2 * n, a + 2 * w, s, rank}, {b + 3 * n, a + 3 * w, s, rank},
+                          {b + 4 * n, a + 4 * w, s, rank}};
+    else
+        v.cf = SmCoef19<T>{{b + 2 * n, a + 2 * w, s, rank}, w, n, mask};
     v.lo = rank << s;
     v.hi = min((rank + 1) << s, (int)D.n());
     return v;
 }
 
-// One colour of the pass (gs_colour_range, 7 points): item t is cell 2t or
+// One colour of the pass (gs_colour_range).  7 points: item t is cell 2t or
 // 2t + 1, so the items of the cells a CTA holds are t in [lo / 2, hi / 2).
-template <typename T>
-__device__ __forceinline__ void sm_gs(const SmLevel<T>& V, const Dims D, int colour) {
-    const int work = D.nr * D.nth * (D.nph >> 1);
-    const int t1 = min(V.hi >> 1, work);
-    for (int t = (V.lo >> 1) + threadIdx.x; t < t1; t += blockDim.x) {
-        int kk, i, j;
-        decode_half(D, t, kk, i, j);
-        Cell7<T> q;
-        q.load(V.cf, D, j, i, 2 * kk + ((colour + i + j) & 1), V.e);
-        V.e.st(q.c, q.gs(V.r(q.c)));
+// 19 points: the CTA's cells of the colour ((i + j) mod 2 + 2 ((j + k) mod 2)).
+template <int S, typename T>
+__device__ __forceinline__ void sm_gs(const SmLevel<S, T>& V, const Dims D, int colour) {
+    if constexpr (S == 7) {
+        const int work = D.nr * D.nth * (D.nph >> 1);
+        const int t1 = min(V.hi >> 1, work);
+        for (int t = (V.lo >> 1) + threadIdx.x; t < t1; t += blockDim.x) {
+            int kk, i, j;
+            decode_half(D, t, kk, i, j);
+            Cell7<T> q;
+            q.load(V.cf, D, j, i, 2 * kk + ((colour + i + j) & 1), V.e);
+            V.e.st(q.c, q.gs(V.r(q.c)));
+        }
+    } else {
+        for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) {
+            const C3 p = decode(D, c);
+            if (((p.i + p.j) & 1) + 2 * ((p.j + p.k) & 1) != colour) continue;
+            Nbr19<T> X;
+            X.load(V.e, D, c, p, !V.cf.has(2));
+            const T r = V.r(c) - apply19<T>(V.cf, X, D, c, p);
+            V.e.st(c, X.v[0] + r / diag_cell<S, T>(V.cf, D, p));
+        }
     }
 }
 
-// Residual restricted into the coarse cells this CTA holds (restrict_range,
-// 7 points), their correction zeroed.
-template <typename T>
-__device__ __forceinline__ void sm_restrict(const SmLevel<T>& F, const Dims D, const SmLevel<T>& C,
+// Residual restricted into the coarse cells this CTA holds (restrict_range),
+// their correction zeroed.
+template <int S, typename T>
+__device__ __forceinline__ void sm_restrict(const SmLevel<S, T>& F, const Dims D, const SmLevel<S, T>& C,
                                             const Dims Dc, int cz, int ce, int cx) {
     for (int t = C.lo + threadIdx.x; t < C.hi; t += blockDim.x) {
         const C3 P = decode(Dc, t);
@@ -418,9 +451,17 @@ __device__ __forceinline__ void sm_restrict(const SmLevel<T>& F, const Dims D, c
         for (int dj = 0; dj < ce; ++dj)
             for (int di = 0; di < cz; ++di)
                 for (int dk = 0; dk < cx; ++dk) {
-                    Cell7<T> q;
-                    q.load(F.cf, D, ce * P.j + dj, cz * P.i + di, cx * P.k + dk, F.e);
-                    s += q.resid(F.r(q.c));
+                    if constexpr (S == 7) {
+                        Cell7<T> q;
+                        q.load(F.cf, D, ce * P.j + dj, cz * P.i + di, cx * P.k + dk, F.e);
+                        s += q.resid(F.r(q.c));
+                    } else {
+                        const C3 c{ce * P.j + dj, cz * P.i + di, cx * P.k + dk};
+                        const int id = cidx(D, c);
+                        Nbr19<T> X;
+                        X.load(F.e, D, id, c, !F.cf.has(2));
+                        s += F.r(id) - apply19<T>(F.cf, X, D, id, c);
+                    }
                 }
         C.r.st(t, s);
         C.e.st(t, (T)0);
@@ -428,8 +469,8 @@ __device__ __forceinline__ void sm_restrict(const SmLevel<T>& F, const Dims D, c
 }
 
 // x += P ec on the fine cells this CTA holds (prolong_range).
-template <typename T>
-__device__ __forceinline__ void sm_prolong(const SmLevel<T>& F, const Dims D, const SmLevel<T>& C,
+template <int S, typename T>
+__device__ __forceinline__ void sm_prolong(const SmLevel<S, T>& F, const Dims D, const SmLevel<S, T>& C,
                                            const Dims Dc, int cz, int ce, int cx) {
     for (int c = F.lo + threadIdx.x; c < F.hi; c += blockDim.x) {
         T* xc = F.e.p + (c - F.lo);   // this CTA's own cell
@@ -470,8 +511,8 @@ __device__ __forceinline__ void sm_prolong(const SmLevel<T>& F, const Dims D, co
 // (coarse_range's sums: each lane over m = lane, lane + 32, ..., then the
 // shuffle tree).  rd: the coarsest r converted to FP64 once, in this CTA's
 // shared memory; the lane's loads of a block of eight terms go out together.
-template <typename T>
-__device__ __forceinline__ void sm_coarse(const double* binv, const double* rd, int n, const SmLevel<T>& V) {
+template <int S, typename T>
+__device__ __forceinline__ void sm_coarse(const double* binv, const double* rd, int n, const SmLevel<S, T>& V) {
     const int lane = threadIdx.x & 31;
     const int hi = min(V.hi, n);
     for (int row = V.lo + (int)(threadIdx.x >> 5); row < hi; row += (int)(blockDim.x >> 5)) {
@@ -490,10 +531,11 @@ __device__ __forceinline__ void sm_coarse(const double* binv, const double* rd, 
     }
 }
 
-// Threads of a shared-memory tail CTA (FP64 halves them for registers).
-template <typename T>
+// Threads of a shared-memory tail CTA (FP64 and 19 points halve them for
+// registers).
+template <int S, typename T>
 constexpr int tail_sm_threads() {
-    return sizeof(T) == 8 ? kTailSmThreads / 2 : kTailSmThreads;
+    return (sizeof(T) == 8 || S == 19) ? kTailSmThreads / 2 : kTailSmThreads;
 }
 
 // Asynchronous 4- or 8-byte copy global -> this CTA's shared memory.
@@ -524,12 +566,13 @@ __device__ __forceinline__ void stage_span(T* sdst, const T* gsrc, int count) {
     for (int q = done + (int)threadIdx.x; q < count; q += blockDim.x) cp_async_val<T>(sdst + q, gsrc + q);
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(tail_sm_threads<T>(), 1) k_tail_sm(const TailTask* __restrict__ tasks, int csize,
+template <int S, typename T, int P>
+__global__ void __launch_bounds__(tail_sm_threads<S, T>(), 1) k_tail_sm(const TailTask* __restrict__ tasks, int csize,
                                                                      unsigned long long* stamp) {
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ TailSmLayout lay;
+    __shared__ unsigned comp[kMaxTail];   // per level: the stored components (19 points)
     cg::cluster_group cl = cg::this_cluster();
     const TailTask& tk = tasks[blockIdx.x / csize];
     stamp_start(stamp);
@@ -538,35 +581,55 @@ __global__ void __launch_bounds__(tail_sm_threads<T>(), 1) k_tail_sm(const TailT
         return;
     }
     const int rank = (int)cl.block_rank();
-    if (threadIdx.x == 0) tail_sm_layout(tk, csize, (int)sizeof(T), lay);
-    __syncthreads();
     const int nl = tk.nlev;
+    if (threadIdx.x == 0) {
+        tail_sm_layout(tk, csize, (int)sizeof(T), lay);
+        for (int l = 0; l < nl; ++l) {
+            unsigned m = 0;
+            for (int a = 0; a < 9; ++a) m |= CoefOf<P>::get(tk.lev[l].v).has(a) ? 1u << a : 0u;
+            comp[l] = m;
+        }
+    }
+    __syncthreads();
+    auto level = [&](int l) { return sm_level<S, T>(dyn, lay, tk.lev[l].v.D, l, rank, comp[l]); };
     // stage (copies all in flight at once): the components of every level, e
-    // and r of the first, this CTA's rows of Binv
+    // and r of the first, this CTA's rows of Binv toward L2
     for (int l = 0; l < nl; ++l) {
         const auto& cf = CoefOf<P>::get(tk.lev[l].v);
-        const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[l].v.D, l, rank);
+        const SmLevel<S, T> V = level(l);
         const int cnt = V.hi - V.lo;
         if (cnt <= 0) continue;
-        if constexpr (P == PREC16) {   // FP16 storage: converted as the global readers do
-            for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) {
-                const int o = c - V.lo;
-                V.cf.g0.p[o] = (T)cf(0, c);
-                V.cf.g4.p[o] = (T)cf(4, c);
-                V.cf.g8.p[o] = (T)cf(8, c);
+        if constexpr (S == 7) {
+            if constexpr (P == PREC16) {   // FP16 storage: converted as the global readers do
+                for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) {
+                    const int o = c - V.lo;
+                    V.cf.g0.p[o] = (T)cf(0, c);
+                    V.cf.g4.p[o] = (T)cf(4, c);
+                    V.cf.g8.p[o] = (T)cf(8, c);
+                }
+            } else {
+                stage_span<T>(V.cf.g0.p, cf.g[0] + V.lo, cnt);
+                stage_span<T>(V.cf.g4.p, cf.g[4] + V.lo, cnt);
+                stage_span<T>(V.cf.g8.p, cf.g[8] + V.lo, cnt);
             }
         } else {
-            stage_span<T>(V.cf.g0.p, cf.g[0] + V.lo, cnt);
-            stage_span<T>(V.cf.g4.p, cf.g[4] + V.lo, cnt);
-            stage_span<T>(V.cf.g8.p, cf.g[8] + V.lo, cnt);
+            for (int a = 0; a < 9; ++a) {
+                if (!cf.has(a)) continue;
+                T* dst = V.cf.chunk(a);
+                if constexpr (P == PREC16) {
+                    for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) dst[c - V.lo] = (T)cf(a, c);
+                } else {
+                    stage_span<T>(dst, cf.g[a] + V.lo, cnt);
+                }
+            }
         }
         if (l == 0) {
             stage_span<T>(V.e.p, (const T*)tk.lev[0].e + V.lo, cnt);
             stage_span<T>(V.r.p, (const T*)tk.lev[0].r + V.lo, cnt);
         }
     }
-    {   // this CTA's rows of Binv toward L2 for the coarse phase
-        const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[nl - 1].v.D, nl - 1, rank);
+    {
+        const SmLevel<S, T> V = level(nl - 1);
         const int n = tk.ncoarse;
         const i64 b0 = (i64)V.lo * n, b1 = (i64)min(V.hi, n) * n;
         for (i64 q = b0 + 16 * (i64)threadIdx.x; q < b1; q += 16 * (i64)blockDim.x)
@@ -574,40 +637,41 @@ __global__ void __launch_bounds__(tail_sm_threads<T>(), 1) k_tail_sm(const TailT
     }
     cp_async_wait_all();
     cl.sync();
+    constexpr int ncol = S == 7 ? 2 : 4;
     for (int l = 0; l < nl - 1; ++l) {
         const LevelView& A = tk.lev[l].v;
-        const SmLevel<T> F = sm_level<T>(dyn, lay, A.D, l, rank);
+        const SmLevel<S, T> F = level(l);
         for (int sw = 0; sw < tk.nu1; ++sw)
-            for (int c = 0; c < 2; ++c) {
-                sm_gs<T>(F, A.D, c);
+            for (int c = 0; c < ncol; ++c) {
+                sm_gs<S, T>(F, A.D, c);
                 cl.sync();
             }
-        const SmLevel<T> C = sm_level<T>(dyn, lay, tk.lev[l + 1].v.D, l + 1, rank);
-        sm_restrict<T>(F, A.D, C, tk.lev[l + 1].v.D, A.cz, A.ce, A.cx);
+        const SmLevel<S, T> C = level(l + 1);
+        sm_restrict<S, T>(F, A.D, C, tk.lev[l + 1].v.D, A.cz, A.ce, A.cx);
         cl.sync();
     }
     {
-        const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[nl - 1].v.D, nl - 1, rank);
+        const SmLevel<S, T> V = level(nl - 1);
         double* rd = reinterpret_cast<double*>(dyn + lay.rd_off);
         for (int m = threadIdx.x; m < tk.ncoarse; m += blockDim.x) rd[m] = (double)V.r(m);
         __syncthreads();
-        sm_coarse<T>(tk.binv, rd, tk.ncoarse, V);
+        sm_coarse<S, T>(tk.binv, rd, tk.ncoarse, V);
     }
     cl.sync();
     for (int l = nl - 2; l >= 0; --l) {
         const LevelView& A = tk.lev[l].v;
-        const SmLevel<T> F = sm_level<T>(dyn, lay, A.D, l, rank);
-        const SmLevel<T> C = sm_level<T>(dyn, lay, tk.lev[l + 1].v.D, l + 1, rank);
-        sm_prolong<T>(F, A.D, C, tk.lev[l + 1].v.D, A.cz, A.ce, A.cx);
+        const SmLevel<S, T> F = level(l);
+        const SmLevel<S, T> C = level(l + 1);
+        sm_prolong<S, T>(F, A.D, C, tk.lev[l + 1].v.D, A.cz, A.ce, A.cx);
         cl.sync();
         for (int sw = 0; sw < tk.nu2; ++sw)
-            for (int c = 0; c < 2; ++c) {
-                sm_gs<T>(F, A.D, c);
+            for (int c = 0; c < ncol; ++c) {
+                sm_gs<S, T>(F, A.D, c);
                 cl.sync();
             }
     }
     // the top level's correction back to global memory
-    const SmLevel<T> V = sm_level<T>(dyn, lay, tk.lev[0].v.D, 0, rank);
+    const SmLevel<S, T> V = level(0);
     for (int c = V.lo + threadIdx.x; c < V.hi; c += blockDim.x) ((T*)tk.lev[0].e)[c] = V.e.p[c - V.lo];
     stamp_end(stamp);
 }
@@ -716,7 +780,7 @@ cudaError_t launch_coarse_solve(const double* binv, int n, int prec, const void*
 // The tail kernel of (stencil, precision); the shared-memory form when smem > 0.
 template <int S, typename T, int P>
 static void* tail_kernel(size_t smem) {
-    if (S == 7 && smem > 0) return reinterpret_cast<void*>(k_tail_sm<T, P>);
+    if (smem > 0) return reinterpret_cast<void*>(k_tail_sm<S, T, P>);
     return reinterpret_cast<void*>(k_tail<S, T, P>);
 }
 
@@ -759,7 +823,6 @@ static cudaError_t tail_attrs(const void* k, size_t smem, int csize) {
 template <int S, typename T, int P>
 static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cudaStream_t s,
                                unsigned long long* stamp, size_t smem) {
-    if (S != 7) smem = 0;
     if (smem > kTailSmMaxBytes) return cudaErrorInvalidValue;
     if (csize < 1 || csize > kTailMaxCluster) return cudaErrorInvalidValue;
     const void* k = tail_kernel<S, T, P>(smem);
@@ -767,14 +830,13 @@ static cudaError_t tail_launch(const TailTask* tasks, int ntasks, int csize, cud
     if (ea != cudaSuccess) return ea;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    tail_config(cfg, attr, ntasks, csize, smem, tail_sm_threads<T>(), s);
+    tail_config(cfg, attr, ntasks, csize, smem, tail_sm_threads<S, T>(), s);
     void* args[] = {(void*)&tasks, (void*)&csize, (void*)&stamp};
     return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 template <int S, typename T, int P>
 static int tail_clusters(int csize, size_t smem) {
-    if (S != 7) smem = 0;
     if (smem > kTailSmMaxBytes) return 0;
     if (csize < 1 || csize > kTailMaxCluster) return 0;
     const void* k = tail_kernel<S, T, P>(smem);
@@ -784,7 +846,7 @@ static int tail_clusters(int csize, size_t smem) {
     }
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    tail_config(cfg, attr, 1, csize, smem, tail_sm_threads<T>(), nullptr);
+    tail_config(cfg, attr, 1, csize, smem, tail_sm_threads<S, T>(), nullptr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
