@@ -120,6 +120,7 @@ __device__ __forceinline__ void st2(double* p, double a, double b) {
 // coarse levels out (its x keeps the normal priority: the next pass reads
 // it again).  Hints change where lines live, never values.
 constexpr long long kL2KeepBytes = 48ll << 20;
+constexpr long long kL2KeepXBytes = 24ll << 20;
 __device__ __forceinline__ unsigned long long l2_policy(int kind) {   // 0 first, 1 normal, 2 last
     unsigned long long p;
     if (kind == 2) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -190,7 +191,8 @@ struct HintMem {
 // The accesses of a level of n cells at vb / cb bytes per value / coefficient.
 __device__ __forceinline__ HintMem level_mem(long long n, int vb, int cb, int ncomp) {
     const bool keep = n * (2ll * vb + (long long)ncomp * cb) <= kL2KeepBytes;
-    return HintMem{l2_policy(keep ? 2 : 1), l2_policy(keep ? 2 : 0)};
+    const bool keep_x = keep || n * vb <= kL2KeepXBytes;   // a fine level whose x alone fits
+    return HintMem{l2_policy(keep_x ? 2 : 1), l2_policy(keep ? 2 : 0)};
 }
 
 // x, b and the six face coefficients of the four cells (j, i, k0 .. k0 + 3)
@@ -682,9 +684,17 @@ __device__ __forceinline__ void prolong_pass(const Dims& D, const Dims& Dc, int 
 // and summation order as prolong_pass.
 template <typename T>
 __device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, int cz, int ce, int cx, const T* ec,
-                                               T* x, i64 first, i64 stride) {
+                                               T* x, i64 first, i64 stride, int cb = 4) {
     const int nq = D.nph >> 2;
     const i64 work = (i64)D.nr * D.nth * nq;
+    // FP32 values: the fine and coarse levels' L2 priorities (cb: bytes of a
+    // stored coefficient, which size the levels as the colour passes do)
+    typedef typename std::conditional<sizeof(T) == 4, HintMem, PlainMem>::type M;
+    M fm{}, cm{};
+    if constexpr (sizeof(T) == 4) {
+        fm = level_mem(D.n(), 4, cb, 3);
+        cm = level_mem(Dc.n(), 4, cb, 3);
+    }
     for (i64 t = first; t < work; t += stride) {
         const unsigned row = D.dq.div((unsigned)t);
         const unsigned jj = D.dth.div(row);
@@ -696,7 +706,7 @@ __device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, in
         lin1d(i, cz, Dc.nth, false, ii, wi);
         const int c0 = (j * D.nth + i) * D.nph + k0;
         T X[4];
-        ld4(x + c0, X);
+        fm.ld4x(x + c0, X);
         if (cx == 1) {   // longitude not halved: coarse groups of four, weight 1 along k
             T s[4] = {(T)0, (T)0, (T)0, (T)0};
 #pragma unroll
@@ -707,12 +717,12 @@ __device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, in
                     if (bb >= cz) break;
                     const T wab = (T)wj[a] * (T)wi[bb];
                     T E[4];
-                    ldg4(ec + (ij[a] * Dc.nth + ii[bb]) * Dc.nph + k0, E);
+                    cm.ld4r(ec + (ij[a] * Dc.nth + ii[bb]) * Dc.nph + k0, E);
                     for (int m = 0; m < 4; ++m) s[m] = fma(wab * (T)1.0f, E[m], s[m]);
                 }
             }
             for (int m = 0; m < 4; ++m) X[m] = X[m] + s[m];
-            st4(x + c0, X);
+            fm.st4x(x + c0, X);
             continue;
         }
         if (cx == 2) {   // halved: fine k0..k0+3 from coarse K0-1 .. K0+2, K0 = k0 / 2
@@ -727,7 +737,7 @@ __device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, in
                     if (bb >= cz) break;
                     const T wab = (T)wj[a] * (T)wi[bb];
                     const T* er = ec + (ij[a] * Dc.nth + ii[bb]) * Dc.nph;
-                    const T e0 = er[K0], e1 = er[K0 + 1], em = er[Km], ep = er[Kp];
+                    const T e0 = cm.ldx(er + K0), e1 = cm.ldx(er + K0 + 1), em = cm.ldx(er + Km), ep = cm.ldx(er + Kp);
                     // weights 3/4 on the coarse cell, 1/4 on its neighbour (e = 0, 1)
                     s[0] = fma(wab * (T)0.75f, e0, s[0]);
                     s[0] = fma(wab * (T)0.25f, em, s[0]);
@@ -740,7 +750,7 @@ __device__ __forceinline__ void prolong_pass_v(const Dims& D, const Dims& Dc, in
                 }
             }
             for (int m = 0; m < 4; ++m) X[m] = X[m] + s[m];
-            st4(x + c0, X);
+            fm.st4x(x + c0, X);
             continue;
         }
 #pragma unroll
@@ -832,7 +842,8 @@ __device__ __forceinline__ void run_block(const BTask& tk, int colour, i64 first
                                                   decode(tk.v.D, c), [](const T* p) { return *p; });
             }
         else if (vec4(tk.v.D))
-            prolong_pass_v<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
+            prolong_pass_v<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride,
+                              P == PREC16 ? 2 : 4);
         else
             prolong_pass<T>(tk.v.D, tk.Dc, tk.v.cz, tk.v.ce, tk.v.cx, (const T*)tk.b, (T*)tk.x, first, stride);
     } else if constexpr (OP == BOP_RESID) {   // FP64 outer residual on the fine level (+ FP32 cast)
