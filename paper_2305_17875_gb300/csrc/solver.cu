@@ -3,6 +3,7 @@
 // shells, the outer iteration captured as one CUDA graph.  A single solve is
 // the batch of one.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -1167,7 +1168,7 @@ mg_status plan_loop(Plan* pl, SolveState* S, bool* unavailable) {
             return MG_OK;
         }
     }
-    int most = 0;
+    long long most = 0;
     for (int i = 0; i < n; ++i) {
         const SolveState& q = S[i];
         LoopShell& L = pl->h_loop[i];
@@ -1180,12 +1181,12 @@ mg_status plan_loop(Plan* pl, SolveState* S, bool* unavailable) {
         L.max_iters = pl->hs[i]->opts.max_iters;
         L.done = q.done ? 1 : 0;
         L.why = LOOP_RUN;
-        if (!q.done) most = std::max(most, L.max_iters - q.it);
+        if (!q.done) most = std::max(most, (long long)L.max_iters - q.it);
     }
     // never binds: every pass moves each active shell one iteration toward
     // its limit
     pl->h_ctl[0] = 0;
-    pl->h_ctl[1] = most + 1;
+    pl->h_ctl[1] = (int)std::min<long long>(most + 1, INT_MAX);
     cudaStream_t s = pl->stream;
     CK(cudaMemcpyAsync(pl->d_loop, pl->h_loop, sizeof(LoopShell) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(pl->d_ctl, pl->h_ctl, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
