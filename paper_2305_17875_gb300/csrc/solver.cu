@@ -671,16 +671,17 @@ mg_status upload_call(Plan* pl, const Program& P) {
     return MG_OK;
 }
 
-// The iteration's clock buffer; a new one retires the graph that holds the
+// The iteration's clock buffer; a new one retires the graphs that hold the
 // old address.
 mg_status iter_stamps(Plan* pl) {
-    unsigned long long* before = pl->d_stamp_it;
-    CKS(stamp_buffers(pl->iter.launches.size(), &pl->d_stamp_it, &pl->h_stamp_it, &pl->stamp_it_cap));
-    if (pl->d_stamp_it != before && pl->gexec) {
-        CK(cudaStreamSynchronize(pl->stream));
-        cudaGraphExecDestroy(pl->gexec);
+    if (pl->iter.launches.size() > pl->stamp_it_cap && (pl->gexec || pl->lexec)) {
+        CK(cudaStreamSynchronize(pl->stream));   // no graph in flight uses the old buffer
+        if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+        if (pl->lexec) cudaGraphExecDestroy(pl->lexec);
         pl->gexec = nullptr;
+        pl->lexec = nullptr;
     }
+    CKS(stamp_buffers(pl->iter.launches.size(), &pl->d_stamp_it, &pl->h_stamp_it, &pl->stamp_it_cap));
     return MG_OK;
 }
 
