@@ -67,3 +67,16 @@ def test_traffic_lookup_scales_a_half_size_capture():
     if not e or e.get("source_hash") != bench.kernel_source_hash(tuple(e.get("sources", bench.BATCH_SOURCES))):
         pytest.skip("no capture for the current kernel sources")
     assert bench.ncu_traffic("single_oblate_256", "fp32", "smooth0") == pytest.approx(8 * e["dram_bytes_per_launch"])
+
+
+def test_event_cross_check_uses_the_same_bytes():
+    """The CUDA-event figure beside the clocks: the same algorithmic bytes over
+    the events' mean launch time."""
+    roof = {"algorithmic_bytes_per_launch": 50.0e6, "peak": 5000.0}
+    prof = {"events": {"smooth0": {"avg_ms": 0.02}, "residual": {"avg_ms": None}}}
+    bench.add_event_check(roof, prof, "smooth0")
+    assert roof["avg_launch_ms_events"] == 0.02
+    assert roof["frac_events"] == pytest.approx(50.0e6 / 20e-6 / 1e9 / 5000.0)
+    roof2 = {"algorithmic_bytes_per_launch": 1.0, "peak": 1.0}
+    bench.add_event_check(roof2, prof, "residual")    # no events figure: nothing added
+    assert "frac_events" not in roof2
